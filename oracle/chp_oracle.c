@@ -1,0 +1,312 @@
+/*
+ * chp_oracle.c -- plain, unpacked CPU stabilizer-tableau simulator.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * CPU-baseline / reference legs of bench.py load this file's library.  The
+ * product path (the CUDA library) never calls it, and the two share no code.
+ *
+ * What it computes: the Clifford backend of Qibo 0.2.9 (arXiv:2408.00384,
+ * section "Simulation of Clifford circuits") is built on the phase-space
+ * (stabilizer tableau) formalism of Aaronson & Gottesman, "Improved
+ * simulation of stabilizer circuits", PRA 70, 052328 (2004).  This file
+ * restates that algorithm (AG Sec. III) one bit per byte, with no packing,
+ * blocking or fusion:
+ *
+ *   rows 0..n-1   destabilizers, rows n..2n-1 stabilizers, row 2n scratch;
+ *   row i is the Pauli (-1)^r_i  (x) P(x_ij, z_ij),
+ *   P(0,0)=I, P(1,0)=X, P(1,1)=Y, P(0,1)=Z.
+ *
+ * Gates: CNOT, H and phase S are AG's three update rules.  Every other gate
+ * is built from them as a product of conjugations (Z = S S, X = H Z H,
+ * Y = X Z up to a global phase, S^dagger = S S S, CZ = H_b CNOT H_b,
+ * SWAP = three CNOTs), so only AG's rules are trusted here.
+ *
+ * Measurement of Z_a: AG's two cases.  The random outcome bit comes from
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+ * easy as 1, 2, 3", SC'11), written here from that paper's definition.
+ *
+ * Readings where the algorithm leaves a choice (listed again in the design doc):
+ *  - pivot p is the smallest stabilizer row with x_pa = 1;
+ *  - the destabilizer row p-n is not passed through rowsum, because AG replace
+ *    it by row p right afterwards (its rowsum would be an anticommuting
+ *    product that is discarded);
+ *  - the k-th measurement op of a (circuit, shot) draws Philox counter
+ *    (k, shot, circuit_id lo, circuit_id hi) under key (seed lo, seed hi) and
+ *    uses bit 0 of output word 0, whether or not the outcome is random;
+ *  - MZR = measure, then apply X_a when the outcome is 1.
+ *
+ * Parity pins: gate rules and g against explicit Pauli matrices; the whole
+ * simulator against brute-force state vectors (n <= 10), known states and the
+ * symplectic invariant; Philox against the Random123 known-answer vectors.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL (-1)
+#define ORC_ERANGE (-2)
+#define ORC_ENOMEM (-3)
+#define ORC_EPHASE (-8) /* rowsum met an odd exponent: not a commuting product */
+
+typedef struct {
+  int32_t n;
+  int64_t rows; /* 2n + 1: the last row is AG's scratch row */
+  uint8_t *x, *z, *r;
+} orc_tab;
+
+/* storage: element (row i, qubit j) at [j * rows + i] */
+#define XB(t, i, j) ((t)->x[(int64_t)(j) * (t)->rows + (i)])
+#define ZB(t, i, j) ((t)->z[(int64_t)(j) * (t)->rows + (i)])
+
+void orc_reset(orc_tab *t) {
+  int64_t cells = (int64_t)t->n * t->rows;
+  memset(t->x, 0, (size_t)cells);
+  memset(t->z, 0, (size_t)cells);
+  memset(t->r, 0, (size_t)t->rows);
+  /* |0^n>: destabilizer i = X_i, stabilizer n+i = Z_i, all signs + */
+  for (int32_t i = 0; i < t->n; i++) {
+    XB(t, i, i) = 1;
+    ZB(t, t->n + i, i) = 1;
+  }
+}
+
+orc_tab *orc_new(int32_t n) {
+  if (n < 1) return NULL;
+  orc_tab *t = (orc_tab *)calloc(1, sizeof(orc_tab));
+  if (!t) return NULL;
+  t->n = n;
+  t->rows = 2 * (int64_t)n + 1;
+  int64_t cells = (int64_t)n * t->rows;
+  t->x = (uint8_t *)malloc((size_t)cells);
+  t->z = (uint8_t *)malloc((size_t)cells);
+  t->r = (uint8_t *)malloc((size_t)t->rows);
+  if (!t->x || !t->z || !t->r) {
+    free(t->x); free(t->z); free(t->r); free(t);
+    return NULL;
+  }
+  orc_reset(t);
+  return t;
+}
+
+void orc_free(orc_tab *t) {
+  if (!t) return;
+  free(t->x); free(t->z); free(t->r); free(t);
+}
+
+int32_t orc_n(const orc_tab *t) { return t->n; }
+
+/* ---- AG's three gate rules, for every row i in [0, 2n) ---------------- */
+
+void orc_cnot(orc_tab *t, int32_t a, int32_t b) {
+  for (int64_t i = 0; i < 2 * (int64_t)t->n; i++) {
+    uint8_t xa = XB(t, i, a), za = ZB(t, i, a), xb = XB(t, i, b), zb = ZB(t, i, b);
+    t->r[i] ^= (uint8_t)(xa & zb & (xb ^ za ^ 1));
+    XB(t, i, b) = (uint8_t)(xb ^ xa);
+    ZB(t, i, a) = (uint8_t)(za ^ zb);
+  }
+}
+
+void orc_h(orc_tab *t, int32_t a) {
+  for (int64_t i = 0; i < 2 * (int64_t)t->n; i++) {
+    uint8_t xa = XB(t, i, a), za = ZB(t, i, a);
+    t->r[i] ^= (uint8_t)(xa & za);
+    XB(t, i, a) = za;
+    ZB(t, i, a) = xa;
+  }
+}
+
+void orc_s(orc_tab *t, int32_t a) {
+  for (int64_t i = 0; i < 2 * (int64_t)t->n; i++) {
+    uint8_t xa = XB(t, i, a), za = ZB(t, i, a);
+    t->r[i] ^= (uint8_t)(xa & za);
+    ZB(t, i, a) = (uint8_t)(za ^ xa);
+  }
+}
+
+/* ---- gates built from the three rules --------------------------------- */
+
+void orc_z(orc_tab *t, int32_t a) { orc_s(t, a); orc_s(t, a); }
+void orc_x(orc_tab *t, int32_t a) { orc_h(t, a); orc_z(t, a); orc_h(t, a); }
+void orc_y(orc_tab *t, int32_t a) { orc_z(t, a); orc_x(t, a); }
+void orc_sdg(orc_tab *t, int32_t a) { orc_s(t, a); orc_s(t, a); orc_s(t, a); }
+void orc_cz(orc_tab *t, int32_t a, int32_t b) { orc_h(t, b); orc_cnot(t, a, b); orc_h(t, b); }
+void orc_swap(orc_tab *t, int32_t a, int32_t b) {
+  orc_cnot(t, a, b); orc_cnot(t, b, a); orc_cnot(t, a, b);
+}
+
+/* ---- rowsum ------------------------------------------------------------ */
+
+/* AG's g: the power of i in P(x1,z1) * P(x2,z2). */
+int32_t orc_g(int32_t x1, int32_t z1, int32_t x2, int32_t z2) {
+  if (x1 == 0 && z1 == 0) return 0;
+  if (x1 == 1 && z1 == 1) return z2 - x2;
+  if (x1 == 1 && z1 == 0) return z2 * (2 * x2 - 1);
+  return x2 * (1 - 2 * z2); /* x1 == 0, z1 == 1 */
+}
+
+/* AG rowsum(h, i): row h := row i * row h.  Returns ORC_EPHASE (and leaves
+ * row h unchanged) when the exponent is odd, i.e. the rows anticommute. */
+int32_t orc_rowsum(orc_tab *t, int64_t h, int64_t i) {
+  int64_t sum = 2 * (int64_t)t->r[h] + 2 * (int64_t)t->r[i];
+  for (int32_t j = 0; j < t->n; j++)
+    sum += orc_g(XB(t, i, j), ZB(t, i, j), XB(t, h, j), ZB(t, h, j));
+  int64_t m = ((sum % 4) + 4) % 4;
+  if (m != 0 && m != 2) return ORC_EPHASE;
+  t->r[h] = (uint8_t)(m == 2);
+  for (int32_t j = 0; j < t->n; j++) {
+    XB(t, h, j) ^= XB(t, i, j);
+    ZB(t, h, j) ^= ZB(t, i, j);
+  }
+  return ORC_OK;
+}
+
+/* ---- Philox4x32-10 ----------------------------------------------------- */
+
+static void philox_round(uint32_t c[4], const uint32_t k[2]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  uint64_t p0 = (uint64_t)M0 * c[0];
+  uint64_t p1 = (uint64_t)M1 * c[2];
+  uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+  uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+  uint32_t n0 = hi1 ^ c[1] ^ k[0];
+  uint32_t n2 = hi0 ^ c[3] ^ k[1];
+  c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+}
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+  uint32_t k[2] = {key[0], key[1]};
+  for (int round = 0; round < 10; round++) {
+    if (round > 0) { k[0] += 0x9E3779B9u; k[1] += 0xBB67AE85u; }
+    philox_round(c, k);
+  }
+  memcpy(out, c, sizeof c);
+}
+
+/* outcome bit of measurement index k of (circuit_id, shot) under seed */
+int32_t orc_outcome_bit(uint64_t seed, uint64_t circuit_id, uint32_t shot, uint64_t k) {
+  uint32_t ctr[4] = {(uint32_t)k, shot, (uint32_t)circuit_id, (uint32_t)(circuit_id >> 32)};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t out[4];
+  orc_philox4x32_10(ctr, key, out);
+  return (int32_t)(out[0] & 1u);
+}
+
+/* ---- measurement (AG Sec. III) ----------------------------------------- */
+
+/* Measure Z_a with the pre-drawn bit `rbit` for the random case.  Returns the
+ * outcome (0/1) or a negative error; *deterministic is set to 1 or 0. */
+int32_t orc_measure(orc_tab *t, int32_t a, int32_t rbit, int32_t *deterministic) {
+  if (a < 0 || a >= t->n) return ORC_ERANGE;
+  const int64_t n = t->n;
+  int64_t p = -1;
+  for (int64_t i = n; i < 2 * n; i++)
+    if (XB(t, i, a)) { p = i; break; }
+  if (p >= 0) {
+    /* case 1: random outcome */
+    for (int64_t i = 0; i < 2 * n; i++) {
+      if (i == p || i == p - n || !XB(t, i, a)) continue;
+      int32_t rc = orc_rowsum(t, i, p);
+      if (rc != ORC_OK) return rc;
+    }
+    for (int32_t j = 0; j < t->n; j++) {
+      XB(t, p - n, j) = XB(t, p, j);
+      ZB(t, p - n, j) = ZB(t, p, j);
+      XB(t, p, j) = 0;
+      ZB(t, p, j) = 0;
+    }
+    t->r[p - n] = t->r[p];
+    ZB(t, p, a) = 1;
+    t->r[p] = (uint8_t)(rbit & 1);
+    if (deterministic) *deterministic = 0;
+    return rbit & 1;
+  }
+  /* case 2: deterministic outcome, via the scratch row 2n */
+  const int64_t s = 2 * n;
+  for (int32_t j = 0; j < t->n; j++) { XB(t, s, j) = 0; ZB(t, s, j) = 0; }
+  t->r[s] = 0;
+  for (int64_t i = 0; i < n; i++) {
+    if (!XB(t, i, a)) continue;
+    int32_t rc = orc_rowsum(t, s, i + n);
+    if (rc != ORC_OK) return rc;
+  }
+  if (deterministic) *deterministic = 1;
+  return t->r[s];
+}
+
+/* ---- gate-list driver ---------------------------------------------------
+ * Gate word: bits 63..56 op, 55..28 q1, 27..0 q2 (the library's format).
+ * Ops: 0 I, 1 X, 2 Y, 3 Z, 4 H, 5 S, 6 SDG, 7 CNOT, 8 CZ, 9 SWAP, 10 MZ,
+ * 11 MZR, 12 BARRIER.  Outcomes are appended to out[] (one byte each,
+ * program order); det[] (optional) gets 1 for deterministic outcomes.
+ * *meas_counter is the next measurement index and is advanced.  Returns the
+ * number of outcomes written, or a negative error. */
+int64_t orc_run(orc_tab *t, const uint64_t *gates, int64_t count, uint64_t seed,
+                uint64_t circuit_id, uint32_t shot, uint64_t *meas_counter,
+                uint8_t *out, int64_t out_cap, uint8_t *det) {
+  int64_t nout = 0;
+  for (int64_t gi = 0; gi < count; gi++) {
+    uint64_t g = gates[gi];
+    int32_t op = (int32_t)(g >> 56);
+    int64_t q1 = (int64_t)((g >> 28) & 0xFFFFFFFull);
+    int64_t q2 = (int64_t)(g & 0xFFFFFFFull);
+    int two = (op == 7 || op == 8 || op == 9);
+    if (op < 0 || op > 12) return ORC_EINVAL;
+    if (op != 12 && q1 >= t->n) return ORC_ERANGE;
+    if (two && (q2 >= t->n)) return ORC_ERANGE;
+    if (two && q1 == q2) return ORC_EINVAL;
+    int32_t a = (int32_t)q1, b = (int32_t)q2;
+    switch (op) {
+      case 0: case 12: break;
+      case 1: orc_x(t, a); break;
+      case 2: orc_y(t, a); break;
+      case 3: orc_z(t, a); break;
+      case 4: orc_h(t, a); break;
+      case 5: orc_s(t, a); break;
+      case 6: orc_sdg(t, a); break;
+      case 7: orc_cnot(t, a, b); break;
+      case 8: orc_cz(t, a, b); break;
+      case 9: orc_swap(t, a, b); break;
+      case 10: case 11: {
+        uint64_t k = (*meas_counter)++;
+        int32_t rbit = orc_outcome_bit(seed, circuit_id, shot, k);
+        int32_t d = 0;
+        int32_t m = orc_measure(t, a, rbit, &d);
+        if (m < 0) return m;
+        if (nout >= out_cap) return ORC_EINVAL;
+        out[nout] = (uint8_t)m;
+        if (det) det[nout] = (uint8_t)d;
+        nout++;
+        if (op == 11 && m == 1) orc_x(t, a);
+        break;
+      }
+      default: return ORC_EINVAL;
+    }
+  }
+  return nout;
+}
+
+/* ---- import / export: row-major unpacked bits, rows 0..2n-1 ------------ */
+
+void orc_get(const orc_tab *t, uint8_t *x, uint8_t *z, uint8_t *r) {
+  int64_t n = t->n;
+  for (int64_t i = 0; i < 2 * n; i++) {
+    for (int64_t j = 0; j < n; j++) {
+      x[i * n + j] = t->x[j * t->rows + i];
+      z[i * n + j] = t->z[j * t->rows + i];
+    }
+    r[i] = t->r[i];
+  }
+}
+
+void orc_set(orc_tab *t, const uint8_t *x, const uint8_t *z, const uint8_t *r) {
+  int64_t n = t->n;
+  for (int64_t i = 0; i < 2 * n; i++) {
+    for (int64_t j = 0; j < n; j++) {
+      t->x[j * t->rows + i] = x[i * n + j] & 1;
+      t->z[j * t->rows + i] = z[i * n + j] & 1;
+    }
+    t->r[i] = r[i] & 1;
+  }
+}

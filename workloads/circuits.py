@@ -1,0 +1,239 @@
+"""Seeded random Clifford circuits in the library's 64-bit gate-list format.
+
+Gate word (little-endian uint64):  bits 63..56 = op code, 55..28 = first qubit,
+27..0 = second qubit (zero for one-qubit ops).  Op codes are the interface
+values of the C-ABI (``include/tab.h``) and of the oracle's decoder; they are a
+data format, not part of either side's arithmetic.
+
+The workloads stand in for the paper's benchmark data set (uniformly random
+Cliffords, Section "Simulation of Clifford circuits", Fig. 2a), which is not
+available here.  Each random layer is:
+
+* one single-qubit gate on every qubit, H or S with probability 1/2 each;
+* a seeded random permutation pi of the qubits, paired as (pi[2k], pi[2k+1])
+  for k < n//2 with the first element as control; each pair is CNOT, or
+  (mixed mode) CNOT with probability 3/4 and CZ with probability 1/4.
+
+A ``TAB_BARRIER`` word separates the single-qubit and two-qubit sub-layers.
+Barriers are hints only: they never change results.
+"""
+
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+# ---- op codes (interface values) -------------------------------------------
+TAB_I, TAB_X, TAB_Y, TAB_Z, TAB_H, TAB_S, TAB_SDG = 0, 1, 2, 3, 4, 5, 6
+TAB_CNOT, TAB_CZ, TAB_SWAP = 7, 8, 9
+TAB_MZ, TAB_MZR, TAB_BARRIER = 10, 11, 12
+
+ONE_QUBIT = (TAB_I, TAB_X, TAB_Y, TAB_Z, TAB_H, TAB_S, TAB_SDG)
+TWO_QUBIT = (TAB_CNOT, TAB_CZ, TAB_SWAP)
+MEASURE = (TAB_MZ, TAB_MZR)
+
+OP_NAMES = {TAB_I: "I", TAB_X: "X", TAB_Y: "Y", TAB_Z: "Z", TAB_H: "H",
+            TAB_S: "S", TAB_SDG: "SDG", TAB_CNOT: "CNOT", TAB_CZ: "CZ",
+            TAB_SWAP: "SWAP", TAB_MZ: "MZ", TAB_MZR: "MZR",
+            TAB_BARRIER: "BARRIER"}
+
+CONFIG_SEED = 240800384   # fixed generator seed of every workload family
+PHILOX_SEED = 1           # fixed outcome seed of every workload family
+
+_MASK28 = (1 << 28) - 1
+
+
+def encode(op, q1=0, q2=0) -> np.ndarray:
+    """Pack op codes and qubit indices (scalars or arrays) into gate words."""
+    op = np.asarray(op, dtype=np.uint64)
+    q1 = np.asarray(q1, dtype=np.uint64)
+    q2 = np.asarray(q2, dtype=np.uint64)
+    return (op << np.uint64(56)) | ((q1 & np.uint64(_MASK28)) << np.uint64(28)) \
+        | (q2 & np.uint64(_MASK28))
+
+
+def decode(gates: np.ndarray):
+    """Split gate words into (op, q1, q2) int64 arrays."""
+    g = np.asarray(gates, dtype=np.uint64)
+    op = (g >> np.uint64(56)).astype(np.int64)
+    q1 = ((g >> np.uint64(28)) & np.uint64(_MASK28)).astype(np.int64)
+    q2 = (g & np.uint64(_MASK28)).astype(np.int64)
+    return op, q1, q2
+
+
+def splitmix64(x: int) -> int:
+    """SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014)."""
+    m = (1 << 64) - 1
+    x = (x + 0x9E3779B97F4A7C15) & m
+    x = ((x ^ (x >> 30)) * 0xBF58476D1CE4E5B9) & m
+    x = ((x ^ (x >> 27)) * 0x94D049BB133111EB) & m
+    return x ^ (x >> 31)
+
+
+def circuit_seed(config_index: int, c: int) -> int:
+    """Generator seed of circuit ``c`` of a workload family."""
+    return splitmix64((CONFIG_SEED + 7919 * config_index) ^ c)
+
+
+@dataclasses.dataclass
+class Circuit:
+    """One synthetic circuit: its gate words and what they contain."""
+    n: int
+    gates: np.ndarray          # uint64 gate words, program order
+    n_gates: int               # Clifford gate ops (barriers and measurements excluded)
+    n_meas: int                # measurement ops per shot
+    shots: int = 1
+    circuit_id: int = 0
+    depth: int = 0
+
+    @property
+    def n_words(self) -> int:
+        return int(self.gates.size)
+
+
+def random_layer_circuit(n: int, depth: int, seed: int, *, mix_cz: bool = True,
+                         meas_every: int = 0, meas_frac: float = 0.0,
+                         reset: bool = True, final_measure: bool = True,
+                         barriers: bool = True, circuit_id: int = 0,
+                         shots: int = 1) -> Circuit:
+    """Random-layer Clifford circuit (module docstring gives the layer).
+
+    ``meas_every``/``meas_frac``: after every ``meas_every``-th layer measure
+    floor(meas_frac * n) distinct uniformly drawn qubits, in ascending order,
+    with reset (``TAB_MZR``) when ``reset`` is true.  ``final_measure`` appends
+    ``TAB_MZ`` on every qubit in ascending order.
+    """
+    if n < 1:
+        raise ValueError("n must be >= 1")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    one_q = np.where(rng.integers(0, 2, size=(depth, n)) == 0, TAB_H, TAB_S)
+    perms = np.argsort(rng.random((depth, n)), axis=1, kind="stable")
+    npairs = n // 2
+    if mix_cz:
+        two_q = np.where(rng.random((depth, npairs)) < 0.75, TAB_CNOT, TAB_CZ)
+    else:
+        two_q = np.full((depth, npairs), TAB_CNOT)
+    n_rounds = depth // meas_every if meas_every else 0
+    k_round = int(math.floor(meas_frac * n)) if meas_every else 0
+    rounds = []
+    for _ in range(n_rounds):
+        rounds.append(np.sort(rng.choice(n, size=k_round, replace=False)))
+
+    qubits = np.arange(n, dtype=np.int64)
+    bar = encode(TAB_BARRIER) if barriers else None
+    parts: List[np.ndarray] = []
+    n_meas = 0
+    mop = TAB_MZR if reset else TAB_MZ
+    for d in range(depth):
+        parts.append(encode(one_q[d], qubits, 0))
+        if barriers:
+            parts.append(bar.reshape(1))
+        if npairs:
+            p = perms[d]
+            parts.append(encode(two_q[d], p[0:2 * npairs:2], p[1:2 * npairs:2]))
+            if barriers:
+                parts.append(bar.reshape(1))
+        if meas_every and (d + 1) % meas_every == 0 and k_round:
+            qs = rounds[(d + 1) // meas_every - 1]
+            parts.append(encode(np.full(qs.size, mop), qs, 0))
+            n_meas += int(qs.size)
+    if final_measure:
+        parts.append(encode(np.full(n, TAB_MZ), qubits, 0))
+        n_meas += n
+    gates = np.concatenate(parts) if parts else np.zeros(0, np.uint64)
+    return Circuit(n=n, gates=gates, n_gates=depth * (n + npairs),
+                   n_meas=n_meas, shots=shots, circuit_id=circuit_id,
+                   depth=depth)
+
+
+# ---- the five workload families ---------------------------------------------
+
+def config1(seed_index: int = 0) -> Circuit:
+    """n=10, 20 layers (H/S per qubit, 5 CNOT pairs), final MZ on all 10."""
+    return random_layer_circuit(10, 20, circuit_seed(1, seed_index), mix_cz=False)
+
+
+def config2(seed_index: int = 0, depth: int = 1000, n: int = 1000) -> Circuit:
+    """n=1000, 1000 layers (CNOT:CZ = 3:1), final MZ on all qubits."""
+    return random_layer_circuit(n, depth, circuit_seed(2, seed_index))
+
+
+def config3(seed_index: int = 0, n: int = 10000, depth: int = 100) -> Circuit:
+    """n=10,000, 100 layers, MZR on floor(n/10) random qubits every 10 layers."""
+    return random_layer_circuit(n, depth, circuit_seed(3, seed_index),
+                                meas_every=10, meas_frac=0.10, reset=True,
+                                final_measure=False)
+
+
+def config4_shapes(m: int = 4096, n_lo: int = 16, n_hi: int = 512,
+                   shots_hi: int = 64):
+    """(n, shots) of the batched family: n ~ U{n_lo..n_hi}, shots ~ U{1..shots_hi}."""
+    rng = np.random.Generator(np.random.PCG64(circuit_seed(4, 1 << 40)))
+    ns = rng.integers(n_lo, n_hi + 1, size=m)
+    shots = rng.integers(1, shots_hi + 1, size=m)
+    return ns.astype(np.int64), shots.astype(np.int64)
+
+
+def config4(m: int = 4096, n_lo: int = 16, n_hi: int = 512, shots_hi: int = 64,
+            only: Optional[List[int]] = None) -> List[Circuit]:
+    """Batched family: m circuits, depth n, final MZ on all qubits, 1..64 shots."""
+    ns, shots = config4_shapes(m, n_lo, n_hi, shots_hi)
+    idx = range(m) if only is None else only
+    return [random_layer_circuit(int(ns[c]), int(ns[c]), circuit_seed(4, c),
+                                 circuit_id=c, shots=int(shots[c]))
+            for c in idx]
+
+
+def config5_request(c: int, n_lo: int = 50, n_hi: int = 5000) -> Circuit:
+    """Served family request c: n log-uniform in [n_lo, n_hi], depth 2n,
+    MZR on floor(n/20) qubits every 20 layers, then final MZ on all qubits."""
+    rng = np.random.Generator(np.random.PCG64(circuit_seed(5, 1 << 40 | c)))
+    n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+    return random_layer_circuit(n, 2 * n, circuit_seed(5, c), meas_every=20,
+                                meas_frac=0.05, reset=True, final_measure=True,
+                                circuit_id=c)
+
+
+def poisson_arrivals(rate_hz: float, count: int, seed: int = CONFIG_SEED):
+    """Arrival times (seconds from 0) of a Poisson stream with the given rate."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.cumsum(rng.exponential(1.0 / rate_hz, size=count))
+
+
+def random_clifford_ops(n: int, count: int, seed: int, *, measure_p: float = 0.0,
+                        reset_p: float = 0.0, ops=None) -> np.ndarray:
+    """Unstructured random gate list over every op (edge-case tests).
+
+    Each entry is a uniformly drawn op from ``ops`` on uniformly drawn distinct
+    qubits; with probability ``measure_p`` an MZ and ``reset_p`` an MZR.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if ops is None:
+        ops = list(ONE_QUBIT) + (list(TWO_QUBIT) if n >= 2 else [])
+    out = np.zeros(count, dtype=np.uint64)
+    for i in range(count):
+        u = rng.random()
+        if u < measure_p:
+            out[i] = encode(TAB_MZ, int(rng.integers(0, n)), 0)
+            continue
+        if u < measure_p + reset_p:
+            out[i] = encode(TAB_MZR, int(rng.integers(0, n)), 0)
+            continue
+        op = int(ops[int(rng.integers(0, len(ops)))])
+        if op in TWO_QUBIT:
+            a, b = rng.choice(n, size=2, replace=False)
+            out[i] = encode(op, int(a), int(b))
+        else:
+            out[i] = encode(op, int(rng.integers(0, n)), 0)
+    return out
+
+
+def count_ops(gates: np.ndarray):
+    """(gate ops, measurement ops) in a gate list; barriers are not counted."""
+    op, _, _ = decode(gates)
+    meas = int(np.isin(op, MEASURE).sum())
+    gates_n = int(np.isin(op, ONE_QUBIT + TWO_QUBIT).sum())
+    return gates_n, meas
