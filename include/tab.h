@@ -1,0 +1,226 @@
+/*
+ * tab.h -- C ABI of libtab: a GB300 (sm_103a) stabilizer-tableau simulator.
+ *
+ * The operation is the Clifford-circuit backend of Qibo 0.2.9 (arXiv:2408.00384,
+ * section "Simulation of Clifford circuits"), which is built on the phase-space
+ * (stabilizer tableau) formalism of Aaronson & Gottesman, PRA 70, 052328 (2004),
+ * Sec. III: an n-qubit state is held as n destabilizer and n stabilizer rows of
+ * X|Z bits plus a sign bit; a Clifford gate updates one or two bit columns of
+ * every row; a Z measurement either draws a random outcome (pivot row, then
+ * rowsum of the pivot into every row that anticommutes with Z_a) or reads a
+ * deterministic one (product of stabilizer rows selected by the destabilizers).
+ *
+ * Conventions shared by every call:
+ *  - Return value: TAB_OK (0) on success, a negative tab_status on error; the
+ *    message of the last error on the calling thread is tab_last_error().
+ *  - Qubit indices are 0-based.  A tableau has 2n rows: rows 0..n-1 are the
+ *    destabilizers, rows n..2n-1 the stabilizers; row i is the Pauli
+ *    (-1)^r_i (x)_j P(x_ij, z_ij) with P(0,0)=I, P(1,0)=X, P(1,1)=Y, P(0,1)=Z.
+ *  - Host buffers passed in are borrowed for the duration of the call only.
+ *    Device memory belongs to the handle, except with tab_create_on, where the
+ *    caller owns it and must keep it alive until tab_destroy.
+ *  - Work is enqueued on the handle's CUDA stream (default: the legacy default
+ *    stream) and runs asynchronously unless a call says it synchronizes.
+ *    Device-side errors (a wait that timed out, a phase-parity violation) are
+ *    latched on the device and reported by the next synchronizing call as
+ *    TAB_ETIMEOUT / TAB_EDEVICE.
+ *  - Random outcomes: the k-th measurement op (k counted from 0 over every
+ *    MZ/MZR of the handle since tab_set_rng, deterministic ones included) of
+ *    (circuit_id, shot) uses bit 0 of word 0 of Philox4x32-10 (Salmon et al.,
+ *    SC'11) with counter (k, shot, circuit_id lo, circuit_id hi) and key
+ *    (seed lo, seed hi).  The bit is used only when the outcome is random.
+ *  - Pivot choice: the smallest stabilizer row with x_pa = 1.  These two
+ *    choices make every outcome and every tableau bit reproducible.
+ */
+#ifndef TAB_H_
+#define TAB_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tab_s *tab_t;
+
+/* Gate word: bits 63..56 op, 55..28 first qubit, 27..0 second qubit (0 for
+ * one-qubit ops).  A gate list is in program order.  The library may reorder
+ * gates that act on disjoint qubits (they commute), which never changes a
+ * result.  TAB_BARRIER is a hint with no effect on results. */
+typedef uint64_t tab_gate;
+
+enum tab_op {
+  TAB_I = 0, TAB_X = 1, TAB_Y = 2, TAB_Z = 3, TAB_H = 4, TAB_S = 5, TAB_SDG = 6,
+  TAB_CNOT = 7, /* first qubit is the control */
+  TAB_CZ = 8, TAB_SWAP = 9,
+  TAB_MZ = 10,  /* measure Z; outcome appended to the handle's outcome log */
+  TAB_MZR = 11, /* measure Z, then apply X when the outcome is 1 (reset to |0>) */
+  TAB_BARRIER = 12
+};
+
+enum tab_status {
+  TAB_OK = 0,
+  TAB_EINVAL = -1,   /* malformed argument (unknown op, q1 == q2, null pointer) */
+  TAB_ERANGE = -2,   /* qubit index >= n, or n outside [1, TAB_MAX_QUBITS] */
+  TAB_ENOMEM = -3,   /* device or host allocation failed, or caller memory too small */
+  TAB_ECUDA = -4,    /* a CUDA runtime call failed */
+  TAB_EDEVICE = -5,  /* a kernel reported an internal inconsistency */
+  TAB_ETIMEOUT = -6, /* a device-side wait exceeded its limit; the handle is unusable */
+  TAB_ESTATE = -7    /* call not valid in the handle's state (e.g. capacity exceeded) */
+};
+
+#define TAB_MAX_QUBITS 16384
+#define TAB_BATCH_MAX_QUBITS 640 /* largest n of the single-CTA engine */
+
+static inline tab_gate tab_make_gate(uint32_t op, uint32_t q1, uint32_t q2) {
+  return ((uint64_t)op << 56) | ((uint64_t)(q1 & 0xFFFFFFFu) << 28) | (uint64_t)(q2 & 0xFFFFFFFu);
+}
+
+/* ---- handles (Aaronson-Gottesman Sec. III: the tableau) ------------------ */
+
+/* Bytes of device memory tab_create_on needs for n qubits (tableau planes plus
+ * the handle's measurement workspace).  0 if n is out of range. */
+size_t tab_bytes_required(int32_t n);
+
+/* Allocate a tableau for n qubits (1 <= n <= TAB_MAX_QUBITS) in |0^n>
+ * (destabilizer i = +X_i, stabilizer i = +Z_i).  *out receives the handle.
+ * TAB_ERANGE for bad n, TAB_ENOMEM if device memory runs out. */
+int tab_create(int32_t n, tab_t *out);
+
+/* As tab_create, but the tableau and workspace live in caller-owned device
+ * memory dev_ptr of at least tab_bytes_required(n) bytes, 256-byte aligned
+ * (e.g. a torch uint8 CUDA tensor).  cuda_stream (a cudaStream_t, may be NULL)
+ * becomes the handle's stream.  The memory must outlive the handle. */
+int tab_create_on(int32_t n, void *dev_ptr, size_t bytes, void *cuda_stream, tab_t *out);
+
+/* Release the handle (and its device memory unless caller-owned).  Waits for
+ * the handle's pending work.  NULL is accepted. */
+int tab_destroy(tab_t h);
+
+int tab_num_qubits(tab_t h, int32_t *n);
+
+/* Bind the handle to a CUDA stream (cudaStream_t; NULL = default stream).
+ * Later work is enqueued there; earlier work is not moved. */
+int tab_set_stream(tab_t h, void *cuda_stream);
+
+/* Set (seed, circuit_id, shot) of the outcome stream and reset the
+ * measurement counter k to 0.  Defaults: seed 1, circuit 0, shot 0. */
+int tab_set_rng(tab_t h, uint64_t seed, uint64_t circuit_id, uint32_t shot);
+
+/* Put the tableau back to |0^n> (Sec. III initial tableau); clears the
+ * outcome log; keeps the RNG settings but resets k to 0.  Asynchronous. */
+int tab_reset(tab_t h);
+
+/* ---- gates and measurements --------------------------------------------- */
+
+/* Apply `count` gate words (host memory, program order, TAB_MZ/TAB_MZR
+ * allowed) to the tableau.  Every qubit index is validated on the host before
+ * anything is launched (TAB_ERANGE / TAB_EINVAL: nothing is applied).  Gates
+ * are the column updates of AG Sec. III (CNOT, H, S) and their products;
+ * measurements are AG's two cases, their outcomes appended to the handle's
+ * outcome log (tab_read_outcomes).  Asynchronous: the host list is copied
+ * before the call returns. */
+int tab_apply(tab_t h, const tab_gate *gates, int64_t count);
+
+/* A gate list compiled once (validated, grouped into layers of disjoint gates,
+ * uploaded to device memory) and replayable on any handle with the same n. */
+typedef struct tab_prog_s *tab_prog_t;
+
+int tab_prog_create(int32_t n, const tab_gate *gates, int64_t count, tab_prog_t *out);
+int tab_prog_destroy(tab_prog_t p);
+/* number of gate ops, measurement ops and gate layers in the program */
+int tab_prog_info(tab_prog_t p, int64_t *n_gates, int64_t *n_meas, int64_t *n_layers);
+/* Run a compiled program on the handle (asynchronous; nothing is copied from
+ * the host).  TAB_EINVAL if the program's n differs from the handle's. */
+int tab_run(tab_t h, tab_prog_t p);
+
+/* Measure Z on k qubits in the given order (AG Sec. III), with `seed` as the
+ * Philox key for this call (circuit_id, shot and k continue from the handle).
+ * Synchronizes; out_bits[i] receives outcome i as 0 or 1.  Outcomes are also
+ * appended to the outcome log. */
+int tab_measure(tab_t h, const int32_t *qubits, int32_t k, uint64_t seed, uint8_t *out_bits);
+
+/* As tab_measure with the handle's seed, without synchronizing: outcome i is
+ * written, as one byte, to dev_out_bits[i] (device memory, >= k bytes, kept
+ * alive by the caller until the stream reaches this point). */
+int tab_measure_async(tab_t h, const int32_t *qubits, int32_t k, uint8_t *dev_out_bits);
+
+/* Synchronize and copy the outcome log (every outcome since the last
+ * tab_reset / tab_clear_outcomes, in program order, one byte each) into out
+ * (capacity max).  *count receives the number of outcomes in the log. */
+int tab_read_outcomes(tab_t h, uint8_t *out, int64_t max, int64_t *count);
+int tab_clear_outcomes(tab_t h);
+
+/* Execution engine for tab_apply / tab_run / tab_measure on this handle.
+ * TAB_ENGINE_SINGLE_CTA keeps the whole tableau in one CTA's shared memory
+ * (n <= TAB_BATCH_MAX_QUBITS; one launch per call); TAB_ENGINE_GRID spreads
+ * it over the GPU (a fused row-slab gate kernel per gate run, a cooperative
+ * measurement kernel per measurement run); TAB_ENGINE_AUTO (default) picks by
+ * size.  Results are bit-identical across engines.  TAB_ERANGE if
+ * SINGLE_CTA is asked for n > TAB_BATCH_MAX_QUBITS. */
+enum tab_engine { TAB_ENGINE_AUTO = 0, TAB_ENGINE_SINGLE_CTA = 1, TAB_ENGINE_GRID = 2 };
+int tab_set_engine(tab_t h, int engine);
+
+/* Number of CUDA kernels this handle has launched since creation. */
+int tab_kernel_launches(tab_t h, int64_t *count);
+
+/* ---- state transfer (checkpoint / oracle comparison) --------------------- */
+
+/* Synchronize and unpack the tableau into row-major host arrays: x and z of
+ * 2n*n bytes (row i, qubit j at [i*n + j]), r of 2n bytes; values 0/1. */
+int tab_export(tab_t h, uint8_t *x, uint8_t *z, uint8_t *r);
+
+/* Load a tableau from the same layout (values are taken mod 2) and set the
+ * measurement counter k.  The rows must form a valid tableau (symplectic);
+ * this is not checked.  Synchronizes. */
+int tab_import(tab_t h, const uint8_t *x, const uint8_t *z, const uint8_t *r,
+               uint64_t meas_counter);
+
+/* Wait for the handle's work; returns latched device errors. */
+int tab_sync(tab_t h);
+
+/* Message of the last error on this thread ("" if none). */
+const char *tab_last_error(void);
+
+/* ---- batched runs: many independent circuits and shots, one launch ------- */
+
+typedef struct {
+  int32_t n;              /* qubits, 1..TAB_BATCH_MAX_QUBITS */
+  const tab_gate *gates;  /* host gate list, program order */
+  int64_t n_gates;        /* number of gate words */
+  int32_t shots;          /* >= 1 independent runs from |0^n> */
+  uint64_t circuit_id;    /* Philox counter words 2..3 */
+} tab_circuit;
+
+/* Run m circuits, each for its number of shots, with Philox key `seed`.
+ * Outcomes of (circuit c, shot s) go, in program order, to
+ * out_bits[out_offsets[c] + s * n_meas(c) ...] where n_meas(c) counts the
+ * MZ/MZR ops of circuit c; out_offsets may be NULL, meaning circuits are
+ * packed back to back in order.  All shots of a circuit share the gates
+ * before its first measurement (gates do not depend on outcomes).  Uses the
+ * current CUDA device and the legacy default stream; synchronizes. */
+int tab_batch_run(const tab_circuit *circuits, int32_t m, uint64_t seed,
+                  uint8_t *out_bits, const int64_t *out_offsets);
+
+/* A batch compiled once (gate lists validated, layered, uploaded, work items
+ * sorted by cost) and replayable with tab_batch_exec; replays are captured in
+ * a CUDA graph on first use. */
+typedef struct tab_batch_s *tab_batch_t;
+
+int tab_batch_create(const tab_circuit *circuits, int32_t m, tab_batch_t *out);
+int tab_batch_destroy(tab_batch_t b);
+/* totals: gate ops (once per circuit), measurement ops (over all shots),
+ * outcome bytes needed */
+int tab_batch_info(tab_batch_t b, int64_t *n_gates, int64_t *n_meas, int64_t *out_bytes);
+/* Enqueue one run of the whole batch on cuda_stream: outcomes (packed back to
+ * back per circuit and shot) go to dev_out (device memory, >= out_bytes). */
+int tab_batch_exec(tab_batch_t b, uint64_t seed, uint8_t *dev_out, void *cuda_stream);
+/* Number of kernels one tab_batch_exec launches. */
+int tab_batch_launches(tab_batch_t b, int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TAB_H_ */

@@ -1,0 +1,367 @@
+// batch.cpp -- batched runs of many independent circuits and shots in one
+// persistent launch (tab_batch_* in include/tab.h).
+//
+// Packing: every circuit's gate list is compiled (validated, ASAP-layered)
+// and the programs are concatenated into one op table, one layer-offset table
+// and one segment table.  Work items are one shared-prefix item per circuit
+// (the gates before its first measurement, run once) and one item per
+// (circuit, shot) (the rest of the circuit with that shot's outcome stream).
+// Items are ordered prefix-first, each class by decreasing estimated cost, so
+// the persistent CTAs pull the long items first and the tail stays short.
+// A replay is a CUDA graph: a memset of the queue / ready flags / error word
+// and the kernel, whose (seed, output) arguments are updated in place.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "sct.h"
+#include "tab_internal.h"
+
+using namespace tab;
+
+#define CUB(call)                                                             \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      set_error("%s failed: %s", #call, cudaGetErrorString(e_));              \
+      return TAB_ECUDA;                                                       \
+    }                                                                         \
+  } while (0)
+
+struct tab_batch_s {
+  int m = 0;
+  int64_t n_gates = 0, n_meas = 0, out_bytes = 0;
+  int max_n = 1;
+  size_t smem = 0;
+  int ctas = 1;
+  int nitems = 0;
+  // device
+  void* dmem = nullptr;
+  BatchArgs args{};
+  void* ctl = nullptr;  // queue counter, ready flags, error word (zeroed per run)
+  size_t ctl_bytes = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraphNode_t knode = nullptr;
+};
+
+namespace {
+
+size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offsets,
+                tab_batch_s* B) {
+  if (m < 0 || (m > 0 && !circuits)) {
+    set_error("bad circuit array");
+    return TAB_EINVAL;
+  }
+  std::vector<uint32_t> ops, layer_off;
+  std::vector<Seg> segs;
+  std::vector<BatchCirc> circs((size_t)m);
+  std::vector<double> pre_cost((size_t)m), shot_cost((size_t)m);
+  uint64_t img_words = 0;
+  int64_t out_packed = 0, out_max = 0;
+  for (int32_t c = 0; c < m; ++c) {
+    const tab_circuit& tc = circuits[c];
+    if (tc.n < 1 || tc.n > TAB_BATCH_MAX_QUBITS) {
+      set_error("circuit %d: n=%d outside [1, %d]", c, tc.n, TAB_BATCH_MAX_QUBITS);
+      return TAB_ERANGE;
+    }
+    if (tc.shots < 1) {
+      set_error("circuit %d: shots=%d < 1", c, tc.shots);
+      return TAB_EINVAL;
+    }
+    HostProgram hp;
+    int rc = build_program(tc.n, tc.gates, tc.n_gates, &hp);
+    if (rc != TAB_OK) {
+      char msg[600];
+      snprintf(msg, sizeof msg, "circuit %d: %s", c, tab_last_error());
+      set_error("%s", msg);
+      return rc;
+    }
+    const uint32_t op_base = (uint32_t)ops.size(), lo_base = (uint32_t)layer_off.size();
+    BatchCirc& bc = circs[(size_t)c];
+    bc.n = tc.n;
+    bc.shots = tc.shots;
+    bc.seg_begin = (uint32_t)segs.size();
+    bc.n_prefix = (!hp.segs.empty() && hp.segs[0].kind == 0) ? 1u : 0u;
+    bc.n_meas = (uint32_t)hp.n_meas;
+    bc.cid = tc.circuit_id;
+    bc.img_off = img_words;
+    img_words += sct_image_words(tc.n);
+    const int64_t span = (int64_t)tc.shots * hp.n_meas;
+    bc.out_off = (uint64_t)(out_offsets ? out_offsets[c] : out_packed);
+    out_packed += span;
+    out_max = std::max<int64_t>(out_max, (int64_t)bc.out_off + span);
+    ops.insert(ops.end(), hp.ops.begin(), hp.ops.end());
+    for (uint32_t v : hp.layer_off) layer_off.push_back(v + op_base);
+    double pre = 0, rest = 0;
+    const double wc = 2.0 * ((tc.n + 31) / 32);
+    for (size_t i = 0; i < hp.segs.size(); ++i) {
+      Seg s = hp.segs[i];
+      const double len = (double)(s.op_end - s.op_begin);
+      if (s.kind == 0) (i == 0 && bc.n_prefix ? pre : rest) += len * wc + (s.layer_end - s.layer_begin) * 8.0;
+      else rest += len * (double)tc.n * wc;
+      s.op_begin += op_base;
+      s.op_end += op_base;
+      s.layer_begin += lo_base;
+      s.layer_end += lo_base;
+      segs.push_back(s);
+    }
+    bc.seg_end = (uint32_t)segs.size();
+    pre_cost[(size_t)c] = pre;
+    shot_cost[(size_t)c] = rest;
+    B->n_gates += hp.n_gates;
+    B->n_meas += span;
+    B->max_n = std::max(B->max_n, tc.n);
+  }
+  B->m = m;
+  B->out_bytes = out_max;
+  // ---- work items, longest first within each class
+  std::vector<uint64_t> items;
+  std::vector<int32_t> order((size_t)m);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t a, int32_t b) { return pre_cost[(size_t)a] > pre_cost[(size_t)b]; });
+  for (int32_t c : order) items.push_back((uint64_t)(uint32_t)c | (0xFFFFFFFFull << 32));
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t a, int32_t b) { return shot_cost[(size_t)a] > shot_cost[(size_t)b]; });
+  for (int32_t c : order) {
+    if (circs[(size_t)c].n_meas == 0) continue;
+    for (int32_t s = 0; s < circs[(size_t)c].shots; ++s)
+      items.push_back((uint64_t)(uint32_t)c | ((uint64_t)(uint32_t)s << 32));
+  }
+  // shot items of equal cost stay grouped per circuit; interleave nothing else
+  B->nitems = (int)items.size();
+  // ---- device image: one allocation
+  const size_t b_circs = a256(circs.size() * sizeof(BatchCirc) + 1);
+  const size_t b_segs = a256(segs.size() * sizeof(Seg) + 1);
+  const size_t b_ops = a256(ops.size() * 4 + 4);
+  const size_t b_lo = a256(layer_off.size() * 4 + 4);
+  const size_t b_items = a256(items.size() * 8 + 8);
+  const size_t b_img = a256(img_words * 4 + 16);
+  B->ctl_bytes = a256(16 + (size_t)m * 4 + 4);
+  const size_t total = b_circs + b_segs + b_ops + b_lo + b_items + b_img + B->ctl_bytes;
+  if (cudaMalloc(&B->dmem, total) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc of %zu bytes for the batch failed", total);
+    return TAB_ENOMEM;
+  }
+  char* p = static_cast<char*>(B->dmem);
+  BatchArgs& A = B->args;
+  A.circs = reinterpret_cast<const BatchCirc*>(p);
+  CUB(cudaMemcpy(p, circs.data(), circs.size() * sizeof(BatchCirc), cudaMemcpyHostToDevice));
+  p += b_circs;
+  A.segs = reinterpret_cast<const Seg*>(p);
+  if (!segs.empty()) CUB(cudaMemcpy(p, segs.data(), segs.size() * sizeof(Seg), cudaMemcpyHostToDevice));
+  p += b_segs;
+  A.ops = reinterpret_cast<const uint32_t*>(p);
+  if (!ops.empty()) CUB(cudaMemcpy(p, ops.data(), ops.size() * 4, cudaMemcpyHostToDevice));
+  p += b_ops;
+  A.layer_off = reinterpret_cast<const uint32_t*>(p);
+  if (!layer_off.empty())
+    CUB(cudaMemcpy(p, layer_off.data(), layer_off.size() * 4, cudaMemcpyHostToDevice));
+  p += b_lo;
+  A.items = reinterpret_cast<const uint64_t*>(p);
+  if (!items.empty()) CUB(cudaMemcpy(p, items.data(), items.size() * 8, cudaMemcpyHostToDevice));
+  p += b_items;
+  A.img = reinterpret_cast<uint32_t*>(p);
+  p += b_img;
+  B->ctl = p;
+  A.queue = reinterpret_cast<unsigned int*>(p);
+  A.err = reinterpret_cast<int*>(p + 4);
+  A.ready = reinterpret_cast<int*>(p + 16);
+  A.nitems = B->nitems;
+  B->smem = sct_smem_bytes(B->max_n);
+  int dev = 0, sms = 1;
+  CUB(cudaGetDevice(&dev));
+  CUB(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  B->ctas = std::max(1, std::min(B->nitems, sms * batch_ctas_per_sm(B->smem)));
+  return TAB_OK;
+}
+
+int make_graph(tab_batch_s* B) {
+  CUB(cudaGraphCreate(&B->graph, 0));
+  cudaMemsetParams mp{};
+  mp.dst = B->ctl;
+  mp.value = 0;
+  mp.elementSize = 1;
+  mp.width = B->ctl_bytes;
+  mp.height = 1;
+  mp.pitch = 0;
+  cudaGraphNode_t mnode;
+  CUB(cudaGraphAddMemsetNode(&mnode, B->graph, nullptr, 0, &mp));
+  void* kargs[] = {&B->args};
+  cudaKernelNodeParams kp{};
+  kp.func = const_cast<void*>(batch_kernel_ptr());
+  kp.gridDim = dim3(B->ctas);
+  kp.blockDim = dim3(batch_threads());
+  kp.sharedMemBytes = (unsigned)B->smem;
+  kp.kernelParams = kargs;
+  CUB(cudaGraphAddKernelNode(&B->knode, B->graph, &mnode, 1, &kp));
+  CUB(cudaGraphInstantiate(&B->gexec, B->graph, 0));
+  return TAB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tab_batch_create(const tab_circuit* circuits, int32_t m, tab_batch_t* out) {
+  if (!out) {
+    set_error("null output pointer");
+    return TAB_EINVAL;
+  }
+  *out = nullptr;
+  tab_batch_s* B = new (std::nothrow) tab_batch_s();
+  if (!B) {
+    set_error("host allocation failed");
+    return TAB_ENOMEM;
+  }
+  int rc = build_batch(circuits, m, nullptr, B);
+  if (rc == TAB_OK) rc = prepare_batch_kernel(B->smem) == cudaSuccess ? TAB_OK : TAB_ECUDA;
+  if (rc != TAB_OK) {
+    tab_batch_destroy(B);
+    return rc;
+  }
+  *out = B;
+  return TAB_OK;
+}
+
+int tab_batch_destroy(tab_batch_t B) {
+  if (!B) return TAB_OK;
+  cudaDeviceSynchronize();
+  if (B->gexec) cudaGraphExecDestroy(B->gexec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  if (B->dmem) cudaFree(B->dmem);
+  delete B;
+  return TAB_OK;
+}
+
+int tab_batch_info(tab_batch_t B, int64_t* n_gates, int64_t* n_meas, int64_t* out_bytes) {
+  if (!B) {
+    set_error("null batch");
+    return TAB_EINVAL;
+  }
+  if (n_gates) *n_gates = B->n_gates;
+  if (n_meas) *n_meas = B->n_meas;
+  if (out_bytes) *out_bytes = B->out_bytes;
+  return TAB_OK;
+}
+
+int tab_batch_launches(tab_batch_t B, int64_t* count) {
+  if (!B || !count) {
+    set_error("null argument");
+    return TAB_EINVAL;
+  }
+  *count = 1;
+  return TAB_OK;
+}
+
+int tab_batch_exec(tab_batch_t B, uint64_t seed, uint8_t* dev_out, void* cuda_stream) {
+  if (!B) {
+    set_error("null batch");
+    return TAB_EINVAL;
+  }
+  if (B->out_bytes > 0 && !dev_out) {
+    set_error("null output buffer");
+    return TAB_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  B->args.seed = seed;
+  B->args.out = dev_out;
+  if (!B->gexec) {
+    int rc = make_graph(B);
+    if (rc != TAB_OK) return rc;
+  } else {
+    void* kargs[] = {&B->args};
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void*>(batch_kernel_ptr());
+    kp.gridDim = dim3(B->ctas);
+    kp.blockDim = dim3(batch_threads());
+    kp.sharedMemBytes = (unsigned)B->smem;
+    kp.kernelParams = kargs;
+    CUB(cudaGraphExecKernelNodeSetParams(B->gexec, B->knode, &kp));
+  }
+  CUB(cudaGraphLaunch(B->gexec, st));
+  return TAB_OK;
+}
+
+}  // extern "C"
+
+static int batch_error(tab_batch_t B, void* cuda_stream) {
+  int err = 0;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  CUB(cudaMemcpyAsync(&err, B->args.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUB(cudaStreamSynchronize(st));
+  if (err == DERR_TIMEOUT) {
+    set_error("a device-side wait timed out");
+    return TAB_ETIMEOUT;
+  }
+  if (err) {
+    set_error("device reported inconsistency code %d", err);
+    return TAB_EDEVICE;
+  }
+  return TAB_OK;
+}
+
+extern "C" {
+
+int tab_batch_run(const tab_circuit* circuits, int32_t m, uint64_t seed, uint8_t* out_bits,
+                  const int64_t* out_offsets) {
+  tab_batch_s* B = new (std::nothrow) tab_batch_s();
+  if (!B) {
+    set_error("host allocation failed");
+    return TAB_ENOMEM;
+  }
+  int rc = build_batch(circuits, m, out_offsets, B);
+  if (rc == TAB_OK && prepare_batch_kernel(B->smem) != cudaSuccess) {
+    set_error("kernel attribute setup failed");
+    rc = TAB_ECUDA;
+  }
+  uint8_t* dout = nullptr;
+  if (rc == TAB_OK && B->out_bytes > 0) {
+    if (!out_bits) {
+      set_error("null output buffer");
+      rc = TAB_EINVAL;
+    } else if (cudaMalloc((void**)&dout, (size_t)B->out_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaMalloc of %lld output bytes failed", (long long)B->out_bytes);
+      rc = TAB_ENOMEM;
+    }
+  }
+  if (rc == TAB_OK) rc = tab_batch_exec(B, seed, dout, nullptr);
+  if (rc == TAB_OK) rc = batch_error(B, nullptr);
+  if (rc == TAB_OK && B->out_bytes > 0) {
+    if (out_offsets) {  // copy only the spans written, leave the rest untouched
+      for (int32_t c = 0; c < m; ++c) {
+        int64_t nm = 0;
+        for (int64_t i = 0; i < circuits[c].n_gates; ++i) {
+          const uint32_t op = (uint32_t)(circuits[c].gates[i] >> 56);
+          nm += (op == TAB_MZ || op == TAB_MZR);
+        }
+        const int64_t span = nm * circuits[c].shots;
+        if (span && cudaMemcpy(out_bits + out_offsets[c], dout + out_offsets[c], (size_t)span,
+                               cudaMemcpyDeviceToHost) != cudaSuccess) {
+          set_error("outcome copy failed");
+          rc = TAB_ECUDA;
+          break;
+        }
+      }
+    } else if (cudaMemcpy(out_bits, dout, (size_t)B->out_bytes, cudaMemcpyDeviceToHost) !=
+               cudaSuccess) {
+      set_error("outcome copy failed");
+      rc = TAB_ECUDA;
+    }
+  }
+  if (dout) cudaFree(dout);
+  tab_batch_destroy(B);
+  return rc;
+}
+
+}  // extern "C"

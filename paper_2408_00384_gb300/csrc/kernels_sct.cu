@@ -1,0 +1,445 @@
+// kernels_sct.cu -- single-CTA tableau engine (whole tableau resident in
+// shared memory) and the persistent batched launch built on it (sm_103a).
+//
+// For n <= 640 a complete tableau (2 planes x n columns x 2n rows, plus signs)
+// fits in one CTA's shared memory, so gates and measurements need only CTA
+// barriers.  Operations are those of Aaronson & Gottesman, PRA 70, 052328,
+// Sec. III (the formalism of the Clifford backend in arXiv:2408.00384,
+// "Simulation of Clifford circuits"):
+//  * gates: column updates (gate_rules.cuh); the lanes of a warp take the
+//    words of one column, so one gate is one conflict-free shared-memory sweep;
+//  * measurement of Z_a: pivot by warp ballot over the stabilizer half of
+//    column a; random case -- rowsum of the pivot row into every row with
+//    x_ha = 1 with the exponent
+//      2 r_h' = 2 r_h + 2 r_p + sum_j [x_pj z_pj + x_hj z_hj - x'_hj z'_hj
+//                                      + 2 z_pj x_hj]   (mod 4)
+//    kept as bit-sliced mod-4 counters (x' = x_h ^ x_p, z' = z_h ^ z_p), then
+//    row p-n := row p and row p := (-1)^b Z_a; deterministic case -- the sign
+//    of the product of the selected stabilizer rows,
+//      e = sum_m (2 r_m + |x_m & z_m|) + 2 sum_{m<l} z_m . x_l   (mod 4),
+//    whose pairwise term is a prefix-parity scan down each column.
+//
+// Shared-memory layout: Whc = ceil(n/32) words per half, Wc = 2*Whc per
+// column, column stride Wp = Wc | 1 (odd, so both "lanes over words of one
+// column" and "lanes over columns at one word" are bank-conflict free).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gate_rules.cuh"
+#include "philox.cuh"
+#include "sct.h"
+#include "tab_internal.h"
+
+namespace tab {
+
+constexpr int kSctThreads = 512;
+constexpr unsigned long long kReadyWaitNs = 2000000000ull;
+
+__host__ __device__ inline int sct_whc(int n) { return (n + 31) / 32; }
+__host__ __device__ inline int sct_wc(int n) { return 2 * sct_whc(n); }
+__host__ __device__ inline int sct_wp(int n) { return sct_wc(n) | 1; }
+
+size_t sct_image_words(int n) {
+  return ((size_t)2 * n * sct_wp(n) + sct_wc(n) + 3) & ~(size_t)3;
+}
+
+size_t sct_smem_bytes(int n) {
+  const int Wc = sct_wc(n);
+  const int GG = kSctThreads / Wc;
+  return sizeof(uint32_t) *
+         ((size_t)2 * n * sct_wp(n) + 2 * (size_t)Wc + (size_t)n + 2 * (size_t)GG * Wc);
+}
+
+struct Sct {
+  int n, Whc, Wc, Wp, GG;
+  uint32_t *X, *Z, *R, *sS, *supp, *redlo, *redhi;
+};
+
+__device__ __forceinline__ void sct_setup(Sct& s, uint32_t* base, int n) {
+  s.n = n;
+  s.Whc = sct_whc(n);
+  s.Wc = 2 * s.Whc;
+  s.Wp = s.Wc | 1;
+  s.GG = kSctThreads / s.Wc;
+  s.X = base;
+  s.Z = s.X + (size_t)n * s.Wp;
+  s.R = s.Z + (size_t)n * s.Wp;
+  s.sS = s.R + s.Wc;
+  s.supp = s.sS + s.Wc;
+  s.redlo = s.supp + n;
+  s.redhi = s.redlo + (size_t)s.GG * s.Wc;
+}
+
+__device__ __forceinline__ unsigned long long sct_gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t prefix_xor_exclusive(uint32_t v) {
+  uint32_t y = v << 1;
+  y ^= y << 1;
+  y ^= y << 2;
+  y ^= y << 4;
+  y ^= y << 8;
+  y ^= y << 16;
+  return y;
+}
+
+__device__ __forceinline__ void add4s(uint32_t& l, uint32_t& h, uint32_t bl, uint32_t bh) {
+  h ^= bh ^ (l & bl);
+  l ^= bl;
+}
+
+// |0^n>: destabilizer i = +X_i, stabilizer i = +Z_i.
+__device__ void sct_identity(const Sct& s) {
+  const int tot = s.n * s.Wp;
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int a = i / s.Wp, w = i - a * s.Wp;
+    const uint32_t bit = 1u << (a & 31);
+    s.X[i] = (w == (a >> 5)) ? bit : 0u;
+    s.Z[i] = (w == s.Whc + (a >> 5)) ? bit : 0u;
+  }
+  for (int w = threadIdx.x; w < s.Wc; w += blockDim.x) s.R[w] = 0u;
+}
+
+// Apply layers [0, nl) of a gate segment; layer_off[L]..layer_off[L+1].
+__device__ void sct_gates(const Sct& s, const uint32_t* __restrict__ ops,
+                          const uint32_t* __restrict__ layer_off, int nl) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t r0 = 0u, r1 = 0u;
+  uint32_t lb = __ldg(layer_off);
+  if (s.Wc >= 32) {  // one gate per warp, lanes over words
+    const bool two = lane + 32 < s.Wc;
+    for (int L = 0; L < nl; ++L) {
+      const uint32_t le = __ldg(layer_off + L + 1);
+      for (uint32_t g = lb + warp; g < le; g += nw) {
+        const uint32_t code = __ldg(ops + g);
+        apply_gate(code, s.X, s.Z, s.Wp, lane, r0);
+        if (two) apply_gate(code, s.X, s.Z, s.Wp, lane + 32, r1);
+      }
+      lb = le;
+      __syncthreads();
+    }
+    if (r0) atomicXor(&s.R[lane], r0);
+    if (two && r1) atomicXor(&s.R[lane + 32], r1);
+  } else {  // several gates per warp, Wc lanes each
+    const int sub = 32 / s.Wc, gsub = lane / s.Wc, w = lane - gsub * s.Wc;
+    const bool active = gsub < sub;
+    for (int L = 0; L < nl; ++L) {
+      const uint32_t le = __ldg(layer_off + L + 1);
+      if (active)
+        for (uint32_t g = lb + warp * sub + gsub; g < le; g += nw * sub)
+          apply_gate(__ldg(ops + g), s.X, s.Z, s.Wp, w, r0);
+      lb = le;
+      __syncthreads();
+    }
+    if (active && r0) atomicXor(&s.R[w], r0);
+  }
+  __syncthreads();
+}
+
+// Measure Z_a (code = MZ / MZR on qubit a) with pre-drawn bit rbit.  Returns
+// the outcome (same value in every thread).
+__device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err) {
+  __shared__ int s_pw, s_nsupp, s_kc;
+  __shared__ uint32_t s_acc;
+  const int tid = threadIdx.x, T = blockDim.x;
+  const int a = (int)dq1(code);
+  const bool reset = dop(code) == OP_MZR;
+  const int n = s.n, Whc = s.Whc, Wc = s.Wc, Wp = s.Wp;
+  const uint32_t* xa = s.X + (size_t)a * Wp;
+  for (int w = tid; w < Wc; w += T) s.sS[w] = xa[w];
+  if (tid < 32) {
+    const uint32_t v = (tid < Whc) ? xa[Whc + tid] : 0u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, v != 0u);
+    if (tid == 0) {
+      s_pw = bal ? Whc + __ffs(bal) - 1 : -1;
+      s_nsupp = 0;
+      s_kc = 0;
+      s_acc = 0u;
+    }
+  }
+  __syncthreads();
+  const int pw = s_pw;
+  if (pw >= 0) {
+    // ---------------- random outcome ----------------
+    const int P = pw * 32 + __ffs(s.sS[pw]) - 1;
+    const int Pd = P - 32 * Whc;
+    const int wp = pw, wd = Pd >> 5;
+    const uint32_t bpm = 1u << (P & 31);
+    const uint32_t rp = (s.R[wp] & bpm) ? 1u : 0u;
+    for (int j = tid; j < n; j += T) {
+      const uint32_t xw = s.X[(size_t)j * Wp + wp], zw = s.Z[(size_t)j * Wp + wp];
+      const uint32_t xp = (xw & bpm) ? 1u : 0u, zp = (zw & bpm) ? 1u : 0u;
+      if (xp | zp) {
+        const int pos = atomicAdd(&s_nsupp, 1);
+        s.supp[pos] = (uint32_t)j | (xp << 30) | (zp << 31);
+        if (xp & zp) atomicAdd(&s_kc, 1);
+      } else {  // row p is I here: row p-n := row p clears this bit
+        s.X[(size_t)j * Wp + wd] &= ~bpm;
+        s.Z[(size_t)j * Wp + wd] &= ~bpm;
+      }
+    }
+    __syncthreads();
+    const int nsupp = s_nsupp;
+    const int g = tid / Wc, w = tid - g * Wc;
+    if (g < s.GG) {
+      uint32_t lo = 0u, hi = 0u;
+      uint32_t Sw = s.sS[w];
+      if (w == wp || w == wd) Sw &= ~bpm;  // S' excludes rows p and p-n
+      for (int idx = g; idx < nsupp; idx += s.GG) {
+        const uint32_t e = s.supp[idx];
+        const int j = (int)(e & 0x3FFFu);
+        const uint32_t XP = (e & (1u << 30)) ? 0xffffffffu : 0u;
+        const uint32_t ZP = (e & (1u << 31)) ? 0xffffffffu : 0u;
+        const size_t i = (size_t)j * Wp + w;
+        const uint32_t x = s.X[i], z = s.Z[i];
+        const uint32_t A0 = x & z, B0 = (x ^ XP) & (z ^ ZP);
+        const uint32_t inc = A0 & ~B0, dec = B0 & ~A0;
+        hi ^= ((lo & inc) | (~lo & dec)) ^ (ZP & x);
+        lo ^= inc | dec;
+        uint32_t xn = x ^ (XP & Sw), zn = z ^ (ZP & Sw);
+        if (w == wd) {  // row p-n := row p
+          xn = (xn & ~bpm) | (XP & bpm);
+          zn = (zn & ~bpm) | (ZP & bpm);
+        }
+        if (w == wp) {  // row p := Z_a
+          xn &= ~bpm;
+          zn = (zn & ~bpm) | ((j == a) ? bpm : 0u);
+        }
+        s.X[i] = xn;
+        s.Z[i] = zn;
+      }
+      s.redlo[g * Wc + w] = lo;
+      s.redhi[g * Wc + w] = hi;
+    }
+    __syncthreads();
+    if (tid < Wc) {
+      const int ww = tid;
+      uint32_t L = 0u, H = 0u;
+      for (int gg = 0; gg < s.GG; ++gg) add4s(L, H, s.redlo[gg * Wc + ww], s.redhi[gg * Wc + ww]);
+      const uint32_t scal = ((uint32_t)s_kc + 2u * rp) & 3u;
+      add4s(L, H, (scal & 1u) ? 0xffffffffu : 0u, (scal & 2u) ? 0xffffffffu : 0u);
+      uint32_t Sw = s.sS[ww];
+      if (ww == wp || ww == wd) Sw &= ~bpm;
+      if (L & Sw) atomicCAS(err, 0, DERR_PHASE);
+      uint32_t r = s.R[ww] ^ (H & Sw);
+      if (ww == wd) r = (r & ~bpm) | (rp ? bpm : 0u);
+      if (ww == wp) r = (r & ~bpm) | (rbit ? bpm : 0u);
+      if (reset && rbit) r ^= s.Z[(size_t)a * Wp + ww];  // X_a on every row
+      s.R[ww] = r;
+    }
+    __syncthreads();
+    return (int)rbit;
+  }
+  // ---------------- deterministic outcome ----------------
+  const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t acc = 0u;
+  for (int j = warp; j < n; j += nw) {
+    uint32_t carry = 0u;
+    for (int base = 0; base < Whc; base += 32) {
+      const int hw = base + lane;
+      uint32_t xT = 0u, zT = 0u;
+      if (hw < Whc) {
+        const uint32_t t = s.sS[hw];
+        xT = s.X[(size_t)j * Wp + Whc + hw] & t;
+        zT = s.Z[(size_t)j * Wp + Whc + hw] & t;
+      }
+      acc += __popc(xT & zT);
+      const uint32_t bal = __ballot_sync(0xffffffffu, __popc(zT) & 1);
+      const uint32_t cin = (__popc(bal & lt) & 1u) ^ carry;
+      const uint32_t zpre = prefix_xor_exclusive(zT) ^ (cin ? 0xffffffffu : 0u);
+      acc += 2u * (__popc(xT & zpre) & 1u);
+      carry ^= __popc(bal) & 1u;
+    }
+  }
+  for (int hw = tid; hw < Whc; hw += T) acc += 2u * __popc(s.R[Whc + hw] & s.sS[hw]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) atomicAdd(&s_acc, acc & 3u);
+  __syncthreads();
+  const uint32_t e = s_acc & 3u;
+  if ((e & 1u) && tid == 0) atomicCAS(err, 0, DERR_PHASE);
+  const int out = (int)(e >> 1);
+  if (reset && out)
+    for (int w = tid; w < Wc; w += T) s.R[w] ^= s.Z[(size_t)a * Wp + w];
+  __syncthreads();
+  return out;
+}
+
+// -------------------------------------------- global <-> shared transfers ---
+// Image layout (batched scratch): the shared-memory X, Z planes then R.
+__device__ void sct_store_image(const Sct& s, uint32_t* __restrict__ img) {
+  const size_t tot = (size_t)2 * s.n * s.Wp + s.Wc;
+  for (size_t i = threadIdx.x; i < tot; i += blockDim.x) img[i] = s.X[i];
+}
+__device__ void sct_load_image(const Sct& s, const uint32_t* __restrict__ img) {
+  const size_t tot = (size_t)2 * s.n * s.Wp + s.Wc;
+  for (size_t i = threadIdx.x; i < tot; i += blockDim.x) s.X[i] = __ldcg(img + i);
+}
+// Handle layout: Wh words per half (multiple of 4), W = 2*Wh per column.
+__device__ void sct_load_global(const Sct& s, const uint32_t* X, const uint32_t* Z,
+                                const uint32_t* R, int Wh) {
+  const int W = 2 * Wh;
+  const int tot = s.n * s.Wc;
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int a = i / s.Wc, w = i - a * s.Wc;
+    const int gw = w < s.Whc ? w : Wh + (w - s.Whc);
+    s.X[(size_t)a * s.Wp + w] = X[(size_t)a * W + gw];
+    s.Z[(size_t)a * s.Wp + w] = Z[(size_t)a * W + gw];
+  }
+  for (int w = threadIdx.x; w < s.Wc; w += blockDim.x)
+    s.R[w] = R[w < s.Whc ? w : Wh + (w - s.Whc)];
+}
+__device__ void sct_store_global(const Sct& s, uint32_t* X, uint32_t* Z, uint32_t* R, int Wh) {
+  const int W = 2 * Wh;
+  const int tot = s.n * s.Wc;
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int a = i / s.Wc, w = i - a * s.Wc;
+    const int gw = w < s.Whc ? w : Wh + (w - s.Whc);
+    X[(size_t)a * W + gw] = s.X[(size_t)a * s.Wp + w];
+    Z[(size_t)a * W + gw] = s.Z[(size_t)a * s.Wp + w];
+  }
+  for (int w = threadIdx.x; w < s.Wc; w += blockDim.x) R[w < s.Whc ? w : Wh + (w - s.Whc)] = s.R[w];
+}
+
+// Run segments [seg_begin, seg_end) of a program on the resident tableau.
+// Outcome k of this run goes to out[k]; k0 is the first measurement index.
+__device__ void sct_run_segments(const Sct& s, const Seg* __restrict__ segs, int seg_begin,
+                                 int seg_end, const uint32_t* __restrict__ ops,
+                                 const uint32_t* __restrict__ layer_off, uint64_t seed,
+                                 uint64_t cid, uint32_t shot, uint64_t k0, uint8_t* out,
+                                 int* err) {
+  uint64_t k = k0;
+  int o = 0;
+  for (int si = seg_begin; si < seg_end; ++si) {
+    const Seg g = segs[si];
+    if (g.kind == 0) {
+      sct_gates(s, ops, layer_off + g.layer_begin, (int)(g.layer_end - g.layer_begin));
+    } else {
+      for (uint32_t op = g.op_begin; op < g.op_end; ++op) {
+        const uint32_t rbit = outcome_bit(seed, cid, shot, k);
+        const int m = sct_measure(s, __ldg(ops + op), rbit, err);
+        if (threadIdx.x == 0) out[o] = (uint8_t)m;
+        ++k;
+        ++o;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------- plain path, one tableau ---
+__global__ void __launch_bounds__(kSctThreads) k_sct_program(SctProgArgs A) {
+  extern __shared__ uint32_t smem[];
+  Sct s;
+  sct_setup(s, smem, A.n);
+  sct_load_global(s, A.X, A.Z, A.R, A.Wh);
+  __syncthreads();
+  sct_run_segments(s, A.segs, 0, A.nsegs, A.ops, A.layer_off, A.seed, A.cid, A.shot, A.k0,
+                   A.out, A.err);
+  __syncthreads();
+  sct_store_global(s, A.X, A.Z, A.R, A.Wh);
+}
+
+cudaError_t launch_sct_program(const SctProgArgs& A, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_sct_program, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sct_smem_bytes(TAB_BATCH_MAX_QUBITS));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_sct_program<<<1, kSctThreads, sct_smem_bytes(A.n), st>>>(A);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------- batched launch ---
+// Work items: one "prefix" item per circuit (identity, then the gates before
+// the first measurement; the resulting image is stored and its ready flag
+// released) followed by one item per (circuit, shot) (wait for the flag, load
+// the image, run the rest of the circuit with that shot's outcome stream).
+// Items are dequeued in order from one atomic counter; every prefix item is
+// dequeued before any shot item, and prefix items never wait, so every wait
+// ends.  Waits are bounded anyway and latch DERR_TIMEOUT.
+__global__ void __launch_bounds__(kSctThreads) k_batch(BatchArgs A) {
+  extern __shared__ uint32_t smem[];
+  __shared__ unsigned int s_item;
+  __shared__ int s_stop;
+  const uint64_t seed = A.seed;
+  uint8_t* out = A.out;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_item = atomicAdd(A.queue, 1u);
+      s_stop = *(volatile int*)A.err != 0;
+    }
+    __syncthreads();
+    const unsigned int it = s_item;
+    const int stop = s_stop;
+    __syncthreads();
+    if (stop || it >= (unsigned int)A.nitems) break;
+    const uint64_t item = A.items[it];
+    const uint32_t ci = (uint32_t)item, shot = (uint32_t)(item >> 32);
+    const BatchCirc C = A.circs[ci];
+    Sct s;
+    sct_setup(s, smem, C.n);
+    uint32_t* img = A.img + C.img_off;
+    if (shot == 0xFFFFFFFFu) {
+      sct_identity(s);
+      __syncthreads();
+      if (C.n_prefix) {
+        const Seg g = A.segs[C.seg_begin];
+        sct_gates(s, A.ops, A.layer_off + g.layer_begin, (int)(g.layer_end - g.layer_begin));
+      }
+      sct_store_image(s, img);
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(A.ready + ci, 1);
+      }
+    } else {
+      if (threadIdx.x == 0) {
+        const unsigned long long t0 = sct_gtimer();
+        int ok = 1;
+        while (atomicAdd(A.ready + ci, 0) == 0) {
+          if (*(volatile int*)A.err != 0 || sct_gtimer() - t0 > kReadyWaitNs) {
+            atomicCAS(A.err, 0, DERR_TIMEOUT);
+            ok = 0;
+            break;
+          }
+        }
+        __threadfence();
+        s_stop = !ok;
+      }
+      __syncthreads();
+      if (s_stop) break;
+      sct_load_image(s, img);
+      __syncthreads();
+      sct_run_segments(s, A.segs, (int)(C.seg_begin + C.n_prefix), (int)C.seg_end, A.ops,
+                       A.layer_off, seed, C.cid, shot, 0,
+                       out + C.out_off + (uint64_t)shot * C.n_meas, A.err);
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t prepare_batch_kernel(size_t smem) {
+  (void)smem;
+  return cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sct_smem_bytes(TAB_BATCH_MAX_QUBITS));
+}
+
+const void* batch_kernel_ptr() { return (const void*)k_batch; }
+int batch_threads() { return kSctThreads; }
+
+int batch_ctas_per_sm(size_t smem) {
+  if (prepare_batch_kernel(smem) != cudaSuccess) return 1;
+  int v = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch, kSctThreads, smem) != cudaSuccess)
+    v = 1;
+  return v < 1 ? 1 : v;
+}
+
+}  // namespace tab

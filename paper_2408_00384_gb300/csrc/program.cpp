@@ -1,0 +1,158 @@
+// program.cpp -- compile a gate list into the device program format:
+// validation, split into gate / measurement segments, and ASAP layering.
+//
+// Gates acting on disjoint qubits commute exactly, so the conjugation they
+// apply to every tableau row (AG Sec. III) is the same in any order.  ASAP
+// layering gives each gate the layer 1 + max(layer of the previous gate on
+// each of its qubits): per-qubit program order is kept, and the gates of one
+// layer act on pairwise-disjoint qubits, so a kernel may apply them in
+// parallel.  Within a layer gates are grouped by op code so that neighbouring
+// threads take the same branch.  A measurement touches every row, so it ends
+// the gate segment before it.
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "tab_internal.h"
+
+namespace tab {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+const char* last_error() { return g_last_error.c_str(); }
+
+int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out) {
+  if (n < 1 || n > TAB_MAX_QUBITS) {
+    set_error("n=%d outside [1, %d]", n, TAB_MAX_QUBITS);
+    return TAB_ERANGE;
+  }
+  if (count < 0 || (count > 0 && gates == nullptr)) {
+    set_error("bad gate list (count=%lld)", (long long)count);
+    return TAB_EINVAL;
+  }
+  // ---- validation: nothing is applied unless every word is valid
+  for (int64_t i = 0; i < count; ++i) {
+    const uint64_t g = gates[i];
+    const uint32_t op = (uint32_t)(g >> 56);
+    const uint64_t q1 = (g >> 28) & 0xFFFFFFFull, q2 = g & 0xFFFFFFFull;
+    if (op > TAB_BARRIER) {
+      set_error("gate %lld: unknown op %u", (long long)i, op);
+      return TAB_EINVAL;
+    }
+    if (op == TAB_BARRIER) continue;
+    if (q1 >= (uint64_t)n) {
+      set_error("gate %lld: qubit %llu >= n=%d", (long long)i, (unsigned long long)q1, n);
+      return TAB_ERANGE;
+    }
+    if (op == TAB_CNOT || op == TAB_CZ || op == TAB_SWAP) {
+      if (q2 >= (uint64_t)n) {
+        set_error("gate %lld: qubit %llu >= n=%d", (long long)i, (unsigned long long)q2, n);
+        return TAB_ERANGE;
+      }
+      if (q1 == q2) {
+        set_error("gate %lld: two-qubit op on one qubit %llu", (long long)i,
+                  (unsigned long long)q1);
+        return TAB_EINVAL;
+      }
+    }
+  }
+
+  HostProgram& P = *out;
+  P = HostProgram();
+  P.n = n;
+  P.ops.reserve((size_t)count);
+  std::vector<int64_t> last((size_t)n, -1);  // global layer of the last gate per qubit
+  int64_t nlayers = 0;                       // layers emitted so far (global)
+  std::vector<uint32_t> seg_codes;
+  std::vector<int64_t> seg_layer;
+
+  // Each gate segment owns one contiguous run of layer_off entries:
+  // layer_off[layer_begin] = op_begin, layer_off[layer_begin + L + 1] = end
+  // of layer L, layer_off[layer_end] = op_end.
+  auto flush_gates = [&]() {
+    if (seg_codes.empty()) return;
+    const int64_t base = nlayers;
+    int64_t top = base;
+    for (int64_t L : seg_layer) top = std::max(top, L + 1);
+    const int64_t nl = top - base;
+    const int kOps = 10;  // bucket by (layer, op) with a counting sort
+    std::vector<uint32_t> cnt((size_t)nl * kOps, 0);
+    for (size_t i = 0; i < seg_codes.size(); ++i)
+      cnt[(size_t)(seg_layer[i] - base) * kOps + dop(seg_codes[i])]++;
+    std::vector<uint32_t> pos(cnt.size(), 0);
+    uint32_t acc = 0;
+    for (size_t b = 0; b < cnt.size(); ++b) {
+      pos[b] = acc;
+      acc += cnt[b];
+    }
+    const uint32_t op_base = (uint32_t)P.ops.size();
+    P.ops.resize(P.ops.size() + seg_codes.size());
+    for (size_t i = 0; i < seg_codes.size(); ++i) {
+      const size_t b = (size_t)(seg_layer[i] - base) * kOps + dop(seg_codes[i]);
+      P.ops[op_base + pos[b]++] = seg_codes[i];
+    }
+    Seg s{};
+    s.kind = 0;
+    s.op_begin = op_base;
+    s.op_end = op_base + (uint32_t)seg_codes.size();
+    s.meas_before = (uint32_t)P.n_meas;
+    s.layer_begin = (uint32_t)P.layer_off.size();
+    P.layer_off.push_back(op_base);
+    uint32_t run = op_base;
+    for (int64_t L = 0; L < nl; ++L) {
+      for (int o = 0; o < kOps; ++o) run += cnt[(size_t)L * kOps + o];
+      P.layer_off.push_back(run);
+    }
+    s.layer_end = (uint32_t)P.layer_off.size() - 1;
+    P.segs.push_back(s);
+    nlayers = top;
+    seg_codes.clear();
+    seg_layer.clear();
+  };
+
+  for (int64_t i = 0; i < count; ++i) {
+    const uint64_t g = gates[i];
+    const uint32_t op = (uint32_t)(g >> 56);
+    const uint32_t q1 = (uint32_t)((g >> 28) & 0xFFFFFFFull), q2 = (uint32_t)(g & 0xFFFFFFFull);
+    if (op == TAB_BARRIER || op == TAB_I) continue;
+    if (op == TAB_MZ || op == TAB_MZR) {
+      flush_gates();
+      if (P.segs.empty() || P.segs.back().kind != 1) {
+        Seg s{};
+        s.kind = 1;
+        s.op_begin = s.op_end = (uint32_t)P.ops.size();
+        s.meas_before = (uint32_t)P.n_meas;
+        P.segs.push_back(s);
+      }
+      P.ops.push_back(dcode(op, q1, 0));
+      P.segs.back().op_end++;
+      P.n_meas++;
+      continue;
+    }
+    const bool two = (op == TAB_CNOT || op == TAB_CZ || op == TAB_SWAP);
+    int64_t L = std::max<int64_t>(last[q1], nlayers - 1);
+    if (two) L = std::max<int64_t>(L, last[q2]);
+    L += 1;
+    last[q1] = L;
+    if (two) last[q2] = L;
+    seg_codes.push_back(dcode(op, q1, two ? q2 : 0));
+    seg_layer.push_back(L);
+    P.n_gates++;
+  }
+  flush_gates();
+  return TAB_OK;
+}
+
+}  // namespace tab

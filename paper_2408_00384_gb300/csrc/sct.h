@@ -1,0 +1,59 @@
+// sct.h -- argument blocks of the single-CTA engine (kernels_sct.cu): the
+// plain-path program kernel for one small tableau and the batched launch.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tab_internal.h"
+
+namespace tab {
+
+struct SctProgArgs {
+  uint32_t *X, *Z, *R;  // handle layout (Wh words per half)
+  int n, Wh;
+  const Seg* segs;
+  int nsegs;
+  const uint32_t* ops;
+  const uint32_t* layer_off;
+  uint64_t seed, cid;
+  uint32_t shot;
+  uint64_t k0;   // first measurement index
+  uint8_t* out;  // outcome k0 + i goes to out[i]
+  int* err;
+};
+
+struct BatchCirc {
+  int32_t n;
+  int32_t shots;
+  uint32_t seg_begin, seg_end;  // into the batch's segment table
+  uint32_t n_prefix;            // 1 if the first segment is shared gates
+  uint32_t n_meas;              // measurement ops per shot
+  uint64_t cid;
+  uint64_t out_off;             // byte offset of shot 0's outcomes
+  uint64_t img_off;             // word offset of the shared-prefix image
+};
+
+struct BatchArgs {
+  const BatchCirc* circs;
+  const Seg* segs;
+  const uint32_t* ops;
+  const uint32_t* layer_off;
+  const uint64_t* items;  // circuit | shot << 32 (shot = ~0: prefix item)
+  int nitems;
+  uint32_t* img;
+  int* ready;
+  unsigned int* queue;
+  int* err;
+  uint64_t seed;  // Philox key of this run
+  uint8_t* out;   // outcome buffer of this run
+};
+
+size_t sct_image_words(int n);
+size_t sct_smem_bytes(int n);
+cudaError_t launch_sct_program(const SctProgArgs& A, cudaStream_t st);
+int batch_ctas_per_sm(size_t smem);
+cudaError_t prepare_batch_kernel(size_t smem);
+const void* batch_kernel_ptr();
+int batch_threads();
+
+}  // namespace tab

@@ -1,0 +1,619 @@
+// tab_api.cpp -- C-ABI entry points of libtab (declared in include/tab.h):
+// handle lifetime, stream binding, gate application, measurement, outcome
+// log, import/export and error reporting.  All tableau arithmetic happens in
+// the CUDA kernels; this file validates, marshals and launches.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "sct.h"
+#include "tab_internal.h"
+
+namespace tab {
+const char* last_error();
+}
+
+using namespace tab;
+
+#define CU(call)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      set_error("%s failed: %s", #call, cudaGetErrorString(e_));                  \
+      return TAB_ECUDA;                                                           \
+    }                                                                             \
+  } while (0)
+
+struct tab_s {
+  int32_t n = 0, Wh = 0, W = 0;
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  bool own_mem = true;
+  void* base = nullptr;
+  uint32_t *X = nullptr, *Z = nullptr, *R = nullptr;
+  MeasWork mw{};
+  int meas_ctas = 1;
+  uint64_t seed = 1, cid = 0;
+  uint32_t shot = 0;
+  uint64_t k = 0;             // next measurement index
+  uint8_t* log = nullptr;     // device outcome log
+  int64_t log_cap = 0, log_len = 0;
+  int64_t launches = 0;
+  int sticky = TAB_OK;        // latched device error
+  int engine = TAB_ENGINE_AUTO;
+};
+
+struct tab_prog_s {
+  HostProgram hp;
+  uint32_t* d_ops = nullptr;
+  uint32_t* d_layer = nullptr;
+  Seg* d_segs = nullptr;
+};
+
+// Device copy of a compiled program.
+struct DevProg {
+  uint32_t* ops = nullptr;
+  uint32_t* layer = nullptr;
+  Seg* segs = nullptr;
+};
+
+namespace {
+
+int sm_count_of(int dev) {
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) v = 1;
+  return v < 1 ? 1 : v;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct Sizes {
+  size_t planes, sign, work, total;
+};
+
+Sizes sizes_for(int n, int max_ctas) {
+  const int Wh = half_words(n), W = 2 * Wh;
+  Sizes s;
+  s.planes = align256((size_t)n * W * 4);
+  s.sign = align256((size_t)W * 4);
+  s.work = align256(measure_work_words(n, max_ctas) * 4);
+  s.total = 2 * s.planes + s.sign + s.work;
+  return s;
+}
+
+int check_handle(tab_t h) {
+  if (!h) {
+    set_error("null handle");
+    return TAB_EINVAL;
+  }
+  if (h->sticky != TAB_OK) {
+    set_error("handle unusable after an earlier device error");
+    return h->sticky;
+  }
+  return TAB_OK;
+}
+
+// Read back the device error word (synchronous) and latch it.
+int poll_device_error(tab_t h) {
+  int err = 0;
+  cudaError_t e = cudaMemcpyAsync(&err, h->mw.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    set_error("device error: %s", cudaGetErrorString(e));
+    h->sticky = TAB_ECUDA;
+    return TAB_ECUDA;
+  }
+  if (err == DERR_TIMEOUT) {
+    set_error("a device-side wait timed out");
+    h->sticky = TAB_ETIMEOUT;
+    return TAB_ETIMEOUT;
+  }
+  if (err != 0) {
+    set_error("device reported inconsistency code %d", err);
+    h->sticky = TAB_EDEVICE;
+    return TAB_EDEVICE;
+  }
+  return TAB_OK;
+}
+
+int setup(tab_t h, int32_t n, void* mem, bool own) {
+  h->n = n;
+  h->Wh = half_words(n);
+  h->W = 2 * h->Wh;
+  CU(cudaGetDevice(&h->dev));
+  const int sms = sm_count_of(h->dev);
+  h->mw.max_ctas = sms;
+  const Sizes s = sizes_for(n, sms);
+  char* b = static_cast<char*>(mem);
+  h->base = mem;
+  h->own_mem = own;
+  h->X = reinterpret_cast<uint32_t*>(b);
+  h->Z = reinterpret_cast<uint32_t*>(b + s.planes);
+  h->R = reinterpret_cast<uint32_t*>(b + 2 * s.planes);
+  uint32_t* w = reinterpret_cast<uint32_t*>(b + 2 * s.planes + s.sign);
+  h->mw.ph = w;
+  w += (size_t)sms * 2 * h->W;
+  h->mw.r4 = w;
+  w += 2 * (size_t)h->W;
+  h->mw.dp = w;
+  w += 2 * (size_t)sms;
+  h->mw.bar = reinterpret_cast<GridBar*>(w);
+  w += 16;
+  h->mw.err = reinterpret_cast<int*>(w);
+  h->meas_ctas = measure_ctas_for(n, sms, sms);
+  CU(cudaMemsetAsync(h->mw.err, 0, sizeof(int), h->stream));
+  launch_init(h->X, h->Z, h->R, n, h->Wh, h->stream);
+  h->launches++;
+  CU(cudaGetLastError());
+  return TAB_OK;
+}
+
+int ensure_log(tab_t h, int64_t extra) {
+  const int64_t need = h->log_len + extra;
+  if (need <= h->log_cap) return TAB_OK;
+  int64_t cap = h->log_cap ? h->log_cap : 4096;
+  while (cap < need) cap *= 2;
+  uint8_t* nl = nullptr;
+  CU(cudaMallocAsync((void**)&nl, (size_t)cap, h->stream));
+  if (h->log_len) CU(cudaMemcpyAsync(nl, h->log, (size_t)h->log_len, cudaMemcpyDeviceToDevice, h->stream));
+  if (h->log) CU(cudaFreeAsync(h->log, h->stream));
+  h->log = nl;
+  h->log_cap = cap;
+  return TAB_OK;
+}
+
+bool use_single_cta(tab_t h) {
+  if (h->engine == TAB_ENGINE_SINGLE_CTA) return true;
+  if (h->engine == TAB_ENGINE_GRID) return false;
+  return h->n <= 256;
+}
+
+// Enqueue the program.  Measurement segments use `seed`.
+int run_program(tab_t h, const HostProgram& hp, const DevProg& dp, uint64_t seed) {
+  if (hp.n_meas) {
+    int rc = ensure_log(h, hp.n_meas);
+    if (rc != TAB_OK) return rc;
+  }
+  if (hp.segs.empty()) return TAB_OK;
+  if (use_single_cta(h)) {
+    SctProgArgs A;
+    A.X = h->X;
+    A.Z = h->Z;
+    A.R = h->R;
+    A.n = h->n;
+    A.Wh = h->Wh;
+    A.segs = dp.segs;
+    A.nsegs = (int)hp.segs.size();
+    A.ops = dp.ops;
+    A.layer_off = dp.layer;
+    A.seed = seed;
+    A.cid = h->cid;
+    A.shot = h->shot;
+    A.k0 = h->k;
+    A.out = h->log + h->log_len;
+    A.err = h->mw.err;
+    CU(launch_sct_program(A, h->stream));
+    h->launches++;
+    h->k += (uint64_t)hp.n_meas;
+    h->log_len += hp.n_meas;
+    return TAB_OK;
+  }
+  for (const Seg& s : hp.segs) {
+    if (s.kind == 0) {
+      CU(launch_gates_slab(h->X, h->Z, h->R, h->n, h->W, dp.ops, dp.layer + s.layer_begin,
+                           (int)(s.layer_end - s.layer_begin), h->stream));
+      h->launches++;
+    } else {
+      const int nm = (int)(s.op_end - s.op_begin);
+      CU(launch_measure(h->X, h->Z, h->R, h->n, h->Wh, dp.ops + s.op_begin, nm, h->k, seed,
+                        h->cid, h->shot, h->log + h->log_len, h->mw, h->meas_ctas, h->stream));
+      h->launches++;
+      h->k += (uint64_t)nm;
+      h->log_len += nm;
+    }
+  }
+  return TAB_OK;
+}
+
+int upload(const HostProgram& hp, DevProg* d, cudaStream_t s, bool async_alloc) {
+  const size_t ob = std::max<size_t>(hp.ops.size(), 1) * 4;
+  const size_t lb = std::max<size_t>(hp.layer_off.size(), 1) * 4;
+  const size_t sb = std::max<size_t>(hp.segs.size(), 1) * sizeof(Seg);
+  if (async_alloc) {
+    CU(cudaMallocAsync((void**)&d->ops, ob, s));
+    CU(cudaMallocAsync((void**)&d->layer, lb, s));
+    CU(cudaMallocAsync((void**)&d->segs, sb, s));
+  } else {
+    CU(cudaMalloc((void**)&d->ops, ob));
+    CU(cudaMalloc((void**)&d->layer, lb));
+    CU(cudaMalloc((void**)&d->segs, sb));
+  }
+  if (!hp.ops.empty())
+    CU(cudaMemcpyAsync(d->ops, hp.ops.data(), hp.ops.size() * 4, cudaMemcpyHostToDevice, s));
+  if (!hp.layer_off.empty())
+    CU(cudaMemcpyAsync(d->layer, hp.layer_off.data(), hp.layer_off.size() * 4,
+                       cudaMemcpyHostToDevice, s));
+  if (!hp.segs.empty())
+    CU(cudaMemcpyAsync(d->segs, hp.segs.data(), hp.segs.size() * sizeof(Seg),
+                       cudaMemcpyHostToDevice, s));
+  return TAB_OK;
+}
+
+void free_async(DevProg& d, cudaStream_t s) {
+  if (d.ops) cudaFreeAsync(d.ops, s);
+  if (d.layer) cudaFreeAsync(d.layer, s);
+  if (d.segs) cudaFreeAsync(d.segs, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tab_last_error(void) { return tab::last_error(); }
+
+size_t tab_bytes_required(int32_t n) {
+  if (n < 1 || n > TAB_MAX_QUBITS) return 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  return sizes_for(n, sm_count_of(dev)).total;
+}
+
+int tab_create(int32_t n, tab_t* out) {
+  if (!out) {
+    set_error("null output pointer");
+    return TAB_EINVAL;
+  }
+  *out = nullptr;
+  if (n < 1 || n > TAB_MAX_QUBITS) {
+    set_error("n=%d outside [1, %d]", n, TAB_MAX_QUBITS);
+    return TAB_ERANGE;
+  }
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  const size_t bytes = sizes_for(n, sm_count_of(dev)).total;
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc of %zu bytes failed", bytes);
+    return TAB_ENOMEM;
+  }
+  tab_t h = new (std::nothrow) tab_s();
+  if (!h) {
+    cudaFree(mem);
+    set_error("host allocation failed");
+    return TAB_ENOMEM;
+  }
+  int rc = setup(h, n, mem, true);
+  if (rc != TAB_OK) {
+    cudaFree(mem);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return TAB_OK;
+}
+
+int tab_create_on(int32_t n, void* dev_ptr, size_t bytes, void* cuda_stream, tab_t* out) {
+  if (!out || !dev_ptr) {
+    set_error("null pointer argument");
+    return TAB_EINVAL;
+  }
+  *out = nullptr;
+  if (n < 1 || n > TAB_MAX_QUBITS) {
+    set_error("n=%d outside [1, %d]", n, TAB_MAX_QUBITS);
+    return TAB_ERANGE;
+  }
+  if (((uintptr_t)dev_ptr & 255) != 0) {
+    set_error("caller memory must be 256-byte aligned");
+    return TAB_EINVAL;
+  }
+  const size_t need = tab_bytes_required(n);
+  if (bytes < need) {
+    set_error("caller memory too small: %zu < %zu bytes", bytes, need);
+    return TAB_ENOMEM;
+  }
+  tab_t h = new (std::nothrow) tab_s();
+  if (!h) {
+    set_error("host allocation failed");
+    return TAB_ENOMEM;
+  }
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  int rc = setup(h, n, dev_ptr, false);
+  if (rc != TAB_OK) {
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return TAB_OK;
+}
+
+int tab_destroy(tab_t h) {
+  if (!h) return TAB_OK;
+  cudaStreamSynchronize(h->stream);
+  if (h->log) cudaFreeAsync(h->log, h->stream);
+  cudaStreamSynchronize(h->stream);
+  if (h->own_mem && h->base) cudaFree(h->base);
+  delete h;
+  return TAB_OK;
+}
+
+int tab_num_qubits(tab_t h, int32_t* n) {
+  if (!h || !n) {
+    set_error("null argument");
+    return TAB_EINVAL;
+  }
+  *n = h->n;
+  return TAB_OK;
+}
+
+int tab_set_stream(tab_t h, void* cuda_stream) {
+  if (!h) {
+    set_error("null handle");
+    return TAB_EINVAL;
+  }
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  return TAB_OK;
+}
+
+int tab_set_rng(tab_t h, uint64_t seed, uint64_t circuit_id, uint32_t shot) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  h->seed = seed;
+  h->cid = circuit_id;
+  h->shot = shot;
+  h->k = 0;
+  return TAB_OK;
+}
+
+int tab_reset(tab_t h) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  launch_init(h->X, h->Z, h->R, h->n, h->Wh, h->stream);
+  h->launches++;
+  CU(cudaGetLastError());
+  h->k = 0;
+  h->log_len = 0;
+  return TAB_OK;
+}
+
+int tab_apply(tab_t h, const tab_gate* gates, int64_t count) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  HostProgram hp;
+  rc = build_program(h->n, gates, count, &hp);
+  if (rc) return rc;
+  if (hp.ops.empty()) return TAB_OK;
+  DevProg d;
+  rc = upload(hp, &d, h->stream, true);
+  if (rc == TAB_OK) rc = run_program(h, hp, d, h->seed);
+  free_async(d, h->stream);
+  return rc;
+}
+
+int tab_prog_create(int32_t n, const tab_gate* gates, int64_t count, tab_prog_t* out) {
+  if (!out) {
+    set_error("null output pointer");
+    return TAB_EINVAL;
+  }
+  *out = nullptr;
+  tab_prog_t p = new (std::nothrow) tab_prog_s();
+  if (!p) {
+    set_error("host allocation failed");
+    return TAB_ENOMEM;
+  }
+  int rc = build_program(n, gates, count, &p->hp);
+  if (rc == TAB_OK) {
+    DevProg d;
+    rc = upload(p->hp, &d, nullptr, false);
+    p->d_ops = d.ops;
+    p->d_layer = d.layer;
+    p->d_segs = d.segs;
+  }
+  if (rc == TAB_OK) {
+    cudaError_t e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) {
+      set_error("upload failed: %s", cudaGetErrorString(e));
+      rc = TAB_ECUDA;
+    }
+  }
+  if (rc != TAB_OK) {
+    tab_prog_destroy(p);
+    return rc;
+  }
+  *out = p;
+  return TAB_OK;
+}
+
+int tab_prog_destroy(tab_prog_t p) {
+  if (!p) return TAB_OK;
+  if (p->d_ops) cudaFree(p->d_ops);
+  if (p->d_layer) cudaFree(p->d_layer);
+  if (p->d_segs) cudaFree(p->d_segs);
+  delete p;
+  return TAB_OK;
+}
+
+int tab_prog_info(tab_prog_t p, int64_t* n_gates, int64_t* n_meas, int64_t* n_layers) {
+  if (!p) {
+    set_error("null program");
+    return TAB_EINVAL;
+  }
+  if (n_gates) *n_gates = p->hp.n_gates;
+  if (n_meas) *n_meas = p->hp.n_meas;
+  if (n_layers) {
+    int64_t L = 0;
+    for (const Seg& s : p->hp.segs)
+      if (s.kind == 0) L += s.layer_end - s.layer_begin;
+    *n_layers = L;
+  }
+  return TAB_OK;
+}
+
+int tab_run(tab_t h, tab_prog_t p) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!p) {
+    set_error("null program");
+    return TAB_EINVAL;
+  }
+  if (p->hp.n != h->n) {
+    set_error("program built for n=%d, handle has n=%d", p->hp.n, h->n);
+    return TAB_EINVAL;
+  }
+  DevProg d;
+  d.ops = p->d_ops;
+  d.layer = p->d_layer;
+  d.segs = p->d_segs;
+  return run_program(h, p->hp, d, h->seed);
+}
+
+static int measure_common(tab_t h, const int32_t* qubits, int32_t k, uint64_t seed,
+                          int64_t* first) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (k < 0 || (k > 0 && !qubits)) {
+    set_error("bad qubit list");
+    return TAB_EINVAL;
+  }
+  std::vector<tab_gate> g((size_t)k);
+  for (int32_t i = 0; i < k; ++i) {
+    if (qubits[i] < 0 || qubits[i] >= h->n) {
+      set_error("qubit %d outside [0, %d)", qubits[i], h->n);
+      return TAB_ERANGE;
+    }
+    g[(size_t)i] = tab_make_gate(TAB_MZ, (uint32_t)qubits[i], 0);
+  }
+  HostProgram hp;
+  rc = build_program(h->n, g.data(), k, &hp);
+  if (rc) return rc;
+  *first = h->log_len;
+  if (hp.ops.empty()) return TAB_OK;
+  DevProg d;
+  rc = upload(hp, &d, h->stream, true);
+  if (rc == TAB_OK) rc = run_program(h, hp, d, seed);
+  free_async(d, h->stream);
+  return rc;
+}
+
+int tab_measure(tab_t h, const int32_t* qubits, int32_t k, uint64_t seed, uint8_t* out_bits) {
+  if (k > 0 && !out_bits) {
+    set_error("null output buffer");
+    return TAB_EINVAL;
+  }
+  int64_t first = 0;
+  int rc = measure_common(h, qubits, k, seed, &first);
+  if (rc) return rc;
+  if (k > 0) CU(cudaMemcpyAsync(out_bits, h->log + first, (size_t)k, cudaMemcpyDeviceToHost, h->stream));
+  return poll_device_error(h);
+}
+
+int tab_measure_async(tab_t h, const int32_t* qubits, int32_t k, uint8_t* dev_out_bits) {
+  if (k > 0 && !dev_out_bits) {
+    set_error("null output buffer");
+    return TAB_EINVAL;
+  }
+  int64_t first = 0;
+  int rc = measure_common(h, qubits, k, h ? h->seed : 0, &first);
+  if (rc) return rc;
+  if (k > 0)
+    CU(cudaMemcpyAsync(dev_out_bits, h->log + first, (size_t)k, cudaMemcpyDeviceToDevice, h->stream));
+  return TAB_OK;
+}
+
+int tab_read_outcomes(tab_t h, uint8_t* out, int64_t max, int64_t* count) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (count) *count = h->log_len;
+  const int64_t nb = std::min<int64_t>(max, h->log_len);
+  if (nb > 0) {
+    if (!out) {
+      set_error("null output buffer");
+      return TAB_EINVAL;
+    }
+    CU(cudaMemcpyAsync(out, h->log, (size_t)nb, cudaMemcpyDeviceToHost, h->stream));
+  }
+  return poll_device_error(h);
+}
+
+int tab_clear_outcomes(tab_t h) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  h->log_len = 0;
+  return TAB_OK;
+}
+
+int tab_set_engine(tab_t h, int engine) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (engine < TAB_ENGINE_AUTO || engine > TAB_ENGINE_GRID) {
+    set_error("unknown engine %d", engine);
+    return TAB_EINVAL;
+  }
+  if (engine == TAB_ENGINE_SINGLE_CTA && h->n > TAB_BATCH_MAX_QUBITS) {
+    set_error("single-CTA engine needs n <= %d (n=%d)", TAB_BATCH_MAX_QUBITS, h->n);
+    return TAB_ERANGE;
+  }
+  h->engine = engine;
+  return TAB_OK;
+}
+
+int tab_kernel_launches(tab_t h, int64_t* count) {
+  if (!h || !count) {
+    set_error("null argument");
+    return TAB_EINVAL;
+  }
+  *count = h->launches;
+  return TAB_OK;
+}
+
+int tab_export(tab_t h, uint8_t* x, uint8_t* z, uint8_t* r) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!x || !z || !r) {
+    set_error("null output buffer");
+    return TAB_EINVAL;
+  }
+  const size_t cells = 2 * (size_t)h->n * h->n, rows = 2 * (size_t)h->n;
+  uint8_t* d = nullptr;
+  CU(cudaMallocAsync((void**)&d, 2 * cells + rows, h->stream));
+  CU(launch_unpack(h->X, h->Z, h->R, d, d + cells, d + 2 * cells, h->n, h->Wh, h->stream));
+  h->launches++;
+  CU(cudaMemcpyAsync(x, d, cells, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaMemcpyAsync(z, d + cells, cells, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaMemcpyAsync(r, d + 2 * cells, rows, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaFreeAsync(d, h->stream));
+  return poll_device_error(h);
+}
+
+int tab_import(tab_t h, const uint8_t* x, const uint8_t* z, const uint8_t* r, uint64_t meas_counter) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!x || !z || !r) {
+    set_error("null input buffer");
+    return TAB_EINVAL;
+  }
+  const size_t cells = 2 * (size_t)h->n * h->n, rows = 2 * (size_t)h->n;
+  uint8_t* d = nullptr;
+  CU(cudaMallocAsync((void**)&d, 2 * cells + rows, h->stream));
+  CU(cudaMemcpyAsync(d, x, cells, cudaMemcpyHostToDevice, h->stream));
+  CU(cudaMemcpyAsync(d + cells, z, cells, cudaMemcpyHostToDevice, h->stream));
+  CU(cudaMemcpyAsync(d + 2 * cells, r, rows, cudaMemcpyHostToDevice, h->stream));
+  CU(launch_pack(h->X, h->Z, h->R, d, d + cells, d + 2 * cells, h->n, h->Wh, h->stream));
+  h->launches++;
+  CU(cudaFreeAsync(d, h->stream));
+  h->k = meas_counter;
+  return poll_device_error(h);
+}
+
+int tab_sync(tab_t h) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  return poll_device_error(h);
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// tab_internal.h -- device layout, compiled-program format and launch
+// declarations shared by the kernels and the C-ABI layer of libtab.
+//
+// Device tableau layout ("qubit-major, bit-packed"):
+//   Wh = ceil(n/32) rounded up to a multiple of 4 words per half-column,
+//   W  = 2*Wh words per column.  Word w of a column holds 32 rows: bit b of
+//   word w is packed row 32*w + b.  Destabilizer i is packed row i, stabilizer
+//   i is packed row 32*Wh + i, so a stabilizer and its paired destabilizer sit
+//   at the same bit of words w and w - Wh.  Pad rows are all-zero with sign 0,
+//   and every gate keeps them so.
+//   X plane: X[a*W + w], Z plane: Z[a*W + w] (a = qubit), sign: R[w].
+// A gate therefore touches whole contiguous columns (coalesced sweeps), and a
+// measurement's pivot search reads one contiguous half-column.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/tab.h"
+
+namespace tab {
+
+// ---- device op codes: op<<28 | q1<<14 | q2 (q < 2^14) --------------------
+enum : uint32_t {
+  OP_I = 0, OP_X = 1, OP_Y = 2, OP_Z = 3, OP_H = 4, OP_S = 5, OP_SDG = 6,
+  OP_CNOT = 7, OP_CZ = 8, OP_SWAP = 9, OP_MZ = 10, OP_MZR = 11
+};
+__host__ __device__ __forceinline__ uint32_t dcode(uint32_t op, uint32_t a, uint32_t b) {
+  return (op << 28) | (a << 14) | b;
+}
+__host__ __device__ __forceinline__ uint32_t dop(uint32_t c) { return c >> 28; }
+__host__ __device__ __forceinline__ uint32_t dq1(uint32_t c) { return (c >> 14) & 0x3FFFu; }
+__host__ __device__ __forceinline__ uint32_t dq2(uint32_t c) { return c & 0x3FFFu; }
+
+inline int half_words(int n) { return (((n + 31) / 32) + 3) & ~3; }
+
+// ---- device error word values ---------------------------------------------
+enum : int { DERR_NONE = 0, DERR_TIMEOUT = 1, DERR_PHASE = 2, DERR_BOUNDS = 3 };
+
+// ---- compiled program ----------------------------------------------------------
+// ops[] holds gate segments (gates grouped by layer; a layer's gates act on
+// pairwise-disjoint qubits) and measurement segments (MZ/MZR codes in program
+// order).  layer_off[] holds absolute op offsets of layer boundaries.
+struct Seg {
+  uint32_t kind;       // 0 = gates, 1 = measurements
+  uint32_t op_begin, op_end;
+  uint32_t layer_begin, layer_end;  // gates: layers [layer_begin, layer_end)
+  uint32_t meas_before;             // measurement ops preceding this segment
+};
+
+struct HostProgram {
+  int32_t n = 0;
+  int64_t n_gates = 0, n_meas = 0;
+  std::vector<uint32_t> ops;
+  std::vector<uint32_t> layer_off;  // size = layers + 1 when any gate exists
+  std::vector<Seg> segs;
+};
+
+// Validate + layer a gate list.  Returns TAB_OK or an error (message set).
+int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out);
+
+// ---- global grid barrier state ----------------------------------------------------
+struct GridBar {
+  unsigned int count;
+  unsigned int gen;
+};
+
+// ---- measurement workspace (per handle) ---------------------------------------------
+struct MeasWork {
+  uint32_t* ph;     // [G][2][W] per-CTA partial phases (lo plane, hi plane)
+  uint32_t* r4;     // [2][W]    base phase (lo, hi), owned by CTA 0
+  uint32_t* dp;     // [2][G]    deterministic partials, double-buffered
+  GridBar* bar;
+  int* err;
+  int max_ctas;
+};
+
+// ---- launches (kernels_*.cu) ---------------------------------------------------------
+void launch_init(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh, cudaStream_t s);
+int gates_max_n();
+cudaError_t launch_gates_slab(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
+                              const uint32_t* ops, const uint32_t* layer_off,
+                              int nlayers, cudaStream_t s);
+cudaError_t launch_measure(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh,
+                           const uint32_t* mops, int nm, uint64_t k0, uint64_t seed,
+                           uint64_t cid, uint32_t shot, uint8_t* out, const MeasWork& mw,
+                           int ctas, cudaStream_t s);
+int measure_ctas_for(int n, int sm_count, int max_ctas);
+size_t measure_work_words(int n, int max_ctas);
+cudaError_t launch_pack(uint32_t* X, uint32_t* Z, uint32_t* R, const uint8_t* xs,
+                        const uint8_t* zs, const uint8_t* rs, int n, int Wh, cudaStream_t s);
+cudaError_t launch_unpack(const uint32_t* X, const uint32_t* Z, const uint32_t* R,
+                          uint8_t* xs, uint8_t* zs, uint8_t* rs, int n, int Wh,
+                          cudaStream_t s);
+
+// thread-local error message
+void set_error(const char* fmt, ...);
+
+}  // namespace tab

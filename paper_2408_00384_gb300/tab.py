@@ -1,0 +1,301 @@
+"""ctypes binding of libtab (include/tab.h): argument marshalling only.
+
+Every step of the tableau path runs in the library's CUDA kernels; this module
+converts numpy arrays and torch streams / tensors to plain pointers and maps
+status codes to exceptions.  Importing it raises ImportError when libtab.so is
+missing -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtab.so")
+
+TAB_OK, TAB_EINVAL, TAB_ERANGE, TAB_ENOMEM = 0, -1, -2, -3
+TAB_ECUDA, TAB_EDEVICE, TAB_ETIMEOUT, TAB_ESTATE = -4, -5, -6, -7
+STATUS_NAMES = {0: "TAB_OK", -1: "TAB_EINVAL", -2: "TAB_ERANGE", -3: "TAB_ENOMEM",
+                -4: "TAB_ECUDA", -5: "TAB_EDEVICE", -6: "TAB_ETIMEOUT", -7: "TAB_ESTATE"}
+MAX_QUBITS = 16384
+ENGINE_AUTO, ENGINE_SINGLE_CTA, ENGINE_GRID = 0, 1, 2
+BATCH_MAX_QUBITS = 640
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"libtab.so not found at {LIB_PATH}: build it with "
+        "`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback exists)")
+
+_L = ctypes.CDLL(LIB_PATH)
+
+_vp, _i32, _i64, _u32, _u64, _sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                    ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t)
+_P = ctypes.POINTER
+
+
+class TabCircuit(ctypes.Structure):
+    _fields_ = [("n", _i32), ("gates", _vp), ("n_gates", _i64), ("shots", _i32),
+                ("circuit_id", _u64)]
+
+
+def _sig(name, res, args):
+    f = getattr(_L, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_sig("tab_last_error", ctypes.c_char_p, [])
+_sig("tab_bytes_required", _sz, [_i32])
+_sig("tab_create", ctypes.c_int, [_i32, _P(_vp)])
+_sig("tab_create_on", ctypes.c_int, [_i32, _vp, _sz, _vp, _P(_vp)])
+_sig("tab_destroy", ctypes.c_int, [_vp])
+_sig("tab_num_qubits", ctypes.c_int, [_vp, _P(_i32)])
+_sig("tab_set_stream", ctypes.c_int, [_vp, _vp])
+_sig("tab_set_rng", ctypes.c_int, [_vp, _u64, _u64, _u32])
+_sig("tab_reset", ctypes.c_int, [_vp])
+_sig("tab_apply", ctypes.c_int, [_vp, _vp, _i64])
+_sig("tab_prog_create", ctypes.c_int, [_i32, _vp, _i64, _P(_vp)])
+_sig("tab_prog_destroy", ctypes.c_int, [_vp])
+_sig("tab_prog_info", ctypes.c_int, [_vp, _P(_i64), _P(_i64), _P(_i64)])
+_sig("tab_run", ctypes.c_int, [_vp, _vp])
+_sig("tab_measure", ctypes.c_int, [_vp, _vp, _i32, _u64, _vp])
+_sig("tab_measure_async", ctypes.c_int, [_vp, _vp, _i32, _vp])
+_sig("tab_read_outcomes", ctypes.c_int, [_vp, _vp, _i64, _P(_i64)])
+_sig("tab_clear_outcomes", ctypes.c_int, [_vp])
+_sig("tab_kernel_launches", ctypes.c_int, [_vp, _P(_i64)])
+_sig("tab_set_engine", ctypes.c_int, [_vp, ctypes.c_int])
+_sig("tab_export", ctypes.c_int, [_vp, _vp, _vp, _vp])
+_sig("tab_import", ctypes.c_int, [_vp, _vp, _vp, _vp, _u64])
+_sig("tab_sync", ctypes.c_int, [_vp])
+_sig("tab_batch_run", ctypes.c_int, [_vp, _i32, _u64, _vp, _vp])
+_sig("tab_batch_create", ctypes.c_int, [_vp, _i32, _P(_vp)])
+_sig("tab_batch_destroy", ctypes.c_int, [_vp])
+_sig("tab_batch_info", ctypes.c_int, [_vp, _P(_i64), _P(_i64), _P(_i64)])
+_sig("tab_batch_exec", ctypes.c_int, [_vp, _u64, _vp, _vp])
+_sig("tab_batch_launches", ctypes.c_int, [_vp, _P(_i64)])
+
+
+class TabError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def last_error() -> str:
+    m = _L.tab_last_error()
+    return m.decode() if m else ""
+
+
+def _check(rc: int):
+    if rc != TAB_OK:
+        raise TabError(rc, last_error())
+
+
+def _u64arr(gates) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(gates, dtype=np.uint64).reshape(-1))
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream"))  # torch.cuda.Stream
+
+
+def bytes_required(n: int) -> int:
+    return int(_L.tab_bytes_required(n))
+
+
+class Program:
+    """A gate list compiled once (validated, layered, uploaded); see tab_prog_create."""
+
+    def __init__(self, n: int, gates):
+        g = _u64arr(gates)
+        h = _vp()
+        _check(_L.tab_prog_create(n, g.ctypes.data if g.size else None, g.size, ctypes.byref(h)))
+        self._h = h
+        self.n = n
+
+    def info(self):
+        a, b, c = _i64(), _i64(), _i64()
+        _check(_L.tab_prog_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"n_gates": a.value, "n_meas": b.value, "n_layers": c.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _L.tab_prog_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+class Tableau:
+    """A device-resident n-qubit tableau (tab_create / tab_create_on)."""
+
+    def __init__(self, n: int, stream=None, memory=None):
+        h = _vp()
+        self._mem = memory
+        if memory is not None:  # a torch CUDA tensor (uint8) the caller keeps alive
+            ptr = int(memory.data_ptr())
+            nbytes = int(memory.numel() * memory.element_size())
+            _check(_L.tab_create_on(n, ptr, nbytes, _stream_handle(stream), ctypes.byref(h)))
+        else:
+            _check(_L.tab_create(n, ctypes.byref(h)))
+            if stream is not None:
+                _check(_L.tab_set_stream(h, _stream_handle(stream)))
+        self._h = h
+        self.n = n
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            _L.tab_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- configuration
+    def set_stream(self, stream):
+        _check(_L.tab_set_stream(self._h, _stream_handle(stream)))
+
+    def set_rng(self, seed: int = 1, circuit_id: int = 0, shot: int = 0):
+        _check(_L.tab_set_rng(self._h, seed, circuit_id, shot))
+
+    def reset(self):
+        _check(_L.tab_reset(self._h))
+
+    def set_engine(self, engine: int):
+        """ENGINE_AUTO, ENGINE_SINGLE_CTA or ENGINE_GRID (bit-identical results)."""
+        _check(_L.tab_set_engine(self._h, engine))
+
+    # -- gates / measurements
+    def apply(self, gates):
+        g = _u64arr(gates)
+        _check(_L.tab_apply(self._h, g.ctypes.data if g.size else None, g.size))
+
+    def run(self, prog: Program):
+        _check(_L.tab_run(self._h, prog._h))
+
+    def measure(self, qubits: Sequence[int], seed: int = 1) -> np.ndarray:
+        q = np.ascontiguousarray(np.asarray(qubits, dtype=np.int32).reshape(-1))
+        out = np.zeros(max(q.size, 1), np.uint8)
+        _check(_L.tab_measure(self._h, q.ctypes.data if q.size else None, q.size, seed,
+                              out.ctypes.data))
+        return out[:q.size]
+
+    def measure_async(self, qubits: Sequence[int], dev_out_ptr: int):
+        q = np.ascontiguousarray(np.asarray(qubits, dtype=np.int32).reshape(-1))
+        _check(_L.tab_measure_async(self._h, q.ctypes.data if q.size else None, q.size,
+                                    dev_out_ptr))
+
+    def read_outcomes(self) -> np.ndarray:
+        cnt = _i64()
+        _check(_L.tab_read_outcomes(self._h, None, 0, ctypes.byref(cnt)))
+        out = np.zeros(max(cnt.value, 1), np.uint8)
+        _check(_L.tab_read_outcomes(self._h, out.ctypes.data, cnt.value, ctypes.byref(cnt)))
+        return out[:cnt.value]
+
+    def clear_outcomes(self):
+        _check(_L.tab_clear_outcomes(self._h))
+
+    def sync(self):
+        _check(_L.tab_sync(self._h))
+
+    @property
+    def launches(self) -> int:
+        c = _i64()
+        _check(_L.tab_kernel_launches(self._h, ctypes.byref(c)))
+        return c.value
+
+    # -- state transfer
+    def export(self):
+        n = self.n
+        x = np.zeros((2 * n, n), np.uint8)
+        z = np.zeros((2 * n, n), np.uint8)
+        r = np.zeros(2 * n, np.uint8)
+        _check(_L.tab_export(self._h, x.ctypes.data, z.ctypes.data, r.ctypes.data))
+        return x, z, r
+
+    def import_(self, x, z, r, meas_counter: int = 0):
+        n = self.n
+        x = np.ascontiguousarray(x, dtype=np.uint8).reshape(2 * n, n)
+        z = np.ascontiguousarray(z, dtype=np.uint8).reshape(2 * n, n)
+        r = np.ascontiguousarray(r, dtype=np.uint8).reshape(2 * n)
+        _check(_L.tab_import(self._h, x.ctypes.data, z.ctypes.data, r.ctypes.data,
+                             meas_counter))
+
+
+def _circuit_array(circuits):
+    """circuits: iterable of (n, gates uint64 array, shots, circuit_id)."""
+    keep = []
+    arr = (TabCircuit * len(circuits))()
+    for i, (n, gates, shots, cid) in enumerate(circuits):
+        g = _u64arr(gates)
+        keep.append(g)
+        arr[i] = TabCircuit(n, g.ctypes.data if g.size else None, g.size, shots, cid)
+    return arr, keep
+
+
+def n_meas_of(gates) -> int:
+    op = (_u64arr(gates) >> np.uint64(56))
+    return int(np.isin(op, (10, 11)).sum())
+
+
+def batch_run(circuits, seed: int = 1) -> list:
+    """Run (n, gates, shots, circuit_id) circuits in one batched call.
+
+    Returns, per circuit, a (shots, n_meas) uint8 array of outcomes."""
+    arr, keep = _circuit_array(circuits)
+    sizes = [shots * n_meas_of(g) for (_, g, shots, _) in circuits]
+    total = int(sum(sizes))
+    out = np.zeros(max(total, 1), np.uint8)
+    _check(_L.tab_batch_run(ctypes.cast(arr, _vp), len(circuits), seed, out.ctypes.data, None))
+    res, off = [], 0
+    for (n, g, shots, _), sz in zip(circuits, sizes):
+        res.append(out[off:off + sz].reshape(shots, -1) if sz else
+                   np.zeros((shots, 0), np.uint8))
+        off += sz
+    return res
+
+
+class Batch:
+    """A compiled batch (tab_batch_create) replayed with exec()."""
+
+    def __init__(self, circuits):
+        arr, keep = _circuit_array(circuits)
+        h = _vp()
+        _check(_L.tab_batch_create(ctypes.cast(arr, _vp), len(circuits), ctypes.byref(h)))
+        self._h = h
+        self.sizes = [shots * n_meas_of(g) for (_, g, shots, _) in circuits]
+
+    def info(self):
+        a, b, c = _i64(), _i64(), _i64()
+        _check(_L.tab_batch_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"n_gates": a.value, "n_meas": b.value, "out_bytes": c.value}
+
+    def exec(self, seed: int, dev_out_ptr: int, stream=None):
+        _check(_L.tab_batch_exec(self._h, seed, dev_out_ptr, _stream_handle(stream)))
+
+    @property
+    def launches(self) -> int:
+        c = _i64()
+        _check(_L.tab_batch_launches(self._h, ctypes.byref(c)))
+        return c.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _L.tab_batch_destroy(self._h)
+            self._h = None
+
+    __del__ = close

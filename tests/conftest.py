@@ -7,5 +7,10 @@ if ROOT not in sys.path:
 
 
 def pytest_configure(config):
+    # the C oracle and libtab are built in-tree (idempotent, seconds when stale)
+    from oracle import build as obuild
+    from paper_2408_00384_gb300 import build as pbuild
+    obuild.build()
+    pbuild.build()
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running CPU test")

@@ -1,0 +1,241 @@
+"""GPU path vs the CPU oracle, bit for bit, through the C ABI.
+
+Every comparison is element by element: all outcome bytes and every tableau bit
+(x, z and sign of all 2n rows).  Both engines (single-CTA and grid) are
+checked.  The oracle's inputs come from the seeded generators only.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import circuits as C
+
+pytestmark = pytest.mark.gpu
+
+from paper_2408_00384_gb300 import tab  # noqa: E402  (fails loudly when libtab.so is missing)
+
+
+def gpu_run(n, gates, seed=1, cid=0, shot=0, engine=None):
+    with tab.Tableau(n) as t:
+        if engine is not None:
+            t.set_engine(engine)
+        t.set_rng(seed, cid, shot)
+        t.apply(gates)
+        out = t.read_outcomes()
+        x, z, r = t.export()
+    return out, (x, z, r)
+
+
+def assert_same(n, gates, seed=1, cid=0, shot=0, engine=None):
+    want_out, want = oracle.run_circuit(n, gates, seed=seed, circuit_id=cid, shot=shot)
+    got_out, got = gpu_run(n, gates, seed, cid, shot, engine)
+    assert np.array_equal(got_out, want_out), (n, engine, np.nonzero(got_out != want_out)[0][:10])
+    for name, g, w in zip("xzr", got, want):
+        bad = np.argwhere(g != w)
+        assert bad.size == 0, (n, engine, name, bad[:10].tolist())
+
+
+ENGINES = [tab.ENGINE_SINGLE_CTA, tab.ENGINE_GRID]
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_config1(engine):
+    c = C.config1()
+    assert_same(c.n, c.gates, seed=C.PHILOX_SEED, engine=engine)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 63, 64, 65, 127, 128, 129, 200])
+def test_random_ops_all_gates(engine, n):
+    gates = C.random_clifford_ops(n, 400, seed=7 * n + 1, measure_p=0.08, reset_p=0.04)
+    assert_same(n, gates, seed=3, cid=n, shot=1, engine=engine)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("n,depth", [(257, 12), (480, 6), (511, 5), (640, 4)])
+def test_layer_circuits_final_measure(engine, n, depth):
+    c = C.random_layer_circuit(n, depth, seed=n, meas_every=3, meas_frac=0.05)
+    assert_same(n, c.gates, seed=11, engine=engine)
+
+
+@pytest.mark.parametrize("n", [700, 1000, 2049])
+def test_grid_engine_larger(n):
+    c = C.random_layer_circuit(n, 8, seed=n, meas_every=4, meas_frac=0.02)
+    assert_same(n, c.gates, seed=5, engine=tab.ENGINE_GRID)
+
+
+def test_config2_full():
+    """n=1000, 1000 random layers, final MZ on all qubits: full compare."""
+    c = C.config2()
+    assert_same(c.n, c.gates, seed=C.PHILOX_SEED)
+
+
+def test_config3_prefix_full_size():
+    """n=10,000: the first 10 layers and the first 24 MZR of the first round,
+    on the full-size tableau, compared with the oracle bit for bit."""
+    c = C.config3()
+    op, _, _ = C.decode(c.gates)
+    first_meas = int(np.argmax(np.isin(op, C.MEASURE)))
+    prefix = c.gates[:first_meas + 24]
+    assert_same(c.n, prefix, seed=C.PHILOX_SEED)
+
+
+def commutation_ok(x, z, rows_a, rows_b, n):
+    """Tableau rows i, j anticommute iff {i, j} = {k, k+n}."""
+    xa, za = x[rows_a].astype(np.int64), z[rows_a].astype(np.int64)
+    xb, zb = x[rows_b].astype(np.int64), z[rows_b].astype(np.int64)
+    sym = (xa @ zb.T + za @ xb.T) % 2
+    want = ((rows_a[:, None] % n == rows_b[None, :] % n) & (rows_a[:, None] != rows_b[None, :]))
+    return np.array_equal(sym, want.astype(np.int64))
+
+
+def test_config3_full_invariants():
+    """Whole config 3 on the GPU: the tableau stays symplectic (sampled row
+    pairs), and the qubits of the last MZR round measure 0 deterministically."""
+    c = C.config3()
+    with tab.Tableau(c.n) as t:
+        t.set_rng(C.PHILOX_SEED, 0, 0)
+        t.apply(c.gates)
+        out = t.read_outcomes()
+        assert out.size == c.n_meas
+        x, z, r = t.export()
+        op, q1, _ = C.decode(c.gates)
+        last_round = q1[np.isin(op, C.MEASURE)][-(c.n // 10):][:64]
+        again = t.measure(last_round.astype(np.int32), seed=99)
+    assert not again.any()
+    assert 0.4 < out.mean() < 0.6
+    rng = np.random.default_rng(0)
+    rows = rng.choice(2 * c.n, size=300, replace=False)
+    assert commutation_ok(x, z, rows, rows, c.n)
+    paired = np.unique(np.concatenate([rows[:100] % c.n, rows[:100] % c.n + c.n]))
+    assert commutation_ok(x, z, paired, paired, c.n)
+
+
+def test_empty_and_measure_first():
+    assert_same(5, np.zeros(0, np.uint64))
+    g = C.encode(np.full(4, C.TAB_MZ), np.array([0, 1, 1, 3]), 0)
+    for e in ENGINES:
+        assert_same(4, g, engine=e)
+
+
+def test_invalid_gate_applies_nothing():
+    n = 8
+    good = C.random_clifford_ops(n, 50, seed=1)
+    bad = np.concatenate([good, C.encode(C.TAB_H, n, 0).reshape(1)])
+    with tab.Tableau(n) as t:
+        t.apply(good)
+        before = t.export()
+        with pytest.raises(tab.TabError) as ei:
+            t.apply(bad)
+        assert ei.value.code == tab.TAB_ERANGE
+        with pytest.raises(tab.TabError) as ei:
+            t.apply(C.encode(C.TAB_CZ, 2, 2).reshape(1))
+        assert ei.value.code == tab.TAB_EINVAL
+        after = t.export()
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_checkpoint_resume(engine):
+    n = 150
+    gates = C.random_clifford_ops(n, 600, seed=42, measure_p=0.05, reset_p=0.05)
+    want_out, want = oracle.run_circuit(n, gates, seed=8, circuit_id=2, shot=5)
+    half = 300
+    op, _, _ = C.decode(gates[:half])
+    k = int(np.isin(op, C.MEASURE).sum())
+    with tab.Tableau(n) as t:
+        t.set_engine(engine)
+        t.set_rng(8, 2, 5)
+        t.apply(gates[:half])
+        out1 = t.read_outcomes()
+        snap = t.export()
+    with tab.Tableau(n) as t2:
+        t2.set_engine(engine)
+        t2.set_rng(8, 2, 5)
+        t2.import_(*snap, meas_counter=k)
+        t2.apply(gates[half:])
+        out2 = t2.read_outcomes()
+        got = t2.export()
+    assert np.array_equal(np.concatenate([out1, out2]), want_out)
+    for g, w in zip(got, want):
+        assert np.array_equal(g, w)
+
+
+def test_measure_call_seed():
+    n = 40
+    gates = C.random_clifford_ops(n, 300, seed=3)
+    qs = np.array([5, 1, 39, 5, 0], np.int32)
+    t_or = oracle.Tableau(n)
+    t_or.run(gates)
+    want = t_or.run(C.encode(np.full(qs.size, C.TAB_MZ), qs, 0), seed=1234)
+    for e in ENGINES:
+        with tab.Tableau(n) as t:
+            t.set_engine(e)
+            t.apply(gates)
+            got = t.measure(qs, seed=1234)
+        assert np.array_equal(got, want)
+
+
+def test_create_on_torch_memory_and_stream():
+    torch = pytest.importorskip("torch")
+    n = 300
+    c = C.random_layer_circuit(n, 10, seed=5)
+    want_out, want = oracle.run_circuit(n, c.gates, seed=1)
+    mem = torch.empty(tab.bytes_required(n), dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    with tab.Tableau(n, stream=s, memory=mem) as t:
+        t.set_engine(tab.ENGINE_GRID)
+        t.apply(c.gates)
+        out = t.read_outcomes()
+        got = t.export()
+    assert np.array_equal(out, want_out)
+    for g, w in zip(got, want):
+        assert np.array_equal(g, w)
+
+
+def test_compiled_program_replay():
+    c = C.random_layer_circuit(180, 20, seed=9)
+    want_out, want = oracle.run_circuit(c.n, c.gates, seed=4)
+    prog = tab.Program(c.n, c.gates)
+    info = prog.info()
+    assert info["n_gates"] == c.n_gates and info["n_meas"] == c.n_meas
+    for e in ENGINES:
+        with tab.Tableau(c.n) as t:
+            t.set_engine(e)
+            for _ in range(2):
+                t.reset()
+                t.set_rng(4, 0, 0)
+                t.run(prog)
+                out = t.read_outcomes()
+                assert np.array_equal(out, want_out)
+            got = t.export()
+        for g, w in zip(got, want):
+            assert np.array_equal(g, w)
+
+
+def test_batch_small_vs_oracle():
+    rng = np.random.default_rng(1)
+    circuits = []
+    for c in range(24):
+        n = int(rng.integers(1, 90))
+        depth = int(rng.integers(1, 12))
+        circ = C.random_layer_circuit(n, depth, seed=100 + c, meas_every=4 if c % 3 == 0 else 0,
+                                      meas_frac=0.2)
+        circuits.append((n, circ.gates, int(rng.integers(1, 5)), 1000 + c))
+    res = tab.batch_run(circuits, seed=77)
+    for (n, g, shots, cid), got in zip(circuits, res):
+        for s in range(shots):
+            want, _ = oracle.run_circuit(n, g, seed=77, circuit_id=cid, shot=s)
+            assert np.array_equal(got[s], want), (n, cid, s)
+
+
+def test_batch_config4_sample():
+    """A slice of the batched family (n up to 512) against the oracle."""
+    circs = C.config4(only=list(range(0, 4096, 512)))
+    circuits = [(c.n, c.gates, min(c.shots, 2), c.circuit_id) for c in circs]
+    res = tab.batch_run(circuits, seed=C.PHILOX_SEED)
+    for (n, g, shots, cid), got in zip(circuits, res):
+        for s in range(shots):
+            want, _ = oracle.run_circuit(n, g, seed=C.PHILOX_SEED, circuit_id=cid, shot=s)
+            assert np.array_equal(got[s], want), (n, cid, s)
