@@ -1,0 +1,444 @@
+"""Benchmark of the stabilizer-tableau hot path on GB300.
+
+Default workload (one "step" = the whole path once): a plain tableau of
+n = 1,000 qubits, reset to |0^n>, 1,000 random layers (H or S on every qubit,
+then n/2 random disjoint CNOT/CZ pairs, CNOT:CZ = 3:1), then a Z measurement
+of every qubit with Philox outcomes -- 1,500,000 gates and 1,000 measurements.
+Inputs are resident in device memory when timing starts (a compiled program);
+L2 is flushed (a 256 MB device write) before every timed step.
+
+Prints ONE JSON line.  `--impl reference` times the CPU oracle (an unpacked
+one-byte-per-bit restatement of the same algorithm) instead.  Under torchrun
+every rank runs an independent replica on its own GPU (weak scaling, no
+collective on the data path); rank 0 prints.
+
+Other workloads (`--workload`): `cfg1` (n=10), `cfg3` (n=10,000 with MZR
+rounds), `batched` (4,096 circuits with n in [16, 512] and 1-64 shots).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("Clifford gates/sec and measurements/sec, batched vs plain path; "
+          "p50/p99 latency")
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "batched"])
+    p.add_argument("--engine", default="auto", choices=["auto", "grid", "single"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------ distributed ---
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------- workloads ---
+
+def workload(name, rank):
+    from workloads import circuits as C
+    if name == "cfg1":
+        c = C.config1(seed_index=rank)
+        desc = ("plain tableau n=10, 20 random layers (H/S per qubit, 5 CNOT pairs), "
+                "final MZ on all qubits, 1 shot")
+    elif name == "cfg2":
+        c = C.config2(seed_index=rank)
+        desc = ("plain tableau n=1000, 1000 random layers (H/S per qubit, n/2 CNOT/CZ "
+                "pairs 3:1), final MZ on all qubits, 1 shot")
+    else:
+        c = C.config3(seed_index=rank)
+        desc = ("plain tableau n=10000, 100 random layers, MZR on 1000 random qubits "
+                "after every 10th layer, 1 shot")
+    return c, desc
+
+
+def split_program(c):
+    """(gate words, measurement words) of a circuit whose measurements are all
+    at the end; None if measurements are interleaved."""
+    from workloads import circuits as C
+    op, _, _ = C.decode(c.gates)
+    m = np.isin(op, C.MEASURE)
+    if not m.any():
+        return c.gates, c.gates[:0]
+    first = int(np.argmax(m))
+    if m[first:].all():
+        return c.gates[:first], c.gates[first:]
+    return None
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.15)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- oracle ---
+
+def oracle_step_seconds(c, budget_s):
+    """Oracle seconds for one full step of circuit c, extrapolated from a
+    time-bounded sample: random layers are run one at a time for about half
+    the budget, then the circuit's measurement ops one at a time for the other
+    half; the full step is (seconds per layer x depth) + (seconds per
+    measurement x measurements)."""
+    import oracle
+    from workloads import circuits as C
+    op, _, _ = C.decode(c.gates)
+    is_meas = np.isin(op, C.MEASURE)
+    gate_words = c.gates[~is_meas]
+    meas_words = c.gates[is_meas]
+    per_layer = c.n + c.n // 2 + 2            # gates + 2 barrier words per layer
+    t = oracle.Tableau(c.n)
+    layers, t0 = 0, time.perf_counter()
+    while layers < c.depth and time.perf_counter() - t0 < budget_s / 2:
+        t.run(gate_words[layers * per_layer:(layers + 1) * per_layer])
+        layers += 1
+    tg = time.perf_counter() - t0
+    meas, t1 = 0, time.perf_counter()
+    while meas < meas_words.size and time.perf_counter() - t1 < budget_s / 2:
+        t.run(meas_words[meas:meas + 1], seed=1)
+        meas += 1
+    tm = time.perf_counter() - t1
+    est = tg * (c.depth / max(layers, 1)) + (tm * (c.n_meas / meas) if meas else 0.0)
+    sample = (f"first {layers} of {c.depth} layers ({tg:.2f} s) and {meas} of {c.n_meas} "
+              f"measurements ({tm:.2f} s) on one core, scaled to the full step")
+    return est, sample
+
+
+# ------------------------------------------------------------- reference ---
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    c, desc = workload(args.workload if args.workload != "batched" else "cfg2", 0)
+    budget = max(1.0, 150.0 / (args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_step_seconds(c, min(budget, 2.0))
+    times, samples = [], []
+    for _ in range(args.steps):
+        est, sample = oracle_step_seconds(c, budget)
+        times.append(est)
+        samples.append(sample)
+    ms = 1000.0 * statistics.mean(times)
+    value = c.n_gates / (ms / 1000.0)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "gates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "meas_per_s": c.n_meas / (ms / 1000.0),
+        "config": {"workload": desc, "n": c.n, "gates": c.n_gates,
+                   "measurements": c.n_meas},
+        "cpu_baseline": {"value": value, "unit": "gates/s", "cores": 1, "kind": "oracle",
+                         "sample": samples[-1]},
+        "e2e": {"value": value, "unit": "gates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ ours ---
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def run_plain(args, ws, rank, local):
+    import torch
+    from paper_2408_00384_gb300 import tab
+    from workloads import circuits as C
+
+    torch.cuda.set_device(local)
+    c, desc = workload(args.workload, rank)
+    parts = split_program(c)
+    stream = torch.cuda.Stream()
+    t = tab.Tableau(c.n, stream=stream)
+    eng = {"auto": tab.ENGINE_AUTO, "grid": tab.ENGINE_GRID, "single": tab.ENGINE_SINGLE_CTA}
+    t.set_engine(eng[args.engine])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    if parts is not None:
+        progs = [tab.Program(c.n, parts[0]), tab.Program(c.n, parts[1])]
+        kinds = ["gates", "measure"]
+    else:
+        progs = [tab.Program(c.n, c.gates)]
+        kinds = ["program"]
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        t.reset()
+        t.set_rng(C.PHILOX_SEED, rank, 0)
+        for i, p in enumerate(progs):
+            t.run(p)
+            if evs:
+                evs[i + 1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    t.sync()
+    nprog = len(progs)
+    all_evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nprog + 1)]
+               for _ in range(args.steps)]
+    launches0 = t.launches
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        with torch.cuda.stream(stream):   # same stream as the timed work
+            flush.fill_(s & 0xFF)
+        step(all_evs[s])
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    t.sync()
+    launches = t.launches - launches0
+    per_step = [all_evs[s][0].elapsed_time(all_evs[s][-1]) for s in range(args.steps)]
+    per_kind = {k: [all_evs[s][i].elapsed_time(all_evs[s][i + 1]) for s in range(args.steps)]
+                for i, k in enumerate(kinds)}
+    ms_local = statistics.mean(per_step)
+    ms = allreduce_max(ms_local, ws)
+    value = ws * c.n_gates / (ms / 1000.0)
+    meas_s = ws * c.n_meas / (ms / 1000.0)
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pinned = torch.from_numpy(c.gates.view(np.int64)).pin_memory()
+        host_gates = pinned.numpy().view(np.uint64)
+        out = np.zeros(c.n_meas, np.uint8)
+        ke = max(3, min(args.steps, 10))
+        for i in range(ke + 2):
+            if i == 2:
+                torch.cuda.synchronize()
+                barrier(ws)
+                t0 = time.perf_counter()
+            t.reset()
+            t.set_rng(C.PHILOX_SEED, rank, 0)
+            t.apply(host_gates)
+            got = t.read_outcomes()   # synchronizes: device -> host copy of the outcomes
+            out[:got.size] = got
+        torch.cuda.synchronize()
+        barrier(ws)
+        e2e_s = allreduce_max((time.perf_counter() - t0) / ke, ws)
+        e2e = {"value": ws * c.n_gates / e2e_s, "unit": "gates/s",
+               "h2d_bytes_per_step": int(c.gates.nbytes), "d2h_bytes_per_step": int(c.n_meas),
+               "ms_per_step": 1000.0 * e2e_s}
+
+    # ---- roofline of the dominant kernel
+    pk, src = peaks()
+    kind_ms = {k: statistics.mean(v) for k, v in per_kind.items()}
+    dom = max(kind_ms, key=kind_ms.get)
+    n, Wh = c.n, ((((c.n + 31) // 32) + 3) // 4) * 4
+    if dom == "measure":
+        # algorithmic bytes per random measurement: rows x supp columns read+written
+        # ~ 0.75 n^2 B (n columns in supp(p) ~ 3/4, 2 planes, 2n/8 B, read + write)
+        alg = 0.75 * n * n * c.n_meas
+        roof = {"kernel": "k_measure", "bound": "hbm", "unit": "GB/s"}
+        roof["achieved"] = alg / (kind_ms[dom] / 1000.0) / 1e9
+        roof["peak"] = pk.get("hbm_gbs", FALLBACK_HBM_GBS)
+    else:
+        # algorithmic bytes of a gate run: each gate reads + writes its columns
+        # (1q: x, z, r = 6 * 2n/8 B; 2q: 10 * 2n/8 B)
+        n1 = c.depth * n
+        n2 = c.n_gates - n1
+        alg = (6 * n1 + 10 * n2) * (2 * n / 8)
+        roof = {"kernel": "k_gates_slab", "bound": "hbm", "unit": "GB/s"}
+        roof["achieved"] = alg / (kind_ms[dom] / 1000.0) / 1e9
+        roof["peak"] = pk.get("hbm_gbs", FALLBACK_HBM_GBS)
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["peak_source"] = f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src
+    roof["traffic"] = None
+    roof["kernel_ms"] = kind_ms
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic",
+        "meas_per_s": meas_s,
+        "latency_ms": {"p50": float(np.percentile(per_step, 50)),
+                       "p99": float(np.percentile(per_step, 99))},
+        "config": {"workload": desc, "n": c.n, "gates": c.n_gates,
+                   "measurements": c.n_meas, "parallelism": f"replicas x{ws}",
+                   "l2": "flushed before every timed step (256 MB device write)",
+                   "engine": args.engine},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "roofline": roof,
+        "e2e": e2e,
+    }
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        est, sample = oracle_step_seconds(c, 12.0)
+        line["cpu_baseline"] = {"value": c.n_gates / est, "unit": "gates/s", "cores": 1,
+                                "kind": "oracle", "sample": sample}
+    elif rank == 0 and ws == 1:
+        line["cpu_baseline"] = None
+    t.close()
+    return line
+
+
+def run_batched(args, ws, rank, local):
+    import torch
+    from paper_2408_00384_gb300 import tab
+    from workloads import circuits as C
+
+    torch.cuda.set_device(local)
+    circs = C.config4()
+    circuits = [(c.n, c.gates, c.shots, c.circuit_id + 4096 * rank) for c in circs]
+    b = tab.Batch(circuits)
+    info = b.info()
+    out = torch.empty(max(info["out_bytes"], 1), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        b.exec(C.PHILOX_SEED, out.data_ptr(), stream)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(s & 0xFF)
+        evs[s][0].record(stream)
+        b.exec(C.PHILOX_SEED, out.data_ptr(), stream)
+        evs[s][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    per = [a.elapsed_time(z) for a, z in evs]
+    ms = allreduce_max(statistics.mean(per), ws)
+    line = {
+        "metric": METRIC, "value": ws * info["n_gates"] / (ms / 1000.0), "unit": "gates/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic", "meas_per_s": ws * info["n_meas"] / (ms / 1000.0),
+        "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
+        "config": {"workload": "batched: 4096 random-layer circuits, n ~ U[16,512], depth n, "
+                               "1-64 shots, final MZ on all qubits",
+                   "gates": info["n_gates"], "measurements": info["n_meas"],
+                   "l2": "flushed before every timed step (256 MB device write)"},
+        "gpu_launches": b.launches * args.steps, "clocks": clk, "roofline": None, "e2e": None,
+    }
+    return line
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    if args.workload == "batched":
+        line = run_batched(args, ws, rank, local)
+    else:
+        line = run_plain(args, ws, rank, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

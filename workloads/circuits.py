@@ -123,23 +123,36 @@ def random_layer_circuit(n: int, depth: int, seed: int, *, mix_cz: bool = True,
         rounds.append(np.sort(rng.choice(n, size=k_round, replace=False)))
 
     qubits = np.arange(n, dtype=np.int64)
-    bar = encode(TAB_BARRIER) if barriers else None
+    # one row of gate words per layer: [1q gates | bar | 2q gates | bar]
+    nb = 1 if barriers else 0
+    width = n + nb + npairs + (nb if npairs else 0)
+    blk = np.empty((depth, width), dtype=np.uint64)
+    blk[:, :n] = encode(one_q, qubits[None, :], 0)
+    col = n
+    if barriers:
+        blk[:, col] = encode(TAB_BARRIER)
+        col += 1
+    if npairs:
+        blk[:, col:col + npairs] = encode(two_q, perms[:, 0:2 * npairs:2],
+                                          perms[:, 1:2 * npairs:2])
+        col += npairs
+        if barriers:
+            blk[:, col] = encode(TAB_BARRIER)
     parts: List[np.ndarray] = []
     n_meas = 0
     mop = TAB_MZR if reset else TAB_MZ
-    for d in range(depth):
-        parts.append(encode(one_q[d], qubits, 0))
-        if barriers:
-            parts.append(bar.reshape(1))
-        if npairs:
-            p = perms[d]
-            parts.append(encode(two_q[d], p[0:2 * npairs:2], p[1:2 * npairs:2]))
-            if barriers:
-                parts.append(bar.reshape(1))
-        if meas_every and (d + 1) % meas_every == 0 and k_round:
-            qs = rounds[(d + 1) // meas_every - 1]
+    if meas_every and k_round:
+        start = 0
+        for r in range(n_rounds):
+            stop = (r + 1) * meas_every
+            parts.append(blk[start:stop].reshape(-1))
+            qs = rounds[r]
             parts.append(encode(np.full(qs.size, mop), qs, 0))
             n_meas += int(qs.size)
+            start = stop
+        parts.append(blk[start:].reshape(-1))
+    else:
+        parts.append(blk.reshape(-1))
     if final_measure:
         parts.append(encode(np.full(n, TAB_MZ), qubits, 0))
         n_meas += n
