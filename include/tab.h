@@ -219,6 +219,60 @@ int tab_batch_exec(tab_batch_t b, uint64_t seed, uint8_t *dev_out, void *cuda_st
 /* Number of kernels one tab_batch_exec launches. */
 int tab_batch_launches(tab_batch_t b, int64_t *count);
 
+/* ---- serving: continuous batching of circuit requests -------------------- */
+
+/* A request server keeps many tableaus resident on the device at once.  A
+ * submitted circuit waits in a FIFO until a slot is free and its tableau fits
+ * the memory budget; it is then compiled and its whole program (gate runs,
+ * mid-circuit measurement runs, outcome copy) is enqueued on one of the
+ * server's streams, overlapping with other requests.  When it completes, its
+ * slot and memory go to the next waiting request.  Outcomes of a request
+ * depend only on its own circuit, circuit_id and shots (Philox key = the
+ * server's seed), never on the mix it ran in.  A worker thread owns the
+ * device work; the calls below are thread-safe. */
+typedef struct tab_server_s *tab_server_t;
+
+typedef struct {
+  uint64_t mem_budget_bytes;  /* device bytes for resident tableaus (admission cap) */
+  int32_t max_inflight;       /* requests on the device at once (>= 1) */
+  int32_t n_streams;          /* CUDA streams the requests are spread over (>= 1) */
+  int32_t meas_ctas;          /* CTAs per grid-engine measurement launch; 0 = default */
+  double request_timeout_s;   /* fail a running request not completed by then; 0 = none */
+  uint64_t seed;              /* Philox key of every request */
+} tab_server_config;
+
+enum tab_req_state { TAB_REQ_PENDING = 0, TAB_REQ_RUNNING = 1, TAB_REQ_DONE = 2, TAB_REQ_FAILED = 3 };
+
+/* Host-side fault injection for tests: drop the completion of a request, so
+ * that it fails with TAB_ETIMEOUT at its deadline and its slot is reclaimed. */
+enum tab_fault { TAB_FAULT_DROP_COMPLETION = 1 };
+
+typedef struct {
+  int64_t submitted, completed, failed, rejected;
+  int64_t inflight, queued, peak_inflight;
+  uint64_t mem_used, peak_mem;
+} tab_server_stats;
+
+int tab_server_create(const tab_server_config *cfg, tab_server_t *out);
+/* Validate and enqueue a request (gates are copied).  Invalid gates are
+ * refused here (TAB_ERANGE / TAB_EINVAL) and never reach the device.
+ * *ticket identifies the request. */
+int tab_server_submit(tab_server_t s, const tab_circuit *c, int64_t *ticket);
+/* Current tab_req_state of a request. */
+int tab_server_query(tab_server_t s, int64_t ticket, int *state);
+/* Wait (timeout_s < 0: forever) for a request; copy up to cap outcome bytes
+ * (shot 0's outcomes, then shot 1's, ...) to out, set *count to the total
+ * and *latency_s to submit-to-completion seconds, and forget the ticket.
+ * Returns the request's status: TAB_OK, TAB_ENOMEM (larger than the whole
+ * budget), TAB_ETIMEOUT (deadline passed), or TAB_ESTATE if timeout_s
+ * passed first (the ticket stays valid). */
+int tab_server_wait(tab_server_t s, int64_t ticket, double timeout_s, uint8_t *out, int64_t cap,
+                    int64_t *count, double *latency_s);
+int tab_server_inject(tab_server_t s, int64_t ticket, int kind);
+int tab_server_stats_get(tab_server_t s, tab_server_stats *out);
+/* Finish every submitted request, then stop the worker and free the server. */
+int tab_server_destroy(tab_server_t s);
+
 #ifdef __cplusplus
 }
 #endif

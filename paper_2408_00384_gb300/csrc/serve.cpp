@@ -1,0 +1,439 @@
+// serve.cpp -- continuous-batching request server over device-resident
+// tableaus (tab_server_* in include/tab.h).
+//
+// A worker thread owns the device side.  Requests wait in a FIFO; one is
+// admitted when a slot is free and its tableau fits the device-memory budget.
+// Admission compiles the circuit, allocates its tableau, and enqueues the
+// whole program (gate runs and mid-circuit measurement runs) plus the
+// device-to-host copy of its outcomes on one of the server's streams; the
+// tableau stays on the device from the first gate to the last measurement.
+// Requests on different streams overlap on the GPU; a finished request
+// (completion event reached) returns its slot and memory, and the next
+// waiting request is admitted at once.  Every request draws its outcomes from
+// its own Philox stream (circuit_id, shot), so its result does not depend on
+// what else is in flight.
+//
+// Failures are detected on the host: a request larger than the whole budget
+// or with an invalid gate is rejected before anything is launched; a request
+// whose completion is not seen within its deadline (fault injection drops a
+// completion on purpose) fails with TAB_ETIMEOUT, and its slot is reclaimed
+// after its stream has drained.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "tab_internal.h"
+
+using namespace tab;
+
+namespace tab {
+int handle_outcomes_async(tab_t h, uint8_t* host, cudaStream_t* used_stream);
+int handle_set_meas_ctas(tab_t h, int ctas);
+size_t handle_device_bytes(int32_t n);
+}
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double now_s() {
+  return std::chrono::duration<double>(Clock::now().time_since_epoch()).count();
+}
+
+struct Req {
+  int64_t ticket = 0;
+  int32_t n = 0, shots = 1;
+  uint64_t cid = 0;
+  std::vector<tab_gate> gates;
+  int64_t n_meas = 0;
+  size_t bytes = 0;
+  tab_t h = nullptr;
+  void* dmem = nullptr;       // stream-ordered allocation holding the tableau
+  int stream_idx = -1;
+  cudaEvent_t done = nullptr;
+  uint8_t* pinned = nullptr;  // outcomes, all shots
+  std::vector<uint8_t> out;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  int state = TAB_REQ_PENDING;
+  int status = TAB_OK;
+  char msg[256] = {0};
+  bool drop_completion = false;
+};
+
+}  // namespace
+
+struct tab_server_s {
+  tab_server_config cfg{};
+  int dev = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Req*> pending;
+  std::vector<Req*> running;
+  std::unordered_map<int64_t, Req*> reqs;
+  std::vector<cudaStream_t> streams;
+  std::vector<int> stream_load;
+  size_t mem_used = 0;
+  int64_t next_ticket = 1;
+  bool stop = false;
+  std::thread worker;
+  tab_server_stats st{};
+};
+
+namespace {
+
+void finish(tab_server_s* S, Req* r, int status, const char* msg) {
+  r->status = status;
+  if (msg) snprintf(r->msg, sizeof r->msg, "%s", msg);
+  r->t_done = now_s();
+  r->state = status == TAB_OK ? TAB_REQ_DONE : TAB_REQ_FAILED;
+  if (status == TAB_OK) {
+    S->st.completed++;
+  } else {
+    S->st.failed++;
+  }
+}
+
+void release(tab_server_s* S, Req* r) {
+  if (r->h) {
+    tab_destroy(r->h);  // waits for the request's stream work first
+    r->h = nullptr;
+  }
+  if (r->dmem) {  // stream-ordered free: no device-wide synchronization
+    cudaFreeAsync(r->dmem, S->streams[(size_t)r->stream_idx]);
+    r->dmem = nullptr;
+  }
+  if (r->done) {
+    cudaEventDestroy(r->done);
+    r->done = nullptr;
+  }
+  if (r->stream_idx >= 0) S->stream_load[(size_t)r->stream_idx]--;
+  S->mem_used -= r->bytes;
+  r->bytes = 0;
+}
+
+// Admit one request: compile, allocate, enqueue the whole program.  Called
+// with the lock held; CUDA calls are asynchronous except allocation.
+int admit(tab_server_s* S, Req* r) {
+  int si = 0;
+  for (size_t i = 1; i < S->streams.size(); ++i)
+    if (S->stream_load[i] < S->stream_load[(size_t)si]) si = (int)i;
+  r->stream_idx = si;
+  S->stream_load[(size_t)si]++;
+  cudaStream_t st = S->streams[(size_t)si];
+  const size_t hb = handle_device_bytes(r->n);
+  int rc = TAB_OK;
+  if (cudaMallocAsync(&r->dmem, hb, st) != cudaSuccess) {
+    cudaGetLastError();
+    r->dmem = nullptr;
+    set_error("device allocation of %zu bytes failed", hb);
+    rc = TAB_ENOMEM;
+  }
+  if (rc == TAB_OK) rc = tab_create_on(r->n, r->dmem, hb, st, &r->h);
+  if (rc == TAB_OK && S->cfg.meas_ctas > 0) rc = handle_set_meas_ctas(r->h, S->cfg.meas_ctas);
+  for (int32_t s = 0; rc == TAB_OK && s < r->shots; ++s) {
+    if (s > 0) rc = tab_reset(r->h);
+    if (rc == TAB_OK) rc = tab_set_rng(r->h, S->cfg.seed, r->cid, (uint32_t)s);
+    if (rc == TAB_OK) rc = tab_apply(r->h, r->gates.data(), (int64_t)r->gates.size());
+    if (rc == TAB_OK && r->n_meas > 0) {
+      cudaStream_t used = nullptr;
+      rc = handle_outcomes_async(r->h, r->pinned + (size_t)s * r->n_meas, &used);
+    }
+  }
+  if (rc == TAB_OK) {
+    if (cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(r->done, st) != cudaSuccess) {
+      set_error("event record failed");
+      rc = TAB_ECUDA;
+    }
+  }
+  r->t_admit = now_s();
+  r->state = TAB_REQ_RUNNING;
+  return rc;
+}
+
+void worker_main(tab_server_s* S) {
+  cudaSetDevice(S->dev);
+  std::unique_lock<std::mutex> lk(S->mu);
+  while (true) {
+    if (S->stop && S->pending.empty() && S->running.empty()) break;
+    bool progressed = false;
+    // ---- completions
+    for (size_t i = 0; i < S->running.size();) {
+      Req* r = S->running[i];
+      bool fin = false;
+      if (!r->drop_completion) {
+        const cudaError_t q = cudaEventQuery(r->done);
+        if (q == cudaSuccess) {
+          const int rc = tab_sync(r->h);  // latched device errors of this request
+          r->out.assign(r->pinned, r->pinned + (size_t)r->n_meas * r->shots);
+          finish(S, r, rc, rc == TAB_OK ? nullptr : tab_last_error());
+          fin = true;
+        } else if (q != cudaErrorNotReady) {
+          finish(S, r, TAB_ECUDA, cudaGetErrorString(q));
+          fin = true;
+        }
+      }
+      if (!fin && S->cfg.request_timeout_s > 0 &&
+          now_s() - r->t_admit > S->cfg.request_timeout_s) {
+        finish(S, r, TAB_ETIMEOUT, "request completion not observed before its deadline");
+        fin = true;
+      }
+      if (fin) {
+        release(S, r);
+        S->running[i] = S->running.back();
+        S->running.pop_back();
+        progressed = true;
+        S->cv_done.notify_all();
+      } else {
+        ++i;
+      }
+    }
+    // ---- admissions (FIFO, memory- and slot-limited)
+    while (!S->pending.empty() && (int)S->running.size() < S->cfg.max_inflight) {
+      Req* r = S->pending.front();
+      if (r->bytes > S->cfg.mem_budget_bytes) {  // can never fit: reject
+        S->pending.pop_front();
+        S->st.rejected++;
+        finish(S, r, TAB_ENOMEM, "request needs more device memory than the server budget");
+        S->cv_done.notify_all();
+        continue;
+      }
+      if (S->mem_used + r->bytes > S->cfg.mem_budget_bytes) break;
+      S->pending.pop_front();
+      S->mem_used += r->bytes;
+      S->st.peak_mem = std::max<uint64_t>(S->st.peak_mem, S->mem_used);
+      const int rc = admit(S, r);
+      if (rc != TAB_OK) {
+        finish(S, r, rc, tab_last_error());
+        release(S, r);
+        S->cv_done.notify_all();
+      } else {
+        S->running.push_back(r);
+        S->st.peak_inflight = std::max<int64_t>(S->st.peak_inflight, (int64_t)S->running.size());
+      }
+      progressed = true;
+    }
+    if (!progressed) {
+      if (S->running.empty() && S->pending.empty() && !S->stop) {
+        S->cv_work.wait(lk);
+      } else {
+        lk.unlock();
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+        lk.lock();
+      }
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int tab_server_create(const tab_server_config* cfg, tab_server_t* out) {
+  if (!cfg || !out) {
+    set_error("null argument");
+    return TAB_EINVAL;
+  }
+  *out = nullptr;
+  if (cfg->max_inflight < 1 || cfg->n_streams < 1 || cfg->mem_budget_bytes == 0) {
+    set_error("bad server configuration");
+    return TAB_EINVAL;
+  }
+  tab_server_s* S = new (std::nothrow) tab_server_s();
+  if (!S) {
+    set_error("host allocation failed");
+    return TAB_ENOMEM;
+  }
+  S->cfg = *cfg;
+  if (cudaGetDevice(&S->dev) != cudaSuccess) {
+    delete S;
+    set_error("no CUDA device");
+    return TAB_ECUDA;
+  }
+  for (int i = 0; i < cfg->n_streams; ++i) {
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      for (cudaStream_t x : S->streams) cudaStreamDestroy(x);
+      delete S;
+      set_error("stream creation failed");
+      return TAB_ECUDA;
+    }
+    S->streams.push_back(st);
+    S->stream_load.push_back(0);
+  }
+  S->worker = std::thread(worker_main, S);
+  *out = S;
+  return TAB_OK;
+}
+
+int tab_server_submit(tab_server_t S, const tab_circuit* c, int64_t* ticket) {
+  if (!S || !c || !ticket) {
+    set_error("null argument");
+    return TAB_EINVAL;
+  }
+  if (c->n < 1 || c->n > TAB_MAX_QUBITS || c->shots < 1 || c->n_gates < 0 ||
+      (c->n_gates > 0 && !c->gates)) {
+    set_error("bad request");
+    return TAB_EINVAL;
+  }
+  // validate now: a corrupted request is refused before it reaches the device
+  int64_t nm = 0;
+  for (int64_t i = 0; i < c->n_gates; ++i) {
+    const uint64_t g = c->gates[i];
+    const uint32_t op = (uint32_t)(g >> 56);
+    const uint64_t q1 = (g >> 28) & 0xFFFFFFFull, q2 = g & 0xFFFFFFFull;
+    if (op > TAB_BARRIER) {
+      set_error("gate %lld: unknown op %u", (long long)i, op);
+      return TAB_EINVAL;
+    }
+    if (op == TAB_BARRIER) continue;
+    const bool two = op == TAB_CNOT || op == TAB_CZ || op == TAB_SWAP;
+    if (q1 >= (uint64_t)c->n || (two && q2 >= (uint64_t)c->n)) {
+      set_error("gate %lld: qubit index out of range", (long long)i);
+      return TAB_ERANGE;
+    }
+    if (two && q1 == q2) {
+      set_error("gate %lld: two-qubit op on one qubit", (long long)i);
+      return TAB_EINVAL;
+    }
+    nm += (op == TAB_MZ || op == TAB_MZR);
+  }
+  Req* r = new (std::nothrow) Req();
+  if (!r) {
+    set_error("host allocation failed");
+    return TAB_ENOMEM;
+  }
+  r->n = c->n;
+  r->shots = c->shots;
+  r->cid = c->circuit_id;
+  r->gates.assign(c->gates, c->gates + c->n_gates);
+  r->n_meas = nm;
+  r->bytes = handle_device_bytes(c->n) + (size_t)c->n_gates * 4 + 8192 +
+             (size_t)nm * c->shots;
+  const size_t ob = std::max<size_t>((size_t)nm * c->shots, 1);
+  if (cudaMallocHost((void**)&r->pinned, ob) != cudaSuccess) {
+    delete r;
+    set_error("pinned allocation failed");
+    return TAB_ENOMEM;
+  }
+  r->t_submit = now_s();
+  {
+    std::lock_guard<std::mutex> g(S->mu);
+    r->ticket = S->next_ticket++;
+    S->reqs[r->ticket] = r;
+    S->pending.push_back(r);
+    S->st.submitted++;
+  }
+  S->cv_work.notify_one();
+  *ticket = r->ticket;
+  return TAB_OK;
+}
+
+int tab_server_query(tab_server_t S, int64_t ticket, int* state) {
+  if (!S || !state) {
+    set_error("null argument");
+    return TAB_EINVAL;
+  }
+  std::lock_guard<std::mutex> g(S->mu);
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) {
+    set_error("unknown ticket %lld", (long long)ticket);
+    return TAB_EINVAL;
+  }
+  *state = it->second->state;
+  return TAB_OK;
+}
+
+int tab_server_wait(tab_server_t S, int64_t ticket, double timeout_s, uint8_t* out, int64_t cap,
+                    int64_t* count, double* latency_s) {
+  if (!S) {
+    set_error("null server");
+    return TAB_EINVAL;
+  }
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) {
+    set_error("unknown ticket %lld", (long long)ticket);
+    return TAB_EINVAL;
+  }
+  Req* r = it->second;
+  const auto pred = [&] { return r->state == TAB_REQ_DONE || r->state == TAB_REQ_FAILED; };
+  if (timeout_s < 0) {
+    S->cv_done.wait(lk, pred);
+  } else if (!S->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred)) {
+    set_error("request %lld not finished within %.3f s", (long long)ticket, timeout_s);
+    return TAB_ESTATE;
+  }
+  if (latency_s) *latency_s = r->t_done - r->t_submit;
+  if (count) *count = (int64_t)r->out.size();
+  const int status = r->status;
+  if (status == TAB_OK && out) memcpy(out, r->out.data(), (size_t)std::min<int64_t>(cap, (int64_t)r->out.size()));
+  if (status != TAB_OK) set_error("%s", r->msg);
+  S->reqs.erase(it);
+  cudaFreeHost(r->pinned);
+  delete r;
+  return status;
+}
+
+int tab_server_inject(tab_server_t S, int64_t ticket, int kind) {
+  if (!S) {
+    set_error("null server");
+    return TAB_EINVAL;
+  }
+  std::lock_guard<std::mutex> g(S->mu);
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) {
+    set_error("unknown ticket %lld", (long long)ticket);
+    return TAB_EINVAL;
+  }
+  if (kind != TAB_FAULT_DROP_COMPLETION) {
+    set_error("unknown fault kind %d", kind);
+    return TAB_EINVAL;
+  }
+  it->second->drop_completion = true;
+  return TAB_OK;
+}
+
+int tab_server_stats_get(tab_server_t S, tab_server_stats* out) {
+  if (!S || !out) {
+    set_error("null argument");
+    return TAB_EINVAL;
+  }
+  std::lock_guard<std::mutex> g(S->mu);
+  *out = S->st;
+  out->inflight = (int64_t)S->running.size();
+  out->queued = (int64_t)S->pending.size();
+  out->mem_used = S->mem_used;
+  return TAB_OK;
+}
+
+int tab_server_destroy(tab_server_t S) {
+  if (!S) return TAB_OK;
+  {
+    std::lock_guard<std::mutex> g(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  if (S->worker.joinable()) S->worker.join();
+  for (auto& kv : S->reqs) {
+    if (kv.second->pinned) cudaFreeHost(kv.second->pinned);
+    delete kv.second;
+  }
+  for (cudaStream_t st : S->streams) cudaStreamDestroy(st);
+  delete S;
+  return TAB_OK;
+}
+
+}  // extern "C"

@@ -617,3 +617,26 @@ int tab_sync(tab_t h) {
 }
 
 }  // extern "C"
+
+namespace tab {
+
+// Internal helpers for the request server (not part of the C ABI).
+int handle_outcomes_async(tab_t h, uint8_t* host, cudaStream_t* used_stream) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (h->log_len > 0)
+    CU(cudaMemcpyAsync(host, h->log, (size_t)h->log_len, cudaMemcpyDeviceToHost, h->stream));
+  if (used_stream) *used_stream = h->stream;
+  return TAB_OK;
+}
+
+int handle_set_meas_ctas(tab_t h, int ctas) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  h->meas_ctas = std::max(1, std::min(ctas, h->mw.max_ctas));
+  return TAB_OK;
+}
+
+size_t handle_device_bytes(int32_t n) { return tab_bytes_required(n); }
+
+}  // namespace tab

@@ -79,6 +79,30 @@ _sig("tab_batch_exec", ctypes.c_int, [_vp, _u64, _vp, _vp])
 _sig("tab_batch_launches", ctypes.c_int, [_vp, _P(_i64)])
 
 
+class TabServerConfig(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", _u64), ("max_inflight", _i32), ("n_streams", _i32),
+                ("meas_ctas", _i32), ("request_timeout_s", ctypes.c_double), ("seed", _u64)]
+
+
+class TabServerStats(ctypes.Structure):
+    _fields_ = [("submitted", _i64), ("completed", _i64), ("failed", _i64), ("rejected", _i64),
+                ("inflight", _i64), ("queued", _i64), ("peak_inflight", _i64),
+                ("mem_used", _u64), ("peak_mem", _u64)]
+
+
+_sig("tab_server_create", ctypes.c_int, [_P(TabServerConfig), _P(_vp)])
+_sig("tab_server_submit", ctypes.c_int, [_vp, _P(TabCircuit), _P(_i64)])
+_sig("tab_server_query", ctypes.c_int, [_vp, _i64, _P(ctypes.c_int)])
+_sig("tab_server_wait", ctypes.c_int, [_vp, _i64, ctypes.c_double, _vp, _i64, _P(_i64),
+                                       _P(ctypes.c_double)])
+_sig("tab_server_inject", ctypes.c_int, [_vp, _i64, ctypes.c_int])
+_sig("tab_server_stats_get", ctypes.c_int, [_vp, _P(TabServerStats)])
+_sig("tab_server_destroy", ctypes.c_int, [_vp])
+
+REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+FAULT_DROP_COMPLETION = 1
+
+
 class TabError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
@@ -299,3 +323,65 @@ class Batch:
             self._h = None
 
     __del__ = close
+
+
+class Server:
+    """Continuous-batching request server (tab_server_*): submit circuits,
+    wait for their outcomes and latencies."""
+
+    def __init__(self, mem_budget_bytes: int = 150 << 30, max_inflight: int = 16,
+                 n_streams: int = 8, meas_ctas: int = 0, request_timeout_s: float = 0.0,
+                 seed: int = 1):
+        cfg = TabServerConfig(mem_budget_bytes, max_inflight, n_streams, meas_ctas,
+                              request_timeout_s, seed)
+        h = _vp()
+        _check(_L.tab_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+        self._nmeas = {}
+
+    def submit(self, n: int, gates, shots: int = 1, circuit_id: int = 0) -> int:
+        g = _u64arr(gates)
+        c = TabCircuit(n, g.ctypes.data if g.size else None, g.size, shots, circuit_id)
+        t = _i64()
+        _check(_L.tab_server_submit(self._h, ctypes.byref(c), ctypes.byref(t)))
+        self._nmeas[t.value] = shots * n_meas_of(g)
+        return t.value
+
+    def query(self, ticket: int) -> int:
+        st = ctypes.c_int()
+        _check(_L.tab_server_query(self._h, ticket, ctypes.byref(st)))
+        return st.value
+
+    def wait(self, ticket: int, timeout_s: float = -1.0):
+        """Returns (status, outcomes uint8 array, latency seconds)."""
+        cap = self._nmeas.get(ticket, 0)
+        out = np.zeros(max(cap, 1), np.uint8)
+        cnt, lat = _i64(), ctypes.c_double()
+        rc = _L.tab_server_wait(self._h, ticket, timeout_s, out.ctypes.data, cap,
+                                ctypes.byref(cnt), ctypes.byref(lat))
+        if rc == TAB_ESTATE:
+            raise TabError(rc, last_error())
+        self._nmeas.pop(ticket, None)
+        return rc, out[:min(cnt.value, cap)], lat.value
+
+    def inject(self, ticket: int, kind: int = FAULT_DROP_COMPLETION):
+        _check(_L.tab_server_inject(self._h, ticket, kind))
+
+    def stats(self) -> dict:
+        st = TabServerStats()
+        _check(_L.tab_server_stats_get(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in TabServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _L.tab_server_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
