@@ -146,6 +146,39 @@ int tab_measure(tab_t h, const int32_t *qubits, int32_t k, uint64_t seed, uint8_
  * alive by the caller until the stream reaches this point). */
 int tab_measure_async(tab_t h, const int32_t *qubits, int32_t k, uint8_t *dev_out_bits);
 
+/* Measurement that allocates no device memory.  (The paper has no
+ * counterpart: this is a deployment variant of tab_measure_async.)
+ *
+ * tab_create, tab_measure and tab_measure_async all allocate device memory.
+ * Some callers cannot: a process whose device memory is owned by another
+ * allocator (a framework that reserved the whole heap up front, where
+ * cudaMalloc fails or fragments its pool), or a latency-critical loop that
+ * must not pay for, or synchronize on, an allocation after start-up.  With a
+ * tableau in caller-owned memory (tab_create_on), this call lets them measure
+ * with no allocation at all.
+ *
+ * Measures Z on the k host-listed qubits in order (MZR when reset != 0),
+ * exactly as tab_measure_async does (same outcomes and tableau, same
+ * outcome-stream counter, which advances by k), writing outcome i as one byte
+ * to dev_out_bits[i] (caller-owned device memory, >= k bytes).  The outcomes
+ * are not added to the handle's outcome log.  Asynchronous on the handle's
+ * stream; device errors surface at the next synchronizing call.
+ *
+ * Scratch: a file-scope device array of TAB_NOALLOC_SCRATCH_BYTES (1 MiB) per
+ * device, held by every process that loads the library until it exits.  A
+ * call uses at most k + (2G + 2)W + 2G + 128 of its 32-bit words (W = 2 * the handle's
+ * words per half-column, G = CTAs of the measurement launch, lowered as far
+ * as 1 to fit); TAB_ERANGE if it does not fit with G = 1.  Every call shares
+ * the array: calls whose GPU work may overlap (different streams) race, so
+ * serialise them on one stream.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with the handle's device
+ * current); make that first call before any stream capture.  TAB_EINVAL if
+ * the handle's device is not current, TAB_ERANGE for a bad qubit (nothing is
+ * launched). */
+#define TAB_NOALLOC_SCRATCH_BYTES (1u << 20)
+int tab_measure_noalloc(tab_t h, const int32_t *qubits, int32_t k, int32_t reset,
+                        uint8_t *dev_out_bits);
+
 /* Synchronize and copy the outcome log (every outcome since the last
  * tab_reset / tab_clear_outcomes, in program order, one byte each) into out
  * (capacity max).  *count receives the number of outcomes in the log. */

@@ -639,4 +639,28 @@ int handle_set_meas_ctas(tab_t h, int ctas) {
 
 size_t handle_device_bytes(int32_t n) { return tab_bytes_required(n); }
 
+int handle_view(tab_t h, HandleView* v) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  v->n = h->n;
+  v->Wh = h->Wh;
+  v->dev = h->dev;
+  v->X = h->X;
+  v->Z = h->Z;
+  v->R = h->R;
+  v->stream = h->stream;
+  v->seed = h->seed;
+  v->cid = h->cid;
+  v->k = h->k;
+  v->shot = h->shot;
+  v->err = h->mw.err;
+  v->meas_ctas = h->meas_ctas;
+  return TAB_OK;
+}
+
+void handle_advance_k(tab_t h, uint64_t dk) {
+  h->k += dk;
+  h->launches++;
+}
+
 }  // namespace tab

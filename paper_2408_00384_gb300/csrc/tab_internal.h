@@ -98,4 +98,17 @@ cudaError_t launch_unpack(const uint32_t* X, const uint32_t* Z, const uint32_t* 
 // thread-local error message
 void set_error(const char* fmt, ...);
 
+// Read-only view of a handle for entry points outside tab_api.cpp.
+struct HandleView {
+  int n, Wh, dev;
+  uint32_t *X, *Z, *R;
+  cudaStream_t stream;
+  uint64_t seed, cid, k;
+  uint32_t shot;
+  int* err;
+  int meas_ctas;
+};
+int handle_view(tab_t h, HandleView* v);     // TAB_OK, or the handle's error
+void handle_advance_k(tab_t h, uint64_t dk);  // count dk more measurement ops
+
 }  // namespace tab

@@ -21,6 +21,7 @@ TAB_ECUDA, TAB_EDEVICE, TAB_ETIMEOUT, TAB_ESTATE = -4, -5, -6, -7
 STATUS_NAMES = {0: "TAB_OK", -1: "TAB_EINVAL", -2: "TAB_ERANGE", -3: "TAB_ENOMEM",
                 -4: "TAB_ECUDA", -5: "TAB_EDEVICE", -6: "TAB_ETIMEOUT", -7: "TAB_ESTATE"}
 MAX_QUBITS = 16384
+NOALLOC_SCRATCH_BYTES = 1 << 20
 ENGINE_AUTO, ENGINE_SINGLE_CTA, ENGINE_GRID = 0, 1, 2
 BATCH_MAX_QUBITS = 640
 
@@ -68,6 +69,7 @@ _sig("tab_read_outcomes", ctypes.c_int, [_vp, _vp, _i64, _P(_i64)])
 _sig("tab_clear_outcomes", ctypes.c_int, [_vp])
 _sig("tab_kernel_launches", ctypes.c_int, [_vp, _P(_i64)])
 _sig("tab_set_engine", ctypes.c_int, [_vp, ctypes.c_int])
+_sig("tab_measure_noalloc", ctypes.c_int, [_vp, _vp, _i32, _i32, _vp])
 _sig("tab_export", ctypes.c_int, [_vp, _vp, _vp, _vp])
 _sig("tab_import", ctypes.c_int, [_vp, _vp, _vp, _vp, _u64])
 _sig("tab_sync", ctypes.c_int, [_vp])
@@ -222,6 +224,13 @@ class Tableau:
         q = np.ascontiguousarray(np.asarray(qubits, dtype=np.int32).reshape(-1))
         _check(_L.tab_measure_async(self._h, q.ctypes.data if q.size else None, q.size,
                                     dev_out_ptr))
+
+    def measure_noalloc(self, qubits: Sequence[int], dev_out_ptr: int, reset: bool = False):
+        """tab_measure_noalloc: like measure_async, but the call allocates no
+        device memory (its scratch is the library's fixed 1 MiB device array)."""
+        q = np.ascontiguousarray(np.asarray(qubits, dtype=np.int32).reshape(-1))
+        _check(_L.tab_measure_noalloc(self._h, q.ctypes.data if q.size else None, q.size,
+                                      1 if reset else 0, dev_out_ptr))
 
     def read_outcomes(self) -> np.ndarray:
         cnt = _i64()
