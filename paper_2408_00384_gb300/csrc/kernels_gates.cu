@@ -51,66 +51,181 @@ void launch_init(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh, cudaStrea
 // ------------------------------------------------- fused row-slab gates ----
 // Grid: one CTA per 32-row slab (row word w = blockIdx.x), W CTAs.  The slab
 // of every column (x and z words, 8 bytes per qubit) is staged in shared
-// memory, the segment's layers are applied in order with a CTA barrier
-// between layers, and the slab is written back.
+// memory, the segment's layers are applied in order with one CTA barrier per
+// layer, and the slab is written back.
+//
+// The gate stream (32-bit codes) is the same for every CTA and is read from
+// L2.  Thread 0 streams it into a shared-memory ring with TMA bulk copies
+// (cp.async.bulk, completion on one mbarrier per ring slot), kGateSlots
+// chunks ahead, so no thread waits on an L2 round trip per gate.  A slot is
+// refilled once every thread has passed the layer barrier after its last
+// code; layers are at most kMaxLayerOps codes (the host splits larger ones),
+// so the chunks of the previous and the current layer always fit in the ring.
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long gate_gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the phase with the given parity; false after ~1 s.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = gate_gtimer();
+  while (!mbar_try_wait(bar, parity))
+    if (gate_gtimer() - t0 > 1000000000ull) return false;
+  return true;
+}
+// One TMA bulk copy of `bytes` (multiple of 16, both addresses 16-B aligned)
+// from global to shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                             uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+constexpr int kGateChunk = 512;                      // codes per TMA copy (2 KB)
+constexpr int kGateSlots = 16;                       // ring slots
+constexpr int kGateRing = kGateChunk * kGateSlots;   // 8192 codes = 32 KB
+
 template <int T>
 __global__ void __launch_bounds__(T) k_gates_slab(uint32_t* __restrict__ X, uint32_t* __restrict__ Z,
                                                   uint32_t* __restrict__ R, int n, int W,
                                                   const uint32_t* __restrict__ ops,
                                                   const uint32_t* __restrict__ layer_off,
-                                                  int nlayers) {
-  extern __shared__ uint32_t sm[];
-  uint32_t* sx = sm;      // X-plane word of every column (this slab's 32 rows)
-  uint32_t* sz = sm + n;  // Z-plane word of every column
+                                                  int nlayers, int* __restrict__ err) {
+  extern __shared__ __align__(128) uint32_t sm[];
+  uint32_t* ring = sm;                // gate-code ring (kGateRing codes)
+  uint32_t* sx = sm + kGateRing;      // X-plane word of every column (this slab's 32 rows)
+  uint32_t* sz = sx + n;              // Z-plane word of every column
+  __shared__ __align__(8) uint64_t bars[kGateSlots];
   __shared__ uint32_t s_r;
-  const int w = blockIdx.x;
-  for (int a = threadIdx.x; a < n; a += T) {
+  __shared__ int s_abort;
+  const int w = blockIdx.x, tid = threadIdx.x;
+  const uint32_t ob = __ldg(layer_off), oe = __ldg(layer_off + nlayers);
+  const uint32_t base = ob & ~3u;     // 16-byte aligned start of the stream
+  const int nchunks = (int)((oe - base + kGateChunk - 1) / kGateChunk);
+  int issued = 0, waited = 0;         // thread 0's pipeline state
+  if (tid == 0) {
+    for (int i = 0; i < kGateSlots; ++i) mbar_init(&bars[i], 1);
+    mbar_fence_init();
+    s_r = 0u;
+    s_abort = 0;
+    for (; issued < nchunks && issued < kGateSlots; ++issued)
+      tma_bulk_g2s(ring + (size_t)issued * kGateChunk, ops + base + (size_t)issued * kGateChunk,
+                   kGateChunk * 4, &bars[issued]);
+  }
+  for (int a = tid; a < n; a += T) {
     sx[a] = X[(size_t)a * W + w];
     sz[a] = Z[(size_t)a * W + w];
   }
-  if (threadIdx.x == 0) s_r = 0u;
   __syncthreads();
 
   uint32_t racc = 0u;
-  uint32_t lb = __ldg(layer_off);
+  uint32_t prev_lb = ob;  // first code of the previous layer
+  uint32_t lb = ob;
   for (int L = 0; L < nlayers; ++L) {
     const uint32_t le = __ldg(layer_off + L + 1);
-    for (uint32_t g = lb + threadIdx.x; g < le; g += T)
-      apply_gate(__ldg(ops + g), sx, sz, 1, 0, racc);
-    lb = le;
+    if (tid == 0) {
+      // refill slots whose chunk ended before the previous layer began: every
+      // thread has passed the barrier after the layer that read it last
+      while (issued < nchunks &&
+             (int64_t)base + (int64_t)(issued - kGateSlots + 1) * kGateChunk <= (int64_t)prev_lb) {
+        const int slot = issued % kGateSlots;
+        fence_proxy_async_smem();
+        tma_bulk_g2s(ring + (size_t)slot * kGateChunk, ops + base + (size_t)issued * kGateChunk,
+                     kGateChunk * 4, &bars[slot]);
+        ++issued;
+      }
+      if (le > lb) {
+        const int c_last = (int)((le - 1 - base) / kGateChunk);
+        if (c_last >= issued) {
+          atomicCAS(err, 0, DERR_BOUNDS);
+          s_abort = 1;
+        } else {
+          for (; waited <= c_last; ++waited)
+            if (!mbar_wait_bounded(&bars[waited % kGateSlots], (uint32_t)(waited / kGateSlots) & 1u)) {
+              atomicCAS(err, 0, DERR_TIMEOUT);
+              s_abort = 1;
+              break;
+            }
+        }
+      }
+    }
     __syncthreads();
+    if (s_abort) break;
+    for (uint32_t g = lb + tid; g < le; g += T)
+      apply_gate(ring[(g - base) & (kGateRing - 1)], sx, sz, 1, 0, racc);
+    prev_lb = lb;
+    lb = le;
   }
+  // every copy issued must land before the CTA exits (normally all have been
+  // waited for already; after an abort some may still be in flight)
+  if (tid == 0)
+    for (; waited < issued; ++waited)
+      mbar_wait_bounded(&bars[waited % kGateSlots], (uint32_t)(waited / kGateSlots) & 1u);
+  __syncthreads();
+  if (s_abort) return;
 
-  for (int a = threadIdx.x; a < n; a += T) {
+  for (int a = tid; a < n; a += T) {
     X[(size_t)a * W + w] = sx[a];
     Z[(size_t)a * W + w] = sz[a];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) racc ^= __shfl_xor_sync(0xffffffffu, racc, o);
-  if ((threadIdx.x & 31) == 0 && racc) atomicXor(&s_r, racc);
+  if ((tid & 31) == 0 && racc) atomicXor(&s_r, racc);
   __syncthreads();
-  if (threadIdx.x == 0) R[w] ^= s_r;
+  if (tid == 0) R[w] ^= s_r;
 }
 
 constexpr int kGateThreads = 256;
 constexpr int kMaxSmemBytes = 227 * 1024;
 
-int gates_max_n() { return (kMaxSmemBytes - 1024) / 8; }
+int gates_max_n() { return (kMaxSmemBytes - 4096 - kGateRing * 4) / 8; }
 
 cudaError_t launch_gates_slab(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
                               const uint32_t* ops, const uint32_t* layer_off, int nlayers,
-                              cudaStream_t s) {
+                              int* err, cudaStream_t s) {
   if (nlayers <= 0) return cudaSuccess;
-  const size_t smem = (size_t)n * 2 * sizeof(uint32_t);
+  const size_t smem = (size_t)kGateRing * 4 + (size_t)n * 2 * sizeof(uint32_t);
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_gates_slab<kGateThreads>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kMaxSmemBytes - 1024);
+                                         kMaxSmemBytes - 4096);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_gates_slab<kGateThreads><<<W, kGateThreads, smem, s>>>(X, Z, R, n, W, ops, layer_off, nlayers);
+  k_gates_slab<kGateThreads><<<W, kGateThreads, smem, s>>>(X, Z, R, n, W, ops, layer_off, nlayers,
+                                                           err);
   return cudaGetLastError();
 }
 

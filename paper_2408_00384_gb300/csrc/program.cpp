@@ -112,7 +112,16 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
     P.layer_off.push_back(op_base);
     uint32_t run = op_base;
     for (int64_t L = 0; L < nl; ++L) {
-      for (int o = 0; o < kOps; ++o) run += cnt[(size_t)L * kOps + o];
+      uint32_t sz = 0;
+      for (int o = 0; o < kOps; ++o) sz += cnt[(size_t)L * kOps + o];
+      // a layer larger than kMaxLayerOps becomes consecutive sub-layers (its
+      // gates are pairwise disjoint, so any split keeps the result)
+      while (sz > (uint32_t)kMaxLayerOps) {
+        run += kMaxLayerOps;
+        sz -= kMaxLayerOps;
+        P.layer_off.push_back(run);
+      }
+      run += sz;
       P.layer_off.push_back(run);
     }
     s.layer_end = (uint32_t)P.layer_off.size() - 1;

@@ -206,7 +206,7 @@ int run_program(tab_t h, const HostProgram& hp, const DevProg& dp, uint64_t seed
   for (const Seg& s : hp.segs) {
     if (s.kind == 0) {
       CU(launch_gates_slab(h->X, h->Z, h->R, h->n, h->W, dp.ops, dp.layer + s.layer_begin,
-                           (int)(s.layer_end - s.layer_begin), h->stream));
+                           (int)(s.layer_end - s.layer_begin), h->mw.err, h->stream));
       h->launches++;
     } else {
       const int nm = (int)(s.op_end - s.op_begin);
@@ -221,7 +221,7 @@ int run_program(tab_t h, const HostProgram& hp, const DevProg& dp, uint64_t seed
 }
 
 int upload(const HostProgram& hp, DevProg* d, cudaStream_t s, bool async_alloc) {
-  const size_t ob = std::max<size_t>(hp.ops.size(), 1) * 4;
+  const size_t ob = (hp.ops.size() + kOpsPad) * 4;  // TMA chunks may read past the end
   const size_t lb = std::max<size_t>(hp.layer_off.size(), 1) * 4;
   const size_t sb = std::max<size_t>(hp.segs.size(), 1) * sizeof(Seg);
   if (async_alloc) {
@@ -235,6 +235,7 @@ int upload(const HostProgram& hp, DevProg* d, cudaStream_t s, bool async_alloc) 
   }
   if (!hp.ops.empty())
     CU(cudaMemcpyAsync(d->ops, hp.ops.data(), hp.ops.size() * 4, cudaMemcpyHostToDevice, s));
+  CU(cudaMemsetAsync(d->ops + hp.ops.size(), 0, (size_t)kOpsPad * 4, s));
   if (!hp.layer_off.empty())
     CU(cudaMemcpyAsync(d->layer, hp.layer_off.data(), hp.layer_off.size() * 4,
                        cudaMemcpyHostToDevice, s));

@@ -80,9 +80,13 @@ struct MeasWork {
 // ---- launches (kernels_*.cu) ---------------------------------------------------------
 void launch_init(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh, cudaStream_t s);
 int gates_max_n();
+// Layers handed to launch_gates_slab hold at most kMaxLayerOps gates, and the
+// device op buffer extends at least kOpsPad codes past its last code.
+constexpr int kMaxLayerOps = 2048;
+constexpr int kOpsPad = 1024;
 cudaError_t launch_gates_slab(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
                               const uint32_t* ops, const uint32_t* layer_off,
-                              int nlayers, cudaStream_t s);
+                              int nlayers, int* err, cudaStream_t s);
 cudaError_t launch_measure(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh,
                            const uint32_t* mops, int nm, uint64_t k0, uint64_t seed,
                            uint64_t cid, uint32_t shot, uint8_t* out, const MeasWork& mw,
