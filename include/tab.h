@@ -187,12 +187,16 @@ int tab_clear_outcomes(tab_t h);
 
 /* Execution engine for tab_apply / tab_run / tab_measure on this handle.
  * TAB_ENGINE_SINGLE_CTA keeps the whole tableau in one CTA's shared memory
- * (n <= TAB_BATCH_MAX_QUBITS; one launch per call); TAB_ENGINE_GRID spreads
- * it over the GPU (a fused row-slab gate kernel per gate run, a cooperative
- * measurement kernel per measurement run); TAB_ENGINE_AUTO (default) picks by
- * size.  Results are bit-identical across engines.  TAB_ERANGE if
- * SINGLE_CTA is asked for n > TAB_BATCH_MAX_QUBITS. */
-enum tab_engine { TAB_ENGINE_AUTO = 0, TAB_ENGINE_SINGLE_CTA = 1, TAB_ENGINE_GRID = 2 };
+ * (n <= TAB_BATCH_MAX_QUBITS; one launch per call).  TAB_ENGINE_GRID spreads
+ * it over the GPU: a fused row-slab gate kernel per gate run and a
+ * cooperative grid-wide kernel per measurement run.  TAB_ENGINE_CLUSTER uses
+ * the same gate kernel, and runs measurements on a tableau held in the shared
+ * memory of one thread-block cluster (n up to about 2,500; TAB_ERANGE beyond).
+ * TAB_ENGINE_AUTO (default) picks by size.  Results are bit-identical across
+ * engines.  TAB_ERANGE if SINGLE_CTA is asked for n > TAB_BATCH_MAX_QUBITS. */
+enum tab_engine {
+  TAB_ENGINE_AUTO = 0, TAB_ENGINE_SINGLE_CTA = 1, TAB_ENGINE_GRID = 2, TAB_ENGINE_CLUSTER = 3
+};
 int tab_set_engine(tab_t h, int engine);
 
 /* Number of CUDA kernels this handle has launched since creation. */

@@ -169,14 +169,27 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err)
     const int wp = pw, wd = Pd >> 5;
     const uint32_t bpm = 1u << (P & 31);
     const uint32_t rp = (s.R[wp] & bpm) ? 1u : 0u;
-    for (int j = tid; j < n; j += T) {
-      const uint32_t xw = s.X[(size_t)j * Wp + wp], zw = s.Z[(size_t)j * Wp + wp];
-      const uint32_t xp = (xw & bpm) ? 1u : 0u, zp = (zw & bpm) ? 1u : 0u;
+    const int lane = tid & 31;
+    for (int j0 = tid - lane; j0 < n; j0 += T) {  // warp-uniform trip count
+      const int j = j0 + lane;
+      uint32_t xp = 0u, zp = 0u;
+      if (j < n) {
+        const uint32_t xw = s.X[(size_t)j * Wp + wp], zw = s.Z[(size_t)j * Wp + wp];
+        xp = (xw & bpm) ? 1u : 0u;
+        zp = (zw & bpm) ? 1u : 0u;
+      }
+      // warp-aggregated append to the support list (one shared atomic per warp)
+      const uint32_t in = __ballot_sync(0xffffffffu, (xp | zp) != 0u);
+      const uint32_t yy = __ballot_sync(0xffffffffu, (xp & zp) != 0u);
+      int base = 0;
+      if (lane == 0 && in) {
+        base = atomicAdd(&s_nsupp, __popc(in));
+        if (yy) atomicAdd(&s_kc, __popc(yy));
+      }
+      base = __shfl_sync(0xffffffffu, base, 0);
       if (xp | zp) {
-        const int pos = atomicAdd(&s_nsupp, 1);
-        s.supp[pos] = (uint32_t)j | (xp << 30) | (zp << 31);
-        if (xp & zp) atomicAdd(&s_kc, 1);
-      } else {  // row p is I here: row p-n := row p clears this bit
+        s.supp[base + __popc(in & ((1u << lane) - 1u))] = (uint32_t)j | (xp << 30) | (zp << 31);
+      } else if (j < n) {  // row p is I here: row p-n := row p clears this bit
         s.X[(size_t)j * Wp + wd] &= ~bpm;
         s.Z[(size_t)j * Wp + wd] &= ~bpm;
       }

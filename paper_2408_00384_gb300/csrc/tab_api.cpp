@@ -210,8 +210,14 @@ int run_program(tab_t h, const HostProgram& hp, const DevProg& dp, uint64_t seed
       h->launches++;
     } else {
       const int nm = (int)(s.op_end - s.op_begin);
-      CU(launch_measure(h->X, h->Z, h->R, h->n, h->Wh, dp.ops + s.op_begin, nm, h->k, seed,
-                        h->cid, h->shot, h->log + h->log_len, h->mw, h->meas_ctas, h->stream));
+      const int C = h->engine == TAB_ENGINE_GRID ? 0 : cluster_size_for(h->n, h->Wh);
+      if (C > 0)
+        CU(launch_measure_cluster(h->X, h->Z, h->R, h->n, h->Wh, dp.ops + s.op_begin, nm, h->k,
+                                  seed, h->cid, h->shot, h->log + h->log_len, h->mw.err, C,
+                                  h->stream));
+      else
+        CU(launch_measure(h->X, h->Z, h->R, h->n, h->Wh, dp.ops + s.op_begin, nm, h->k, seed,
+                          h->cid, h->shot, h->log + h->log_len, h->mw, h->meas_ctas, h->stream));
       h->launches++;
       h->k += (uint64_t)nm;
       h->log_len += nm;
@@ -551,12 +557,16 @@ int tab_clear_outcomes(tab_t h) {
 int tab_set_engine(tab_t h, int engine) {
   int rc = check_handle(h);
   if (rc) return rc;
-  if (engine < TAB_ENGINE_AUTO || engine > TAB_ENGINE_GRID) {
+  if (engine < TAB_ENGINE_AUTO || engine > TAB_ENGINE_CLUSTER) {
     set_error("unknown engine %d", engine);
     return TAB_EINVAL;
   }
   if (engine == TAB_ENGINE_SINGLE_CTA && h->n > TAB_BATCH_MAX_QUBITS) {
     set_error("single-CTA engine needs n <= %d (n=%d)", TAB_BATCH_MAX_QUBITS, h->n);
+    return TAB_ERANGE;
+  }
+  if (engine == TAB_ENGINE_CLUSTER && cluster_size_for(h->n, h->Wh) == 0) {
+    set_error("the tableau (n=%d) does not fit one cluster's shared memory", h->n);
     return TAB_ERANGE;
   }
   h->engine = engine;

@@ -92,6 +92,13 @@ cudaError_t launch_measure(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh,
                            uint64_t cid, uint32_t shot, uint8_t* out, const MeasWork& mw,
                            int ctas, cudaStream_t s);
 int measure_ctas_for(int n, int sm_count, int max_ctas);
+// Cluster measurement engine (kernels_cluster.cu): cluster size for a tableau
+// of n qubits, or 0 when it does not fit in one cluster's shared memory.
+int cluster_size_for(int n, int Wh);
+cudaError_t launch_measure_cluster(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh,
+                                   const uint32_t* mops, int nm, uint64_t k0, uint64_t seed,
+                                   uint64_t cid, uint32_t shot, uint8_t* out, int* err, int C,
+                                   cudaStream_t s);
 size_t measure_work_words(int n, int max_ctas);
 cudaError_t launch_pack(uint32_t* X, uint32_t* Z, uint32_t* R, const uint8_t* xs,
                         const uint8_t* zs, const uint8_t* rs, int n, int Wh, cudaStream_t s);

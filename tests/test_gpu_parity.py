@@ -18,7 +18,12 @@ from paper_2408_00384_gb300 import tab  # noqa: E402  (fails loudly when libtab.
 def gpu_run(n, gates, seed=1, cid=0, shot=0, engine=None):
     with tab.Tableau(n) as t:
         if engine is not None:
-            t.set_engine(engine)
+            try:
+                t.set_engine(engine)
+            except tab.TabError as e:
+                if e.code == tab.TAB_ERANGE:
+                    pytest.skip(f"engine {engine} does not hold n={n}")
+                raise
         t.set_rng(seed, cid, shot)
         t.apply(gates)
         out = t.read_outcomes()
@@ -35,7 +40,7 @@ def assert_same(n, gates, seed=1, cid=0, shot=0, engine=None):
         assert bad.size == 0, (n, engine, name, bad[:10].tolist())
 
 
-ENGINES = [tab.ENGINE_SINGLE_CTA, tab.ENGINE_GRID]
+ENGINES = [tab.ENGINE_SINGLE_CTA, tab.ENGINE_GRID, tab.ENGINE_CLUSTER]
 
 
 @pytest.mark.parametrize("engine", ENGINES)
@@ -58,16 +63,18 @@ def test_layer_circuits_final_measure(engine, n, depth):
     assert_same(n, c.gates, seed=11, engine=engine)
 
 
-@pytest.mark.parametrize("n", [700, 1000, 2049])
-def test_grid_engine_larger(n):
+@pytest.mark.parametrize("engine", [tab.ENGINE_GRID, tab.ENGINE_CLUSTER])
+@pytest.mark.parametrize("n", [700, 1000, 2049, 2400])
+def test_grid_and_cluster_larger(engine, n):
     c = C.random_layer_circuit(n, 8, seed=n, meas_every=4, meas_frac=0.02)
-    assert_same(n, c.gates, seed=5, engine=tab.ENGINE_GRID)
+    assert_same(n, c.gates, seed=5, engine=engine)
 
 
-def test_config2_full():
+@pytest.mark.parametrize("engine", [tab.ENGINE_AUTO, tab.ENGINE_GRID])
+def test_config2_full(engine):
     """n=1000, 1000 random layers, final MZ on all qubits: full compare."""
     c = C.config2()
-    assert_same(c.n, c.gates, seed=C.PHILOX_SEED)
+    assert_same(c.n, c.gates, seed=C.PHILOX_SEED, engine=engine)
 
 
 def test_config3_prefix_full_size():
