@@ -42,7 +42,9 @@ def parse():
     p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "batched"])
+    p.add_argument("--workload", default="cfg2",
+                   choices=["cfg1", "cfg2", "cfg3", "batched", "served"])
+    p.add_argument("--requests", type=int, default=48, help="served: number of requests")
     p.add_argument("--engine", default="auto", choices=["auto", "grid", "single"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -423,6 +425,84 @@ def run_batched(args, ws, rank, local):
     return line
 
 
+def run_served(args, ws, rank, local):
+    """Served family: circuits with n log-uniform in [50, 5000], depth 2n, MZR on
+    5 % every 20 layers, final MZ on all qubits.  Pass 1 submits every request
+    at once (saturated) to calibrate the service rate mu; pass 2 submits them
+    as a Poisson stream at lambda = 0.7 mu and records arrival-to-outcome
+    latency.  Tableaus stay resident for their whole circuit; admission is by
+    device memory (150 GB cap) and slots."""
+    import torch
+    from paper_2408_00384_gb300 import tab
+    from workloads import circuits as C
+
+    torch.cuda.set_device(local)
+    reqs = [C.config5_request(c + 100000 * rank) for c in range(args.requests)]
+    gates_total = sum(r.n_gates for r in reqs)
+    meas_total = sum(r.n_meas for r in reqs)
+    cfg = dict(mem_budget_bytes=150 << 30, max_inflight=16, n_streams=8, meas_ctas=32, seed=C.PHILOX_SEED)
+
+    def serve(arrivals):
+        lat = []
+        launches = 0
+        with tab.Server(**cfg) as srv:
+            t0 = time.perf_counter()
+            tickets = []
+            for i, r in enumerate(reqs):
+                if arrivals is not None:
+                    delay = t0 + arrivals[i] - time.perf_counter()
+                    if delay > 0:
+                        time.sleep(delay)
+                tickets.append((srv.submit(r.n, r.gates, 1, r.circuit_id), time.perf_counter()))
+            for (tk, ts), r in zip(tickets, reqs):
+                rc, out, l = srv.wait(tk)
+                if rc != tab.TAB_OK or out.size != r.n_meas:
+                    raise RuntimeError(f"request failed: {rc} {tab.last_error()}")
+                lat.append(l)
+            wall = time.perf_counter() - t0
+            st = srv.stats()
+        return wall, lat, st
+
+    # warm-up: a few small requests
+    with tab.Server(**cfg) as srv:
+        for r in reqs[:2]:
+            srv.wait(srv.submit(r.n, r.gates, 1, r.circuit_id))
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    wall_sat, lat_sat, st_sat = serve(None)
+    mu = len(reqs) / wall_sat
+    lam = 0.7 * mu
+    arrivals = C.poisson_arrivals(lam, len(reqs))
+    wall, lat, st = serve(arrivals)
+    barrier(ws)
+    clk = clocks.stop()
+    wall = allreduce_max(wall, ws)
+    ms = 1000.0 * wall
+    line = {
+        "metric": METRIC, "value": ws * gates_total / wall, "unit": "gates/s", "n_gpus": ws,
+        "steps": 1, "warmup": 1, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "meas_per_s": ws * meas_total / wall,
+        "latency_ms": {"p50": 1000.0 * float(np.percentile(lat, 50)),
+                       "p99": 1000.0 * float(np.percentile(lat, 99))},
+        "throughput_req_per_s": len(reqs) / wall,
+        "saturated": {"req_per_s": mu, "gates_per_s": gates_total / wall_sat,
+                      "p50_ms": 1000.0 * float(np.percentile(lat_sat, 50)),
+                      "p99_ms": 1000.0 * float(np.percentile(lat_sat, 99)),
+                      "peak_inflight": st_sat["peak_inflight"]},
+        "config": {"workload": f"served: {len(reqs)} requests, n log-uniform [50, 5000], depth 2n, "
+                               "MZR on 5% every 20 layers, final MZ on all; Poisson arrivals at "
+                               f"0.7 x saturated rate ({lam:.2f} req/s)",
+                   "gates": gates_total, "measurements": meas_total,
+                   "arrival_rate_per_s": lam, "mem_budget_bytes": 150 << 30,
+                   "max_inflight": cfg["max_inflight"], "peak_inflight": st["peak_inflight"],
+                   "peak_mem_bytes": st["peak_mem"]},
+        "clocks": clk, "roofline": None, "e2e": None,
+    }
+    return line
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args)
@@ -431,6 +511,8 @@ def main():
         return
     if args.workload == "batched":
         line = run_batched(args, ws, rank, local)
+    elif args.workload == "served":
+        line = run_served(args, ws, rank, local)
     else:
         line = run_plain(args, ws, rank, local)
     if rank == 0:

@@ -28,7 +28,7 @@
 namespace tab {
 
 constexpr int kClThreads = 512;
-constexpr int kClMaxSmem = 227 * 1024;
+constexpr int kClMaxSmem = 226 * 1024;  // dynamic; static shared memory comes on top
 
 struct ClArgs {
   uint32_t *X, *Z, *R;  // handle layout: W = 2*Wh words per column
@@ -394,8 +394,8 @@ int cluster_size_for(int n, int Wh) {
             nclusters > 0)
           max_c = c;
       }
-      cudaGetLastError();
     }
+    cudaGetLastError();  // a failed probe must not leave an error behind
   }
   if (max_c == 0 || 2 * Wh > kClThreads) return 0;
   // the largest cluster spreads the tableau thinnest; if it does not fit, no
