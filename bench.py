@@ -333,7 +333,10 @@ def run_plain(args, ws, rank, local):
         # algorithmic bytes per random measurement: rows x supp columns read+written
         # ~ 0.75 n^2 B (n columns in supp(p) ~ 3/4, 2 planes, 2n/8 B, read + write)
         alg = 0.75 * n * n * c.n_meas
-        roof = {"kernel": "k_measure", "bound": "hbm", "unit": "GB/s"}
+        kname = {"auto": "k_measure_cluster" if 256 < n <= 2400 else
+                 ("k_sct_program" if n <= 256 else "k_measure_resident/k_measure"),
+                 "grid": "k_measure_resident", "single": "k_sct_program"}[args.engine]
+        roof = {"kernel": kname, "bound": "hbm", "unit": "GB/s"}
         roof["achieved"] = alg / (kind_ms[dom] / 1000.0) / 1e9
         roof["peak"] = pk.get("hbm_gbs", FALLBACK_HBM_GBS)
     else:

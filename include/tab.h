@@ -187,15 +187,20 @@ int tab_clear_outcomes(tab_t h);
 
 /* Execution engine for tab_apply / tab_run / tab_measure on this handle.
  * TAB_ENGINE_SINGLE_CTA keeps the whole tableau in one CTA's shared memory
- * (n <= TAB_BATCH_MAX_QUBITS; one launch per call).  TAB_ENGINE_GRID spreads
- * it over the GPU: a fused row-slab gate kernel per gate run and a
- * cooperative grid-wide kernel per measurement run.  TAB_ENGINE_CLUSTER uses
- * the same gate kernel, and runs measurements on a tableau held in the shared
- * memory of one thread-block cluster (n up to about 2,500; TAB_ERANGE beyond).
+ * (n <= TAB_BATCH_MAX_QUBITS; one launch per call).  The other engines apply
+ * gate runs with a fused row-slab kernel spread over the GPU and differ in
+ * how a run of measurements executes:
+ *   TAB_ENGINE_CLUSTER  tableau in the shared memory of one thread-block
+ *                       cluster (n up to about 2,500);
+ *   TAB_ENGINE_GRID     tableau in the shared memory of a cooperative grid
+ *                       (n up to about 8,000), else streamed from HBM/L2;
+ *   TAB_ENGINE_STREAM   always streamed from HBM/L2 by a cooperative grid.
  * TAB_ENGINE_AUTO (default) picks by size.  Results are bit-identical across
- * engines.  TAB_ERANGE if SINGLE_CTA is asked for n > TAB_BATCH_MAX_QUBITS. */
+ * engines.  TAB_ERANGE if SINGLE_CTA is asked for n > TAB_BATCH_MAX_QUBITS or
+ * CLUSTER for a tableau larger than one cluster holds. */
 enum tab_engine {
-  TAB_ENGINE_AUTO = 0, TAB_ENGINE_SINGLE_CTA = 1, TAB_ENGINE_GRID = 2, TAB_ENGINE_CLUSTER = 3
+  TAB_ENGINE_AUTO = 0, TAB_ENGINE_SINGLE_CTA = 1, TAB_ENGINE_GRID = 2, TAB_ENGINE_CLUSTER = 3,
+  TAB_ENGINE_STREAM = 4
 };
 int tab_set_engine(tab_t h, int engine);
 

@@ -18,6 +18,7 @@
 // contributions XOR into a per-thread register and are reduced once at the end.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "gate_rules.cuh"
 #include "tab_internal.h"
@@ -206,27 +207,50 @@ __global__ void __launch_bounds__(T) k_gates_slab(uint32_t* __restrict__ X, uint
   if (tid == 0) R[w] ^= s_r;
 }
 
-constexpr int kGateThreads = 256;
 constexpr int kMaxSmemBytes = 227 * 1024;
 
 int gates_max_n() { return (kMaxSmemBytes - 4096 - kGateRing * 4) / 8; }
+
+// Threads per CTA of the slab kernel: more threads shorten each thread's chain
+// of gates per layer (the kernel is latency-bound per layer).  TAB_GATE_THREADS
+// (256, 512 or 1024) overrides the default for tuning sweeps.
+static int gate_threads() {
+  static int t = 0;
+  if (t == 0) {
+    t = 512;
+    if (const char* e = getenv("TAB_GATE_THREADS")) {
+      const int v = atoi(e);
+      if (v == 256 || v == 512 || v == 1024) t = v;
+    }
+  }
+  return t;
+}
+
+template <int T>
+static cudaError_t launch_gates_t(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
+                                  const uint32_t* ops, const uint32_t* layer_off, int nlayers,
+                                  int* err, cudaStream_t s) {
+  const size_t smem = (size_t)kGateRing * 4 + (size_t)n * 2 * sizeof(uint32_t);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_gates_slab<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kMaxSmemBytes - 4096);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_gates_slab<T><<<W, T, smem, s>>>(X, Z, R, n, W, ops, layer_off, nlayers, err);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gates_slab(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
                               const uint32_t* ops, const uint32_t* layer_off, int nlayers,
                               int* err, cudaStream_t s) {
   if (nlayers <= 0) return cudaSuccess;
-  const size_t smem = (size_t)kGateRing * 4 + (size_t)n * 2 * sizeof(uint32_t);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_gates_slab<kGateThreads>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kMaxSmemBytes - 4096);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
+  switch (gate_threads()) {
+    case 256: return launch_gates_t<256>(X, Z, R, n, W, ops, layer_off, nlayers, err, s);
+    case 1024: return launch_gates_t<1024>(X, Z, R, n, W, ops, layer_off, nlayers, err, s);
+    default: return launch_gates_t<512>(X, Z, R, n, W, ops, layer_off, nlayers, err, s);
   }
-  k_gates_slab<kGateThreads><<<W, kGateThreads, smem, s>>>(X, Z, R, n, W, ops, layer_off, nlayers,
-                                                           err);
-  return cudaGetLastError();
 }
 
 // --------------------------------------------------------- pack / unpack ---

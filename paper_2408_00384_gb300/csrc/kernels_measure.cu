@@ -30,13 +30,13 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "grid_sync.cuh"
 #include "philox.cuh"
 #include "tab_internal.h"
 
 namespace tab {
 
 constexpr int kMeasThreads = 512;
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per barrier wait
 
 struct MArgs {
   uint32_t* X;
@@ -54,50 +54,6 @@ struct MArgs {
   GridBar* bar;
   int* err;
 };
-
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
-  unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Grid-wide barrier (all CTAs are co-resident: cooperative launch).  Bounded
-// wait: after kWaitLimitNs, or when another CTA has latched an error, the
-// barrier latches DERR_TIMEOUT and returns false so every CTA exits.
-__device__ bool grid_sync(GridBar* bar, int* err) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned int gen = ld_acquire(&bar->gen);
-    __threadfence();
-    const unsigned int arrived = atomicAdd(&bar->count, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
-      const unsigned long long t0 = gtimer();
-      while (ld_acquire(&bar->gen) == gen) {
-        if (*(volatile int*)err != 0 || gtimer() - t0 > kWaitLimitNs) {
-          atomicCAS(err, 0, DERR_TIMEOUT);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    __threadfence();
-    s_ok = ok && (*(volatile int*)err == 0);
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
 
 // mod-4 bit-sliced add: (h, l) += (bh, bl)
 __device__ __forceinline__ void add4(uint32_t& l, uint32_t& h, uint32_t bl, uint32_t bh) {

@@ -38,6 +38,9 @@ struct tab_s {
   uint32_t *X = nullptr, *Z = nullptr, *R = nullptr;
   MeasWork mw{};
   int meas_ctas = 1;
+  uint32_t* rw = nullptr;     // grid-resident measurement workspace
+  GridBar* rbar = nullptr;
+  int res_ctas = 0;           // CTAs of the grid-resident engine (0: does not fit)
   uint64_t seed = 1, cid = 0;
   uint32_t shot = 0;
   uint64_t k = 0;             // next measurement index
@@ -73,7 +76,7 @@ int sm_count_of(int dev) {
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct Sizes {
-  size_t planes, sign, work, total;
+  size_t planes, sign, work, rwork, total;
 };
 
 Sizes sizes_for(int n, int max_ctas) {
@@ -82,7 +85,8 @@ Sizes sizes_for(int n, int max_ctas) {
   s.planes = align256((size_t)n * W * 4);
   s.sign = align256((size_t)W * 4);
   s.work = align256(measure_work_words(n, max_ctas) * 4);
-  s.total = 2 * s.planes + s.sign + s.work;
+  s.rwork = align256(resident_work_words(n, max_ctas) * 4 + sizeof(GridBar) + 64);
+  s.total = 2 * s.planes + s.sign + s.work + s.rwork;
   return s;
 }
 
@@ -146,6 +150,10 @@ int setup(tab_t h, int32_t n, void* mem, bool own) {
   w += 16;
   h->mw.err = reinterpret_cast<int*>(w);
   h->meas_ctas = measure_ctas_for(n, sms, sms);
+  char* rb = b + 2 * s.planes + s.sign + s.work;
+  h->rbar = reinterpret_cast<GridBar*>(rb);
+  h->rw = reinterpret_cast<uint32_t*>(rb + 64);
+  h->res_ctas = resident_ctas_for(n, h->Wh, sms);
   CU(cudaMemsetAsync(h->mw.err, 0, sizeof(int), h->stream));
   launch_init(h->X, h->Z, h->R, n, h->Wh, h->stream);
   h->launches++;
@@ -169,7 +177,7 @@ int ensure_log(tab_t h, int64_t extra) {
 
 bool use_single_cta(tab_t h) {
   if (h->engine == TAB_ENGINE_SINGLE_CTA) return true;
-  if (h->engine == TAB_ENGINE_GRID) return false;
+  if (h->engine != TAB_ENGINE_AUTO) return false;
   return h->n <= 256;
 }
 
@@ -210,11 +218,18 @@ int run_program(tab_t h, const HostProgram& hp, const DevProg& dp, uint64_t seed
       h->launches++;
     } else {
       const int nm = (int)(s.op_end - s.op_begin);
-      const int C = h->engine == TAB_ENGINE_GRID ? 0 : cluster_size_for(h->n, h->Wh);
+      // cluster-resident > grid-resident > streaming, as the engine allows
+      const bool any = h->engine == TAB_ENGINE_AUTO || h->engine == TAB_ENGINE_SINGLE_CTA;
+      const int C = (any || h->engine == TAB_ENGINE_CLUSTER) ? cluster_size_for(h->n, h->Wh) : 0;
+      const int G = (any || h->engine == TAB_ENGINE_GRID) ? h->res_ctas : 0;
       if (C > 0)
         CU(launch_measure_cluster(h->X, h->Z, h->R, h->n, h->Wh, dp.ops + s.op_begin, nm, h->k,
                                   seed, h->cid, h->shot, h->log + h->log_len, h->mw.err, C,
                                   h->stream));
+      else if (G > 0)
+        CU(launch_measure_resident(h->X, h->Z, h->R, h->n, h->Wh, dp.ops + s.op_begin, nm, h->k,
+                                   seed, h->cid, h->shot, h->log + h->log_len, h->mw.err, h->rw,
+                                   h->rbar, G, h->stream));
       else
         CU(launch_measure(h->X, h->Z, h->R, h->n, h->Wh, dp.ops + s.op_begin, nm, h->k, seed,
                           h->cid, h->shot, h->log + h->log_len, h->mw, h->meas_ctas, h->stream));
@@ -557,7 +572,7 @@ int tab_clear_outcomes(tab_t h) {
 int tab_set_engine(tab_t h, int engine) {
   int rc = check_handle(h);
   if (rc) return rc;
-  if (engine < TAB_ENGINE_AUTO || engine > TAB_ENGINE_CLUSTER) {
+  if (engine < TAB_ENGINE_AUTO || engine > TAB_ENGINE_STREAM) {
     set_error("unknown engine %d", engine);
     return TAB_EINVAL;
   }

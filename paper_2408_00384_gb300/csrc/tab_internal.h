@@ -99,6 +99,15 @@ cudaError_t launch_measure_cluster(uint32_t* X, uint32_t* Z, uint32_t* R, int n,
                                    const uint32_t* mops, int nm, uint64_t k0, uint64_t seed,
                                    uint64_t cid, uint32_t shot, uint8_t* out, int* err, int C,
                                    cudaStream_t s);
+// Grid-resident measurement engine (kernels_cluster.cu): CTA count for n
+// qubits (0 if the tableau does not fit the GPU's shared memory), its global
+// workspace in words, and the launch.
+int resident_ctas_for(int n, int Wh, int sm_count);
+size_t resident_work_words(int n, int max_ctas);
+cudaError_t launch_measure_resident(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh,
+                                    const uint32_t* mops, int nm, uint64_t k0, uint64_t seed,
+                                    uint64_t cid, uint32_t shot, uint8_t* out, int* err,
+                                    uint32_t* work, GridBar* bar, int G, cudaStream_t s);
 size_t measure_work_words(int n, int max_ctas);
 cudaError_t launch_pack(uint32_t* X, uint32_t* Z, uint32_t* R, const uint8_t* xs,
                         const uint8_t* zs, const uint8_t* rs, int n, int Wh, cudaStream_t s);

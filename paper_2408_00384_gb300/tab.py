@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "TAB_OK", -1: "TAB_EINVAL", -2: "TAB_ERANGE", -3: "TAB_ENOMEM
                 -4: "TAB_ECUDA", -5: "TAB_EDEVICE", -6: "TAB_ETIMEOUT", -7: "TAB_ESTATE"}
 MAX_QUBITS = 16384
 NOALLOC_SCRATCH_BYTES = 1 << 20
-ENGINE_AUTO, ENGINE_SINGLE_CTA, ENGINE_GRID, ENGINE_CLUSTER = 0, 1, 2, 3
+ENGINE_AUTO, ENGINE_SINGLE_CTA, ENGINE_GRID, ENGINE_CLUSTER, ENGINE_STREAM = 0, 1, 2, 3, 4
 BATCH_MAX_QUBITS = 640
 
 if not os.path.exists(LIB_PATH):

@@ -40,7 +40,7 @@ def assert_same(n, gates, seed=1, cid=0, shot=0, engine=None):
         assert bad.size == 0, (n, engine, name, bad[:10].tolist())
 
 
-ENGINES = [tab.ENGINE_SINGLE_CTA, tab.ENGINE_GRID, tab.ENGINE_CLUSTER]
+ENGINES = [tab.ENGINE_SINGLE_CTA, tab.ENGINE_GRID, tab.ENGINE_CLUSTER, tab.ENGINE_STREAM]
 
 
 @pytest.mark.parametrize("engine", ENGINES)
@@ -63,14 +63,14 @@ def test_layer_circuits_final_measure(engine, n, depth):
     assert_same(n, c.gates, seed=11, engine=engine)
 
 
-@pytest.mark.parametrize("engine", [tab.ENGINE_GRID, tab.ENGINE_CLUSTER])
-@pytest.mark.parametrize("n", [700, 1000, 2049, 2400])
-def test_grid_and_cluster_larger(engine, n):
+@pytest.mark.parametrize("engine", [tab.ENGINE_GRID, tab.ENGINE_CLUSTER, tab.ENGINE_STREAM])
+@pytest.mark.parametrize("n", [700, 1000, 2049, 2400, 4100, 8000])
+def test_larger_tableaus(engine, n):
     c = C.random_layer_circuit(n, 8, seed=n, meas_every=4, meas_frac=0.02)
     assert_same(n, c.gates, seed=5, engine=engine)
 
 
-@pytest.mark.parametrize("engine", [tab.ENGINE_AUTO, tab.ENGINE_GRID])
+@pytest.mark.parametrize("engine", [tab.ENGINE_AUTO, tab.ENGINE_GRID, tab.ENGINE_STREAM])
 def test_config2_full(engine):
     """n=1000, 1000 random layers, final MZ on all qubits: full compare."""
     c = C.config2()
