@@ -45,6 +45,7 @@ def parse():
     p.add_argument("--workload", default="cfg2",
                    choices=["cfg1", "cfg2", "cfg3", "batched", "served"])
     p.add_argument("--requests", type=int, default=48, help="served: number of requests")
+    p.add_argument("--circuits", type=int, default=4096, help="batched: number of circuits")
     p.add_argument("--engine", default="auto", choices=["auto", "grid", "single"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -386,7 +387,7 @@ def run_batched(args, ws, rank, local):
     from workloads import circuits as C
 
     torch.cuda.set_device(local)
-    circs = C.config4()
+    circs = C.config4(only=list(range(args.circuits)) if args.circuits < 4096 else None)
     circuits = [(c.n, c.gates, c.shots, c.circuit_id + 4096 * rank) for c in circs]
     b = tab.Batch(circuits)
     info = b.info()
@@ -413,17 +414,45 @@ def run_batched(args, ws, rank, local):
     clk = clocks.stop()
     per = [a.elapsed_time(z) for a, z in evs]
     ms = allreduce_max(statistics.mean(per), ws)
+
+    # plain one-circuit-per-launch path on a 1/64 sample of the same circuits
+    # (circuits are i.i.d., so 64 x the sample estimates the whole batch)
+    stride = 64
+    plain_ms = 0.0
+    for c in circs[::stride]:
+        prog = tab.Program(c.n, c.gates)
+        with tab.Tableau(c.n, stream=stream) as t:
+            t.reset()
+            t.run(prog)   # warm the engine's first-use set-up outside the timing
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for shot in range(c.shots):
+                t.reset()
+                t.set_rng(C.PHILOX_SEED, c.circuit_id + 4096 * rank, shot)
+                t.run(prog)
+            e1.record(stream)
+            t.sync()
+            plain_ms += e0.elapsed_time(e1)
+        prog.close()
+    plain_est_ms = plain_ms * stride
     line = {
         "metric": METRIC, "value": ws * info["n_gates"] / (ms / 1000.0), "unit": "gates/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic", "meas_per_s": ws * info["n_meas"] / (ms / 1000.0),
         "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
-        "config": {"workload": "batched: 4096 random-layer circuits, n ~ U[16,512], depth n, "
-                               "1-64 shots, final MZ on all qubits",
+        "config": {"workload": f"batched: {len(circs)} random-layer circuits, n ~ U[16,512], "
+                               "depth n, 1-64 shots, final MZ on all qubits",
                    "gates": info["n_gates"], "measurements": info["n_meas"],
                    "l2": "flushed before every timed step (256 MB device write)"},
         "gpu_launches": b.launches * args.steps, "clocks": clk, "roofline": None, "e2e": None,
+        "plain_path": {"ms_estimated": plain_est_ms,
+                       "gates_per_s": info["n_gates"] / (plain_est_ms / 1000.0),
+                       "meas_per_s": info["n_meas"] / (plain_est_ms / 1000.0),
+                       "sample": f"every {stride}th circuit, all its shots, one launch "
+                                 "sequence per shot, CUDA events, x{stride}",
+                       "batched_speedup": plain_est_ms / ms},
     }
     return line
 
@@ -440,7 +469,10 @@ def run_served(args, ws, rank, local):
     from workloads import circuits as C
 
     torch.cuda.set_device(local)
+    t_gen = time.perf_counter()
     reqs = [C.config5_request(c + 100000 * rank) for c in range(args.requests)]
+    print(f"[served] generated {len(reqs)} requests in {time.perf_counter() - t_gen:.1f} s",
+          file=sys.stderr, flush=True)
     gates_total = sum(r.n_gates for r in reqs)
     meas_total = sum(r.n_meas for r in reqs)
     cfg = dict(mem_budget_bytes=150 << 30, max_inflight=16, n_streams=8, meas_ctas=32, seed=C.PHILOX_SEED)
@@ -457,8 +489,10 @@ def run_served(args, ws, rank, local):
                     if delay > 0:
                         time.sleep(delay)
                 tickets.append((srv.submit(r.n, r.gates, 1, r.circuit_id), time.perf_counter()))
-            for (tk, ts), r in zip(tickets, reqs):
-                rc, out, l = srv.wait(tk)
+            for i, ((tk, ts), r) in enumerate(zip(tickets, reqs)):
+                rc, out, l = srv.wait(tk, timeout_s=300.0)
+                print(f"[served] request {i} n={r.n} done in {l:.3f} s", file=sys.stderr,
+                      flush=True)
                 if rc != tab.TAB_OK or out.size != r.n_meas:
                     raise RuntimeError(f"request failed: {rc} {tab.last_error()}")
                 lat.append(l)

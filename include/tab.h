@@ -281,6 +281,9 @@ typedef struct {
   int32_t meas_ctas;          /* CTAs per grid-engine measurement launch; 0 = default */
   double request_timeout_s;   /* fail a running request not completed by then; 0 = none */
   uint64_t seed;              /* Philox key of every request */
+  int32_t max_grid_inflight;  /* requests with n > TAB_BATCH_MAX_QUBITS (which spread over
+                                 many SMs) on the device at once; 0 = 1.  Smaller requests
+                                 run on one SM each and fill the rest of the GPU. */
 } tab_server_config;
 
 enum tab_req_state { TAB_REQ_PENDING = 0, TAB_REQ_RUNNING = 1, TAB_REQ_DONE = 2, TAB_REQ_FAILED = 3 };

@@ -12,6 +12,7 @@
 //    the column updates themselves never leave shared memory.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "measure_resident.cuh"
 #include "tab_internal.h"
@@ -181,9 +182,20 @@ int cluster_size_for(int n, int Wh) {
     cudaGetLastError();  // a failed probe must not leave an error behind
   }
   if (max_c == 0 || 2 * Wh > kResThreads) return 0;
-  // the largest cluster spreads the tableau thinnest; if it does not fit, no
-  // smaller one does
-  return res_layout(n, Wh, max_c).words * 4 <= (size_t)kClMaxSmem ? max_c : 0;
+  // Preferred size: TAB_CLUSTER_SIZE (2..16, a power of two) if set, else the
+  // largest supported.  A smaller cluster has a cheaper barrier and more work
+  // per CTA; the smallest size at least the preferred one that fits is used.
+  static int pref = -1;
+  if (pref < 0) {
+    pref = max_c;
+    if (const char* e = getenv("TAB_CLUSTER_SIZE")) {
+      const int v = atoi(e);
+      if (v >= 2 && v <= max_c && (v & (v - 1)) == 0) pref = v;
+    }
+  }
+  for (int c = pref; c <= max_c; c *= 2)
+    if (res_layout(n, Wh, c).words * 4 <= (size_t)kClMaxSmem) return c;
+  return 0;
 }
 
 static ResArgs res_args(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh, const uint32_t* mops,

@@ -114,7 +114,10 @@ __global__ void __launch_bounds__(kMeasThreads) k_measure(MArgs A) {
   int pend_a = -1, pend_pd = -1;              // column whose X write is deferred
   int prev_det = 0, prev_a = 0, prev_reset = 0;  // unresolved deterministic outcome
 
+  uint32_t next_code = A.nm > 0 ? __ldg(A.mops) : 0u;  // fetched one step ahead
   for (int m = 0; m < A.nm; ++m) {
+    const uint32_t code = next_code;
+    if (m + 1 < A.nm) next_code = __ldg(A.mops + m + 1);
     if (m > 0 && !grid_sync(A.bar, A.err)) return;
     // ---- resolve the previous deterministic outcome (needs every CTA's partial)
     if (prev_det) {
@@ -136,7 +139,6 @@ __global__ void __launch_bounds__(kMeasThreads) k_measure(MArgs A) {
       prev_det = 0;
     }
 
-    const uint32_t code = __ldg(A.mops + m);
     const int a = (int)dq1(code);
     const int reset = dop(code) == OP_MZR;
     const uint32_t rbit = outcome_bit(A.seed, A.cid, A.shot, A.k0 + (uint64_t)m);

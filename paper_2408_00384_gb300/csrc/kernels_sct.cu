@@ -61,6 +61,7 @@ __device__ __forceinline__ void sct_setup(Sct& s, uint32_t* base, int n) {
   s.Wc = 2 * s.Whc;
   s.Wp = s.Wc | 1;
   s.GG = kSctThreads / s.Wc;
+  if (s.GG > n) s.GG = n;  // a group per column at most
   s.X = base;
   s.Z = s.X + (size_t)n * s.Wp;
   s.R = s.Z + (size_t)n * s.Wp;
@@ -228,10 +229,19 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err)
       s.redhi[g * Wc + w] = hi;
     }
     __syncthreads();
-    if (tid < Wc) {
-      const int ww = tid;
+    // combine the column groups: one warp per word, lanes over groups, then a
+    // shuffle tree (mod-4 addition is associative and commutative)
+    const int cwarp = tid >> 5, cnw = T >> 5;
+    for (int ww = cwarp; ww < Wc; ww += cnw) {
       uint32_t L = 0u, H = 0u;
-      for (int gg = 0; gg < s.GG; ++gg) add4s(L, H, s.redlo[gg * Wc + ww], s.redhi[gg * Wc + ww]);
+      for (int gg = lane; gg < s.GG; gg += 32) add4s(L, H, s.redlo[gg * Wc + ww], s.redhi[gg * Wc + ww]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const uint32_t l2 = __shfl_xor_sync(0xffffffffu, L, o);
+        const uint32_t h2 = __shfl_xor_sync(0xffffffffu, H, o);
+        add4s(L, H, l2, h2);
+      }
+      if (lane != 0) continue;
       const uint32_t scal = ((uint32_t)s_kc + 2u * rp) & 3u;
       add4s(L, H, (scal & 1u) ? 0xffffffffu : 0u, (scal & 2u) ? 0xffffffffu : 0u);
       uint32_t Sw = s.sS[ww];
@@ -247,7 +257,7 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err)
     return (int)rbit;
   }
   // ---------------- deterministic outcome ----------------
-  const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+  const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;  // (random case returned above)
   const uint32_t lt = (1u << lane) - 1u;
   uint32_t acc = 0u;
   for (int j = warp; j < n; j += nw) {
@@ -332,9 +342,12 @@ __device__ void sct_run_segments(const Sct& s, const Seg* __restrict__ segs, int
     if (g.kind == 0) {
       sct_gates(s, ops, layer_off + g.layer_begin, (int)(g.layer_end - g.layer_begin));
     } else {
+      uint32_t next_code = __ldg(ops + g.op_begin);  // fetched one step ahead
       for (uint32_t op = g.op_begin; op < g.op_end; ++op) {
+        const uint32_t code = next_code;
+        if (op + 1 < g.op_end) next_code = __ldg(ops + op + 1);
         const uint32_t rbit = outcome_bit(seed, cid, shot, k);
-        const int m = sct_measure(s, __ldg(ops + op), rbit, err);
+        const int m = sct_measure(s, code, rbit, err);
         if (threadIdx.x == 0) out[o] = (uint8_t)m;
         ++k;
         ++o;

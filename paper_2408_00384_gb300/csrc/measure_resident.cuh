@@ -140,9 +140,11 @@ __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
   __syncthreads();
 
   int prev_det = 0, prev_a = 0, prev_reset = 0;
+  uint32_t next_code = A.nm > 0 ? __ldg(A.mops) : 0u;  // fetched one step ahead
   for (int m = 0; m < A.nm; ++m) {
     const int buf = m & 1;
-    const uint32_t code = __ldg(A.mops + m);
+    const uint32_t code = next_code;
+    if (m + 1 < A.nm) next_code = __ldg(A.mops + m + 1);
     const int a = (int)dq1(code);
     const bool reset = dop(code) == OP_MZR;
     const uint32_t rbit = outcome_bit(A.seed, A.cid, A.shot, A.k0 + (uint64_t)m);

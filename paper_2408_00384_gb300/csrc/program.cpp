@@ -76,7 +76,8 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
   std::vector<int64_t> last((size_t)n, -1);  // global layer of the last gate per qubit
   int64_t nlayers = 0;                       // layers emitted so far (global)
   std::vector<uint32_t> seg_codes;
-  std::vector<int64_t> seg_layer;
+  std::vector<int32_t> seg_layer;
+  std::vector<uint32_t> seg_ver((size_t)n, 0u);
 
   // Each gate segment owns one contiguous run of layer_off entries:
   // layer_off[layer_begin] = op_begin, layer_off[layer_begin + L + 1] = end
@@ -85,7 +86,7 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
     if (seg_codes.empty()) return;
     const int64_t base = nlayers;
     int64_t top = base;
-    for (int64_t L : seg_layer) top = std::max(top, L + 1);
+    for (int32_t L : seg_layer) top = std::max<int64_t>(top, (int64_t)L + 1);
     const int64_t nl = top - base;
     const int kOps = 10;  // bucket by (layer, op) with a counting sort
     std::vector<uint32_t> cnt((size_t)nl * kOps, 0);
@@ -126,6 +127,21 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
     }
     s.layer_end = (uint32_t)P.layer_off.size() - 1;
     P.segs.push_back(s);
+    // column versions in the final (layered) order
+    P.vers.resize(P.ops.size(), 0u);
+    for (uint32_t i = op_base; i < (uint32_t)P.ops.size(); ++i) {
+      const uint32_t c = P.ops[i];
+      const uint32_t a = dq1(c), b = dq2(c), op = dop(c);
+      const bool two = op == OP_CNOT || op == OP_CZ || op == OP_SWAP;
+      uint32_t v = seg_ver[a]++ & 0xFFFFu;
+      if (two) v |= (seg_ver[b]++ & 0xFFFFu) << 16;
+      P.vers[i] = v;
+    }
+    for (uint32_t i = op_base; i < (uint32_t)P.ops.size(); ++i) {  // reset touched counters
+      const uint32_t c = P.ops[i];
+      seg_ver[dq1(c)] = 0;
+      seg_ver[dq2(c)] = 0;
+    }
     nlayers = top;
     seg_codes.clear();
     seg_layer.clear();
@@ -146,6 +162,7 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
         P.segs.push_back(s);
       }
       P.ops.push_back(dcode(op, q1, 0));
+      P.vers.push_back(0u);
       P.segs.back().op_end++;
       P.n_meas++;
       continue;
@@ -157,7 +174,7 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
     last[q1] = L;
     if (two) last[q2] = L;
     seg_codes.push_back(dcode(op, q1, two ? q2 : 0));
-    seg_layer.push_back(L);
+    seg_layer.push_back((int32_t)L);
     P.n_gates++;
   }
   flush_gates();

@@ -40,6 +40,7 @@ using namespace tab;
 
 namespace tab {
 int handle_outcomes_async(tab_t h, uint8_t* host, cudaStream_t* used_stream);
+int handle_apply_program(tab_t h, const HostProgram& hp);
 int handle_set_meas_ctas(tab_t h, int ctas);
 size_t handle_device_bytes(int32_t n);
 }
@@ -56,7 +57,7 @@ struct Req {
   int64_t ticket = 0;
   int32_t n = 0, shots = 1;
   uint64_t cid = 0;
-  std::vector<tab_gate> gates;
+  HostProgram prog;           // compiled at submit, in the caller's thread
   int64_t n_meas = 0;
   size_t bytes = 0;
   tab_t h = nullptr;
@@ -82,8 +83,11 @@ struct tab_server_s {
   std::deque<Req*> pending;
   std::vector<Req*> running;
   std::unordered_map<int64_t, Req*> reqs;
-  std::vector<cudaStream_t> streams;
+  std::vector<cudaStream_t> streams;       // single-SM requests
   std::vector<int> stream_load;
+  std::vector<cudaStream_t> grid_streams;  // grid-wide requests, highest priority
+  std::vector<int> grid_busy;              // 1 while a request owns that stream
+  int grid_running = 0;  // running requests on grid-wide engines
   size_t mem_used = 0;
   int64_t next_ticket = 1;
   bool stop = false;
@@ -105,33 +109,50 @@ void finish(tab_server_s* S, Req* r, int status, const char* msg) {
   }
 }
 
+cudaStream_t request_stream(tab_server_s* S, const Req* r) {
+  return r->n > TAB_BATCH_MAX_QUBITS ? S->grid_streams[(size_t)r->stream_idx]
+                                     : S->streams[(size_t)r->stream_idx];
+}
+
 void release(tab_server_s* S, Req* r) {
   if (r->h) {
     tab_destroy(r->h);  // waits for the request's stream work first
     r->h = nullptr;
   }
   if (r->dmem) {  // stream-ordered free: no device-wide synchronization
-    cudaFreeAsync(r->dmem, S->streams[(size_t)r->stream_idx]);
+    cudaFreeAsync(r->dmem, request_stream(S, r));
     r->dmem = nullptr;
   }
   if (r->done) {
     cudaEventDestroy(r->done);
     r->done = nullptr;
   }
-  if (r->stream_idx >= 0) S->stream_load[(size_t)r->stream_idx]--;
+  if (r->n > TAB_BATCH_MAX_QUBITS) {
+    S->grid_running--;
+    if (r->stream_idx >= 0) S->grid_busy[(size_t)r->stream_idx] = 0;
+  } else if (r->stream_idx >= 0) {
+    S->stream_load[(size_t)r->stream_idx]--;
+  }
   S->mem_used -= r->bytes;
   r->bytes = 0;
 }
 
-// Admit one request: compile, allocate, enqueue the whole program.  Called
-// with the lock held; CUDA calls are asynchronous except allocation.
+// Admit one request: allocate, upload and enqueue its compiled program.
+// Called by the worker thread without the lock.
 int admit(tab_server_s* S, Req* r) {
   int si = 0;
-  for (size_t i = 1; i < S->streams.size(); ++i)
-    if (S->stream_load[i] < S->stream_load[(size_t)si]) si = (int)i;
-  r->stream_idx = si;
-  S->stream_load[(size_t)si]++;
-  cudaStream_t st = S->streams[(size_t)si];
+  if (r->n > TAB_BATCH_MAX_QUBITS) {
+    // at most grid_streams.size() grid-wide requests run at once: take a free one
+    while (si + 1 < (int)S->grid_busy.size() && S->grid_busy[(size_t)si]) ++si;
+    S->grid_busy[(size_t)si] = 1;
+    r->stream_idx = si;
+  } else {
+    for (size_t i = 1; i < S->streams.size(); ++i)
+      if (S->stream_load[i] < S->stream_load[(size_t)si]) si = (int)i;
+    r->stream_idx = si;
+    S->stream_load[(size_t)si]++;
+  }
+  cudaStream_t st = request_stream(S, r);
   const size_t hb = handle_device_bytes(r->n);
   int rc = TAB_OK;
   if (cudaMallocAsync(&r->dmem, hb, st) != cudaSuccess) {
@@ -141,11 +162,13 @@ int admit(tab_server_s* S, Req* r) {
     rc = TAB_ENOMEM;
   }
   if (rc == TAB_OK) rc = tab_create_on(r->n, r->dmem, hb, st, &r->h);
+  // small tableaus run whole on one SM; larger ones on the grid-wide engines
+  if (rc == TAB_OK && r->n <= TAB_BATCH_MAX_QUBITS) rc = tab_set_engine(r->h, TAB_ENGINE_SINGLE_CTA);
   if (rc == TAB_OK && S->cfg.meas_ctas > 0) rc = handle_set_meas_ctas(r->h, S->cfg.meas_ctas);
   for (int32_t s = 0; rc == TAB_OK && s < r->shots; ++s) {
     if (s > 0) rc = tab_reset(r->h);
     if (rc == TAB_OK) rc = tab_set_rng(r->h, S->cfg.seed, r->cid, (uint32_t)s);
-    if (rc == TAB_OK) rc = tab_apply(r->h, r->gates.data(), (int64_t)r->gates.size());
+    if (rc == TAB_OK) rc = handle_apply_program(r->h, r->prog);
     if (rc == TAB_OK && r->n_meas > 0) {
       cudaStream_t used = nullptr;
       rc = handle_outcomes_async(r->h, r->pinned + (size_t)s * r->n_meas, &used);
@@ -159,11 +182,11 @@ int admit(tab_server_s* S, Req* r) {
     }
   }
   r->t_admit = now_s();
-  r->state = TAB_REQ_RUNNING;
   return rc;
 }
 
 void worker_main(tab_server_s* S) {
+  // stream_load and the running set are only touched by this thread
   cudaSetDevice(S->dev);
   std::unique_lock<std::mutex> lk(S->mu);
   while (true) {
@@ -211,15 +234,38 @@ void worker_main(tab_server_s* S) {
         continue;
       }
       if (S->mem_used + r->bytes > S->cfg.mem_budget_bytes) break;
+      const bool grid = r->n > TAB_BATCH_MAX_QUBITS;
+      if (grid && S->grid_running >= std::max(1, S->cfg.max_grid_inflight)) {
+        // FIFO among grid-wide requests; small ones behind it may still go
+        bool admitted_small = false;
+        for (auto it = S->pending.begin(); it != S->pending.end(); ++it) {
+          Req* q = *it;
+          if (q->n > TAB_BATCH_MAX_QUBITS || q->bytes > S->cfg.mem_budget_bytes ||
+              S->mem_used + q->bytes > S->cfg.mem_budget_bytes)
+            continue;
+          S->pending.erase(it);
+          S->pending.push_front(q);
+          admitted_small = true;
+          break;
+        }
+        if (!admitted_small) break;
+        continue;
+      }
+      if (grid) S->grid_running++;
       S->pending.pop_front();
       S->mem_used += r->bytes;
       S->st.peak_mem = std::max<uint64_t>(S->st.peak_mem, S->mem_used);
+      // upload and enqueue without the lock: only this thread touches the
+      // running set, memory accounting and streams
+      lk.unlock();
       const int rc = admit(S, r);
+      lk.lock();
       if (rc != TAB_OK) {
         finish(S, r, rc, tab_last_error());
         release(S, r);
         S->cv_done.notify_all();
       } else {
+        r->state = TAB_REQ_RUNNING;
         S->running.push_back(r);
         S->st.peak_inflight = std::max<int64_t>(S->st.peak_inflight, (int64_t)S->running.size());
       }
@@ -262,16 +308,27 @@ int tab_server_create(const tab_server_config* cfg, tab_server_t* out) {
     set_error("no CUDA device");
     return TAB_ECUDA;
   }
-  for (int i = 0; i < cfg->n_streams; ++i) {
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);  // hi is numerically lowest
+  const int ngrid = std::max(1, cfg->max_grid_inflight);
+  for (int i = 0; i < cfg->n_streams + ngrid; ++i) {
     cudaStream_t st;
-    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    const bool grid = i >= cfg->n_streams;
+    if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, grid ? prio_hi : prio_lo) !=
+        cudaSuccess) {
       for (cudaStream_t x : S->streams) cudaStreamDestroy(x);
+      for (cudaStream_t x : S->grid_streams) cudaStreamDestroy(x);
       delete S;
       set_error("stream creation failed");
       return TAB_ECUDA;
     }
-    S->streams.push_back(st);
-    S->stream_load.push_back(0);
+    if (grid) {
+      S->grid_streams.push_back(st);
+      S->grid_busy.push_back(0);
+    } else {
+      S->streams.push_back(st);
+      S->stream_load.push_back(0);
+    }
   }
   S->worker = std::thread(worker_main, S);
   *out = S;
@@ -315,10 +372,14 @@ int tab_server_submit(tab_server_t S, const tab_circuit* c, int64_t* ticket) {
     set_error("host allocation failed");
     return TAB_ENOMEM;
   }
+  const int crc = build_program(c->n, c->gates, c->n_gates, &r->prog);
+  if (crc != TAB_OK) {
+    delete r;
+    return crc;
+  }
   r->n = c->n;
   r->shots = c->shots;
   r->cid = c->circuit_id;
-  r->gates.assign(c->gates, c->gates + c->n_gates);
   r->n_meas = nm;
   r->bytes = handle_device_bytes(c->n) + (size_t)c->n_gates * 4 + 8192 +
              (size_t)nm * c->shots;
@@ -432,6 +493,7 @@ int tab_server_destroy(tab_server_t S) {
     delete kv.second;
   }
   for (cudaStream_t st : S->streams) cudaStreamDestroy(st);
+  for (cudaStream_t st : S->grid_streams) cudaStreamDestroy(st);
   delete S;
   return TAB_OK;
 }

@@ -4,6 +4,7 @@
 // the CUDA kernels; this file validates, marshals and launches.
 #include <cuda_runtime.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -56,6 +57,7 @@ struct tab_prog_s {
   uint32_t* d_ops = nullptr;
   uint32_t* d_layer = nullptr;
   Seg* d_segs = nullptr;
+  uint2* d_rec = nullptr;
 };
 
 // Device copy of a compiled program.
@@ -63,9 +65,12 @@ struct DevProg {
   uint32_t* ops = nullptr;
   uint32_t* layer = nullptr;
   Seg* segs = nullptr;
+  uint2* rec = nullptr;  // (code, versions) per op, for the dataflow gate kernel
 };
 
 namespace {
+
+bool use_flow_gates(int n);
 
 int sm_count_of(int dev) {
   int v = 0;
@@ -213,8 +218,12 @@ int run_program(tab_t h, const HostProgram& hp, const DevProg& dp, uint64_t seed
   }
   for (const Seg& s : hp.segs) {
     if (s.kind == 0) {
-      CU(launch_gates_slab(h->X, h->Z, h->R, h->n, h->W, dp.ops, dp.layer + s.layer_begin,
-                           (int)(s.layer_end - s.layer_begin), h->mw.err, h->stream));
+      if (use_flow_gates(h->n))
+        CU(launch_gates_flow(h->X, h->Z, h->R, h->n, h->W, dp.rec, s.op_begin, s.op_end,
+                             h->mw.err, h->stream));
+      else
+        CU(launch_gates_slab(h->X, h->Z, h->R, h->n, h->W, dp.ops, dp.layer + s.layer_begin,
+                             (int)(s.layer_end - s.layer_begin), h->mw.err, h->stream));
       h->launches++;
     } else {
       const int nm = (int)(s.op_end - s.op_begin);
@@ -263,6 +272,22 @@ int upload(const HostProgram& hp, DevProg* d, cudaStream_t s, bool async_alloc) 
   if (!hp.segs.empty())
     CU(cudaMemcpyAsync(d->segs, hp.segs.data(), hp.segs.size() * sizeof(Seg),
                        cudaMemcpyHostToDevice, s));
+  // 64-bit records for the dataflow gate kernel (same padding rule as ops);
+  // only when that kernel will run for this n
+  if (hp.n_gates == 0 || !use_flow_gates(hp.n)) return TAB_OK;
+  const size_t rb = (hp.ops.size() + kOpsPad) * sizeof(uint2);
+  if (async_alloc) {
+    CU(cudaMallocAsync((void**)&d->rec, rb, s));
+  } else {
+    CU(cudaMalloc((void**)&d->rec, rb));
+  }
+  {
+    std::vector<uint2> rec(hp.ops.size() + kOpsPad);
+    for (size_t i = 0; i < hp.ops.size(); ++i) rec[i] = make_uint2(hp.ops[i], hp.vers[i]);
+    for (size_t i = hp.ops.size(); i < rec.size(); ++i) rec[i] = make_uint2(0u, 0u);
+    CU(cudaMemcpyAsync(d->rec, rec.data(), rb, cudaMemcpyHostToDevice, s));
+    if (async_alloc) CU(cudaStreamSynchronize(s));  // rec is a stack temporary
+  }
   return TAB_OK;
 }
 
@@ -270,6 +295,19 @@ void free_async(DevProg& d, cudaStream_t s) {
   if (d.ops) cudaFreeAsync(d.ops, s);
   if (d.layer) cudaFreeAsync(d.layer, s);
   if (d.segs) cudaFreeAsync(d.segs, s);
+  if (d.rec) cudaFreeAsync(d.rec, s);
+}
+
+// Gate kernel choice: the dataflow kernel (no layer barriers) when the slab,
+// its version words and the record ring fit; TAB_GATE_KERNEL=layer forces the
+// layer-barrier kernel (for comparisons).
+bool use_flow_gates(int n) {
+  static int mode = -1;
+  if (mode < 0) {
+    const char* e = getenv("TAB_GATE_KERNEL");
+    mode = (e && strcmp(e, "layer") == 0) ? 0 : 1;
+  }
+  return mode == 1 && n <= gates_flow_max_n();
 }
 
 }  // namespace
@@ -435,6 +473,7 @@ int tab_prog_create(int32_t n, const tab_gate* gates, int64_t count, tab_prog_t*
     p->d_ops = d.ops;
     p->d_layer = d.layer;
     p->d_segs = d.segs;
+    p->d_rec = d.rec;
   }
   if (rc == TAB_OK) {
     cudaError_t e = cudaStreamSynchronize(nullptr);
@@ -456,6 +495,7 @@ int tab_prog_destroy(tab_prog_t p) {
   if (p->d_ops) cudaFree(p->d_ops);
   if (p->d_layer) cudaFree(p->d_layer);
   if (p->d_segs) cudaFree(p->d_segs);
+  if (p->d_rec) cudaFree(p->d_rec);
   delete p;
   return TAB_OK;
 }
@@ -491,6 +531,7 @@ int tab_run(tab_t h, tab_prog_t p) {
   d.ops = p->d_ops;
   d.layer = p->d_layer;
   d.segs = p->d_segs;
+  d.rec = p->d_rec;
   return run_program(h, p->hp, d, h->seed);
 }
 
@@ -664,6 +705,22 @@ int handle_set_meas_ctas(tab_t h, int ctas) {
 }
 
 size_t handle_device_bytes(int32_t n) { return tab_bytes_required(n); }
+
+// Enqueue an already compiled program (the request server compiles at submit).
+int handle_apply_program(tab_t h, const HostProgram& hp) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (hp.n != h->n) {
+    set_error("program built for n=%d, handle has n=%d", hp.n, h->n);
+    return TAB_EINVAL;
+  }
+  if (hp.ops.empty()) return TAB_OK;
+  DevProg d;
+  rc = upload(hp, &d, h->stream, true);
+  if (rc == TAB_OK) rc = run_program(h, hp, d, h->seed);
+  free_async(d, h->stream);
+  return rc;
+}
 
 int handle_view(tab_t h, HandleView* v) {
   int rc = check_handle(h);

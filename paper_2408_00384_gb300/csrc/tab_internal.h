@@ -54,6 +54,10 @@ struct HostProgram {
   int32_t n = 0;
   int64_t n_gates = 0, n_meas = 0;
   std::vector<uint32_t> ops;
+  // per gate op: versions its qubits must have reached within the segment
+  // (count of earlier gates on each qubit, mod 2^16): q1 in bits 0..15, q2 in
+  // 16..31; zero for measurement ops
+  std::vector<uint32_t> vers;
   std::vector<uint32_t> layer_off;  // size = layers + 1 when any gate exists
   std::vector<Seg> segs;
 };
@@ -80,6 +84,10 @@ struct MeasWork {
 // ---- launches (kernels_*.cu) ---------------------------------------------------------
 void launch_init(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh, cudaStream_t s);
 int gates_max_n();
+int gates_flow_max_n();
+cudaError_t launch_gates_flow(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
+                              const uint2* rec, uint32_t rb, uint32_t re, int* err,
+                              cudaStream_t s);
 // Layers handed to launch_gates_slab hold at most kMaxLayerOps gates, and the
 // device op buffer extends at least kOpsPad codes past its last code.
 constexpr int kMaxLayerOps = 2048;

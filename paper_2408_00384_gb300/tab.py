@@ -83,7 +83,8 @@ _sig("tab_batch_launches", ctypes.c_int, [_vp, _P(_i64)])
 
 class TabServerConfig(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", _u64), ("max_inflight", _i32), ("n_streams", _i32),
-                ("meas_ctas", _i32), ("request_timeout_s", ctypes.c_double), ("seed", _u64)]
+                ("meas_ctas", _i32), ("request_timeout_s", ctypes.c_double), ("seed", _u64),
+                ("max_grid_inflight", _i32)]
 
 
 class TabServerStats(ctypes.Structure):
@@ -340,9 +341,9 @@ class Server:
 
     def __init__(self, mem_budget_bytes: int = 150 << 30, max_inflight: int = 16,
                  n_streams: int = 8, meas_ctas: int = 0, request_timeout_s: float = 0.0,
-                 seed: int = 1):
+                 seed: int = 1, max_grid_inflight: int = 1):
         cfg = TabServerConfig(mem_budget_bytes, max_inflight, n_streams, meas_ctas,
-                              request_timeout_s, seed)
+                              request_timeout_s, seed, max_grid_inflight)
         h = _vp()
         _check(_L.tab_server_create(ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h

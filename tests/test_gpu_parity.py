@@ -246,3 +246,40 @@ def test_batch_config4_sample():
         for s in range(shots):
             want, _ = oracle.run_circuit(n, g, seed=C.PHILOX_SEED, circuit_id=cid, shot=s)
             assert np.array_equal(got[s], want), (n, cid, s)
+
+
+_LAYER_KERNEL_SCRIPT = r"""
+import sys, numpy as np
+sys.path.insert(0, %r)
+import oracle
+from workloads import circuits as C
+from paper_2408_00384_gb300 import tab
+cases = [(C.random_clifford_ops(40, 500, seed=3, measure_p=0.05, reset_p=0.05), 40),
+         (C.random_layer_circuit(700, 10, seed=7, meas_every=5, meas_frac=0.02).gates, 700),
+         (C.random_layer_circuit(3000, 4, seed=8, meas_every=2, meas_frac=0.01).gates, 3000)]
+for gates, n in cases:
+    want_out, want = oracle.run_circuit(n, gates, seed=2)
+    with tab.Tableau(n) as t:
+        t.set_engine(tab.ENGINE_GRID)
+        t.set_rng(2, 0, 0)
+        t.apply(gates)
+        out = t.read_outcomes()
+        got = t.export()
+    assert np.array_equal(out, want_out), n
+    for g, w in zip(got, want):
+        assert np.array_equal(g, w), n
+print("ok")
+"""
+
+
+def test_layer_barrier_gate_kernel():
+    """The layer-barrier gate kernel (selected with TAB_GATE_KERNEL=layer)
+    against the oracle, in a fresh process so the selection takes effect."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, TAB_GATE_KERNEL="layer")
+    r = subprocess.run([sys.executable, "-c", _LAYER_KERNEL_SCRIPT % root], env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
