@@ -205,7 +205,7 @@ def oracle_step_seconds(c, budget_s):
 def run_reference(args, ws, rank):
     if rank != 0:
         return
-    c, desc = workload(args.workload if args.workload != "batched" else "cfg2", 0)
+    c, desc = workload(args.workload if args.workload in ("cfg1", "cfg2", "cfg3") else "cfg2", 0)
     budget = max(1.0, 150.0 / (args.steps + args.warmup))
     for _ in range(args.warmup):
         oracle_step_seconds(c, min(budget, 2.0))

@@ -62,20 +62,31 @@ struct CommCluster {
     cl_sync();
     return true;
   }
-  // owner: its column into the mask buffer of every CTA (same smem offset)
-  __device__ void publish_mask(uint32_t* S, const uint32_t* col, int W, int) {
-    for (int i = threadIdx.x; i < C * W; i += blockDim.x) {
-      const int t = i / W, w = i - t * W;
-      cl_st(cl_map(S + w, (uint32_t)t), col[w]);
+  __device__ void stage_columns(const ResSmem&, int, int, int, const int*, int, int,
+                                const ResArgs&) {}
+  // read the measured columns from their owners' shared memory
+  __device__ void gather_columns(const ResSmem& s, int, int D, const int* q, int W, int Wp,
+                                 const ResArgs&) {
+    for (int e = threadIdx.x; e < D * W; e += blockDim.x) {
+      const int d = e / W, w = e - d * W;
+      const int a = q[d];
+      const size_t off = (size_t)(a / C) * Wp + w;
+      s.TX[e] = cl_ld(cl_map(s.Xs + off, (uint32_t)(a % C)));
+      s.TZ[e] = cl_ld(cl_map(s.Zs + off, (uint32_t)(a % C)));
     }
   }
-  __device__ void fetch_mask(uint32_t*, int, int) {}
-  __device__ void publish_dp(uint32_t* dpv, int buf, uint32_t v) {
-    if ((int)threadIdx.x < C) cl_st(cl_map(dpv + buf * C + r, threadIdx.x), v);
+  // nobody may change a column before every CTA has read it
+  __device__ bool after_gather() {
+    cl_sync();
+    return true;
   }
-  __device__ uint32_t sum_dp(const uint32_t* dpv, int buf) {
+  __device__ void publish_dp(uint32_t* dpv, int buf, int i, int kb, uint32_t v) {
+    if ((int)threadIdx.x < C)
+      cl_st(cl_map(dpv + ((size_t)buf * kb + i) * C + r, threadIdx.x), v);
+  }
+  __device__ uint32_t sum_dp(const uint32_t* dpv, int buf, int i, int kb) {
     uint32_t e = 0;
-    for (int t = 0; t < C; ++t) e += dpv[buf * C + t];
+    for (int t = 0; t < C; ++t) e += dpv[((size_t)buf * kb + i) * C + t];
     return e;
   }
   // fold every CTA's sign partials (and CTA 0's base) into R
@@ -94,7 +105,8 @@ struct CommCluster {
   __device__ void finish() { cl_sync(); }
 };
 
-// A cooperative grid: a global mask buffer, global partials, grid barrier.
+// A cooperative grid: owners stage measured columns in global memory (L2),
+// global deterministic partials, bounded grid barrier.
 struct CommGrid {
   const ResArgs& A;
   int C, r;
@@ -102,19 +114,38 @@ struct CommGrid {
   __device__ int size() const { return C; }
   __device__ int rank() const { return r; }
   __device__ bool sync() { return grid_sync(A.bar, A.err); }
-  __device__ void publish_mask(uint32_t*, const uint32_t* col, int W, int buf) {
-    for (int w = threadIdx.x; w < W; w += blockDim.x) A.mb[(size_t)buf * W + w] = col[w];
+  // owners write the next batch's measured columns (their current state)
+  __device__ void stage_columns(const ResSmem& s, int buf, int, int D, const int* q, int W, int Wp,
+                                const ResArgs&) {
+    const int KB = A.kb;
+    for (int e = threadIdx.x; e < D * W; e += blockDim.x) {
+      const int d = e / W, w = e - d * W;
+      const int a = q[d];
+      if (a % C != r) continue;
+      const size_t off = (size_t)(a / C) * Wp + w;
+      uint32_t* dst = A.stage + (((size_t)buf * KB + d) * 2) * W;
+      dst[w] = s.Xs[off];
+      dst[W + w] = s.Zs[off];
+    }
   }
-  __device__ void fetch_mask(uint32_t* S, int W, int buf) {
-    for (int w = threadIdx.x; w < W; w += blockDim.x) S[w] = __ldcg(A.mb + (size_t)buf * W + w);
+  __device__ void gather_columns(const ResSmem& s, int buf, int D, const int*, int W, int,
+                                 const ResArgs&) {
+    const int KB = A.kb;
+    for (int e = threadIdx.x; e < D * W; e += blockDim.x) {
+      const int d = e / W, w = e - d * W;
+      const uint32_t* src = A.stage + (((size_t)buf * KB + d) * 2) * W;
+      s.TX[e] = __ldcg(src + w);
+      s.TZ[e] = __ldcg(src + W + w);
+    }
     __syncthreads();
   }
-  __device__ void publish_dp(uint32_t*, int buf, uint32_t v) {
-    if (threadIdx.x == 0) A.dp[(size_t)buf * C + r] = v;
+  __device__ bool after_gather() { return true; }
+  __device__ void publish_dp(uint32_t*, int buf, int i, int kb, uint32_t v) {
+    if (threadIdx.x == 0) A.dp[((size_t)buf * kb + i) * C + r] = v;
   }
-  __device__ uint32_t sum_dp(const uint32_t*, int buf) {
+  __device__ uint32_t sum_dp(const uint32_t*, int buf, int i, int kb) {
     uint32_t e = 0;
-    for (int t = 0; t < C; ++t) e += __ldcg(A.dp + (size_t)buf * C + t);
+    for (int t = 0; t < C; ++t) e += __ldcg(A.dp + ((size_t)buf * kb + i) * C + t);
     return e;
   }
   __device__ bool fold(const ResSmem& s, int W, const ResArgs&) {
@@ -194,7 +225,7 @@ int cluster_size_for(int n, int Wh) {
     }
   }
   for (int c = pref; c <= max_c; c *= 2)
-    if (res_layout(n, Wh, c).words * 4 <= (size_t)kClMaxSmem) return c;
+    if (res_batch_for(n, Wh, c, kClMaxSmem) >= 4) return c;
   return 0;
 }
 
@@ -224,6 +255,7 @@ cudaError_t launch_measure_cluster(uint32_t* X, uint32_t* Z, uint32_t* R, int n,
                                    cudaStream_t s) {
   if (nm <= 0) return cudaSuccess;
   ResArgs A = res_args(X, Z, R, n, Wh, mops, nm, k0, seed, cid, shot, out, err);
+  A.kb = res_batch_for(n, Wh, C, kClMaxSmem);
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -232,7 +264,7 @@ cudaError_t launch_measure_cluster(uint32_t* X, uint32_t* Z, uint32_t* R, int n,
   at[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3((unsigned)C);
   cfg.blockDim = dim3(kResThreads);
-  cfg.dynamicSmemBytes = res_layout(n, Wh, C).words * 4;
+  cfg.dynamicSmemBytes = res_layout(n, Wh, C, A.kb).words * 4;
   cfg.stream = s;
   cfg.attrs = at;
   cfg.numAttrs = 1;
@@ -254,13 +286,16 @@ int resident_ctas_for(int n, int Wh, int sm_count) {
   }
   if (2 * Wh > kResThreads) return 0;
   for (int g = 16; g <= sm_count; g += 8)
-    if (res_layout(n, Wh, g).words * 4 <= (size_t)kClMaxSmem && (n + g - 1) / g < (1 << 14)) return g;
+    if (res_batch_for(n, Wh, g, kClMaxSmem) >= 4 && (n + g - 1) / g < (1 << 14)) return g;
   return 0;
 }
 
 size_t resident_work_words(int n, int max_ctas) {
   const int W = 2 * half_words(n);
-  return 2 * (size_t)W + 2 * (size_t)max_ctas + (size_t)max_ctas * 2 * W + 2 * (size_t)W + 16;
+  return 4 * (size_t)kBatchMax * W          // staged columns [2][kb][2][W]
+         + 2 * (size_t)kBatchMax * max_ctas // deterministic partials [2][kb][G]
+         + (size_t)max_ctas * 2 * W         // sign partials for the fold
+         + 2 * (size_t)W + 16;              // base signs
 }
 
 cudaError_t launch_measure_resident(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh,
@@ -270,16 +305,17 @@ cudaError_t launch_measure_resident(uint32_t* X, uint32_t* Z, uint32_t* R, int n
   if (nm <= 0) return cudaSuccess;
   ResArgs A = res_args(X, Z, R, n, Wh, mops, nm, k0, seed, cid, shot, out, err);
   const int W = 2 * Wh;
-  A.mb = work;
-  A.dp = A.mb + 2 * (size_t)W;
-  A.ph = A.dp + 2 * (size_t)G;
+  A.kb = res_batch_for(n, Wh, G, kClMaxSmem);
+  A.stage = work;
+  A.dp = A.stage + 4 * (size_t)A.kb * W;
+  A.ph = A.dp + 2 * (size_t)A.kb * G;
   A.r4 = A.ph + (size_t)G * 2 * W;
   A.bar = bar;
   cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBar), s);
   if (e != cudaSuccess) return e;
   void* args[] = {&A};
   return cudaLaunchCooperativeKernel((const void*)k_measure_resident, dim3((unsigned)G),
-                                     dim3(kResThreads), args, res_layout(n, Wh, G).words * 4, s);
+                                     dim3(kResThreads), args, res_layout(n, Wh, G, A.kb).words * 4, s);
 }
 
 }  // namespace tab
