@@ -33,7 +33,66 @@ void set_error(const char* fmt, ...) {
 
 const char* last_error() { return g_last_error.c_str(); }
 
-int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out) {
+// Program-order compile for the dataflow gate kernel: one pass, no layering.
+// Program order is itself a topological order of the gate dependencies, and a
+// gate's column versions are its per-qubit positions in program order within
+// its gate run.  Gate runs carry no layer table (layer_begin == layer_end).
+static int build_program_stream(int32_t n, const tab_gate* gates, int64_t count,
+                                HostProgram* out) {
+  HostProgram& P = *out;
+  P = HostProgram();
+  P.n = n;
+  P.layered = false;
+  P.ops.reserve((size_t)count);
+  P.vers.reserve((size_t)count);
+  std::vector<uint32_t> cnt((size_t)n, 0u), stamp((size_t)n, 0u);
+  uint32_t seg_id = 1;  // stamps: counters restart in every gate run
+  int cur = -1;         // kind of the open segment (-1: none)
+  for (int64_t i = 0; i < count; ++i) {
+    const uint64_t g = gates[i];
+    const uint32_t op = (uint32_t)(g >> 56);
+    const uint32_t q1 = (uint32_t)((g >> 28) & 0xFFFFFFFull), q2 = (uint32_t)(g & 0xFFFFFFFull);
+    if (op == TAB_BARRIER || op == TAB_I) continue;
+    const bool meas = op == TAB_MZ || op == TAB_MZR;
+    const int kind = meas ? 1 : 0;
+    if (cur != kind) {
+      if (cur == 0) ++seg_id;
+      Seg s{};
+      s.kind = (uint32_t)kind;
+      s.op_begin = s.op_end = (uint32_t)P.ops.size();
+      s.meas_before = (uint32_t)P.n_meas;
+      P.segs.push_back(s);
+      cur = kind;
+    }
+    if (meas) {
+      P.ops.push_back(dcode(op, q1, 0));
+      P.vers.push_back(0u);
+      P.n_meas++;
+    } else {
+      const bool two = (op == TAB_CNOT || op == TAB_CZ || op == TAB_SWAP);
+      if (stamp[q1] != seg_id) {
+        stamp[q1] = seg_id;
+        cnt[q1] = 0;
+      }
+      uint32_t v = cnt[q1]++ & 0xFFFFu;
+      if (two) {
+        if (stamp[q2] != seg_id) {
+          stamp[q2] = seg_id;
+          cnt[q2] = 0;
+        }
+        v |= (cnt[q2]++ & 0xFFFFu) << 16;
+      }
+      P.ops.push_back(dcode(op, q1, two ? q2 : 0));
+      P.vers.push_back(v);
+      P.n_gates++;
+    }
+    P.segs.back().op_end++;
+  }
+  return TAB_OK;
+}
+
+int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out,
+                  bool layered) {
   if (n < 1 || n > TAB_MAX_QUBITS) {
     set_error("n=%d outside [1, %d]", n, TAB_MAX_QUBITS);
     return TAB_ERANGE;
@@ -69,6 +128,7 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
     }
   }
 
+  if (!layered) return build_program_stream(n, gates, count, out);
   HostProgram& P = *out;
   P = HostProgram();
   P.n = n;

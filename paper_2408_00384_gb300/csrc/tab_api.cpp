@@ -50,6 +50,11 @@ struct tab_s {
   int64_t launches = 0;
   int sticky = TAB_OK;        // latched device error
   int engine = TAB_ENGINE_AUTO;
+  // pinned staging area for program uploads (one H2D copy per call)
+  uint8_t* stg = nullptr;
+  size_t stg_cap = 0;
+  cudaEvent_t stg_ev = nullptr;
+  bool stg_pending = false;
 };
 
 struct tab_prog_s {
@@ -66,6 +71,7 @@ struct DevProg {
   uint32_t* layer = nullptr;
   Seg* segs = nullptr;
   uint2* rec = nullptr;  // (code, versions) per op, for the dataflow gate kernel
+  void* base = nullptr;  // single allocation holding all of the above (staged uploads)
 };
 
 namespace {
@@ -218,7 +224,7 @@ int run_program(tab_t h, const HostProgram& hp, const DevProg& dp, uint64_t seed
   }
   for (const Seg& s : hp.segs) {
     if (s.kind == 0) {
-      if (use_flow_gates(h->n))
+      if (!hp.layered || use_flow_gates(h->n))
         CU(launch_gates_flow(h->X, h->Z, h->R, h->n, h->W, dp.rec, s.op_begin, s.op_end,
                              h->mw.err, h->stream));
       else
@@ -292,11 +298,67 @@ int upload(const HostProgram& hp, DevProg* d, cudaStream_t s, bool async_alloc) 
 }
 
 void free_async(DevProg& d, cudaStream_t s) {
+  if (d.base) {
+    cudaFreeAsync(d.base, s);
+    return;
+  }
   if (d.ops) cudaFreeAsync(d.ops, s);
   if (d.layer) cudaFreeAsync(d.layer, s);
   if (d.segs) cudaFreeAsync(d.segs, s);
   if (d.rec) cudaFreeAsync(d.rec, s);
 }
+
+// Upload a compiled program through the handle's pinned staging area: one
+// stream-ordered allocation and one asynchronous copy.  The staging area is
+// reused once the previous copy out of it has completed.
+int upload_staged(tab_t h, const HostProgram& hp, DevProg* d) {
+  const bool want_rec = hp.n_gates > 0 && use_flow_gates(hp.n);
+  const size_t ob = align256((hp.ops.size() + kOpsPad) * 4);
+  const size_t lb = align256(std::max<size_t>(hp.layer_off.size(), 1) * 4);
+  const size_t sb = align256(std::max<size_t>(hp.segs.size(), 1) * sizeof(Seg));
+  const size_t rb = want_rec ? align256((hp.ops.size() + kOpsPad) * sizeof(uint2)) : 0;
+  const size_t total = ob + lb + sb + rb;
+  if (h->stg_pending) {
+    CU(cudaEventSynchronize(h->stg_ev));
+    h->stg_pending = false;
+  }
+  if (h->stg_cap < total) {
+    if (h->stg) cudaFreeHost(h->stg);
+    h->stg = nullptr;
+    h->stg_cap = 0;
+    const size_t cap = total + total / 4;
+    CU(cudaMallocHost((void**)&h->stg, cap));
+    h->stg_cap = cap;
+  }
+  if (!h->stg_ev) CU(cudaEventCreateWithFlags(&h->stg_ev, cudaEventDisableTiming));
+  uint8_t* st = h->stg;
+  uint32_t* ops = reinterpret_cast<uint32_t*>(st);
+  if (!hp.ops.empty()) memcpy(ops, hp.ops.data(), hp.ops.size() * 4);
+  memset(ops + hp.ops.size(), 0, (size_t)kOpsPad * 4);
+  if (!hp.layer_off.empty()) memcpy(st + ob, hp.layer_off.data(), hp.layer_off.size() * 4);
+  if (!hp.segs.empty()) memcpy(st + ob + lb, hp.segs.data(), hp.segs.size() * sizeof(Seg));
+  if (want_rec) {
+    uint2* rec = reinterpret_cast<uint2*>(st + ob + lb + sb);
+    const size_t no = hp.ops.size();
+    for (size_t i = 0; i < no; ++i) rec[i] = make_uint2(hp.ops[i], hp.vers[i]);
+    memset(rec + no, 0, (size_t)kOpsPad * sizeof(uint2));
+  }
+  uint8_t* dev = nullptr;
+  CU(cudaMallocAsync((void**)&dev, total, h->stream));
+  CU(cudaMemcpyAsync(dev, st, total, cudaMemcpyHostToDevice, h->stream));
+  CU(cudaEventRecord(h->stg_ev, h->stream));
+  h->stg_pending = true;
+  d->base = dev;
+  d->ops = reinterpret_cast<uint32_t*>(dev);
+  d->layer = reinterpret_cast<uint32_t*>(dev + ob);
+  d->segs = reinterpret_cast<Seg*>(dev + ob + lb);
+  d->rec = want_rec ? reinterpret_cast<uint2*>(dev + ob + lb + sb) : nullptr;
+  return TAB_OK;
+}
+
+// Compile mode for a call on this handle: program order (one pass) when the
+// dataflow gate kernel will run its gates, ASAP layers otherwise.
+bool layered_for(tab_t h) { return use_single_cta(h) || !use_flow_gates(h->n); }
 
 // Gate kernel choice: the dataflow kernel (no layer barriers) when the slab,
 // its version words and the record ring fit; TAB_GATE_KERNEL=layer forces the
@@ -398,6 +460,8 @@ int tab_destroy(tab_t h) {
   if (h->log) cudaFreeAsync(h->log, h->stream);
   cudaStreamSynchronize(h->stream);
   if (h->own_mem && h->base) cudaFree(h->base);
+  if (h->stg) cudaFreeHost(h->stg);
+  if (h->stg_ev) cudaEventDestroy(h->stg_ev);
   delete h;
   return TAB_OK;
 }
@@ -445,11 +509,11 @@ int tab_apply(tab_t h, const tab_gate* gates, int64_t count) {
   int rc = check_handle(h);
   if (rc) return rc;
   HostProgram hp;
-  rc = build_program(h->n, gates, count, &hp);
+  rc = build_program(h->n, gates, count, &hp, layered_for(h));
   if (rc) return rc;
   if (hp.ops.empty()) return TAB_OK;
   DevProg d;
-  rc = upload(hp, &d, h->stream, true);
+  rc = upload_staged(h, hp, &d);
   if (rc == TAB_OK) rc = run_program(h, hp, d, h->seed);
   free_async(d, h->stream);
   return rc;
@@ -552,12 +616,12 @@ static int measure_common(tab_t h, const int32_t* qubits, int32_t k, uint64_t se
     g[(size_t)i] = tab_make_gate(TAB_MZ, (uint32_t)qubits[i], 0);
   }
   HostProgram hp;
-  rc = build_program(h->n, g.data(), k, &hp);
+  rc = build_program(h->n, g.data(), k, &hp, false);  // measurements only
   if (rc) return rc;
   *first = h->log_len;
   if (hp.ops.empty()) return TAB_OK;
   DevProg d;
-  rc = upload(hp, &d, h->stream, true);
+  rc = upload_staged(h, hp, &d);
   if (rc == TAB_OK) rc = run_program(h, hp, d, seed);
   free_async(d, h->stream);
   return rc;
@@ -706,6 +770,10 @@ int handle_set_meas_ctas(tab_t h, int ctas) {
 
 size_t handle_device_bytes(int32_t n) { return tab_bytes_required(n); }
 
+// Whether a grid-engine handle of n qubits runs gates with the dataflow kernel
+// (then a program-order compile suffices).
+bool flow_gates_for(int n) { return use_flow_gates(n); }
+
 // Enqueue an already compiled program (the request server compiles at submit).
 int handle_apply_program(tab_t h, const HostProgram& hp) {
   int rc = check_handle(h);
@@ -715,8 +783,12 @@ int handle_apply_program(tab_t h, const HostProgram& hp) {
     return TAB_EINVAL;
   }
   if (hp.ops.empty()) return TAB_OK;
+  if (!hp.layered && use_single_cta(h)) {
+    set_error("a program-order program needs a grid engine");
+    return TAB_EINVAL;
+  }
   DevProg d;
-  rc = upload(hp, &d, h->stream, true);
+  rc = upload_staged(h, hp, &d);
   if (rc == TAB_OK) rc = run_program(h, hp, d, h->seed);
   free_async(d, h->stream);
   return rc;

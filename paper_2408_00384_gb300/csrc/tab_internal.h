@@ -52,6 +52,7 @@ struct Seg {
 
 struct HostProgram {
   int32_t n = 0;
+  bool layered = true;  // gate runs grouped into ASAP layers (else program order)
   int64_t n_gates = 0, n_meas = 0;
   std::vector<uint32_t> ops;
   // per gate op: versions its qubits must have reached within the segment
@@ -62,8 +63,12 @@ struct HostProgram {
   std::vector<Seg> segs;
 };
 
-// Validate + layer a gate list.  Returns TAB_OK or an error (message set).
-int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out);
+// Validate and compile a gate list.  layered: gate runs grouped into ASAP
+// layers of disjoint gates (every engine can run it); otherwise program order
+// with per-gate column versions only (the dataflow gate kernel; one pass).
+// Returns TAB_OK or an error (message set).
+int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out,
+                  bool layered = true);
 
 // ---- global grid barrier state ----------------------------------------------------
 struct GridBar {
