@@ -19,6 +19,20 @@
 
 namespace tab {
 
+// Measurements per batch: TAB_MEAS_BATCH (1, 2, 4, ..., 32) caps it for
+// tuning sweeps; the default is the largest that fits.
+static int batch_cap() {
+  static int cap = 0;
+  if (cap == 0) {
+    cap = kBatchMax;
+    if (const char* e = getenv("TAB_MEAS_BATCH")) {
+      const int v = atoi(e);
+      if (v >= 1 && v <= kBatchMax && (v & (v - 1)) == 0) cap = v;
+    }
+  }
+  return cap;
+}
+
 constexpr int kClMaxSmem = 226 * 1024;  // dynamic; static shared memory comes on top
 
 __device__ __forceinline__ uint32_t cl_smem(const void* p) {
@@ -255,7 +269,7 @@ cudaError_t launch_measure_cluster(uint32_t* X, uint32_t* Z, uint32_t* R, int n,
                                    cudaStream_t s) {
   if (nm <= 0) return cudaSuccess;
   ResArgs A = res_args(X, Z, R, n, Wh, mops, nm, k0, seed, cid, shot, out, err);
-  A.kb = res_batch_for(n, Wh, C, kClMaxSmem);
+  A.kb = res_batch_for(n, Wh, C, kClMaxSmem, batch_cap());
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -305,7 +319,7 @@ cudaError_t launch_measure_resident(uint32_t* X, uint32_t* Z, uint32_t* R, int n
   if (nm <= 0) return cudaSuccess;
   ResArgs A = res_args(X, Z, R, n, Wh, mops, nm, k0, seed, cid, shot, out, err);
   const int W = 2 * Wh;
-  A.kb = res_batch_for(n, Wh, G, kClMaxSmem);
+  A.kb = res_batch_for(n, Wh, G, kClMaxSmem, batch_cap());
   A.stage = work;
   A.dp = A.stage + 4 * (size_t)A.kb * W;
   A.ph = A.dp + 2 * (size_t)A.kb * G;

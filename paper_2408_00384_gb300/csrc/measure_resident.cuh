@@ -90,10 +90,11 @@ __host__ __device__ inline ResLayout res_layout(int n, int Wh, int C, int kb) {
   return L;
 }
 
-// Largest batch size (power of two <= kBatchMax) that fits `limit` bytes; 0
-// if even single measurements do not fit.
-__host__ __device__ inline int res_batch_for(int n, int Wh, int C, size_t limit) {
-  for (int kb = kBatchMax; kb >= 1; kb >>= 1)
+// Largest batch size (power of two <= cap <= kBatchMax) that fits `limit`
+// bytes; 0 if even single measurements do not fit.
+__host__ __device__ inline int res_batch_for(int n, int Wh, int C, size_t limit,
+                                             int cap = kBatchMax) {
+  for (int kb = cap; kb >= 1; kb >>= 1)
     if (res_layout(n, Wh, C, kb).words * 4 <= limit) return kb;
   return 0;
 }

@@ -360,14 +360,14 @@ int upload_staged(tab_t h, const HostProgram& hp, DevProg* d) {
 // dataflow gate kernel will run its gates, ASAP layers otherwise.
 bool layered_for(tab_t h) { return use_single_cta(h) || !use_flow_gates(h->n); }
 
-// Gate kernel choice: the dataflow kernel (no layer barriers) when the slab,
-// its version words and the record ring fit; TAB_GATE_KERNEL=layer forces the
-// layer-barrier kernel (for comparisons).
+// Gate kernel choice: the layer-barrier kernel by default (faster on the
+// measured workloads); TAB_GATE_KERNEL=flow selects the dataflow kernel (no
+// layer barriers) when its slab, version words and record ring fit.
 bool use_flow_gates(int n) {
   static int mode = -1;
   if (mode < 0) {
     const char* e = getenv("TAB_GATE_KERNEL");
-    mode = (e && strcmp(e, "layer") == 0) ? 0 : 1;
+    mode = (e && strcmp(e, "flow") == 0) ? 1 : 0;
   }
   return mode == 1 && n <= gates_flow_max_n();
 }

@@ -31,8 +31,22 @@ def gpu_run(n, gates, seed=1, cid=0, shot=0, engine=None):
     return out, (x, z, r)
 
 
+_ORACLE_CACHE = {}
+
+
+def oracle_result(n, gates, seed, cid, shot):
+    """The oracle's run, computed once per distinct case and shared by every
+    engine that is compared with it (the large cases take the CPU seconds)."""
+    key = (n, seed, cid, shot, gates.size, hash(gates.tobytes()))
+    if key not in _ORACLE_CACHE:
+        if len(_ORACLE_CACHE) >= 2:
+            _ORACLE_CACHE.clear()
+        _ORACLE_CACHE[key] = oracle.run_circuit(n, gates, seed=seed, circuit_id=cid, shot=shot)
+    return _ORACLE_CACHE[key]
+
+
 def assert_same(n, gates, seed=1, cid=0, shot=0, engine=None):
-    want_out, want = oracle.run_circuit(n, gates, seed=seed, circuit_id=cid, shot=shot)
+    want_out, want = oracle_result(n, gates, seed, cid, shot)
     got_out, got = gpu_run(n, gates, seed, cid, shot, engine)
     assert np.array_equal(got_out, want_out), (n, engine, np.nonzero(got_out != want_out)[0][:10])
     for name, g, w in zip("xzr", got, want):
@@ -250,7 +264,7 @@ def test_batch_config4_sample():
             assert np.array_equal(got[s], want), (n, cid, s)
 
 
-_LAYER_KERNEL_SCRIPT = r"""
+_FLOW_KERNEL_SCRIPT = r"""
 import sys, numpy as np
 sys.path.insert(0, %r)
 import oracle
@@ -274,14 +288,14 @@ print("ok")
 """
 
 
-def test_layer_barrier_gate_kernel():
-    """The layer-barrier gate kernel (selected with TAB_GATE_KERNEL=layer)
-    against the oracle, in a fresh process so the selection takes effect."""
+def test_dataflow_gate_kernel():
+    """The dataflow gate kernel (selected with TAB_GATE_KERNEL=flow) against
+    the oracle, in a fresh process so the selection takes effect."""
     import os
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    env = dict(os.environ, TAB_GATE_KERNEL="layer")
-    r = subprocess.run([sys.executable, "-c", _LAYER_KERNEL_SCRIPT % root], env=env,
+    env = dict(os.environ, TAB_GATE_KERNEL="flow")
+    r = subprocess.run([sys.executable, "-c", _FLOW_KERNEL_SCRIPT % root], env=env,
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
