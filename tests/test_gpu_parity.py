@@ -82,7 +82,8 @@ def test_layer_circuits_final_measure(engine, n, depth):
 def test_larger_tableaus(engine, n):
     # the oracle's rowsum costs ~n^2 cache misses per measurement on the CPU:
     # at most ~24 measurements keeps every case within seconds
-    c = C.random_layer_circuit(n, 8, seed=n, meas_every=4, meas_frac=min(0.02, 12.0 / n))
+    c = C.random_layer_circuit(n, 8, seed=n, meas_every=4, meas_frac=min(0.02, 12.0 / n),
+                               final_measure=n <= 1000)
     assert_same(n, c.gates, seed=5, engine=engine)
 
 
