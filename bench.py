@@ -46,7 +46,8 @@ def parse():
                    choices=["cfg1", "cfg2", "cfg3", "batched", "served"])
     p.add_argument("--requests", type=int, default=48, help="served: number of requests")
     p.add_argument("--circuits", type=int, default=4096, help="batched: number of circuits")
-    p.add_argument("--engine", default="auto", choices=["auto", "grid", "single"])
+    p.add_argument("--engine", default="auto",
+                   choices=["auto", "single", "cluster", "grid", "stream"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -252,7 +253,8 @@ def run_plain(args, ws, rank, local):
     parts = split_program(c)
     stream = torch.cuda.Stream()
     t = tab.Tableau(c.n, stream=stream)
-    eng = {"auto": tab.ENGINE_AUTO, "grid": tab.ENGINE_GRID, "single": tab.ENGINE_SINGLE_CTA}
+    eng = {"auto": tab.ENGINE_AUTO, "single": tab.ENGINE_SINGLE_CTA, "cluster": tab.ENGINE_CLUSTER,
+           "grid": tab.ENGINE_GRID, "stream": tab.ENGINE_STREAM}
     t.set_engine(eng[args.engine])
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     if parts is not None:
@@ -336,7 +338,8 @@ def run_plain(args, ws, rank, local):
         alg = 0.75 * n * n * c.n_meas
         kname = {"auto": "k_measure_cluster" if 256 < n <= 2400 else
                  ("k_sct_program" if n <= 256 else "k_measure_resident/k_measure"),
-                 "grid": "k_measure_resident", "single": "k_sct_program"}[args.engine]
+                 "grid": "k_measure_resident", "single": "k_sct_program",
+                 "cluster": "k_measure_cluster", "stream": "k_measure"}[args.engine]
         roof = {"kernel": kname, "bound": "hbm", "unit": "GB/s"}
         roof["achieved"] = alg / (kind_ms[dom] / 1000.0) / 1e9
         roof["peak"] = pk.get("hbm_gbs", FALLBACK_HBM_GBS)

@@ -204,6 +204,13 @@ enum tab_engine {
 };
 int tab_set_engine(tab_t h, int engine);
 
+/* The engine a run of Z measurements takes on this handle under its selected
+ * engine and size (TAB_ENGINE_SINGLE_CTA, _CLUSTER, _GRID or _STREAM; never
+ * _AUTO) in *engine, and the CTAs it launches in *ctas.  GRID falls back to
+ * STREAM for a tableau that no cooperative grid holds in shared memory; this
+ * call shows which one runs.  No device work.  TAB_EINVAL on null pointers. */
+int tab_engine_resolved(tab_t h, int* engine, int* ctas);
+
 /* Number of CUDA kernels this handle has launched since creation. */
 int tab_kernel_launches(tab_t h, int64_t *count);
 

@@ -33,7 +33,6 @@ static int batch_cap() {
   return cap;
 }
 
-constexpr int kClMaxSmem = 226 * 1024;  // dynamic; static shared memory comes on top
 
 __device__ __forceinline__ uint32_t cl_smem(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -72,28 +71,31 @@ struct CommCluster {
   __device__ CommCluster() : C((int)cl_nrank()), r((int)cl_rank()) {}
   __device__ int size() const { return C; }
   __device__ int rank() const { return r; }
+  // every CTA of the cluster runs before anyone touches its shared memory
+  __device__ bool start() {
+    cl_sync();
+    return true;
+  }
   __device__ bool sync() {
     cl_sync();
     return true;
   }
-  __device__ void stage_columns(const ResSmem&, int, int, int, const int*, int, int,
-                                const ResArgs&) {}
-  // read the measured columns from their owners' shared memory
-  __device__ void gather_columns(const ResSmem& s, int, int D, const int* q, int W, int Wp,
-                                 const ResArgs&) {
-    for (int e = threadIdx.x; e < D * W; e += blockDim.x) {
-      const int d = e / W, w = e - d * W;
-      const int a = q[d];
-      const size_t off = (size_t)(a / C) * Wp + w;
-      s.TX[e] = cl_ld(cl_map(s.Xs + off, (uint32_t)(a % C)));
-      s.TZ[e] = cl_ld(cl_map(s.Zs + off, (uint32_t)(a % C)));
+  // owners push the measured columns (their current state) into buffer
+  // `buf` of every CTA; the next cluster barrier publishes them
+  __device__ void stage_columns(const ResSmem& s, int buf, const ResBatch& b, int W, int Wp,
+                                int KB) {
+    const int per = b.nown * W;
+    for (int e = threadIdx.x; e < per * C; e += blockDim.x) {
+      const int dst = e / per, rem = e - dst * per;
+      const int j = rem / W, w = rem - j * W;
+      const int d = b.own[j];
+      const size_t off = (size_t)(b.q[d] / C) * Wp + w;
+      const size_t to = ((size_t)buf * KB + d) * W + w;
+      cl_st(cl_map(s.TX + to, (uint32_t)dst), s.Xs[off]);
+      cl_st(cl_map(s.TZ + to, (uint32_t)dst), s.Zs[off]);
     }
   }
-  // nobody may change a column before every CTA has read it
-  __device__ bool after_gather() {
-    cl_sync();
-    return true;
-  }
+  __device__ void gather_columns(const ResSmem&, int, const ResBatch&, int, int) {}
   __device__ void publish_dp(uint32_t* dpv, int buf, int i, int kb, uint32_t v) {
     if ((int)threadIdx.x < C)
       cl_st(cl_map(dpv + ((size_t)buf * kb + i) * C + r, threadIdx.x), v);
@@ -127,33 +129,33 @@ struct CommGrid {
   __device__ explicit CommGrid(const ResArgs& a) : A(a), C((int)gridDim.x), r((int)blockIdx.x) {}
   __device__ int size() const { return C; }
   __device__ int rank() const { return r; }
+  __device__ bool start() {
+    __syncthreads();
+    return true;
+  }
   __device__ bool sync() { return grid_sync(A.bar, A.err); }
-  // owners write the next batch's measured columns (their current state)
-  __device__ void stage_columns(const ResSmem& s, int buf, int, int D, const int* q, int W, int Wp,
-                                const ResArgs&) {
-    const int KB = A.kb;
-    for (int e = threadIdx.x; e < D * W; e += blockDim.x) {
-      const int d = e / W, w = e - d * W;
-      const int a = q[d];
-      if (a % C != r) continue;
-      const size_t off = (size_t)(a / C) * Wp + w;
+  // owners write the measured columns (their current state) to stage[buf]
+  __device__ void stage_columns(const ResSmem& s, int buf, const ResBatch& b, int W, int Wp,
+                                int KB) {
+    for (int e = threadIdx.x; e < b.nown * W; e += blockDim.x) {
+      const int j = e / W, w = e - j * W;
+      const int d = b.own[j];
+      const size_t off = (size_t)(b.q[d] / C) * Wp + w;
       uint32_t* dst = A.stage + (((size_t)buf * KB + d) * 2) * W;
       dst[w] = s.Xs[off];
       dst[W + w] = s.Zs[off];
     }
   }
-  __device__ void gather_columns(const ResSmem& s, int buf, int D, const int*, int W, int,
-                                 const ResArgs&) {
-    const int KB = A.kb;
-    for (int e = threadIdx.x; e < D * W; e += blockDim.x) {
+  // every CTA copies stage[buf] into its own buffer `buf`
+  __device__ void gather_columns(const ResSmem& s, int buf, const ResBatch& b, int W, int KB) {
+    for (int e = threadIdx.x; e < b.D * W; e += blockDim.x) {
       const int d = e / W, w = e - d * W;
       const uint32_t* src = A.stage + (((size_t)buf * KB + d) * 2) * W;
-      s.TX[e] = __ldcg(src + w);
-      s.TZ[e] = __ldcg(src + W + w);
+      const size_t to = ((size_t)buf * KB + d) * W + w;
+      s.TX[to] = __ldcg(src + w);
+      s.TZ[to] = __ldcg(src + W + w);
     }
-    __syncthreads();
   }
-  __device__ bool after_gather() { return true; }
   __device__ void publish_dp(uint32_t*, int buf, int i, int kb, uint32_t v) {
     if (threadIdx.x == 0) A.dp[((size_t)buf * kb + i) * C + r] = v;
   }
@@ -185,16 +187,61 @@ struct CommGrid {
   __device__ void finish() {}
 };
 
+template <int WL>
 __global__ void __launch_bounds__(kResThreads) k_measure_cluster(ResArgs A) {
   extern __shared__ __align__(16) uint32_t sm[];
   CommCluster cm;
-  measure_resident(A, cm, sm);
+  measure_resident<WL>(A, cm, sm);
 }
 
+template <int WL>
 __global__ void __launch_bounds__(kResThreads) k_measure_resident(ResArgs A) {
   extern __shared__ __align__(16) uint32_t sm[];
   CommGrid cm(A);
-  measure_resident(A, cm, sm);
+  measure_resident<WL>(A, cm, sm);
+}
+
+// Kernel instance for the register share of W = 2*Wh words.
+static const void* cluster_kernel(int wl) {
+  switch (wl) {
+    case 2: return (const void*)k_measure_cluster<2>;
+    case 4: return (const void*)k_measure_cluster<4>;
+    case 8: return (const void*)k_measure_cluster<8>;
+    default: return nullptr;
+  }
+}
+static const void* resident_kernel(int wl) {
+  switch (wl) {
+    case 2: return (const void*)k_measure_resident<2>;
+    case 4: return (const void*)k_measure_resident<4>;
+    case 8: return (const void*)k_measure_resident<8>;
+    case 16: return (const void*)k_measure_resident<16>;
+    default: return nullptr;
+  }
+}
+
+// Dynamic shared memory every measurement kernel instance can take: the
+// device's opt-in maximum per block less the largest static share.
+static int res_dyn_limit() {
+  static int lim = -1;
+  if (lim < 0) {
+    int dev = 0, optin = 0;
+    size_t stat = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      optin = 0;
+    for (int wl = 2; wl <= 16; wl *= 2) {
+      const void* fns[2] = {cluster_kernel(wl), resident_kernel(wl)};
+      for (const void* fn : fns) {
+        cudaFuncAttributes fa;
+        if (fn != nullptr && cudaFuncGetAttributes(&fa, fn) == cudaSuccess && fa.sharedSizeBytes > stat)
+          stat = fa.sharedSizeBytes;
+      }
+    }
+    cudaGetLastError();
+    lim = optin > (int)stat + 1024 ? (optin - (int)stat) & ~255 : 0;
+  }
+  return lim;
 }
 
 // Cluster size for n qubits (0 if the tableau does not fit one cluster).
@@ -202,10 +249,14 @@ int cluster_size_for(int n, int Wh) {
   static int max_c = -1;
   if (max_c < 0) {
     max_c = 0;
-    if (cudaFuncSetAttribute(k_measure_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-            cudaSuccess &&
-        cudaFuncSetAttribute(k_measure_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kClMaxSmem) == cudaSuccess) {
+    bool ok = true;
+    for (int wl = 2; wl <= 8; wl *= 2)
+      ok = ok &&
+           cudaFuncSetAttribute(cluster_kernel(wl), cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                1) == cudaSuccess &&
+           cudaFuncSetAttribute(cluster_kernel(wl), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                res_dyn_limit()) == cudaSuccess;
+    if (ok) {
       for (int c = 16; c >= 2 && max_c == 0; c /= 2) {
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute at[1];
@@ -215,18 +266,19 @@ int cluster_size_for(int n, int Wh) {
         at[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3((unsigned)c);
         cfg.blockDim = dim3(kResThreads);
-        cfg.dynamicSmemBytes = kClMaxSmem;
+        cfg.dynamicSmemBytes = res_dyn_limit();
         cfg.attrs = at;
         cfg.numAttrs = 1;
         int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, k_measure_cluster, &cfg) == cudaSuccess &&
+        if (cudaOccupancyMaxActiveClusters(&nclusters, cluster_kernel(8), &cfg) == cudaSuccess &&
             nclusters > 0)
           max_c = c;
       }
     }
     cudaGetLastError();  // a failed probe must not leave an error behind
   }
-  if (max_c == 0 || 2 * Wh > kResThreads) return 0;
+  const int wl = res_words_per_lane(Wh);
+  if (max_c == 0 || wl == 0 || cluster_kernel(wl) == nullptr) return 0;
   // Preferred size: TAB_CLUSTER_SIZE (2..16, a power of two) if set, else the
   // largest supported.  A smaller cluster has a cheaper barrier and more work
   // per CTA; the smallest size at least the preferred one that fits is used.
@@ -239,7 +291,7 @@ int cluster_size_for(int n, int Wh) {
     }
   }
   for (int c = pref; c <= max_c; c *= 2)
-    if (res_batch_for(n, Wh, c, kClMaxSmem) >= 4) return c;
+    if (res_batch_for(n, Wh, c, res_dyn_limit()) >= 4) return c;
   return 0;
 }
 
@@ -268,8 +320,11 @@ cudaError_t launch_measure_cluster(uint32_t* X, uint32_t* Z, uint32_t* R, int n,
                                    uint64_t cid, uint32_t shot, uint8_t* out, int* err, int C,
                                    cudaStream_t s) {
   if (nm <= 0) return cudaSuccess;
+  const void* fn = cluster_kernel(res_words_per_lane(Wh));
+  if (fn == nullptr) return cudaErrorInvalidValue;
   ResArgs A = res_args(X, Z, R, n, Wh, mops, nm, k0, seed, cid, shot, out, err);
-  A.kb = res_batch_for(n, Wh, C, kClMaxSmem, batch_cap());
+  A.kb = res_batch_for(n, Wh, C, res_dyn_limit(), batch_cap());
+  if (A.kb == 0) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -282,25 +337,32 @@ cudaError_t launch_measure_cluster(uint32_t* X, uint32_t* Z, uint32_t* R, int n,
   cfg.stream = s;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_measure_cluster, A);
+  void* args[] = {&A};
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 // CTAs for the grid-resident engine (0 if the tableau does not fit): the
-// smallest count whose share fits, so that the barrier stays cheap, but at
-// least enough CTAs to keep per-CTA work short.
+// smallest count (from 16, in steps of 8) whose share fits, or, with
+// TAB_GRID_CTAS set, that many if the share fits (tuning sweeps).
 int resident_ctas_for(int n, int Wh, int sm_count) {
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_measure_resident, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kClMaxSmem) != cudaSuccess) {
-      cudaGetLastError();
-      return 0;
-    }
-    attr = true;
+  static int pref = -1;
+  if (pref < 0) {
+    pref = 0;
+    if (const char* e = getenv("TAB_GRID_CTAS")) pref = atoi(e);
   }
-  if (2 * Wh > kResThreads) return 0;
+  static int attr = -1;
+  if (attr < 0) {
+    attr = 1;
+    for (int wl = 2; wl <= 16; wl *= 2)
+      if (cudaFuncSetAttribute(resident_kernel(wl), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               res_dyn_limit()) != cudaSuccess)
+        attr = 0;
+    cudaGetLastError();
+  }
+  if (attr == 0 || res_words_per_lane(Wh) == 0) return 0;
+  if (pref >= 2 && pref <= sm_count && res_batch_for(n, Wh, pref, res_dyn_limit()) >= 4) return pref;
   for (int g = 16; g <= sm_count; g += 8)
-    if (res_batch_for(n, Wh, g, kClMaxSmem) >= 4 && (n + g - 1) / g < (1 << 14)) return g;
+    if (res_batch_for(n, Wh, g, res_dyn_limit()) >= 4) return g;
   return 0;
 }
 
@@ -317,9 +379,12 @@ cudaError_t launch_measure_resident(uint32_t* X, uint32_t* Z, uint32_t* R, int n
                                     uint64_t cid, uint32_t shot, uint8_t* out, int* err,
                                     uint32_t* work, GridBar* bar, int G, cudaStream_t s) {
   if (nm <= 0) return cudaSuccess;
+  const void* fn = resident_kernel(res_words_per_lane(Wh));
+  if (fn == nullptr) return cudaErrorInvalidValue;
   ResArgs A = res_args(X, Z, R, n, Wh, mops, nm, k0, seed, cid, shot, out, err);
   const int W = 2 * Wh;
-  A.kb = res_batch_for(n, Wh, G, kClMaxSmem, batch_cap());
+  A.kb = res_batch_for(n, Wh, G, res_dyn_limit(), batch_cap());
+  if (A.kb == 0) return cudaErrorInvalidValue;
   A.stage = work;
   A.dp = A.stage + 4 * (size_t)A.kb * W;
   A.ph = A.dp + 2 * (size_t)A.kb * G;
@@ -328,8 +393,8 @@ cudaError_t launch_measure_resident(uint32_t* X, uint32_t* Z, uint32_t* R, int n
   cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBar), s);
   if (e != cudaSuccess) return e;
   void* args[] = {&A};
-  return cudaLaunchCooperativeKernel((const void*)k_measure_resident, dim3((unsigned)G),
-                                     dim3(kResThreads), args, res_layout(n, Wh, G, A.kb).words * 4, s);
+  return cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(kResThreads), args,
+                                     res_layout(n, Wh, G, A.kb).words * 4, s);
 }
 
 }  // namespace tab

@@ -192,6 +192,29 @@ bool use_single_cta(tab_t h) {
   return h->n <= 256;
 }
 
+// Engine that runs a run of measurements on this handle (single-CTA runs the
+// whole program), and its CTA count: cluster-resident > grid-resident >
+// streaming, as the selected engine allows.
+int measure_engine(tab_t h, int* ctas) {
+  if (use_single_cta(h)) {
+    *ctas = 1;
+    return TAB_ENGINE_SINGLE_CTA;
+  }
+  const bool any = h->engine == TAB_ENGINE_AUTO;
+  const int C = (any || h->engine == TAB_ENGINE_CLUSTER) ? cluster_size_for(h->n, h->Wh) : 0;
+  if (C > 0) {
+    *ctas = C;
+    return TAB_ENGINE_CLUSTER;
+  }
+  const int G = (any || h->engine == TAB_ENGINE_GRID) ? h->res_ctas : 0;
+  if (G > 0) {
+    *ctas = G;
+    return TAB_ENGINE_GRID;
+  }
+  *ctas = h->meas_ctas;
+  return TAB_ENGINE_STREAM;
+}
+
 // Enqueue the program.  Measurement segments use `seed`.
 int run_program(tab_t h, const HostProgram& hp, const DevProg& dp, uint64_t seed) {
   if (hp.n_meas) {
@@ -233,18 +256,16 @@ int run_program(tab_t h, const HostProgram& hp, const DevProg& dp, uint64_t seed
       h->launches++;
     } else {
       const int nm = (int)(s.op_end - s.op_begin);
-      // cluster-resident > grid-resident > streaming, as the engine allows
-      const bool any = h->engine == TAB_ENGINE_AUTO || h->engine == TAB_ENGINE_SINGLE_CTA;
-      const int C = (any || h->engine == TAB_ENGINE_CLUSTER) ? cluster_size_for(h->n, h->Wh) : 0;
-      const int G = (any || h->engine == TAB_ENGINE_GRID) ? h->res_ctas : 0;
-      if (C > 0)
+      int ctas = 0;
+      const int me = measure_engine(h, &ctas);
+      if (me == TAB_ENGINE_CLUSTER)
         CU(launch_measure_cluster(h->X, h->Z, h->R, h->n, h->Wh, dp.ops + s.op_begin, nm, h->k,
-                                  seed, h->cid, h->shot, h->log + h->log_len, h->mw.err, C,
+                                  seed, h->cid, h->shot, h->log + h->log_len, h->mw.err, ctas,
                                   h->stream));
-      else if (G > 0)
+      else if (me == TAB_ENGINE_GRID)
         CU(launch_measure_resident(h->X, h->Z, h->R, h->n, h->Wh, dp.ops + s.op_begin, nm, h->k,
                                    seed, h->cid, h->shot, h->log + h->log_len, h->mw.err, h->rw,
-                                   h->rbar, G, h->stream));
+                                   h->rbar, ctas, h->stream));
       else
         CU(launch_measure(h->X, h->Z, h->R, h->n, h->Wh, dp.ops + s.op_begin, nm, h->k, seed,
                           h->cid, h->shot, h->log + h->log_len, h->mw, h->meas_ctas, h->stream));
@@ -690,6 +711,17 @@ int tab_set_engine(tab_t h, int engine) {
     return TAB_ERANGE;
   }
   h->engine = engine;
+  return TAB_OK;
+}
+
+int tab_engine_resolved(tab_t h, int* engine, int* ctas) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!engine || !ctas) {
+    set_error("null argument");
+    return TAB_EINVAL;
+  }
+  *engine = measure_engine(h, ctas);
   return TAB_OK;
 }
 

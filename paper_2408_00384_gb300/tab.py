@@ -69,6 +69,7 @@ _sig("tab_read_outcomes", ctypes.c_int, [_vp, _vp, _i64, _P(_i64)])
 _sig("tab_clear_outcomes", ctypes.c_int, [_vp])
 _sig("tab_kernel_launches", ctypes.c_int, [_vp, _P(_i64)])
 _sig("tab_set_engine", ctypes.c_int, [_vp, ctypes.c_int])
+_sig("tab_engine_resolved", ctypes.c_int, [_vp, _P(ctypes.c_int), _P(ctypes.c_int)])
 _sig("tab_measure_noalloc", ctypes.c_int, [_vp, _vp, _i32, _i32, _vp])
 _sig("tab_export", ctypes.c_int, [_vp, _vp, _vp, _vp])
 _sig("tab_import", ctypes.c_int, [_vp, _vp, _vp, _vp, _u64])
@@ -203,8 +204,14 @@ class Tableau:
         _check(_L.tab_reset(self._h))
 
     def set_engine(self, engine: int):
-        """ENGINE_AUTO, ENGINE_SINGLE_CTA or ENGINE_GRID (bit-identical results)."""
+        """One of the ENGINE_* constants (bit-identical results)."""
         _check(_L.tab_set_engine(self._h, engine))
+
+    def engine_resolved(self):
+        """(engine, ctas) that a run of measurements takes on this handle."""
+        e, c = ctypes.c_int(0), ctypes.c_int(0)
+        _check(_L.tab_engine_resolved(self._h, ctypes.byref(e), ctypes.byref(c)))
+        return e.value, c.value
 
     # -- gates / measurements
     def apply(self, gates):

@@ -87,6 +87,28 @@ def test_larger_tableaus(engine, n):
     assert_same(n, c.gates, seed=5, engine=engine)
 
 
+_E = tab
+@pytest.mark.parametrize("n,engine,want", [
+    (200, _E.ENGINE_AUTO, _E.ENGINE_SINGLE_CTA),
+    (1000, _E.ENGINE_AUTO, _E.ENGINE_CLUSTER),
+    (1000, _E.ENGINE_CLUSTER, _E.ENGINE_CLUSTER),
+    (2400, _E.ENGINE_CLUSTER, _E.ENGINE_CLUSTER),
+    (1000, _E.ENGINE_GRID, _E.ENGINE_GRID),
+    (4100, _E.ENGINE_GRID, _E.ENGINE_GRID),
+    (8000, _E.ENGINE_GRID, _E.ENGINE_STREAM),
+    (10000, _E.ENGINE_AUTO, _E.ENGINE_STREAM),
+    (1000, _E.ENGINE_STREAM, _E.ENGINE_STREAM),
+])
+def test_engine_resolution(n, engine, want):
+    """The engine a measurement run takes: the parity cases of each engine
+    above exercise that engine's kernel, not a fallback."""
+    with tab.Tableau(n) as t:
+        t.set_engine(engine)
+        got, ctas = t.engine_resolved()
+    assert got == want, (n, engine, got)
+    assert ctas >= 1
+
+
 @pytest.mark.parametrize("engine", [tab.ENGINE_AUTO, tab.ENGINE_GRID, tab.ENGINE_STREAM])
 def test_config2_full(engine):
     """n=1000, 1000 random layers, final MZ on all qubits: full compare."""
