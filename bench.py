@@ -336,10 +336,9 @@ def run_plain(args, ws, rank, local):
         # algorithmic bytes per random measurement: rows x supp columns read+written
         # ~ 0.75 n^2 B (n columns in supp(p) ~ 3/4, 2 planes, 2n/8 B, read + write)
         alg = 0.75 * n * n * c.n_meas
-        kname = {"auto": "k_measure_cluster" if 256 < n <= 2400 else
-                 ("k_sct_program" if n <= 256 else "k_measure_resident/k_measure"),
-                 "grid": "k_measure_resident", "single": "k_sct_program",
-                 "cluster": "k_measure_cluster", "stream": "k_measure"}[args.engine]
+        kname = {tab.ENGINE_SINGLE_CTA: "k_sct_program", tab.ENGINE_CLUSTER: "k_measure_cluster",
+                 tab.ENGINE_GRID: "k_measure_resident",
+                 tab.ENGINE_STREAM: "k_measure"}[t.engine_resolved()[0]]
         roof = {"kernel": kname, "bound": "hbm", "unit": "GB/s"}
         roof["achieved"] = alg / (kind_ms[dom] / 1000.0) / 1e9
         roof["peak"] = pk.get("hbm_gbs", FALLBACK_HBM_GBS)
@@ -368,7 +367,10 @@ def run_plain(args, ws, rank, local):
         "config": {"workload": desc, "n": c.n, "gates": c.n_gates,
                    "measurements": c.n_meas, "parallelism": f"replicas x{ws}",
                    "l2": "flushed before every timed step (256 MB device write)",
-                   "engine": args.engine},
+                   "engine": args.engine,
+                   "measure_engine": {tab.ENGINE_SINGLE_CTA: "single-CTA", tab.ENGINE_CLUSTER: "cluster",
+                                      tab.ENGINE_GRID: "grid-resident",
+                                      tab.ENGINE_STREAM: "streaming"}[t.engine_resolved()[0]]},
         "gpu_launches": int(launches),
         "clocks": clk,
         "roofline": roof,

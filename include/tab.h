@@ -191,12 +191,14 @@ int tab_clear_outcomes(tab_t h);
  * gate runs with a fused row-slab kernel spread over the GPU and differ in
  * how a run of measurements executes:
  *   TAB_ENGINE_CLUSTER  tableau in the shared memory of one thread-block
- *                       cluster (n up to about 2,500);
+ *                       cluster of 16 CTAs (n up to about 2,500);
  *   TAB_ENGINE_GRID     tableau in the shared memory of a cooperative grid
- *                       (n up to about 8,000), else streamed from HBM/L2;
+ *                       of one CTA per SM (n up to about 7,900), else
+ *                       streamed from HBM/L2;
  *   TAB_ENGINE_STREAM   always streamed from HBM/L2 by a cooperative grid.
- * TAB_ENGINE_AUTO (default) picks by size.  Results are bit-identical across
- * engines.  TAB_ERANGE if SINGLE_CTA is asked for n > TAB_BATCH_MAX_QUBITS or
+ * TAB_ENGINE_AUTO (default) picks by size: single-CTA for n <= 256, else
+ * grid-resident where it fits, else streaming.  Results are bit-identical
+ * across engines.  TAB_ERANGE if SINGLE_CTA is asked for n > TAB_BATCH_MAX_QUBITS or
  * CLUSTER for a tableau larger than one cluster holds. */
 enum tab_engine {
   TAB_ENGINE_AUTO = 0, TAB_ENGINE_SINGLE_CTA = 1, TAB_ENGINE_GRID = 2, TAB_ENGINE_CLUSTER = 3,

@@ -1,0 +1,181 @@
+// blocks.cpp -- compile a gate run into two-qubit blocks for the block gate
+// kernel.
+//
+// Rows of the tableau are independent under gates (Aaronson & Gottesman,
+// PRA 70, 052328, Sec. III), so one thread can apply a whole sequence of
+// gates on a qubit pair to 32 rows held in registers.  A block is
+//   U_0 (x) U_1, then one entangler (none, CNOT either way, or CZ), then
+//   V_0 (x) V_1, then an optional swap of the two columns on the way out,
+// where U, V are single-qubit Cliffords (clifford1.h: any run of H, S, S^dag,
+// X, Y, Z on one qubit is one 7-bit code).  A SWAP never costs a gate: it
+// swaps which register holds which qubit for the rest of the block.
+//
+// Blocks are assigned to super-layers greedily, in program order:
+//  * a gate on qubits that all sit in the latest block of those qubits is
+//    folded into it (single-qubit gates always; an entangler if the block
+//    has none yet);
+//  * two single-qubit blocks (or one and an untouched qubit) that are the
+//    latest on their qubits merge into one two-qubit block, at the later of
+//    their super-layers -- nothing later depends on them yet;
+//  * otherwise the gate opens a block one super-layer above the latest
+//    blocks of its qubits.
+// So per-qubit gate order is kept, and the blocks of one super-layer act on
+// pairwise-disjoint qubits: a kernel may apply them in parallel.
+#include <algorithm>
+#include <vector>
+
+#include "clifford1.h"
+#include "tab_internal.h"
+
+namespace tab {
+
+void BlockBuilder::reset(int32_t n) {
+  if ((int32_t)cur_.size() < n) {
+    cur_.assign((size_t)n, -1);
+    role_.assign((size_t)n, 0);
+    stamp_.assign((size_t)n, 0u);
+  }
+  ++seg_;
+  blk_.clear();
+}
+
+// One gate (tab_op numbering) of the current run.
+void BlockBuilder::add(uint32_t op, uint32_t a, uint32_t b) {
+  auto latest = [&](uint32_t q) -> int32_t { return stamp_[q] == seg_ ? cur_[q] : -1; };
+  auto bind = [&](uint32_t q, int32_t B, uint8_t role) {
+    stamp_[q] = seg_;
+    cur_[q] = B;
+    role_[q] = role;
+  };
+  auto open = [&](uint32_t qa, uint32_t qb, bool two, int32_t layer) -> int32_t {
+    BlkRec k{};
+    k.qa = qa;
+    k.qb = two ? qb : 0u;
+    k.layer = layer;
+    k.has_b = two;
+    k.U[0] = k.U[1] = k.V[0] = k.V[1] = kC1Ident;
+    blk_.push_back(k);
+    const int32_t B = (int32_t)blk_.size() - 1;
+    bind(qa, B, 0);
+    if (two) bind(qb, B, 1);
+    return B;
+  };
+  const bool two = op == TAB_CNOT || op == TAB_CZ || op == TAB_SWAP;
+  if (!two) {
+    const uint32_t c = c1_of_op(op);
+    int32_t B = latest(a);
+    if (B < 0) B = open(a, 0, false, 0);
+    BlkRec& k = blk_[(size_t)B];
+    const uint8_t r = role_[a];
+    if (k.ent) k.V[r] = c1_compose(c, k.V[r]);
+    else k.U[r] = c1_compose(c, k.U[r]);
+    return;
+  }
+  int32_t Ba = latest(a), Bb = latest(b);
+  int32_t B = -1;
+  if (Ba >= 0 && Ba == Bb) {
+    B = Ba;  // both qubits in one block
+    if (op != TAB_SWAP && blk_[(size_t)B].ent) B = -1;
+  } else {
+    const bool sa = Ba < 0 || !blk_[(size_t)Ba].has_b;
+    const bool sb = Bb < 0 || !blk_[(size_t)Bb].has_b;
+    if (sa && sb) {  // single-qubit blocks (or untouched qubits): merge
+      if (Ba >= 0 && Bb >= 0) {
+        BlkRec& ka = blk_[(size_t)Ba];
+        BlkRec& kb = blk_[(size_t)Bb];
+        ka.qb = b;
+        ka.has_b = 1;
+        ka.U[1] = kb.U[0];
+        ka.layer = std::max(ka.layer, kb.layer);
+        kb.dead = 1;
+        bind(b, Ba, 1);
+        B = Ba;
+      } else if (Ba >= 0) {
+        BlkRec& ka = blk_[(size_t)Ba];
+        ka.qb = b;
+        ka.has_b = 1;
+        bind(b, Ba, 1);
+        B = Ba;
+      } else if (Bb >= 0) {
+        BlkRec& kb = blk_[(size_t)Bb];
+        kb.qb = a;
+        kb.has_b = 1;
+        bind(a, Bb, 1);
+        B = Bb;
+      } else {
+        B = open(a, b, true, 0);
+      }
+    }
+  }
+  if (B < 0) {
+    int32_t L = 0;
+    if (Ba >= 0) L = std::max(L, blk_[(size_t)Ba].layer + 1);
+    if (Bb >= 0) L = std::max(L, blk_[(size_t)Bb].layer + 1);
+    B = open(a, b, true, L);
+  }
+  BlkRec& k = blk_[(size_t)B];
+  const uint8_t ra = role_[a], rb = role_[b];
+  if (op == TAB_SWAP) {  // relabel: the registers stay, the qubits trade places
+    k.swp ^= 1;
+    role_[a] = rb;
+    role_[b] = ra;
+  } else if (op == TAB_CNOT) {
+    k.ent = 1;
+    k.dir = ra;  // 0: control in register 0, target in 1; 1: the reverse
+  } else {
+    k.ent = 2;  // CZ is symmetric
+  }
+}
+
+// Emit the run's blocks, grouped by super-layer (and, inside one, by kind so
+// that neighbouring threads take the same path); super-layers above
+// kMaxLayerOps blocks become consecutive sub-layers.  Appends to P.blk and
+// P.blk_off and sets s.blk_begin / s.blk_end.
+void BlockBuilder::emit(HostProgram& P, Seg& s) {
+  int32_t top = 0;
+  size_t live = 0;
+  for (const BlkRec& k : blk_)
+    if (!k.dead) {
+      top = std::max(top, k.layer + 1);
+      ++live;
+    }
+  const int kKinds = 4;  // 1q; 2q none / CNOT / CZ  (swaps ride along)
+  auto kind = [](const BlkRec& k) { return k.has_b ? 1 + (int)k.ent : 0; };
+  std::vector<uint32_t> cnt((size_t)top * kKinds + 1, 0u);
+  for (const BlkRec& k : blk_)
+    if (!k.dead) cnt[(size_t)k.layer * kKinds + kind(k)]++;
+  std::vector<uint32_t> pos(cnt.size(), 0u);
+  uint32_t acc = 0;
+  for (size_t i = 0; i < cnt.size(); ++i) {
+    pos[i] = acc;
+    acc += cnt[i];
+  }
+  const uint32_t base = (uint32_t)P.blk.size();
+  P.blk.resize(P.blk.size() + live);
+  for (const BlkRec& k : blk_) {
+    if (k.dead) continue;
+    const uint32_t lo = k.qa | (k.qb << 14) | ((uint32_t)k.has_b << 28) |
+                        ((uint32_t)k.ent << 29) | ((uint32_t)k.dir << 31);
+    const uint32_t hi = k.U[0] | (k.U[1] << 7) | (k.V[0] << 14) | (k.V[1] << 21) |
+                        ((uint32_t)k.swp << 28);
+    P.blk[base + pos[(size_t)k.layer * kKinds + kind(k)]++] = make_uint2(lo, hi);
+  }
+  s.blk_begin = (uint32_t)P.blk_off.size();
+  P.blk_off.push_back(base);
+  uint32_t run = base;
+  for (int32_t L = 0; L < top; ++L) {
+    uint32_t sz = 0;
+    for (int t = 0; t < kKinds; ++t) sz += cnt[(size_t)L * kKinds + t];
+    while (sz > (uint32_t)kMaxLayerOps) {
+      run += kMaxLayerOps;
+      sz -= kMaxLayerOps;
+      P.blk_off.push_back(run);
+    }
+    run += sz;
+    P.blk_off.push_back(run);
+  }
+  s.blk_end = (uint32_t)P.blk_off.size() - 1;
+  blk_.clear();
+}
+
+}  // namespace tab

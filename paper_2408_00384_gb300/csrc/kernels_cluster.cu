@@ -19,7 +19,7 @@
 
 namespace tab {
 
-// Measurements per batch: TAB_MEAS_BATCH (1, 2, 4, ..., 32) caps it for
+// Measurements per batch: TAB_MEAS_BATCH (1, 2, 4, 8, 16) caps it for
 // tuning sweeps; the default is the largest that fits.
 static int batch_cap() {
   static int cap = 0;
@@ -67,6 +67,7 @@ __device__ __forceinline__ uint32_t cl_nrank() {
 
 // One thread-block cluster: DSMEM and the hardware cluster barrier.
 struct CommCluster {
+  static constexpr bool kPush = true;
   int C, r;
   __device__ CommCluster() : C((int)cl_nrank()), r((int)cl_rank()) {}
   __device__ int size() const { return C; }
@@ -95,7 +96,11 @@ struct CommCluster {
       cl_st(cl_map(s.TZ + to, (uint32_t)dst), s.Zs[off]);
     }
   }
-  __device__ void gather_columns(const ResSmem&, int, const ResBatch&, int, int) {}
+  // word w of slot d's measured column (plane 0: X, 1: Z), pushed by its owner
+  __device__ uint32_t slot_word(const ResSmem& s, int buf, int d, int w, int plane, int W,
+                                int KB) const {
+    return (plane ? s.TZ : s.TX)[((size_t)buf * KB + d) * W + w];
+  }
   __device__ void publish_dp(uint32_t* dpv, int buf, int i, int kb, uint32_t v) {
     if ((int)threadIdx.x < C)
       cl_st(cl_map(dpv + ((size_t)buf * kb + i) * C + r, threadIdx.x), v);
@@ -124,6 +129,7 @@ struct CommCluster {
 // A cooperative grid: owners stage measured columns in global memory (L2),
 // global deterministic partials, bounded grid barrier.
 struct CommGrid {
+  static constexpr bool kPush = false;
   const ResArgs& A;
   int C, r;
   __device__ explicit CommGrid(const ResArgs& a) : A(a), C((int)gridDim.x), r((int)blockIdx.x) {}
@@ -146,15 +152,10 @@ struct CommGrid {
       dst[W + w] = s.Zs[off];
     }
   }
-  // every CTA copies stage[buf] into its own buffer `buf`
-  __device__ void gather_columns(const ResSmem& s, int buf, const ResBatch& b, int W, int KB) {
-    for (int e = threadIdx.x; e < b.D * W; e += blockDim.x) {
-      const int d = e / W, w = e - d * W;
-      const uint32_t* src = A.stage + (((size_t)buf * KB + d) * 2) * W;
-      const size_t to = ((size_t)buf * KB + d) * W + w;
-      s.TX[to] = __ldcg(src + w);
-      s.TZ[to] = __ldcg(src + W + w);
-    }
+  // word w of slot d's measured column (plane 0: X, 1: Z), staged in L2
+  __device__ uint32_t slot_word(const ResSmem&, int buf, int d, int w, int plane, int W,
+                                int KB) const {
+    return __ldcg(A.stage + (((size_t)buf * KB + d) * 2 + plane) * W + w);
   }
   __device__ void publish_dp(uint32_t*, int buf, int i, int kb, uint32_t v) {
     if (threadIdx.x == 0) A.dp[((size_t)buf * kb + i) * C + r] = v;
@@ -291,7 +292,7 @@ int cluster_size_for(int n, int Wh) {
     }
   }
   for (int c = pref; c <= max_c; c *= 2)
-    if (res_batch_for(n, Wh, c, res_dyn_limit()) >= 4) return c;
+    if (res_batch_for(n, Wh, c, res_dyn_limit(), kBatchMax, true) >= 4) return c;
   return 0;
 }
 
@@ -323,7 +324,7 @@ cudaError_t launch_measure_cluster(uint32_t* X, uint32_t* Z, uint32_t* R, int n,
   const void* fn = cluster_kernel(res_words_per_lane(Wh));
   if (fn == nullptr) return cudaErrorInvalidValue;
   ResArgs A = res_args(X, Z, R, n, Wh, mops, nm, k0, seed, cid, shot, out, err);
-  A.kb = res_batch_for(n, Wh, C, res_dyn_limit(), batch_cap());
+  A.kb = res_batch_for(n, Wh, C, res_dyn_limit(), batch_cap(), true);
   if (A.kb == 0) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
@@ -333,7 +334,7 @@ cudaError_t launch_measure_cluster(uint32_t* X, uint32_t* Z, uint32_t* R, int n,
   at[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3((unsigned)C);
   cfg.blockDim = dim3(kResThreads);
-  cfg.dynamicSmemBytes = res_layout(n, Wh, C, A.kb).words * 4;
+  cfg.dynamicSmemBytes = res_layout(n, Wh, C, A.kb, true).words * 4;
   cfg.stream = s;
   cfg.attrs = at;
   cfg.numAttrs = 1;
@@ -341,9 +342,10 @@ cudaError_t launch_measure_cluster(uint32_t* X, uint32_t* Z, uint32_t* R, int n,
   return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
-// CTAs for the grid-resident engine (0 if the tableau does not fit): the
-// smallest count (from 16, in steps of 8) whose share fits, or, with
-// TAB_GRID_CTAS set, that many if the share fits (tuning sweeps).
+// CTAs for the grid-resident engine (0 if the tableau does not fit): one
+// per SM -- phase 2 of a batch is spread over more columns-owning warps the
+// more CTAs there are, and the per-batch barrier costs about the same -- or
+// TAB_GRID_CTAS if set and the share fits (tuning sweeps).
 int resident_ctas_for(int n, int Wh, int sm_count) {
   static int pref = -1;
   if (pref < 0) {
@@ -360,10 +362,10 @@ int resident_ctas_for(int n, int Wh, int sm_count) {
     cudaGetLastError();
   }
   if (attr == 0 || res_words_per_lane(Wh) == 0) return 0;
-  if (pref >= 2 && pref <= sm_count && res_batch_for(n, Wh, pref, res_dyn_limit()) >= 4) return pref;
-  for (int g = 16; g <= sm_count; g += 8)
-    if (res_batch_for(n, Wh, g, res_dyn_limit()) >= 4) return g;
-  return 0;
+  if (pref >= 2 && pref <= sm_count &&
+      res_batch_for(n, Wh, pref, res_dyn_limit(), kBatchMax, false) >= 4)
+    return pref;
+  return res_batch_for(n, Wh, sm_count, res_dyn_limit(), kBatchMax, false) >= 4 ? sm_count : 0;
 }
 
 size_t resident_work_words(int n, int max_ctas) {
@@ -383,7 +385,7 @@ cudaError_t launch_measure_resident(uint32_t* X, uint32_t* Z, uint32_t* R, int n
   if (fn == nullptr) return cudaErrorInvalidValue;
   ResArgs A = res_args(X, Z, R, n, Wh, mops, nm, k0, seed, cid, shot, out, err);
   const int W = 2 * Wh;
-  A.kb = res_batch_for(n, Wh, G, res_dyn_limit(), batch_cap());
+  A.kb = res_batch_for(n, Wh, G, res_dyn_limit(), batch_cap(), false);
   if (A.kb == 0) return cudaErrorInvalidValue;
   A.stage = work;
   A.dp = A.stage + 4 * (size_t)A.kb * W;
@@ -394,7 +396,7 @@ cudaError_t launch_measure_resident(uint32_t* X, uint32_t* Z, uint32_t* R, int n
   if (e != cudaSuccess) return e;
   void* args[] = {&A};
   return cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(kResThreads), args,
-                                     res_layout(n, Wh, G, A.kb).words * 4, s);
+                                     res_layout(n, Wh, G, A.kb, false).words * 4, s);
 }
 
 }  // namespace tab

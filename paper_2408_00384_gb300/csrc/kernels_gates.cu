@@ -20,6 +20,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 
+#include "clifford1.h"
 #include "gate_rules.cuh"
 #include "tab_internal.h"
 
@@ -369,6 +370,144 @@ __global__ void __launch_bounds__(T) k_gates_flow(uint32_t* __restrict__ X, uint
   if (tid == 0) R[w] ^= s_r;
 }
 
+// ------------------------------------------------ block row-slab gates ----
+// Same slab layout as k_gates_slab; the gate run is compiled into two-qubit
+// blocks (blocks.cpp) grouped in super-layers of pairwise-disjoint blocks,
+// with one CTA barrier per super-layer instead of one per ASAP layer.  A
+// thread applies a whole block to the slab's 32 rows in registers -- U_0 (x)
+// U_1, the entangler, V_0 (x) V_1 -- without branching on the gates, and
+// stores the two columns back (exchanged if the block swaps them).  The
+// records (8 bytes) stream through the same kind of TMA ring as the codes.
+constexpr int kBlkChunk = 512;                  // records per TMA copy (4 KB)
+constexpr int kBlkSlots = 16;                   // 64 KB ring
+constexpr int kBlkRing = kBlkChunk * kBlkSlots;
+
+__device__ __forceinline__ void apply_block(uint2 rec, uint32_t* sx, uint32_t* sz, uint32_t& r) {
+  const uint32_t qa = rec.x & 0x3FFFu, qb = (rec.x >> 14) & 0x3FFFu;
+  const bool two = (rec.x >> 28) & 1u;
+  const uint32_t ent = (rec.x >> 29) & 3u, dir = rec.x >> 31;
+  const uint32_t m = rec.y;
+  uint32_t x0 = sx[qa], z0 = sz[qa];
+  c1_apply(m & 0x7Fu, x0, z0, r);
+  if (!two) {
+    sx[qa] = x0;
+    sz[qa] = z0;
+    return;
+  }
+  uint32_t x1 = sx[qb], z1 = sz[qb];
+  c1_apply((m >> 7) & 0x7Fu, x1, z1, r);
+  if (ent == 1u) {  // CNOT, control in register `dir`
+    const uint32_t xc = dir ? x1 : x0, zc = dir ? z1 : z0;
+    const uint32_t xt = dir ? x0 : x1, zt = dir ? z0 : z1;
+    r ^= xc & zt & ~(xt ^ zc);
+    const uint32_t xt2 = xt ^ xc, zc2 = zc ^ zt;
+    x0 = dir ? xt2 : xc;
+    z0 = dir ? zt : zc2;
+    x1 = dir ? xc : xt2;
+    z1 = dir ? zc2 : zt;
+  } else if (ent == 2u) {  // CZ
+    r ^= x0 & x1 & (z0 ^ z1);
+    const uint32_t z0n = z0 ^ x1;
+    z1 ^= x0;
+    z0 = z0n;
+  }
+  c1_apply((m >> 14) & 0x7Fu, x0, z0, r);
+  c1_apply((m >> 21) & 0x7Fu, x1, z1, r);
+  const bool sw = (m >> 28) & 1u;
+  const uint32_t da = sw ? qb : qa, db = sw ? qa : qb;
+  sx[da] = x0;
+  sz[da] = z0;
+  sx[db] = x1;
+  sz[db] = z1;
+}
+
+template <int T>
+__global__ void __launch_bounds__(T) k_gates_block(uint32_t* __restrict__ X, uint32_t* __restrict__ Z,
+                                                   uint32_t* __restrict__ R, int n, int W,
+                                                   const uint2* __restrict__ blk,
+                                                   const uint32_t* __restrict__ blk_off,
+                                                   int nlayers, int* __restrict__ err) {
+  extern __shared__ __align__(128) uint32_t sm[];
+  uint2* ring = reinterpret_cast<uint2*>(sm);  // block-record ring (kBlkRing records)
+  uint32_t* sx = sm + 2 * kBlkRing;            // X-plane word of every column (this slab)
+  uint32_t* sz = sx + n;                       // Z-plane word of every column
+  __shared__ __align__(8) uint64_t bars[kBlkSlots];
+  __shared__ uint32_t s_r;
+  __shared__ int s_abort;
+  const int w = blockIdx.x, tid = threadIdx.x;
+  const uint32_t ob = __ldg(blk_off), oe = __ldg(blk_off + nlayers);
+  const uint32_t base = ob & ~1u;  // 16-byte aligned start of the stream
+  const int nchunks = (int)((oe - base + kBlkChunk - 1) / kBlkChunk);
+  int issued = 0, waited = 0;      // thread 0's pipeline state
+  if (tid == 0) {
+    for (int i = 0; i < kBlkSlots; ++i) mbar_init(&bars[i], 1);
+    mbar_fence_init();
+    s_r = 0u;
+    s_abort = 0;
+    for (; issued < nchunks && issued < kBlkSlots; ++issued)
+      tma_bulk_g2s(ring + (size_t)issued * kBlkChunk, blk + base + (size_t)issued * kBlkChunk,
+                   kBlkChunk * 8, &bars[issued]);
+  }
+  for (int a = tid; a < n; a += T) {
+    sx[a] = X[(size_t)a * W + w];
+    sz[a] = Z[(size_t)a * W + w];
+  }
+  __syncthreads();
+
+  uint32_t racc = 0u;
+  uint32_t prev_lb = ob, lb = ob;
+  for (int L = 0; L < nlayers; ++L) {
+    const uint32_t le = __ldg(blk_off + L + 1);
+    if (tid == 0) {
+      // refill slots whose chunk ended before the previous super-layer began
+      while (issued < nchunks &&
+             (int64_t)base + (int64_t)(issued - kBlkSlots + 1) * kBlkChunk <= (int64_t)prev_lb) {
+        const int slot = issued % kBlkSlots;
+        fence_proxy_async_smem();
+        tma_bulk_g2s(ring + (size_t)slot * kBlkChunk, blk + base + (size_t)issued * kBlkChunk,
+                     kBlkChunk * 8, &bars[slot]);
+        ++issued;
+      }
+      if (le > lb) {
+        const int c_last = (int)((le - 1 - base) / kBlkChunk);
+        if (c_last >= issued) {
+          atomicCAS(err, 0, DERR_BOUNDS);
+          s_abort = 1;
+        } else {
+          for (; waited <= c_last; ++waited)
+            if (!mbar_wait_bounded(&bars[waited % kBlkSlots], (uint32_t)(waited / kBlkSlots) & 1u)) {
+              atomicCAS(err, 0, DERR_TIMEOUT);
+              s_abort = 1;
+              break;
+            }
+        }
+      }
+    }
+    __syncthreads();
+    if (s_abort) break;
+    for (uint32_t g = lb + tid; g < le; g += T)
+      apply_block(ring[(g - base) & (kBlkRing - 1)], sx, sz, racc);
+    prev_lb = lb;
+    lb = le;
+  }
+  // every copy issued must land before the CTA exits
+  if (tid == 0)
+    for (; waited < issued; ++waited)
+      mbar_wait_bounded(&bars[waited % kBlkSlots], (uint32_t)(waited / kBlkSlots) & 1u);
+  __syncthreads();
+  if (s_abort) return;
+
+  for (int a = tid; a < n; a += T) {
+    X[(size_t)a * W + w] = sx[a];
+    Z[(size_t)a * W + w] = sz[a];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) racc ^= __shfl_xor_sync(0xffffffffu, racc, o);
+  if ((tid & 31) == 0 && racc) atomicXor(&s_r, racc);
+  __syncthreads();
+  if (tid == 0) R[w] ^= s_r;
+}
+
 constexpr int kMaxSmemBytes = 227 * 1024;
 
 int gates_max_n() { return (kMaxSmemBytes - 4096 - kGateRing * 4) / 8; }
@@ -420,6 +559,26 @@ cudaError_t launch_gates_flow(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int 
     attr_set = true;
   }
   k_gates_flow<T><<<W, T, smem, s>>>(X, Z, R, n, W, rec, rb, re, err);
+  return cudaGetLastError();
+}
+
+int gates_block_max_n() { return (kMaxSmemBytes - 4096 - kBlkRing * 8) / 8; }
+
+cudaError_t launch_gates_block(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
+                               const uint2* blk, const uint32_t* blk_off, int nlayers, int* err,
+                               cudaStream_t s) {
+  if (nlayers <= 0) return cudaSuccess;
+  constexpr int T = 512;
+  const size_t smem = (size_t)kBlkRing * 8 + (size_t)n * 2 * sizeof(uint32_t);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_gates_block<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kMaxSmemBytes - 4096);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_gates_block<T><<<W, T, smem, s>>>(X, Z, R, n, W, blk, blk_off, nlayers, err);
   return cudaGetLastError();
 }
 

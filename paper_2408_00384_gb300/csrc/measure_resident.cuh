@@ -13,29 +13,42 @@
 //                           + 2 sum_{m<l in T} z_m . x_l  (mod 4), outcome e/2.
 //
 // Ownership.  CTA r of C owns the columns j = r, r+C, r+2C, ... in shared
-// memory; within the CTA, warp v owns the local columns v, v+16, v+32, ...
-// The sign exponent 2 r_h (mod 4) of every row is kept as a sum of shares:
-// one base (CTA 0, warp 0) plus one share per warp, held in that warp's
-// registers (bit-sliced, lane l holds words l, l+32, ...).  Every term of the
-// rowsum exponent is a sum over columns, and "2 r_p" is the sum of the
-// shares of row p, so a warp adds only its own columns' terms and its own
-// share of row p: applying a measurement needs no communication inside the
-// CTA or between CTAs.  The shares are folded once, at the end.
+// memory; within the CTA, warp v owns a contiguous block of them.  The sign
+// exponent 2 r_h (mod 4) of every row is kept as a sum of shares: one base
+// (CTA 0, warp 0) plus one share per warp, held in that warp's registers
+// (bit-sliced, lane l holds words l, l+32, ...).  Every term of the rowsum
+// exponent is a sum over columns, and "2 r_p" is the sum of the shares of
+// row p, so a warp adds only its own columns' terms and its own share of
+// row p: applying a measurement needs no communication inside the CTA or
+// between CTAs.  The shares are folded once, at the end.
+//
+// Per column j of the pivot row, (x_pj, z_pj) is X, Z or Y (or I: nothing to
+// do), and the exponent terms of a row h in S' reduce to (with a mod-4
+// counter lo + 2 hi per row):
+//   X: +1 if x_hj z_hj, -1 if !x_hj z_hj              ; x_hj ^= 1
+//   Z: +1 if x_hj z_hj, -1 if x_hj !z_hj, +2 if x_hj  ; z_hj ^= 1
+//   Y: +1 if x_hj z_hj, -1 if !x_hj !z_hj, +2 if x_hj ; x_hj ^= 1, z_hj ^= 1
+// which is what the three column kernels below add, 32 rows per word.
 //
 // Blocked measurements.  The X|Z bits a measurement leaves behind depend only
 // on X|Z bits (never on signs or outcomes), and the pivot and the mask of rows
 // with x_ha = 1 of measurement m depend only on the measured columns.  So a
-// batch of K consecutive measurements runs in two phases:
-//   phase 1: the measured columns of the batch (pushed by their owners at the
-//            end of the previous batch) are replayed through the K
-//            measurements, one warp per column, one named barrier per
-//            measurement; this gives every measurement's pivot p_m and mask
-//            S_m (the measured column at that time);
-//   phase 2: every warp applies the K rowsums, in order, to its own columns
-//            and its own share -- no barrier at all.
-// One CTA barrier between the phases and one cluster/grid barrier per batch.
-// A deterministic measurement with reset ends its batch (its outcome, needed
-// for the reset, is only known once every share is summed).
+// batch of K consecutive measurements runs in two overlapping phases:
+//   phase 1: the measured columns of the batch (pushed or staged by their
+//            owners at the end of the previous batch) are replayed through
+//            the K measurements, one warp per column, in registers, until the
+//            column's last measurement in the batch; one named barrier per
+//            measurement among the warps still replaying.  The warp whose
+//            column measurement m measures publishes its pivot p_m and mask
+//            S_m (the measured column at that time) with a release store of a
+//            counter;
+//   phase 2: every warp that owns columns applies the K rowsums, in order, to
+//            its columns and its share, each as soon as the counter shows it
+//            published (an acquire load, a bounded wait) -- a warp leaves
+//            phase 1 and starts phase 2 at once, so the two overlap.
+// One CTA barrier and one cluster/grid barrier per batch.  A deterministic
+// measurement with reset ends its batch (its outcome, needed for the reset,
+// is only known once every share is summed).
 //
 // The communication policy decides how batches meet:
 //   CommCluster -- one thread-block cluster: owners push the next batch's
@@ -53,10 +66,11 @@
 
 namespace tab {
 
-constexpr int kResThreads = 512;
-constexpr int kResWarps = kResThreads / 32;
-constexpr int kBatchMax = 32;
-constexpr int kResMaxLocalCols = 32 * kResWarps;  // a warp's columns fit one ballot
+constexpr int kResWarps = 16;
+constexpr int kResThreads = 32 * kResWarps;
+constexpr int kBatchMax = kResWarps;                // phase 1: one measured column per warp
+constexpr int kResMaxLocalCols = 32 * kResWarps;    // a warp's columns fit one ballot
+constexpr int kPubSpinMax = 1 << 22;              // polls (64 ns apart) before a wait gives up
 
 struct ResArgs {
   uint32_t *X, *Z, *R;  // handle layout: W = 2*Wh words per column
@@ -81,26 +95,30 @@ struct ResLayout {
   size_t words;
 };
 
-__host__ __device__ inline ResLayout res_layout(int n, int Wh, int C, int kb) {
+// Shared-memory words per CTA.  `push`: the measured columns of the next
+// batch land in shared memory (cluster, double-buffered), not in global
+// memory (grid).
+__host__ __device__ inline ResLayout res_layout(int n, int Wh, int C, int kb, bool push) {
   ResLayout L;
   const int W = 2 * Wh;
   L.ncl = (n + C - 1) / C;
   L.Wp = W + 1;
-  L.words = 2 * (size_t)L.ncl * L.Wp   // own X, Z columns
-            + 4 * (size_t)W             // CTA sign partial (lo, hi), base signs (lo, hi)
-            + (size_t)kb * W            // mask of each measurement of the batch
-            + 4 * (size_t)kb * W        // measured columns X, Z, double-buffered
-            + 2 * (size_t)kb * C;       // deterministic partials, double-buffered
+  L.words = 2 * (size_t)L.ncl * L.Wp            // own X, Z columns
+            + 4 * (size_t)W                      // CTA sign partial (lo, hi), base signs (lo, hi)
+            + (size_t)kb * W                     // mask of each measurement of the batch
+            + (push ? 4 * (size_t)kb * W : 0)    // measured columns X, Z, double-buffered
+            + 2 * (size_t)kb * C;                // deterministic partials, double-buffered
   return L;
 }
 
 // Largest batch size (power of two <= cap <= kBatchMax) that fits `limit`
 // bytes; 0 if even single measurements do not fit.
-__host__ __device__ inline int res_batch_for(int n, int Wh, int C, size_t limit,
-                                             int cap = kBatchMax) {
+__host__ __device__ inline int res_batch_for(int n, int Wh, int C, size_t limit, int cap,
+                                             bool push) {
   if ((n + C - 1) / C > kResMaxLocalCols) return 0;
+  if (cap > kBatchMax) cap = kBatchMax;
   for (int kb = cap; kb >= 1; kb >>= 1)
-    if (res_layout(n, Wh, C, kb).words * 4 <= limit) return kb;
+    if (res_layout(n, Wh, C, kb, push).words * 4 <= limit) return kb;
   return 0;
 }
 
@@ -129,13 +147,36 @@ __device__ __forceinline__ uint32_t res_prefix_xor_excl(uint32_t v) {
 __device__ __forceinline__ void res_named_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
+// publish / observe a counter in shared memory (release / acquire, CTA scope)
+__device__ __forceinline__ void res_st_release(int* p, int v) {
+  asm volatile("st.release.cta.shared.b32 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(p)),
+               "r"(v)
+               : "memory");
+}
+__device__ __forceinline__ int res_ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.cta.shared.b32 %0, [%1];"
+               : "=r"(v)
+               : "r"((uint32_t)__cvta_generic_to_shared(p))
+               : "memory");
+  return v;
+}
+// v[k] for a warp-uniform k, without dynamic register indexing
+template <int WL>
+__device__ __forceinline__ uint32_t res_pick(const uint32_t (&v)[WL], int k) {
+  uint32_t o = 0u;
+#pragma unroll
+  for (int j = 0; j < WL; ++j) o |= v[j] & (0u - (uint32_t)(j == k));
+  return o;
+}
 
 // Shared-memory pointers of the per-CTA state.
 struct ResSmem {
   uint32_t *Xs, *Zs, *PHlo, *PHhi, *R4lo, *R4hi, *SM, *TX, *TZ, *dpv;
 };
 
-__device__ __forceinline__ ResSmem res_smem(uint32_t* sm, const ResLayout& Ly, int W, int kb) {
+__device__ __forceinline__ ResSmem res_smem(uint32_t* sm, const ResLayout& Ly, int W, int kb,
+                                            bool push) {
   ResSmem s;
   s.Xs = sm;
   s.Zs = s.Xs + (size_t)Ly.ncl * Ly.Wp;
@@ -143,10 +184,10 @@ __device__ __forceinline__ ResSmem res_smem(uint32_t* sm, const ResLayout& Ly, i
   s.PHhi = s.PHlo + W;
   s.R4lo = s.PHhi + W;
   s.R4hi = s.R4lo + W;
-  s.SM = s.R4hi + W;                  // [kb][W] mask of each measurement of the batch
-  s.TX = s.SM + (size_t)kb * W;       // [2][kb][W] measured columns, X plane
-  s.TZ = s.TX + 2 * (size_t)kb * W;   // [2][kb][W] Z plane
-  s.dpv = s.TZ + 2 * (size_t)kb * W;  // [2][kb][C]
+  s.SM = s.R4hi + W;             // [kb][W] mask of each measurement of the batch
+  s.TX = s.SM + (size_t)kb * W;  // [2][kb][W] measured columns, X plane (push only)
+  s.TZ = s.TX + (push ? 2 * (size_t)kb * W : 0);
+  s.dpv = s.TZ + (push ? 2 * (size_t)kb * W : 0);  // [2][kb][C]
   return s;
 }
 
@@ -154,49 +195,80 @@ __device__ __forceinline__ ResSmem res_smem(uint32_t* sm, const ResLayout& Ly, i
 struct ResBatch {
   uint32_t code[kBatchMax];  // measurement codes of the batch
   int slot[kBatchMax];       // measured-column slot of each measurement
+  int la[kBatchMax];         // local column of the measured qubit in this CTA, or -1
+  int lw[kBatchMax];         // warp of this CTA owning that column, or -1
   int q[kBatchMax];          // qubit of each slot
+  int last[kBatchMax];       // last measurement of each slot
+  int cnt[kBatchMax];        // slots still live at each measurement (replaying warps)
   int own[kBatchMax];        // slots whose column this CTA owns
   int P[kBatchMax];          // pivot row of each measurement (-1: deterministic)
-  uint32_t rbit[kBatchMax];  // Philox outcome bit of each measurement
   uint32_t dacc[kBatchMax];  // this CTA's deterministic partial
   int ptype[kBatchMax];      // previous batch: 1 = deterministic
   int det[kBatchMax];        // previous batch: resolved deterministic outcome
-  int D, nown, keff;
+  int D, nown, anydet;
+  volatile int keff;         // measurements of the batch (a deterministic reset ends it)
+  int npub;                  // measurements whose pivot and mask are published
   uint32_t plast;            // code of the previous batch's last measurement
 };
 
-// Distinct measured qubits of the batch starting at m (first occurrence
-// order) and the slots this CTA owns.  Thread 0 only.
-__device__ __forceinline__ void res_batch_slots(const uint32_t* mops, int m, int K, int C, int r,
+// Slots of a batch of K <= 32 measurements, lane i holding code i: distinct
+// measured qubits in first-occurrence order, each slot's last measurement,
+// the slots live at each measurement, and the slots, columns and warps this
+// CTA owns.  Warp-wide (one warp).
+__device__ __forceinline__ void res_batch_slots(uint32_t code, int K, int C, int r, int cpw,
                                                 ResBatch& b) {
-  int D = 0;
-  for (int i = 0; i < K; ++i) {
-    b.code[i] = __ldg(mops + m + i);
-    const int a = (int)dq1(b.code[i]);
-    int d = 0;
-    while (d < D && b.q[d] != a) ++d;
-    if (d == D) b.q[D++] = a;
-    b.slot[i] = d;
+  const int lane = threadIdx.x & 31;
+  const bool v = lane < K;
+  const int a = v ? (int)dq1(code) : -1 - lane;
+  const uint32_t grp = __match_any_sync(0xffffffffu, a);
+  const int first = __ffs(grp) - 1;
+  const bool lead = v && first == lane;
+  const uint32_t firsts = __ballot_sync(0xffffffffu, lead);
+  const int slot = __popc(firsts & ((1u << first) - 1u));
+  const bool mine = lead && (a % C == r);
+  const uint32_t owned = __ballot_sync(0xffffffffu, mine);
+  const int lastv = lead ? 31 - __clz(grp) : -1;
+  if (v) {
+    const int la = (a % C == r) ? a / C : -1;
+    b.code[lane] = code;
+    b.slot[lane] = slot;
+    b.la[lane] = la;
+    b.lw[lane] = (la >= 0 && cpw > 0) ? la / cpw : -1;
   }
-  int no = 0;
-  for (int d = 0; d < D; ++d)
-    if (b.q[d] % C == r) b.own[no++] = d;
-  b.D = D;
-  b.nown = no;
+  if (lead) {
+    b.q[slot] = a;
+    b.last[slot] = lastv;
+  }
+  __syncwarp();
+  if (v) {  // slots whose last measurement is at or after this one
+    const int D = __popc(firsts);
+    int cnt = 0;
+    for (int d = 0; d < D; ++d) cnt += b.last[d] >= lane;
+    b.cnt[lane] = cnt;
+  }
+  if (mine) b.own[__popc(owned & ((1u << lane) - 1u))] = slot;
+  if (lane == 0) {
+    b.D = __popc(firsts);
+    b.nown = __popc(owned);
+  }
 }
 
 template <int WL, class Comm>
 __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
   constexpr int NW = kResWarps;
+  constexpr bool kPush = Comm::kPush;
   const int C = cm.size(), r = cm.rank(), tid = threadIdx.x, T = blockDim.x;
   const int n = A.n, Wh = A.Wh, W = 2 * Wh, KB = A.kb;
-  const ResLayout Ly = res_layout(n, Wh, C, KB);
+  const ResLayout Ly = res_layout(n, Wh, C, KB, kPush);
   const int Wp = Ly.Wp;
   const int nown = (n - r + C - 1) / C;  // columns owned: r, r+C, ...
-  const ResSmem s = res_smem(sm, Ly, W, KB);
+  const ResSmem s = res_smem(sm, Ly, W, KB, kPush);
   const int lane = tid & 31, warp = tid >> 5;
-  const int ncw = warp < nown ? (nown - warp + NW - 1) / NW : 0;  // this warp's columns
+  const int cpw = (nown + NW - 1) / NW;  // this warp's local columns: c0 .. c0+ncw-1
+  const int c0 = warp * cpw;
+  const int ncw = nown - c0 < 0 ? 0 : (nown - c0 < cpw ? nown - c0 : cpw);
   const bool base_warp = (r == 0 && warp == 0);
+  const uint32_t lt = (1u << lane) - 1u;
   __shared__ ResBatch b;
 
   // this warp's share of every row's sign exponent (lo, hi bit planes)
@@ -204,7 +276,7 @@ __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
 #pragma unroll
   for (int k = 0; k < WL; ++k) plo[k] = phi[k] = 0u;
 
-  // ---- load own columns, base signs
+  // ---- load own columns, base signs, first batch
   for (int i = tid; i < nown * W; i += T) {
     const int lj = i / W, w = i - lj * W;
     const size_t g = (size_t)(r + lj * C) * W + w;
@@ -215,9 +287,11 @@ __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
     s.R4lo[w] = 0u;
     s.R4hi[w] = (r == 0) ? A.R[w] : 0u;
   }
-  if (tid == 0) {  // slots of the first batch
+  if (warp == 0) {
     const int K0 = A.nm < KB ? A.nm : KB;
-    res_batch_slots(A.mops, 0, K0, C, r, b);
+    const uint32_t c = lane < K0 ? __ldg(A.mops + lane) : 0u;
+    res_batch_slots(c, K0, C, r, cpw, b);
+    if (lane == 0) b.anydet = 0;
   }
   if (!cm.start()) return;
   cm.stage_columns(s, 0, b, W, Wp, KB);  // first batch's measured columns
@@ -226,172 +300,231 @@ __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
   while (m < A.nm) {
     const int par = batch & 1;
     const int K = (A.nm - m < KB) ? A.nm - m : KB;
+    // outcome bits of the batch (lane i: measurement m+i) and the codes of
+    // the batch after it: both known now, their latency hides in the barrier
+    const uint32_t my_rbit =
+        lane < K ? outcome_bit(A.seed, A.cid, A.shot, A.k0 + (uint64_t)(m + lane)) : 0u;
+    uint32_t next_code = 0u;
+    if (warp == 0 && lane < KB && m + K + lane < A.nm) next_code = __ldg(A.mops + m + K + lane);
     // ---- barrier: the previous batch's column updates, staged columns and
     // deterministic partials are visible everywhere
     if (!cm.sync()) return;
     // ---- resolve the previous batch's deterministic outcomes
-    if (tid < prev_count && b.ptype[tid]) {
-      const uint32_t e = cm.sum_dp(s.dpv, par ^ 1, tid, KB) & 3u;
-      if (e & 1u) atomicCAS(A.err, 0, DERR_PHASE);
-      b.det[tid] = (int)(e >> 1);
-      if (r == 0) A.out[prev_base + tid] = (uint8_t)(e >> 1);
-    }
-    cm.gather_columns(s, par, b, W, KB);
-    if (tid < K) b.rbit[tid] = outcome_bit(A.seed, A.cid, A.shot, A.k0 + (uint64_t)(m + tid));
-    if (tid < KB) b.dacc[tid] = 0u;
-    if (tid == 0) b.keff = K;
-    __syncthreads();
-    // a deterministic measure-and-reset ends its batch, so only the last
-    // measurement of the previous batch can need its X_a: every sign ^= z_a,
-    // added to the share of the warp that owns column a
-    if (prev_count > 0 && b.ptype[prev_count - 1] && b.det[prev_count - 1] &&
-        dop(b.plast) == OP_MZR) {
-      const int pa = (int)dq1(b.plast);
-      if (pa % C == r && (pa / C) % NW == warp) {
-        const uint32_t* zc = s.Zs + (size_t)(pa / C) * Wp;
+    if (b.anydet) {
+      if (tid < prev_count && b.ptype[tid]) {
+        const uint32_t e = cm.sum_dp(s.dpv, par ^ 1, tid, KB) & 3u;
+        if (e & 1u) atomicCAS(A.err, 0, DERR_PHASE);
+        b.det[tid] = (int)(e >> 1);
+        if (r == 0) A.out[prev_base + tid] = (uint8_t)(e >> 1);
+      }
+      __syncthreads();
+      // a deterministic measure-and-reset ends its batch, so only the last
+      // measurement of the previous batch can need its X_a: every sign ^= z_a,
+      // added to the share of the warp that owns column a
+      if (b.ptype[prev_count - 1] && b.det[prev_count - 1] && dop(b.plast) == OP_MZR) {
+        const int pa = (int)dq1(b.plast);
+        if (pa % C == r && (pa / C) / cpw == warp) {
+          const uint32_t* zc = s.Zs + (size_t)(pa / C) * Wp;
 #pragma unroll
-        for (int k = 0; k < WL; ++k) {
-          const int w = lane + 32 * k;
-          if (w < W) phi[k] ^= zc[w];
+          for (int k = 0; k < WL; ++k) {
+            const int w = lane + 32 * k;
+            if (w < W) phi[k] ^= zc[w];
+          }
         }
       }
     }
+    if (tid < KB) b.dacc[tid] = 0u;
+    if (tid == 0) {
+      b.keff = K;
+      b.npub = 0;
+    }
+    __syncthreads();
 
-    // ---- phase 1: replay the K measurements on the measured columns only
+    // ---- phase 1: replay the batch on its measured columns, warp d holding
+    // slot d's column in registers until that column's last measurement; the
+    // owner of measurement i publishes its mask S_i and pivot P_i
     const int D = b.D;
-    const int np1 = D < NW ? D : NW;
-    uint32_t* TXp = s.TX + (size_t)par * KB * W;
-    uint32_t* TZp = s.TZ + (size_t)par * KB * W;
-    if (warp < np1) {
-      for (int i = 0; i < K; ++i) {
+    if (warp < D) {
+      uint32_t tx[WL], tz[WL];
+#pragma unroll
+      for (int k = 0; k < WL; ++k) {
+        const int w = lane + 32 * k;
+        tx[k] = w < W ? cm.slot_word(s, par, warp, w, 0, W, KB) : 0u;
+        tz[k] = w < W ? cm.slot_word(s, par, warp, w, 1, W, KB) : 0u;
+      }
+      const int qd = b.q[warp], lastd = b.last[warp];
+      for (int i = 0; i <= lastd; ++i) {
         const uint32_t code = b.code[i];
-        const int a = (int)dq1(code);
-        const int d0 = b.slot[i];
-        uint32_t* Si = s.SM + (size_t)i * W;
-        if (d0 % NW == warp)
-          for (int w = lane; w < W; w += 32) Si[w] = TXp[(size_t)d0 * W + w];
-        res_named_sync(1, 32 * np1);
-        int pw = -1;
-        for (int base = 0; base < Wh && pw < 0; base += 32) {
-          const int hw = base + lane;
-          const uint32_t bal = __ballot_sync(0xffffffffu, hw < Wh && Si[Wh + hw] != 0u);
-          if (bal) pw = Wh + base + __ffs(bal) - 1;
-        }
-        const int P = pw < 0 ? -1 : pw * 32 + __ffs(Si[pw]) - 1;
-        if (warp == 0 && lane == 0) b.P[i] = P;
-        if (P < 0) {  // deterministic: X|Z unchanged; with reset the batch ends
-          if (dop(code) == OP_MZR) {
-            if (warp == 0 && lane == 0) b.keff = i + 1;
-            break;
+        if (b.slot[i] == warp) {
+          uint32_t* Si = s.SM + (size_t)i * W;
+          int P = -1;
+#pragma unroll
+          for (int k = 0; k < WL; ++k) {
+            const int w = lane + 32 * k;
+            if (w < W) Si[w] = tx[k];
+            const uint32_t bal = __ballot_sync(0xffffffffu, w >= Wh && w < W && tx[k] != 0u);
+            if (P < 0 && bal) {
+              const int l = __ffs(bal) - 1;
+              const uint32_t word = __shfl_sync(0xffffffffu, tx[k], l);
+              P = (32 * k + l) * 32 + __ffs(word) - 1;
+            }
           }
+          if (lane == 0) {
+            b.P[i] = P;
+            if (P < 0 && dop(code) == OP_MZR) b.keff = i + 1;  // ends the batch
+          }
+          __syncwarp();
+          if (lane == 0) res_st_release(&b.npub, i + 1);
+        }
+        res_named_sync(1, 32 * b.cnt[i]);
+        const int P = b.P[i];
+        if (P < 0) {  // deterministic: X|Z unchanged; with reset the batch ends
+          if (dop(code) == OP_MZR) break;
           continue;
         }
+        if (i == lastd) break;  // this column is not needed any more
         const int wp = P >> 5, wd = (P - 32 * Wh) >> 5;
         const uint32_t bpm = 1u << (P & 31);
-        for (int d = warp; d < D; d += NW) {
-          uint32_t* tx = TXp + (size_t)d * W;
-          uint32_t* tz = TZp + (size_t)d * W;
-          const uint32_t XP = (tx[wp] & bpm) ? 0xffffffffu : 0u;
-          const uint32_t ZP = (tz[wp] & bpm) ? 0xffffffffu : 0u;
-          const bool is_a = b.q[d] == a;
-          __syncwarp();
-          for (int w = lane; w < W; w += 32) {
+        const uint32_t* Si = s.SM + (size_t)i * W;
+        const uint32_t XP =
+            (__shfl_sync(0xffffffffu, res_pick(tx, wp >> 5), wp & 31) & bpm) ? 0xffffffffu : 0u;
+        const uint32_t ZP =
+            (__shfl_sync(0xffffffffu, res_pick(tz, wp >> 5), wp & 31) & bpm) ? 0xffffffffu : 0u;
+        const uint32_t zpa = (qd == (int)dq1(code)) ? bpm : 0u;
+#pragma unroll
+        for (int k = 0; k < WL; ++k) {
+          const int w = lane + 32 * k;
+          if (w < W) {
             uint32_t Sw = Si[w];
             if (w == wp || w == wd) Sw &= ~bpm;
-            uint32_t x = tx[w] ^ (Sw & XP), z = tz[w] ^ (Sw & ZP);
+            uint32_t x = tx[k] ^ (Sw & XP), z = tz[k] ^ (Sw & ZP);
             if (w == wd) {  // row p-n := row p
               x = (x & ~bpm) | (XP & bpm);
               z = (z & ~bpm) | (ZP & bpm);
             }
             if (w == wp) {  // row p := Z_a
               x &= ~bpm;
-              z = (z & ~bpm) | (is_a ? bpm : 0u);
+              z = (z & ~bpm) | zpa;
             }
-            tx[w] = x;
-            tz[w] = z;
+            tx[k] = x;
+            tz[k] = z;
           }
-          __syncwarp();
         }
       }
     }
-    __syncthreads();
-    const int keff = b.keff;
-    if (r == 0 && tid < keff && b.P[tid] >= 0) A.out[m + tid] = (uint8_t)b.rbit[tid];
 
-    // ---- phase 2: every warp applies the batch to its columns and its share
-    for (int i = 0; i < keff; ++i) {
-      const uint32_t code = b.code[i];
-      const int a = (int)dq1(code);
-      const int P = b.P[i];
-      const uint32_t* S = s.SM + (size_t)i * W;
-      __syncwarp();  // the previous measurement's column writes, across lanes
-      if (P >= 0) {
-        // ============ random outcome ============
-        const uint32_t rbit = b.rbit[i];
-        const int wp = P >> 5, wd = (P - 32 * Wh) >> 5;
-        const uint32_t bpm = 1u << (P & 31);
-        // this warp's share of 2 r_p (and the base, for the base warp)
-        uint32_t pl = 0u, ph = 0u;
+    // ---- phase 2: every warp with columns (and the base warp) applies the
+    // batch to its columns and its share, each measurement as soon as it is
+    // published; a warp without columns keeps a zero share and has no work
+    if (ncw > 0 || base_warp) {
+      int seen = 0;
+      for (int i = 0; i < K; ++i) {
+        if (i >= seen) {  // wait for measurement i (bounded)
+          for (int it = 0;; ++it) {
+            seen = __shfl_sync(0xffffffffu, lane == 0 ? res_ld_acquire(&b.npub) : 0, 0);
+            if (seen > i || it > kPubSpinMax) break;
+            __nanosleep(64);
+          }
+          if (seen <= i) {
+            if (lane == 0) atomicCAS(A.err, 0, DERR_TIMEOUT);
+            break;
+          }
+        }
+        const uint32_t code = b.code[i];
+        const int P = b.P[i];
+        const uint32_t* S = s.SM + (size_t)i * W;
+        const uint32_t rbit = __shfl_sync(0xffffffffu, my_rbit, i);
+        __syncwarp();  // the previous measurement's column writes, across lanes
+        if (P >= 0) {
+          // ============ random outcome ============
+          const int wp = P >> 5, wd = (P - 32 * Wh) >> 5;
+          const uint32_t bpm = 1u << (P & 31);
+          const int la = b.la[i];  // local column of qubit a (or -1)
+          // this warp's share of 2 r_p (and the base, for the base warp)
+          const uint32_t pl = __shfl_sync(0xffffffffu, res_pick(plo, wp >> 5), wp & 31);
+          const uint32_t ph = __shfl_sync(0xffffffffu, res_pick(phi, wp >> 5), wp & 31);
+          const uint32_t php = ((pl & bpm) ? 1u : 0u) | ((ph & bpm) ? 2u : 0u);
+          uint32_t r4p = 0u;
+          if (base_warp) r4p = ((s.R4lo[wp] & bpm) ? 1u : 0u) | ((s.R4hi[wp] & bpm) ? 2u : 0u);
+          // pivot row over this warp's columns (lane c: local column c0 + c)
+          bool xb = false, zb = false;
+          if (lane < ncw) {
+            const size_t ii = (size_t)(c0 + lane) * Wp + wp;
+            xb = (s.Xs[ii] & bpm) != 0u;
+            zb = (s.Zs[ii] & bpm) != 0u;
+          }
+          const uint32_t supx = __ballot_sync(0xffffffffu, xb);
+          const uint32_t supz = __ballot_sync(0xffffffffu, zb);
+          const uint32_t scal = ((uint32_t)__popc(supx & supz) + php + r4p) & 3u;
+          // S': rows with x_ha = 1 other than p and p-n
+          uint32_t Sw[WL];
 #pragma unroll
-        for (int k = 0; k < WL; ++k) {  // mask select: keeps the shares in registers
-          const uint32_t sel = 0u - (uint32_t)(k == (wp >> 5));
-          pl |= plo[k] & sel;
-          ph |= phi[k] & sel;
-        }
-        pl = __shfl_sync(0xffffffffu, pl, wp & 31);
-        ph = __shfl_sync(0xffffffffu, ph, wp & 31);
-        const uint32_t php = ((pl & bpm) ? 1u : 0u) | ((ph & bpm) ? 2u : 0u);
-        uint32_t r4p = 0u;
-        if (base_warp) r4p = ((s.R4lo[wp] & bpm) ? 1u : 0u) | ((s.R4hi[wp] & bpm) ? 2u : 0u);
-        // pivot row over this warp's columns (lane c: column warp + 16 c)
-        bool xb = false, zb = false;
-        if (lane < ncw) {
-          const size_t ii = (size_t)(warp + lane * NW) * Wp + wp;
-          xb = (s.Xs[ii] & bpm) != 0u;
-          zb = (s.Zs[ii] & bpm) != 0u;
-        }
-        const uint32_t supx = __ballot_sync(0xffffffffu, xb);
-        const uint32_t supz = __ballot_sync(0xffffffffu, zb);
-        if (lane < ncw && !xb && !zb) {  // row p is I here: row p-n := row p clears it
-          const size_t ii = (size_t)(warp + lane * NW) * Wp + wd;
-          s.Xs[ii] &= ~bpm;
-          s.Zs[ii] &= ~bpm;
-        }
-        __syncwarp();
-        const int la = (a % C == r) ? a / C : -1;  // local column of qubit a
-        const uint32_t scal = ((uint32_t)__popc(supx & supz) + php + r4p) & 3u;
-        const uint32_t sup = supx | supz;
+          for (int k = 0; k < WL; ++k) {
+            const int w = lane + 32 * k;
+            Sw[k] = w < W ? S[w] : 0u;
+            if (w == wp || w == wd) Sw[k] &= ~bpm;
+          }
+          // the rowsum on every column where row p is X, Z or Y
+          for (uint32_t left = supx | supz; left; left &= left - 1u) {
+            const int c = __ffs(left) - 1;
+            const bool cx = (supx >> c) & 1u, cz = (supz >> c) & 1u;
+            uint32_t* xc = s.Xs + (size_t)(c0 + c) * Wp;
+            uint32_t* zc = s.Zs + (size_t)(c0 + c) * Wp;
+            if (cx && !cz) {  // X
 #pragma unroll
-        for (int k = 0; k < WL; ++k) {
-          const int w = lane + 32 * k;
-          if (w < W) {
-            uint32_t Sw = S[w];
-            if (w == wp || w == wd) Sw &= ~bpm;  // S' excludes rows p and p-n
-            uint32_t lo = plo[k], hi = phi[k];
-            for (uint32_t left = sup; left; left &= left - 1u) {
-              const int c = __ffs(left) - 1;
-              const uint32_t XP = 0u - ((supx >> c) & 1u), ZP = 0u - ((supz >> c) & 1u);
-              const int lj = warp + c * NW;
-              const size_t ii = (size_t)lj * Wp + w;
-              const uint32_t x = s.Xs[ii], z = s.Zs[ii];
-              const uint32_t A0 = x & z, B0 = (x ^ XP) & (z ^ ZP);
-              const uint32_t inc = A0 & ~B0 & Sw, dec = B0 & ~A0 & Sw;
-              hi ^= ((lo & inc) | (~lo & dec)) ^ (ZP & x & Sw);
-              lo ^= inc | dec;
-              uint32_t xn = x ^ (XP & Sw), zn = z ^ (ZP & Sw);
-              if (w == wd) {  // row p-n := row p
-                xn = (xn & ~bpm) | (XP & bpm);
-                zn = (zn & ~bpm) | (ZP & bpm);
+              for (int k = 0; k < WL; ++k) {
+                const int w = lane + 32 * k;
+                if (w < W) {
+                  const uint32_t x = xc[w], t = zc[w] & Sw[k];
+                  phi[k] ^= t & ~(x ^ plo[k]);
+                  plo[k] ^= t;
+                  xc[w] = x ^ Sw[k];
+                }
               }
-              if (w == wp) {  // row p := Z_a
-                xn &= ~bpm;
-                zn = (zn & ~bpm) | ((lj == la) ? bpm : 0u);
+            } else if (!cx) {  // Z
+#pragma unroll
+              for (int k = 0; k < WL; ++k) {
+                const int w = lane + 32 * k;
+                if (w < W) {
+                  const uint32_t z = zc[w], t = xc[w] & Sw[k];
+                  phi[k] ^= t & (z ^ plo[k]);
+                  plo[k] ^= t;
+                  zc[w] = z ^ Sw[k];
+                }
               }
-              s.Xs[ii] = xn;
-              s.Zs[ii] = zn;
+            } else {  // Y
+#pragma unroll
+              for (int k = 0; k < WL; ++k) {
+                const int w = lane + 32 * k;
+                if (w < W) {
+                  const uint32_t x = xc[w], z = zc[w];
+                  const uint32_t e = ~(x ^ z) & Sw[k];
+                  phi[k] ^= (e & ~(x ^ plo[k])) ^ (x & Sw[k]);
+                  plo[k] ^= e;
+                  xc[w] = x ^ Sw[k];
+                  zc[w] = z ^ Sw[k];
+                }
+              }
             }
-            // this warp's share of 2 r_p and of sum_j x_pj z_pj, on every row in S'
-            res_add4(lo, hi, (scal & 1u) ? Sw : 0u, (scal & 2u) ? Sw : 0u);
+          }
+          __syncwarp();
+          // rows p-n and p of every column of this warp: row p-n := row p,
+          // row p := Z_a (lane c: local column c0 + c)
+          if (lane < ncw) {
+            const int lj = c0 + lane;
+            uint32_t* xc = s.Xs + (size_t)lj * Wp;
+            uint32_t* zc = s.Zs + (size_t)lj * Wp;
+            xc[wd] = (xc[wd] & ~bpm) | (xb ? bpm : 0u);
+            zc[wd] = (zc[wd] & ~bpm) | (zb ? bpm : 0u);
+            xc[wp] &= ~bpm;
+            zc[wp] = (zc[wp] & ~bpm) | ((lj == la) ? bpm : 0u);
+          }
+          // this warp's share of 2 r_p and of sum_j x_pj z_pj, on every row in S'
+#pragma unroll
+          for (int k = 0; k < WL; ++k) {
+            const int w = lane + 32 * k;
+            uint32_t lo = plo[k], hi = phi[k];
+            res_add4(lo, hi, (scal & 1u) ? Sw[k] : 0u, (scal & 2u) ? Sw[k] : 0u);
             if (w == wd) {  // share of row p-n := share of row p
               lo = (lo & ~bpm) | ((php & 1u) ? bpm : 0u);
               hi = (hi & ~bpm) | ((php & 2u) ? bpm : 0u);
@@ -403,77 +536,87 @@ __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
             plo[k] = lo;
             phi[k] = hi;
           }
-        }
-        if (dop(code) == OP_MZR && rbit && la >= 0 && la % NW == warp) {
-          __syncwarp();  // reset: X_a on every row, sign ^= z_a
-          const uint32_t* zc = s.Zs + (size_t)la * Wp;
+          if (dop(code) == OP_MZR && rbit && b.lw[i] == warp) {
+            __syncwarp();  // reset: X_a on every row, sign ^= z_a
+            const uint32_t* zc = s.Zs + (size_t)la * Wp;
+#pragma unroll
+            for (int k = 0; k < WL; ++k) {
+              const int w = lane + 32 * k;
+              if (w < W) phi[k] ^= zc[w];
+            }
+          }
+          if (base_warp) {
+            __syncwarp();
+            if (lane == 0) {
+              s.R4lo[wd] = (s.R4lo[wd] & ~bpm) | ((r4p & 1u) ? bpm : 0u);
+              s.R4hi[wd] = (s.R4hi[wd] & ~bpm) | ((r4p & 2u) ? bpm : 0u);
+              s.R4lo[wp] &= ~bpm;
+              s.R4hi[wp] = (s.R4hi[wp] & ~bpm) | (rbit ? bpm : 0u);
+            }
+            __syncwarp();
+          }
+        } else {
+          // ============ deterministic outcome: this warp's partial ============
+          uint32_t acc = 0u;
 #pragma unroll
           for (int k = 0; k < WL; ++k) {
             const int w = lane + 32 * k;
-            if (w < W) phi[k] ^= zc[w];
-          }
-        }
-        if (base_warp) {
-          __syncwarp();
-          if (lane == 0) {
-            s.R4lo[wd] = (s.R4lo[wd] & ~bpm) | ((r4p & 1u) ? bpm : 0u);
-            s.R4hi[wd] = (s.R4hi[wd] & ~bpm) | ((r4p & 2u) ? bpm : 0u);
-            s.R4lo[wp] &= ~bpm;
-            s.R4hi[wp] = (s.R4hi[wp] & ~bpm) | (rbit ? bpm : 0u);
-          }
-          __syncwarp();
-        }
-      } else {
-        // ============ deterministic outcome: this warp's partial ============
-        uint32_t acc = 0u;
-#pragma unroll
-        for (int k = 0; k < WL; ++k) {
-          const int w = lane + 32 * k;
-          if (w >= Wh && w < W) {
-            const uint32_t t = S[w - Wh];
-            acc += __popc(plo[k] & t) + 2u * __popc(phi[k] & t);
-            if (base_warp) acc += __popc(s.R4lo[w] & t) + 2u * __popc(s.R4hi[w] & t);
-          }
-        }
-        const uint32_t lt = (1u << lane) - 1u;
-        for (int c = 0; c < ncw; ++c) {
-          const size_t col = (size_t)(warp + c * NW) * Wp + Wh;
-          uint32_t carry = 0u;
-          for (int base = 0; base < Wh; base += 32) {
-            const int hw = base + lane;
-            uint32_t xT = 0u, zT = 0u;
-            if (hw < Wh) {
-              const uint32_t t = S[hw];
-              xT = s.Xs[col + hw] & t;
-              zT = s.Zs[col + hw] & t;
+            if (w >= Wh && w < W) {
+              const uint32_t t = S[w - Wh];
+              acc += __popc(plo[k] & t) + 2u * __popc(phi[k] & t);
+              if (base_warp) acc += __popc(s.R4lo[w] & t) + 2u * __popc(s.R4hi[w] & t);
             }
-            acc += __popc(xT & zT);
-            const uint32_t bal = __ballot_sync(0xffffffffu, __popc(zT) & 1);
-            const uint32_t cin = (__popc(bal & lt) & 1u) ^ carry;
-            const uint32_t zpre = res_prefix_xor_excl(zT) ^ (cin ? 0xffffffffu : 0u);
-            acc += 2u * (__popc(xT & zpre) & 1u);
-            carry ^= __popc(bal) & 1u;
           }
-        }
+          for (int c = 0; c < ncw; ++c) {
+            const size_t col = (size_t)(c0 + c) * Wp + Wh;
+            uint32_t carry = 0u;
+            for (int base = 0; base < Wh; base += 32) {
+              const int hw = base + lane;
+              uint32_t xT = 0u, zT = 0u;
+              if (hw < Wh) {
+                const uint32_t t = S[hw];
+                xT = s.Xs[col + hw] & t;
+                zT = s.Zs[col + hw] & t;
+              }
+              acc += __popc(xT & zT);
+              const uint32_t bal = __ballot_sync(0xffffffffu, __popc(zT) & 1);
+              const uint32_t cin = (__popc(bal & lt) & 1u) ^ carry;
+              const uint32_t zpre = res_prefix_xor_excl(zT) ^ (cin ? 0xffffffffu : 0u);
+              acc += 2u * (__popc(xT & zpre) & 1u);
+              carry ^= __popc(bal) & 1u;
+            }
+          }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0 && (acc & 3u)) atomicAdd(&b.dacc[i], acc & 3u);
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+          if (lane == 0 && (acc & 3u)) atomicAdd(&b.dacc[i], acc & 3u);
+        }
+        if (__shfl_sync(0xffffffffu, lane == 0 ? b.keff : 0, 0) == i + 1) break;  // batch ends here
       }
     }
     __syncthreads();
+    const int keff = b.keff;
+    if (r == 0 && warp == 0 && lane < keff && b.P[lane] >= 0)
+      A.out[m + lane] = (uint8_t)my_rbit;
 
     // ---- publish the deterministic partials; bookkeeping for the next batch
+    int anydet = 0;
     for (int i = 0; i < keff; ++i)
-      if (b.P[i] < 0) cm.publish_dp(s.dpv, par, i, KB, b.dacc[i] & 3u);
+      if (b.P[i] < 0) {
+        cm.publish_dp(s.dpv, par, i, KB, b.dacc[i] & 3u);
+        anydet = 1;
+      }
     __syncthreads();
     if (tid < keff) b.ptype[tid] = b.P[tid] < 0;
-    __syncthreads();
     if (tid == 0) {
       b.plast = b.code[keff - 1];
+      b.anydet = anydet;
+    }
+    __syncthreads();
+    if (warp == 0) {
       const int mn = m + keff;
       const int Kn = (A.nm - mn < KB) ? A.nm - mn : KB;
-      if (Kn > 0) res_batch_slots(A.mops, mn, Kn, C, r, b);
-      else b.D = b.nown = 0;
+      if (keff != K && lane < Kn) next_code = __ldg(A.mops + mn + lane);  // batch ended early
+      res_batch_slots(next_code, Kn > 0 ? Kn : 0, C, r, cpw, b);
     }
     __syncthreads();
     cm.stage_columns(s, par ^ 1, b, W, Wp, KB);  // next batch's measured columns
@@ -485,7 +628,7 @@ __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
 
   // ---- epilogue: last batch's deterministic outcomes, fold, write back
   if (!cm.sync()) return;
-  {
+  if (b.anydet) {
     const int par = batch & 1;
     if (tid < prev_count && b.ptype[tid]) {
       const uint32_t e = cm.sum_dp(s.dpv, par ^ 1, tid, KB) & 3u;
@@ -499,10 +642,9 @@ __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
     s.PHhi[w] = 0u;
   }
   __syncthreads();
-  if (prev_count > 0 && b.ptype[prev_count - 1] && b.det[prev_count - 1] &&
-      dop(b.plast) == OP_MZR) {
+  if (b.anydet && b.ptype[prev_count - 1] && b.det[prev_count - 1] && dop(b.plast) == OP_MZR) {
     const int pa = (int)dq1(b.plast);
-    if (pa % C == r && (pa / C) % NW == warp) {
+    if (pa % C == r && (pa / C) / cpw == warp) {
       const uint32_t* zc = s.Zs + (size_t)(pa / C) * Wp;
 #pragma unroll
       for (int k = 0; k < WL; ++k) {

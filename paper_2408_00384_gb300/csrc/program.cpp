@@ -92,7 +92,7 @@ static int build_program_stream(int32_t n, const tab_gate* gates, int64_t count,
 }
 
 int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out,
-                  bool layered) {
+                  int mode) {
   if (n < 1 || n > TAB_MAX_QUBITS) {
     set_error("n=%d outside [1, %d]", n, TAB_MAX_QUBITS);
     return TAB_ERANGE;
@@ -128,11 +128,23 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
     }
   }
 
-  if (!layered) return build_program_stream(n, gates, count, out);
+  if (mode & kProgStream) {
+    const int rc = build_program_stream(n, gates, count, out);
+    out->mode = kProgStream;
+    return rc;
+  }
+  const bool layers = (mode & kProgLayers) != 0, blocks = (mode & kProgBlocks) != 0;
   HostProgram& P = *out;
   P = HostProgram();
   P.n = n;
-  P.ops.reserve((size_t)count);
+  P.mode = mode & (kProgLayers | kProgBlocks);
+  if (layers) P.ops.reserve((size_t)count);
+  BlockBuilder bb;
+  if (blocks) {
+    bb.reset(n);
+    P.blk.reserve((size_t)count / 2 + 16);
+  }
+  int64_t run_gates = 0;  // gates in the open gate run
   std::vector<int64_t> last((size_t)n, -1);  // global layer of the last gate per qubit
   int64_t nlayers = 0;                       // layers emitted so far (global)
   std::vector<uint32_t> seg_codes;
@@ -143,7 +155,19 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
   // layer_off[layer_begin] = op_begin, layer_off[layer_begin + L + 1] = end
   // of layer L, layer_off[layer_end] = op_end.
   auto flush_gates = [&]() {
-    if (seg_codes.empty()) return;
+    if (run_gates == 0) return;
+    run_gates = 0;
+    if (!layers) {  // blocks only: the run owns no gate codes
+      Seg s{};
+      s.kind = 0;
+      s.op_begin = s.op_end = (uint32_t)P.ops.size();
+      s.meas_before = (uint32_t)P.n_meas;
+      s.layer_begin = s.layer_end = (uint32_t)P.layer_off.size();
+      bb.emit(P, s);
+      bb.reset(n);
+      P.segs.push_back(s);
+      return;
+    }
     const int64_t base = nlayers;
     int64_t top = base;
     for (int32_t L : seg_layer) top = std::max<int64_t>(top, (int64_t)L + 1);
@@ -186,6 +210,12 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
       P.layer_off.push_back(run);
     }
     s.layer_end = (uint32_t)P.layer_off.size() - 1;
+    if (blocks) {
+      bb.emit(P, s);
+      bb.reset(n);
+    } else {
+      s.blk_begin = s.blk_end = (uint32_t)P.blk_off.size();
+    }
     P.segs.push_back(s);
     // column versions in the final (layered) order
     P.vers.resize(P.ops.size(), 0u);
@@ -228,6 +258,10 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
       continue;
     }
     const bool two = (op == TAB_CNOT || op == TAB_CZ || op == TAB_SWAP);
+    ++run_gates;
+    P.n_gates++;
+    if (blocks) bb.add(op, q1, two ? q2 : 0);
+    if (!layers) continue;
     int64_t L = std::max<int64_t>(last[q1], nlayers - 1);
     if (two) L = std::max<int64_t>(L, last[q2]);
     L += 1;
@@ -235,7 +269,6 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
     if (two) last[q2] = L;
     seg_codes.push_back(dcode(op, q1, two ? q2 : 0));
     seg_layer.push_back((int32_t)L);
-    P.n_gates++;
   }
   flush_gates();
   return TAB_OK;

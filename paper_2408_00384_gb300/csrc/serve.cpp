@@ -41,7 +41,7 @@ using namespace tab;
 namespace tab {
 int handle_outcomes_async(tab_t h, uint8_t* host, cudaStream_t* used_stream);
 int handle_apply_program(tab_t h, const HostProgram& hp);
-bool flow_gates_for(int n);
+int grid_compile_mode(int n);
 int handle_set_meas_ctas(tab_t h, int ctas);
 size_t handle_device_bytes(int32_t n);
 }
@@ -373,9 +373,9 @@ int tab_server_submit(tab_server_t S, const tab_circuit* c, int64_t* ticket) {
     set_error("host allocation failed");
     return TAB_ENOMEM;
   }
-  // single-SM requests need layers; grid-wide ones run in program order
-  const bool layered = c->n <= TAB_BATCH_MAX_QUBITS || !flow_gates_for(c->n);
-  const int crc = build_program(c->n, c->gates, c->n_gates, &r->prog, layered);
+  // single-SM requests need layers; grid-wide ones the form their gate kernel reads
+  const int mode = c->n <= TAB_BATCH_MAX_QUBITS ? kProgLayers : grid_compile_mode(c->n);
+  const int crc = build_program(c->n, c->gates, c->n_gates, &r->prog, mode);
   if (crc != TAB_OK) {
     delete r;
     return crc;

@@ -63,6 +63,8 @@ struct tab_prog_s {
   uint32_t* d_layer = nullptr;
   Seg* d_segs = nullptr;
   uint2* d_rec = nullptr;
+  uint2* d_blk = nullptr;
+  uint32_t* d_blk_off = nullptr;
 };
 
 // Device copy of a compiled program.
@@ -70,13 +72,17 @@ struct DevProg {
   uint32_t* ops = nullptr;
   uint32_t* layer = nullptr;
   Seg* segs = nullptr;
-  uint2* rec = nullptr;  // (code, versions) per op, for the dataflow gate kernel
-  void* base = nullptr;  // single allocation holding all of the above (staged uploads)
+  uint2* rec = nullptr;       // (code, versions) per op, for the dataflow gate kernel
+  uint2* blk = nullptr;       // block records, for the block gate kernel
+  uint32_t* blk_off = nullptr;
+  void* base = nullptr;       // single allocation holding all of the above (staged uploads)
 };
 
 namespace {
 
 bool use_flow_gates(int n);
+enum GateKernel { GK_BLOCK = 0, GK_SLAB = 1, GK_FLOW = 2 };
+GateKernel gate_kernel(int n);
 
 int sm_count_of(int dev) {
   int v = 0;
@@ -193,23 +199,24 @@ bool use_single_cta(tab_t h) {
 }
 
 // Engine that runs a run of measurements on this handle (single-CTA runs the
-// whole program), and its CTA count: cluster-resident > grid-resident >
-// streaming, as the selected engine allows.
+// whole program), and its CTA count: grid-resident > cluster-resident >
+// streaming, as the selected engine allows (the grid-resident engine spreads
+// a batch over every SM; a cluster holds it on at most 16).
 int measure_engine(tab_t h, int* ctas) {
   if (use_single_cta(h)) {
     *ctas = 1;
     return TAB_ENGINE_SINGLE_CTA;
   }
   const bool any = h->engine == TAB_ENGINE_AUTO;
-  const int C = (any || h->engine == TAB_ENGINE_CLUSTER) ? cluster_size_for(h->n, h->Wh) : 0;
-  if (C > 0) {
-    *ctas = C;
-    return TAB_ENGINE_CLUSTER;
-  }
   const int G = (any || h->engine == TAB_ENGINE_GRID) ? h->res_ctas : 0;
   if (G > 0) {
     *ctas = G;
     return TAB_ENGINE_GRID;
+  }
+  const int C = (any || h->engine == TAB_ENGINE_CLUSTER) ? cluster_size_for(h->n, h->Wh) : 0;
+  if (C > 0) {
+    *ctas = C;
+    return TAB_ENGINE_CLUSTER;
   }
   *ctas = h->meas_ctas;
   return TAB_ENGINE_STREAM;
@@ -245,9 +252,14 @@ int run_program(tab_t h, const HostProgram& hp, const DevProg& dp, uint64_t seed
     h->log_len += hp.n_meas;
     return TAB_OK;
   }
+  const GateKernel gk = gate_kernel(h->n);
+  const bool can_blk = (hp.mode & kProgBlocks) != 0, can_lay = (hp.mode & kProgLayers) != 0;
   for (const Seg& s : hp.segs) {
     if (s.kind == 0) {
-      if (!hp.layered || use_flow_gates(h->n))
+      if (can_blk && (gk == GK_BLOCK || (!can_lay && dp.rec == nullptr)))
+        CU(launch_gates_block(h->X, h->Z, h->R, h->n, h->W, dp.blk, dp.blk_off + s.blk_begin,
+                              (int)(s.blk_end - s.blk_begin), h->mw.err, h->stream));
+      else if (dp.rec != nullptr && (gk == GK_FLOW || !can_lay))
         CU(launch_gates_flow(h->X, h->Z, h->R, h->n, h->W, dp.rec, s.op_begin, s.op_end,
                              h->mw.err, h->stream));
       else
@@ -299,9 +311,30 @@ int upload(const HostProgram& hp, DevProg* d, cudaStream_t s, bool async_alloc) 
   if (!hp.segs.empty())
     CU(cudaMemcpyAsync(d->segs, hp.segs.data(), hp.segs.size() * sizeof(Seg),
                        cudaMemcpyHostToDevice, s));
+  // block records (padded like ops: TMA chunks may read past the end)
+  if (hp.mode & kProgBlocks) {
+    const size_t bb = (hp.blk.size() + kOpsPad) * sizeof(uint2);
+    const size_t bo = std::max<size_t>(hp.blk_off.size(), 1) * 4;
+    if (async_alloc) {
+      CU(cudaMallocAsync((void**)&d->blk, bb, s));
+      CU(cudaMallocAsync((void**)&d->blk_off, bo, s));
+    } else {
+      CU(cudaMalloc((void**)&d->blk, bb));
+      CU(cudaMalloc((void**)&d->blk_off, bo));
+    }
+    if (!hp.blk.empty())
+      CU(cudaMemcpyAsync(d->blk, hp.blk.data(), hp.blk.size() * sizeof(uint2),
+                         cudaMemcpyHostToDevice, s));
+    CU(cudaMemsetAsync(d->blk + hp.blk.size(), 0, (size_t)kOpsPad * sizeof(uint2), s));
+    if (!hp.blk_off.empty())
+      CU(cudaMemcpyAsync(d->blk_off, hp.blk_off.data(), hp.blk_off.size() * 4,
+                         cudaMemcpyHostToDevice, s));
+  }
   // 64-bit records for the dataflow gate kernel (same padding rule as ops);
   // only when that kernel will run for this n
-  if (hp.n_gates == 0 || !use_flow_gates(hp.n)) return TAB_OK;
+  if (hp.n_gates == 0 ||
+      !((hp.mode & kProgStream) || ((hp.mode & kProgLayers) && use_flow_gates(hp.n))))
+    return TAB_OK;
   const size_t rb = (hp.ops.size() + kOpsPad) * sizeof(uint2);
   if (async_alloc) {
     CU(cudaMallocAsync((void**)&d->rec, rb, s));
@@ -327,18 +360,24 @@ void free_async(DevProg& d, cudaStream_t s) {
   if (d.layer) cudaFreeAsync(d.layer, s);
   if (d.segs) cudaFreeAsync(d.segs, s);
   if (d.rec) cudaFreeAsync(d.rec, s);
+  if (d.blk) cudaFreeAsync(d.blk, s);
+  if (d.blk_off) cudaFreeAsync(d.blk_off, s);
 }
 
 // Upload a compiled program through the handle's pinned staging area: one
 // stream-ordered allocation and one asynchronous copy.  The staging area is
 // reused once the previous copy out of it has completed.
 int upload_staged(tab_t h, const HostProgram& hp, DevProg* d) {
-  const bool want_rec = hp.n_gates > 0 && use_flow_gates(hp.n);
+  const bool want_rec =
+      hp.n_gates > 0 && ((hp.mode & kProgStream) || ((hp.mode & kProgLayers) && use_flow_gates(hp.n)));
+  const bool want_blk = (hp.mode & kProgBlocks) != 0;
   const size_t ob = align256((hp.ops.size() + kOpsPad) * 4);
   const size_t lb = align256(std::max<size_t>(hp.layer_off.size(), 1) * 4);
   const size_t sb = align256(std::max<size_t>(hp.segs.size(), 1) * sizeof(Seg));
   const size_t rb = want_rec ? align256((hp.ops.size() + kOpsPad) * sizeof(uint2)) : 0;
-  const size_t total = ob + lb + sb + rb;
+  const size_t bb = want_blk ? align256((hp.blk.size() + kOpsPad) * sizeof(uint2)) : 0;
+  const size_t bo = want_blk ? align256(std::max<size_t>(hp.blk_off.size(), 1) * 4) : 0;
+  const size_t total = ob + lb + sb + rb + bb + bo;
   if (h->stg_pending) {
     CU(cudaEventSynchronize(h->stg_ev));
     h->stg_pending = false;
@@ -364,6 +403,12 @@ int upload_staged(tab_t h, const HostProgram& hp, DevProg* d) {
     for (size_t i = 0; i < no; ++i) rec[i] = make_uint2(hp.ops[i], hp.vers[i]);
     memset(rec + no, 0, (size_t)kOpsPad * sizeof(uint2));
   }
+  if (want_blk) {
+    uint8_t* b0 = st + ob + lb + sb + rb;
+    if (!hp.blk.empty()) memcpy(b0, hp.blk.data(), hp.blk.size() * sizeof(uint2));
+    memset(b0 + hp.blk.size() * sizeof(uint2), 0, (size_t)kOpsPad * sizeof(uint2));
+    if (!hp.blk_off.empty()) memcpy(b0 + bb, hp.blk_off.data(), hp.blk_off.size() * 4);
+  }
   uint8_t* dev = nullptr;
   CU(cudaMallocAsync((void**)&dev, total, h->stream));
   CU(cudaMemcpyAsync(dev, st, total, cudaMemcpyHostToDevice, h->stream));
@@ -374,23 +419,39 @@ int upload_staged(tab_t h, const HostProgram& hp, DevProg* d) {
   d->layer = reinterpret_cast<uint32_t*>(dev + ob);
   d->segs = reinterpret_cast<Seg*>(dev + ob + lb);
   d->rec = want_rec ? reinterpret_cast<uint2*>(dev + ob + lb + sb) : nullptr;
+  d->blk = want_blk ? reinterpret_cast<uint2*>(dev + ob + lb + sb + rb) : nullptr;
+  d->blk_off = want_blk ? reinterpret_cast<uint32_t*>(dev + ob + lb + sb + rb + bb) : nullptr;
   return TAB_OK;
 }
 
-// Compile mode for a call on this handle: program order (one pass) when the
-// dataflow gate kernel will run its gates, ASAP layers otherwise.
-bool layered_for(tab_t h) { return use_single_cta(h) || !use_flow_gates(h->n); }
-
-// Gate kernel choice: the layer-barrier kernel by default (faster on the
-// measured workloads); TAB_GATE_KERNEL=flow selects the dataflow kernel (no
-// layer barriers) when its slab, version words and record ring fit.
-bool use_flow_gates(int n) {
+// Gate kernel of the multi-CTA engines: the block kernel by default (one
+// barrier per super-layer of two-qubit blocks); TAB_GATE_KERNEL=slab selects
+// the layer-barrier kernel and TAB_GATE_KERNEL=flow the dataflow kernel, each
+// where its shared-memory slab fits.
+GateKernel gate_kernel(int n) {
   static int mode = -1;
   if (mode < 0) {
     const char* e = getenv("TAB_GATE_KERNEL");
-    mode = (e && strcmp(e, "flow") == 0) ? 1 : 0;
+    mode = GK_BLOCK;
+    if (e && strcmp(e, "slab") == 0) mode = GK_SLAB;
+    if (e && strcmp(e, "flow") == 0) mode = GK_FLOW;
   }
-  return mode == 1 && n <= gates_flow_max_n();
+  if (mode == GK_FLOW && n > gates_flow_max_n()) return GK_SLAB;
+  if (mode == GK_BLOCK && n > gates_block_max_n()) return GK_SLAB;
+  return (GateKernel)mode;
+}
+
+bool use_flow_gates(int n) { return gate_kernel(n) == GK_FLOW; }
+
+// Compile forms for a call on this handle: ASAP layers for the single-CTA
+// engine, else what the gate kernel reads.
+int compile_mode_for(tab_t h) {
+  if (use_single_cta(h)) return kProgLayers;
+  switch (gate_kernel(h->n)) {
+    case GK_BLOCK: return kProgBlocks;
+    case GK_FLOW: return kProgStream;
+    default: return kProgLayers;
+  }
 }
 
 }  // namespace
@@ -530,9 +591,9 @@ int tab_apply(tab_t h, const tab_gate* gates, int64_t count) {
   int rc = check_handle(h);
   if (rc) return rc;
   HostProgram hp;
-  rc = build_program(h->n, gates, count, &hp, layered_for(h));
+  rc = build_program(h->n, gates, count, &hp, compile_mode_for(h));
   if (rc) return rc;
-  if (hp.ops.empty()) return TAB_OK;
+  if (hp.n_gates + hp.n_meas == 0) return TAB_OK;
   DevProg d;
   rc = upload_staged(h, hp, &d);
   if (rc == TAB_OK) rc = run_program(h, hp, d, h->seed);
@@ -551,7 +612,8 @@ int tab_prog_create(int32_t n, const tab_gate* gates, int64_t count, tab_prog_t*
     set_error("host allocation failed");
     return TAB_ENOMEM;
   }
-  int rc = build_program(n, gates, count, &p->hp);
+  // both forms: the program may run on any engine
+  int rc = build_program(n, gates, count, &p->hp, kProgLayers | kProgBlocks);
   if (rc == TAB_OK) {
     DevProg d;
     rc = upload(p->hp, &d, nullptr, false);
@@ -559,6 +621,8 @@ int tab_prog_create(int32_t n, const tab_gate* gates, int64_t count, tab_prog_t*
     p->d_layer = d.layer;
     p->d_segs = d.segs;
     p->d_rec = d.rec;
+    p->d_blk = d.blk;
+    p->d_blk_off = d.blk_off;
   }
   if (rc == TAB_OK) {
     cudaError_t e = cudaStreamSynchronize(nullptr);
@@ -581,6 +645,8 @@ int tab_prog_destroy(tab_prog_t p) {
   if (p->d_layer) cudaFree(p->d_layer);
   if (p->d_segs) cudaFree(p->d_segs);
   if (p->d_rec) cudaFree(p->d_rec);
+  if (p->d_blk) cudaFree(p->d_blk);
+  if (p->d_blk_off) cudaFree(p->d_blk_off);
   delete p;
   return TAB_OK;
 }
@@ -617,6 +683,8 @@ int tab_run(tab_t h, tab_prog_t p) {
   d.layer = p->d_layer;
   d.segs = p->d_segs;
   d.rec = p->d_rec;
+  d.blk = p->d_blk;
+  d.blk_off = p->d_blk_off;
   return run_program(h, p->hp, d, h->seed);
 }
 
@@ -637,7 +705,7 @@ static int measure_common(tab_t h, const int32_t* qubits, int32_t k, uint64_t se
     g[(size_t)i] = tab_make_gate(TAB_MZ, (uint32_t)qubits[i], 0);
   }
   HostProgram hp;
-  rc = build_program(h->n, g.data(), k, &hp, false);  // measurements only
+  rc = build_program(h->n, g.data(), k, &hp, kProgStream);  // measurements only
   if (rc) return rc;
   *first = h->log_len;
   if (hp.ops.empty()) return TAB_OK;
@@ -802,9 +870,14 @@ int handle_set_meas_ctas(tab_t h, int ctas) {
 
 size_t handle_device_bytes(int32_t n) { return tab_bytes_required(n); }
 
-// Whether a grid-engine handle of n qubits runs gates with the dataflow kernel
-// (then a program-order compile suffices).
-bool flow_gates_for(int n) { return use_flow_gates(n); }
+// Compile forms a request of n qubits needs on a multi-CTA engine handle.
+int grid_compile_mode(int n) {
+  switch (gate_kernel(n)) {
+    case GK_BLOCK: return kProgBlocks;
+    case GK_FLOW: return kProgStream;
+    default: return kProgLayers;
+  }
+}
 
 // Enqueue an already compiled program (the request server compiles at submit).
 int handle_apply_program(tab_t h, const HostProgram& hp) {
@@ -814,9 +887,9 @@ int handle_apply_program(tab_t h, const HostProgram& hp) {
     set_error("program built for n=%d, handle has n=%d", hp.n, h->n);
     return TAB_EINVAL;
   }
-  if (hp.ops.empty()) return TAB_OK;
-  if (!hp.layered && use_single_cta(h)) {
-    set_error("a program-order program needs a grid engine");
+  if (hp.n_gates + hp.n_meas == 0) return TAB_OK;
+  if (hp.n_gates > 0 && !(hp.mode & kProgLayers) && use_single_cta(h)) {
+    set_error("the single-CTA engine needs a layered program");
     return TAB_EINVAL;
   }
   DevProg d;

@@ -48,12 +48,28 @@ struct Seg {
   uint32_t op_begin, op_end;
   uint32_t layer_begin, layer_end;  // gates: layers [layer_begin, layer_end)
   uint32_t meas_before;             // measurement ops preceding this segment
+  uint32_t blk_begin, blk_end;      // gates: block super-layers [blk_begin, blk_end)
 };
+
+// Compile forms of gate runs (build_program's mode, any combination):
+//   kProgLayers  ASAP layers of gate codes (ops, layer_off): the single-CTA
+//                engine and the layer-barrier slab kernel;
+//   kProgBlocks  two-qubit blocks in super-layers (blk, blk_off): the block
+//                gate kernel (blocks.cpp);
+//   kProgStream  program order with column versions (ops, vers): the
+//                dataflow gate kernel (exclusive with kProgLayers).
+enum : int { kProgLayers = 1, kProgBlocks = 2, kProgStream = 4 };
 
 struct HostProgram {
   int32_t n = 0;
   bool layered = true;  // gate runs grouped into ASAP layers (else program order)
+  int mode = kProgLayers;
   int64_t n_gates = 0, n_meas = 0;
+  // block records: lo = qa | qb<<14 | has_b<<28 | ent<<29 (0 none, 1 CNOT,
+  // 2 CZ) | dir<<31 (CNOT control in register 1); hi = U0 | U1<<7 | V0<<14 |
+  // V1<<21 | swap<<28 (7-bit single-qubit Cliffords, clifford1.h)
+  std::vector<uint2> blk;
+  std::vector<uint32_t> blk_off;  // absolute record offsets of super-layer bounds
   std::vector<uint32_t> ops;
   // per gate op: versions its qubits must have reached within the segment
   // (count of earlier gates on each qubit, mod 2^16): q1 in bits 0..15, q2 in
@@ -63,12 +79,31 @@ struct HostProgram {
   std::vector<Seg> segs;
 };
 
-// Validate and compile a gate list.  layered: gate runs grouped into ASAP
-// layers of disjoint gates (every engine can run it); otherwise program order
-// with per-gate column versions only (the dataflow gate kernel; one pass).
+// Validate and compile a gate list into the forms `mode` asks for (see
+// kProgLayers etc.; measurement runs are always MZ/MZR codes in ops).
 // Returns TAB_OK or an error (message set).
 int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out,
-                  bool layered = true);
+                  int mode = kProgLayers);
+
+// Block compiler for one gate run at a time (blocks.cpp).
+struct BlkRec {
+  uint32_t qa, qb;
+  int32_t layer;
+  uint8_t has_b, ent, dir, swp, dead;
+  uint32_t U[2], V[2];
+};
+class BlockBuilder {
+ public:
+  void reset(int32_t n);                          // start a gate run
+  void add(uint32_t op, uint32_t a, uint32_t b);  // next gate of the run (tab_op)
+  void emit(HostProgram& P, Seg& s);              // append the run's blocks
+ private:
+  std::vector<int32_t> cur_;    // latest block of each qubit in this run
+  std::vector<uint8_t> role_;   // register of that block holding the qubit
+  std::vector<uint32_t> stamp_; // run id of cur_ / role_ entries
+  uint32_t seg_ = 0;
+  std::vector<BlkRec> blk_;
+};
 
 // ---- global grid barrier state ----------------------------------------------------
 struct GridBar {
@@ -100,6 +135,12 @@ constexpr int kOpsPad = 1024;
 cudaError_t launch_gates_slab(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
                               const uint32_t* ops, const uint32_t* layer_off,
                               int nlayers, int* err, cudaStream_t s);
+// Block gate kernel: super-layers of at most kMaxLayerOps records, the
+// device record buffer padded by kOpsPad records past its end.
+int gates_block_max_n();
+cudaError_t launch_gates_block(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
+                               const uint2* blk, const uint32_t* blk_off, int nlayers,
+                               int* err, cudaStream_t s);
 cudaError_t launch_measure(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh,
                            const uint32_t* mops, int nm, uint64_t k0, uint64_t seed,
                            uint64_t cid, uint32_t shot, uint8_t* out, const MeasWork& mw,

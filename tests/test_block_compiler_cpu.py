@@ -1,0 +1,38 @@
+"""Host logic of the block gate compiler, without a GPU.
+
+The C++ check in tests/cpp compiles random gate lists into two-qubit blocks
+with the library's own compiler (program.cpp, blocks.cpp), applies the blocks
+to random 32-row words with the device kernel's block formulas, and compares
+with the gates applied one at a time by the Aaronson-Gottesman rules.
+"""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(ROOT, "paper_2408_00384_gb300", "csrc")
+
+
+def _cuda_include():
+    for d in (os.environ.get("CUDA_HOME", ""), "/usr/local/cuda"):
+        if d and os.path.exists(os.path.join(d, "include", "cuda_runtime.h")):
+            return os.path.join(d, "include")
+    return None
+
+
+def test_block_compiler_matches_gate_rules(tmp_path):
+    cxx = shutil.which("g++")
+    inc = _cuda_include()
+    if cxx is None or inc is None:
+        pytest.skip("needs g++ and the CUDA headers")
+    exe = str(tmp_path / "block_compiler_check")
+    cmd = [cxx, "-O2", "-std=c++17", "-I", inc, "-I", CSRC, "-I", os.path.join(ROOT, "include"),
+           os.path.join(HERE, "cpp", "block_compiler_check.cpp"),
+           os.path.join(CSRC, "program.cpp"), os.path.join(CSRC, "blocks.cpp"), "-o", exe]
+    subprocess.run(cmd, check=True, capture_output=True, text=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "bad 0" in r.stdout

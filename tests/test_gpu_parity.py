@@ -90,7 +90,7 @@ def test_larger_tableaus(engine, n):
 _E = tab
 @pytest.mark.parametrize("n,engine,want", [
     (200, _E.ENGINE_AUTO, _E.ENGINE_SINGLE_CTA),
-    (1000, _E.ENGINE_AUTO, _E.ENGINE_CLUSTER),
+    (1000, _E.ENGINE_AUTO, _E.ENGINE_GRID),
     (1000, _E.ENGINE_CLUSTER, _E.ENGINE_CLUSTER),
     (2400, _E.ENGINE_CLUSTER, _E.ENGINE_CLUSTER),
     (1000, _E.ENGINE_GRID, _E.ENGINE_GRID),
