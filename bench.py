@@ -34,6 +34,17 @@ METRIC = ("Clifford gates/sec and measurements/sec, batched vs plain path; "
           "p50/p99 latency")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+# INT32 logic lanes per SM (4 sub-partitions x 16) and SMs of a GB300: the
+# peak of the "alu" roofline is SMs x lanes x the SM clock sampled during the
+# timed region.
+ALU_LANES_PER_SM = 64
+GB300_SMS = 152
+# DRAM bytes (read + write) per launch of each kernel from one ncu capture of
+# this workload (profiles/); None once a kernel has changed since its capture.
+TRAFFIC_BYTES = {
+    "k_measure_resident": 582656 + 11008,
+    "k_gates_block": 4537088,
+}
 
 
 def parse():
@@ -315,6 +326,7 @@ def run_plain(args, ws, rank, local):
                 torch.cuda.synchronize()
                 barrier(ws)
                 t0 = time.perf_counter()
+                x0 = t.transfer_bytes()
             t.reset()
             t.set_rng(C.PHILOX_SEED, rank, 0)
             t.apply(host_gates)
@@ -323,38 +335,53 @@ def run_plain(args, ws, rank, local):
         torch.cuda.synchronize()
         barrier(ws)
         e2e_s = allreduce_max((time.perf_counter() - t0) / ke, ws)
+        x1 = t.transfer_bytes()
+        # the gate list is read on the host (validated and compiled there);
+        # what crosses to the device is the compiled program
         e2e = {"value": ws * c.n_gates / e2e_s, "unit": "gates/s",
-               "h2d_bytes_per_step": int(c.gates.nbytes), "d2h_bytes_per_step": int(c.n_meas),
+               "h2d_bytes_per_step": (x1[0] - x0[0]) // ke,
+               "d2h_bytes_per_step": (x1[1] - x0[1]) // ke,
+               "host_input_bytes_per_step": int(c.gates.nbytes),
                "ms_per_step": 1000.0 * e2e_s}
 
-    # ---- roofline of the dominant kernel
+    # ---- roofline of the dominant kernel.  Both kernels of this path keep
+    # the tableau on chip (the gate kernel a 32-row slab per CTA, the
+    # measurement kernel every column in some CTA's shared memory); DRAM
+    # carries only the program and one load/store of the tableau, so the bound
+    # is the integer logic the AG rules need, the "alu" roofline.
     pk, src = peaks()
     kind_ms = {k: statistics.mean(v) for k, v in per_kind.items()}
     dom = max(kind_ms, key=kind_ms.get)
-    n, Wh = c.n, ((((c.n + 31) // 32) + 3) // 4) * 4
+    n = c.n
+    words = 2.0 * n / 32.0  # 32-row words of the 2n tableau rows
     if dom == "measure":
-        # algorithmic bytes per random measurement: rows x supp columns read+written
-        # ~ 0.75 n^2 B (n columns in supp(p) ~ 3/4, 2 planes, 2n/8 B, read + write)
-        alg = 0.75 * n * n * c.n_meas
+        # a random-outcome measurement is a rowsum of row p into the rows of
+        # S' on every column where row p is not I (3/4 of the n columns for a
+        # random state); per such column and word: x ^= S, z ^= S (as row p
+        # has X / Z there) and the mod-4 exponent update, 6 logic ops
+        alg = 6.0 * 0.75 * n * words * c.n_meas
         kname = {tab.ENGINE_SINGLE_CTA: "k_sct_program", tab.ENGINE_CLUSTER: "k_measure_cluster",
                  tab.ENGINE_GRID: "k_measure_resident",
                  tab.ENGINE_STREAM: "k_measure"}[t.engine_resolved()[0]]
-        roof = {"kernel": kname, "bound": "hbm", "unit": "GB/s"}
-        roof["achieved"] = alg / (kind_ms[dom] / 1000.0) / 1e9
-        roof["peak"] = pk.get("hbm_gbs", FALLBACK_HBM_GBS)
     else:
-        # algorithmic bytes of a gate run: each gate reads + writes its columns
-        # (1q: x, z, r = 6 * 2n/8 B; 2q: 10 * 2n/8 B)
-        n1 = c.depth * n
-        n2 = c.n_gates - n1
-        alg = (6 * n1 + 10 * n2) * (2 * n / 8)
-        roof = {"kernel": "k_gates_slab", "bound": "hbm", "unit": "GB/s"}
-        roof["achieved"] = alg / (kind_ms[dom] / 1000.0) / 1e9
-        roof["peak"] = pk.get("hbm_gbs", FALLBACK_HBM_GBS)
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["peak_source"] = f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src
-    roof["traffic"] = None
-    roof["kernel_ms"] = kind_ms
+        # logic ops of each gate rule on one 32-row word (x, z, r):
+        # X/Z 1, Y 2, H 2, S 3, S^dag 3, CNOT 6, CZ 6, SWAP 0
+        opsof = {1: 1, 2: 2, 3: 1, 4: 2, 5: 3, 6: 3, 7: 6, 8: 6, 9: 0}
+        op, _, _ = C.decode(c.gates)
+        hist = np.bincount(op.astype(np.int64), minlength=16)
+        alg = words * float(sum(opsof.get(i, 0) * int(hist[i]) for i in range(16)))
+        kname = "k_gates_block"
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    peak_tops = GB300_SMS * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    achieved = alg / (kind_ms[dom] / 1000.0) / 1e12
+    roof = {"kernel": kname, "bound": "alu", "unit": "Top/s", "achieved": achieved,
+            "peak": peak_tops, "frac": achieved / peak_tops,
+            "peak_source": f"{GB300_SMS} SMs x {ALU_LANES_PER_SM} INT32 lanes x {sm_mhz:.0f} MHz "
+                           "(unit counts and the sampled SM clock)",
+            "traffic": TRAFFIC_BYTES.get(kname),
+            "kernel_ms": kind_ms,
+            "hbm_peak_gbs": pk.get("hbm_gbs", FALLBACK_HBM_GBS),
+            "hbm_peak_source": src}
 
     line = {
         "metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": ws,

@@ -213,6 +213,11 @@ int tab_set_engine(tab_t h, int engine);
  * call shows which one runs.  No device work.  TAB_EINVAL on null pointers. */
 int tab_engine_resolved(tab_t h, int* engine, int* ctas);
 
+/* Bytes this handle has copied host -> device (compiled programs, imports)
+ * and device -> host (outcomes, exports) for its callers since creation.
+ * Either pointer may be null.  No device work. */
+int tab_transfer_bytes(tab_t h, int64_t* h2d, int64_t* d2h);
+
 /* Number of CUDA kernels this handle has launched since creation. */
 int tab_kernel_launches(tab_t h, int64_t *count);
 

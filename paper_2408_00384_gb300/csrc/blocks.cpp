@@ -29,7 +29,18 @@
 
 namespace tab {
 
-void BlockBuilder::reset(int32_t n) {
+// c1_compose as a table: entry [b][a] is b after a (7-bit codes)
+static const uint8_t* c1_table() {
+  static const std::vector<uint8_t> t = [] {
+    std::vector<uint8_t> v(128 * 128);
+    for (uint32_t b = 0; b < 128; ++b)
+      for (uint32_t a = 0; a < 128; ++a) v[b * 128 + a] = (uint8_t)c1_compose(b, a);
+    return v;
+  }();
+  return t.data();
+}
+
+void BlockBuilder::reset(int32_t n, size_t hint) {
   if ((int32_t)cur_.size() < n) {
     cur_.assign((size_t)n, -1);
     role_.assign((size_t)n, 0);
@@ -37,6 +48,7 @@ void BlockBuilder::reset(int32_t n) {
   }
   ++seg_;
   blk_.clear();
+  if (hint > blk_.capacity()) blk_.reserve(hint);
 }
 
 // One gate (tab_op numbering) of the current run.
@@ -49,8 +61,8 @@ void BlockBuilder::add(uint32_t op, uint32_t a, uint32_t b) {
   };
   auto open = [&](uint32_t qa, uint32_t qb, bool two, int32_t layer) -> int32_t {
     BlkRec k{};
-    k.qa = qa;
-    k.qb = two ? qb : 0u;
+    k.qa = (uint16_t)qa;
+    k.qb = (uint16_t)(two ? qb : 0u);
     k.layer = layer;
     k.has_b = two;
     k.U[0] = k.U[1] = k.V[0] = k.V[1] = kC1Ident;
@@ -62,13 +74,13 @@ void BlockBuilder::add(uint32_t op, uint32_t a, uint32_t b) {
   };
   const bool two = op == TAB_CNOT || op == TAB_CZ || op == TAB_SWAP;
   if (!two) {
-    const uint32_t c = c1_of_op(op);
+    const uint8_t* tab = c1_table() + 128 * c1_of_op(op);
     int32_t B = latest(a);
     if (B < 0) B = open(a, 0, false, 0);
     BlkRec& k = blk_[(size_t)B];
     const uint8_t r = role_[a];
-    if (k.ent) k.V[r] = c1_compose(c, k.V[r]);
-    else k.U[r] = c1_compose(c, k.U[r]);
+    if (k.ent) k.V[r] = tab[k.V[r]];
+    else k.U[r] = tab[k.U[r]];
     return;
   }
   int32_t Ba = latest(a), Bb = latest(b);
@@ -83,7 +95,7 @@ void BlockBuilder::add(uint32_t op, uint32_t a, uint32_t b) {
       if (Ba >= 0 && Bb >= 0) {
         BlkRec& ka = blk_[(size_t)Ba];
         BlkRec& kb = blk_[(size_t)Bb];
-        ka.qb = b;
+        ka.qb = (uint16_t)b;
         ka.has_b = 1;
         ka.U[1] = kb.U[0];
         ka.layer = std::max(ka.layer, kb.layer);
@@ -92,13 +104,13 @@ void BlockBuilder::add(uint32_t op, uint32_t a, uint32_t b) {
         B = Ba;
       } else if (Ba >= 0) {
         BlkRec& ka = blk_[(size_t)Ba];
-        ka.qb = b;
+        ka.qb = (uint16_t)b;
         ka.has_b = 1;
         bind(b, Ba, 1);
         B = Ba;
       } else if (Bb >= 0) {
         BlkRec& kb = blk_[(size_t)Bb];
-        kb.qb = a;
+        kb.qb = (uint16_t)a;
         kb.has_b = 1;
         bind(a, Bb, 1);
         B = Bb;
@@ -127,10 +139,11 @@ void BlockBuilder::add(uint32_t op, uint32_t a, uint32_t b) {
   }
 }
 
-// Emit the run's blocks, grouped by super-layer (and, inside one, by kind so
-// that neighbouring threads take the same path); super-layers above
-// kMaxLayerOps blocks become consecutive sub-layers.  Appends to P.blk and
-// P.blk_off and sets s.blk_begin / s.blk_end.
+// Emit the run's blocks, grouped by super-layer and, inside one, by kind
+// (single- or two-qubit, entangler, whether the U and V codes are identities)
+// so that the threads of a warp take the same path and skip the same
+// identity codes; super-layers above kMaxLayerOps blocks become consecutive
+// sub-layers.  Appends to P.blk and P.blk_off and sets s.blk_begin / s.blk_end.
 void BlockBuilder::emit(HostProgram& P, Seg& s) {
   int32_t top = 0;
   size_t live = 0;
@@ -139,8 +152,13 @@ void BlockBuilder::emit(HostProgram& P, Seg& s) {
       top = std::max(top, k.layer + 1);
       ++live;
     }
-  const int kKinds = 4;  // 1q; 2q none / CNOT / CZ  (swaps ride along)
-  auto kind = [](const BlkRec& k) { return k.has_b ? 1 + (int)k.ent : 0; };
+  const int kKinds = 16;  // (1q | 2q none / CNOT / CZ) x (U identity) x (V identity)
+  auto kind = [](const BlkRec& k) {
+    const int e = k.has_b ? 1 + (int)k.ent : 0;
+    const int u = (k.U[0] == kC1Ident && k.U[1] == kC1Ident) ? 0 : 1;
+    const int v = (k.V[0] == kC1Ident && k.V[1] == kC1Ident) ? 0 : 1;
+    return e * 4 + u * 2 + v;
+  };
   std::vector<uint32_t> cnt((size_t)top * kKinds + 1, 0u);
   for (const BlkRec& k : blk_)
     if (!k.dead) cnt[(size_t)k.layer * kKinds + kind(k)]++;
@@ -154,10 +172,10 @@ void BlockBuilder::emit(HostProgram& P, Seg& s) {
   P.blk.resize(P.blk.size() + live);
   for (const BlkRec& k : blk_) {
     if (k.dead) continue;
-    const uint32_t lo = k.qa | (k.qb << 14) | ((uint32_t)k.has_b << 28) |
+    const uint32_t lo = (uint32_t)k.qa | ((uint32_t)k.qb << 14) | ((uint32_t)k.has_b << 28) |
                         ((uint32_t)k.ent << 29) | ((uint32_t)k.dir << 31);
-    const uint32_t hi = k.U[0] | (k.U[1] << 7) | (k.V[0] << 14) | (k.V[1] << 21) |
-                        ((uint32_t)k.swp << 28);
+    const uint32_t hi = (uint32_t)k.U[0] | ((uint32_t)k.U[1] << 7) | ((uint32_t)k.V[0] << 14) |
+                        ((uint32_t)k.V[1] << 21) | ((uint32_t)k.swp << 28);
     P.blk[base + pos[(size_t)k.layer * kKinds + kind(k)]++] = make_uint2(lo, hi);
   }
   s.blk_begin = (uint32_t)P.blk_off.size();

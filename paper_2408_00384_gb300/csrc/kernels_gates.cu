@@ -382,20 +382,27 @@ constexpr int kBlkChunk = 512;                  // records per TMA copy (4 KB)
 constexpr int kBlkSlots = 16;                   // 64 KB ring
 constexpr int kBlkRing = kBlkChunk * kBlkSlots;
 
-__device__ __forceinline__ void apply_block(uint2 rec, uint32_t* sx, uint32_t* sz, uint32_t& r) {
+// Identity codes are skipped when no thread of the warp needs the code (the
+// compiler groups blocks by which codes are identities); the lanes of a warp
+// that take part are given by `act`.
+__device__ __forceinline__ void apply_block(uint2 rec, uint32_t* sx, uint32_t* sz, uint32_t& r,
+                                            uint32_t act) {
   const uint32_t qa = rec.x & 0x3FFFu, qb = (rec.x >> 14) & 0x3FFFu;
   const bool two = (rec.x >> 28) & 1u;
   const uint32_t ent = (rec.x >> 29) & 3u, dir = rec.x >> 31;
   const uint32_t m = rec.y;
+  constexpr uint32_t kUId = kC1Ident | (kC1Ident << 7), kVId = kUId << 14;
+  const bool need_u = __any_sync(act, (m & 0x3FFFu) != kUId);
+  const bool need_v = __any_sync(act, (m & 0xFFFC000u) != kVId);
   uint32_t x0 = sx[qa], z0 = sz[qa];
-  c1_apply(m & 0x7Fu, x0, z0, r);
+  if (need_u) c1_apply(m & 0x7Fu, x0, z0, r);
   if (!two) {
     sx[qa] = x0;
     sz[qa] = z0;
     return;
   }
   uint32_t x1 = sx[qb], z1 = sz[qb];
-  c1_apply((m >> 7) & 0x7Fu, x1, z1, r);
+  if (need_u) c1_apply((m >> 7) & 0x7Fu, x1, z1, r);
   if (ent == 1u) {  // CNOT, control in register `dir`
     const uint32_t xc = dir ? x1 : x0, zc = dir ? z1 : z0;
     const uint32_t xt = dir ? x0 : x1, zt = dir ? z0 : z1;
@@ -411,8 +418,10 @@ __device__ __forceinline__ void apply_block(uint2 rec, uint32_t* sx, uint32_t* s
     z1 ^= x0;
     z0 = z0n;
   }
-  c1_apply((m >> 14) & 0x7Fu, x0, z0, r);
-  c1_apply((m >> 21) & 0x7Fu, x1, z1, r);
+  if (need_v) {
+    c1_apply((m >> 14) & 0x7Fu, x0, z0, r);
+    c1_apply((m >> 21) & 0x7Fu, x1, z1, r);
+  }
   const bool sw = (m >> 28) & 1u;
   const uint32_t da = sw ? qb : qa, db = sw ? qa : qb;
   sx[da] = x0;
@@ -485,8 +494,11 @@ __global__ void __launch_bounds__(T) k_gates_block(uint32_t* __restrict__ X, uin
     }
     __syncthreads();
     if (s_abort) break;
-    for (uint32_t g = lb + tid; g < le; g += T)
-      apply_block(ring[(g - base) & (kBlkRing - 1)], sx, sz, racc);
+    for (uint32_t g0 = lb + (tid & ~31u); g0 < le; g0 += T) {  // warp-uniform trip count
+      const uint32_t g = g0 + (tid & 31);
+      const uint32_t act = __ballot_sync(0xffffffffu, g < le);
+      if (g < le) apply_block(ring[(g - base) & (kBlkRing - 1)], sx, sz, racc, act);
+    }
     prev_lb = lb;
     lb = le;
   }

@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "tab_internal.h"
@@ -91,18 +92,10 @@ static int build_program_stream(int32_t n, const tab_gate* gates, int64_t count,
   return TAB_OK;
 }
 
-int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out,
-                  int mode) {
-  if (n < 1 || n > TAB_MAX_QUBITS) {
-    set_error("n=%d outside [1, %d]", n, TAB_MAX_QUBITS);
-    return TAB_ERANGE;
-  }
-  if (count < 0 || (count > 0 && gates == nullptr)) {
-    set_error("bad gate list (count=%lld)", (long long)count);
-    return TAB_EINVAL;
-  }
-  // ---- validation: nothing is applied unless every word is valid
-  for (int64_t i = 0; i < count; ++i) {
+// Every word of gates[begin, end) is a valid gate for n qubits (index i in
+// messages is the position in the whole list).
+static int validate(int32_t n, const tab_gate* gates, int64_t begin, int64_t end) {
+  for (int64_t i = begin; i < end; ++i) {
     const uint64_t g = gates[i];
     const uint32_t op = (uint32_t)(g >> 56);
     const uint64_t q1 = (g >> 28) & 0xFFFFFFFull, q2 = g & 0xFFFFFFFull;
@@ -127,12 +120,93 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
       }
     }
   }
+  return TAB_OK;
+}
+
+// Compile a validated gate list into the forms `mode` names (not kProgStream).
+static int build_range(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out,
+                       int mode);
+
+// Append program Q (compiled for the gates after those of P) to P.
+static void append_program(HostProgram& P, const HostProgram& Q) {
+  const uint32_t op_base = (uint32_t)P.ops.size(), blk_base = (uint32_t)P.blk.size();
+  const uint32_t loff_base = (uint32_t)P.layer_off.size(), boff_base = (uint32_t)P.blk_off.size();
+  const uint32_t meas_base = (uint32_t)P.n_meas;
+  P.ops.insert(P.ops.end(), Q.ops.begin(), Q.ops.end());
+  P.vers.insert(P.vers.end(), Q.vers.begin(), Q.vers.end());
+  P.blk.insert(P.blk.end(), Q.blk.begin(), Q.blk.end());
+  for (uint32_t x : Q.layer_off) P.layer_off.push_back(x + op_base);
+  for (uint32_t x : Q.blk_off) P.blk_off.push_back(x + blk_base);
+  for (Seg s : Q.segs) {
+    s.op_begin += op_base;
+    s.op_end += op_base;
+    s.layer_begin += loff_base;
+    s.layer_end += loff_base;
+    s.blk_begin += boff_base;
+    s.blk_end += boff_base;
+    s.meas_before += meas_base;
+    P.segs.push_back(s);
+  }
+  P.n_gates += Q.n_gates;
+  P.n_meas += Q.n_meas;
+}
+
+int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out,
+                  int mode) {
+  if (n < 1 || n > TAB_MAX_QUBITS) {
+    set_error("n=%d outside [1, %d]", n, TAB_MAX_QUBITS);
+    return TAB_ERANGE;
+  }
+  if (count < 0 || (count > 0 && gates == nullptr)) {
+    set_error("bad gate list (count=%lld)", (long long)count);
+    return TAB_EINVAL;
+  }
+  // Long lists compiled to blocks only (the multi-CTA engines' per-call path)
+  // are cut into chunks that worker threads validate and compile at once;
+  // each chunk's gates become gate runs of their own, appended in order.
+  const int64_t kChunk = 1 << 18;
+  if (mode == kProgBlocks && count >= 2 * kChunk) {
+    const unsigned hw = std::thread::hardware_concurrency();
+    int T = (int)std::min<int64_t>(count / kChunk, std::min<unsigned>(hw ? hw : 1, 16u));
+    if (T >= 2) {
+      std::vector<HostProgram> part((size_t)T);
+      std::vector<int> rcs((size_t)T, TAB_OK);
+      std::vector<std::string> msg((size_t)T);
+      auto work = [&](int t) {
+        const int64_t b = count * t / T, e = count * (t + 1) / T;
+        int rc = validate(n, gates, b, e);
+        if (rc == TAB_OK) rc = build_range(n, gates + b, e - b, &part[(size_t)t], mode);
+        rcs[(size_t)t] = rc;
+        if (rc != TAB_OK) msg[(size_t)t] = last_error();
+      };
+      std::vector<std::thread> th;
+      for (int t = 1; t < T; ++t) th.emplace_back(work, t);
+      work(0);
+      for (auto& x : th) x.join();
+      for (int t = 0; t < T; ++t)
+        if (rcs[(size_t)t] != TAB_OK) {
+          set_error("%s", msg[(size_t)t].c_str());
+          return rcs[(size_t)t];
+        }
+      HostProgram& P = *out;
+      P = std::move(part[0]);
+      for (int t = 1; t < T; ++t) append_program(P, part[(size_t)t]);
+      return TAB_OK;
+    }
+  }
+  const int vrc = validate(n, gates, 0, count);
+  if (vrc != TAB_OK) return vrc;
 
   if (mode & kProgStream) {
     const int rc = build_program_stream(n, gates, count, out);
     out->mode = kProgStream;
     return rc;
   }
+  return build_range(n, gates, count, out, mode);
+}
+
+static int build_range(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out,
+                       int mode) {
   const bool layers = (mode & kProgLayers) != 0, blocks = (mode & kProgBlocks) != 0;
   HostProgram& P = *out;
   P = HostProgram();
@@ -141,7 +215,7 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
   if (layers) P.ops.reserve((size_t)count);
   BlockBuilder bb;
   if (blocks) {
-    bb.reset(n);
+    bb.reset(n, (size_t)count / 2 + 16);
     P.blk.reserve((size_t)count / 2 + 16);
   }
   int64_t run_gates = 0;  // gates in the open gate run
@@ -164,7 +238,7 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
       s.meas_before = (uint32_t)P.n_meas;
       s.layer_begin = s.layer_end = (uint32_t)P.layer_off.size();
       bb.emit(P, s);
-      bb.reset(n);
+      bb.reset(n, 0);
       P.segs.push_back(s);
       return;
     }
@@ -212,7 +286,7 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
     s.layer_end = (uint32_t)P.layer_off.size() - 1;
     if (blocks) {
       bb.emit(P, s);
-      bb.reset(n);
+      bb.reset(n, 0);
     } else {
       s.blk_begin = s.blk_end = (uint32_t)P.blk_off.size();
     }

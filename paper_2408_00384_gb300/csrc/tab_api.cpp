@@ -48,6 +48,7 @@ struct tab_s {
   uint8_t* log = nullptr;     // device outcome log
   int64_t log_cap = 0, log_len = 0;
   int64_t launches = 0;
+  int64_t h2d_bytes = 0, d2h_bytes = 0;  // host <-> device copies made for callers
   int sticky = TAB_OK;        // latched device error
   int engine = TAB_ENGINE_AUTO;
   // pinned staging area for program uploads (one H2D copy per call)
@@ -412,6 +413,7 @@ int upload_staged(tab_t h, const HostProgram& hp, DevProg* d) {
   uint8_t* dev = nullptr;
   CU(cudaMallocAsync((void**)&dev, total, h->stream));
   CU(cudaMemcpyAsync(dev, st, total, cudaMemcpyHostToDevice, h->stream));
+  h->h2d_bytes += (int64_t)total;
   CU(cudaEventRecord(h->stg_ev, h->stream));
   h->stg_pending = true;
   d->base = dev;
@@ -752,6 +754,7 @@ int tab_read_outcomes(tab_t h, uint8_t* out, int64_t max, int64_t* count) {
       return TAB_EINVAL;
     }
     CU(cudaMemcpyAsync(out, h->log, (size_t)nb, cudaMemcpyDeviceToHost, h->stream));
+    h->d2h_bytes += (int64_t)nb;
   }
   return poll_device_error(h);
 }
@@ -793,6 +796,14 @@ int tab_engine_resolved(tab_t h, int* engine, int* ctas) {
   return TAB_OK;
 }
 
+int tab_transfer_bytes(tab_t h, int64_t* h2d, int64_t* d2h) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (h2d) *h2d = h->h2d_bytes;
+  if (d2h) *d2h = h->d2h_bytes;
+  return TAB_OK;
+}
+
 int tab_kernel_launches(tab_t h, int64_t* count) {
   if (!h || !count) {
     set_error("null argument");
@@ -817,6 +828,7 @@ int tab_export(tab_t h, uint8_t* x, uint8_t* z, uint8_t* r) {
   CU(cudaMemcpyAsync(x, d, cells, cudaMemcpyDeviceToHost, h->stream));
   CU(cudaMemcpyAsync(z, d + cells, cells, cudaMemcpyDeviceToHost, h->stream));
   CU(cudaMemcpyAsync(r, d + 2 * cells, rows, cudaMemcpyDeviceToHost, h->stream));
+  h->d2h_bytes += (int64_t)(2 * cells + rows);
   CU(cudaFreeAsync(d, h->stream));
   return poll_device_error(h);
 }
@@ -834,6 +846,7 @@ int tab_import(tab_t h, const uint8_t* x, const uint8_t* z, const uint8_t* r, ui
   CU(cudaMemcpyAsync(d, x, cells, cudaMemcpyHostToDevice, h->stream));
   CU(cudaMemcpyAsync(d + cells, z, cells, cudaMemcpyHostToDevice, h->stream));
   CU(cudaMemcpyAsync(d + 2 * cells, r, rows, cudaMemcpyHostToDevice, h->stream));
+  h->h2d_bytes += (int64_t)(2 * cells + rows);
   CU(launch_pack(h->X, h->Z, h->R, d, d + cells, d + 2 * cells, h->n, h->Wh, h->stream));
   h->launches++;
   CU(cudaFreeAsync(d, h->stream));

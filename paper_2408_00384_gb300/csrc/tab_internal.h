@@ -87,14 +87,14 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
 
 // Block compiler for one gate run at a time (blocks.cpp).
 struct BlkRec {
-  uint32_t qa, qb;
+  uint16_t qa, qb;
   int32_t layer;
   uint8_t has_b, ent, dir, swp, dead;
-  uint32_t U[2], V[2];
+  uint8_t U[2], V[2];
 };
 class BlockBuilder {
  public:
-  void reset(int32_t n);                          // start a gate run
+  void reset(int32_t n, size_t hint);             // start a gate run (hint: blocks)
   void add(uint32_t op, uint32_t a, uint32_t b);  // next gate of the run (tab_op)
   void emit(HostProgram& P, Seg& s);              // append the run's blocks
  private:

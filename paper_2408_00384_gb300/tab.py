@@ -70,6 +70,7 @@ _sig("tab_clear_outcomes", ctypes.c_int, [_vp])
 _sig("tab_kernel_launches", ctypes.c_int, [_vp, _P(_i64)])
 _sig("tab_set_engine", ctypes.c_int, [_vp, ctypes.c_int])
 _sig("tab_engine_resolved", ctypes.c_int, [_vp, _P(ctypes.c_int), _P(ctypes.c_int)])
+_sig("tab_transfer_bytes", ctypes.c_int, [_vp, _P(_i64), _P(_i64)])
 _sig("tab_measure_noalloc", ctypes.c_int, [_vp, _vp, _i32, _i32, _vp])
 _sig("tab_export", ctypes.c_int, [_vp, _vp, _vp, _vp])
 _sig("tab_import", ctypes.c_int, [_vp, _vp, _vp, _vp, _u64])
@@ -206,6 +207,12 @@ class Tableau:
     def set_engine(self, engine: int):
         """One of the ENGINE_* constants (bit-identical results)."""
         _check(_L.tab_set_engine(self._h, engine))
+
+    def transfer_bytes(self):
+        """(host->device, device->host) bytes this handle has copied for callers."""
+        a, b = _i64(0), _i64(0)
+        _check(_L.tab_transfer_bytes(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def engine_resolved(self):
         """(engine, ctas) that a run of measurements takes on this handle."""

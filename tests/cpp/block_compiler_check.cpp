@@ -104,6 +104,35 @@ int main() {
     if (X != X2 || Z != Z2 || r != r2) { if (bad < 5) printf("mismatch case %d n=%d ng=%d\n", t, n, ng); ++bad; }
   }
   printf("cases %d bad %d gates %lld blocks %lld superlayers %lld\n", cases, bad, gates_total, blocks, layers);
+  // a list long enough to be compiled in chunks by worker threads (each chunk
+  // its own gate runs, appended in order)
+  {
+    const int n = 300, ng = 600000;
+    std::vector<tab_gate> g;
+    for (int i = 0; i < ng; ++i) {
+      uint32_t op = 1 + (uint32_t)(rng() % 9);
+      uint32_t a = (uint32_t)(rng() % n), b = (uint32_t)(rng() % n);
+      if (op >= TAB_CNOT) while (b == a) b = (uint32_t)(rng() % n);
+      g.push_back(tab_make_gate(op, a, op >= TAB_CNOT ? b : 0));
+    }
+    HostProgram hp;
+    if (build_program(n, g.data(), (int64_t)g.size(), &hp, kProgBlocks) != TAB_OK) return 1;
+    std::vector<uint32_t> X(n), Z(n);
+    for (int a = 0; a < n; ++a) { X[a] = (uint32_t)rng(); Z[a] = (uint32_t)rng(); }
+    uint32_t r = (uint32_t)rng(), r2 = r;
+    std::vector<uint32_t> X2 = X, Z2 = Z;
+    for (auto w : g) gate((uint32_t)(w >> 56), (uint32_t)((w >> 28) & 0xFFFFFFF), (uint32_t)(w & 0xFFFFFFF), X, Z, r);
+    int runs = 0;
+    for (const Seg& s : hp.segs) {
+      if (s.kind != 0) continue;
+      ++runs;
+      for (uint32_t L = s.blk_begin; L < s.blk_end; ++L)
+        for (uint32_t i = hp.blk_off[L]; i < hp.blk_off[L + 1]; ++i) blockh(hp.blk[i], X2, Z2, r2);
+    }
+    const bool ok = X == X2 && Z == Z2 && r == r2 && hp.n_gates == ng;
+    printf("long list: %d gates, %d gate runs, %s\n", ng, runs, ok ? "equal" : "MISMATCH");
+    if (!ok) ++bad;
+  }
   // random-layer circuit shape: n=1000, 50 layers, H/S per qubit, n/2 CNOT:CZ
   // 3:1 -- one super-layer per layer
   {

@@ -29,7 +29,7 @@ def test_block_compiler_matches_gate_rules(tmp_path):
     if cxx is None or inc is None:
         pytest.skip("needs g++ and the CUDA headers")
     exe = str(tmp_path / "block_compiler_check")
-    cmd = [cxx, "-O2", "-std=c++17", "-I", inc, "-I", CSRC, "-I", os.path.join(ROOT, "include"),
+    cmd = [cxx, "-O2", "-std=c++17", "-pthread", "-I", inc, "-I", CSRC, "-I", os.path.join(ROOT, "include"),
            os.path.join(HERE, "cpp", "block_compiler_check.cpp"),
            os.path.join(CSRC, "program.cpp"), os.path.join(CSRC, "blocks.cpp"), "-o", exe]
     subprocess.run(cmd, check=True, capture_output=True, text=True)
