@@ -113,18 +113,17 @@ def workload(name, rank):
     return c, desc
 
 
-def split_program(c):
-    """(gate words, measurement words) of a circuit whose measurements are all
-    at the end; None if measurements are interleaved."""
+def split_runs(c):
+    """Maximal runs of gates and of measurements of a circuit, in program
+    order: [("gates", words), ("measure", words), ...]."""
     from workloads import circuits as C
     op, _, _ = C.decode(c.gates)
     m = np.isin(op, C.MEASURE)
-    if not m.any():
-        return c.gates, c.gates[:0]
-    first = int(np.argmax(m))
-    if m[first:].all():
-        return c.gates[:first], c.gates[first:]
-    return None
+    if m.size == 0:
+        return []
+    cuts = np.flatnonzero(np.diff(m.astype(np.int8))) + 1
+    bounds = [0] + cuts.tolist() + [int(m.size)]
+    return [("measure" if m[a] else "gates", c.gates[a:b]) for a, b in zip(bounds[:-1], bounds[1:])]
 
 
 # ------------------------------------------------------------------ clocks --
@@ -261,19 +260,17 @@ def run_plain(args, ws, rank, local):
 
     torch.cuda.set_device(local)
     c, desc = workload(args.workload, rank)
-    parts = split_program(c)
+    runs = split_runs(c)
     stream = torch.cuda.Stream()
     t = tab.Tableau(c.n, stream=stream)
     eng = {"auto": tab.ENGINE_AUTO, "single": tab.ENGINE_SINGLE_CTA, "cluster": tab.ENGINE_CLUSTER,
            "grid": tab.ENGINE_GRID, "stream": tab.ENGINE_STREAM}
     t.set_engine(eng[args.engine])
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    if parts is not None:
-        progs = [tab.Program(c.n, parts[0]), tab.Program(c.n, parts[1])]
-        kinds = ["gates", "measure"]
-    else:
-        progs = [tab.Program(c.n, c.gates)]
-        kinds = ["program"]
+    # one program per run of gates / of measurements, timed separately (the
+    # same launches as one program of all the runs)
+    progs = [tab.Program(c.n, words) for _, words in runs]
+    kinds = [k for k, _ in runs]
 
     def step(evs=None):
         if evs:
@@ -307,8 +304,10 @@ def run_plain(args, ws, rank, local):
     t.sync()
     launches = t.launches - launches0
     per_step = [all_evs[s][0].elapsed_time(all_evs[s][-1]) for s in range(args.steps)]
-    per_kind = {k: [all_evs[s][i].elapsed_time(all_evs[s][i + 1]) for s in range(args.steps)]
-                for i, k in enumerate(kinds)}
+    per_kind = {}
+    for k in set(kinds):
+        per_kind[k] = [sum(all_evs[s][i].elapsed_time(all_evs[s][i + 1])
+                           for i, kk in enumerate(kinds) if kk == k) for s in range(args.steps)]
     ms_local = statistics.mean(per_step)
     ms = allreduce_max(ms_local, ws)
     value = ws * c.n_gates / (ms / 1000.0)
@@ -354,6 +353,7 @@ def run_plain(args, ws, rank, local):
     dom = max(kind_ms, key=kind_ms.get)
     n = c.n
     words = 2.0 * n / 32.0  # 32-row words of the 2n tableau rows
+    eng_res = t.engine_resolved()[0]
     if dom == "measure":
         # a random-outcome measurement is a rowsum of row p into the rows of
         # S' on every column where row p is not I (3/4 of the n columns for a
@@ -362,7 +362,7 @@ def run_plain(args, ws, rank, local):
         alg = 6.0 * 0.75 * n * words * c.n_meas
         kname = {tab.ENGINE_SINGLE_CTA: "k_sct_program", tab.ENGINE_CLUSTER: "k_measure_cluster",
                  tab.ENGINE_GRID: "k_measure_resident",
-                 tab.ENGINE_STREAM: "k_measure"}[t.engine_resolved()[0]]
+                 tab.ENGINE_STREAM: "k_measure"}[eng_res]
     else:
         # logic ops of each gate rule on one 32-row word (x, z, r):
         # X/Z 1, Y 2, H 2, S 3, S^dag 3, CNOT 6, CZ 6, SWAP 0
@@ -370,18 +370,30 @@ def run_plain(args, ws, rank, local):
         op, _, _ = C.decode(c.gates)
         hist = np.bincount(op.astype(np.int64), minlength=16)
         alg = words * float(sum(opsof.get(i, 0) * int(hist[i]) for i in range(16)))
-        kname = "k_gates_block"
+        kname = "k_sct_program" if eng_res == tab.ENGINE_SINGLE_CTA else "k_gates_block"
     sm_mhz = clk.get("sm_mhz") or 2070.0
-    peak_tops = GB300_SMS * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12
-    achieved = alg / (kind_ms[dom] / 1000.0) / 1e12
-    roof = {"kernel": kname, "bound": "alu", "unit": "Top/s", "achieved": achieved,
-            "peak": peak_tops, "frac": achieved / peak_tops,
-            "peak_source": f"{GB300_SMS} SMs x {ALU_LANES_PER_SM} INT32 lanes x {sm_mhz:.0f} MHz "
-                           "(unit counts and the sampled SM clock)",
-            "traffic": TRAFFIC_BYTES.get(kname),
-            "kernel_ms": kind_ms,
-            "hbm_peak_gbs": pk.get("hbm_gbs", FALLBACK_HBM_GBS),
-            "hbm_peak_source": src}
+    if kname == "k_measure":
+        # the streaming engine sweeps the tableau in HBM/L2: a random
+        # measurement reads and writes the ~3/4 n supported columns, 2 planes
+        # of 2n/8 bytes each, ~0.75 n^2 bytes
+        alg_bytes = 0.75 * n * n * c.n_meas
+        achieved = alg_bytes / (kind_ms[dom] / 1000.0) / 1e9
+        peak = pk.get("hbm_gbs", FALLBACK_HBM_GBS)
+        roof = {"kernel": kname, "bound": "hbm", "unit": "GB/s", "achieved": achieved,
+                "peak": peak, "frac": achieved / peak,
+                "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": TRAFFIC_BYTES.get(kname), "kernel_ms": kind_ms}
+    else:
+        peak_tops = GB300_SMS * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+        achieved = alg / (kind_ms[dom] / 1000.0) / 1e12
+        roof = {"kernel": kname, "bound": "alu", "unit": "Top/s", "achieved": achieved,
+                "peak": peak_tops, "frac": achieved / peak_tops,
+                "peak_source": f"{GB300_SMS} SMs x {ALU_LANES_PER_SM} INT32 lanes x {sm_mhz:.0f} "
+                               "MHz (unit counts and the sampled SM clock)",
+                "traffic": TRAFFIC_BYTES.get(kname),
+                "kernel_ms": kind_ms,
+                "hbm_peak_gbs": pk.get("hbm_gbs", FALLBACK_HBM_GBS),
+                "hbm_peak_source": src}
 
     line = {
         "metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": ws,
@@ -426,6 +438,9 @@ def run_batched(args, ws, rank, local):
     out = torch.empty(max(info["out_bytes"], 1), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    # autotune the persistent launch's CTA shape on this batch (untimed)
+    tuned_threads, tuned_ms = b.tune(C.PHILOX_SEED, out.data_ptr(), stream)
+    launch = b.config()
     for _ in range(args.warmup):
         b.exec(C.PHILOX_SEED, out.data_ptr(), stream)
     torch.cuda.synchronize()
@@ -477,7 +492,10 @@ def run_batched(args, ws, rank, local):
         "config": {"workload": f"batched: {len(circs)} random-layer circuits, n ~ U[16,512], "
                                "depth n, 1-64 shots, final MZ on all qubits",
                    "gates": info["n_gates"], "measurements": info["n_meas"],
-                   "l2": "flushed before every timed step (256 MB device write)"},
+                   "l2": "flushed before every timed step (256 MB device write)",
+                   "launch": launch,
+                   "autotune": {"threads": tuned_threads, "best_run_ms": tuned_ms,
+                                "tried": "128/256/512/1024 threads per CTA, one full run each"}},
         "gpu_launches": b.launches * args.steps, "clocks": clk, "roofline": None, "e2e": None,
         "plain_path": {"ms_estimated": plain_est_ms,
                        "gates_per_s": info["n_gates"] / (plain_est_ms / 1000.0),

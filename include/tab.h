@@ -274,6 +274,19 @@ int tab_batch_info(tab_batch_t b, int64_t *n_gates, int64_t *n_meas, int64_t *ou
 int tab_batch_exec(tab_batch_t b, uint64_t seed, uint8_t *dev_out, void *cuda_stream);
 /* Number of kernels one tab_batch_exec launches. */
 int tab_batch_launches(tab_batch_t b, int64_t *count);
+/* Autotuner: runs the whole batch once per CTA shape the persistent kernel is
+ * built for (128, 256, 512 or 1024 threads per CTA; shared memory sized to
+ * the largest tableau; as many CTAs as fit on the GPU), timed with events on
+ * cuda_stream, and keeps the fastest for later tab_batch_exec replays.  Each
+ * run writes the outcomes an exec with this seed writes (dev_out as for
+ * tab_batch_exec).  Synchronises cuda_stream.  *threads_out / *best_ms_out
+ * (either may be null) get the choice and its time.  TAB_EDEVICE /
+ * TAB_ETIMEOUT if a run reports a device error. */
+int tab_batch_tune(tab_batch_t b, uint64_t seed, uint8_t *dev_out, void *cuda_stream,
+                   int32_t *threads_out, float *best_ms_out);
+/* Current CTA shape of the batch's launch (threads per CTA, CTAs, dynamic
+ * shared memory bytes); any pointer may be null. */
+int tab_batch_config(tab_batch_t b, int32_t *threads, int32_t *ctas, int64_t *smem_bytes);
 
 /* ---- serving: continuous batching of circuit requests -------------------- */
 

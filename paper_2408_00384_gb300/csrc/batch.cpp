@@ -39,6 +39,8 @@ struct tab_batch_s {
   int max_n = 1;
   size_t smem = 0;
   int ctas = 1;
+  int threads = kBatchDefaultThreads;  // CTA shape (set by tab_batch_tune)
+  int sms = 1;
   int nitems = 0;
   // device
   void* dmem = nullptr;
@@ -53,6 +55,7 @@ struct tab_batch_s {
 namespace {
 
 size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+int configure(tab_batch_s* B, int threads);
 
 int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offsets,
                 tab_batch_s* B) {
@@ -177,11 +180,24 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
   A.err = reinterpret_cast<int*>(p + 4);
   A.ready = reinterpret_cast<int*>(p + 16);
   A.nitems = B->nitems;
-  B->smem = sct_smem_bytes(B->max_n);
-  int dev = 0, sms = 1;
+  int dev = 0;
   CUB(cudaGetDevice(&dev));
-  CUB(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  B->ctas = std::max(1, std::min(B->nitems, sms * batch_ctas_per_sm(B->smem)));
+  CUB(cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, dev));
+  return configure(B, kBatchDefaultThreads);
+}
+
+// CTA shape of the persistent launch: `threads` per CTA, shared memory for
+// the batch's largest tableau, and as many CTAs as fit on the GPU at once.
+int configure(tab_batch_s* B, int threads) {
+  const size_t smem = sct_smem_bytes(B->max_n, threads);
+  const int occ = batch_ctas_per_sm(threads, smem);
+  if (occ <= 0) {
+    set_error("the batched kernel does not launch with %d threads", threads);
+    return TAB_ECUDA;
+  }
+  B->threads = threads;
+  B->smem = smem;
+  B->ctas = std::max(1, std::min(B->nitems, B->sms * occ));
   return TAB_OK;
 }
 
@@ -198,9 +214,9 @@ int make_graph(tab_batch_s* B) {
   CUB(cudaGraphAddMemsetNode(&mnode, B->graph, nullptr, 0, &mp));
   void* kargs[] = {&B->args};
   cudaKernelNodeParams kp{};
-  kp.func = const_cast<void*>(batch_kernel_ptr());
+  kp.func = const_cast<void*>(batch_kernel_ptr(B->threads));
   kp.gridDim = dim3(B->ctas);
-  kp.blockDim = dim3(batch_threads());
+  kp.blockDim = dim3(B->threads);
   kp.sharedMemBytes = (unsigned)B->smem;
   kp.kernelParams = kargs;
   CUB(cudaGraphAddKernelNode(&B->knode, B->graph, &mnode, 1, &kp));
@@ -224,7 +240,7 @@ int tab_batch_create(const tab_circuit* circuits, int32_t m, tab_batch_t* out) {
     return TAB_ENOMEM;
   }
   int rc = build_batch(circuits, m, nullptr, B);
-  if (rc == TAB_OK) rc = prepare_batch_kernel(B->smem) == cudaSuccess ? TAB_OK : TAB_ECUDA;
+  if (rc == TAB_OK) rc = prepare_batch_kernel(B->threads) == cudaSuccess ? TAB_OK : TAB_ECUDA;
   if (rc != TAB_OK) {
     tab_batch_destroy(B);
     return rc;
@@ -281,9 +297,9 @@ int tab_batch_exec(tab_batch_t B, uint64_t seed, uint8_t* dev_out, void* cuda_st
   } else {
     void* kargs[] = {&B->args};
     cudaKernelNodeParams kp{};
-    kp.func = const_cast<void*>(batch_kernel_ptr());
+    kp.func = const_cast<void*>(batch_kernel_ptr(B->threads));
     kp.gridDim = dim3(B->ctas);
-    kp.blockDim = dim3(batch_threads());
+    kp.blockDim = dim3(B->threads);
     kp.sharedMemBytes = (unsigned)B->smem;
     kp.kernelParams = kargs;
     CUB(cudaGraphExecKernelNodeSetParams(B->gexec, B->knode, &kp));
@@ -320,7 +336,7 @@ int tab_batch_run(const tab_circuit* circuits, int32_t m, uint64_t seed, uint8_t
     return TAB_ENOMEM;
   }
   int rc = build_batch(circuits, m, out_offsets, B);
-  if (rc == TAB_OK && prepare_batch_kernel(B->smem) != cudaSuccess) {
+  if (rc == TAB_OK && prepare_batch_kernel(B->threads) != cudaSuccess) {
     set_error("kernel attribute setup failed");
     rc = TAB_ECUDA;
   }
@@ -362,6 +378,82 @@ int tab_batch_run(const tab_circuit* circuits, int32_t m, uint64_t seed, uint8_t
   if (dout) cudaFree(dout);
   tab_batch_destroy(B);
   return rc;
+}
+
+// Autotuner: run the whole batch once with every CTA shape the kernel is
+// built for (threads per CTA; shared memory sized to the largest tableau; as
+// many CTAs as fit), time each run with events on `cuda_stream`, keep the
+// fastest for later tab_batch_exec replays.  The runs write the same outcomes
+// as an exec with this seed would.
+int tab_batch_tune(tab_batch_t B, uint64_t seed, uint8_t* dev_out, void* cuda_stream,
+                   int32_t* threads_out, float* best_ms_out) {
+  if (!B) {
+    set_error("null batch");
+    return TAB_EINVAL;
+  }
+  if (B->out_bytes > 0 && !dev_out) {
+    set_error("null output buffer");
+    return TAB_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUB(cudaEventCreate(&e0));
+  CUB(cudaEventCreate(&e1));
+  int best = -1;
+  float best_ms = 0.f;
+  int rc = TAB_OK;
+  for (int threads : kBatchThreadChoices) {
+    if (configure(B, threads) != TAB_OK) continue;
+    B->args.seed = seed;
+    B->args.out = dev_out;
+    void* kargs[] = {&B->args};
+    cudaError_t e = cudaMemsetAsync(B->ctl, 0, B->ctl_bytes, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess)
+      e = cudaLaunchKernel(batch_kernel_ptr(threads), dim3(B->ctas), dim3(threads), kargs, B->smem,
+                           st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e != cudaSuccess) {
+      set_error("tuning launch failed: %s", cudaGetErrorString(e));
+      rc = TAB_ECUDA;
+      break;
+    }
+    rc = batch_error(B, cuda_stream);
+    if (rc != TAB_OK) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best < 0 || ms < best_ms) {
+      best = threads;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != TAB_OK) return rc;
+  if (best < 0) {
+    set_error("no CTA shape of the batched kernel launches");
+    return TAB_ECUDA;
+  }
+  rc = configure(B, best);
+  if (rc != TAB_OK) return rc;
+  if (B->gexec) cudaGraphExecDestroy(B->gexec);  // rebuilt with the new shape
+  if (B->graph) cudaGraphDestroy(B->graph);
+  B->gexec = nullptr;
+  B->graph = nullptr;
+  if (threads_out) *threads_out = best;
+  if (best_ms_out) *best_ms_out = best_ms;
+  return TAB_OK;
+}
+
+int tab_batch_config(tab_batch_t B, int32_t* threads, int32_t* ctas, int64_t* smem_bytes) {
+  if (!B) {
+    set_error("null batch");
+    return TAB_EINVAL;
+  }
+  if (threads) *threads = B->threads;
+  if (ctas) *ctas = B->ctas;
+  if (smem_bytes) *smem_bytes = (int64_t)B->smem;
+  return TAB_OK;
 }
 
 }  // extern "C"

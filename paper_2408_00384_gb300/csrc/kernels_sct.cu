@@ -43,9 +43,10 @@ size_t sct_image_words(int n) {
   return ((size_t)2 * n * sct_wp(n) + sct_wc(n) + 3) & ~(size_t)3;
 }
 
-size_t sct_smem_bytes(int n) {
+size_t sct_smem_bytes(int n, int threads) {
   const int Wc = sct_wc(n);
-  const int GG = kSctThreads / Wc;
+  int GG = threads / Wc;
+  if (GG < 1) GG = 1;
   return sizeof(uint32_t) *
          ((size_t)2 * n * sct_wp(n) + 2 * (size_t)Wc + (size_t)n + 2 * (size_t)GG * Wc);
 }
@@ -60,7 +61,8 @@ __device__ __forceinline__ void sct_setup(Sct& s, uint32_t* base, int n) {
   s.Whc = sct_whc(n);
   s.Wc = 2 * s.Whc;
   s.Wp = s.Wc | 1;
-  s.GG = kSctThreads / s.Wc;
+  s.GG = (int)blockDim.x / s.Wc;
+  if (s.GG < 1) s.GG = 1;
   if (s.GG > n) s.GG = n;  // a group per column at most
   s.X = base;
   s.Z = s.X + (size_t)n * s.Wp;
@@ -373,11 +375,11 @@ cudaError_t launch_sct_program(const SctProgArgs& A, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_sct_program, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sct_smem_bytes(TAB_BATCH_MAX_QUBITS));
+                                         (int)sct_smem_bytes(TAB_BATCH_MAX_QUBITS, kSctThreads));
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_sct_program<<<1, kSctThreads, sct_smem_bytes(A.n), st>>>(A);
+  k_sct_program<<<1, kSctThreads, sct_smem_bytes(A.n, kSctThreads), st>>>(A);
   return cudaGetLastError();
 }
 
@@ -389,7 +391,8 @@ cudaError_t launch_sct_program(const SctProgArgs& A, cudaStream_t st) {
 // Items are dequeued in order from one atomic counter; every prefix item is
 // dequeued before any shot item, and prefix items never wait, so every wait
 // ends.  Waits are bounded anyway and latch DERR_TIMEOUT.
-__global__ void __launch_bounds__(kSctThreads) k_batch(BatchArgs A) {
+template <int T>
+__global__ void __launch_bounds__(T) k_batch(BatchArgs A) {
   extern __shared__ uint32_t smem[];
   __shared__ unsigned int s_item;
   __shared__ int s_stop;
@@ -451,21 +454,40 @@ __global__ void __launch_bounds__(kSctThreads) k_batch(BatchArgs A) {
   }
 }
 
-cudaError_t prepare_batch_kernel(size_t smem) {
-  (void)smem;
-  return cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sct_smem_bytes(TAB_BATCH_MAX_QUBITS));
+// Thread counts the batched kernel is built for; the autotuner
+// (tab_batch_tune) times each on the batch itself.
+static const void* batch_kernel_for(int threads) {
+  switch (threads) {
+    case 128: return (const void*)k_batch<128>;
+    case 256: return (const void*)k_batch<256>;
+    case 512: return (const void*)k_batch<512>;
+    case 1024: return (const void*)k_batch<1024>;
+    default: return nullptr;
+  }
 }
 
-const void* batch_kernel_ptr() { return (const void*)k_batch; }
-int batch_threads() { return kSctThreads; }
+const void* batch_kernel_ptr(int threads) { return batch_kernel_for(threads); }
 
-int batch_ctas_per_sm(size_t smem) {
-  if (prepare_batch_kernel(smem) != cudaSuccess) return 1;
+cudaError_t prepare_batch_kernel(int threads) {
+  const void* fn = batch_kernel_for(threads);
+  if (!fn) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sct_smem_bytes(TAB_BATCH_MAX_QUBITS, threads));
+}
+
+// Resident CTAs per SM for `threads` and `smem` bytes (0: does not launch).
+int batch_ctas_per_sm(int threads, size_t smem) {
+  const void* fn = batch_kernel_for(threads);
+  if (!fn || prepare_batch_kernel(threads) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   int v = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch, kSctThreads, smem) != cudaSuccess)
-    v = 1;
-  return v < 1 ? 1 : v;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, fn, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    v = 0;
+  }
+  return v < 0 ? 0 : v;
 }
 
 }  // namespace tab

@@ -49,11 +49,14 @@ struct BatchArgs {
 };
 
 size_t sct_image_words(int n);
-size_t sct_smem_bytes(int n);
+// Shared memory of one tableau of n qubits run by a CTA of `threads`.
+size_t sct_smem_bytes(int n, int threads);
 cudaError_t launch_sct_program(const SctProgArgs& A, cudaStream_t st);
-int batch_ctas_per_sm(size_t smem);
-cudaError_t prepare_batch_kernel(size_t smem);
-const void* batch_kernel_ptr();
-int batch_threads();
+// Batched kernel instances: threads per CTA in {128, 256, 512, 1024}.
+constexpr int kBatchThreadChoices[4] = {128, 256, 512, 1024};
+constexpr int kBatchDefaultThreads = 512;
+int batch_ctas_per_sm(int threads, size_t smem);
+cudaError_t prepare_batch_kernel(int threads);
+const void* batch_kernel_ptr(int threads);
 
 }  // namespace tab

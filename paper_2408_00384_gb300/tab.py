@@ -81,6 +81,8 @@ _sig("tab_batch_destroy", ctypes.c_int, [_vp])
 _sig("tab_batch_info", ctypes.c_int, [_vp, _P(_i64), _P(_i64), _P(_i64)])
 _sig("tab_batch_exec", ctypes.c_int, [_vp, _u64, _vp, _vp])
 _sig("tab_batch_launches", ctypes.c_int, [_vp, _P(_i64)])
+_sig("tab_batch_tune", ctypes.c_int, [_vp, _u64, _vp, _vp, _P(_i32), _P(ctypes.c_float)])
+_sig("tab_batch_config", ctypes.c_int, [_vp, _P(_i32), _P(_i32), _P(_i64)])
 
 
 class TabServerConfig(ctypes.Structure):
@@ -334,6 +336,20 @@ class Batch:
 
     def exec(self, seed: int, dev_out_ptr: int, stream=None):
         _check(_L.tab_batch_exec(self._h, seed, dev_out_ptr, _stream_handle(stream)))
+
+    def tune(self, seed: int, dev_out_ptr: int, stream=None):
+        """Autotune the launch's CTA shape on this batch (tab_batch_tune);
+        returns (threads per CTA, time of the best run in ms)."""
+        t, ms = _i32(), ctypes.c_float()
+        _check(_L.tab_batch_tune(self._h, seed, dev_out_ptr, _stream_handle(stream),
+                                 ctypes.byref(t), ctypes.byref(ms)))
+        return t.value, ms.value
+
+    def config(self):
+        """Current launch shape: {"threads", "ctas", "smem_bytes"}."""
+        t, c, s = _i32(), _i32(), _i64()
+        _check(_L.tab_batch_config(self._h, ctypes.byref(t), ctypes.byref(c), ctypes.byref(s)))
+        return {"threads": t.value, "ctas": c.value, "smem_bytes": s.value}
 
     @property
     def launches(self) -> int:

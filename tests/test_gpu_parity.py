@@ -287,6 +287,31 @@ def test_batch_config4_sample():
             assert np.array_equal(got[s], want), (n, cid, s)
 
 
+def test_batch_autotune_keeps_outcomes():
+    """Every CTA shape the autotuner tries writes the same outcomes, and the
+    shape it keeps replays them bit for bit (first circuit also vs the oracle)."""
+    import torch
+    circs = C.config4(only=list(range(3, 4096, 128)))
+    circuits = [(c.n, c.gates, min(c.shots, 3), c.circuit_id) for c in circs]
+    b = tab.Batch(circuits)
+    nbytes = max(b.info()["out_bytes"], 1)
+    out0 = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    out1 = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    out2 = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    b.exec(C.PHILOX_SEED, out0.data_ptr(), stream)
+    threads, ms = b.tune(C.PHILOX_SEED, out1.data_ptr(), stream)
+    assert threads in (128, 256, 512, 1024) and ms > 0
+    assert b.config()["threads"] == threads
+    b.exec(C.PHILOX_SEED, out2.data_ptr(), stream)
+    torch.cuda.synchronize()
+    assert torch.equal(out0, out1) and torch.equal(out0, out2)
+    n, g, shots, cid = circuits[0]
+    want, _ = oracle.run_circuit(n, g, seed=C.PHILOX_SEED, circuit_id=cid, shot=0)
+    assert np.array_equal(out2[:want.size].cpu().numpy(), want)
+    b.close()
+
+
 _FLOW_KERNEL_SCRIPT = r"""
 import sys, numpy as np
 sys.path.insert(0, %r)
