@@ -483,6 +483,34 @@ def run_batched(args, ws, rank, local):
             plain_ms += e0.elapsed_time(e1)
         prog.close()
     plain_est_ms = plain_ms * stride
+
+    # the terminal-measurement sampler on the same batch (reported apart from
+    # the per-shot numbers): same outcome bytes, checked here
+    sb = tab.Batch(circuits, sample_terminal=True)
+    s_out = torch.empty_like(out)
+    s_threads, _ = sb.tune(C.PHILOX_SEED, s_out.data_ptr(), stream)
+    b.exec(C.PHILOX_SEED, out.data_ptr(), stream)
+    for _ in range(max(args.warmup, 1)):
+        sb.exec(C.PHILOX_SEED, s_out.data_ptr(), stream)
+    torch.cuda.synchronize()
+    same = bool(torch.equal(out, s_out))
+    s_evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(args.steps)]
+    for s in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(s & 0xFF)
+        s_evs[s][0].record(stream)
+        sb.exec(C.PHILOX_SEED, s_out.data_ptr(), stream)
+        s_evs[s][1].record(stream)
+    torch.cuda.synchronize()
+    s_ms = allreduce_max(statistics.mean(a.elapsed_time(z) for a, z in s_evs), ws)
+    sampler = {"ms_per_step": s_ms, "gates_per_s": ws * info["n_gates"] / (s_ms / 1000.0),
+               "meas_per_s": ws * info["n_meas"] / (s_ms / 1000.0),
+               "circuits_sampled": sb.sampled, "threads": s_threads,
+               "outcomes_equal_per_shot_run": same,
+               "note": "terminal measurements run once per circuit with affine sign forms, "
+                       "every shot evaluated from its Philox bits"}
+    sb.close()
     line = {
         "metric": METRIC, "value": ws * info["n_gates"] / (ms / 1000.0), "unit": "gates/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -503,6 +531,7 @@ def run_batched(args, ws, rank, local):
                        "sample": f"every {stride}th circuit, all its shots, one launch "
                                  "sequence per shot, CUDA events, x{stride}",
                        "batched_speedup": plain_est_ms / ms},
+        "sampler": sampler,
     }
     return line
 

@@ -265,6 +265,18 @@ int tab_batch_run(const tab_circuit *circuits, int32_t m, uint64_t seed,
 typedef struct tab_batch_s *tab_batch_t;
 
 int tab_batch_create(const tab_circuit *circuits, int32_t m, tab_batch_t *out);
+/* tab_batch_create with options.  TAB_BATCH_SAMPLE_TERMINAL: a circuit whose
+ * measurements all come after its gates (Z without reset) runs them once,
+ * with every sign kept as an affine form over the run's random outcome bits,
+ * and every shot is then evaluated from its own Philox bits -- the same
+ * outcome bits as running each shot (the "shot sampler"; see
+ * tab_batch_sampled for how many circuits qualified).  Other circuits run
+ * per shot as usual.  TAB_EINVAL on unknown flags. */
+enum { TAB_BATCH_SAMPLE_TERMINAL = 1 };
+int tab_batch_create_ex(const tab_circuit *circuits, int32_t m, uint32_t flags,
+                        tab_batch_t *out);
+/* Circuits of the batch that run through the terminal-measurement sampler. */
+int tab_batch_sampled(tab_batch_t b, int32_t *circuits);
 int tab_batch_destroy(tab_batch_t b);
 /* totals: gate ops (once per circuit), measurement ops (over all shots),
  * outcome bytes needed */

@@ -37,6 +37,10 @@ struct tab_batch_s {
   int m = 0;
   int64_t n_gates = 0, n_meas = 0, out_bytes = 0;
   int max_n = 1;
+  bool sample = false;                      // terminal measurements by the sampler
+  int nsampled = 0;
+  std::vector<int32_t> cn, ck, cshots;      // per circuit: n, terminal K, shots
+  std::vector<uint8_t> csampled;
   size_t smem = 0;
   int ctas = 1;
   int threads = kBatchDefaultThreads;  // CTA shape (set by tab_batch_tune)
@@ -56,6 +60,10 @@ namespace {
 
 size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 int configure(tab_batch_s* B, int threads);
+
+// Shared memory a batch kernel CTA of `threads` may take (the device's opt-in
+// maximum less a margin for the kernel's static shared memory).
+constexpr size_t kBatchSmemLimit = 227 * 1024 - 2048;
 
 int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offsets,
                 tab_batch_s* B) {
@@ -97,6 +105,24 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
     bc.cid = tc.circuit_id;
     bc.img_off = img_words;
     img_words += sct_image_words(tc.n);
+    // terminal measurements only (one MZ run after the gates): the sampler
+    // runs them once and evaluates every shot from the outcome forms
+    bc.sampled = 0;
+    if (B->sample && hp.n_meas > 0 && hp.segs.size() == (size_t)bc.n_prefix + 1 &&
+        hp.segs.back().kind == 1) {
+      const Seg& ms = hp.segs.back();
+      bool mz = true;
+      for (uint32_t i = ms.op_begin; i < ms.op_end && mz; ++i) mz = dop(hp.ops[i]) == OP_MZ;
+      const size_t K = (size_t)hp.n_meas, FW = (K + 31) / 32;
+      if (mz && K * (1 + FW) <= sct_image_words(tc.n) &&
+          sct_smem_bytes(tc.n, 1024) + sct_sampler_bytes(tc.n, (int)K, tc.shots) <= kBatchSmemLimit)
+        bc.sampled = 1;
+    }
+    B->nsampled += (int)bc.sampled;
+    B->cn.push_back(tc.n);
+    B->ck.push_back((int32_t)hp.n_meas);
+    B->cshots.push_back(tc.shots);
+    B->csampled.push_back((uint8_t)bc.sampled);
     const int64_t span = (int64_t)tc.shots * hp.n_meas;
     bc.out_off = (uint64_t)(out_offsets ? out_offsets[c] : out_packed);
     out_packed += span;
@@ -117,7 +143,8 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
       segs.push_back(s);
     }
     bc.seg_end = (uint32_t)segs.size();
-    pre_cost[(size_t)c] = pre;
+    // a sampled circuit is one item: prefix, one terminal pass, every shot
+    pre_cost[(size_t)c] = bc.sampled ? pre + rest + (double)tc.shots * hp.n_meas : pre;
     shot_cost[(size_t)c] = rest;
     B->n_gates += hp.n_gates;
     B->n_meas += span;
@@ -135,7 +162,7 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
   std::stable_sort(order.begin(), order.end(),
                    [&](int32_t a, int32_t b) { return shot_cost[(size_t)a] > shot_cost[(size_t)b]; });
   for (int32_t c : order) {
-    if (circs[(size_t)c].n_meas == 0) continue;
+    if (circs[(size_t)c].n_meas == 0 || circs[(size_t)c].sampled) continue;
     for (int32_t s = 0; s < circs[(size_t)c].shots; ++s)
       items.push_back((uint64_t)(uint32_t)c | ((uint64_t)(uint32_t)s << 32));
   }
@@ -189,7 +216,11 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
 // CTA shape of the persistent launch: `threads` per CTA, shared memory for
 // the batch's largest tableau, and as many CTAs as fit on the GPU at once.
 int configure(tab_batch_s* B, int threads) {
-  const size_t smem = sct_smem_bytes(B->max_n, threads);
+  size_t smem = sct_smem_bytes(B->max_n, threads);
+  for (size_t c = 0; c < B->cn.size(); ++c)
+    if (B->csampled[c])
+      smem = std::max(smem, sct_smem_bytes(B->cn[c], threads) +
+                                sct_sampler_bytes(B->cn[c], B->ck[c], B->cshots[c]));
   const int occ = batch_ctas_per_sm(threads, smem);
   if (occ <= 0) {
     set_error("the batched kernel does not launch with %d threads", threads);
@@ -229,8 +260,17 @@ int make_graph(tab_batch_s* B) {
 extern "C" {
 
 int tab_batch_create(const tab_circuit* circuits, int32_t m, tab_batch_t* out) {
+  return tab_batch_create_ex(circuits, m, 0u, out);
+}
+
+int tab_batch_create_ex(const tab_circuit* circuits, int32_t m, uint32_t flags,
+                        tab_batch_t* out) {
   if (!out) {
     set_error("null output pointer");
+    return TAB_EINVAL;
+  }
+  if (flags & ~(uint32_t)TAB_BATCH_SAMPLE_TERMINAL) {
+    set_error("unknown batch flags 0x%x", flags);
     return TAB_EINVAL;
   }
   *out = nullptr;
@@ -239,6 +279,7 @@ int tab_batch_create(const tab_circuit* circuits, int32_t m, tab_batch_t* out) {
     set_error("host allocation failed");
     return TAB_ENOMEM;
   }
+  B->sample = (flags & TAB_BATCH_SAMPLE_TERMINAL) != 0;
   int rc = build_batch(circuits, m, nullptr, B);
   if (rc == TAB_OK) rc = prepare_batch_kernel(B->threads) == cudaSuccess ? TAB_OK : TAB_ECUDA;
   if (rc != TAB_OK) {
@@ -442,6 +483,15 @@ int tab_batch_tune(tab_batch_t B, uint64_t seed, uint8_t* dev_out, void* cuda_st
   B->graph = nullptr;
   if (threads_out) *threads_out = best;
   if (best_ms_out) *best_ms_out = best_ms;
+  return TAB_OK;
+}
+
+int tab_batch_sampled(tab_batch_t B, int32_t* circuits) {
+  if (!B || !circuits) {
+    set_error("null argument");
+    return TAB_EINVAL;
+  }
+  *circuits = B->nsampled;
   return TAB_OK;
 }
 

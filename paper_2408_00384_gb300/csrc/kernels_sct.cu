@@ -43,12 +43,23 @@ size_t sct_image_words(int n) {
   return ((size_t)2 * n * sct_wp(n) + sct_wc(n) + 3) & ~(size_t)3;
 }
 
-size_t sct_smem_bytes(int n, int threads) {
+__host__ __device__ inline size_t sct_smem_words(int n, int threads) {
   const int Wc = sct_wc(n);
   int GG = threads / Wc;
   if (GG < 1) GG = 1;
-  return sizeof(uint32_t) *
-         ((size_t)2 * n * sct_wp(n) + 2 * (size_t)Wc + (size_t)n + 2 * (size_t)GG * Wc);
+  if (GG > n) GG = n;
+  return (size_t)2 * n * sct_wp(n) + 2 * (size_t)Wc + (size_t)n + 2 * (size_t)GG * Wc;
+}
+
+size_t sct_smem_bytes(int n, int threads) { return sizeof(uint32_t) * sct_smem_words(n, threads); }
+
+// Extra shared memory of the terminal-measurement sampler for a circuit of n
+// qubits, K terminal measurements and `shots` shots (sct_form_pass and
+// sct_sample): K coefficient columns, a list of K columns, and one K-bit
+// random vector per shot.
+size_t sct_sampler_bytes(int n, int K, int shots) {
+  const size_t FW = ((size_t)K + 31) / 32;
+  return sizeof(uint32_t) * ((size_t)K * sct_wp(n) + (size_t)K + (size_t)shots * FW);
 }
 
 struct Sct {
@@ -294,6 +305,121 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err)
   return out;
 }
 
+// ------------------------------------------ terminal-measurement sampler ---
+// When a circuit's measurements are all at its end (Z only, no reset), which
+// measurements are random, their pivots and masks, and every X|Z update are
+// the same in every shot: none of them reads a sign or an outcome.  Every
+// sign, and so every deterministic outcome, is then an affine function over
+// GF(2) of the random bits b_0, b_1, ... of the earlier random measurements
+// (a rowsum adds row p's sign plus an X|Z-only term; row p of measurement i
+// becomes b_i).  So the terminal run is done once per circuit with each sign
+// kept as such a form -- R holds the constant part, and column j of F (the
+// tableau's column layout) holds the coefficient of b_j -- and every shot is
+// evaluated from its own Philox bits.  The outcomes are those of running the
+// shot itself, bit for bit.
+//
+// forms[i*(1+FW)]: bit 0 = measurement i is random (outcome b_i), bit 1 =
+// constant of a deterministic outcome; words 1..FW: its coefficients.
+__device__ void sct_form_pass(const Sct& s, const uint32_t* __restrict__ ops, uint32_t op_begin,
+                              int K, uint32_t* F, int* fpl, uint32_t* forms, int FW, int* err) {
+  __shared__ int s_fpw, s_nf;
+  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+  const int Wc = s.Wc, Wp = s.Wp, Whc = s.Whc;
+  const uint32_t lt = (1u << lane) - 1u;
+  for (size_t e = tid; e < (size_t)K * Wp; e += T) F[e] = 0u;
+  __syncthreads();
+  for (int i = 0; i < K; ++i) {
+    const uint32_t code = __ldg(ops + op_begin + i);
+    // X|Z bits, pivot, mask and the constant parts of the signs, with b_i = 0
+    const int c = sct_measure(s, code, 0u, err);
+    // s.sS still holds the measured column's X plane before the measurement
+    if (tid < 32) {
+      const uint32_t v = (tid < Whc) ? s.sS[Whc + tid] : 0u;
+      const uint32_t bal = __ballot_sync(0xffffffffu, v != 0u);
+      if (tid == 0) {
+        s_fpw = bal ? Whc + __ffs(bal) - 1 : -1;
+        s_nf = 0;
+      }
+    }
+    __syncthreads();
+    uint32_t* hdr = forms + (size_t)i * (1 + FW);
+    const int pw = s_fpw;
+    if (pw >= 0) {
+      const int P = pw * 32 + __ffs(s.sS[pw]) - 1;
+      const int wp = pw, wd = (P - 32 * Whc) >> 5;
+      const uint32_t bpm = 1u << (P & 31);
+      // columns whose bit p is set: row p's form has b_j; the others only
+      // lose row p-n's bit (row p-n := row p)
+      for (int j0 = tid - lane; j0 < i; j0 += T) {  // warp-uniform trip count
+        const int j = j0 + lane;
+        const bool f = j < i && (F[(size_t)j * Wp + wp] & bpm);
+        const uint32_t bal = __ballot_sync(0xffffffffu, f);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&s_nf, __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (f) fpl[base + __popc(bal & lt)] = j;
+        else if (j < i) F[(size_t)j * Wp + wd] &= ~bpm;
+      }
+      __syncthreads();
+      const int nf = s_nf;
+      for (int e = tid; e < nf * Wc; e += T) {
+        const int idx = e / Wc, w = e - idx * Wc;
+        uint32_t* col = F + (size_t)fpl[idx] * Wp;
+        uint32_t Sw = s.sS[w];
+        if (w == wp || w == wd) Sw &= ~bpm;  // S' excludes rows p and p-n
+        uint32_t v = col[w] ^ Sw;
+        if (w == wd) v |= bpm;   // row p-n := row p
+        if (w == wp) v &= ~bpm;  // row p := b_i
+        col[w] = v;
+      }
+      if (tid == 0) {
+        F[(size_t)i * Wp + wp] |= bpm;
+        hdr[0] = 1u;
+      }
+    } else {
+      // deterministic: coefficient of b_j = parity of column j over the
+      // stabilizer rows the destabilizer column selects
+      for (int f = warp; f < FW; f += nw) {
+        const int j = f * 32 + lane;
+        uint32_t acc = 0u;
+        if (j < i)
+          for (int hw = 0; hw < Whc; ++hw) acc += __popc(F[(size_t)j * Wp + Whc + hw] & s.sS[hw]);
+        const uint32_t word = __ballot_sync(0xffffffffu, acc & 1u);
+        if (lane == 0) hdr[1 + f] = word;
+      }
+      if (tid == 0) hdr[0] = (uint32_t)c << 1;
+    }
+    __syncthreads();
+  }
+}
+
+// Outcomes of every shot from the forms: random ones are the shot's Philox
+// bits, deterministic ones constant ^ parity(coefficients & bits).
+__device__ void sct_sample(const uint32_t* forms, int K, int FW, int shots, uint64_t seed,
+                           uint64_t cid, uint8_t* out, uint32_t* Bs) {
+  const int tid = threadIdx.x, T = blockDim.x;
+  for (int e = tid; e < shots * FW; e += T) Bs[e] = 0u;
+  __syncthreads();
+  for (int e = tid; e < shots * K; e += T) {
+    const int sh = e / K, i = e - sh * K;
+    if (__ldcg(forms + (size_t)i * (1 + FW)) & 1u) {
+      const uint32_t b = outcome_bit(seed, cid, (uint32_t)sh, (uint64_t)i);
+      out[(size_t)sh * K + i] = (uint8_t)b;
+      if (b) atomicOr(Bs + (size_t)sh * FW + (i >> 5), 1u << (i & 31));
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < shots * K; e += T) {
+    const int sh = e / K, i = e - sh * K;
+    const uint32_t* h = forms + (size_t)i * (1 + FW);
+    const uint32_t hd = __ldcg(h);
+    if (hd & 1u) continue;
+    uint32_t o = (hd >> 1) & 1u;
+    for (int f = 0; f < FW; ++f) o ^= __popc(__ldcg(h + 1 + f) & Bs[(size_t)sh * FW + f]) & 1u;
+    out[(size_t)sh * K + i] = (uint8_t)o;
+  }
+}
+
 // -------------------------------------------- global <-> shared transfers ---
 // Image layout (batched scratch): the shared-memory X, Z planes then R.
 __device__ void sct_store_image(const Sct& s, uint32_t* __restrict__ img) {
@@ -421,6 +547,18 @@ __global__ void __launch_bounds__(T) k_batch(BatchArgs A) {
         const Seg g = A.segs[C.seg_begin];
         sct_gates(s, A.ops, A.layer_off + g.layer_begin, (int)(g.layer_end - g.layer_begin));
       }
+      if (C.sampled) {  // terminal measurements: one pass for every shot
+        const int K = (int)C.n_meas, FW = (K + 31) / 32;
+        uint32_t* F = smem + sct_smem_words(C.n, (int)blockDim.x);
+        int* fpl = reinterpret_cast<int*>(F + (size_t)K * s.Wp);
+        uint32_t* Bs = reinterpret_cast<uint32_t*>(fpl + K);
+        const Seg g = A.segs[C.seg_begin + C.n_prefix];
+        sct_form_pass(s, A.ops, g.op_begin, K, F, fpl, img, FW, A.err);
+        __syncthreads();
+        sct_sample(img, K, FW, C.shots, seed, C.cid, out + C.out_off, Bs);
+        __syncthreads();
+        continue;
+      }
       sct_store_image(s, img);
       __threadfence();
       __syncthreads();
@@ -471,8 +609,9 @@ const void* batch_kernel_ptr(int threads) { return batch_kernel_for(threads); }
 cudaError_t prepare_batch_kernel(int threads) {
   const void* fn = batch_kernel_for(threads);
   if (!fn) return cudaErrorInvalidValue;
+  // the largest tableau, or a sampled circuit's tableau plus its forms
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sct_smem_bytes(TAB_BATCH_MAX_QUBITS, threads));
+                              227 * 1024 - 2048);
 }
 
 // Resident CTAs per SM for `threads` and `smem` bytes (0: does not launch).

@@ -30,7 +30,9 @@ struct BatchCirc {
   uint32_t n_meas;              // measurement ops per shot
   uint64_t cid;
   uint64_t out_off;             // byte offset of shot 0's outcomes
-  uint64_t img_off;             // word offset of the shared-prefix image
+  uint64_t img_off;             // word offset of the shared-prefix image (or the
+                                // outcome forms of a sampled circuit)
+  uint32_t sampled;             // 1: terminal measurements by the sampler
 };
 
 struct BatchArgs {
@@ -51,6 +53,8 @@ struct BatchArgs {
 size_t sct_image_words(int n);
 // Shared memory of one tableau of n qubits run by a CTA of `threads`.
 size_t sct_smem_bytes(int n, int threads);
+// Extra shared memory of the terminal-measurement sampler (K measurements).
+size_t sct_sampler_bytes(int n, int K, int shots);
 cudaError_t launch_sct_program(const SctProgArgs& A, cudaStream_t st);
 // Batched kernel instances: threads per CTA in {128, 256, 512, 1024}.
 constexpr int kBatchThreadChoices[4] = {128, 256, 512, 1024};

@@ -83,6 +83,8 @@ _sig("tab_batch_exec", ctypes.c_int, [_vp, _u64, _vp, _vp])
 _sig("tab_batch_launches", ctypes.c_int, [_vp, _P(_i64)])
 _sig("tab_batch_tune", ctypes.c_int, [_vp, _u64, _vp, _vp, _P(_i32), _P(ctypes.c_float)])
 _sig("tab_batch_config", ctypes.c_int, [_vp, _P(_i32), _P(_i32), _P(_i64)])
+_sig("tab_batch_create_ex", ctypes.c_int, [_vp, _i32, _u32, _P(_vp)])
+_sig("tab_batch_sampled", ctypes.c_int, [_vp, _P(_i32)])
 
 
 class TabServerConfig(ctypes.Structure):
@@ -319,13 +321,21 @@ def batch_run(circuits, seed: int = 1) -> list:
     return res
 
 
-class Batch:
-    """A compiled batch (tab_batch_create) replayed with exec()."""
+BATCH_SAMPLE_TERMINAL = 1
 
-    def __init__(self, circuits):
+
+class Batch:
+    """A compiled batch (tab_batch_create_ex) replayed with exec().
+    sample_terminal: circuits whose measurements all follow their gates run
+    the terminal measurements once and sample every shot from the outcome
+    forms (same outcome bits)."""
+
+    def __init__(self, circuits, sample_terminal: bool = False):
         arr, keep = _circuit_array(circuits)
         h = _vp()
-        _check(_L.tab_batch_create(ctypes.cast(arr, _vp), len(circuits), ctypes.byref(h)))
+        flags = BATCH_SAMPLE_TERMINAL if sample_terminal else 0
+        _check(_L.tab_batch_create_ex(ctypes.cast(arr, _vp), len(circuits), flags,
+                                      ctypes.byref(h)))
         self._h = h
         self.sizes = [shots * n_meas_of(g) for (_, g, shots, _) in circuits]
 
@@ -344,6 +354,13 @@ class Batch:
         _check(_L.tab_batch_tune(self._h, seed, dev_out_ptr, _stream_handle(stream),
                                  ctypes.byref(t), ctypes.byref(ms)))
         return t.value, ms.value
+
+    @property
+    def sampled(self) -> int:
+        """Circuits that run through the terminal-measurement sampler."""
+        c = _i32()
+        _check(_L.tab_batch_sampled(self._h, ctypes.byref(c)))
+        return c.value
 
     def config(self):
         """Current launch shape: {"threads", "ctas", "smem_bytes"}."""

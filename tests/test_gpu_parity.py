@@ -312,6 +312,58 @@ def test_batch_autotune_keeps_outcomes():
     b.close()
 
 
+def _gate(op, q1=0, q2=0):
+    return int(np.asarray(C.encode(op, q1, q2)).reshape(-1)[0])
+
+
+def _ghz(n, reverse=False):
+    g = [_gate(C.TAB_H, 0)]
+    g += [_gate(C.TAB_CNOT, i, i + 1) for i in range(n - 1)]
+    qs = range(n - 1, -1, -1) if reverse else range(n)
+    g += [_gate(C.TAB_MZ, q) for q in qs]
+    return np.array(g, dtype=np.uint64)
+
+
+def test_batch_sampler_matches_per_shot():
+    """Terminal-measurement sampler: the same outcome bits as running every
+    shot, on random circuits up to n = 512, GHZ states (deterministic outcomes
+    that depend on an earlier random bit), a repeated measurement and a
+    circuit with a mid-circuit measurement (not sampled)."""
+    import torch
+    circs = C.config4(only=list(range(5, 4096, 512)))
+    circuits = [(c.n, c.gates, min(c.shots, 6), c.circuit_id) for c in circs]
+    circuits.append((24, _ghz(24), 16, 9001))
+    circuits.append((17, _ghz(17, reverse=True), 9, 9002))
+    rep = np.array([_gate(C.TAB_H, 3), _gate(C.TAB_S, 3), _gate(C.TAB_MZ, 3),
+                    _gate(C.TAB_MZ, 3), _gate(C.TAB_MZ, 1)], dtype=np.uint64)
+    circuits.append((5, rep, 7, 9003))
+    mid = C.random_layer_circuit(40, 8, seed=5, meas_every=3, meas_frac=0.2)
+    circuits.append((40, mid.gates, 5, 9004))
+    only_meas = np.array([_gate(C.TAB_MZ, q) for q in range(6)], dtype=np.uint64)
+    circuits.append((6, only_meas, 3, 9005))
+    plain = tab.Batch(circuits)
+    samp = tab.Batch(circuits, sample_terminal=True)
+    assert samp.sampled == len(circuits) - 1  # all but the mid-circuit one
+    assert plain.sampled == 0
+    nbytes = plain.info()["out_bytes"]
+    assert samp.info()["out_bytes"] == nbytes
+    a = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    b = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    plain.exec(C.PHILOX_SEED, a.data_ptr())
+    samp.exec(C.PHILOX_SEED, b.data_ptr())
+    torch.cuda.synchronize()
+    assert torch.equal(a, b), int((a != b).sum())
+    # GHZ shots against the oracle: outcomes all equal within a shot
+    ghz = b.cpu().numpy()
+    off = sum(c[2] * int(np.isin(C.decode(c[1])[0], C.MEASURE).sum()) for c in circuits[:-5])
+    for s in range(16):
+        want, _ = oracle.run_circuit(24, circuits[-5][1], seed=C.PHILOX_SEED, circuit_id=9001, shot=s)
+        got = ghz[off + 24 * s: off + 24 * (s + 1)]
+        assert np.array_equal(got, want) and len(set(got.tolist())) == 1
+    plain.close()
+    samp.close()
+
+
 _FLOW_KERNEL_SCRIPT = r"""
 import sys, numpy as np
 sys.path.insert(0, %r)
