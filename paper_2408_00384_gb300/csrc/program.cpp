@@ -14,9 +14,9 @@
 
 #include <algorithm>
 #include <string>
-#include <thread>
 #include <vector>
 
+#include "pool.h"
 #include "tab_internal.h"
 
 namespace tab {
@@ -127,28 +127,57 @@ static int validate(int32_t n, const tab_gate* gates, int64_t begin, int64_t end
 static int build_range(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out,
                        int mode);
 
-// Append program Q (compiled for the gates after those of P) to P.
-static void append_program(HostProgram& P, const HostProgram& Q) {
-  const uint32_t op_base = (uint32_t)P.ops.size(), blk_base = (uint32_t)P.blk.size();
-  const uint32_t loff_base = (uint32_t)P.layer_off.size(), boff_base = (uint32_t)P.blk_off.size();
-  const uint32_t meas_base = (uint32_t)P.n_meas;
-  P.ops.insert(P.ops.end(), Q.ops.begin(), Q.ops.end());
-  P.vers.insert(P.vers.end(), Q.vers.begin(), Q.vers.end());
-  P.blk.insert(P.blk.end(), Q.blk.begin(), Q.blk.end());
-  for (uint32_t x : Q.layer_off) P.layer_off.push_back(x + op_base);
-  for (uint32_t x : Q.blk_off) P.blk_off.push_back(x + blk_base);
-  for (Seg s : Q.segs) {
-    s.op_begin += op_base;
-    s.op_end += op_base;
-    s.layer_begin += loff_base;
-    s.layer_end += loff_base;
-    s.blk_begin += boff_base;
-    s.blk_end += boff_base;
-    s.meas_before += meas_base;
-    P.segs.push_back(s);
+// Concatenate programs compiled for consecutive pieces of one gate list
+// into P, each piece's arrays copied (and its offsets shifted) in parallel.
+static void concat_programs(HostProgram& P, std::vector<HostProgram>& part) {
+  const size_t T = part.size();
+  std::vector<size_t> o_ops(T + 1, 0), o_vers(T + 1, 0), o_blk(T + 1, 0), o_loff(T + 1, 0),
+      o_boff(T + 1, 0), o_segs(T + 1, 0), o_meas(T + 1, 0);
+  for (size_t t = 0; t < T; ++t) {
+    o_ops[t + 1] = o_ops[t] + part[t].ops.size();
+    o_vers[t + 1] = o_vers[t] + part[t].vers.size();
+    o_blk[t + 1] = o_blk[t] + part[t].blk.size();
+    o_loff[t + 1] = o_loff[t] + part[t].layer_off.size();
+    o_boff[t + 1] = o_boff[t] + part[t].blk_off.size();
+    o_segs[t + 1] = o_segs[t] + part[t].segs.size();
+    o_meas[t + 1] = o_meas[t] + (size_t)part[t].n_meas;
   }
-  P.n_gates += Q.n_gates;
-  P.n_meas += Q.n_meas;
+  P = HostProgram();
+  P.n = part[0].n;
+  P.mode = part[0].mode;
+  P.layered = part[0].layered;
+  P.ops.resize(o_ops[T]);
+  P.vers.resize(o_vers[T]);
+  P.blk.resize(o_blk[T]);
+  P.layer_off.resize(o_loff[T]);
+  P.blk_off.resize(o_boff[T]);
+  P.segs.resize(o_segs[T]);
+  for (size_t t = 0; t < T; ++t) {
+    P.n_gates += part[t].n_gates;
+    P.n_meas += part[t].n_meas;
+  }
+  pool_run((int)T, [&](int ti) {
+    const size_t t = (size_t)ti;
+    const HostProgram& Q = part[t];
+    std::copy(Q.ops.begin(), Q.ops.end(), P.ops.begin() + (ptrdiff_t)o_ops[t]);
+    std::copy(Q.vers.begin(), Q.vers.end(), P.vers.begin() + (ptrdiff_t)o_vers[t]);
+    std::copy(Q.blk.begin(), Q.blk.end(), P.blk.begin() + (ptrdiff_t)o_blk[t]);
+    for (size_t i = 0; i < Q.layer_off.size(); ++i)
+      P.layer_off[o_loff[t] + i] = Q.layer_off[i] + (uint32_t)o_ops[t];
+    for (size_t i = 0; i < Q.blk_off.size(); ++i)
+      P.blk_off[o_boff[t] + i] = Q.blk_off[i] + (uint32_t)o_blk[t];
+    for (size_t i = 0; i < Q.segs.size(); ++i) {
+      Seg s = Q.segs[i];
+      s.op_begin += (uint32_t)o_ops[t];
+      s.op_end += (uint32_t)o_ops[t];
+      s.layer_begin += (uint32_t)o_loff[t];
+      s.layer_end += (uint32_t)o_loff[t];
+      s.blk_begin += (uint32_t)o_boff[t];
+      s.blk_end += (uint32_t)o_boff[t];
+      s.meas_before += (uint32_t)o_meas[t];
+      P.segs[o_segs[t] + i] = s;
+    }
+  });
 }
 
 int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out,
@@ -162,35 +191,28 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
     return TAB_EINVAL;
   }
   // Long lists compiled to blocks only (the multi-CTA engines' per-call path)
-  // are cut into chunks that worker threads validate and compile at once;
-  // each chunk's gates become gate runs of their own, appended in order.
-  const int64_t kChunk = 1 << 18;
+  // are cut into chunks that the pool's threads validate and compile at once;
+  // each chunk's gates become gate runs of their own, concatenated in order.
+  const int64_t kChunk = 1 << 16;
   if (mode == kProgBlocks && count >= 2 * kChunk) {
-    const unsigned hw = std::thread::hardware_concurrency();
-    int T = (int)std::min<int64_t>(count / kChunk, std::min<unsigned>(hw ? hw : 1, 16u));
+    const int T = (int)std::min<int64_t>(count / kChunk, pool_threads());
     if (T >= 2) {
       std::vector<HostProgram> part((size_t)T);
       std::vector<int> rcs((size_t)T, TAB_OK);
       std::vector<std::string> msg((size_t)T);
-      auto work = [&](int t) {
+      pool_run(T, [&](int t) {
         const int64_t b = count * t / T, e = count * (t + 1) / T;
         int rc = validate(n, gates, b, e);
         if (rc == TAB_OK) rc = build_range(n, gates + b, e - b, &part[(size_t)t], mode);
         rcs[(size_t)t] = rc;
         if (rc != TAB_OK) msg[(size_t)t] = last_error();
-      };
-      std::vector<std::thread> th;
-      for (int t = 1; t < T; ++t) th.emplace_back(work, t);
-      work(0);
-      for (auto& x : th) x.join();
+      });
       for (int t = 0; t < T; ++t)
         if (rcs[(size_t)t] != TAB_OK) {
           set_error("%s", msg[(size_t)t].c_str());
           return rcs[(size_t)t];
         }
-      HostProgram& P = *out;
-      P = std::move(part[0]);
-      for (int t = 1; t < T; ++t) append_program(P, part[(size_t)t]);
+      concat_programs(*out, part);
       return TAB_OK;
     }
   }

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "sct.h"
+#include "pool.h"
 #include "tab_internal.h"
 
 namespace tab {
@@ -406,7 +407,16 @@ int upload_staged(tab_t h, const HostProgram& hp, DevProg* d) {
   }
   if (want_blk) {
     uint8_t* b0 = st + ob + lb + sb + rb;
-    if (!hp.blk.empty()) memcpy(b0, hp.blk.data(), hp.blk.size() * sizeof(uint2));
+    if (!hp.blk.empty()) {  // large programs: the copy into pinned memory in pieces
+      const size_t bytes = hp.blk.size() * sizeof(uint2);
+      const int pieces = bytes >= ((size_t)1 << 20) ? pool_threads() : 1;
+      const uint8_t* src = reinterpret_cast<const uint8_t*>(hp.blk.data());
+      pool_run(pieces, [&](int i) {
+        const size_t a = bytes * (size_t)i / (size_t)pieces;
+        const size_t e = bytes * (size_t)(i + 1) / (size_t)pieces;
+        memcpy(b0 + a, src + a, e - a);
+      });
+    }
     memset(b0 + hp.blk.size() * sizeof(uint2), 0, (size_t)kOpsPad * sizeof(uint2));
     if (!hp.blk_off.empty()) memcpy(b0 + bb, hp.blk_off.data(), hp.blk_off.size() * 4);
   }

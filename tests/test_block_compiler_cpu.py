@@ -31,7 +31,8 @@ def test_block_compiler_matches_gate_rules(tmp_path):
     exe = str(tmp_path / "block_compiler_check")
     cmd = [cxx, "-O2", "-std=c++17", "-pthread", "-I", inc, "-I", CSRC, "-I", os.path.join(ROOT, "include"),
            os.path.join(HERE, "cpp", "block_compiler_check.cpp"),
-           os.path.join(CSRC, "program.cpp"), os.path.join(CSRC, "blocks.cpp"), "-o", exe]
+           os.path.join(CSRC, "program.cpp"), os.path.join(CSRC, "blocks.cpp"),
+           os.path.join(CSRC, "pool.cpp"), "-o", exe]
     subprocess.run(cmd, check=True, capture_output=True, text=True)
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
