@@ -14,12 +14,14 @@
 #include <stdint.h>
 #include <stdlib.h>
 
+#include <algorithm>
+
 #include "measure_resident.cuh"
 #include "tab_internal.h"
 
 namespace tab {
 
-// Measurements per batch: TAB_MEAS_BATCH (1, 2, 4, 8, 16) caps it for
+// Measurements per batch: TAB_MEAS_BATCH (1, 2, 4, ..., 32) caps it for
 // tuning sweeps; the default is the largest that fits.
 static int batch_cap() {
   static int cap = 0;
@@ -189,14 +191,14 @@ struct CommGrid {
 };
 
 template <int WL>
-__global__ void __launch_bounds__(kResThreads) k_measure_cluster(ResArgs A) {
+__global__ void __launch_bounds__(32 * res_warps(WL)) k_measure_cluster(ResArgs A) {
   extern __shared__ __align__(16) uint32_t sm[];
   CommCluster cm;
   measure_resident<WL>(A, cm, sm);
 }
 
 template <int WL>
-__global__ void __launch_bounds__(kResThreads) k_measure_resident(ResArgs A) {
+__global__ void __launch_bounds__(32 * res_warps(WL)) k_measure_resident(ResArgs A) {
   extern __shared__ __align__(16) uint32_t sm[];
   CommGrid cm(A);
   measure_resident<WL>(A, cm, sm);
@@ -266,7 +268,7 @@ int cluster_size_for(int n, int Wh) {
         at[0].val.clusterDim.y = 1;
         at[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3((unsigned)c);
-        cfg.blockDim = dim3(kResThreads);
+        cfg.blockDim = dim3(32 * res_warps(8));
         cfg.dynamicSmemBytes = res_dyn_limit();
         cfg.attrs = at;
         cfg.numAttrs = 1;
@@ -321,10 +323,11 @@ cudaError_t launch_measure_cluster(uint32_t* X, uint32_t* Z, uint32_t* R, int n,
                                    uint64_t cid, uint32_t shot, uint8_t* out, int* err, int C,
                                    cudaStream_t s) {
   if (nm <= 0) return cudaSuccess;
-  const void* fn = cluster_kernel(res_words_per_lane(Wh));
+  const int wl = res_words_per_lane(Wh);
+  const void* fn = cluster_kernel(wl);
   if (fn == nullptr) return cudaErrorInvalidValue;
   ResArgs A = res_args(X, Z, R, n, Wh, mops, nm, k0, seed, cid, shot, out, err);
-  A.kb = res_batch_for(n, Wh, C, res_dyn_limit(), batch_cap(), true);
+  A.kb = res_batch_for(n, Wh, C, res_dyn_limit(), std::min(batch_cap(), res_warps(wl)), true);
   if (A.kb == 0) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
@@ -333,7 +336,7 @@ cudaError_t launch_measure_cluster(uint32_t* X, uint32_t* Z, uint32_t* R, int n,
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3((unsigned)C);
-  cfg.blockDim = dim3(kResThreads);
+  cfg.blockDim = dim3(32 * res_warps(wl));
   cfg.dynamicSmemBytes = res_layout(n, Wh, C, A.kb, true).words * 4;
   cfg.stream = s;
   cfg.attrs = at;
@@ -381,11 +384,12 @@ cudaError_t launch_measure_resident(uint32_t* X, uint32_t* Z, uint32_t* R, int n
                                     uint64_t cid, uint32_t shot, uint8_t* out, int* err,
                                     uint32_t* work, GridBar* bar, int G, cudaStream_t s) {
   if (nm <= 0) return cudaSuccess;
-  const void* fn = resident_kernel(res_words_per_lane(Wh));
+  const int wl = res_words_per_lane(Wh);
+  const void* fn = resident_kernel(wl);
   if (fn == nullptr) return cudaErrorInvalidValue;
   ResArgs A = res_args(X, Z, R, n, Wh, mops, nm, k0, seed, cid, shot, out, err);
   const int W = 2 * Wh;
-  A.kb = res_batch_for(n, Wh, G, res_dyn_limit(), batch_cap(), false);
+  A.kb = res_batch_for(n, Wh, G, res_dyn_limit(), std::min(batch_cap(), res_warps(wl)), false);
   if (A.kb == 0) return cudaErrorInvalidValue;
   A.stage = work;
   A.dp = A.stage + 4 * (size_t)A.kb * W;
@@ -395,7 +399,7 @@ cudaError_t launch_measure_resident(uint32_t* X, uint32_t* Z, uint32_t* R, int n
   cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBar), s);
   if (e != cudaSuccess) return e;
   void* args[] = {&A};
-  return cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(kResThreads), args,
+  return cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(32 * res_warps(wl)), args,
                                      res_layout(n, Wh, G, A.kb, false).words * 4, s);
 }
 

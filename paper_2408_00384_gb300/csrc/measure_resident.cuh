@@ -66,10 +66,12 @@
 
 namespace tab {
 
-constexpr int kResWarps = 16;
-constexpr int kResThreads = 32 * kResWarps;
-constexpr int kBatchMax = kResWarps;                // phase 1: one measured column per warp
-constexpr int kResMaxLocalCols = 32 * kResWarps;    // a warp's columns fit one ballot
+// Warps per CTA: 32 (1,024 threads) while the register share is small
+// (W <= 128 words, n <= 2,048), else 16; batches hold at most one measured
+// column per warp (phase 1).
+__host__ __device__ constexpr int res_warps(int wl) { return wl <= 4 ? 32 : 16; }
+constexpr int kBatchMax = 32;                       // largest batch of any instance
+constexpr int kResMaxLocalCols = 32 * 16;           // a warp's columns fit one ballot
 constexpr int kPubSpinMax = 1 << 22;              // polls (64 ns apart) before a wait gives up
 
 struct ResArgs {
@@ -255,7 +257,7 @@ __device__ __forceinline__ void res_batch_slots(uint32_t code, int K, int C, int
 
 template <int WL, class Comm>
 __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
-  constexpr int NW = kResWarps;
+  constexpr int NW = res_warps(WL);
   constexpr bool kPush = Comm::kPush;
   const int C = cm.size(), r = cm.rank(), tid = threadIdx.x, T = blockDim.x;
   const int n = A.n, Wh = A.Wh, W = 2 * Wh, KB = A.kb;
