@@ -140,10 +140,14 @@ void BlockBuilder::add(uint32_t op, uint32_t a, uint32_t b) {
 }
 
 // Emit the run's blocks, grouped by super-layer and, inside one, by kind
-// (single- or two-qubit, entangler, whether the U and V codes are identities)
-// so that the threads of a warp take the same path and skip the same
-// identity codes; super-layers above kMaxLayerOps blocks become consecutive
-// sub-layers.  Appends to P.blk and P.blk_off and sets s.blk_begin / s.blk_end.
+// (single- or two-qubit, entangler, whether the U codes are identities, and
+// the class -- identity, H, S or other -- of each V code) so that the threads
+// of a warp take the same path: identity codes are skipped and H / S take
+// their two-operation forms.  A CNOT is stored with its control in register
+// 0 (the block's two registers relabelled if needed: the qubits, the U and
+// the V codes trade places; the swap flag keeps its meaning).  Super-layers
+// above kMaxLayerOps blocks become consecutive sub-layers.  Appends to P.blk
+// and P.blk_off and sets s.blk_begin / s.blk_end.
 void BlockBuilder::emit(HostProgram& P, Seg& s) {
   int32_t top = 0;
   size_t live = 0;
@@ -152,12 +156,20 @@ void BlockBuilder::emit(HostProgram& P, Seg& s) {
       top = std::max(top, k.layer + 1);
       ++live;
     }
-  const int kKinds = 16;  // (1q | 2q none / CNOT / CZ) x (U identity) x (V identity)
-  auto kind = [](const BlkRec& k) {
+  for (BlkRec& k : blk_)
+    if (!k.dead && k.has_b && k.ent == 1 && k.dir == 1) {
+      std::swap(k.qa, k.qb);
+      std::swap(k.U[0], k.U[1]);
+      std::swap(k.V[0], k.V[1]);
+      k.dir = 0;
+    }
+  // (1q | 2q none / CNOT / CZ) x (U identity) x (V_0 class) x (V_1 class)
+  const int kKinds = 128;
+  auto cls = [](uint8_t c) { return c == kC1Ident ? 0 : c == kC1H ? 1 : c == kC1S ? 2 : 3; };
+  auto kind = [&](const BlkRec& k) {
     const int e = k.has_b ? 1 + (int)k.ent : 0;
     const int u = (k.U[0] == kC1Ident && k.U[1] == kC1Ident) ? 0 : 1;
-    const int v = (k.V[0] == kC1Ident && k.V[1] == kC1Ident) ? 0 : 1;
-    return e * 4 + u * 2 + v;
+    return ((e * 2 + u) * 4 + cls(k.V[0])) * 4 + cls(k.V[1]);
   };
   std::vector<uint32_t> cnt((size_t)top * kKinds + 1, 0u);
   for (const BlkRec& k : blk_)

@@ -21,6 +21,8 @@
 namespace tab {
 
 constexpr uint32_t kC1Ident = 0x09u;  // alpha = delta = 1
+constexpr uint32_t kC1H = 0x46u;      // x' = z, z' = x, r ^= xz
+constexpr uint32_t kC1S = 0x4Du;      // z' = x ^ z, r ^= xz
 
 // code of one gate (tab_op numbering: X=1 Y=2 Z=3 H=4 S=5 SDG=6; else I)
 inline uint32_t c1_of_op(uint32_t op) {
@@ -62,6 +64,27 @@ __device__ __forceinline__ void c1_apply(uint32_t m, uint32_t& x, uint32_t& z, u
   const uint32_t xn = (al & x) ^ (be & z);
   z = (ga & x) ^ (de & z);
   x = xn;
+}
+
+// c1_apply for a code that the lanes in `act` hold: when they all hold the
+// identity, H or S (the codes random layers use), the warp takes the short
+// form; otherwise every lane applies its own code in general form.
+__device__ __forceinline__ void c1_apply_warp(uint32_t m, uint32_t act, uint32_t& x, uint32_t& z,
+                                              uint32_t& r) {
+  if (__all_sync(act, m == kC1Ident)) return;
+  if (__all_sync(act, m == kC1H)) {
+    r ^= x & z;
+    const uint32_t t = x;
+    x = z;
+    z = t;
+    return;
+  }
+  if (__all_sync(act, m == kC1S)) {
+    r ^= x & z;
+    z ^= x;
+    return;
+  }
+  c1_apply(m, x, z, r);
 }
 #endif
 

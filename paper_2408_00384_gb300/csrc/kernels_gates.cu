@@ -382,46 +382,40 @@ constexpr int kBlkChunk = 512;                  // records per TMA copy (4 KB)
 constexpr int kBlkSlots = 16;                   // 64 KB ring
 constexpr int kBlkRing = kBlkChunk * kBlkSlots;
 
-// Identity codes are skipped when no thread of the warp needs the code (the
-// compiler groups blocks by which codes are identities); the lanes of a warp
-// that take part are given by `act`.
+// Identity, H and S codes take their short forms when every thread of the
+// warp holds the same one (the compiler groups blocks by those classes); the
+// lanes of a warp that take part are given by `act`, and every warp vote
+// names exactly the lanes that reach it.
 __device__ __forceinline__ void apply_block(uint2 rec, uint32_t* sx, uint32_t* sz, uint32_t& r,
                                             uint32_t act) {
   const uint32_t qa = rec.x & 0x3FFFu, qb = (rec.x >> 14) & 0x3FFFu;
   const bool two = (rec.x >> 28) & 1u;
-  const uint32_t ent = (rec.x >> 29) & 3u, dir = rec.x >> 31;
+  const uint32_t ent = (rec.x >> 29) & 3u;
   const uint32_t m = rec.y;
-  constexpr uint32_t kUId = kC1Ident | (kC1Ident << 7), kVId = kUId << 14;
-  const bool need_u = __any_sync(act, (m & 0x3FFFu) != kUId);
-  const bool need_v = __any_sync(act, (m & 0xFFFC000u) != kVId);
+  // the lanes of `act` holding two-qubit blocks: the only lanes that take
+  // part in the votes after the single-qubit lanes leave
+  const uint32_t act2 = __ballot_sync(act, two);
   uint32_t x0 = sx[qa], z0 = sz[qa];
-  if (need_u) c1_apply(m & 0x7Fu, x0, z0, r);
+  c1_apply_warp(m & 0x7Fu, act, x0, z0, r);
   if (!two) {
     sx[qa] = x0;
     sz[qa] = z0;
     return;
   }
   uint32_t x1 = sx[qb], z1 = sz[qb];
-  if (need_u) c1_apply((m >> 7) & 0x7Fu, x1, z1, r);
-  if (ent == 1u) {  // CNOT, control in register `dir`
-    const uint32_t xc = dir ? x1 : x0, zc = dir ? z1 : z0;
-    const uint32_t xt = dir ? x0 : x1, zt = dir ? z0 : z1;
-    r ^= xc & zt & ~(xt ^ zc);
-    const uint32_t xt2 = xt ^ xc, zc2 = zc ^ zt;
-    x0 = dir ? xt2 : xc;
-    z0 = dir ? zt : zc2;
-    x1 = dir ? xc : xt2;
-    z1 = dir ? zc2 : zt;
+  c1_apply_warp((m >> 7) & 0x7Fu, act2, x1, z1, r);
+  if (ent == 1u) {  // CNOT, control in register 0 (the compiler's convention)
+    r ^= x0 & z1 & ~(x1 ^ z0);
+    x1 ^= x0;
+    z0 ^= z1;
   } else if (ent == 2u) {  // CZ
     r ^= x0 & x1 & (z0 ^ z1);
     const uint32_t z0n = z0 ^ x1;
     z1 ^= x0;
     z0 = z0n;
   }
-  if (need_v) {
-    c1_apply((m >> 14) & 0x7Fu, x0, z0, r);
-    c1_apply((m >> 21) & 0x7Fu, x1, z1, r);
-  }
+  c1_apply_warp((m >> 14) & 0x7Fu, act2, x0, z0, r);
+  c1_apply_warp((m >> 21) & 0x7Fu, act2, x1, z1, r);
   const bool sw = (m >> 28) & 1u;
   const uint32_t da = sw ? qb : qa, db = sw ? qa : qb;
   sx[da] = x0;
