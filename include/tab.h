@@ -101,7 +101,9 @@ int tab_destroy(tab_t h);
 int tab_num_qubits(tab_t h, int32_t *n);
 
 /* Bind the handle to a CUDA stream (cudaStream_t; NULL = default stream).
- * Later work is enqueued there; earlier work is not moved. */
+ * Later work is enqueued there; earlier work is not moved.  When the stream
+ * changes, the call first waits for the work already enqueued on the
+ * previous one (TAB_ECUDA if that work failed). */
 int tab_set_stream(tab_t h, void *cuda_stream);
 
 /* Set (seed, circuit_id, shot) of the outcome stream and reset the

@@ -40,6 +40,16 @@ static const uint8_t* c1_table() {
   return t.data();
 }
 
+// row of c1_table for each gate op (tab_op numbering, 4 bits)
+static const uint8_t* c1_row_of_op() {
+  static const std::vector<uint8_t> t = [] {
+    std::vector<uint8_t> v(16);
+    for (uint32_t op = 0; op < 16; ++op) v[op] = (uint8_t)c1_of_op(op);
+    return v;
+  }();
+  return t.data();
+}
+
 void BlockBuilder::reset(int32_t n, size_t hint) {
   if ((int32_t)cur_.size() < n) {
     cur_.assign((size_t)n, -1);
@@ -74,7 +84,7 @@ void BlockBuilder::add(uint32_t op, uint32_t a, uint32_t b) {
   };
   const bool two = op == TAB_CNOT || op == TAB_CZ || op == TAB_SWAP;
   if (!two) {
-    const uint8_t* tab = c1_table() + 128 * c1_of_op(op);
+    const uint8_t* tab = c1_table() + 128 * c1_row_of_op()[op & 15u];
     int32_t B = latest(a);
     if (B < 0) B = open(a, 0, false, 0);
     BlkRec& k = blk_[(size_t)B];
@@ -149,31 +159,48 @@ void BlockBuilder::add(uint32_t op, uint32_t a, uint32_t b) {
 // above kMaxLayerOps blocks become consecutive sub-layers.  Appends to P.blk
 // and P.blk_off and sets s.blk_begin / s.blk_end.
 void BlockBuilder::emit(HostProgram& P, Seg& s) {
+  // (1q | 2q none / CNOT / CZ) x (U identity) x (V_0 class) x (V_1 class);
+  // the sort key of each live block and its record are formed in one pass
+  // (table lookups in place of data-dependent branches)
+  const int kKinds = 128;
+  static const std::vector<uint8_t> cls = [] {
+    std::vector<uint8_t> v(128, 3);
+    v[kC1Ident] = 0;
+    v[kC1H] = 1;
+    v[kC1S] = 2;
+    return v;
+  }();
+  const size_t nb = blk_.size();
+  key_.resize(nb);
+  rec_.resize(nb);
   int32_t top = 0;
   size_t live = 0;
-  for (const BlkRec& k : blk_)
-    if (!k.dead) {
-      top = std::max(top, k.layer + 1);
-      ++live;
+  for (size_t i = 0; i < nb; ++i) {
+    BlkRec& k = blk_[i];
+    if (k.dead) {
+      key_[i] = UINT32_MAX;
+      continue;
     }
-  for (BlkRec& k : blk_)
-    if (!k.dead && k.has_b && k.ent == 1 && k.dir == 1) {
+    if (k.has_b && k.ent == 1 && k.dir == 1) {
       std::swap(k.qa, k.qb);
       std::swap(k.U[0], k.U[1]);
       std::swap(k.V[0], k.V[1]);
       k.dir = 0;
     }
-  // (1q | 2q none / CNOT / CZ) x (U identity) x (V_0 class) x (V_1 class)
-  const int kKinds = 128;
-  auto cls = [](uint8_t c) { return c == kC1Ident ? 0 : c == kC1H ? 1 : c == kC1S ? 2 : 3; };
-  auto kind = [&](const BlkRec& k) {
-    const int e = k.has_b ? 1 + (int)k.ent : 0;
-    const int u = (k.U[0] == kC1Ident && k.U[1] == kC1Ident) ? 0 : 1;
-    return ((e * 2 + u) * 4 + cls(k.V[0])) * 4 + cls(k.V[1]);
-  };
-  std::vector<uint32_t> cnt((size_t)top * kKinds + 1, 0u);
-  for (const BlkRec& k : blk_)
-    if (!k.dead) cnt[(size_t)k.layer * kKinds + kind(k)]++;
+    const uint32_t e = k.has_b ? 1u + k.ent : 0u;
+    const uint32_t u = ((k.U[0] ^ kC1Ident) | (k.U[1] ^ kC1Ident)) != 0;
+    key_[i] = (uint32_t)k.layer * kKinds + ((e * 2 + u) * 4 + cls[k.V[0]]) * 4 + cls[k.V[1]];
+    rec_[i] = make_uint2((uint32_t)k.qa | ((uint32_t)k.qb << 14) | ((uint32_t)k.has_b << 28) |
+                             ((uint32_t)k.ent << 29) | ((uint32_t)k.dir << 31),
+                         (uint32_t)k.U[0] | ((uint32_t)k.U[1] << 7) | ((uint32_t)k.V[0] << 14) |
+                             ((uint32_t)k.V[1] << 21) | ((uint32_t)k.swp << 28));
+    top = std::max(top, k.layer + 1);
+    ++live;
+  }
+  std::vector<uint32_t>& cnt = cnt_;
+  cnt.assign((size_t)top * kKinds + 1, 0u);
+  for (size_t i = 0; i < nb; ++i)
+    if (key_[i] != UINT32_MAX) cnt[key_[i]]++;
   std::vector<uint32_t> pos(cnt.size(), 0u);
   uint32_t acc = 0;
   for (size_t i = 0; i < cnt.size(); ++i) {
@@ -182,14 +209,9 @@ void BlockBuilder::emit(HostProgram& P, Seg& s) {
   }
   const uint32_t base = (uint32_t)P.blk.size();
   P.blk.resize(P.blk.size() + live);
-  for (const BlkRec& k : blk_) {
-    if (k.dead) continue;
-    const uint32_t lo = (uint32_t)k.qa | ((uint32_t)k.qb << 14) | ((uint32_t)k.has_b << 28) |
-                        ((uint32_t)k.ent << 29) | ((uint32_t)k.dir << 31);
-    const uint32_t hi = (uint32_t)k.U[0] | ((uint32_t)k.U[1] << 7) | ((uint32_t)k.V[0] << 14) |
-                        ((uint32_t)k.V[1] << 21) | ((uint32_t)k.swp << 28);
-    P.blk[base + pos[(size_t)k.layer * kKinds + kind(k)]++] = make_uint2(lo, hi);
-  }
+  uint2* out = P.blk.data() + base;
+  for (size_t i = 0; i < nb; ++i)
+    if (key_[i] != UINT32_MAX) out[pos[key_[i]]++] = rec_[i];
   s.blk_begin = (uint32_t)P.blk_off.size();
   P.blk_off.push_back(base);
   uint32_t run = base;

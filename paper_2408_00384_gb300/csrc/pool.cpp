@@ -3,7 +3,8 @@
 // The workers start on first use (one fewer than the hardware threads, at
 // most 15) and sleep on a condition variable between jobs.  A job hands out
 // indices from an atomic counter; the caller takes indices too and then waits
-// until every index has finished.
+// until every index has finished.  A pool_run called from inside a job runs
+// its indices on the calling thread.
 #include "pool.h"
 
 #include <algorithm>
@@ -16,6 +17,8 @@
 namespace tab {
 
 namespace {
+
+thread_local bool t_in_job = false;  // this thread is running a job's index
 
 class Pool {
  public:
@@ -37,7 +40,7 @@ class Pool {
 
   void run(int n, const std::function<void(int)>& fn) {
     if (n <= 0) return;
-    if (n == 1 || workers_.empty()) {
+    if (n == 1 || workers_.empty() || t_in_job) {
       for (int i = 0; i < n; ++i) fn(i);
       return;
     }
@@ -62,7 +65,9 @@ class Pool {
     for (;;) {
       const int i = next_.fetch_add(1);
       if (i >= n_) return;
+      t_in_job = true;
       (*fn_)(i);
+      t_in_job = false;
       if (done_.fetch_add(1) + 1 == n_) {
         std::lock_guard<std::mutex> lk(m_);
         done_cv_.notify_all();

@@ -95,6 +95,20 @@ static int build_program_stream(int32_t n, const tab_gate* gates, int64_t count,
 // Every word of gates[begin, end) is a valid gate for n qubits (index i in
 // messages is the position in the whole list).
 static int validate(int32_t n, const tab_gate* gates, int64_t begin, int64_t end) {
+  // fast pass: one flag over the whole range without data-dependent branches
+  // (two-qubit ops are CNOT, CZ, SWAP = 7, 8, 9); the exact scan below runs
+  // only when some word is bad, to name the first one
+  uint64_t bad = 0;
+  const uint64_t un = (uint64_t)n;
+  for (int64_t i = begin; i < end; ++i) {
+    const uint64_t g = gates[i];
+    const uint64_t op = g >> 56;
+    const uint64_t q1 = (g >> 28) & 0xFFFFFFFull, q2 = g & 0xFFFFFFFull;
+    const uint64_t two = (uint64_t)(op - TAB_CNOT) <= (uint64_t)(TAB_SWAP - TAB_CNOT);
+    bad |= (uint64_t)(op > TAB_BARRIER) | ((uint64_t)(op != TAB_BARRIER) & (uint64_t)(q1 >= un)) |
+           (two & ((uint64_t)(q2 >= un) | (uint64_t)(q1 == q2)));
+  }
+  if (!bad) return TAB_OK;
   for (int64_t i = begin; i < end; ++i) {
     const uint64_t g = gates[i];
     const uint32_t op = (uint32_t)(g >> 56);
@@ -127,10 +141,7 @@ static int validate(int32_t n, const tab_gate* gates, int64_t begin, int64_t end
 static int build_range(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out,
                        int mode);
 
-// Concatenate programs compiled for consecutive pieces of one gate list
-// into P, each piece's arrays copied (and its offsets shifted) in parallel.
-static void concat_programs(HostProgram& P, std::vector<HostProgram>& part) {
-  const size_t T = part.size();
+void concat_programs(HostProgram& P, const HostProgram* part, size_t T) {
   std::vector<size_t> o_ops(T + 1, 0), o_vers(T + 1, 0), o_blk(T + 1, 0), o_loff(T + 1, 0),
       o_boff(T + 1, 0), o_segs(T + 1, 0), o_meas(T + 1, 0);
   for (size_t t = 0; t < T; ++t) {
@@ -142,8 +153,7 @@ static void concat_programs(HostProgram& P, std::vector<HostProgram>& part) {
     o_segs[t + 1] = o_segs[t] + part[t].segs.size();
     o_meas[t + 1] = o_meas[t] + (size_t)part[t].n_meas;
   }
-  P = HostProgram();
-  P.n = part[0].n;
+  P.clear(part[0].n);
   P.mode = part[0].mode;
   P.layered = part[0].layered;
   P.ops.resize(o_ops[T]);
@@ -180,6 +190,34 @@ static void concat_programs(HostProgram& P, std::vector<HostProgram>& part) {
   });
 }
 
+int validate_program(int32_t n, const tab_gate* gates, int64_t count) {
+  if (n < 1 || n > TAB_MAX_QUBITS) {
+    set_error("n=%d outside [1, %d]", n, TAB_MAX_QUBITS);
+    return TAB_ERANGE;
+  }
+  if (count < 0 || (count > 0 && gates == nullptr)) {
+    set_error("bad gate list (count=%lld)", (long long)count);
+    return TAB_EINVAL;
+  }
+  const int T = (int)std::max<int64_t>(1, std::min<int64_t>(count >> 16, pool_threads()));
+  std::vector<int> rcs((size_t)T, TAB_OK);
+  std::vector<std::string> msg((size_t)T);
+  pool_run(T, [&](int t) {
+    rcs[(size_t)t] = validate(n, gates, count * t / T, count * (t + 1) / T);
+    if (rcs[(size_t)t] != TAB_OK) msg[(size_t)t] = last_error();
+  });
+  for (int t = 0; t < T; ++t)  // the first bad word in list order
+    if (rcs[(size_t)t] != TAB_OK) {
+      set_error("%s", msg[(size_t)t].c_str());
+      return rcs[(size_t)t];
+    }
+  return TAB_OK;
+}
+
+int build_validated_blocks(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out) {
+  return build_range(n, gates, count, out, kProgBlocks);
+}
+
 int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out,
                   int mode) {
   if (n < 1 || n > TAB_MAX_QUBITS) {
@@ -212,7 +250,7 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
           set_error("%s", msg[(size_t)t].c_str());
           return rcs[(size_t)t];
         }
-      concat_programs(*out, part);
+      concat_programs(*out, part.data(), part.size());
       return TAB_OK;
     }
   }
@@ -231,11 +269,11 @@ static int build_range(int32_t n, const tab_gate* gates, int64_t count, HostProg
                        int mode) {
   const bool layers = (mode & kProgLayers) != 0, blocks = (mode & kProgBlocks) != 0;
   HostProgram& P = *out;
-  P = HostProgram();
-  P.n = n;
+  P.clear(n);
   P.mode = mode & (kProgLayers | kProgBlocks);
   if (layers) P.ops.reserve((size_t)count);
-  BlockBuilder bb;
+  // one builder per thread, kept between calls with its arrays' capacity
+  static thread_local BlockBuilder bb;
   if (blocks) {
     bb.reset(n, (size_t)count / 2 + 16);
     P.blk.reserve((size_t)count / 2 + 16);

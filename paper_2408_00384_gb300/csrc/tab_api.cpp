@@ -8,6 +8,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <string>
+#include <thread>
+#include <memory>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -52,11 +56,21 @@ struct tab_s {
   int64_t h2d_bytes = 0, d2h_bytes = 0;  // host <-> device copies made for callers
   int sticky = TAB_OK;        // latched device error
   int engine = TAB_ENGINE_AUTO;
-  // pinned staging area for program uploads (one H2D copy per call)
-  uint8_t* stg = nullptr;
-  size_t stg_cap = 0;
-  cudaEvent_t stg_ev = nullptr;
-  bool stg_pending = false;
+  // pinned staging areas for program uploads (one H2D copy per upload), used
+  // in turn: an upload waits only for the copy out of the area it reuses
+  struct Stage {
+    uint8_t* p = nullptr;  // pinned host buffer
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+    bool pending = false;
+    uint8_t* dev = nullptr;  // device buffer the copy goes to (stream-ordered reuse)
+    size_t dcap = 0;
+  };
+  static constexpr int kStages = 4;
+  Stage stg[kStages];
+  int stg_next = 0;
+  std::vector<HostProgram> pipe;  // chunk programs of the pipelined apply (reused)
+  HostProgram pipe_merged;        // consecutive chunks taken as one program
 };
 
 struct tab_prog_s {
@@ -78,6 +92,7 @@ struct DevProg {
   uint2* blk = nullptr;       // block records, for the block gate kernel
   uint32_t* blk_off = nullptr;
   void* base = nullptr;       // single allocation holding all of the above (staged uploads)
+  bool kept = false;          // base is a staging area's device buffer: not freed after use
 };
 
 namespace {
@@ -256,12 +271,21 @@ int run_program(tab_t h, const HostProgram& hp, const DevProg& dp, uint64_t seed
   }
   const GateKernel gk = gate_kernel(h->n);
   const bool can_blk = (hp.mode & kProgBlocks) != 0, can_lay = (hp.mode & kProgLayers) != 0;
-  for (const Seg& s : hp.segs) {
+  for (size_t si = 0; si < hp.segs.size(); ++si) {
+    const Seg& s = hp.segs[si];
     if (s.kind == 0) {
-      if (can_blk && (gk == GK_BLOCK || (!can_lay && dp.rec == nullptr)))
+      if (can_blk && (gk == GK_BLOCK || (!can_lay && dp.rec == nullptr))) {
+        // gate runs that follow one another with adjacent super-layer offsets
+        // (pieces of one list compiled apart) run as one launch: the shared
+        // bound between two runs is an empty super-layer
+        size_t sj = si;
+        while (sj + 1 < hp.segs.size() && hp.segs[sj + 1].kind == 0 &&
+               hp.segs[sj + 1].blk_begin == hp.segs[sj].blk_end + 1)
+          ++sj;
         CU(launch_gates_block(h->X, h->Z, h->R, h->n, h->W, dp.blk, dp.blk_off + s.blk_begin,
-                              (int)(s.blk_end - s.blk_begin), h->mw.err, h->stream));
-      else if (dp.rec != nullptr && (gk == GK_FLOW || !can_lay))
+                              (int)(hp.segs[sj].blk_end - s.blk_begin), h->mw.err, h->stream));
+        si = sj;
+      } else if (dp.rec != nullptr && (gk == GK_FLOW || !can_lay))
         CU(launch_gates_flow(h->X, h->Z, h->R, h->n, h->W, dp.rec, s.op_begin, s.op_end,
                              h->mw.err, h->stream));
       else
@@ -354,6 +378,7 @@ int upload(const HostProgram& hp, DevProg* d, cudaStream_t s, bool async_alloc) 
 }
 
 void free_async(DevProg& d, cudaStream_t s) {
+  if (d.kept) return;
   if (d.base) {
     cudaFreeAsync(d.base, s);
     return;
@@ -366,9 +391,13 @@ void free_async(DevProg& d, cudaStream_t s) {
   if (d.blk_off) cudaFreeAsync(d.blk_off, s);
 }
 
-// Upload a compiled program through the handle's pinned staging area: one
-// stream-ordered allocation and one asynchronous copy.  The staging area is
-// reused once the previous copy out of it has completed.
+// Upload a compiled program through the handle's next staging area: one
+// asynchronous copy from its pinned host buffer into its device buffer.  The
+// host buffer is reused once the copy out of it has completed, so up to
+// kStages uploads can be in flight behind the kernels of earlier ones; the
+// device buffer is rewritten only by later work on the handle's stream, after
+// the kernels that read it.  Programs above kKeptMax bytes get a device
+// allocation of their own, freed after use.
 int upload_staged(tab_t h, const HostProgram& hp, DevProg* d) {
   const bool want_rec =
       hp.n_gates > 0 && ((hp.mode & kProgStream) || ((hp.mode & kProgLayers) && use_flow_gates(hp.n)));
@@ -380,20 +409,22 @@ int upload_staged(tab_t h, const HostProgram& hp, DevProg* d) {
   const size_t bb = want_blk ? align256((hp.blk.size() + kOpsPad) * sizeof(uint2)) : 0;
   const size_t bo = want_blk ? align256(std::max<size_t>(hp.blk_off.size(), 1) * 4) : 0;
   const size_t total = ob + lb + sb + rb + bb + bo;
-  if (h->stg_pending) {
-    CU(cudaEventSynchronize(h->stg_ev));
-    h->stg_pending = false;
+  tab_s::Stage& sg = h->stg[h->stg_next];
+  h->stg_next = (h->stg_next + 1) % tab_s::kStages;
+  if (sg.pending) {
+    CU(cudaEventSynchronize(sg.ev));
+    sg.pending = false;
   }
-  if (h->stg_cap < total) {
-    if (h->stg) cudaFreeHost(h->stg);
-    h->stg = nullptr;
-    h->stg_cap = 0;
+  if (sg.cap < total) {
+    if (sg.p) cudaFreeHost(sg.p);
+    sg.p = nullptr;
+    sg.cap = 0;
     const size_t cap = total + total / 4;
-    CU(cudaMallocHost((void**)&h->stg, cap));
-    h->stg_cap = cap;
+    CU(cudaMallocHost((void**)&sg.p, cap));
+    sg.cap = cap;
   }
-  if (!h->stg_ev) CU(cudaEventCreateWithFlags(&h->stg_ev, cudaEventDisableTiming));
-  uint8_t* st = h->stg;
+  if (!sg.ev) CU(cudaEventCreateWithFlags(&sg.ev, cudaEventDisableTiming));
+  uint8_t* st = sg.p;
   uint32_t* ops = reinterpret_cast<uint32_t*>(st);
   if (!hp.ops.empty()) memcpy(ops, hp.ops.data(), hp.ops.size() * 4);
   memset(ops + hp.ops.size(), 0, (size_t)kOpsPad * 4);
@@ -420,12 +451,26 @@ int upload_staged(tab_t h, const HostProgram& hp, DevProg* d) {
     memset(b0 + hp.blk.size() * sizeof(uint2), 0, (size_t)kOpsPad * sizeof(uint2));
     if (!hp.blk_off.empty()) memcpy(b0 + bb, hp.blk_off.data(), hp.blk_off.size() * 4);
   }
+  constexpr size_t kKeptMax = (size_t)64 << 20;
   uint8_t* dev = nullptr;
-  CU(cudaMallocAsync((void**)&dev, total, h->stream));
+  d->kept = total <= kKeptMax;
+  if (d->kept) {
+    if (sg.dcap < total) {
+      if (sg.dev) CU(cudaFreeAsync(sg.dev, h->stream));
+      sg.dev = nullptr;
+      sg.dcap = 0;
+      const size_t cap = std::min(kKeptMax, total + total / 4);
+      CU(cudaMallocAsync((void**)&sg.dev, cap, h->stream));
+      sg.dcap = cap;
+    }
+    dev = sg.dev;
+  } else {
+    CU(cudaMallocAsync((void**)&dev, total, h->stream));
+  }
   CU(cudaMemcpyAsync(dev, st, total, cudaMemcpyHostToDevice, h->stream));
   h->h2d_bytes += (int64_t)total;
-  CU(cudaEventRecord(h->stg_ev, h->stream));
-  h->stg_pending = true;
+  CU(cudaEventRecord(sg.ev, h->stream));
+  sg.pending = true;
   d->base = dev;
   d->ops = reinterpret_cast<uint32_t*>(dev);
   d->layer = reinterpret_cast<uint32_t*>(dev + ob);
@@ -552,10 +597,14 @@ int tab_destroy(tab_t h) {
   if (!h) return TAB_OK;
   cudaStreamSynchronize(h->stream);
   if (h->log) cudaFreeAsync(h->log, h->stream);
+  for (tab_s::Stage& sg : h->stg)
+    if (sg.dev) cudaFreeAsync(sg.dev, h->stream);
   cudaStreamSynchronize(h->stream);
   if (h->own_mem && h->base) cudaFree(h->base);
-  if (h->stg) cudaFreeHost(h->stg);
-  if (h->stg_ev) cudaEventDestroy(h->stg_ev);
+  for (tab_s::Stage& sg : h->stg) {
+    if (sg.p) cudaFreeHost(sg.p);
+    if (sg.ev) cudaEventDestroy(sg.ev);
+  }
   delete h;
   return TAB_OK;
 }
@@ -574,7 +623,16 @@ int tab_set_stream(tab_t h, void* cuda_stream) {
     set_error("null handle");
     return TAB_EINVAL;
   }
-  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (s != h->stream) {
+    // the staging buffers are reused in the order of the handle's stream
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      set_error("cuda: %s", cudaGetErrorString(e));
+      return TAB_ECUDA;
+    }
+  }
+  h->stream = s;
   return TAB_OK;
 }
 
@@ -599,9 +657,86 @@ int tab_reset(tab_t h) {
   return TAB_OK;
 }
 
+// Largest chunk (words) of the pipelined tab_apply: TAB_APPLY_CHUNK when set
+// (0 turns the pipeline off), else about a quarter of the list per compile
+// thread, within [2^13, 2^16] -- several rounds of chunks, so that the GPU
+// work of the last round, which no compile hides, stays short.
+static int64_t apply_chunk(int64_t count) {
+  static int64_t env = -2;
+  if (env == -2) {
+    const char* e = getenv("TAB_APPLY_CHUNK");
+    env = e ? std::max<int64_t>(0, atoll(e)) : -1;
+  }
+  if (env >= 0) return env;
+  const int64_t per = count / (4 * (int64_t)std::max(1, pool_threads() - 1));
+  return std::min<int64_t>((int64_t)1 << 16, std::max<int64_t>((int64_t)1 << 13, per));
+}
+
+// tab_apply for a long list on the block-kernel engines: the whole list is
+// validated first (nothing runs if any word is bad), then its chunks are
+// compiled by the host pool in list order while one pool thread uploads and
+// launches them, so the GPU starts on the first chunk while later ones are
+// still being compiled.  The chunks grow from 2^13 words (the GPU starts
+// early) to `chunk`; the launcher takes every chunk compiled by the time it
+// is free as one program (one upload, one gate launch per gate run).
+static int apply_pipelined(tab_t h, const tab_gate* gates, int64_t count, int64_t chunk) {
+  int rc = validate_program(h->n, gates, count);
+  if (rc) return rc;
+  std::vector<int64_t> bnd(1, 0);
+  for (int64_t s = std::min<int64_t>(chunk, (int64_t)1 << 13); bnd.back() < count;
+       s = std::min<int64_t>(chunk, 2 * s))
+    bnd.push_back(std::min<int64_t>(count, bnd.back() + s));
+  const int nc = (int)bnd.size() - 1;
+  if (h->pipe.size() < (size_t)nc) h->pipe.resize((size_t)nc);
+  std::vector<HostProgram>& parts = h->pipe;
+  std::unique_ptr<std::atomic<int>[]> state(new std::atomic<int>[(size_t)nc]);
+  for (int i = 0; i < nc; ++i) state[i].store(0);
+  int crc = TAB_OK;
+  std::string cmsg;
+  pool_run(nc + 1, [&](int idx) {
+    if (idx == 0) {  // the launcher (indices are taken in order: it starts first)
+      cudaSetDevice(h->dev);
+      for (int i = 0; i < nc;) {
+        while (state[i].load(std::memory_order_acquire) == 0) std::this_thread::yield();
+        int j = i + 1;
+        while (j < nc && state[j].load(std::memory_order_acquire) != 0) ++j;
+        int r = TAB_OK;
+        for (int c = i; c < j; ++c)
+          if (state[c].load(std::memory_order_relaxed) < 0) r = TAB_EINVAL;
+        if (r != TAB_OK && crc == TAB_OK) cmsg = "chunk compile failed";
+        const HostProgram* hp = &parts[(size_t)i];
+        if (r == TAB_OK && crc == TAB_OK && j - i > 1) {
+          concat_programs(h->pipe_merged, hp, (size_t)(j - i));
+          hp = &h->pipe_merged;
+        }
+        if (r == TAB_OK && crc == TAB_OK && hp->n_gates + hp->n_meas > 0) {
+          DevProg d;
+          r = upload_staged(h, *hp, &d);
+          if (r == TAB_OK) r = run_program(h, *hp, d, h->seed);
+          free_async(d, h->stream);
+          if (r != TAB_OK) cmsg = last_error();
+        }
+        if (r != TAB_OK && crc == TAB_OK) crc = r;
+        i = j;
+      }
+      return;
+    }
+    const int i = idx - 1;
+    const int64_t b = bnd[(size_t)i], e = bnd[(size_t)i + 1];
+    const int r = build_validated_blocks(h->n, gates + b, e - b, &parts[(size_t)i]);
+    state[i].store(r == TAB_OK ? 1 : -1, std::memory_order_release);
+  });
+  if (crc != TAB_OK) set_error("%s", cmsg.c_str());
+  return crc;
+}
+
 int tab_apply(tab_t h, const tab_gate* gates, int64_t count) {
   int rc = check_handle(h);
   if (rc) return rc;
+  if (compile_mode_for(h) == kProgBlocks && count >= ((int64_t)1 << 17) && pool_threads() >= 3) {
+    const int64_t chunk = apply_chunk(count);
+    if (chunk > 0) return apply_pipelined(h, gates, count, chunk);
+  }
   HostProgram hp;
   rc = build_program(h->n, gates, count, &hp, compile_mode_for(h));
   if (rc) return rc;

@@ -77,6 +77,19 @@ struct HostProgram {
   std::vector<uint32_t> vers;
   std::vector<uint32_t> layer_off;  // size = layers + 1 when any gate exists
   std::vector<Seg> segs;
+  // empty program for n qubits (the arrays keep their capacity)
+  void clear(int32_t n_) {
+    n = n_;
+    layered = true;
+    mode = kProgLayers;
+    n_gates = n_meas = 0;
+    blk.clear();
+    blk_off.clear();
+    ops.clear();
+    vers.clear();
+    layer_off.clear();
+    segs.clear();
+  }
 };
 
 // Validate and compile a gate list into the forms `mode` asks for (see
@@ -84,6 +97,17 @@ struct HostProgram {
 // Returns TAB_OK or an error (message set).
 int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out,
                   int mode = kProgLayers);
+// Validate a gate list (in parallel on the host pool): TAB_OK, or the error of
+// the first bad word in list order (message set).
+int validate_program(int32_t n, const tab_gate* gates, int64_t count);
+// Compile an already validated piece of a gate list into blocks (kProgBlocks).
+int build_validated_blocks(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out);
+// Concatenate part[0..T) -- programs compiled for consecutive pieces of one
+// gate list, in list order -- into P: each piece's arrays copied and its
+// offsets shifted (pieces in parallel on the host pool).  Consecutive gate
+// runs keep adjacent super-layer offsets: the last bound of one run equals
+// the first of the next.
+void concat_programs(HostProgram& P, const HostProgram* part, size_t T);
 
 // Block compiler for one gate run at a time (blocks.cpp).
 struct BlkRec {
@@ -103,6 +127,8 @@ class BlockBuilder {
   std::vector<uint32_t> stamp_; // run id of cur_ / role_ entries
   uint32_t seg_ = 0;
   std::vector<BlkRec> blk_;
+  std::vector<uint32_t> key_, cnt_;  // emit scratch: sort key per block, bucket counts
+  std::vector<uint2> rec_;           // emit scratch: packed record per block
 };
 
 // ---- global grid barrier state ----------------------------------------------------

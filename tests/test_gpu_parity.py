@@ -182,6 +182,44 @@ def test_invalid_gate_applies_nothing():
         assert np.array_equal(a, b)
 
 
+def test_pipelined_apply_mid_circuit_measurements():
+    """A list of more than 2^17 words on the grid engine is compiled in 2^16-
+    word chunks while earlier chunks already run; MZR rounds every 5 layers put
+    measurement runs across chunk boundaries.  Compared with the oracle bit for
+    bit, and with the same list applied in pieces that each run whole."""
+    c = C.random_layer_circuit(700, 140, seed=21, meas_every=5, meas_frac=0.05)
+    assert c.gates.size >= (1 << 17)
+    assert_same(c.n, c.gates, seed=3, engine=tab.ENGINE_GRID)
+    with tab.Tableau(c.n) as t:
+        t.set_engine(tab.ENGINE_GRID)
+        t.set_rng(3, 0, 0)
+        for s in range(0, c.gates.size, 40_000):
+            t.apply(c.gates[s:s + 40_000])
+        out = t.read_outcomes()
+        got = t.export()
+    want_out, want = oracle_result(c.n, c.gates, 3, 0, 0)
+    assert np.array_equal(out, want_out)
+    for g, w in zip(got, want):
+        assert np.array_equal(g, w)
+
+
+def test_pipelined_apply_invalid_word_applies_nothing():
+    """The long-list path validates the whole list before its first launch."""
+    c = C.random_layer_circuit(600, 160, seed=22, final_measure=False)
+    bad = np.concatenate([c.gates, C.encode(C.TAB_CNOT, 3, 600).reshape(1)])
+    assert bad.size >= (1 << 17)
+    with tab.Tableau(c.n) as t:
+        t.set_engine(tab.ENGINE_GRID)
+        t.apply(c.gates[:1000])
+        before = t.export()
+        with pytest.raises(tab.TabError) as ei:
+            t.apply(bad)
+        assert ei.value.code == tab.TAB_ERANGE
+        after = t.export()
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("engine", ENGINES)
 def test_checkpoint_resume(engine):
     n = 150
