@@ -13,7 +13,9 @@ every rank runs an independent replica on its own GPU (weak scaling, no
 collective on the data path); rank 0 prints.
 
 Other workloads (`--workload`): `cfg1` (n=10), `cfg3` (n=10,000 with MZR
-rounds), `batched` (4,096 circuits with n in [16, 512] and 1-64 shots).
+rounds), `batched` (4,096 circuits with n in [16, 512] and 1-64 shots),
+`sweep` (the paper's own benchmark: uniformly random n-qubit Cliffords, no
+measurements, n = 2 ... 8192; one JSON line with a point per n).
 """
 from __future__ import annotations
 
@@ -54,7 +56,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="cfg2",
-                   choices=["cfg1", "cfg2", "cfg3", "batched", "served"])
+                   choices=["cfg1", "cfg2", "cfg3", "batched", "served", "sweep"])
+    p.add_argument("--sweep-max", type=int, default=8192, help="sweep: largest n")
     p.add_argument("--requests", type=int, default=48, help="served: number of requests")
     p.add_argument("--circuits", type=int, default=4096, help="batched: number of circuits")
     p.add_argument("--engine", default="auto",
@@ -619,13 +622,98 @@ def run_served(args, ws, rank, local):
     return line
 
 
+# ----------------------------------------------------------------- sweep ---
+
+SWEEP_COUNT = {1024: 10, 2048: 5, 4096: 3, 8192: 2}   # circuits per n (100 below 512)
+
+
+def run_sweep(args, ws, rank, local):
+    """Uniformly random Cliffords (the paper's Fig. 2a workload), no
+    measurements: per n, each circuit is applied to |0^n> through the public
+    API with its gate list in host memory (host compile, upload and device
+    work inside the timed region), after one untimed warm-up circuit.  The
+    device column is CUDA-event time of the same circuit compiled and uploaded
+    beforehand (tab.Program), on the handle's stream; the CPU column is the
+    oracle on one core for n <= 512 (a time-bounded sample of circuits)."""
+    import torch
+    from paper_2408_00384_gb300 import tab
+    from workloads import circuits as C
+
+    torch.cuda.set_device(local)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    clocks = ClockSampler(local)
+    clocks.start()
+    points = []
+    for n in [m for m in C.CLIFFORD_SWEEP_N if m <= args.sweep_max]:
+        count = SWEEP_COUNT.get(n, 30 if n == 512 else 100)
+        circs = C.clifford_sweep(n, count + 1)
+        t = tab.Tableau(n)
+        t.apply(circs[0].gates)          # warm-up: kernels, staging, host pool
+        t.sync()
+        e2e, dev = [], []
+        for c in circs[1:]:
+            flush.fill_(len(e2e) & 0xFF)
+            t.reset()
+            torch.cuda.synchronize()
+            h0 = time.perf_counter()
+            t.apply(c.gates)
+            t.sync()
+            e2e.append(time.perf_counter() - h0)
+            # device time: the same circuit compiled and uploaded beforehand
+            prog = tab.Program(n, c.gates)
+            flush.fill_(len(e2e) & 0xFF)
+            t.reset()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            t.run(prog)
+            e1.record()
+            torch.cuda.synchronize()
+            dev.append(e0.elapsed_time(e1) / 1000.0)
+            prog.close()
+        t.close()
+        gates = statistics.mean(c.n_gates for c in circs[1:])
+        pt = {"n": n, "circuits": count, "gates_per_circuit": gates,
+              "e2e_ms": 1000.0 * statistics.median(e2e),
+              "device_ms": 1000.0 * statistics.median(dev),
+              "gates_per_s_e2e": gates / statistics.median(e2e)}
+        if n <= 512 and not args.no_cpu_baseline and rank == 0:
+            import oracle
+            done, t0 = 0, time.perf_counter()
+            while done < count and time.perf_counter() - t0 < 2.0:
+                oracle.run_circuit(n, circs[1 + done].gates)
+                done += 1
+            cpu = (time.perf_counter() - t0) / done
+            pt["cpu_baseline"] = {"ms": 1000.0 * cpu, "cores": 1, "kind": "oracle",
+                                  "sample": f"{done} of {count} circuits"}
+        points.append(pt)
+    clk = clocks.stop()
+    # smallest n from which every compared point has the GPU ahead of the oracle
+    cmp_pts = [p for p in points if "cpu_baseline" in p]
+    cross = None
+    for i, p in enumerate(cmp_pts):
+        if all(q["e2e_ms"] < q["cpu_baseline"]["ms"] for q in cmp_pts[i:]):
+            cross = p["n"]
+            break
+    return {"metric": "uniformly random Clifford circuits: time per circuit vs n",
+            "unit": "ms per circuit", "n_gpus": ws, "higher_is_better": False,
+            "data": "synthetic", "dtype": "u32",
+            "config": {"workload": "uniformly random n-qubit Cliffords (Bruhat form "
+                                   "b1 w b2 of Sp(2n,2)), no measurements, n = 2 ... "
+                                   f"{args.sweep_max}", "l2": "flushed before every circuit"},
+            "points": points, "gpu_faster_than_oracle_from_n": cross, "clocks": clk}
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)
         return
-    if args.workload == "batched":
+    if args.workload == "sweep":
+        line = run_sweep(args, ws, rank, local)
+    elif args.workload == "batched":
         line = run_batched(args, ws, rank, local)
     elif args.workload == "served":
         line = run_served(args, ws, rank, local)

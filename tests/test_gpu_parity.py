@@ -182,6 +182,20 @@ def test_invalid_gate_applies_nothing():
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 33, 64, 100, 257, 600])
+def test_uniform_random_cliffords(n):
+    """The paper's own workload (uniformly random Cliffords, no measurements)
+    on the default engines, bit for bit against the oracle."""
+    c = C.random_clifford(n, C.splitmix64(4242 + n))
+    assert_same(n, c.gates)
+
+
+@pytest.mark.parametrize("engine", [tab.ENGINE_GRID, tab.ENGINE_CLUSTER, tab.ENGINE_STREAM])
+def test_uniform_random_clifford_engines(engine):
+    c = C.random_clifford(300, C.splitmix64(4343))
+    assert_same(300, c.gates, engine=engine)
+
+
 def test_pipelined_apply_mid_circuit_measurements():
     """A list of more than 2^17 words on the grid engine is compiled in 2^16-
     word chunks while earlier chunks already run; MZR rounds every 5 layers put

@@ -250,3 +250,193 @@ def count_ops(gates: np.ndarray):
     meas = int(np.isin(op, MEASURE).sum())
     gates_n = int(np.isin(op, ONE_QUBIT + TWO_QUBIT).sum())
     return gates_n, meas
+
+
+# ---- uniformly random Cliffords (the paper's own benchmark family) ---------
+#
+# The paper times uniformly random n-qubit Clifford circuits drawn with the
+# method of Bravyi and Maslov (Section "Simulation of Clifford circuits",
+# Fig. 2a).  Their canonical form writes a Clifford as F1 . (Hadamards,
+# permutation) . F2 with Hadamard-free F1, F2; it is the Bruhat decomposition
+# of the symplectic group Sp(2n, 2) with respect to the Borel subgroup B of
+# Hadamard-free Cliffords that keep the flag <Z_1> < <Z_1, Z_2> < ... .  The
+# sampler below draws from that decomposition directly:
+#
+#   C = P . b1 . w . b2        (b2 applied first)
+#
+# * b1, b2 uniform in B (mod Paulis).  B is the product of the group of CNOT
+#   circuits whose map on computational basis states is unit lower triangular
+#   (CNOT c -> t with c < t) and the abelian group of diagonal CZ / S layers
+#   (a symmetric GF(2) matrix Gamma: CZ(i, j) where Gamma_ij = 1, S(i) where
+#   Gamma_ii = 1); |B| = 2^(n(n-1)/2) 2^(n(n+1)/2) = 2^(n^2).
+# * w a Weyl group element (a signed permutation: Hadamards on a subset, then
+#   a qubit permutation) drawn with probability 2^len(w) / prod_j (4^j - 1),
+#   len the Coxeter length.  The double coset B w B holds |B| 2^len(w)
+#   elements and every element of it is b1 w b2 for exactly |B| / 2^len(w)
+#   pairs (b1, b2), so C mod Paulis is uniform on Sp(2n, 2).
+# * P a uniform Pauli layer, which makes the signs uniform.
+#
+# The Weyl group is the hyperoctahedral group B_n with generators s_0 (sign
+# change of the first letter) and s_i (exchange of letters i, i+1); its
+# length is inv(w) + #{i <= j : w(i) + w(j) < 0} (Bjorner & Brenti,
+# Combinatorics of Coxeter Groups, Sec. 8.1).  Letter k of a signed
+# permutation stands for qubit n - k (0-based), sign + for X and - for Z:
+# s_0 is H on qubit n - 1 and s_i is SWAP(n - i, n - i - 1), the Weyl elements
+# of length one for the flag above.  A signed permutation is built by
+# inserting the letters 1, 2, ..., n: +m inserted with c smaller letters after
+# it adds c to the length (c in [0, m)), -m inserted with c - m letters
+# before it adds c (c in [m, 2m)); drawing c with probability proportional to
+# 2^c at each step gives the 2^len(w) law exactly.
+
+
+def _trunc_geometric(rng: np.random.Generator, m: int) -> int:
+    """K in [0, 2m) with P(K = k) = 2^(2m-1-k) / (4^m - 1): the count of
+    leading zeros of a uniform nonzero 2m-bit integer, read from raw 64-bit
+    draws (exact, platform independent)."""
+    total = 2 * m
+    while True:
+        k = 0
+        while k < total:
+            take = min(64, total - k)
+            word = int(rng.bit_generator.random_raw()) >> (64 - take)
+            if word:
+                return k + take - word.bit_length()
+            k += take
+
+
+def signed_perm_from_code(code) -> List[int]:
+    """The signed permutation (letters w(1..n)) whose insertion code is
+    ``code`` (code[m-1] in [0, 2m) is the length added by letter m)."""
+    seq: List[int] = []
+    for m, c in enumerate(code, start=1):
+        if not 0 <= c < 2 * m:
+            raise ValueError(f"code[{m - 1}] = {c} outside [0, {2 * m})")
+        if c < m:
+            seq.insert(m - 1 - c, m)
+        else:
+            seq.insert(c - m, -m)
+    return seq
+
+
+def sample_weyl(rng: np.random.Generator, n: int) -> List[int]:
+    """A signed permutation of n letters with probability 2^len / prod (4^j - 1)."""
+    return signed_perm_from_code([2 * m - 1 - _trunc_geometric(rng, m)
+                                  for m in range(1, n + 1)])
+
+
+def borel_words(L: np.ndarray, G: np.ndarray) -> List[np.ndarray]:
+    """Gate words of the element of B (mod Paulis) given by the n x n GF(2)
+    matrices L (entries below the diagonal: L[t, c] = 1 puts CNOT c -> t) and
+    G (upper triangle and diagonal: G[i, j] = 1 puts CZ(i, j), G[i, i] = 1
+    puts S(i)); the CNOT part comes first."""
+    n = L.shape[0]
+    parts: List[np.ndarray] = []
+    # CNOT c -> t (c < t) in rounds of equal c + t, largest sum first.  A
+    # round is a set of disjoint pairs, and every gate controlled by q (sum
+    # > 2q) precedes every gate targeting q (sum < 2q), so each x_t ^= x_c
+    # reads the original x_c: the basis-state map is I + (lower part of L),
+    # in 2n - 3 rounds instead of the n^2/4 of a target-by-target order
+    for sm in range(2 * n - 3, 0, -1):
+        c = np.arange(max(0, sm - n + 1), (sm - 1) // 2 + 1)
+        t = sm - c
+        on = L[t, c].astype(bool)
+        if on.any():
+            parts.append(encode(np.full(int(on.sum()), TAB_CNOT), c[on], t[on]))
+    # CZ on the pairs of a round-robin schedule (n - 1 rounds of disjoint
+    # pairs; the gates commute, so the order only sets the depth), then S
+    m = n + (n & 1)
+    ring = np.arange(1, m)
+    for r in range(m - 1):
+        rot = np.roll(ring, r)
+        a = np.concatenate(([0], rot[: m // 2 - 1]))
+        b = rot[::-1][: m // 2]
+        keep = (a < n) & (b < n)
+        lo, hi = np.minimum(a, b)[keep], np.maximum(a, b)[keep]
+        on = G[lo, hi].astype(bool)
+        if on.any():
+            parts.append(encode(np.full(int(on.sum()), TAB_CZ), lo[on], hi[on]))
+    s = np.nonzero(np.diagonal(G))[0]
+    if s.size:
+        parts.append(encode(np.full(s.size, TAB_S), s, 0))
+    return parts
+
+
+def _borel_words(rng: np.random.Generator, n: int) -> List[np.ndarray]:
+    """A uniform element of B (mod Paulis): every entry of L and G that
+    borel_words reads is an independent fair bit."""
+    L = rng.integers(0, 2, size=(n, n), dtype=np.uint8)
+    G = rng.integers(0, 2, size=(n, n), dtype=np.uint8)
+    return borel_words(L, G)
+
+
+def _weyl_words(w: List[int]) -> List[np.ndarray]:
+    """Gate words of the Weyl element ``w``: H on every qubit whose letter is
+    negative, then SWAPs that carry qubit n - k to qubit n - |w(k)|."""
+    n = len(w)
+    parts: List[np.ndarray] = []
+    neg = np.array([n - k for k in range(1, n + 1) if w[k - 1] < 0], dtype=np.int64)
+    if neg.size:
+        parts.append(encode(np.full(neg.size, TAB_H), np.sort(neg), 0))
+    dest = [0] * n                      # dest[q]: where the state of qubit q goes
+    for k in range(1, n + 1):
+        dest[n - k] = n - abs(w[k - 1])
+    src = [0] * n
+    for q in range(n):
+        src[dest[q]] = q
+    loc = list(range(n))                # loc[s]: qubit now holding state s
+    at = list(range(n))                 # at[p]: state now on qubit p
+    sw_a, sw_b = [], []
+    for t in range(n):
+        s_ = src[t]
+        p = loc[s_]
+        if p != t:
+            sw_a.append(min(p, t))
+            sw_b.append(max(p, t))
+            u = at[t]
+            at[p], at[t] = u, s_
+            loc[u], loc[s_] = p, t
+    if sw_a:
+        parts.append(encode(np.full(len(sw_a), TAB_SWAP), np.array(sw_a), np.array(sw_b)))
+    return parts
+
+
+def _pauli_words(rng: np.random.Generator, n: int) -> List[np.ndarray]:
+    xz = rng.integers(0, 4, size=n)
+    q = np.nonzero(xz)[0]
+    if not q.size:
+        return []
+    op = np.array([TAB_I, TAB_X, TAB_Z, TAB_Y], dtype=np.int64)[xz[q]]
+    return [encode(op, q, 0)]
+
+
+def clifford_from_parts(n: int, b2: List[np.ndarray], w: List[int], b1: List[np.ndarray],
+                        pauli: List[np.ndarray]) -> np.ndarray:
+    """Gate list of P . b1 . w . b2 (b2 first) from the parts' gate words."""
+    parts = list(b2) + _weyl_words(w) + list(b1) + list(pauli)
+    return np.concatenate(parts) if parts else np.zeros(0, np.uint64)
+
+
+def random_clifford(n: int, seed: int, circuit_id: int = 0) -> Circuit:
+    """A uniformly random n-qubit Clifford (mod global phase) as a gate list,
+    no measurements: the circuit applied to |0^n> leaves the tableau of that
+    Clifford.  About n^2 gates (n^2/4 CNOT and n^2/4 CZ in each of b1, b2)."""
+    if n < 1:
+        raise ValueError("n must be >= 1")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    b2 = _borel_words(rng, n)
+    w = sample_weyl(rng, n)
+    b1 = _borel_words(rng, n)
+    pauli = _pauli_words(rng, n)
+    gates = clifford_from_parts(n, b2, w, b1, pauli)
+    return Circuit(n=n, gates=gates, n_gates=int(gates.size), n_meas=0,
+                   circuit_id=circuit_id)
+
+
+CLIFFORD_SWEEP_N = tuple(2 ** k for k in range(1, 14))   # 2 .. 8192, as in Fig. 2a
+
+
+def clifford_sweep(n: int, count: int):
+    """``count`` seeded uniformly random Cliffords on n qubits (the paper
+    draws 100 per n)."""
+    return [random_clifford(n, splitmix64((CONFIG_SEED + 7919 * 6 + n) ^ c), circuit_id=c)
+            for c in range(count)]
