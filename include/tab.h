@@ -56,8 +56,26 @@ enum tab_op {
   TAB_CZ = 8, TAB_SWAP = 9,
   TAB_MZ = 10,  /* measure Z; outcome appended to the handle's outcome log */
   TAB_MZR = 11, /* measure Z, then apply X when the outcome is 1 (reset to |0>) */
-  TAB_BARRIER = 12
+  TAB_BARRIER = 12,
+  /* Extended ops, accepted by tab_apply and (all but the noise ops) by
+   * tab_prog_create; batches and the server reject them (TAB_EINVAL).  They
+   * are lowered to the ops above on the host. */
+  TAB_MX = 13,     /* measure X: H, TAB_MZ, H (outcome logged like TAB_MZ) */
+  TAB_MY = 14,     /* measure Y: S^dag, H, TAB_MZ, H, S */
+  TAB_DEPOL1 = 15, /* depolarizing noise on q1: X, Y or Z with total probability p */
+  TAB_XERR = 16,   /* X on q1 with probability p */
+  TAB_ZERR = 17    /* Z on q1 with probability p */
 };
+
+/* Noise ops carry p in the second-qubit field as a 28-bit fraction (p = field
+ * / 2^28).  Noise op j -- counted per handle from 0 after tab_set_rng or
+ * tab_reset, in program order -- draws r = Philox4x32-10 with counter
+ * (j, shot, circuit_id lo, circuit_id hi) and key (seed lo, seed hi XOR
+ * 0x4E4F4953).  It fires when (r.x >> 4) < field; TAB_DEPOL1 then applies
+ * X, Y or Z for floor(r.y * 3 / 2^32) = 0, 1 or 2.  The draws are taken on
+ * the host when tab_apply compiles the list (the noise of a circuit does not
+ * depend on its state), so a fired noise op costs one Pauli gate and an
+ * unfired one nothing. */
 
 enum tab_status {
   TAB_OK = 0,

@@ -129,7 +129,7 @@ class Tableau:
         """Run a gate-word list; returns outcome bytes (and deterministic flags)."""
         gates = np.ascontiguousarray(gates, dtype=np.uint64)
         op = (gates >> np.uint64(56)).astype(np.int64)
-        cap = int(np.isin(op, (10, 11)).sum())
+        cap = int(np.isin(op, (10, 11, 13, 14)).sum())
         out = np.zeros(max(cap, 1), dtype=np.uint8)
         det = np.zeros(max(cap, 1), dtype=np.uint8)
         ctr = ctypes.c_uint64(self.meas_counter)

@@ -33,7 +33,15 @@
  *  - the k-th measurement op of a (circuit, shot) draws Philox counter
  *    (k, shot, circuit_id lo, circuit_id hi) under key (seed lo, seed hi) and
  *    uses bit 0 of output word 0, whether or not the outcome is random;
- *  - MZR = measure, then apply X_a when the outcome is 1.
+ *  - MZR = measure, then apply X_a when the outcome is 1;
+ *  - MX and MY measure X_a and Y_a by conjugation: X = H Z H, and
+ *    Y = (H S^dagger)^dagger Z (H S^dagger), i.e. S^dagger, H, measure Z,
+ *    H, S; they draw from the same measurement counter as MZ;
+ *  - noise op j (DEPOL1, XERR, ZERR; counted per tableau from 0 in program
+ *    order) draws Philox counter (j, shot, circuit_id lo, circuit_id hi) under
+ *    key (seed lo, seed hi XOR 0x4E4F4953); it fires when word 0 shifted
+ *    right by 4 is below the 28-bit probability field, and DEPOL1 then takes
+ *    X, Y or Z by floor(word 1 * 3 / 2^32).
  *
  * Parity pins: gate rules and g against explicit Pauli matrices; the whole
  * simulator against brute-force state vectors (n <= 10), known states and the
@@ -53,6 +61,7 @@ typedef struct {
   int32_t n;
   int64_t rows; /* 2n + 1: the last row is AG's scratch row */
   uint8_t *x, *z, *r;
+  uint64_t noise_counter; /* next noise-op index */
 } orc_tab;
 
 /* storage: element (row i, qubit j) at [j * rows + i] */
@@ -64,6 +73,7 @@ void orc_reset(orc_tab *t) {
   memset(t->x, 0, (size_t)cells);
   memset(t->z, 0, (size_t)cells);
   memset(t->r, 0, (size_t)t->rows);
+  t->noise_counter = 0;
   /* |0^n>: destabilizer i = X_i, stabilizer n+i = Z_i, all signs + */
   for (int32_t i = 0; i < t->n; i++) {
     XB(t, i, i) = 1;
@@ -252,7 +262,7 @@ int64_t orc_run(orc_tab *t, const uint64_t *gates, int64_t count, uint64_t seed,
     int64_t q1 = (int64_t)((g >> 28) & 0xFFFFFFFull);
     int64_t q2 = (int64_t)(g & 0xFFFFFFFull);
     int two = (op == 7 || op == 8 || op == 9);
-    if (op < 0 || op > 12) return ORC_EINVAL;
+    if (op < 0 || op > 17) return ORC_EINVAL;
     if (op != 12 && q1 >= t->n) return ORC_ERANGE;
     if (two && (q2 >= t->n)) return ORC_ERANGE;
     if (two && q1 == q2) return ORC_EINVAL;
@@ -268,7 +278,10 @@ int64_t orc_run(orc_tab *t, const uint64_t *gates, int64_t count, uint64_t seed,
       case 7: orc_cnot(t, a, b); break;
       case 8: orc_cz(t, a, b); break;
       case 9: orc_swap(t, a, b); break;
-      case 10: case 11: {
+      case 10: case 11: case 13: case 14: {
+        /* MX, MY: rotate the measured Pauli onto Z_a, measure, rotate back */
+        if (op == 14) orc_sdg(t, a);
+        if (op == 13 || op == 14) orc_h(t, a);
         uint64_t k = (*meas_counter)++;
         int32_t rbit = orc_outcome_bit(seed, circuit_id, shot, k);
         int32_t d = 0;
@@ -279,6 +292,22 @@ int64_t orc_run(orc_tab *t, const uint64_t *gates, int64_t count, uint64_t seed,
         if (det) det[nout] = (uint8_t)d;
         nout++;
         if (op == 11 && m == 1) orc_x(t, a);
+        if (op == 13 || op == 14) orc_h(t, a);
+        if (op == 14) orc_s(t, a);
+        break;
+      }
+      case 15: case 16: case 17: {
+        uint64_t j = t->noise_counter++;
+        uint32_t ctr[4] = {(uint32_t)j, shot, (uint32_t)circuit_id, (uint32_t)(circuit_id >> 32)};
+        uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ 0x4E4F4953u};
+        uint32_t w[4];
+        orc_philox4x32_10(ctr, key, w);
+        if ((w[0] >> 4) < (uint32_t)q2) {
+          uint32_t which = op == 16 ? 0u : op == 17 ? 2u : (uint32_t)(((uint64_t)w[1] * 3u) >> 32);
+          if (which == 0) orc_x(t, a);
+          else if (which == 1) orc_y(t, a);
+          else orc_z(t, a);
+        }
         break;
       }
       default: return ORC_EINVAL;

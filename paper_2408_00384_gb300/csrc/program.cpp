@@ -93,8 +93,11 @@ static int build_program_stream(int32_t n, const tab_gate* gates, int64_t count,
 }
 
 // Every word of gates[begin, end) is a valid gate for n qubits (index i in
-// messages is the position in the whole list).
-static int validate(int32_t n, const tab_gate* gates, int64_t begin, int64_t end) {
+// messages is the position in the whole list).  Extended ops (TAB_MX ..
+// TAB_ZERR, one-qubit) are valid only when `ext` is given; *ext then counts
+// them.
+static int validate(int32_t n, const tab_gate* gates, int64_t begin, int64_t end,
+                    int64_t* ext = nullptr) {
   // fast pass: one flag over the whole range without data-dependent branches
   // (two-qubit ops are CNOT, CZ, SWAP = 7, 8, 9); the exact scan below runs
   // only when some word is bad, to name the first one
@@ -109,12 +112,23 @@ static int validate(int32_t n, const tab_gate* gates, int64_t begin, int64_t end
            (two & ((uint64_t)(q2 >= un) | (uint64_t)(q1 == q2)));
   }
   if (!bad) return TAB_OK;
+  int64_t n_ext = 0;
   for (int64_t i = begin; i < end; ++i) {
     const uint64_t g = gates[i];
     const uint32_t op = (uint32_t)(g >> 56);
     const uint64_t q1 = (g >> 28) & 0xFFFFFFFull, q2 = g & 0xFFFFFFFull;
+    if (op > TAB_BARRIER && op <= TAB_ZERR && ext != nullptr) {
+      if (q1 >= (uint64_t)n) {
+        set_error("gate %lld: qubit %llu >= n=%d", (long long)i, (unsigned long long)q1, n);
+        return TAB_ERANGE;
+      }
+      ++n_ext;
+      continue;
+    }
     if (op > TAB_BARRIER) {
-      set_error("gate %lld: unknown op %u", (long long)i, op);
+      set_error(op <= TAB_ZERR ? "gate %lld: op %u is not accepted here"
+                               : "gate %lld: unknown op %u",
+                (long long)i, op);
       return TAB_EINVAL;
     }
     if (op == TAB_BARRIER) continue;
@@ -134,6 +148,7 @@ static int validate(int32_t n, const tab_gate* gates, int64_t begin, int64_t end
       }
     }
   }
+  if (ext) *ext += n_ext;
   return TAB_OK;
 }
 
@@ -190,7 +205,7 @@ void concat_programs(HostProgram& P, const HostProgram* part, size_t T) {
   });
 }
 
-int validate_program(int32_t n, const tab_gate* gates, int64_t count) {
+int validate_program(int32_t n, const tab_gate* gates, int64_t count, int64_t* ext) {
   if (n < 1 || n > TAB_MAX_QUBITS) {
     set_error("n=%d outside [1, %d]", n, TAB_MAX_QUBITS);
     return TAB_ERANGE;
@@ -201,9 +216,11 @@ int validate_program(int32_t n, const tab_gate* gates, int64_t count) {
   }
   const int T = (int)std::max<int64_t>(1, std::min<int64_t>(count >> 16, pool_threads()));
   std::vector<int> rcs((size_t)T, TAB_OK);
+  std::vector<int64_t> nx((size_t)T, 0);
   std::vector<std::string> msg((size_t)T);
   pool_run(T, [&](int t) {
-    rcs[(size_t)t] = validate(n, gates, count * t / T, count * (t + 1) / T);
+    rcs[(size_t)t] = validate(n, gates, count * t / T, count * (t + 1) / T,
+                              ext ? &nx[(size_t)t] : nullptr);
     if (rcs[(size_t)t] != TAB_OK) msg[(size_t)t] = last_error();
   });
   for (int t = 0; t < T; ++t)  // the first bad word in list order
@@ -211,6 +228,8 @@ int validate_program(int32_t n, const tab_gate* gates, int64_t count) {
       set_error("%s", msg[(size_t)t].c_str());
       return rcs[(size_t)t];
     }
+  if (ext)
+    for (int t = 0; t < T; ++t) *ext += nx[(size_t)t];
   return TAB_OK;
 }
 

@@ -16,8 +16,9 @@
 #include <new>
 #include <vector>
 
-#include "sct.h"
+#include "philox.cuh"
 #include "pool.h"
+#include "sct.h"
 #include "tab_internal.h"
 
 namespace tab {
@@ -50,6 +51,7 @@ struct tab_s {
   uint64_t seed = 1, cid = 0;
   uint32_t shot = 0;
   uint64_t k = 0;             // next measurement index
+  uint64_t noise_k = 0;       // next noise-op index (TAB_DEPOL1 / TAB_XERR / TAB_ZERR)
   uint8_t* log = nullptr;     // device outcome log
   int64_t log_cap = 0, log_len = 0;
   int64_t launches = 0;
@@ -643,6 +645,7 @@ int tab_set_rng(tab_t h, uint64_t seed, uint64_t circuit_id, uint32_t shot) {
   h->cid = circuit_id;
   h->shot = shot;
   h->k = 0;
+  h->noise_k = 0;
   return TAB_OK;
 }
 
@@ -653,6 +656,7 @@ int tab_reset(tab_t h) {
   h->launches++;
   CU(cudaGetLastError());
   h->k = 0;
+  h->noise_k = 0;
   h->log_len = 0;
   return TAB_OK;
 }
@@ -672,16 +676,14 @@ static int64_t apply_chunk(int64_t count) {
   return std::min<int64_t>((int64_t)1 << 16, std::max<int64_t>((int64_t)1 << 13, per));
 }
 
-// tab_apply for a long list on the block-kernel engines: the whole list is
-// validated first (nothing runs if any word is bad), then its chunks are
+// tab_apply for a long list on the block-kernel engines, once the whole list
+// has been validated (nothing runs if any word is bad): its chunks are
 // compiled by the host pool in list order while one pool thread uploads and
 // launches them, so the GPU starts on the first chunk while later ones are
 // still being compiled.  The chunks grow from 2^13 words (the GPU starts
 // early) to `chunk`; the launcher takes every chunk compiled by the time it
 // is free as one program (one upload, one gate launch per gate run).
 static int apply_pipelined(tab_t h, const tab_gate* gates, int64_t count, int64_t chunk) {
-  int rc = validate_program(h->n, gates, count);
-  if (rc) return rc;
   std::vector<int64_t> bnd(1, 0);
   for (int64_t s = std::min<int64_t>(chunk, (int64_t)1 << 13); bnd.back() < count;
        s = std::min<int64_t>(chunk, 2 * s))
@@ -730,9 +732,66 @@ static int apply_pipelined(tab_t h, const tab_gate* gates, int64_t count, int64_
   return crc;
 }
 
+// Extended ops (tab.h) lowered to base ops: MX -> H, MZ, H; MY -> S^dag, H,
+// MZ, H, S; a noise op -> the Pauli its Philox draw selects, or nothing.  The
+// list has been validated with extended ops allowed.  Noise ops need a handle
+// (its RNG settings and noise counter, which this advances); with h == nullptr
+// they are rejected.
+static int lower_extended(tab_t h, const tab_gate* g, int64_t count, std::vector<tab_gate>& out) {
+  constexpr uint32_t kNoiseKeyTag = 0x4E4F4953u;  // noise draws use a key of their own
+  out.clear();
+  out.reserve((size_t)count + (size_t)count / 4 + 8);
+  auto put = [&](uint32_t op, uint64_t q) { out.push_back(tab_make_gate(op, (uint32_t)q, 0)); };
+  for (int64_t i = 0; i < count; ++i) {
+    const uint32_t op = (uint32_t)(g[i] >> 56);
+    const uint64_t q1 = (g[i] >> 28) & 0xFFFFFFFull, q2 = g[i] & 0xFFFFFFFull;
+    switch (op) {
+      case TAB_MX:
+        for (uint32_t o : {TAB_H, TAB_MZ, TAB_H}) put(o, q1);
+        break;
+      case TAB_MY:
+        for (uint32_t o : {TAB_SDG, TAB_H, TAB_MZ, TAB_H, TAB_S}) put(o, q1);
+        break;
+      case TAB_DEPOL1:
+      case TAB_XERR:
+      case TAB_ZERR: {
+        if (!h) {
+          set_error("gate %lld: noise ops are accepted by tab_apply only", (long long)i);
+          return TAB_EINVAL;
+        }
+        const uint64_t j = h->noise_k++;
+        const uint4 r = philox4x32_10(
+            make_uint4((uint32_t)j, h->shot, (uint32_t)h->cid, (uint32_t)(h->cid >> 32)),
+            make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32) ^ kNoiseKeyTag));
+        if ((r.x >> 4) < (uint32_t)q2) {
+          static const uint32_t kDepol[3] = {TAB_X, TAB_Y, TAB_Z};
+          put(op == TAB_XERR ? TAB_X
+              : op == TAB_ZERR ? TAB_Z
+                               : kDepol[((uint64_t)r.y * 3u) >> 32],
+              q1);
+        }
+        break;
+      }
+      default:
+        out.push_back(g[i]);
+    }
+  }
+  return TAB_OK;
+}
+
 int tab_apply(tab_t h, const tab_gate* gates, int64_t count) {
   int rc = check_handle(h);
   if (rc) return rc;
+  int64_t ext = 0;
+  rc = validate_program(h->n, gates, count, &ext);
+  if (rc) return rc;
+  std::vector<tab_gate> lowered;
+  if (ext) {
+    rc = lower_extended(h, gates, count, lowered);
+    if (rc) return rc;
+    gates = lowered.data();
+    count = (int64_t)lowered.size();
+  }
   if (compile_mode_for(h) == kProgBlocks && count >= ((int64_t)1 << 17) && pool_threads() >= 3) {
     const int64_t chunk = apply_chunk(count);
     if (chunk > 0) return apply_pipelined(h, gates, count, chunk);
@@ -759,8 +818,17 @@ int tab_prog_create(int32_t n, const tab_gate* gates, int64_t count, tab_prog_t*
     set_error("host allocation failed");
     return TAB_ENOMEM;
   }
+  // extended ops other than noise are lowered first
+  int64_t ext = 0;
+  std::vector<tab_gate> lowered;
+  int rc = (n >= 1 && n <= TAB_MAX_QUBITS) ? validate_program(n, gates, count, &ext) : TAB_OK;
+  if (rc == TAB_OK && ext) {
+    rc = lower_extended(nullptr, gates, count, lowered);
+    gates = lowered.data();
+    count = (int64_t)lowered.size();
+  }
   // both forms: the program may run on any engine
-  int rc = build_program(n, gates, count, &p->hp, kProgLayers | kProgBlocks);
+  if (rc == TAB_OK) rc = build_program(n, gates, count, &p->hp, kProgLayers | kProgBlocks);
   if (rc == TAB_OK) {
     DevProg d;
     rc = upload(p->hp, &d, nullptr, false);

@@ -98,8 +98,10 @@ struct HostProgram {
 int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out,
                   int mode = kProgLayers);
 // Validate a gate list (in parallel on the host pool): TAB_OK, or the error of
-// the first bad word in list order (message set).
-int validate_program(int32_t n, const tab_gate* gates, int64_t count);
+// the first bad word in list order (message set).  With `ext` given, the
+// extended ops (TAB_MX .. TAB_ZERR) are accepted and *ext counts them;
+// without it they are errors.
+int validate_program(int32_t n, const tab_gate* gates, int64_t count, int64_t* ext = nullptr);
 // Compile an already validated piece of a gate list into blocks (kProgBlocks).
 int build_validated_blocks(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out);
 // Concatenate part[0..T) -- programs compiled for consecutive pieces of one

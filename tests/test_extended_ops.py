@@ -1,0 +1,148 @@
+"""Oracle pins of the extended ops (CPU): X / Y measurement and Pauli noise.
+
+* MX and MY against a state vector that measures with the projectors
+  (I +- X)/2 and (I +- Y)/2 directly (not by basis change): deterministic
+  outcomes have probability 1, random ones 1/2 and equal the Philox bit, and
+  the final stabilizers hold on the projected state.
+* Noise: with the probability field 0 nothing happens; op j's Pauli (read
+  back from the signs of a one-qubit destabilizer / stabilizer pair) is the
+  one the documented Philox rule selects, evaluated here with the oracle's
+  Philox (pinned to the Random123 known-answer vectors); the firing rate and
+  the X / Y / Z split of DEPOL1 are close to p and 1/3.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from tests.statevector import MAT1, StateVector
+from tests.test_oracle_pins import stabilizers_hold
+from workloads import circuits as C
+
+PAULI = {C.TAB_MX: MAT1["X"], C.TAB_MY: MAT1["Y"]}
+NAME1 = {C.TAB_I: "I", C.TAB_X: "X", C.TAB_Y: "Y", C.TAB_Z: "Z", C.TAB_H: "H",
+         C.TAB_S: "S", C.TAB_SDG: "SDG"}
+NAME2 = {C.TAB_CNOT: "CNOT", C.TAB_CZ: "CZ", C.TAB_SWAP: "SWAP"}
+
+
+def apply_1q(sv, m, a):
+    idx = sv.idx
+    b = (idx >> a) & 1
+    partner = idx ^ (1 << a)
+    psi = sv.psi
+    sv.psi = np.where(b == 0, m[0, 0] * psi + m[0, 1] * psi[partner],
+                      m[1, 0] * psi[partner] + m[1, 1] * psi)
+
+
+def prob(sv, m, a, outcome):
+    """Probability of eigenvalue (-1)^outcome of the one-qubit Pauli m on a."""
+    save = sv.psi.copy()
+    proj = 0.5 * (np.eye(2) + (-1) ** outcome * m)
+    apply_1q(sv, proj, a)
+    p = float(np.vdot(sv.psi, sv.psi).real)
+    sv.psi = save
+    return p
+
+
+def project(sv, m, a, outcome):
+    apply_1q(sv, 0.5 * (np.eye(2) + (-1) ** outcome * m), a)
+    sv.psi /= np.linalg.norm(sv.psi)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5])
+def test_mx_my_against_projectors(n):
+    for s in range(5):
+        gates = C.random_extended_ops(n, 70, seed=500 * n + s, p_meas=0.25, p_noise=0.0)
+        t = oracle.Tableau(n)
+        out, det = t.run(gates, seed=s + 3, circuit_id=s, with_det=True)
+        sv = StateVector(n)
+        op, q1, q2 = C.decode(gates)
+        k = 0
+        for o, a, b in zip(op.tolist(), q1.tolist(), q2.tolist()):
+            if o in NAME1:
+                sv.apply(NAME1[o], [a])
+            elif o in NAME2:
+                sv.apply(NAME2[o], [a, b])
+            elif o in C.MEASURE_ANY:
+                m = MAT1["Z"] if o in C.MEASURE else PAULI[o]
+                bit = int(out[k])
+                p = prob(sv, m, a, bit)
+                if det[k]:
+                    assert abs(p - 1.0) < 1e-9, (o, p)
+                else:
+                    assert abs(p - 0.5) < 1e-9, (o, p)
+                    assert bit == oracle.outcome_bit(s + 3, s, 0, k)
+                project(sv, m, a, bit)
+                if o == C.TAB_MZR and bit:
+                    sv.apply("X", [a])
+                k += 1
+        assert k == out.size
+        assert stabilizers_hold(t, sv)
+
+
+def test_mx_my_known_states():
+    def run(prep, op):
+        n = 1
+        g = np.concatenate([C.encode(np.array(prep, dtype=np.int64), 0, 0).reshape(-1),
+                            C.encode(op, 0, 0).reshape(1), C.encode(op, 0, 0).reshape(1)])
+        out, det = oracle.Tableau(n).run(g, with_det=True)
+        return out.tolist(), det.tolist()
+    assert run([C.TAB_H], C.TAB_MX) == ([0, 0], [True, True])                  # |+>
+    assert run([C.TAB_X, C.TAB_H], C.TAB_MX) == ([1, 1], [True, True])         # |->
+    assert run([C.TAB_H, C.TAB_S], C.TAB_MY) == ([0, 0], [True, True])         # |+i>
+    assert run([C.TAB_H, C.TAB_SDG], C.TAB_MY) == ([1, 1], [True, True])       # |-i>
+    out, det = run([], C.TAB_MX)                                               # |0>: random, then repeatable
+    assert det == [False, True] and out[0] == out[1]
+
+
+def applied_paulis(n, ops, field, seed, cid, shot):
+    """Run noise op ops[i] on qubit i of |0^n>; read which Pauli hit each qubit
+    from the signs of destabilizer X_i and stabilizer Z_i."""
+    g = C.encode(np.array(ops, dtype=np.int64), np.arange(n), field)
+    _, (x, z, r) = oracle.run_circuit(n, g, seed=seed, circuit_id=cid, shot=shot)
+    return [{(0, 0): "I", (0, 1): "X", (1, 1): "Y", (1, 0): "Z"}[(int(r[i]), int(r[n + i]))]
+            for i in range(n)]
+
+
+def expected_paulis(ops, field, seed, cid, shot):
+    out = []
+    for j, op in enumerate(ops):
+        w = oracle.philox4x32_10([j, shot, cid & 0xFFFFFFFF, cid >> 32],
+                                 [seed & 0xFFFFFFFF, (seed >> 32) ^ 0x4E4F4953])
+        if (int(w[0]) >> 4) >= field:
+            out.append("I")
+        elif op == C.TAB_XERR:
+            out.append("X")
+        elif op == C.TAB_ZERR:
+            out.append("Z")
+        else:
+            out.append("XYZ"[(int(w[1]) * 3) >> 32])
+    return out
+
+
+def test_noise_rule_matches_philox():
+    rng = np.random.default_rng(5)
+    n = 400
+    ops = rng.choice(C.NOISE, size=n).tolist()
+    for field, seed, cid, shot in [(C.noise_field(0.4), 7, 3, 2),
+                                   (C.noise_field(0.999), (1 << 40) + 5, (1 << 33) + 1, 9)]:
+        assert applied_paulis(n, ops, field, seed, cid, shot) == \
+            expected_paulis(ops, field, seed, cid, shot)
+
+
+def test_noise_zero_probability_is_identity():
+    n = 50
+    base = C.random_clifford_ops(n, 300, seed=3)
+    noise = C.encode(np.full(n, C.TAB_DEPOL1), np.arange(n), 0)
+    _, want = oracle.run_circuit(n, base)
+    _, got = oracle.run_circuit(n, np.concatenate([base[:150], noise, base[150:]]))
+    for a, b in zip(want, got):
+        assert np.array_equal(a, b)
+
+
+def test_depolarizing_rates():
+    n = 6000
+    got = applied_paulis(n, [C.TAB_DEPOL1] * n, C.noise_field(0.6), 11, 0, 0)
+    fired = [p for p in got if p != "I"]
+    assert abs(len(fired) / n - 0.6) < 0.03
+    for p in "XYZ":
+        assert abs(fired.count(p) / len(fired) - 1 / 3) < 0.03

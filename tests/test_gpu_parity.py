@@ -196,6 +196,52 @@ def test_uniform_random_clifford_engines(engine):
     assert_same(300, c.gates, engine=engine)
 
 
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("n", [1, 2, 5, 33, 130, 300])
+def test_extended_ops(engine, n):
+    """MX / MY and the three noise ops among every other op, bit for bit
+    against the oracle (noise draws under a non-default RNG context)."""
+    g = C.random_extended_ops(n, 400, seed=77 + n, p_meas=0.1, p_noise=0.15, noise_p=0.4)
+    assert_same(n, g, seed=5, cid=2, shot=1, engine=engine)
+
+
+def test_extended_ops_long_list():
+    """Extended ops in a list long enough for the pipelined apply."""
+    c = C.random_layer_circuit(700, 140, seed=23, final_measure=False)
+    rng = np.random.default_rng(1)
+    pos = np.sort(rng.choice(c.gates.size, 3000, replace=False))
+    kind = rng.choice([C.TAB_MX, C.TAB_MY, C.TAB_DEPOL1, C.TAB_XERR, C.TAB_ZERR], size=3000)
+    field = np.where(np.isin(kind, C.NOISE), C.noise_field(0.3), 0)
+    g = np.insert(c.gates, pos, C.encode(kind, rng.integers(0, 700, size=3000), field))
+    assert g.size >= (1 << 17)
+    assert_same(700, g, seed=4, cid=1, engine=tab.ENGINE_GRID)
+
+
+def test_extended_ops_in_programs_and_batches():
+    """Programs take MX / MY (lowered once) but not noise ops; batches take
+    neither."""
+    n = 40
+    g = C.random_extended_ops(n, 300, seed=8, p_noise=0.0)
+    with tab.Tableau(n) as t:
+        t.set_rng(3, 0, 0)
+        p = tab.Program(n, g)
+        t.run(p)
+        out = t.read_outcomes()
+        got = t.export()
+        p.close()
+    want_out, want = oracle_result(n, g, 3, 0, 0)
+    assert np.array_equal(out, want_out)
+    for a, b in zip(got, want):
+        assert np.array_equal(a, b)
+    noisy = C.random_extended_ops(n, 60, seed=9, p_meas=0.0, p_noise=0.5)
+    with pytest.raises(tab.TabError) as ei:
+        tab.Program(n, noisy)
+    assert ei.value.code == tab.TAB_EINVAL
+    with pytest.raises(tab.TabError) as ei:
+        tab.Batch([(n, g, 2, 0)])
+    assert ei.value.code == tab.TAB_EINVAL
+
+
 def test_pipelined_apply_mid_circuit_measurements():
     """A list of more than 2^17 words on the grid engine is compiled in 2^16-
     word chunks while earlier chunks already run; MZR rounds every 5 layers put

@@ -355,7 +355,7 @@ def test_invalid_inputs_rejected():
     with pytest.raises(RuntimeError):
         t.run(C.encode(C.TAB_CNOT, 1, 1).reshape(1))
     with pytest.raises(RuntimeError):
-        t.run(C.encode(13, 0, 0).reshape(1))
+        t.run(C.encode(18, 0, 0).reshape(1))
 
 
 # ------------------------------------------- readings the physics leaves open

@@ -30,15 +30,21 @@ import numpy as np
 TAB_I, TAB_X, TAB_Y, TAB_Z, TAB_H, TAB_S, TAB_SDG = 0, 1, 2, 3, 4, 5, 6
 TAB_CNOT, TAB_CZ, TAB_SWAP = 7, 8, 9
 TAB_MZ, TAB_MZR, TAB_BARRIER = 10, 11, 12
+# extended ops: X / Y measurement and single-qubit Pauli noise (the second
+# qubit field of a noise op holds its probability as a 28-bit fraction)
+TAB_MX, TAB_MY, TAB_DEPOL1, TAB_XERR, TAB_ZERR = 13, 14, 15, 16, 17
 
 ONE_QUBIT = (TAB_I, TAB_X, TAB_Y, TAB_Z, TAB_H, TAB_S, TAB_SDG)
 TWO_QUBIT = (TAB_CNOT, TAB_CZ, TAB_SWAP)
 MEASURE = (TAB_MZ, TAB_MZR)
+MEASURE_ANY = (TAB_MZ, TAB_MZR, TAB_MX, TAB_MY)   # ops that log an outcome
+NOISE = (TAB_DEPOL1, TAB_XERR, TAB_ZERR)
 
 OP_NAMES = {TAB_I: "I", TAB_X: "X", TAB_Y: "Y", TAB_Z: "Z", TAB_H: "H",
             TAB_S: "S", TAB_SDG: "SDG", TAB_CNOT: "CNOT", TAB_CZ: "CZ",
             TAB_SWAP: "SWAP", TAB_MZ: "MZ", TAB_MZR: "MZR",
-            TAB_BARRIER: "BARRIER"}
+            TAB_BARRIER: "BARRIER", TAB_MX: "MX", TAB_MY: "MY",
+            TAB_DEPOL1: "DEPOL1", TAB_XERR: "XERR", TAB_ZERR: "ZERR"}
 
 CONFIG_SEED = 240800384   # fixed generator seed of every workload family
 PHILOX_SEED = 1           # fixed outcome seed of every workload family
@@ -244,10 +250,43 @@ def random_clifford_ops(n: int, count: int, seed: int, *, measure_p: float = 0.0
     return out
 
 
+def noise_field(p: float) -> int:
+    """The 28-bit probability field of a noise op for probability p in [0, 1)."""
+    if not 0.0 <= p < 1.0:
+        raise ValueError("p must be in [0, 1)")
+    return int(p * (1 << 28))
+
+
+def random_extended_ops(n: int, count: int, seed: int, *, p_meas: float = 0.1,
+                        p_noise: float = 0.1, noise_p: float = 0.3) -> np.ndarray:
+    """Random gate list over every op, extended ones included: MZ / MZR / MX /
+    MY with total probability p_meas, a noise op (DEPOL1, XERR or ZERR with
+    probability noise_p) with probability p_noise, else a uniform gate."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gates = list(ONE_QUBIT) + (list(TWO_QUBIT) if n >= 2 else [])
+    field = noise_field(noise_p)
+    out = np.zeros(count, dtype=np.uint64)
+    for i in range(count):
+        u = rng.random()
+        if u < p_meas:
+            out[i] = encode(int(rng.choice(MEASURE_ANY)), int(rng.integers(0, n)), 0)
+        elif u < p_meas + p_noise:
+            out[i] = encode(int(rng.choice(NOISE)), int(rng.integers(0, n)), field)
+        else:
+            op = int(gates[int(rng.integers(0, len(gates)))])
+            if op in TWO_QUBIT:
+                a, b = rng.choice(n, size=2, replace=False)
+                out[i] = encode(op, int(a), int(b))
+            else:
+                out[i] = encode(op, int(rng.integers(0, n)), 0)
+    return out
+
+
 def count_ops(gates: np.ndarray):
-    """(gate ops, measurement ops) in a gate list; barriers are not counted."""
+    """(gate ops, measurement ops) in a gate list; barriers and noise ops are
+    not counted."""
     op, _, _ = decode(gates)
-    meas = int(np.isin(op, MEASURE).sum())
+    meas = int(np.isin(op, MEASURE_ANY).sum())
     gates_n = int(np.isin(op, ONE_QUBIT + TWO_QUBIT).sum())
     return gates_n, meas
 
