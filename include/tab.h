@@ -143,6 +143,17 @@ int tab_reset(tab_t h);
  * before the call returns. */
 int tab_apply(tab_t h, const tab_gate *gates, int64_t count);
 
+/* Expectation values <psi|P_i|psi> of k Pauli strings on the handle's
+ * stabilizer state (AG Sec. III: +-P is in the stabilizer group exactly when
+ * P commutes with every stabilizer row, and then it is the product of the
+ * stabilizer rows whose destabilizer partners anticommute with P).
+ * `paulis`: k x n host bytes, row-major; entry j of string i is the Pauli on
+ * qubit j: 0 = I, 1 = X, 2 = Z, 3 = Y (bit 0 = x, bit 1 = z).  `out`: k host
+ * bytes, each -1, 0 or +1.  The state is not changed and no measurement index
+ * is used.  Synchronous.  TAB_EINVAL on a code above 3 or a null pointer
+ * (nothing launched); TAB_EDEVICE if a product fails its consistency checks. */
+int tab_expect(tab_t h, const uint8_t *paulis, int32_t k, int8_t *out);
+
 /* A gate list compiled once (validated, grouped into layers of disjoint gates,
  * uploaded to device memory) and replayable on any handle with the same n. */
 typedef struct tab_prog_s *tab_prog_t;

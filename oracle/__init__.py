@@ -55,6 +55,8 @@ def lib():
         L.orc_run.argtypes = [vp, P(u64), i64, u64, u64, u32, P(u64),
                               P(ctypes.c_uint8), i64, P(ctypes.c_uint8)]
         L.orc_get.argtypes = [vp, vp, vp, vp]
+        L.orc_expect.restype = i32
+        L.orc_expect.argtypes = [vp, vp]
         L.orc_set.argtypes = [vp, vp, vp, vp]
         _lib = L
     return _lib
@@ -142,6 +144,14 @@ class Tableau:
         if with_det:
             return out[:rc].copy(), det[:rc].astype(bool)
         return out[:rc].copy()
+
+    def expect(self, codes) -> int:
+        """<P> in {-1, 0, 1} for one Pauli string (n codes: 0 I, 1 X, 2 Z, 3 Y)."""
+        c = np.ascontiguousarray(codes, dtype=np.uint8).reshape(self.n)
+        v = int(lib().orc_expect(self._h, c.ctypes.data))
+        if v < -1:
+            raise RuntimeError(f"orc_expect error {v}")
+        return v
 
     def get(self):
         """(x, z, r) as uint8 arrays of shape (2n, n), (2n, n), (2n,)."""

@@ -316,6 +316,44 @@ int64_t orc_run(orc_tab *t, const uint64_t *gates, int64_t count, uint64_t seed,
   return nout;
 }
 
+/* ---- expectation value of a Pauli string ------------------------------ */
+
+/* <psi|P|psi> for the Pauli with codes p[0..n) (0 I, 1 X, 2 Z, 3 Y; bit 0 is
+ * x, bit 1 is z).  AG Sec. III: the state is the +1 eigenstate of the
+ * stabilizer rows, so <P> = 0 when P anticommutes with one of them; otherwise
+ * +-P is the product of the stabilizer rows n+i over the destabilizers i that
+ * anticommute with P (the product the deterministic measurement forms for
+ * Z_a), built here in the scratch row by rowsum, and <P> is its sign.
+ * Returns -1, 0 or +1; ORC_EINVAL for a bad code; ORC_EPHASE if the product
+ * is not +-P.  Rows 0..2n-1 are unchanged. */
+int32_t orc_expect(orc_tab *t, const uint8_t *p) {
+  int32_t n = t->n;
+  int64_t s = 2 * (int64_t)n;
+  for (int32_t j = 0; j < n; j++)
+    if (p[j] > 3) return ORC_EINVAL;
+  uint8_t *anti = (uint8_t *)calloc((size_t)t->rows, 1);
+  if (!anti) return ORC_ENOMEM;
+  for (int64_t i = 0; i < 2 * (int64_t)n; i++) {
+    int c = 0;
+    for (int32_t j = 0; j < n; j++)
+      c ^= (XB(t, i, j) & (p[j] >> 1)) ^ (ZB(t, i, j) & (p[j] & 1));
+    anti[i] = (uint8_t)c;
+  }
+  for (int64_t i = n; i < 2 * (int64_t)n; i++)
+    if (anti[i]) { free(anti); return 0; }
+  for (int32_t j = 0; j < n; j++) { XB(t, s, j) = 0; ZB(t, s, j) = 0; }
+  t->r[s] = 0;
+  for (int64_t i = 0; i < n; i++) {
+    if (!anti[i]) continue;
+    int32_t rc = orc_rowsum(t, s, n + i);
+    if (rc < 0) { free(anti); return rc; }
+  }
+  free(anti);
+  for (int32_t j = 0; j < n; j++)
+    if (XB(t, s, j) != (p[j] & 1) || ZB(t, s, j) != (p[j] >> 1)) return ORC_EPHASE;
+  return t->r[s] ? -1 : 1;
+}
+
 /* ---- import / export: row-major unpacked bits, rows 0..2n-1 ------------ */
 
 void orc_get(const orc_tab *t, uint8_t *x, uint8_t *z, uint8_t *r) {

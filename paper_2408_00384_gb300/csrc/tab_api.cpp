@@ -956,6 +956,40 @@ int tab_measure_async(tab_t h, const int32_t* qubits, int32_t k, uint8_t* dev_ou
   return TAB_OK;
 }
 
+int tab_expect(tab_t h, const uint8_t* paulis, int32_t k, int8_t* out) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (k < 0 || (k > 0 && (!paulis || !out))) {
+    set_error("bad Pauli list (k=%d)", k);
+    return TAB_EINVAL;
+  }
+  if (k == 0) return TAB_OK;
+  const size_t bytes = (size_t)k * (size_t)h->n;
+  for (size_t i = 0; i < bytes; ++i)
+    if (paulis[i] > 3u) {
+      set_error("Pauli %lld, qubit %lld: code %u is not 0..3", (long long)(i / h->n),
+                (long long)(i % h->n), (unsigned)paulis[i]);
+      return TAB_EINVAL;
+    }
+  uint8_t* d = nullptr;
+  CU(cudaMallocAsync((void**)&d, bytes + (size_t)k, h->stream));
+  CU(cudaMemcpyAsync(d, paulis, bytes, cudaMemcpyHostToDevice, h->stream));
+  h->h2d_bytes += (int64_t)bytes;
+  int8_t* dout = reinterpret_cast<int8_t*>(d + bytes);
+  cudaError_t e = launch_expect(h->X, h->Z, h->R, h->n, h->Wh, d, k, dout, h->mw.err, h->stream);
+  if (e == cudaSuccess) {
+    h->launches++;
+    e = cudaMemcpyAsync(out, dout, (size_t)k, cudaMemcpyDeviceToHost, h->stream);
+    h->d2h_bytes += k;
+  }
+  cudaFreeAsync(d, h->stream);
+  if (e != cudaSuccess) {
+    set_error("cuda: %s", cudaGetErrorString(e));
+    return TAB_ECUDA;
+  }
+  return poll_device_error(h);
+}
+
 int tab_read_outcomes(tab_t h, uint8_t* out, int64_t max, int64_t* count) {
   int rc = check_handle(h);
   if (rc) return rc;

@@ -66,6 +66,7 @@ _sig("tab_run", ctypes.c_int, [_vp, _vp])
 _sig("tab_measure", ctypes.c_int, [_vp, _vp, _i32, _u64, _vp])
 _sig("tab_measure_async", ctypes.c_int, [_vp, _vp, _i32, _vp])
 _sig("tab_read_outcomes", ctypes.c_int, [_vp, _vp, _i64, _P(_i64)])
+_sig("tab_expect", ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp])
 _sig("tab_clear_outcomes", ctypes.c_int, [_vp])
 _sig("tab_kernel_launches", ctypes.c_int, [_vp, _P(_i64)])
 _sig("tab_set_engine", ctypes.c_int, [_vp, ctypes.c_int])
@@ -250,6 +251,17 @@ class Tableau:
         q = np.ascontiguousarray(np.asarray(qubits, dtype=np.int32).reshape(-1))
         _check(_L.tab_measure_noalloc(self._h, q.ctypes.data if q.size else None, q.size,
                                       1 if reset else 0, dev_out_ptr))
+
+    def expect(self, paulis) -> np.ndarray:
+        """<P> in {-1, 0, 1} for each row of `paulis` (k x n codes 0=I, 1=X,
+        2=Z, 3=Y) or for each string over "IXYZ" in a list."""
+        if isinstance(paulis, (list, tuple)) and paulis and isinstance(paulis[0], str):
+            lut = {"I": 0, "X": 1, "Z": 2, "Y": 3}
+            paulis = np.array([[lut[ch] for ch in s] for s in paulis], dtype=np.uint8)
+        codes = np.ascontiguousarray(paulis, dtype=np.uint8).reshape(-1, self.n)
+        out = np.zeros(max(codes.shape[0], 1), np.int8)
+        _check(_L.tab_expect(self._h, codes.ctypes.data, codes.shape[0], out.ctypes.data))
+        return out[:codes.shape[0]]
 
     def read_outcomes(self) -> np.ndarray:
         cnt = _i64()

@@ -146,3 +146,31 @@ def test_depolarizing_rates():
     assert abs(len(fired) / n - 0.6) < 0.03
     for p in "XYZ":
         assert abs(fired.count(p) / len(fired) - 1 / 3) < 0.03
+
+
+# ---------------------------------------------- expectation values (oracle)
+
+def sv_expect(sv, codes):
+    x = [c & 1 for c in codes]
+    z = [c >> 1 for c in codes]
+    return float(np.vdot(sv.psi, sv.apply_pauli(x, z, 0)).real)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_expectation_all_paulis_vs_statevector(n):
+    """Every one of the 4^n Pauli strings on random stabilizer states."""
+    import itertools
+    for s in range(4):
+        gates = C.random_clifford_ops(n, 40, seed=700 * n + s)
+        t = oracle.Tableau(n)
+        t.run(gates)
+        sv = StateVector(n)
+        op, q1, q2 = C.decode(gates)
+        for o, a, b in zip(op.tolist(), q1.tolist(), q2.tolist()):
+            sv.apply(NAME1[o], [a]) if o in NAME1 else sv.apply(NAME2[o], [a, b])
+        before = t.get()
+        for codes in itertools.product(range(4), repeat=n):
+            want = sv_expect(sv, codes)
+            assert abs(want - t.expect(codes)) < 1e-9, (codes, want)
+        for a, b in zip(before, t.get()):
+            assert np.array_equal(a, b)

@@ -242,6 +242,70 @@ def test_extended_ops_in_programs_and_batches():
     assert ei.value.code == tab.TAB_EINVAL
 
 
+def _expect_cases(n, x, z, rng):
+    """Pauli strings (k x n codes) for a state with tableau rows (x, z): random
+    dense and sparse strings, single-qubit X_a / Z_a, and products of random
+    stabilizer subsets (which have expectation +-1)."""
+    out = [rng.integers(0, 4, size=n) for _ in range(6)]
+    for _ in range(6):
+        s = np.zeros(n, np.int64)
+        sup = rng.choice(n, size=min(n, 3), replace=False)
+        s[sup] = rng.integers(1, 4, size=sup.size)
+        out.append(s)
+    for a in rng.choice(n, size=min(n, 4), replace=False):
+        for code in (1, 2):
+            s = np.zeros(n, np.int64)
+            s[a] = code
+            out.append(s)
+    for _ in range(12):
+        pick = rng.integers(0, 2, size=n).astype(bool)
+        px = np.bitwise_xor.reduce(x[n:][pick].astype(np.int64), axis=0) if pick.any() else np.zeros(n, np.int64)
+        pz = np.bitwise_xor.reduce(z[n:][pick].astype(np.int64), axis=0) if pick.any() else np.zeros(n, np.int64)
+        out.append(px | (pz << 1))
+    return np.array(out, dtype=np.uint8)
+
+
+@pytest.mark.parametrize("engine", [tab.ENGINE_AUTO, tab.ENGINE_GRID])
+@pytest.mark.parametrize("n", [1, 3, 31, 32, 33, 100, 257, 1000, 2100])
+def test_expectation_values(n, engine):
+    """tab_expect against the oracle's product-of-stabilizers expectation, on
+    random states; the state is left unchanged."""
+    import oracle as orc
+    if n <= 300:
+        gates = C.random_clifford(n, C.splitmix64(5150 + n)).gates
+    else:
+        gates = C.random_layer_circuit(n, 8, seed=n, final_measure=False).gates
+    t_o = orc.Tableau(n)
+    t_o.run(gates)
+    x, z, _ = t_o.get()
+    cases = _expect_cases(n, x, z, np.random.default_rng(n))
+    want = np.array([t_o.expect(s) for s in cases], dtype=np.int8)
+    assert (want != 0).sum() >= 12
+    with tab.Tableau(n) as t:
+        try:
+            t.set_engine(engine)
+        except tab.TabError as e:
+            if e.code == tab.TAB_ERANGE:
+                pytest.skip(f"engine {engine} does not hold n={n}")
+            raise
+        t.apply(gates)
+        before = t.export()
+        got = t.expect(cases)
+        after = t.export()
+    assert np.array_equal(got, want), np.nonzero(got != want)[0][:10]
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+
+
+def test_expectation_strings_and_errors():
+    with tab.Tableau(2) as t:
+        t.apply(np.array([C.encode(C.TAB_H, 0, 0), C.encode(C.TAB_CNOT, 0, 1)], np.uint64))
+        assert t.expect(["XX", "ZZ", "YY", "XI", "IZ", "II"]).tolist() == [1, 1, -1, 0, 0, 1]
+        with pytest.raises(tab.TabError) as ei:
+            t.expect(np.array([[0, 4]], np.uint8))
+        assert ei.value.code == tab.TAB_EINVAL
+
+
 def test_pipelined_apply_mid_circuit_measurements():
     """A list of more than 2^17 words on the grid engine is compiled in 2^16-
     word chunks while earlier chunks already run; MZR rounds every 5 layers put
