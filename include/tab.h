@@ -154,6 +154,18 @@ int tab_apply(tab_t h, const tab_gate *gates, int64_t count);
  * (nothing launched); TAB_EDEVICE if a product fails its consistency checks. */
 int tab_expect(tab_t h, const uint8_t *paulis, int32_t k, int8_t *out);
 
+/* State vector of the handle's state, for n <= TAB_SV_MAX_QUBITS.
+ * `amps`: host array of at least 2^(n+1) floats, filled with the 2^n complex
+ * amplitudes as (re, im) pairs; basis index bit q is qubit q.  The global
+ * phase is fixed so that the nonzero amplitude of smallest index is real and
+ * positive.  Computed on the device as prod_i (I + S_i)/2 |b> over the
+ * stabilizer rows S_i, normalised, with b a basis state in the support (the Z
+ * outcomes of a copy of the tableau).  The handle's state, outcome log and
+ * counters are unchanged.  Synchronous.  TAB_ERANGE if n is above the limit,
+ * TAB_EINVAL if `amps` is null or too short. */
+#define TAB_SV_MAX_QUBITS 26
+int tab_statevector(tab_t h, float *amps, int64_t len);
+
 /* A gate list compiled once (validated, grouped into layers of disjoint gates,
  * uploaded to device memory) and replayable on any handle with the same n. */
 typedef struct tab_prog_s *tab_prog_t;

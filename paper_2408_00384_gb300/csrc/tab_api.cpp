@@ -990,6 +990,63 @@ int tab_expect(tab_t h, const uint8_t* paulis, int32_t k, int8_t* out) {
   return poll_device_error(h);
 }
 
+int tab_statevector(tab_t h, float* amps, int64_t len) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  const int n = h->n;
+  if (n > TAB_SV_MAX_QUBITS) {
+    set_error("n=%d above the state-vector limit %d", n, TAB_SV_MAX_QUBITS);
+    return TAB_ERANGE;
+  }
+  if (!amps || len < ((int64_t)2 << n)) {
+    set_error("amplitude buffer needs %lld floats", (long long)((int64_t)2 << n));
+    return TAB_EINVAL;
+  }
+  // a basis state in the support: the Z outcomes of every qubit of a copy
+  tab_t c = nullptr;
+  rc = tab_create(n, &c);
+  if (rc) return rc;
+  rc = tab_set_stream(c, h->stream);
+  uint32_t b = 0u;
+  if (rc == TAB_OK) {
+    const size_t planes = (size_t)n * h->W * 4;
+    cudaError_t e = cudaMemcpyAsync(c->X, h->X, planes, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->Z, h->Z, planes, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->R, h->R, (size_t)h->W * 4, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) {
+      set_error("cuda: %s", cudaGetErrorString(e));
+      rc = TAB_ECUDA;
+    }
+  }
+  if (rc == TAB_OK) {
+    std::vector<int32_t> q((size_t)n);
+    for (int i = 0; i < n; ++i) q[(size_t)i] = i;
+    std::vector<uint8_t> bits((size_t)n);
+    rc = tab_measure(c, q.data(), n, 1, bits.data());
+    for (int i = 0; rc == TAB_OK && i < n; ++i) b |= (uint32_t)(bits[(size_t)i] & 1u) << i;
+  }
+  tab_destroy(c);
+  if (rc) return rc;
+  const size_t vb = (size_t)8 << n;
+  char* d = nullptr;
+  CU(cudaMallocAsync((void**)&d, vb + sv_work_bytes(n), h->stream));
+  cudaError_t e = launch_statevector(h->X, h->Z, h->R, n, h->Wh, b, reinterpret_cast<float2*>(d),
+                                     d + vb, h->stream);
+  if (e == cudaSuccess) {
+    h->launches += n + 5;
+    e = cudaMemcpyAsync(amps, d, vb, cudaMemcpyDeviceToHost, h->stream);
+    h->d2h_bytes += (int64_t)vb;
+  }
+  cudaFreeAsync(d, h->stream);
+  if (e != cudaSuccess) {
+    set_error("cuda: %s", cudaGetErrorString(e));
+    return TAB_ECUDA;
+  }
+  return poll_device_error(h);
+}
+
 int tab_read_outcomes(tab_t h, uint8_t* out, int64_t max, int64_t* count) {
   int rc = check_handle(h);
   if (rc) return rc;

@@ -193,6 +193,9 @@ cudaError_t launch_measure_resident(uint32_t* X, uint32_t* Z, uint32_t* R, int n
 size_t measure_work_words(int n, int max_ctas);
 cudaError_t launch_expect(const uint32_t* X, const uint32_t* Z, const uint32_t* R, int n, int Wh,
                           const uint8_t* codes, int k, int8_t* out, int* err, cudaStream_t s);
+size_t sv_work_bytes(int n);
+cudaError_t launch_statevector(const uint32_t* X, const uint32_t* Z, const uint32_t* R, int n,
+                               int Wh, uint32_t b, float2* v, void* work, cudaStream_t s);
 cudaError_t launch_pack(uint32_t* X, uint32_t* Z, uint32_t* R, const uint8_t* xs,
                         const uint8_t* zs, const uint8_t* rs, int n, int Wh, cudaStream_t s);
 cudaError_t launch_unpack(const uint32_t* X, const uint32_t* Z, const uint32_t* R,

@@ -67,6 +67,7 @@ _sig("tab_measure", ctypes.c_int, [_vp, _vp, _i32, _u64, _vp])
 _sig("tab_measure_async", ctypes.c_int, [_vp, _vp, _i32, _vp])
 _sig("tab_read_outcomes", ctypes.c_int, [_vp, _vp, _i64, _P(_i64)])
 _sig("tab_expect", ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp])
+_sig("tab_statevector", ctypes.c_int, [_vp, _vp, _i64])
 _sig("tab_clear_outcomes", ctypes.c_int, [_vp])
 _sig("tab_kernel_launches", ctypes.c_int, [_vp, _P(_i64)])
 _sig("tab_set_engine", ctypes.c_int, [_vp, ctypes.c_int])
@@ -262,6 +263,13 @@ class Tableau:
         out = np.zeros(max(codes.shape[0], 1), np.int8)
         _check(_L.tab_expect(self._h, codes.ctypes.data, codes.shape[0], out.ctypes.data))
         return out[:codes.shape[0]]
+
+    def statevector(self) -> np.ndarray:
+        """The 2^n amplitudes (complex64; basis index bit q = qubit q; the
+        first nonzero amplitude real and positive), n <= 26."""
+        out = np.zeros(2 << self.n, np.float32)
+        _check(_L.tab_statevector(self._h, out.ctypes.data, out.size))
+        return out.view(np.complex64)
 
     def read_outcomes(self) -> np.ndarray:
         cnt = _i64()

@@ -306,6 +306,91 @@ def test_expectation_strings_and_errors():
         assert ei.value.code == tab.TAB_EINVAL
 
 
+def _sv_name(o):
+    return {C.TAB_I: "I", C.TAB_X: "X", C.TAB_Y: "Y", C.TAB_Z: "Z", C.TAB_H: "H",
+            C.TAB_S: "S", C.TAB_SDG: "SDG", C.TAB_CNOT: "CNOT", C.TAB_CZ: "CZ",
+            C.TAB_SWAP: "SWAP"}[o]
+
+
+def _phase_fixed(psi):
+    k = int(np.flatnonzero(np.abs(psi) > 1e-9)[0])
+    return psi * (np.conj(psi[k]) / abs(psi[k]))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 12])
+def test_statevector_export(n):
+    """tab_statevector against a brute-force state vector of the same circuit
+    (gate matrices), up to the documented global phase; the handle's state is
+    unchanged."""
+    from tests.statevector import StateVector
+    gates = C.random_clifford(n, C.splitmix64(6060 + n)).gates
+    sv = StateVector(n)
+    op, q1, q2 = C.decode(gates)
+    for o, a, b in zip(op.tolist(), q1.tolist(), q2.tolist()):
+        sv.apply(_sv_name(o), [a] if o in C.ONE_QUBIT else [a, b])
+    with tab.Tableau(n) as t:
+        t.apply(gates)
+        before = t.export()
+        v = t.statevector()
+        after = t.export()
+    assert np.allclose(v, _phase_fixed(sv.psi), atol=1e-5)
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+
+
+def test_statevector_after_measurement_and_expectations():
+    """A post-measurement state (outcomes read back), and at n = 16 the
+    exported vector reproduces tab_expect on stabilizer products."""
+    from tests.statevector import StateVector
+    n = 6
+    g = np.concatenate([C.encode(C.TAB_H, 0, 0).reshape(1),
+                        C.encode(np.full(n - 1, C.TAB_CNOT), 0, np.arange(1, n)),
+                        C.encode(C.TAB_H, 2, 0).reshape(1),
+                        C.encode(C.TAB_MZ, 2, 0).reshape(1),
+                        C.encode(C.TAB_S, 4, 0).reshape(1)])
+    with tab.Tableau(n) as t:
+        t.set_rng(7, 0, 0)
+        t.apply(g)
+        m = int(t.read_outcomes()[0])
+        v = t.statevector()
+    sv = StateVector(n)
+    sv.apply("H", [0])
+    for j in range(1, n):
+        sv.apply("CNOT", [0, j])
+    sv.apply("H", [2])
+    sv.project(2, m)
+    sv.apply("S", [4])
+    assert np.allclose(v, _phase_fixed(sv.psi), atol=1e-5)
+
+    n = 16
+    gates = C.random_clifford(n, C.splitmix64(6161)).gates
+    with tab.Tableau(n) as t:
+        t.apply(gates)
+        v = t.statevector().astype(np.complex128)
+        x, z, _ = t.export()
+        rng = np.random.default_rng(3)
+        cases = []
+        for _ in range(8):
+            pick = rng.integers(0, 2, size=n).astype(bool)
+            px = np.bitwise_xor.reduce(x[n:][pick].astype(np.int64), axis=0)
+            pz = np.bitwise_xor.reduce(z[n:][pick].astype(np.int64), axis=0)
+            cases.append(px | (pz << 1))
+        cases += [rng.integers(0, 4, size=n) for _ in range(4)]
+        cases = np.array(cases, dtype=np.uint8)
+        want = t.expect(cases)
+    assert abs(np.vdot(v, v).real - 1.0) < 1e-5
+    idx = np.arange(1 << n)
+    for codes, w in zip(cases, want):
+        xm = int(sum(int(c & 1) << j for j, c in enumerate(codes)))
+        zm = int(sum(int(c >> 1) << j for j, c in enumerate(codes)))
+        ny = int(sum(1 for c in codes if c == 3))
+        par = np.array([bin(int(u)).count("1") & 1 for u in (idx & zm)])
+        pv = np.zeros_like(v)
+        pv[idx ^ xm] = v * np.where(par == 1, -1, 1)
+        e = np.vdot(v, pv * (1j ** ny))
+        assert abs(e - w) < 1e-4, (codes, e, w)
+
+
 def test_pipelined_apply_mid_circuit_measurements():
     """A list of more than 2^17 words on the grid engine is compiled in 2^16-
     word chunks while earlier chunks already run; MZR rounds every 5 layers put
