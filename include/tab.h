@@ -166,6 +166,30 @@ int tab_expect(tab_t h, const uint8_t *paulis, int32_t k, int8_t *out);
 #define TAB_SV_MAX_QUBITS 26
 int tab_statevector(tab_t h, float *amps, int64_t len);
 
+/* ---- one tableau split by rows over shards ---------------------------------- */
+
+/* A tableau whose qubit-row indices are split over `shards` shards (shard s
+ * holds destabilizer i and stabilizer n+i for its range of i, every column;
+ * 1 <= shards <= ceil(n/32)), each driven by its own host thread.  Gates need
+ * no exchange (AG Sec. III: rows are independent).  A Z measurement
+ * exchanges, between launches: the minimum of the shards' pivot candidates;
+ * in the random case the pivot row (2n bits and a sign), broadcast by its
+ * owner; in the deterministic case the shards' partial products of selected
+ * stabilizer rows, gathered on shard 0 and multiplied in shard order; then
+ * the outcome.  Results are identical to a single tableau's (same Philox
+ * outcome stream).  The handle owns its device memory; calls on one handle
+ * are not concurrent-safe. */
+typedef struct tab_shard_s *tab_shard_t;
+int tab_sharded_create(int32_t n, int32_t shards, tab_shard_t *out);
+int tab_sharded_destroy(tab_shard_t h);
+/* as tab_set_rng: (seed, circuit_id, shot) of the outcome stream, counter k = 0 */
+int tab_sharded_set_rng(tab_shard_t h, uint64_t seed, uint64_t circuit_id, uint32_t shot);
+/* as tab_apply, synchronous; base ops only (the extended ops are TAB_EINVAL) */
+int tab_sharded_apply(tab_shard_t h, const tab_gate *gates, int64_t count);
+int tab_sharded_read_outcomes(tab_shard_t h, uint8_t *out, int64_t max, int64_t *count);
+/* as tab_export: rows 0..2n-1 unpacked, gathered from the shards */
+int tab_sharded_export(tab_shard_t h, uint8_t *x, uint8_t *z, uint8_t *r);
+
 /* A gate list compiled once (validated, grouped into layers of disjoint gates,
  * uploaded to device memory) and replayable on any handle with the same n. */
 typedef struct tab_prog_s *tab_prog_t;

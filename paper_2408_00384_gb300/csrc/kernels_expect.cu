@@ -28,20 +28,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "pauli_product.cuh"
 #include "tab_internal.h"
 
 namespace tab {
 
 constexpr int kExpectThreads = 256;
-
-__device__ __forceinline__ uint32_t prefix_xor_inclusive(uint32_t v) {
-  v ^= v << 1;
-  v ^= v << 2;
-  v ^= v << 4;
-  v ^= v << 8;
-  v ^= v << 16;
-  return v;
-}
 
 template <int T>
 __global__ void __launch_bounds__(T) k_expect(const uint32_t* __restrict__ X,
@@ -90,39 +82,12 @@ __global__ void __launch_bounds__(T) k_expect(const uint32_t* __restrict__ X,
   for (int w = tid; w < Wh; w += T) rs ^= __popc(__ldg(R + Wh + w) & c[w]) & 1u;
   if (rs) atomicXor(&s_r, 1u);
   for (int j = warp; j < n; j += T / 32) {
-    const uint32_t* xc = X + (size_t)j * W + Wh;
-    const uint32_t* zc = Z + (size_t)j * W + Wh;
-    uint32_t cx = 0u, cz = 0u, e = 0u;  // running product of the rows so far
-    for (int w0 = 0; w0 < Wh; w0 += 32) {
-      const int w = w0 + lane;
-      const uint32_t m = w < Wh ? c[w] : 0u;
-      const uint32_t x1 = m ? __ldg(xc + w) & m : 0u;
-      const uint32_t z1 = m ? __ldg(zc + w) & m : 0u;
-      const uint32_t ix = prefix_xor_inclusive(x1), iz = prefix_xor_inclusive(z1);
-      // carry into this lane: parities of the lanes before it, then earlier chunks
-      const uint32_t bx = ix >> 31, bz = iz >> 31;
-      uint32_t sx = bx, sz = bz;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t tx = __shfl_up_sync(0xffffffffu, sx, o);
-        const uint32_t tz = __shfl_up_sync(0xffffffffu, sz, o);
-        if (lane >= o) {
-          sx ^= tx;
-          sz ^= tz;
-        }
-      }
-      const uint32_t inx = (sx ^ bx) ^ cx, inz = (sz ^ bz) ^ cz;  // exclusive over lanes
-      const uint32_t x2 = (ix << 1) ^ (0u - inx), z2 = (iz << 1) ^ (0u - inz);
-      const uint32_t plus = (x1 & z1 & ~x2 & z2) | (x1 & ~z1 & x2 & z2) | (~x1 & z1 & x2 & ~z2);
-      const uint32_t minus = (x1 & z1 & x2 & ~z2) | (x1 & ~z1 & ~x2 & z2) | (~x1 & z1 & x2 & z2);
-      e += (uint32_t)__popc(plus) + 3u * (uint32_t)__popc(minus);
-      cx ^= __shfl_sync(0xffffffffu, sx, 31);
-      cz ^= __shfl_sync(0xffffffffu, sz, 31);
-    }
-    e = __reduce_add_sync(0xffffffffu, e);
+    uint32_t qx, qz;
+    const uint32_t e = pp_column_product(X + (size_t)j * W + Wh, Z + (size_t)j * W + Wh, Wh,
+                                         [&](int w) { return c[w]; }, qx, qz);
     if (lane == 0) {
-      atomicAdd(&s_e, e & 3u);
-      if (cx != (p[j] & 1u) || cz != (p[j] >> 1)) atomicOr(&s_bad, 1u);
+      atomicAdd(&s_e, e);
+      if (qx != (p[j] & 1u) || qz != (p[j] >> 1)) atomicOr(&s_bad, 1u);
     }
   }
   __syncthreads();

@@ -68,6 +68,12 @@ _sig("tab_measure_async", ctypes.c_int, [_vp, _vp, _i32, _vp])
 _sig("tab_read_outcomes", ctypes.c_int, [_vp, _vp, _i64, _P(_i64)])
 _sig("tab_expect", ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp])
 _sig("tab_statevector", ctypes.c_int, [_vp, _vp, _i64])
+_sig("tab_sharded_create", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P(_vp)])
+_sig("tab_sharded_destroy", ctypes.c_int, [_vp])
+_sig("tab_sharded_set_rng", ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32])
+_sig("tab_sharded_apply", ctypes.c_int, [_vp, _vp, _i64])
+_sig("tab_sharded_read_outcomes", ctypes.c_int, [_vp, _vp, _i64, _P(_i64)])
+_sig("tab_sharded_export", ctypes.c_int, [_vp, _vp, _vp, _vp])
 _sig("tab_clear_outcomes", ctypes.c_int, [_vp])
 _sig("tab_kernel_launches", ctypes.c_int, [_vp, _P(_i64)])
 _sig("tab_set_engine", ctypes.c_int, [_vp, ctypes.c_int])
@@ -306,6 +312,50 @@ class Tableau:
         r = np.ascontiguousarray(r, dtype=np.uint8).reshape(2 * n)
         _check(_L.tab_import(self._h, x.ctypes.data, z.ctypes.data, r.ctypes.data,
                              meas_counter))
+
+
+class ShardedTableau:
+    """A tableau split by rows over `shards` shards driven by host threads
+    (tab_sharded_*): the same results as a Tableau."""
+
+    def __init__(self, n: int, shards: int):
+        self.n = n
+        h = _vp()
+        _check(_L.tab_sharded_create(n, shards, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if self._h:
+            _L.tab_sharded_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_rng(self, seed: int = 1, circuit_id: int = 0, shot: int = 0):
+        _check(_L.tab_sharded_set_rng(self._h, seed, circuit_id, shot))
+
+    def apply(self, gates):
+        g = _u64arr(gates)
+        _check(_L.tab_sharded_apply(self._h, g.ctypes.data if g.size else None, g.size))
+
+    def read_outcomes(self) -> np.ndarray:
+        cnt = _i64()
+        _check(_L.tab_sharded_read_outcomes(self._h, None, 0, ctypes.byref(cnt)))
+        out = np.zeros(max(cnt.value, 1), np.uint8)
+        _check(_L.tab_sharded_read_outcomes(self._h, out.ctypes.data, cnt.value, ctypes.byref(cnt)))
+        return out[:cnt.value]
+
+    def export(self):
+        n = self.n
+        x = np.zeros((2 * n, n), np.uint8)
+        z = np.zeros((2 * n, n), np.uint8)
+        r = np.zeros(2 * n, np.uint8)
+        _check(_L.tab_sharded_export(self._h, x.ctypes.data, z.ctypes.data, r.ctypes.data))
+        return x, z, r
 
 
 def _circuit_array(circuits):

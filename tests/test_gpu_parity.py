@@ -391,6 +391,46 @@ def test_statevector_after_measurement_and_expectations():
         assert abs(e - w) < 1e-4, (codes, e, w)
 
 
+@pytest.mark.parametrize("n,shards", [(1, 1), (33, 2), (64, 2), (100, 3), (129, 4), (257, 5),
+                                      (300, 1), (700, 7)])
+def test_sharded_tableau(n, shards):
+    """Rows split over shards driven by host threads (pivot all-reduce, row
+    broadcast, partial-product gather): outcomes and the gathered tableau
+    bit for bit against the oracle, over two apply calls."""
+    g = C.random_clifford_ops(n, 600, seed=90 + n, measure_p=0.08, reset_p=0.04)
+    want_out, want = oracle_result(n, g, 6, 1, 0)
+    with tab.ShardedTableau(n, shards) as t:
+        t.set_rng(6, 1, 0)
+        t.apply(g[:300])
+        t.apply(g[300:])
+        out = t.read_outcomes()
+        got = t.export()
+    assert np.array_equal(out, want_out)
+    for name, a, b in zip("xzr", got, want):
+        assert np.array_equal(a, b), name
+
+
+def test_sharded_ghz_and_layers():
+    """Deterministic outcomes across shards (GHZ: one random outcome, then
+    equal ones) and a random-layer circuit with a final measurement."""
+    n = 200
+    g = np.concatenate([C.encode(C.TAB_H, 0, 0).reshape(1),
+                        C.encode(np.full(n - 1, C.TAB_CNOT), np.arange(n - 1), np.arange(1, n)),
+                        C.encode(np.full(n, C.TAB_MZ), np.arange(n)[::-1].copy(), 0)])
+    with tab.ShardedTableau(n, 4) as t:
+        t.apply(g)
+        out = t.read_outcomes()
+    assert len(set(out.tolist())) == 1
+    c = C.random_layer_circuit(300, 20, seed=5)
+    want_out, want = oracle_result(c.n, c.gates, 2, 0, 0)
+    with tab.ShardedTableau(c.n, 3) as t:
+        t.set_rng(2, 0, 0)
+        t.apply(c.gates)
+        assert np.array_equal(t.read_outcomes(), want_out)
+        for a, b in zip(t.export(), want):
+            assert np.array_equal(a, b)
+
+
 def test_pipelined_apply_mid_circuit_measurements():
     """A list of more than 2^17 words on the grid engine is compiled in 2^16-
     word chunks while earlier chunks already run; MZR rounds every 5 layers put
