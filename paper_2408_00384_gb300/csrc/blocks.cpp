@@ -51,11 +51,11 @@ static const uint8_t* c1_row_of_op() {
 }
 
 void BlockBuilder::reset(int32_t n, size_t hint) {
-  if ((int32_t)cur_.size() < n) {
-    cur_.assign((size_t)n, -1);
-    role_.assign((size_t)n, 0);
-    stamp_.assign((size_t)n, 0u);
+  if (!comp_) {
+    comp_ = c1_table();
+    code_ = c1_row_of_op();
   }
+  if ((int32_t)q_.size() < n) q_.assign((size_t)n, QSlot{-1, 0u, 0u});
   ++seg_;
   blk_.clear();
   if (hint > blk_.capacity()) blk_.reserve(hint);
@@ -63,12 +63,8 @@ void BlockBuilder::reset(int32_t n, size_t hint) {
 
 // One gate (tab_op numbering) of the current run.
 void BlockBuilder::add(uint32_t op, uint32_t a, uint32_t b) {
-  auto latest = [&](uint32_t q) -> int32_t { return stamp_[q] == seg_ ? cur_[q] : -1; };
-  auto bind = [&](uint32_t q, int32_t B, uint8_t role) {
-    stamp_[q] = seg_;
-    cur_[q] = B;
-    role_[q] = role;
-  };
+  auto latest = [&](uint32_t q) -> int32_t { return q_[q].stamp == seg_ ? q_[q].cur : -1; };
+  auto bind = [&](uint32_t q, int32_t B, uint8_t role) { q_[q] = QSlot{B, seg_, role}; };
   auto open = [&](uint32_t qa, uint32_t qb, bool two, int32_t layer) -> int32_t {
     BlkRec k{};
     k.qa = (uint16_t)qa;
@@ -82,15 +78,14 @@ void BlockBuilder::add(uint32_t op, uint32_t a, uint32_t b) {
     if (two) bind(qb, B, 1);
     return B;
   };
-  const bool two = op == TAB_CNOT || op == TAB_CZ || op == TAB_SWAP;
+  const bool two = op - TAB_CNOT <= (uint32_t)(TAB_SWAP - TAB_CNOT);
   if (!two) {
-    const uint8_t* tab = c1_table() + 128 * c1_row_of_op()[op & 15u];
+    const uint8_t* tab = comp_ + 128u * code_[op & 15u];
     int32_t B = latest(a);
     if (B < 0) B = open(a, 0, false, 0);
     BlkRec& k = blk_[(size_t)B];
-    const uint8_t r = role_[a];
-    if (k.ent) k.V[r] = tab[k.V[r]];
-    else k.U[r] = tab[k.U[r]];
+    uint8_t* c = (k.ent ? k.V : k.U) + q_[a].role;
+    *c = tab[*c];
     return;
   }
   int32_t Ba = latest(a), Bb = latest(b);
@@ -136,14 +131,14 @@ void BlockBuilder::add(uint32_t op, uint32_t a, uint32_t b) {
     B = open(a, b, true, L);
   }
   BlkRec& k = blk_[(size_t)B];
-  const uint8_t ra = role_[a], rb = role_[b];
+  const uint32_t ra = q_[a].role, rb = q_[b].role;
   if (op == TAB_SWAP) {  // relabel: the registers stay, the qubits trade places
     k.swp ^= 1;
-    role_[a] = rb;
-    role_[b] = ra;
+    q_[a].role = rb;
+    q_[b].role = ra;
   } else if (op == TAB_CNOT) {
     k.ent = 1;
-    k.dir = ra;  // 0: control in register 0, target in 1; 1: the reverse
+    k.dir = (uint8_t)ra;  // 0: control in register 0, target in 1; 1: the reverse
   } else {
     k.ent = 2;  // CZ is symmetric
   }

@@ -73,6 +73,8 @@ struct tab_s {
   int stg_next = 0;
   std::vector<HostProgram> pipe;  // chunk programs of the pipelined apply (reused)
   HostProgram pipe_merged;        // consecutive chunks taken as one program
+  static constexpr int kPipeEv = 4;
+  cudaEvent_t pipe_ev[kPipeEv] = {};  // ends of the pipelined apply's launches
 };
 
 struct tab_prog_s {
@@ -607,6 +609,8 @@ int tab_destroy(tab_t h) {
     if (sg.p) cudaFreeHost(sg.p);
     if (sg.ev) cudaEventDestroy(sg.ev);
   }
+  for (cudaEvent_t ev : h->pipe_ev)
+    if (ev) cudaEventDestroy(ev);
   delete h;
   return TAB_OK;
 }
@@ -681,13 +685,22 @@ static int64_t apply_chunk(int64_t count) {
 // compiled by the host pool in list order while one pool thread uploads and
 // launches them, so the GPU starts on the first chunk while later ones are
 // still being compiled.  The chunks grow from 2^13 words (the GPU starts
-// early) to `chunk`; the launcher takes every chunk compiled by the time it
-// is free as one program (one upload, one gate launch per gate run).
+// early) to `chunk` and shrink again over the tail; the launcher takes every
+// chunk compiled by the time it is free as one program (one upload, one gate
+// launch per gate run).
 static int apply_pipelined(tab_t h, const tab_gate* gates, int64_t count, int64_t chunk) {
+  // chunk bounds: doubling from 2^13 words up to `chunk`, then `chunk`, and
+  // over the tail guided sizes (a share of what is left per compile thread,
+  // at least 2^12), so the last chunks finish close together and little GPU
+  // work is still queued when the host is done
+  const int64_t T = std::max(1, pool_threads() - 1), lo = (int64_t)1 << 12;
   std::vector<int64_t> bnd(1, 0);
   for (int64_t s = std::min<int64_t>(chunk, (int64_t)1 << 13); bnd.back() < count;
-       s = std::min<int64_t>(chunk, 2 * s))
-    bnd.push_back(std::min<int64_t>(count, bnd.back() + s));
+       s = std::min<int64_t>(chunk, 2 * s)) {
+    const int64_t left = count - bnd.back();
+    const int64_t step = 2 * left > T * chunk ? s : std::max(lo, std::min(s, left / T));
+    bnd.push_back(std::min<int64_t>(count, bnd.back() + step));
+  }
   const int nc = (int)bnd.size() - 1;
   if (h->pipe.size() < (size_t)nc) h->pipe.resize((size_t)nc);
   std::vector<HostProgram>& parts = h->pipe;
@@ -698,10 +711,28 @@ static int apply_pipelined(tab_t h, const tab_gate* gates, int64_t count, int64_
   pool_run(nc + 1, [&](int idx) {
     if (idx == 0) {  // the launcher (indices are taken in order: it starts first)
       cudaSetDevice(h->dev);
+      for (cudaEvent_t& ev : h->pipe_ev)
+        if (!ev && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) ev = nullptr;
+      // launches recorded, and known finished: with two still queued on the
+      // GPU, the launcher keeps merging chunks instead of adding a third
+      // (fewer, larger launches while the GPU is behind)
+      int issued = 0, finished = 0;
+      auto in_flight = [&]() {
+        while (finished < issued) {
+          cudaEvent_t ev = h->pipe_ev[finished % tab_s::kPipeEv];
+          if (ev && cudaEventQuery(ev) != cudaSuccess) break;
+          ++finished;
+        }
+        return issued - finished;
+      };
       for (int i = 0; i < nc;) {
         while (state[i].load(std::memory_order_acquire) == 0) std::this_thread::yield();
         int j = i + 1;
-        while (j < nc && state[j].load(std::memory_order_acquire) != 0) ++j;
+        for (;;) {
+          while (j < nc && state[j].load(std::memory_order_acquire) != 0) ++j;
+          if (j == nc || in_flight() < 2) break;
+          std::this_thread::yield();
+        }
         int r = TAB_OK;
         for (int c = i; c < j; ++c)
           if (state[c].load(std::memory_order_relaxed) < 0) r = TAB_EINVAL;
@@ -717,6 +748,8 @@ static int apply_pipelined(tab_t h, const tab_gate* gates, int64_t count, int64_
           if (r == TAB_OK) r = run_program(h, *hp, d, h->seed);
           free_async(d, h->stream);
           if (r != TAB_OK) cmsg = last_error();
+          cudaEvent_t ev = h->pipe_ev[issued % tab_s::kPipeEv];
+          if (r == TAB_OK && ev && cudaEventRecord(ev, h->stream) == cudaSuccess) ++issued;
         }
         if (r != TAB_OK && crc == TAB_OK) crc = r;
         i = j;

@@ -124,10 +124,15 @@ class BlockBuilder {
   void add(uint32_t op, uint32_t a, uint32_t b);  // next gate of the run (tab_op)
   void emit(HostProgram& P, Seg& s);              // append the run's blocks
  private:
-  std::vector<int32_t> cur_;    // latest block of each qubit in this run
-  std::vector<uint8_t> role_;   // register of that block holding the qubit
-  std::vector<uint32_t> stamp_; // run id of cur_ / role_ entries
+  struct QSlot {
+    int32_t cur;     // latest block of the qubit in this run
+    uint32_t stamp;  // run id of `cur` / `role`
+    uint32_t role;   // register of that block holding the qubit
+  };
+  std::vector<QSlot> q_;
   uint32_t seg_ = 0;
+  const uint8_t* comp_ = nullptr;  // single-qubit code composition table
+  const uint8_t* code_ = nullptr;  // code of each one-qubit op
   std::vector<BlkRec> blk_;
   std::vector<uint32_t> key_, cnt_;  // emit scratch: sort key per block, bucket counts
   std::vector<uint2> rec_;           // emit scratch: packed record per block
