@@ -570,11 +570,27 @@ cudaError_t launch_gates_flow(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int 
 
 int gates_block_max_n() { return (kMaxSmemBytes - 4096 - kBlkRing * 8) / 8; }
 
-cudaError_t launch_gates_block(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
-                               const uint2* blk, const uint32_t* blk_off, int nlayers, int* err,
-                               cudaStream_t s) {
-  if (nlayers <= 0) return cudaSuccess;
-  constexpr int T = 512;
+// Threads per CTA of the block kernel: the kernel is latency-bound per
+// super-layer, so a CTA just large enough for one block per thread (n/2
+// blocks in a full layer) keeps its barrier cheap: 128, 256 or 512 threads.
+// TAB_BLOCK_THREADS overrides (tuning sweeps).
+static int block_threads(int n) {
+  static int forced = -1;
+  if (forced < 0) {
+    forced = 0;
+    if (const char* e = getenv("TAB_BLOCK_THREADS")) {
+      const int v = atoi(e);
+      if (v == 128 || v == 256 || v == 512) forced = v;
+    }
+  }
+  if (forced) return forced;
+  return n <= 256 ? 128 : n <= 512 ? 256 : 512;
+}
+
+template <int T>
+static cudaError_t launch_gates_block_t(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
+                                        const uint2* blk, const uint32_t* blk_off, int nlayers,
+                                        int* err, cudaStream_t s) {
   const size_t smem = (size_t)kBlkRing * 8 + (size_t)n * 2 * sizeof(uint32_t);
   static bool attr_set = false;
   if (!attr_set) {
@@ -586,6 +602,17 @@ cudaError_t launch_gates_block(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int
   }
   k_gates_block<T><<<W, T, smem, s>>>(X, Z, R, n, W, blk, blk_off, nlayers, err);
   return cudaGetLastError();
+}
+
+cudaError_t launch_gates_block(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
+                               const uint2* blk, const uint32_t* blk_off, int nlayers, int* err,
+                               cudaStream_t s) {
+  if (nlayers <= 0) return cudaSuccess;
+  switch (block_threads(n)) {
+    case 128: return launch_gates_block_t<128>(X, Z, R, n, W, blk, blk_off, nlayers, err, s);
+    case 256: return launch_gates_block_t<256>(X, Z, R, n, W, blk, blk_off, nlayers, err, s);
+    default: return launch_gates_block_t<512>(X, Z, R, n, W, blk, blk_off, nlayers, err, s);
+  }
 }
 
 cudaError_t launch_gates_slab(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
