@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(T) k_gates_flow(uint32_t* __restrict__ X, uint
 // stores the two columns back (exchanged if the block swaps them).  The
 // records (8 bytes) stream through the same kind of TMA ring as the codes.
 constexpr int kBlkChunk = 512;                  // records per TMA copy (4 KB)
-constexpr int kBlkSlots = 16;                   // 64 KB ring
+constexpr int kBlkSlots = 16;                   // 64 KB ring (12 slots, 48 KB, for large n)
 constexpr int kBlkRing = kBlkChunk * kBlkSlots;
 
 // Identity, H and S codes take their short forms when every thread of the
@@ -424,17 +424,17 @@ __device__ __forceinline__ void apply_block(uint2 rec, uint32_t* sx, uint32_t* s
   sz[db] = z1;
 }
 
-template <int T>
+template <int T, int SLOTS>
 __global__ void __launch_bounds__(T) k_gates_block(uint32_t* __restrict__ X, uint32_t* __restrict__ Z,
                                                    uint32_t* __restrict__ R, int n, int W,
                                                    const uint2* __restrict__ blk,
                                                    const uint32_t* __restrict__ blk_off,
                                                    int nlayers, int* __restrict__ err) {
   extern __shared__ __align__(128) uint32_t sm[];
-  uint2* ring = reinterpret_cast<uint2*>(sm);  // block-record ring (kBlkRing records)
-  uint32_t* sx = sm + 2 * kBlkRing;            // X-plane word of every column (this slab)
+  uint2* ring = reinterpret_cast<uint2*>(sm);  // block-record ring (SLOTS * kBlkChunk records)
+  uint32_t* sx = sm + 2 * SLOTS * kBlkChunk;            // X-plane word of every column (this slab)
   uint32_t* sz = sx + n;                       // Z-plane word of every column
-  __shared__ __align__(8) uint64_t bars[kBlkSlots];
+  __shared__ __align__(8) uint64_t bars[SLOTS];
   __shared__ uint32_t s_r;
   __shared__ int s_abort;
   const int w = blockIdx.x, tid = threadIdx.x;
@@ -443,11 +443,11 @@ __global__ void __launch_bounds__(T) k_gates_block(uint32_t* __restrict__ X, uin
   const int nchunks = (int)((oe - base + kBlkChunk - 1) / kBlkChunk);
   int issued = 0, waited = 0;      // thread 0's pipeline state
   if (tid == 0) {
-    for (int i = 0; i < kBlkSlots; ++i) mbar_init(&bars[i], 1);
+    for (int i = 0; i < SLOTS; ++i) mbar_init(&bars[i], 1);
     mbar_fence_init();
     s_r = 0u;
     s_abort = 0;
-    for (; issued < nchunks && issued < kBlkSlots; ++issued)
+    for (; issued < nchunks && issued < SLOTS; ++issued)
       tma_bulk_g2s(ring + (size_t)issued * kBlkChunk, blk + base + (size_t)issued * kBlkChunk,
                    kBlkChunk * 8, &bars[issued]);
   }
@@ -464,8 +464,8 @@ __global__ void __launch_bounds__(T) k_gates_block(uint32_t* __restrict__ X, uin
     if (tid == 0) {
       // refill slots whose chunk ended before the previous super-layer began
       while (issued < nchunks &&
-             (int64_t)base + (int64_t)(issued - kBlkSlots + 1) * kBlkChunk <= (int64_t)prev_lb) {
-        const int slot = issued % kBlkSlots;
+             (int64_t)base + (int64_t)(issued - SLOTS + 1) * kBlkChunk <= (int64_t)prev_lb) {
+        const int slot = issued % SLOTS;
         fence_proxy_async_smem();
         tma_bulk_g2s(ring + (size_t)slot * kBlkChunk, blk + base + (size_t)issued * kBlkChunk,
                      kBlkChunk * 8, &bars[slot]);
@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(T) k_gates_block(uint32_t* __restrict__ X, uin
           s_abort = 1;
         } else {
           for (; waited <= c_last; ++waited)
-            if (!mbar_wait_bounded(&bars[waited % kBlkSlots], (uint32_t)(waited / kBlkSlots) & 1u)) {
+            if (!mbar_wait_bounded(&bars[waited % SLOTS], (uint32_t)(waited / SLOTS) & 1u)) {
               atomicCAS(err, 0, DERR_TIMEOUT);
               s_abort = 1;
               break;
@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(T) k_gates_block(uint32_t* __restrict__ X, uin
     for (uint32_t g0 = lb + (tid & ~31u); g0 < le; g0 += T) {  // warp-uniform trip count
       const uint32_t g = g0 + (tid & 31);
       const uint32_t act = __ballot_sync(0xffffffffu, g < le);
-      if (g < le) apply_block(ring[(g - base) & (kBlkRing - 1)], sx, sz, racc, act);
+      if (g < le) apply_block(ring[(g - base) % (SLOTS * kBlkChunk)], sx, sz, racc, act);
     }
     prev_lb = lb;
     lb = le;
@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(T) k_gates_block(uint32_t* __restrict__ X, uin
   // every copy issued must land before the CTA exits
   if (tid == 0)
     for (; waited < issued; ++waited)
-      mbar_wait_bounded(&bars[waited % kBlkSlots], (uint32_t)(waited / kBlkSlots) & 1u);
+      mbar_wait_bounded(&bars[waited % SLOTS], (uint32_t)(waited / SLOTS) & 1u);
   __syncthreads();
   if (s_abort) return;
 
@@ -587,31 +587,44 @@ static int block_threads(int n) {
   return n <= 256 ? 128 : n <= 512 ? 256 : 512;
 }
 
-template <int T>
+template <int T, int SLOTS>
 static cudaError_t launch_gates_block_t(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
                                         const uint2* blk, const uint32_t* blk_off, int nlayers,
                                         int* err, cudaStream_t s) {
-  const size_t smem = (size_t)kBlkRing * 8 + (size_t)n * 2 * sizeof(uint32_t);
+  const size_t smem = (size_t)SLOTS * kBlkChunk * 8 + (size_t)n * 2 * sizeof(uint32_t);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_gates_block<T>,
+    cudaError_t e = cudaFuncSetAttribute(k_gates_block<T, SLOTS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kMaxSmemBytes - 4096);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_gates_block<T><<<W, T, smem, s>>>(X, Z, R, n, W, blk, blk_off, nlayers, err);
+  k_gates_block<T, SLOTS><<<W, T, smem, s>>>(X, Z, R, n, W, blk, blk_off, nlayers, err);
   return cudaGetLastError();
+}
+
+// Ring slots: 16, or 12 where the smaller ring (still two super-layers of at
+// most kMaxLayerOps records plus a chunk on each side) is what lets two CTAs
+// share an SM (228 KB per SM, 1 KB of it reserved per CTA, a few hundred
+// bytes of static shared memory).
+static int block_slots(int n) {
+  const size_t two_per_sm = 115000;
+  const size_t c16 = (size_t)16 * kBlkChunk * 8 + (size_t)8 * n;
+  const size_t c12 = (size_t)12 * kBlkChunk * 8 + (size_t)8 * n;
+  return (c16 > two_per_sm && c12 <= two_per_sm) ? 12 : 16;
 }
 
 cudaError_t launch_gates_block(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
                                const uint2* blk, const uint32_t* blk_off, int nlayers, int* err,
                                cudaStream_t s) {
   if (nlayers <= 0) return cudaSuccess;
+  if (block_slots(n) == 12)
+    return launch_gates_block_t<512, 12>(X, Z, R, n, W, blk, blk_off, nlayers, err, s);
   switch (block_threads(n)) {
-    case 128: return launch_gates_block_t<128>(X, Z, R, n, W, blk, blk_off, nlayers, err, s);
-    case 256: return launch_gates_block_t<256>(X, Z, R, n, W, blk, blk_off, nlayers, err, s);
-    default: return launch_gates_block_t<512>(X, Z, R, n, W, blk, blk_off, nlayers, err, s);
+    case 128: return launch_gates_block_t<128, 16>(X, Z, R, n, W, blk, blk_off, nlayers, err, s);
+    case 256: return launch_gates_block_t<256, 16>(X, Z, R, n, W, blk, blk_off, nlayers, err, s);
+    default: return launch_gates_block_t<512, 16>(X, Z, R, n, W, blk, blk_off, nlayers, err, s);
   }
 }
 
