@@ -156,7 +156,7 @@ static int validate(int32_t n, const tab_gate* gates, int64_t begin, int64_t end
 static int build_range(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out,
                        int mode);
 
-void concat_programs(HostProgram& P, const HostProgram* part, size_t T) {
+void concat_programs(HostProgram& P, const HostProgram* part, size_t T, bool with_blk) {
   std::vector<size_t> o_ops(T + 1, 0), o_vers(T + 1, 0), o_blk(T + 1, 0), o_loff(T + 1, 0),
       o_boff(T + 1, 0), o_segs(T + 1, 0), o_meas(T + 1, 0);
   for (size_t t = 0; t < T; ++t) {
@@ -173,7 +173,7 @@ void concat_programs(HostProgram& P, const HostProgram* part, size_t T) {
   P.layered = part[0].layered;
   P.ops.resize(o_ops[T]);
   P.vers.resize(o_vers[T]);
-  P.blk.resize(o_blk[T]);
+  if (with_blk) P.blk.resize(o_blk[T]);
   P.layer_off.resize(o_loff[T]);
   P.blk_off.resize(o_boff[T]);
   P.segs.resize(o_segs[T]);
@@ -186,7 +186,7 @@ void concat_programs(HostProgram& P, const HostProgram* part, size_t T) {
     const HostProgram& Q = part[t];
     std::copy(Q.ops.begin(), Q.ops.end(), P.ops.begin() + (ptrdiff_t)o_ops[t]);
     std::copy(Q.vers.begin(), Q.vers.end(), P.vers.begin() + (ptrdiff_t)o_vers[t]);
-    std::copy(Q.blk.begin(), Q.blk.end(), P.blk.begin() + (ptrdiff_t)o_blk[t]);
+    if (with_blk) std::copy(Q.blk.begin(), Q.blk.end(), P.blk.begin() + (ptrdiff_t)o_blk[t]);
     for (size_t i = 0; i < Q.layer_off.size(); ++i)
       P.layer_off[o_loff[t] + i] = Q.layer_off[i] + (uint32_t)o_ops[t];
     for (size_t i = 0; i < Q.blk_off.size(); ++i)

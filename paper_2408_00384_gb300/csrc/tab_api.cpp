@@ -72,7 +72,10 @@ struct tab_s {
   Stage stg[kStages];
   int stg_next = 0;
   std::vector<HostProgram> pipe;  // chunk programs of the pipelined apply (reused)
-  HostProgram pipe_merged;        // consecutive chunks taken as one program
+  HostProgram pipe_merged;        // consecutive chunks taken as one program (no records)
+  std::vector<uint2*> pipe_pin;   // per chunk: its block records in pinned memory
+  std::vector<size_t> pipe_cap;   //   and that buffer's capacity (records)
+  cudaEvent_t pipe_end = nullptr; // after the last copy out of the pinned buffers
   static constexpr int kPipeEv = 4;
   cudaEvent_t pipe_ev[kPipeEv] = {};  // ends of the pipelined apply's launches
 };
@@ -402,15 +405,25 @@ void free_async(DevProg& d, cudaStream_t s) {
 // device buffer is rewritten only by later work on the handle's stream, after
 // the kernels that read it.  Programs above kKeptMax bytes get a device
 // allocation of their own, freed after use.
-int upload_staged(tab_t h, const HostProgram& hp, DevProg* d) {
+// With `ext` the block records are not in hp.blk but in ext->n pinned host
+// buffers, copied in order straight into the device buffer.
+struct ExtBlocks {
+  const uint2* const* ptr;
+  const size_t* cnt;
+  int n;
+  size_t total;
+};
+
+int upload_staged(tab_t h, const HostProgram& hp, DevProg* d, const ExtBlocks* ext = nullptr) {
   const bool want_rec =
       hp.n_gates > 0 && ((hp.mode & kProgStream) || ((hp.mode & kProgLayers) && use_flow_gates(hp.n)));
   const bool want_blk = (hp.mode & kProgBlocks) != 0;
+  const size_t nblk = ext ? ext->total : hp.blk.size();
   const size_t ob = align256((hp.ops.size() + kOpsPad) * 4);
   const size_t lb = align256(std::max<size_t>(hp.layer_off.size(), 1) * 4);
   const size_t sb = align256(std::max<size_t>(hp.segs.size(), 1) * sizeof(Seg));
   const size_t rb = want_rec ? align256((hp.ops.size() + kOpsPad) * sizeof(uint2)) : 0;
-  const size_t bb = want_blk ? align256((hp.blk.size() + kOpsPad) * sizeof(uint2)) : 0;
+  const size_t bb = want_blk ? align256((nblk + kOpsPad) * sizeof(uint2)) : 0;
   const size_t bo = want_blk ? align256(std::max<size_t>(hp.blk_off.size(), 1) * 4) : 0;
   const size_t total = ob + lb + sb + rb + bb + bo;
   tab_s::Stage& sg = h->stg[h->stg_next];
@@ -452,7 +465,7 @@ int upload_staged(tab_t h, const HostProgram& hp, DevProg* d) {
         memcpy(b0 + a, src + a, e - a);
       });
     }
-    memset(b0 + hp.blk.size() * sizeof(uint2), 0, (size_t)kOpsPad * sizeof(uint2));
+    memset(b0 + nblk * sizeof(uint2), 0, (size_t)kOpsPad * sizeof(uint2));
     if (!hp.blk_off.empty()) memcpy(b0 + bb, hp.blk_off.data(), hp.blk_off.size() * 4);
   }
   constexpr size_t kKeptMax = (size_t)64 << 20;
@@ -471,7 +484,22 @@ int upload_staged(tab_t h, const HostProgram& hp, DevProg* d) {
   } else {
     CU(cudaMallocAsync((void**)&dev, total, h->stream));
   }
-  CU(cudaMemcpyAsync(dev, st, total, cudaMemcpyHostToDevice, h->stream));
+  if (ext && want_blk) {
+    // everything but the records through the staging area, the records from
+    // the parts' own pinned buffers
+    const size_t rec0 = ob + lb + sb + rb, recb = nblk * sizeof(uint2);
+    CU(cudaMemcpyAsync(dev, st, rec0, cudaMemcpyHostToDevice, h->stream));
+    size_t at = rec0;
+    for (int i = 0; i < ext->n; ++i) {
+      const size_t b = ext->cnt[i] * sizeof(uint2);
+      if (b) CU(cudaMemcpyAsync(dev + at, ext->ptr[i], b, cudaMemcpyHostToDevice, h->stream));
+      at += b;
+    }
+    CU(cudaMemcpyAsync(dev + rec0 + recb, st + rec0 + recb, total - rec0 - recb,
+                       cudaMemcpyHostToDevice, h->stream));
+  } else {
+    CU(cudaMemcpyAsync(dev, st, total, cudaMemcpyHostToDevice, h->stream));
+  }
   h->h2d_bytes += (int64_t)total;
   CU(cudaEventRecord(sg.ev, h->stream));
   sg.pending = true;
@@ -611,6 +639,9 @@ int tab_destroy(tab_t h) {
   }
   for (cudaEvent_t ev : h->pipe_ev)
     if (ev) cudaEventDestroy(ev);
+  for (uint2* p : h->pipe_pin)
+    if (p) cudaFreeHost(p);
+  if (h->pipe_end) cudaEventDestroy(h->pipe_end);
   delete h;
   return TAB_OK;
 }
@@ -703,6 +734,13 @@ static int apply_pipelined(tab_t h, const tab_gate* gates, int64_t count, int64_
   }
   const int nc = (int)bnd.size() - 1;
   if (h->pipe.size() < (size_t)nc) h->pipe.resize((size_t)nc);
+  if (h->pipe_pin.size() < (size_t)nc) {
+    h->pipe_pin.resize((size_t)nc, nullptr);
+    h->pipe_cap.resize((size_t)nc, 0);
+  }
+  // the previous call's copies out of the pinned record buffers are done
+  // before the compile threads write them again
+  if (h->pipe_end) CU(cudaEventSynchronize(h->pipe_end));
   std::vector<HostProgram>& parts = h->pipe;
   std::unique_ptr<std::atomic<int>[]> state(new std::atomic<int>[(size_t)nc]);
   for (int i = 0; i < nc; ++i) state[i].store(0);
@@ -737,14 +775,21 @@ static int apply_pipelined(tab_t h, const tab_gate* gates, int64_t count, int64_
         for (int c = i; c < j; ++c)
           if (state[c].load(std::memory_order_relaxed) < 0) r = TAB_EINVAL;
         if (r != TAB_OK && crc == TAB_OK) cmsg = "chunk compile failed";
-        const HostProgram* hp = &parts[(size_t)i];
-        if (r == TAB_OK && crc == TAB_OK && j - i > 1) {
-          concat_programs(h->pipe_merged, hp, (size_t)(j - i));
-          hp = &h->pipe_merged;
+        // chunks i .. j-1 as one program: the small arrays merged here, the
+        // block records copied from each chunk's pinned buffer
+        const HostProgram* hp = &h->pipe_merged;
+        std::vector<size_t> cnt((size_t)(j - i));
+        ExtBlocks ext{&h->pipe_pin[(size_t)i], cnt.data(), j - i, 0};
+        if (r == TAB_OK && crc == TAB_OK) {
+          concat_programs(h->pipe_merged, &parts[(size_t)i], (size_t)(j - i), false);
+          for (int c = i; c < j; ++c) {
+            cnt[(size_t)(c - i)] = parts[(size_t)c].blk.size();
+            ext.total += parts[(size_t)c].blk.size();
+          }
         }
         if (r == TAB_OK && crc == TAB_OK && hp->n_gates + hp->n_meas > 0) {
           DevProg d;
-          r = upload_staged(h, *hp, &d);
+          r = upload_staged(h, *hp, &d, &ext);
           if (r == TAB_OK) r = run_program(h, *hp, d, h->seed);
           free_async(d, h->stream);
           if (r != TAB_OK) cmsg = last_error();
@@ -758,9 +803,24 @@ static int apply_pipelined(tab_t h, const tab_gate* gates, int64_t count, int64_
     }
     const int i = idx - 1;
     const int64_t b = bnd[(size_t)i], e = bnd[(size_t)i + 1];
-    const int r = build_validated_blocks(h->n, gates + b, e - b, &parts[(size_t)i]);
+    int r = build_validated_blocks(h->n, gates + b, e - b, &parts[(size_t)i]);
+    const size_t nb = parts[(size_t)i].blk.size();
+    if (r == TAB_OK && nb > h->pipe_cap[(size_t)i]) {  // grow this chunk's pinned buffer
+      if (h->pipe_pin[(size_t)i]) cudaFreeHost(h->pipe_pin[(size_t)i]);
+      h->pipe_pin[(size_t)i] = nullptr;
+      h->pipe_cap[(size_t)i] = 0;
+      const size_t cap = nb + nb / 4 + 64;
+      if (cudaMallocHost((void**)&h->pipe_pin[(size_t)i], cap * sizeof(uint2)) == cudaSuccess)
+        h->pipe_cap[(size_t)i] = cap;
+      else
+        r = TAB_ENOMEM;
+    }
+    if (r == TAB_OK && nb)
+      memcpy(h->pipe_pin[(size_t)i], parts[(size_t)i].blk.data(), nb * sizeof(uint2));
     state[i].store(r == TAB_OK ? 1 : -1, std::memory_order_release);
   });
+  if (!h->pipe_end) CU(cudaEventCreateWithFlags(&h->pipe_end, cudaEventDisableTiming));
+  CU(cudaEventRecord(h->pipe_end, h->stream));
   if (crc != TAB_OK) set_error("%s", cmsg.c_str());
   return crc;
 }

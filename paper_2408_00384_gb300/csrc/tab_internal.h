@@ -108,8 +108,9 @@ int build_validated_blocks(int32_t n, const tab_gate* gates, int64_t count, Host
 // gate list, in list order -- into P: each piece's arrays copied and its
 // offsets shifted (pieces in parallel on the host pool).  Consecutive gate
 // runs keep adjacent super-layer offsets: the last bound of one run equals
-// the first of the next.
-void concat_programs(HostProgram& P, const HostProgram* part, size_t T);
+// the first of the next.  With with_blk false the block records are not
+// copied (P.blk stays empty; the offsets are those of the full concatenation).
+void concat_programs(HostProgram& P, const HostProgram* part, size_t T, bool with_blk = true);
 
 // Block compiler for one gate run at a time (blocks.cpp).
 struct BlkRec {
