@@ -67,7 +67,10 @@ struct tab_s {
     bool pending = false;
     uint8_t* dev = nullptr;  // device buffer the copy goes to (stream-ordered reuse)
     size_t dcap = 0;
+    cudaEvent_t done = nullptr;  // after the kernels that read `dev` (side-stream uploads)
+    bool done_pending = false;
   };
+  cudaStream_t cstream = nullptr;  // copy stream of the pipelined apply's uploads
   static constexpr int kStages = 4;
   Stage stg[kStages];
   int stg_next = 0;
@@ -100,6 +103,7 @@ struct DevProg {
   uint32_t* blk_off = nullptr;
   void* base = nullptr;       // single allocation holding all of the above (staged uploads)
   bool kept = false;          // base is a staging area's device buffer: not freed after use
+  int stage = -1;             // that staging area
 };
 
 namespace {
@@ -414,7 +418,12 @@ struct ExtBlocks {
   size_t total;
 };
 
-int upload_staged(tab_t h, const HostProgram& hp, DevProg* d, const ExtBlocks* ext = nullptr) {
+// With `side` the copies run on the handle's copy stream, after the kernels
+// that last read this staging area's device buffer (its `done` event, which
+// the caller records once the program has run), and the handle's stream
+// waits for them: a program's upload overlaps the previous program's kernels.
+int upload_staged(tab_t h, const HostProgram& hp, DevProg* d, const ExtBlocks* ext = nullptr,
+                  bool side = false) {
   const bool want_rec =
       hp.n_gates > 0 && ((hp.mode & kProgStream) || ((hp.mode & kProgLayers) && use_flow_gates(hp.n)));
   const bool want_blk = (hp.mode & kProgBlocks) != 0;
@@ -426,7 +435,8 @@ int upload_staged(tab_t h, const HostProgram& hp, DevProg* d, const ExtBlocks* e
   const size_t bb = want_blk ? align256((nblk + kOpsPad) * sizeof(uint2)) : 0;
   const size_t bo = want_blk ? align256(std::max<size_t>(hp.blk_off.size(), 1) * 4) : 0;
   const size_t total = ob + lb + sb + rb + bb + bo;
-  tab_s::Stage& sg = h->stg[h->stg_next];
+  const int stage = h->stg_next;
+  tab_s::Stage& sg = h->stg[stage];
   h->stg_next = (h->stg_next + 1) % tab_s::kStages;
   if (sg.pending) {
     CU(cudaEventSynchronize(sg.ev));
@@ -471,6 +481,12 @@ int upload_staged(tab_t h, const HostProgram& hp, DevProg* d, const ExtBlocks* e
   constexpr size_t kKeptMax = (size_t)64 << 20;
   uint8_t* dev = nullptr;
   d->kept = total <= kKeptMax;
+  d->stage = stage;
+  side = side && d->kept;  // a buffer of its own is allocated in the handle's stream order
+  bool grown = false;
+  if (side && !h->cstream) CU(cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking));
+  if (side && !sg.done) CU(cudaEventCreateWithFlags(&sg.done, cudaEventDisableTiming));
+  cudaStream_t cs = side ? h->cstream : h->stream;
   if (d->kept) {
     if (sg.dcap < total) {
       if (sg.dev) CU(cudaFreeAsync(sg.dev, h->stream));
@@ -479,30 +495,40 @@ int upload_staged(tab_t h, const HostProgram& hp, DevProg* d, const ExtBlocks* e
       const size_t cap = std::min(kKeptMax, total + total / 4);
       CU(cudaMallocAsync((void**)&sg.dev, cap, h->stream));
       sg.dcap = cap;
+      grown = true;
     }
     dev = sg.dev;
   } else {
     CU(cudaMallocAsync((void**)&dev, total, h->stream));
   }
+  if (side) {  // after the last kernels that read this buffer (and a new allocation)
+    if (grown) {
+      CU(cudaEventRecord(sg.done, h->stream));
+      sg.done_pending = true;
+    }
+    if (sg.done_pending) CU(cudaStreamWaitEvent(cs, sg.done, 0));
+    sg.done_pending = false;
+  }
   if (ext && want_blk) {
     // everything but the records through the staging area, the records from
     // the parts' own pinned buffers
     const size_t rec0 = ob + lb + sb + rb, recb = nblk * sizeof(uint2);
-    CU(cudaMemcpyAsync(dev, st, rec0, cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(dev, st, rec0, cudaMemcpyHostToDevice, cs));
     size_t at = rec0;
     for (int i = 0; i < ext->n; ++i) {
       const size_t b = ext->cnt[i] * sizeof(uint2);
-      if (b) CU(cudaMemcpyAsync(dev + at, ext->ptr[i], b, cudaMemcpyHostToDevice, h->stream));
+      if (b) CU(cudaMemcpyAsync(dev + at, ext->ptr[i], b, cudaMemcpyHostToDevice, cs));
       at += b;
     }
     CU(cudaMemcpyAsync(dev + rec0 + recb, st + rec0 + recb, total - rec0 - recb,
-                       cudaMemcpyHostToDevice, h->stream));
+                       cudaMemcpyHostToDevice, cs));
   } else {
-    CU(cudaMemcpyAsync(dev, st, total, cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(dev, st, total, cudaMemcpyHostToDevice, cs));
   }
   h->h2d_bytes += (int64_t)total;
-  CU(cudaEventRecord(sg.ev, h->stream));
+  CU(cudaEventRecord(sg.ev, cs));
   sg.pending = true;
+  if (side) CU(cudaStreamWaitEvent(h->stream, sg.ev, 0));
   d->base = dev;
   d->ops = reinterpret_cast<uint32_t*>(dev);
   d->layer = reinterpret_cast<uint32_t*>(dev + ob);
@@ -639,6 +665,12 @@ int tab_destroy(tab_t h) {
   }
   for (cudaEvent_t ev : h->pipe_ev)
     if (ev) cudaEventDestroy(ev);
+  for (tab_s::Stage& sg : h->stg)
+    if (sg.done) cudaEventDestroy(sg.done);
+  if (h->cstream) {
+    cudaStreamSynchronize(h->cstream);
+    cudaStreamDestroy(h->cstream);
+  }
   for (uint2* p : h->pipe_pin)
     if (p) cudaFreeHost(p);
   if (h->pipe_end) cudaEventDestroy(h->pipe_end);
@@ -741,6 +773,13 @@ static int apply_pipelined(tab_t h, const tab_gate* gates, int64_t count, int64_
   // the previous call's copies out of the pinned record buffers are done
   // before the compile threads write them again
   if (h->pipe_end) CU(cudaEventSynchronize(h->pipe_end));
+  // the uploads run on the copy stream: it first waits for everything already
+  // queued on the handle's stream (earlier programs may still read the
+  // staging areas' device buffers)
+  if (!h->cstream) CU(cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking));
+  if (!h->pipe_end) CU(cudaEventCreateWithFlags(&h->pipe_end, cudaEventDisableTiming));
+  CU(cudaEventRecord(h->pipe_end, h->stream));
+  CU(cudaStreamWaitEvent(h->cstream, h->pipe_end, 0));
   std::vector<HostProgram>& parts = h->pipe;
   std::unique_ptr<std::atomic<int>[]> state(new std::atomic<int>[(size_t)nc]);
   for (int i = 0; i < nc; ++i) state[i].store(0);
@@ -789,8 +828,12 @@ static int apply_pipelined(tab_t h, const tab_gate* gates, int64_t count, int64_
         }
         if (r == TAB_OK && crc == TAB_OK && hp->n_gates + hp->n_meas > 0) {
           DevProg d;
-          r = upload_staged(h, *hp, &d, &ext);
+          r = upload_staged(h, *hp, &d, &ext, true);
           if (r == TAB_OK) r = run_program(h, *hp, d, h->seed);
+          if (r == TAB_OK && d.kept) {  // the staging area's buffer is free after these kernels
+            tab_s::Stage& sg = h->stg[d.stage];
+            if (sg.done && cudaEventRecord(sg.done, h->stream) == cudaSuccess) sg.done_pending = true;
+          }
           free_async(d, h->stream);
           if (r != TAB_OK) cmsg = last_error();
           cudaEvent_t ev = h->pipe_ev[issued % tab_s::kPipeEv];
