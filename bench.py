@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -139,7 +140,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.proc = None
         self.gpu = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # the sampled clock log (TAB_CLOCKS_DIR, else the system temp directory)
+        self.path = os.path.join(os.environ.get("TAB_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"tab_clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:

@@ -25,7 +25,7 @@
  * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
  * easy as 1, 2, 3", SC'11), written here from that paper's definition.
  *
- * Readings where the algorithm leaves a choice (listed again in the design doc):
+ * Readings where the algorithm leaves a choice:
  *  - pivot p is the smallest stabilizer row with x_pa = 1;
  *  - the destabilizer row p-n is not passed through rowsum, because AG replace
  *    it by row p right afterwards (its rowsum would be an anticommuting
