@@ -575,14 +575,13 @@ int gates_block_max_n() { return (kMaxSmemBytes - 4096 - kBlkRing * 8) / 8; }
 // blocks in a full layer) keeps its barrier cheap: 128, 256 or 512 threads.
 // TAB_BLOCK_THREADS overrides (tuning sweeps).
 static int block_threads(int n) {
-  static int forced = -1;
-  if (forced < 0) {
-    forced = 0;
+  static const int forced = [] {  // read once (thread-safe initialisation)
     if (const char* e = getenv("TAB_BLOCK_THREADS")) {
       const int v = atoi(e);
-      if (v == 128 || v == 256 || v == 512) forced = v;
+      if (v == 128 || v == 256 || v == 512) return v;
     }
-  }
+    return 0;
+  }();
   if (forced) return forced;
   return n <= 256 ? 128 : n <= 512 ? 256 : 512;
 }
@@ -592,14 +591,10 @@ static cudaError_t launch_gates_block_t(uint32_t* X, uint32_t* Z, uint32_t* R, i
                                         const uint2* blk, const uint32_t* blk_off, int nlayers,
                                         int* err, cudaStream_t s) {
   const size_t smem = (size_t)SLOTS * kBlkChunk * 8 + (size_t)n * 2 * sizeof(uint32_t);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_gates_block<T, SLOTS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kMaxSmemBytes - 4096);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  // set once per instance; shard threads may launch concurrently
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      k_gates_block<T, SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes - 4096);
+  if (attr != cudaSuccess) return attr;
   k_gates_block<T, SLOTS><<<W, T, smem, s>>>(X, Z, R, n, W, blk, blk_off, nlayers, err);
   return cudaGetLastError();
 }

@@ -1,8 +1,10 @@
 // Host check of the thread-rank collectives (shard_comm.h): ranks as threads
 // run many rounds of all-reduce-min, broadcast from a rotating root and
 // gather, and every rank checks every result; then one rank aborts in the
-// middle and the others must leave their collectives (no rank left waiting).
+// middle and the others must leave their collectives (no rank left waiting);
+// then one rank never arrives and the others must give up after the limit.
 // Exit status 0 on success.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <thread>
@@ -57,6 +59,18 @@ int main() {
       });
     for (auto& t : th) t.join();
   }
-  printf("bad %d left %d\n", bad.load(), left.load());
-  return (bad.load() == 0 && left.load() == R) ? 0 : 1;
+  // a rank that never arrives: the others give up after the limit
+  std::atomic<int> timed_out{0};
+  {
+    HostComm comm(R, 0.2);
+    std::vector<std::thread> th;
+    for (int r = 0; r < R - 1; ++r)  // rank R-1 never joins
+      th.emplace_back([&, r] {
+        int64_t m;
+        if (!comm.allreduce_min(r, r, &m)) timed_out++;
+      });
+    for (auto& t : th) t.join();
+  }
+  printf("bad %d left %d timed_out %d\n", bad.load(), left.load(), timed_out.load());
+  return (bad.load() == 0 && left.load() == R && timed_out.load() == R - 1) ? 0 : 1;
 }
