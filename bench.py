@@ -15,7 +15,9 @@ collective on the data path); rank 0 prints.
 Other workloads (`--workload`): `cfg1` (n=10), `cfg3` (n=10,000 with MZR
 rounds), `batched` (4,096 circuits with n in [16, 512] and 1-64 shots),
 `sweep` (the paper's own benchmark: uniformly random n-qubit Cliffords, no
-measurements, n = 2 ... 8192; one JSON line with a point per n).
+measurements, n = 2 ... 8192; one JSON line with a point per n), `extras`
+(the next-step features timed on their own: expectation values, the state
+vector export, the row-sharded tableau, noisy and X/Y-measured circuits).
 """
 from __future__ import annotations
 
@@ -57,7 +59,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="cfg2",
-                   choices=["cfg1", "cfg2", "cfg3", "batched", "served", "sweep"])
+                   choices=["cfg1", "cfg2", "cfg3", "batched", "served", "sweep", "extras"])
     p.add_argument("--sweep-max", type=int, default=8192, help="sweep: largest n")
     p.add_argument("--requests", type=int, default=48, help="served: number of requests")
     p.add_argument("--circuits", type=int, default=4096, help="batched: number of circuits")
@@ -708,13 +710,129 @@ def run_sweep(args, ws, rank, local):
             "points": points, "gpu_faster_than_oracle_from_n": cross, "clocks": clk}
 
 
+# ---------------------------------------------------------------- extras ---
+
+def run_extras(args, ws, rank, local):
+    """The next-step features, each timed on its own (CUDA events or host
+    wall time around synchronous calls, after one untimed call):
+    * expectation values: 1,000 Pauli strings (products of random stabilizer
+      subsets and random strings) on the n=1000 random-layer state;
+    * the state vector export at n = 20 and 24 (n projector passes over
+      2^n amplitudes, then the copy to the host);
+    * the row-sharded tableau on the n=1000 random-layer circuit with its
+      1,000 final measurements, 1, 2 and 4 shards, against one tableau;
+    * the same circuit with 1 % depolarizing noise ops and X / Y measurements
+      (host lowering inside tab_apply)."""
+    import torch
+    from paper_2408_00384_gb300 import tab
+    from workloads import circuits as C
+
+    torch.cuda.set_device(local)
+    c = C.config2()
+    out = {"metric": "next-step features: time per call", "unit": "ms", "n_gpus": ws,
+           "higher_is_better": False, "data": "synthetic", "dtype": "u32"}
+    # expectation values
+    rng = np.random.default_rng(1)
+    with tab.Tableau(c.n) as t:
+        t.apply(c.gates)
+        x, z, _ = t.export()
+        strings = []
+        for _ in range(900):
+            pick = rng.integers(0, 2, size=c.n).astype(bool)
+            px = np.bitwise_xor.reduce(x[c.n:][pick].astype(np.int64), axis=0)
+            pz = np.bitwise_xor.reduce(z[c.n:][pick].astype(np.int64), axis=0)
+            strings.append(px | (pz << 1))
+        strings += [rng.integers(0, 4, size=c.n) for _ in range(100)]
+        codes = np.array(strings, dtype=np.uint8)
+        t.expect(codes[:10])
+        reps = []
+        for _ in range(5):
+            h0 = time.perf_counter()
+            v = t.expect(codes)
+            reps.append(time.perf_counter() - h0)
+        ms = 1000.0 * statistics.median(reps)
+        out["expect"] = {"n": c.n, "strings": len(codes), "ms": ms,
+                         "strings_per_s": len(codes) / (ms / 1000.0),
+                         "nonzero": int((v != 0).sum())}
+    # state vector export
+    sv = []
+    for n in (20, 24):
+        g = C.random_clifford(n, C.splitmix64(99 + n)).gates
+        with tab.Tableau(n) as t:
+            t.apply(g)
+            t.statevector()
+            reps = []
+            for _ in range(3):
+                h0 = time.perf_counter()
+                t.statevector()
+                reps.append(time.perf_counter() - h0)
+        ms = 1000.0 * statistics.median(reps)
+        sv.append({"n": n, "ms": ms, "amplitudes": 1 << n,
+                   "device_bytes_moved": n * 2 * 8 * (1 << n)})
+    out["statevector"] = sv
+    # row-sharded tableau vs one tableau, the same circuit and outcomes
+    sh = []
+    with tab.Tableau(c.n) as t:
+        t.set_rng(C.PHILOX_SEED, 0, 0)
+        t.apply(c.gates)
+        want = t.read_outcomes()
+        reps = []
+        for _ in range(3):
+            t.reset()
+            t.set_rng(C.PHILOX_SEED, 0, 0)
+            h0 = time.perf_counter()
+            t.apply(c.gates)
+            t.read_outcomes()
+            reps.append(time.perf_counter() - h0)
+        sh.append({"shards": 0, "ms": 1000.0 * statistics.median(reps)})
+    for shards in (1, 2, 4):
+        reps, same = [], True
+        for _ in range(2):
+            with tab.ShardedTableau(c.n, shards) as t:
+                t.set_rng(C.PHILOX_SEED, 0, 0)
+                h0 = time.perf_counter()
+                t.apply(c.gates)
+                got = t.read_outcomes()
+                reps.append(time.perf_counter() - h0)
+                same = same and bool(np.array_equal(got, want))
+        sh.append({"shards": shards, "ms": 1000.0 * min(reps), "outcomes_equal": same})
+    out["sharded"] = {"workload": "n=1000, 1000 random layers, 1000 final MZ",
+                      "points": sh, "note": "shards 0 = one tableau (tab_apply)"}
+    # noisy circuit with X / Y measurements
+    op, q1, _ = C.decode(c.gates)
+    gate_pos = np.flatnonzero(~np.isin(op, C.MEASURE + (C.TAB_BARRIER,)))
+    pos = np.sort(rng.choice(gate_pos, size=gate_pos.size // 100, replace=False))
+    noise = C.encode(np.full(pos.size, C.TAB_DEPOL1), rng.integers(0, c.n, size=pos.size),
+                     C.noise_field(0.01))
+    noisy = np.insert(c.gates, pos, noise)
+    mz = np.isin(C.decode(noisy)[0], C.MEASURE)
+    mx = noisy.copy()
+    kinds = np.where(np.arange(mz.sum()) % 2 == 0, C.TAB_MX, C.TAB_MY)
+    mx[mz] = C.encode(kinds, C.decode(noisy[mz])[1], 0)
+    with tab.Tableau(c.n) as t:
+        t.apply(mx)
+        t.sync()
+        reps = []
+        for _ in range(5):
+            t.reset()
+            h0 = time.perf_counter()
+            t.apply(mx)
+            t.read_outcomes()
+            reps.append(time.perf_counter() - h0)
+    out["noisy_xy"] = {"workload": "the n=1000 circuit + 1 % DEPOL1 ops, final MX/MY",
+                       "noise_ops": int(pos.size), "ms": 1000.0 * statistics.median(reps)}
+    return out
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)
         return
-    if args.workload == "sweep":
+    if args.workload == "extras":
+        line = run_extras(args, ws, rank, local)
+    elif args.workload == "sweep":
         line = run_sweep(args, ws, rank, local)
     elif args.workload == "batched":
         line = run_batched(args, ws, rank, local)

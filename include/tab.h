@@ -132,6 +132,17 @@ int tab_set_rng(tab_t h, uint64_t seed, uint64_t circuit_id, uint32_t shot);
  * outcome log; keeps the RNG settings but resets k to 0.  Asynchronous. */
 int tab_reset(tab_t h);
 
+/* Host only (no device work): the base-op list that tab_apply runs for a list
+ * holding extended ops, under RNG context (seed, circuit_id, shot) and noise
+ * counter *noise_counter (advanced; NULL: noise ops are TAB_EINVAL).  MX / MY
+ * become Z measurements between basis changes; a run of consecutive
+ * measurement ops on distinct qubits shares one block of pre-rotations and
+ * one of post-rotations (the same tableau as op by op).  *out_count is the
+ * number of words; TAB_ENOMEM (nothing written) when it exceeds out_cap. */
+int tab_lower_ops(int32_t n, const tab_gate *gates, int64_t count, uint64_t seed,
+                  uint64_t circuit_id, uint32_t shot, uint64_t *noise_counter, tab_gate *out,
+                  int64_t out_cap, int64_t *out_count);
+
 /* ---- gates and measurements --------------------------------------------- */
 
 /* Apply `count` gate words (host memory, program order, TAB_MZ/TAB_MZR

@@ -868,50 +868,117 @@ static int apply_pipelined(tab_t h, const tab_gate* gates, int64_t count, int64_
   return crc;
 }
 
-// Extended ops (tab.h) lowered to base ops: MX -> H, MZ, H; MY -> S^dag, H,
-// MZ, H, S; a noise op -> the Pauli its Philox draw selects, or nothing.  The
-// list has been validated with extended ops allowed.  Noise ops need a handle
-// (its RNG settings and noise counter, which this advances); with h == nullptr
-// they are rejected.
-static int lower_extended(tab_t h, const tab_gate* g, int64_t count, std::vector<tab_gate>& out) {
+// Extended ops (tab.h) lowered to base ops.
+//  * A noise op becomes the Pauli its Philox draw selects, or nothing.  The
+//    draw uses the RNG context (seed, circuit, shot) and the noise counter
+//    *noise_k, which this advances; with noise_k == nullptr noise ops are
+//    rejected.
+//  * MX and MY are Z measurements between basis changes (MX: H, MZ, H; MY:
+//    S^dag H, MZ, H S).  A maximal run of consecutive measurement ops (MZ,
+//    MZR, MX, MY) on pairwise distinct qubits is lowered as: every
+//    pre-rotation, then the Z measurements in their order, then every
+//    post-rotation.  A one-qubit gate on qubit b commutes with everything a Z
+//    measurement of qubit a != b does to the tableau (it conjugates every row
+//    alike, and conjugation respects row products and signs), so the result is
+//    the one of the ops taken one by one, and the run stays one measurement
+//    segment.
+// The list has been validated with extended ops allowed.  Plain words are
+// copied in spans.
+static int lower_ops(int32_t n, const tab_gate* g, int64_t count, uint64_t seed, uint64_t cid,
+                     uint32_t shot, uint64_t* noise_k, std::vector<tab_gate>& out) {
   constexpr uint32_t kNoiseKeyTag = 0x4E4F4953u;  // noise draws use a key of their own
   out.clear();
   out.reserve((size_t)count + (size_t)count / 4 + 8);
   auto put = [&](uint32_t op, uint64_t q) { out.push_back(tab_make_gate(op, (uint32_t)q, 0)); };
+  auto op_of = [&](int64_t i) { return (uint32_t)(g[i] >> 56); };
+  auto q1_of = [&](int64_t i) { return (g[i] >> 28) & 0xFFFFFFFull; };
+  auto is_meas = [](uint32_t op) {
+    return op == TAB_MZ || op == TAB_MZR || op == TAB_MX || op == TAB_MY;
+  };
+  std::vector<uint32_t> seen((size_t)n, 0u);  // run stamp per qubit
+  uint32_t stamp = 0;
+  int64_t span = 0;  // first plain word not yet copied
   for (int64_t i = 0; i < count; ++i) {
-    const uint32_t op = (uint32_t)(g[i] >> 56);
-    const uint64_t q1 = (g[i] >> 28) & 0xFFFFFFFull, q2 = g[i] & 0xFFFFFFFull;
-    switch (op) {
-      case TAB_MX:
-        for (uint32_t o : {TAB_H, TAB_MZ, TAB_H}) put(o, q1);
-        break;
-      case TAB_MY:
-        for (uint32_t o : {TAB_SDG, TAB_H, TAB_MZ, TAB_H, TAB_S}) put(o, q1);
-        break;
-      case TAB_DEPOL1:
-      case TAB_XERR:
-      case TAB_ZERR: {
-        if (!h) {
-          set_error("gate %lld: noise ops are accepted by tab_apply only", (long long)i);
-          return TAB_EINVAL;
-        }
-        const uint64_t j = h->noise_k++;
-        const uint4 r = philox4x32_10(
-            make_uint4((uint32_t)j, h->shot, (uint32_t)h->cid, (uint32_t)(h->cid >> 32)),
-            make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32) ^ kNoiseKeyTag));
-        if ((r.x >> 4) < (uint32_t)q2) {
-          static const uint32_t kDepol[3] = {TAB_X, TAB_Y, TAB_Z};
-          put(op == TAB_XERR ? TAB_X
-              : op == TAB_ZERR ? TAB_Z
-                               : kDepol[((uint64_t)r.y * 3u) >> 32],
-              q1);
-        }
-        break;
+    const uint32_t op = op_of(i);
+    if (op < TAB_MX && !is_meas(op)) continue;  // plain gate word
+    out.insert(out.end(), g + span, g + i);
+    if (is_meas(op)) {
+      // the run: consecutive measurement ops on distinct qubits
+      ++stamp;
+      int64_t e = i;
+      bool ext = false;
+      while (e < count && is_meas(op_of(e)) && seen[(size_t)q1_of(e)] != stamp) {
+        seen[(size_t)q1_of(e)] = stamp;
+        ext = ext || op_of(e) == TAB_MX || op_of(e) == TAB_MY;
+        ++e;
       }
-      default:
-        out.push_back(g[i]);
+      if (!ext) {  // plain measurements only: copy them as they are
+        out.insert(out.end(), g + i, g + e);
+      } else {
+        for (int64_t k = i; k < e; ++k) {
+          if (op_of(k) == TAB_MY) put(TAB_SDG, q1_of(k));
+          if (op_of(k) == TAB_MX || op_of(k) == TAB_MY) put(TAB_H, q1_of(k));
+        }
+        for (int64_t k = i; k < e; ++k) put(op_of(k) == TAB_MZR ? TAB_MZR : TAB_MZ, q1_of(k));
+        for (int64_t k = i; k < e; ++k) {
+          if (op_of(k) == TAB_MX || op_of(k) == TAB_MY) put(TAB_H, q1_of(k));
+          if (op_of(k) == TAB_MY) put(TAB_S, q1_of(k));
+        }
+      }
+      span = e;
+      i = e - 1;
+      continue;
     }
+    // a noise op
+    if (!noise_k) {
+      set_error("gate %lld: noise ops are accepted by tab_apply only", (long long)i);
+      return TAB_EINVAL;
+    }
+    const uint64_t j = (*noise_k)++;
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)j, shot, (uint32_t)cid, (uint32_t)(cid >> 32)),
+                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32) ^ kNoiseKeyTag));
+    if ((r.x >> 4) < (uint32_t)(g[i] & 0xFFFFFFFull)) {
+      static const uint32_t kDepol[3] = {TAB_X, TAB_Y, TAB_Z};
+      put(op == TAB_XERR ? TAB_X : op == TAB_ZERR ? TAB_Z : kDepol[((uint64_t)r.y * 3u) >> 32],
+          q1_of(i));
+    }
+    span = i + 1;
   }
+  out.insert(out.end(), g + span, g + count);
+  return TAB_OK;
+}
+
+static int lower_extended(tab_t h, int32_t n, const tab_gate* g, int64_t count,
+                          std::vector<tab_gate>& out) {
+  if (!h) return lower_ops(n, g, count, 0, 0, 0, nullptr, out);
+  return lower_ops(n, g, count, h->seed, h->cid, h->shot, &h->noise_k, out);
+}
+
+int tab_lower_ops(int32_t n, const tab_gate* gates, int64_t count, uint64_t seed,
+                  uint64_t circuit_id, uint32_t shot, uint64_t* noise_counter, tab_gate* out,
+                  int64_t out_cap, int64_t* out_count) {
+  if (n < 1 || n > TAB_MAX_QUBITS) {
+    set_error("n=%d outside [1, %d]", n, TAB_MAX_QUBITS);
+    return TAB_ERANGE;
+  }
+  if (!out_count || (out_cap > 0 && !out)) {
+    set_error("null output pointer");
+    return TAB_EINVAL;
+  }
+  int64_t ext = 0;
+  int rc = validate_program(n, gates, count, &ext);
+  if (rc) return rc;
+  std::vector<tab_gate> low;
+  uint64_t nk = noise_counter ? *noise_counter : 0;
+  rc = lower_ops(n, gates, count, seed, circuit_id, shot, &nk, low);
+  if (rc) return rc;
+  *out_count = (int64_t)low.size();
+  if ((int64_t)low.size() > out_cap) {
+    set_error("output needs %lld words", (long long)low.size());
+    return TAB_ENOMEM;
+  }
+  if (!low.empty()) memcpy(out, low.data(), low.size() * sizeof(tab_gate));
+  if (noise_counter) *noise_counter = nk;
   return TAB_OK;
 }
 
@@ -923,7 +990,7 @@ int tab_apply(tab_t h, const tab_gate* gates, int64_t count) {
   if (rc) return rc;
   std::vector<tab_gate> lowered;
   if (ext) {
-    rc = lower_extended(h, gates, count, lowered);
+    rc = lower_extended(h, h->n, gates, count, lowered);
     if (rc) return rc;
     gates = lowered.data();
     count = (int64_t)lowered.size();
@@ -959,7 +1026,7 @@ int tab_prog_create(int32_t n, const tab_gate* gates, int64_t count, tab_prog_t*
   std::vector<tab_gate> lowered;
   int rc = (n >= 1 && n <= TAB_MAX_QUBITS) ? validate_program(n, gates, count, &ext) : TAB_OK;
   if (rc == TAB_OK && ext) {
-    rc = lower_extended(nullptr, gates, count, lowered);
+    rc = lower_extended(nullptr, n, gates, count, lowered);
     gates = lowered.data();
     count = (int64_t)lowered.size();
   }

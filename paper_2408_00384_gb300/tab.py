@@ -68,6 +68,8 @@ _sig("tab_measure_async", ctypes.c_int, [_vp, _vp, _i32, _vp])
 _sig("tab_read_outcomes", ctypes.c_int, [_vp, _vp, _i64, _P(_i64)])
 _sig("tab_expect", ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp])
 _sig("tab_statevector", ctypes.c_int, [_vp, _vp, _i64])
+_sig("tab_lower_ops", ctypes.c_int, [ctypes.c_int32, _vp, _i64, ctypes.c_uint64, ctypes.c_uint64,
+                                     ctypes.c_uint32, _P(ctypes.c_uint64), _vp, _i64, _P(_i64)])
 _sig("tab_sharded_create", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P(_vp)])
 _sig("tab_sharded_destroy", ctypes.c_int, [_vp])
 _sig("tab_sharded_set_rng", ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32])
@@ -356,6 +358,20 @@ class ShardedTableau:
         r = np.zeros(2 * n, np.uint8)
         _check(_L.tab_sharded_export(self._h, x.ctypes.data, z.ctypes.data, r.ctypes.data))
         return x, z, r
+
+
+def lower_ops(n: int, gates, seed: int = 1, circuit_id: int = 0, shot: int = 0,
+              noise_counter: int = 0):
+    """The base-op list tab_apply runs for `gates` (host only; no GPU needed)
+    and the noise counter after it."""
+    g = _u64arr(gates)
+    cap = max(4 * g.size + 8, 16)
+    out = np.zeros(cap, np.uint64)
+    cnt = _i64()
+    nk = ctypes.c_uint64(noise_counter)
+    _check(_L.tab_lower_ops(n, g.ctypes.data if g.size else None, g.size, seed, circuit_id, shot,
+                            ctypes.byref(nk), out.ctypes.data, cap, ctypes.byref(cnt)))
+    return out[:cnt.value].copy(), nk.value
 
 
 def _circuit_array(circuits):

@@ -174,3 +174,34 @@ def test_expectation_all_paulis_vs_statevector(n):
             assert abs(want - t.expect(codes)) < 1e-9, (codes, want)
         for a, b in zip(before, t.get()):
             assert np.array_equal(a, b)
+
+
+# -------------------------------------------- host lowering (library, CPU)
+
+def test_lowering_equals_op_by_op():
+    """tab_lower_ops (what tab_apply runs) gives, in the oracle, the outcomes
+    and tableau of the extended ops taken one by one; a run of X / Y
+    measurements on distinct qubits becomes one block of Z measurements."""
+    tab = pytest.importorskip("paper_2408_00384_gb300.tab")
+    rng = np.random.default_rng(4)
+    for n, seed in [(7, 3), (40, 5), (130, 8)]:
+        base = C.random_extended_ops(n, 400, seed=seed, p_meas=0.15, p_noise=0.1)
+        qs = rng.choice(n, size=min(n, 30), replace=False)
+        kinds = rng.choice([C.TAB_MX, C.TAB_MY, C.TAB_MZ, C.TAB_MZR], size=qs.size)
+        run = C.encode(kinds, qs, 0)
+        bar = C.encode(C.TAB_BARRIER, 0, 0).reshape(1)
+        g = np.concatenate([base[:200], bar, run, bar, base[200:]])
+        low, nk = tab.lower_ops(n, g, seed=9, circuit_id=2, shot=1)
+        assert not np.isin(C.decode(low)[0], (13, 14, 15, 16, 17)).any()
+        assert nk == int(np.isin(C.decode(g)[0], C.NOISE).sum())
+        want_out, want = oracle.run_circuit(n, g, seed=9, circuit_id=2, shot=1)
+        got_out, got = oracle.run_circuit(n, low, seed=9, circuit_id=2, shot=1)
+        assert np.array_equal(got_out, want_out)
+        for a, b in zip(got, want):
+            assert np.array_equal(a, b)
+        # the run's measurements are consecutive in the lowered list
+        op = C.decode(low)[0]
+        m = np.isin(op, C.MEASURE)
+        runs = np.diff(np.concatenate([[0], m.astype(np.int8), [0]]))
+        longest = (np.flatnonzero(runs == -1) - np.flatnonzero(runs == 1)).max()
+        assert longest >= qs.size
