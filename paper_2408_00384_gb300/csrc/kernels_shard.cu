@@ -82,38 +82,55 @@ __global__ void k_sh_getrow(const uint32_t* __restrict__ X, const uint32_t* __re
 }
 
 // Every local row h with x_ha = 1, h != p and h != p-n (li >= 0 on the owner
-// of p), becomes row_p * row_h with the sign AG's rowsum gives.  One thread per
-// local word; bit-sliced mod-4 exponent counters (lo, hi).
+// of p), becomes row_p * row_h with the sign AG's rowsum gives.  One CTA per
+// local word; its threads split the columns, each keeping bit-sliced mod-4
+// exponent counters (lo, hi) of the 32 rows for its columns, and the
+// counters are summed over the threads (mod-4 addition, bit-sliced) before
+// the sign update.
 __global__ void k_sh_rowsum(uint32_t* __restrict__ X, uint32_t* __restrict__ Z,
                             uint32_t* __restrict__ R, int n, int Whs, int a, int li,
                             const uint32_t* __restrict__ row_g, int* __restrict__ err) {
-  extern __shared__ uint32_t row[];
-  const int Ws = 2 * Whs, nw = (n + 31) / 32;
-  for (int k = threadIdx.x; k < 2 * nw + 1; k += blockDim.x) row[k] = row_g[k];
+  extern __shared__ uint32_t row[];  // 2 nw + 1 words, then 2 * blockDim.x counters
+  const int Ws = 2 * Whs, nw = (n + 31) / 32, w = blockIdx.x, T = blockDim.x;
+  uint32_t* clo = row + 2 * nw + 1;
+  uint32_t* chi = clo + T;
+  for (int k = threadIdx.x; k < 2 * nw + 1; k += T) row[k] = row_g[k];
   __syncthreads();
-  const int w = blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= Ws) return;
-  uint32_t m = X[(size_t)a * Ws + w];
-  if (li >= 0) {
-    if (w == li / 32 || w == Whs + li / 32) m &= ~(1u << (li % 32));
-  }
-  if (!m) return;
+  uint32_t m = X[(size_t)a * Ws + w];  // rows with x_ha = 1, read before any update
+  if (li >= 0 && (w == li / 32 || w == Whs + li / 32)) m &= ~(1u << (li % 32));
   uint32_t lo = 0u, hi = 0u;
-  for (int j = 0; j < n; ++j) {
-    const uint32_t xp = 0u - ((row[j >> 5] >> (j & 31)) & 1u);
-    const uint32_t zp = 0u - ((row[nw + (j >> 5)] >> (j & 31)) & 1u);
-    if (!(xp | zp)) continue;
-    const size_t k = (size_t)j * Ws + w;
-    const uint32_t x2 = X[k], z2 = Z[k];
-    const uint32_t plus = (xp & zp & ~x2 & z2) | (xp & ~zp & x2 & z2) | (~xp & zp & x2 & ~z2);
-    const uint32_t minus = (xp & zp & x2 & ~z2) | (xp & ~zp & ~x2 & z2) | (~xp & zp & x2 & z2);
-    hi ^= (lo & plus) | (~lo & minus);
-    lo ^= plus | minus;
-    X[k] = x2 ^ (m & xp);
-    Z[k] = z2 ^ (m & zp);
+  __syncthreads();  // every thread has read column a before it changes
+  if (m) {
+    for (int j = threadIdx.x; j < n; j += T) {
+      const uint32_t xp = 0u - ((row[j >> 5] >> (j & 31)) & 1u);
+      const uint32_t zp = 0u - ((row[nw + (j >> 5)] >> (j & 31)) & 1u);
+      if (!(xp | zp)) continue;
+      const size_t k = (size_t)j * Ws + w;
+      const uint32_t x2 = X[k], z2 = Z[k];
+      const uint32_t plus = (xp & zp & ~x2 & z2) | (xp & ~zp & x2 & z2) | (~xp & zp & x2 & ~z2);
+      const uint32_t minus = (xp & zp & x2 & ~z2) | (xp & ~zp & ~x2 & z2) | (~xp & zp & x2 & z2);
+      hi ^= (lo & plus) | (~lo & minus);
+      lo ^= plus | minus;
+      X[k] = x2 ^ (m & xp);
+      Z[k] = z2 ^ (m & zp);
+    }
   }
-  if (lo & m) atomicCAS(err, 0, DERR_PHASE);
-  R[w] ^= m & ((0u - row[2 * nw]) ^ hi);
+  clo[threadIdx.x] = lo;
+  chi[threadIdx.x] = hi;
+  __syncthreads();
+  for (int o = T / 2; o > 0; o >>= 1) {  // (lo, hi) + (lo', hi') mod 4, bit-sliced
+    if (threadIdx.x < o) {
+      const uint32_t l2 = clo[threadIdx.x + o], h2 = chi[threadIdx.x + o];
+      const uint32_t l1 = clo[threadIdx.x];
+      chi[threadIdx.x] ^= h2 ^ (l1 & l2);
+      clo[threadIdx.x] = l1 ^ l2;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && m) {
+    if (clo[0] & m) atomicCAS(err, 0, DERR_PHASE);
+    R[w] ^= m & ((0u - row[2 * nw]) ^ chi[0]);
+  }
 }
 
 // Owner of p (local index li): row p-n := row p (the broadcast copy), row
@@ -263,9 +280,8 @@ cudaError_t sh_getrow(const uint32_t* X, const uint32_t* Z, const uint32_t* R, i
 }
 cudaError_t sh_rowsum(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Whs, int a, int li,
                       const uint32_t* row, int* err, cudaStream_t s) {
-  const size_t smem = (size_t)(2 * ((n + 31) / 32) + 1) * 4;
-  k_sh_rowsum<<<sh_blocks((size_t)2 * Whs), kShThreads, smem, s>>>(X, Z, R, n, Whs, a, li, row,
-                                                                    err);
+  const size_t smem = (size_t)(2 * ((n + 31) / 32) + 1 + 2 * kShThreads) * 4;
+  k_sh_rowsum<<<2 * Whs, kShThreads, smem, s>>>(X, Z, R, n, Whs, a, li, row, err);
   return cudaGetLastError();
 }
 cudaError_t sh_setrows(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Whs, int a, int li,

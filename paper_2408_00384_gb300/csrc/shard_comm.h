@@ -5,11 +5,13 @@
 // Every collective is entered by all ranks in the same order.  A rank that
 // fails calls abort(); from then on every collective returns false at once
 // (and a wait that outlasts the limit aborts too), so no rank is left
-// waiting on one that has gone.
+// waiting on one that has gone.  A barrier spins for a few microseconds
+// before it blocks: the exchanges of a measurement are short and frequent.
 #pragma once
 #include <stdint.h>
 #include <string.h>
 
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <limits>
@@ -26,32 +28,39 @@ class HostComm {
 
   void abort() {
     std::lock_guard<std::mutex> lk(m_);
-    aborted_ = true;
+    aborted_.store(true);
     cv_.notify_all();
   }
-  bool aborted() {
-    std::lock_guard<std::mutex> lk(m_);
-    return aborted_;
-  }
+  bool aborted() { return aborted_.load(); }
 
   // false when aborted (or when the wait outlasts the limit, which aborts)
   bool barrier() {
+    if (aborted_.load()) return false;
+    const uint64_t gen = gen_.load(std::memory_order_acquire);
+    if (arrived_.fetch_add(1, std::memory_order_acq_rel) + 1 == ranks_) {
+      arrived_.store(0, std::memory_order_relaxed);
+      {
+        std::lock_guard<std::mutex> lk(m_);
+        gen_.fetch_add(1, std::memory_order_release);
+      }
+      cv_.notify_all();
+      return !aborted_.load();
+    }
+    // spin a little (the other ranks are usually microseconds away), then block
+    const auto t0 = std::chrono::steady_clock::now();
+    while (std::chrono::steady_clock::now() - t0 < std::chrono::microseconds(50)) {
+      if (gen_.load(std::memory_order_acquire) != gen) return !aborted_.load();
+      if (aborted_.load()) return false;
+    }
     std::unique_lock<std::mutex> lk(m_);
-    if (aborted_) return false;
-    const uint64_t gen = gen_;
-    if (++arrived_ == ranks_) {
-      arrived_ = 0;
-      ++gen_;
-      cv_.notify_all();
-      return true;
-    }
-    const bool ok = cv_.wait_for(lk, std::chrono::duration<double>(limit_),
-                                 [&] { return gen_ != gen || aborted_; });
+    const bool ok = cv_.wait_for(lk, std::chrono::duration<double>(limit_), [&] {
+      return gen_.load(std::memory_order_acquire) != gen || aborted_.load();
+    });
     if (!ok) {
-      aborted_ = true;
+      aborted_.store(true);
       cv_.notify_all();
     }
-    return !aborted_;
+    return !aborted_.load();
   }
 
   // the minimum of every rank's v, returned to every rank
@@ -87,9 +96,9 @@ class HostComm {
   std::condition_variable cv_;
   const int ranks_;
   const double limit_;
-  int arrived_ = 0;
-  uint64_t gen_ = 0;
-  bool aborted_ = false;
+  std::atomic<int> arrived_{0};
+  std::atomic<uint64_t> gen_{0};
+  std::atomic<bool> aborted_{false};
   std::vector<int64_t> vals_;
   std::vector<const void*> srcs_;
 };
