@@ -842,6 +842,10 @@ def main():
         line = run_plain(args, ws, rank, local)
     if rank == 0:
         print(json.dumps(line), flush=True)
+        log = os.environ.get("TAB_BENCH_LOG")  # optional JSONL history of bench lines
+        if log:
+            with open(log, "a") as f:
+                f.write(json.dumps(dict(line, time=time.strftime("%Y-%m-%dT%H:%M:%S"))) + "\n")
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -21,6 +21,7 @@
 
 #include "sct.h"
 #include "tab_internal.h"
+#include "trace.h"
 
 using namespace tab;
 
@@ -321,6 +322,7 @@ int tab_batch_launches(tab_batch_t B, int64_t* count) {
 }
 
 int tab_batch_exec(tab_batch_t B, uint64_t seed, uint8_t* dev_out, void* cuda_stream) {
+  tab::TraceRange trace_("tab_batch_exec");
   if (!B) {
     set_error("null batch");
     return TAB_EINVAL;

@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "tab_internal.h"
+#include "trace.h"
 
 using namespace tab;
 
@@ -337,6 +338,7 @@ int tab_server_create(const tab_server_config* cfg, tab_server_t* out) {
 }
 
 int tab_server_submit(tab_server_t S, const tab_circuit* c, int64_t* ticket) {
+  tab::TraceRange trace_("tab_server_submit");
   if (!S || !c || !ticket) {
     set_error("null argument");
     return TAB_EINVAL;

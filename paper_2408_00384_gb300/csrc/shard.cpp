@@ -30,6 +30,7 @@
 
 #include "shard_comm.h"
 #include "tab_internal.h"
+#include "trace.h"
 
 namespace tab {
 
@@ -294,6 +295,7 @@ int tab_sharded_set_rng(tab_shard_t h, uint64_t seed, uint64_t circuit_id, uint3
 }
 
 int tab_sharded_apply(tab_shard_t h, const tab_gate* gates, int64_t count) {
+  tab::TraceRange trace_("tab_sharded_apply");
   if (!h) {
     set_error("null handle");
     return TAB_EINVAL;

@@ -20,6 +20,7 @@
 #include "pool.h"
 #include "sct.h"
 #include "tab_internal.h"
+#include "trace.h"
 
 namespace tab {
 const char* last_error();
@@ -983,6 +984,7 @@ int tab_lower_ops(int32_t n, const tab_gate* gates, int64_t count, uint64_t seed
 }
 
 int tab_apply(tab_t h, const tab_gate* gates, int64_t count) {
+  tab::TraceRange trace_("tab_apply");
   int rc = check_handle(h);
   if (rc) return rc;
   int64_t ext = 0;
@@ -1011,6 +1013,7 @@ int tab_apply(tab_t h, const tab_gate* gates, int64_t count) {
 }
 
 int tab_prog_create(int32_t n, const tab_gate* gates, int64_t count, tab_prog_t* out) {
+  tab::TraceRange trace_("tab_prog_create");
   if (!out) {
     set_error("null output pointer");
     return TAB_EINVAL;
@@ -1086,6 +1089,7 @@ int tab_prog_info(tab_prog_t p, int64_t* n_gates, int64_t* n_meas, int64_t* n_la
 }
 
 int tab_run(tab_t h, tab_prog_t p) {
+  tab::TraceRange trace_("tab_run");
   int rc = check_handle(h);
   if (rc) return rc;
   if (!p) {
@@ -1135,6 +1139,7 @@ static int measure_common(tab_t h, const int32_t* qubits, int32_t k, uint64_t se
 }
 
 int tab_measure(tab_t h, const int32_t* qubits, int32_t k, uint64_t seed, uint8_t* out_bits) {
+  tab::TraceRange trace_("tab_measure");
   if (k > 0 && !out_bits) {
     set_error("null output buffer");
     return TAB_EINVAL;
@@ -1147,6 +1152,7 @@ int tab_measure(tab_t h, const int32_t* qubits, int32_t k, uint64_t seed, uint8_
 }
 
 int tab_measure_async(tab_t h, const int32_t* qubits, int32_t k, uint8_t* dev_out_bits) {
+  tab::TraceRange trace_("tab_measure_async");
   if (k > 0 && !dev_out_bits) {
     set_error("null output buffer");
     return TAB_EINVAL;
@@ -1160,6 +1166,7 @@ int tab_measure_async(tab_t h, const int32_t* qubits, int32_t k, uint8_t* dev_ou
 }
 
 int tab_expect(tab_t h, const uint8_t* paulis, int32_t k, int8_t* out) {
+  tab::TraceRange trace_("tab_expect");
   int rc = check_handle(h);
   if (rc) return rc;
   if (k < 0 || (k > 0 && (!paulis || !out))) {
@@ -1194,6 +1201,7 @@ int tab_expect(tab_t h, const uint8_t* paulis, int32_t k, int8_t* out) {
 }
 
 int tab_statevector(tab_t h, float* amps, int64_t len) {
+  tab::TraceRange trace_("tab_statevector");
   int rc = check_handle(h);
   if (rc) return rc;
   const int n = h->n;
@@ -1251,6 +1259,7 @@ int tab_statevector(tab_t h, float* amps, int64_t len) {
 }
 
 int tab_read_outcomes(tab_t h, uint8_t* out, int64_t max, int64_t* count) {
+  tab::TraceRange trace_("tab_read_outcomes");
   int rc = check_handle(h);
   if (rc) return rc;
   if (count) *count = h->log_len;
