@@ -527,6 +527,43 @@ def test_create_on_torch_memory_and_stream():
         assert np.array_equal(g, w)
 
 
+def test_pipelined_apply_on_user_stream_and_stream_switch():
+    """Two pipelined applies, the first on a caller's stream and the second
+    after a switch to another stream: the copy stream and the staging areas
+    follow the stream order, and the result is the oracle's."""
+    torch = pytest.importorskip("torch")
+    c = C.random_layer_circuit(600, 300, seed=31)
+    half = c.gates.size // 2
+    assert half >= (1 << 17)
+    want_out, want = oracle_result(c.n, c.gates, 1, 0, 0)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    with tab.Tableau(c.n, stream=s1) as t:
+        t.set_engine(tab.ENGINE_GRID)
+        t.apply(c.gates[:half])
+        t.set_stream(s2)
+        t.apply(c.gates[half:])
+        out = t.read_outcomes()
+        got = t.export()
+    assert np.array_equal(out, want_out)
+    for g, w in zip(got, want):
+        assert np.array_equal(g, w)
+
+
+def test_next_step_calls_reject_bad_arguments():
+    with tab.Tableau(27) as t:
+        with pytest.raises(tab.TabError) as ei:
+            t.statevector()
+        assert ei.value.code == tab.TAB_ERANGE
+        assert t.expect(np.zeros((0, 27), np.uint8)).size == 0
+    with pytest.raises(tab.TabError) as ei:
+        tab.ShardedTableau(64, 3)  # 64 qubits hold two 32-row words
+    assert ei.value.code == tab.TAB_ERANGE
+    with tab.ShardedTableau(100, 2) as t:
+        with pytest.raises(tab.TabError) as ei:
+            t.apply(C.encode(C.TAB_MX, 3, 0).reshape(1))
+        assert ei.value.code == tab.TAB_EINVAL
+
+
 def test_compiled_program_replay():
     c = C.random_layer_circuit(180, 20, seed=9)
     want_out, want = oracle.run_circuit(c.n, c.gates, seed=4)
