@@ -205,3 +205,38 @@ def test_lowering_equals_op_by_op():
         runs = np.diff(np.concatenate([[0], m.astype(np.int8), [0]]))
         longest = (np.flatnonzero(runs == -1) - np.flatnonzero(runs == 1)).max()
         assert longest >= qs.size
+
+
+def test_expectation_after_measurements_vs_statevector():
+    """orc_expect on post-measurement states (MZ, MZR, MX, MY in the circuit),
+    every Pauli string against the projected state vector; a measured Pauli
+    has expectation (-1)^outcome right after its measurement."""
+    import itertools
+    for n in (2, 3, 4):
+        for s in range(3):
+            gates = C.random_extended_ops(n, 50, seed=900 * n + s, p_meas=0.2, p_noise=0.0)
+            t = oracle.Tableau(n)
+            out = t.run(gates, seed=s + 1, circuit_id=s)
+            sv = StateVector(n)
+            op, q1, q2 = C.decode(gates)
+            k = 0
+            for o, a, b in zip(op.tolist(), q1.tolist(), q2.tolist()):
+                if o in NAME1:
+                    sv.apply(NAME1[o], [a])
+                elif o in NAME2:
+                    sv.apply(NAME2[o], [a, b])
+                elif o in C.MEASURE_ANY:
+                    m = MAT1["Z"] if o in C.MEASURE else PAULI[o]
+                    project(sv, m, a, int(out[k]))
+                    if o == C.TAB_MZR and out[k]:
+                        sv.apply("X", [a])
+                    k += 1
+            for codes in itertools.product(range(4), repeat=n):
+                assert abs(sv_expect(sv, codes) - t.expect(codes)) < 1e-9, (n, s, codes)
+    # right after MX / MY on qubit 0, <X_0> / <Y_0> = (-1)^outcome
+    for kind, code in ((C.TAB_MX, 1), (C.TAB_MY, 3)):
+        g = np.concatenate([C.random_clifford_ops(3, 30, seed=kind),
+                            C.encode(kind, 0, 0).reshape(1)])
+        t = oracle.Tableau(3)
+        o = t.run(g, seed=2)
+        assert t.expect([code, 0, 0]) == (-1) ** int(o[-1])
