@@ -240,3 +240,33 @@ def test_expectation_after_measurements_vs_statevector():
         t = oracle.Tableau(3)
         o = t.run(g, seed=2)
         assert t.expect([code, 0, 0]) == (-1) ** int(o[-1])
+
+
+def test_noise_threshold_is_strict():
+    """The draw fires when (word 0 >> 4) < field: at field equal to the drawn
+    value it does not, one above it does (a boundary no rate test sees)."""
+    seed, cid, shot = 12345, 6, 2
+    w = oracle.philox4x32_10([0, shot, cid, 0], [seed & 0xFFFFFFFF, (seed >> 32) ^ 0x4E4F4953])
+    v = int(w[0]) >> 4
+    for field, fires in ((v, False), (v + 1, True)):
+        if field >= (1 << 28):
+            continue
+        g = C.encode(C.TAB_XERR, 0, field).reshape(1)
+        _, (x, z, r) = oracle.run_circuit(1, g, seed=seed, circuit_id=cid, shot=shot)
+        assert bool(r[1]) == fires, (field, v)
+
+
+def test_library_noise_threshold_matches():
+    """The library's host lowering (what tab_apply runs) takes the same strict
+    threshold: field == drawn value -> no Pauli, one above -> X."""
+    tab = pytest.importorskip("paper_2408_00384_gb300.tab")
+    seed, cid, shot = 12345, 6, 2
+    w = oracle.philox4x32_10([0, shot, cid, 0], [seed & 0xFFFFFFFF, (seed >> 32) ^ 0x4E4F4953])
+    v = int(w[0]) >> 4
+    for field, fires in ((v, False), (v + 1, True)):
+        if field >= (1 << 28):
+            continue
+        low, nk = tab.lower_ops(1, C.encode(C.TAB_XERR, 0, field).reshape(1), seed=seed,
+                                circuit_id=cid, shot=shot)
+        assert nk == 1
+        assert C.decode(low)[0].tolist() == ([C.TAB_X] if fires else [])
