@@ -158,3 +158,43 @@ def test_sampled_destabilizer_uniform(n, samples):
     expect = samples / cells
     stat = float((((counts[1:] - expect) ** 2) / expect).sum())
     assert chi2.sf(stat, cells - 1) > 1e-4, stat
+
+
+def _symplectic(n, gates):
+    """The linear part of a Clifford: row g = (x | z) bits of the image of
+    generator g (X_1..X_n, then Z_1..Z_n) -- the tableau the oracle leaves
+    after running the circuit on |0^n>."""
+    _, (x, z, _) = oracle.run_circuit(n, gates)
+    return np.concatenate([x, z], axis=1).astype(np.uint8)
+
+
+def test_bruhat_double_cosets_n3():
+    """At n = 3, for each of the 48 signed permutations w, the set
+    {b2 w b1 : b1, b2 in B} (linear parts, as products of the oracle's
+    matrices) has exactly |B| 2^len(w) elements, the sets are disjoint, and
+    together they are all |Sp(6, 2)| = 1,451,520 elements: the weights
+    2^len(w) the sampler draws are the double-coset sizes."""
+    n = 3
+    gates_of = lambda words: np.concatenate(words) if words else np.zeros(0, np.uint64)
+    MB = np.array([_symplectic(n, gates_of(b)) for b in borel_elements(n)])  # (512, 6, 6)
+    assert len({m.tobytes() for m in MB}) == 512
+    # row j of Q as a 6-bit integer, for every matrix Q
+    QB = (MB.astype(np.int64) << np.arange(2 * n)[None, None, :]).sum(axis=2)  # (512, 6)
+    seen = set()
+    total = 0
+    for code in all_codes(n):
+        w = C.signed_perm_from_code(code)
+        Mw = _symplectic(n, gates_of(C._weyl_words(w)))
+        P = (MB.astype(np.int64) @ Mw.astype(np.int64)) % 2  # b2 first, then w: (512, 6, 6)
+        # R[a, b] = P[a] . MB[b] over GF(2), rows packed as 6-bit integers
+        R = np.zeros((512, 512, 2 * n), np.int64)
+        for i in range(2 * n):
+            for j in range(2 * n):
+                R[:, :, i] ^= np.where(P[:, i, j][:, None] == 1, QB[None, :, j], 0)
+        keys = np.unique((R << (6 * np.arange(2 * n))[None, None, :]).sum(axis=2))
+        assert keys.size == 512 * 2 ** sum(code), (w, keys.size)
+        before = len(seen)
+        seen.update(keys.tolist())
+        assert len(seen) == before + keys.size  # disjoint from the other cosets
+        total += keys.size
+    assert total == 2 ** (n * n) * poincare(n) == 1451520
