@@ -198,3 +198,19 @@ def test_bruhat_double_cosets_n3():
         assert len(seen) == before + keys.size  # disjoint from the other cosets
         total += keys.size
     assert total == 2 ** (n * n) * poincare(n) == 1451520
+
+
+def test_sampled_one_qubit_cliffords_uniform_with_signs():
+    """random_clifford itself (with its Pauli layer) at n = 1: the 24
+    Cliffords, signs included, are drawn uniformly (chi-square, fixed seeds)."""
+    chi2 = pytest.importorskip("scipy.stats").chi2
+    counts = {}
+    samples = 2400
+    for c in range(samples):
+        circ = C.random_clifford(1, C.splitmix64(77000 + c))
+        key = tableau(1, circ.gates)
+        counts[key] = counts.get(key, 0) + 1
+    assert len(counts) == 24
+    expect = samples / 24
+    stat = sum((v - expect) ** 2 / expect for v in counts.values())
+    assert chi2.sf(stat, 23) > 1e-4, stat
