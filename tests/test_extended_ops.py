@@ -270,3 +270,27 @@ def test_library_noise_threshold_matches():
                                 circuit_id=cid, shot=shot)
         assert nk == 1
         assert C.decode(low)[0].tolist() == ([C.TAB_X] if fires else [])
+
+
+def test_host_validation_through_lowering():
+    """The host validator every entry point runs first (exercised on the CPU
+    through tab_lower_ops): out-of-range qubits, a two-qubit op on one qubit
+    and unknown ops are refused with the documented codes; barriers carry no
+    qubits to check."""
+    tab = pytest.importorskip("paper_2408_00384_gb300.tab")
+    n = 5
+    ok = np.concatenate([C.encode([C.TAB_H, C.TAB_CNOT, C.TAB_BARRIER, C.TAB_MX],
+                                  [0, 1, (1 << 28) - 1, 4], [0, 4, 7, 0])])
+    low, _ = tab.lower_ops(n, ok)
+    assert low.size >= 3
+    cases = [(C.encode(C.TAB_H, n, 0), tab.TAB_ERANGE),
+             (C.encode(C.TAB_CZ, 1, n), tab.TAB_ERANGE),
+             (C.encode(C.TAB_SWAP, 2, 2), tab.TAB_EINVAL),
+             (C.encode(18, 0, 0), tab.TAB_EINVAL),
+             (C.encode(C.TAB_MY, n + 3, 0), tab.TAB_ERANGE),
+             (C.encode(C.TAB_DEPOL1, n, 5), tab.TAB_ERANGE)]
+    for word, code in cases:
+        g = np.concatenate([ok, np.asarray(word, np.uint64).reshape(1), ok])
+        with pytest.raises(tab.TabError) as ei:
+            tab.lower_ops(n, g)
+        assert ei.value.code == code, (word, ei.value.code)
