@@ -146,5 +146,57 @@ int main() {
     printf("layer circuit: %zu gates -> %zu blocks, %zu super-layers\n", g.size(), hp.blk.size(), hp.blk_off.size() - 1);
     if (hp.blk_off.size() - 1 != 50 || hp.blk.size() != 25000) ++bad;
   }
+  // the pipelined apply's host side: chunks compiled apart (build_validated_
+  // blocks), groups of consecutive chunks merged without their records
+  // (concat_programs with_blk = false) while the records are concatenated on
+  // their own, and adjacent gate runs taken as one run over the shared bound
+  // (an empty super-layer) -- the result must equal the gates one at a time
+  {
+    const int n = 200, ng = 300000;
+    std::vector<tab_gate> g;
+    for (int i = 0; i < ng; ++i) {
+      uint32_t op = 1 + (uint32_t)(rng() % 9);
+      uint32_t a = (uint32_t)(rng() % n), b = (uint32_t)(rng() % n);
+      if (op >= TAB_CNOT) while (b == a) b = (uint32_t)(rng() % n);
+      g.push_back(tab_make_gate(op, a, op >= TAB_CNOT ? b : 0));
+    }
+    std::vector<int64_t> bnd{0};
+    for (int64_t s = 1 << 12; bnd.back() < ng; s = std::min<int64_t>(1 << 15, s * 2))
+      bnd.push_back(std::min<int64_t>(ng, bnd.back() + s));
+    const int nc = (int)bnd.size() - 1;
+    std::vector<HostProgram> parts((size_t)nc);
+    for (int c = 0; c < nc; ++c)
+      if (build_validated_blocks(n, g.data() + bnd[c], bnd[c + 1] - bnd[c], &parts[(size_t)c]) != TAB_OK)
+        return 1;
+    std::vector<uint32_t> X(n), Z(n);
+    for (int a = 0; a < n; ++a) { X[a] = (uint32_t)rng(); Z[a] = (uint32_t)rng(); }
+    uint32_t r = (uint32_t)rng(), r2 = r;
+    std::vector<uint32_t> X2 = X, Z2 = Z;
+    for (auto w : g) gate((uint32_t)(w >> 56), (uint32_t)((w >> 28) & 0xFFFFFFF), (uint32_t)(w & 0xFFFFFFF), X, Z, r);
+    int launches = 0;
+    for (int i = 0; i < nc;) {
+      const int j = std::min(nc, i + 1 + (int)(rng() % 5));  // merge 1..5 chunks
+      HostProgram M;
+      concat_programs(M, &parts[(size_t)i], (size_t)(j - i), false);
+      std::vector<uint2> rec;
+      for (int c = i; c < j; ++c) rec.insert(rec.end(), parts[(size_t)c].blk.begin(), parts[(size_t)c].blk.end());
+      if (!M.blk.empty()) ++bad;
+      for (size_t si = 0; si < M.segs.size(); ++si) {
+        if (M.segs[si].kind != 0) continue;
+        size_t sj = si;
+        while (sj + 1 < M.segs.size() && M.segs[sj + 1].kind == 0 &&
+               M.segs[sj + 1].blk_begin == M.segs[sj].blk_end + 1)
+          ++sj;
+        ++launches;
+        for (uint32_t L = M.segs[si].blk_begin; L < M.segs[sj].blk_end; ++L)
+          for (uint32_t k = M.blk_off[L]; k < M.blk_off[L + 1]; ++k) blockh(rec[k], X2, Z2, r2);
+        si = sj;
+      }
+      i = j;
+    }
+    const bool ok = X == X2 && Z == Z2 && r == r2;
+    printf("pipelined merge: %d chunks, %d launches, %s\n", nc, launches, ok ? "equal" : "MISMATCH");
+    if (!ok) ++bad;
+  }
   return bad != 0;
 }
