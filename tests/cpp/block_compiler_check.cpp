@@ -3,7 +3,9 @@
 // random 32-row words with the block formulas of the device kernel, and the
 // result must equal the gates applied one at a time with the Aaronson &
 // Gottesman rules (PRA 70, 052328, Sec. III).  Each super-layer must act on
-// pairwise-disjoint qubits.  Exit status 0 on success.
+// pairwise-disjoint qubits.  The pipelined apply's host side (chunks
+// compiled apart, merged without their records, adjacent gate runs taken as
+// one) must give the same result.  Exit status 0 on success.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
