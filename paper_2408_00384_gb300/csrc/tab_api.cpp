@@ -940,8 +940,10 @@ static int lower_ops(int32_t n, const tab_gate* g, int64_t count, uint64_t seed,
                                   make_uint2((uint32_t)seed, (uint32_t)(seed >> 32) ^ kNoiseKeyTag));
     if ((r.x >> 4) < (uint32_t)(g[i] & 0xFFFFFFFull)) {
       static const uint32_t kDepol[3] = {TAB_X, TAB_Y, TAB_Z};
-      put(op == TAB_XERR ? TAB_X : op == TAB_ZERR ? TAB_Z : kDepol[((uint64_t)r.y * 3u) >> 32],
-          q1_of(i));
+      const uint32_t pauli = op == TAB_XERR   ? (uint32_t)TAB_X
+                             : op == TAB_ZERR ? (uint32_t)TAB_Z
+                                              : kDepol[((uint64_t)r.y * 3u) >> 32];
+      put(pauli, q1_of(i));
     }
     span = i + 1;
   }
