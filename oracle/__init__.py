@@ -58,6 +58,10 @@ def lib():
         L.orc_expect.restype = i32
         L.orc_expect.argtypes = [vp, vp]
         L.orc_set.argtypes = [vp, vp, vp, vp]
+        L.orc_set_threads.restype = i32
+        L.orc_set_threads.argtypes = [vp, i32]
+        L.orc_threads.restype = i32
+        L.orc_threads.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -84,15 +88,38 @@ def g(x1, z1, x2, z2) -> int:
     return int(lib().orc_g(x1, z1, x2, z2))
 
 
-class Tableau:
-    """Unpacked AG tableau: rows 0..n-1 destabilizers, n..2n-1 stabilizers."""
+def all_cores() -> int:
+    """Cores this process may run on (its affinity mask)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
 
-    def __init__(self, n: int):
+
+class Tableau:
+    """Unpacked AG tableau: rows 0..n-1 destabilizers, n..2n-1 stabilizers.
+
+    ``threads`` > 1 splits each gate's loop over rows, and the target rows of a
+    random-outcome measurement's rowsums, into contiguous shares on that many
+    threads (results are identical to one thread)."""
+
+    def __init__(self, n: int, threads: int = 1):
         self.n = int(n)
         self._h = lib().orc_new(self.n)
         if not self._h:
             raise MemoryError("orc_new failed")
         self.meas_counter = 0
+        if threads != 1:
+            self.set_threads(threads)
+
+    def set_threads(self, threads: int):
+        rc = lib().orc_set_threads(self._h, int(threads))
+        if rc != ORC_OK:
+            raise RuntimeError(f"orc_set_threads error {rc}")
+
+    @property
+    def threads(self) -> int:
+        return int(lib().orc_threads(self._h))
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -170,8 +197,9 @@ class Tableau:
         lib().orc_set(self._h, x.ctypes.data, z.ctypes.data, r.ctypes.data)
 
 
-def run_circuit(n: int, gates, seed: int = 1, circuit_id: int = 0, shot: int = 0):
+def run_circuit(n: int, gates, seed: int = 1, circuit_id: int = 0, shot: int = 0,
+                threads: int = 1):
     """Fresh |0^n>, run gates; returns (outcomes, (x, z, r))."""
-    t = Tableau(n)
+    t = Tableau(n, threads=threads)
     out = t.run(gates, seed=seed, circuit_id=circuit_id, shot=shot)
     return out, t.get()

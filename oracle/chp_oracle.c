@@ -43,10 +43,21 @@
  *    right by 4 is below the 28-bit probability field, and DEPOL1 then takes
  *    X, Y or Z by floor(word 1 * 3 / 2^32).
  *
+ * Threads (orc_set_threads): AG's gate rules update every row from that
+ * row's own bits, and the rowsums of a random-outcome measurement each write
+ * a different target row while reading only the pivot row.  Those two loops
+ * over rows may therefore be split into contiguous shares, one per thread,
+ * with results identical to the one-thread run; nothing else is reordered.
+ * The one-thread mode is the default.
+ *
  * Parity pins: gate rules and g against explicit Pauli matrices; the whole
  * simulator against brute-force state vectors (n <= 10), known states and the
- * symplectic invariant; Philox against the Random123 known-answer vectors.
+ * symplectic invariant; Philox against the Random123 known-answer vectors;
+ * every thread count against the one-thread run.
  */
+#include <pthread.h>
+#include <sched.h>
+#include <stdatomic.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -57,16 +68,146 @@
 #define ORC_ENOMEM (-3)
 #define ORC_EPHASE (-8) /* rowsum met an odd exponent: not a commuting product */
 
+typedef struct orc_pool orc_pool;
+
 typedef struct {
   int32_t n;
   int64_t rows; /* 2n + 1: the last row is AG's scratch row */
   uint8_t *x, *z, *r;
   uint64_t noise_counter; /* next noise-op index */
+  orc_pool *pool;         /* worker threads, or NULL for one thread */
 } orc_tab;
 
 /* storage: element (row i, qubit j) at [j * rows + i] */
 #define XB(t, i, j) ((t)->x[(int64_t)(j) * (t)->rows + (i)])
 #define ZB(t, i, j) ((t)->z[(int64_t)(j) * (t)->rows + (i)])
+
+/* ---- worker threads over a range of rows --------------------------------
+ * A job is a function applied to rows [lo, hi).  With T threads, thread i
+ * (the caller is thread 0) takes rows [R*i/T, R*(i+1)/T) of the R rows, and
+ * the caller returns once every share is done. */
+typedef void (*orc_rows_fn)(orc_tab *t, void *arg, int64_t lo, int64_t hi);
+
+struct orc_pool {
+  int32_t threads;
+  pthread_t *tid;
+  pthread_mutex_t mu;
+  pthread_cond_t cv;
+  atomic_uint_fast64_t gen; /* bumped once per job */
+  atomic_int done;          /* workers finished with the current job */
+  int quit;
+  orc_rows_fn fn;
+  orc_tab *t;
+  void *arg;
+  int64_t nrows;
+};
+
+typedef struct { orc_pool *p; int32_t index; } orc_worker_arg;
+
+static void share_of(int64_t nrows, int32_t threads, int32_t i, int64_t *lo, int64_t *hi) {
+  *lo = nrows * i / threads;
+  *hi = nrows * (i + 1) / threads;
+}
+
+static void *orc_worker(void *varg) {
+  orc_worker_arg *wa = (orc_worker_arg *)varg;
+  orc_pool *p = wa->p;
+  int32_t index = wa->index;
+  free(wa);
+  uint_fast64_t seen = 0;
+  for (;;) {
+    uint_fast64_t g;
+    long spins = 0;
+    /* spin briefly (jobs come back to back inside a run), then sleep */
+    while ((g = atomic_load_explicit(&p->gen, memory_order_acquire)) == seen) {
+      if (++spins < (1L << 16)) continue;
+      if (spins < (1L << 18)) { sched_yield(); continue; }
+      pthread_mutex_lock(&p->mu);
+      while ((g = atomic_load_explicit(&p->gen, memory_order_acquire)) == seen)
+        pthread_cond_wait(&p->cv, &p->mu);
+      pthread_mutex_unlock(&p->mu);
+      break;
+    }
+    seen = g;
+    if (p->quit) return NULL;
+    int64_t lo, hi;
+    share_of(p->nrows, p->threads, index, &lo, &hi);
+    if (lo < hi) p->fn(p->t, p->arg, lo, hi);
+    atomic_fetch_add_explicit(&p->done, 1, memory_order_acq_rel);
+  }
+}
+
+static void pool_stop(orc_pool *p, int32_t started) {
+  pthread_mutex_lock(&p->mu);
+  p->quit = 1;
+  atomic_fetch_add_explicit(&p->gen, 1, memory_order_release);
+  pthread_cond_broadcast(&p->cv);
+  pthread_mutex_unlock(&p->mu);
+  for (int32_t i = 0; i < started; i++) pthread_join(p->tid[i], NULL);
+  pthread_cond_destroy(&p->cv);
+  pthread_mutex_destroy(&p->mu);
+  free(p->tid);
+  free(p);
+}
+
+/* Run fn over rows [0, nrows) on the tableau's threads. */
+static void for_rows(orc_tab *t, orc_rows_fn fn, void *arg, int64_t nrows) {
+  orc_pool *p = t->pool;
+  if (!p) {
+    fn(t, arg, 0, nrows);
+    return;
+  }
+  p->fn = fn;
+  p->t = t;
+  p->arg = arg;
+  p->nrows = nrows;
+  atomic_store_explicit(&p->done, 0, memory_order_relaxed);
+  pthread_mutex_lock(&p->mu);
+  atomic_fetch_add_explicit(&p->gen, 1, memory_order_release);
+  pthread_cond_broadcast(&p->cv);
+  pthread_mutex_unlock(&p->mu);
+  int64_t lo, hi;
+  share_of(nrows, p->threads, 0, &lo, &hi);
+  if (lo < hi) fn(t, arg, lo, hi);
+  long spins = 0;
+  while (atomic_load_explicit(&p->done, memory_order_acquire) != p->threads - 1)
+    if (++spins > (1L << 12)) sched_yield();
+}
+
+/* Use `threads` threads (>= 1) for this tableau's row loops. */
+int32_t orc_set_threads(orc_tab *t, int32_t threads) {
+  if (threads < 1) return ORC_EINVAL;
+  if (t->pool) {
+    pool_stop(t->pool, t->pool->threads - 1);
+    t->pool = NULL;
+  }
+  if (threads == 1) return ORC_OK;
+  orc_pool *p = (orc_pool *)calloc(1, sizeof(orc_pool));
+  if (!p) return ORC_ENOMEM;
+  p->threads = threads;
+  p->tid = (pthread_t *)calloc((size_t)threads, sizeof(pthread_t));
+  if (!p->tid) { free(p); return ORC_ENOMEM; }
+  pthread_mutex_init(&p->mu, NULL);
+  pthread_cond_init(&p->cv, NULL);
+  atomic_init(&p->gen, 0);
+  atomic_init(&p->done, 0);
+  for (int32_t i = 1; i < threads; i++) {
+    orc_worker_arg *wa = (orc_worker_arg *)malloc(sizeof(orc_worker_arg));
+    if (wa) {
+      wa->p = p;
+      wa->index = i;
+    }
+    if (!wa || pthread_create(&p->tid[i - 1], NULL, orc_worker, wa) != 0) {
+      free(wa);
+      pool_stop(p, i - 1);
+      return ORC_ENOMEM;
+    }
+  }
+  t->pool = p;
+  return ORC_OK;
+}
+
+int32_t orc_threads(const orc_tab *t) { return t->pool ? t->pool->threads : 1; }
 
 void orc_reset(orc_tab *t) {
   int64_t cells = (int64_t)t->n * t->rows;
@@ -101,15 +242,19 @@ orc_tab *orc_new(int32_t n) {
 
 void orc_free(orc_tab *t) {
   if (!t) return;
+  if (t->pool) pool_stop(t->pool, t->pool->threads - 1);
   free(t->x); free(t->z); free(t->r); free(t);
 }
 
 int32_t orc_n(const orc_tab *t) { return t->n; }
 
-/* ---- AG's three gate rules, for every row i in [0, 2n) ---------------- */
+/* ---- AG's three gate rules, for every row i in [0, 2n) ----------------
+ * Each rule is written for a range of rows; the public function runs it over
+ * all 2n rows (split over the tableau's threads, if it has any). */
 
-void orc_cnot(orc_tab *t, int32_t a, int32_t b) {
-  for (int64_t i = 0; i < 2 * (int64_t)t->n; i++) {
+static void cnot_rows(orc_tab *t, void *arg, int64_t lo, int64_t hi) {
+  const int32_t a = ((const int32_t *)arg)[0], b = ((const int32_t *)arg)[1];
+  for (int64_t i = lo; i < hi; i++) {
     uint8_t xa = XB(t, i, a), za = ZB(t, i, a), xb = XB(t, i, b), zb = ZB(t, i, b);
     t->r[i] ^= (uint8_t)(xa & zb & (xb ^ za ^ 1));
     XB(t, i, b) = (uint8_t)(xb ^ xa);
@@ -117,8 +262,9 @@ void orc_cnot(orc_tab *t, int32_t a, int32_t b) {
   }
 }
 
-void orc_h(orc_tab *t, int32_t a) {
-  for (int64_t i = 0; i < 2 * (int64_t)t->n; i++) {
+static void h_rows(orc_tab *t, void *arg, int64_t lo, int64_t hi) {
+  const int32_t a = *(const int32_t *)arg;
+  for (int64_t i = lo; i < hi; i++) {
     uint8_t xa = XB(t, i, a), za = ZB(t, i, a);
     t->r[i] ^= (uint8_t)(xa & za);
     XB(t, i, a) = za;
@@ -126,13 +272,23 @@ void orc_h(orc_tab *t, int32_t a) {
   }
 }
 
-void orc_s(orc_tab *t, int32_t a) {
-  for (int64_t i = 0; i < 2 * (int64_t)t->n; i++) {
+static void s_rows(orc_tab *t, void *arg, int64_t lo, int64_t hi) {
+  const int32_t a = *(const int32_t *)arg;
+  for (int64_t i = lo; i < hi; i++) {
     uint8_t xa = XB(t, i, a), za = ZB(t, i, a);
     t->r[i] ^= (uint8_t)(xa & za);
     ZB(t, i, a) = (uint8_t)(za ^ xa);
   }
 }
+
+void orc_cnot(orc_tab *t, int32_t a, int32_t b) {
+  int32_t ab[2] = {a, b};
+  for_rows(t, cnot_rows, ab, 2 * (int64_t)t->n);
+}
+
+void orc_h(orc_tab *t, int32_t a) { for_rows(t, h_rows, &a, 2 * (int64_t)t->n); }
+
+void orc_s(orc_tab *t, int32_t a) { for_rows(t, s_rows, &a, 2 * (int64_t)t->n); }
 
 /* ---- gates built from the three rules --------------------------------- */
 
@@ -205,6 +361,28 @@ int32_t orc_outcome_bit(uint64_t seed, uint64_t circuit_id, uint32_t shot, uint6
 
 /* ---- measurement (AG Sec. III) ----------------------------------------- */
 
+/* Case 1's rowsums: every row i != p, p-n with x_ia = 1 takes rowsum(i, p).
+ * Each writes only row i and reads row p, which none of them writes. */
+typedef struct {
+  int64_t p;
+  int32_t a;
+  atomic_int rc; /* the first error seen by any share */
+} random_case_job;
+
+static void random_case_rows(orc_tab *t, void *arg, int64_t lo, int64_t hi) {
+  random_case_job *job = (random_case_job *)arg;
+  const int64_t p = job->p, n = t->n;
+  for (int64_t i = lo; i < hi; i++) {
+    if (i == p || i == p - n || !XB(t, i, job->a)) continue;
+    int32_t rc = orc_rowsum(t, i, p);
+    if (rc != ORC_OK) {
+      int expected = ORC_OK;
+      atomic_compare_exchange_strong(&job->rc, &expected, rc);
+      return;
+    }
+  }
+}
+
 /* Measure Z_a with the pre-drawn bit `rbit` for the random case.  Returns the
  * outcome (0/1) or a negative error; *deterministic is set to 1 or 0. */
 int32_t orc_measure(orc_tab *t, int32_t a, int32_t rbit, int32_t *deterministic) {
@@ -215,11 +393,9 @@ int32_t orc_measure(orc_tab *t, int32_t a, int32_t rbit, int32_t *deterministic)
     if (XB(t, i, a)) { p = i; break; }
   if (p >= 0) {
     /* case 1: random outcome */
-    for (int64_t i = 0; i < 2 * n; i++) {
-      if (i == p || i == p - n || !XB(t, i, a)) continue;
-      int32_t rc = orc_rowsum(t, i, p);
-      if (rc != ORC_OK) return rc;
-    }
+    random_case_job job = {p, a, ORC_OK};
+    for_rows(t, random_case_rows, &job, 2 * n);
+    if (job.rc != ORC_OK) return job.rc;
     for (int32_t j = 0; j < t->n; j++) {
       XB(t, p - n, j) = XB(t, p, j);
       ZB(t, p - n, j) = ZB(t, p, j);
