@@ -355,16 +355,12 @@ int resident_ctas_for(int n, int Wh, int sm_count) {
     pref = 0;
     if (const char* e = getenv("TAB_GRID_CTAS")) pref = atoi(e);
   }
-  static int attr = -1;
-  if (attr < 0) {
-    attr = 1;
-    for (int wl = 2; wl <= 16; wl *= 2)
-      if (cudaFuncSetAttribute(resident_kernel(wl), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               res_dyn_limit()) != cudaSuccess)
-        attr = 0;
+  const int wl = res_words_per_lane(Wh);
+  if (wl == 0) return 0;
+  if (ensure_smem_limit(resident_kernel(wl), res_dyn_limit()) != cudaSuccess) {
     cudaGetLastError();
+    return 0;
   }
-  if (attr == 0 || res_words_per_lane(Wh) == 0) return 0;
   if (pref >= 2 && pref <= sm_count &&
       res_batch_for(n, Wh, pref, res_dyn_limit(), kBatchMax, false) >= 4)
     return pref;

@@ -110,14 +110,9 @@ cudaError_t launch_expect(const uint32_t* X, const uint32_t* Z, const uint32_t* 
                           const uint8_t* codes, int k, int8_t* out, int* err, cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
   const size_t smem = expect_smem_bytes(n);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_expect<kExpectThreads>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)expect_smem_bytes(TAB_MAX_QUBITS));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  cudaError_t e = ensure_smem_limit((const void*)k_expect<kExpectThreads>,
+                                    (int)expect_smem_bytes(TAB_MAX_QUBITS));
+  if (e != cudaSuccess) return e;
   k_expect<kExpectThreads><<<k, kExpectThreads, smem, s>>>(X, Z, R, n, Wh, codes, out, err);
   return cudaGetLastError();
 }

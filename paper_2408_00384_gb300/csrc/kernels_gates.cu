@@ -591,9 +591,9 @@ static cudaError_t launch_gates_block_t(uint32_t* X, uint32_t* Z, uint32_t* R, i
                                         const uint2* blk, const uint32_t* blk_off, int nlayers,
                                         int* err, cudaStream_t s) {
   const size_t smem = (size_t)SLOTS * kBlkChunk * 8 + (size_t)n * 2 * sizeof(uint32_t);
-  // set once per instance; shard threads may launch concurrently
-  static const cudaError_t attr = cudaFuncSetAttribute(
-      k_gates_block<T, SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemBytes - 4096);
+  // once per device; shard threads may launch concurrently
+  const cudaError_t attr =
+      ensure_smem_limit((const void*)k_gates_block<T, SLOTS>, kMaxSmemBytes - 4096);
   if (attr != cudaSuccess) return attr;
   k_gates_block<T, SLOTS><<<W, T, smem, s>>>(X, Z, R, n, W, blk, blk_off, nlayers, err);
   return cudaGetLastError();

@@ -433,14 +433,9 @@ cudaError_t launch_measure(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh,
   A.out = out;
   A.ph = mw.ph; A.r4 = mw.r4; A.dp = mw.dp; A.bar = mw.bar; A.err = mw.err;
   const size_t smem = meas_smem_bytes(n, A.W, ctas);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_measure, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         200 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  cudaError_t e = cudaMemsetAsync(mw.bar, 0, sizeof(GridBar), s);
+  cudaError_t e = ensure_smem_limit((const void*)k_measure, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(mw.bar, 0, sizeof(GridBar), s);
   if (e != cudaSuccess) return e;
   void* args[] = {&A};
   return cudaLaunchCooperativeKernel((const void*)k_measure, dim3(ctas), dim3(kMeasThreads), args,

@@ -498,13 +498,9 @@ __global__ void __launch_bounds__(kSctThreads) k_sct_program(SctProgArgs A) {
 }
 
 cudaError_t launch_sct_program(const SctProgArgs& A, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_sct_program, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sct_smem_bytes(TAB_BATCH_MAX_QUBITS, kSctThreads));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = ensure_smem_limit((const void*)k_sct_program,
+                                    (int)sct_smem_bytes(TAB_BATCH_MAX_QUBITS, kSctThreads));
+  if (e != cudaSuccess) return e;
   k_sct_program<<<1, kSctThreads, sct_smem_bytes(A.n, kSctThreads), st>>>(A);
   return cudaGetLastError();
 }

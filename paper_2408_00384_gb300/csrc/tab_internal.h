@@ -211,6 +211,10 @@ cudaError_t launch_unpack(const uint32_t* X, const uint32_t* Z, const uint32_t* 
 // thread-local error message
 void set_error(const char* fmt, ...);
 
+// Raise fn's dynamic shared-memory limit to `bytes` on the current device,
+// once per (kernel, device, limit).  Thread-safe; never allocates.
+cudaError_t ensure_smem_limit(const void* fn, int bytes);
+
 // Read-only view of a handle for entry points outside tab_api.cpp.
 struct HandleView {
   int n, Wh, dev;
