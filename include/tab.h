@@ -240,7 +240,9 @@ int tab_measure_async(tab_t h, const int32_t *qubits, int32_t k, uint8_t *dev_ou
  * outcome-stream counter, which advances by k), writing outcome i as one byte
  * to dev_out_bits[i] (caller-owned device memory, >= k bytes).  The outcomes
  * are not added to the handle's outcome log.  Asynchronous on the handle's
- * stream; device errors surface at the next synchronizing call.
+ * stream; device errors surface at the next synchronizing call.  The host
+ * qubit list is read only during the call: the qubit codes travel to the
+ * device as kernel parameters, with no host buffer and no host-to-device copy.
  *
  * Scratch: a file-scope device array of TAB_NOALLOC_SCRATCH_BYTES (1 MiB) per
  * device, held by every process that loads the library until it exits.  A

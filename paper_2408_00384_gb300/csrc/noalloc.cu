@@ -9,7 +9,9 @@
 // signs, deterministic partials, grid-barrier word, error word) live in one
 // file-scope __device__ array of fixed size, so the call allocates nothing;
 // the caller brings the tableau (e.g. from tab_create_on) and the device
-// buffer for the outcomes.
+// buffer for the outcomes.  The qubit codes reach the array as kernel
+// parameters of small staging launches (copied when each launch is issued),
+// so the call keeps no host buffer and issues no host-to-device copy.
 //
 // The array is one per device per process and keeps what the last call left
 // in it: the barrier and error words are cleared at every call, the rest is
@@ -20,7 +22,6 @@
 
 #include <algorithm>
 #include <mutex>
-#include <vector>
 
 #include "tab_internal.h"
 
@@ -32,13 +33,18 @@ static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
 
 // Host-side device addresses of g_noalloc_scratch, one per device.  In host
 // code the symbol itself is only a host stand-in, never a device address.
+constexpr int kNoAllocMaxDevices = 128;
 static std::mutex g_addr_mu;
-static std::vector<uint32_t*> g_addr;
+static uint32_t* g_addr[kNoAllocMaxDevices];
 
 static int scratch_address(int dev, uint32_t** out) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) {
+    set_error("device %d is beyond the %d devices the measurement scratch table holds", dev,
+              kNoAllocMaxDevices);
+    return TAB_EINVAL;
+  }
   std::lock_guard<std::mutex> lk(g_addr_mu);
-  if ((int)g_addr.size() <= dev) g_addr.resize((size_t)dev + 1, nullptr);
-  if (!g_addr[(size_t)dev]) {
+  if (!g_addr[dev]) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr) {
@@ -46,10 +52,21 @@ static int scratch_address(int dev, uint32_t** out) {
                 cudaGetErrorString(e));
       return TAB_ECUDA;
     }
-    g_addr[(size_t)dev] = static_cast<uint32_t*>(p);
+    g_addr[dev] = static_cast<uint32_t*>(p);
   }
-  *out = g_addr[(size_t)dev];
+  *out = g_addr[dev];
   return TAB_OK;
+}
+
+// Qubit codes per staging launch: 3,840 bytes of parameters, inside the
+// 4 KB kernel-parameter limit.
+constexpr int kNoAllocStage = 960;
+struct StageCodes {
+  uint32_t code[kNoAllocStage];
+};
+
+__global__ void k_noalloc_stage(const StageCodes c, int count, uint32_t* __restrict__ dst) {
+  for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = c.code[i];
 }
 
 // Copy a latched device error into the handle's error word (keeps the first).
@@ -78,13 +95,11 @@ extern "C" int tab_measure_noalloc(tab_t h, const int32_t* qubits, int32_t k, in
     return TAB_EINVAL;
   }
   const uint32_t op = reset ? OP_MZR : OP_MZ;
-  std::vector<uint32_t> codes((size_t)k);
   for (int32_t i = 0; i < k; ++i) {
     if (qubits[i] < 0 || qubits[i] >= v.n) {
       set_error("qubit %d outside [0, %d)", qubits[i], v.n);
       return TAB_ERANGE;
     }
-    codes[(size_t)i] = dcode(op, (uint32_t)qubits[i], 0);
   }
   // layout in the array: [codes | ph | r4 | dp | barrier | error]
   const size_t code_words = ((size_t)k + 63) & ~(size_t)63;
@@ -111,8 +126,14 @@ extern "C" int tab_measure_noalloc(tab_t h, const int32_t* qubits, int32_t k, in
   w += 16;
   mw.err = reinterpret_cast<int*>(w);
   mw.max_ctas = G;
-  cudaError_t e = cudaMemcpyAsync(base, codes.data(), (size_t)k * sizeof(uint32_t),
-                                  cudaMemcpyHostToDevice, v.stream);
+  cudaError_t e = cudaSuccess;
+  for (int32_t i0 = 0; i0 < k && e == cudaSuccess; i0 += kNoAllocStage) {
+    const int cnt = std::min(kNoAllocStage, k - i0);
+    StageCodes sc;
+    for (int i = 0; i < cnt; ++i) sc.code[i] = dcode(op, (uint32_t)qubits[i0 + i], 0);
+    k_noalloc_stage<<<1, 256, 0, v.stream>>>(sc, cnt, base + i0);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(w, 0, sizeof(int), v.stream);  // error word
   if (e == cudaSuccess)
     e = launch_measure(v.X, v.Z, v.R, v.n, v.Wh, base, k, v.k, v.seed, v.cid, v.shot, dev_out_bits,
