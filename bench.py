@@ -64,7 +64,7 @@ def parse():
     p.add_argument("--requests", type=int, default=48, help="served: number of requests")
     p.add_argument("--circuits", type=int, default=4096, help="batched: number of circuits")
     p.add_argument("--engine", default="auto",
-                   choices=["auto", "single", "cluster", "grid", "stream"])
+                   choices=["auto", "single", "grid", "stream"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -271,7 +271,7 @@ def run_plain(args, ws, rank, local):
     runs = split_runs(c)
     stream = torch.cuda.Stream()
     t = tab.Tableau(c.n, stream=stream)
-    eng = {"auto": tab.ENGINE_AUTO, "single": tab.ENGINE_SINGLE_CTA, "cluster": tab.ENGINE_CLUSTER,
+    eng = {"auto": tab.ENGINE_AUTO, "single": tab.ENGINE_SINGLE_CTA,
            "grid": tab.ENGINE_GRID, "stream": tab.ENGINE_STREAM}
     t.set_engine(eng[args.engine])
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -368,7 +368,7 @@ def run_plain(args, ws, rank, local):
         # random state); per such column and word: x ^= S, z ^= S (as row p
         # has X / Z there) and the mod-4 exponent update, 6 logic ops
         alg = 6.0 * 0.75 * n * words * c.n_meas
-        kname = {tab.ENGINE_SINGLE_CTA: "k_sct_program", tab.ENGINE_CLUSTER: "k_measure_cluster",
+        kname = {tab.ENGINE_SINGLE_CTA: "k_sct_program",
                  tab.ENGINE_GRID: "k_measure_resident",
                  tab.ENGINE_STREAM: "k_measure"}[eng_res]
     else:
@@ -415,7 +415,7 @@ def run_plain(args, ws, rank, local):
                    "measurements": c.n_meas, "parallelism": f"replicas x{ws}",
                    "l2": "flushed before every timed step (256 MB device write)",
                    "engine": args.engine,
-                   "measure_engine": {tab.ENGINE_SINGLE_CTA: "single-CTA", tab.ENGINE_CLUSTER: "cluster",
+                   "measure_engine": {tab.ENGINE_SINGLE_CTA: "single-CTA",
                                       tab.ENGINE_GRID: "grid-resident",
                                       tab.ENGINE_STREAM: "streaming"}[t.engine_resolved()[0]]},
         "gpu_launches": int(launches),

@@ -268,26 +268,23 @@ int tab_clear_outcomes(tab_t h);
 /* Execution engine for tab_apply / tab_run / tab_measure on this handle.
  * TAB_ENGINE_SINGLE_CTA keeps the whole tableau in one CTA's shared memory
  * (n <= TAB_BATCH_MAX_QUBITS; one launch per call).  The other engines apply
- * gate runs with a fused row-slab kernel spread over the GPU and differ in
- * how a run of measurements executes:
- *   TAB_ENGINE_CLUSTER  tableau in the shared memory of one thread-block
- *                       cluster of 16 CTAs (n up to about 2,500);
+ * gate runs with the block gate kernel (one CTA per 32-row word of the
+ * tableau) and differ in how a run of measurements executes:
  *   TAB_ENGINE_GRID     tableau in the shared memory of a cooperative grid
  *                       of one CTA per SM (n up to about 7,900), else
  *                       streamed from HBM/L2;
  *   TAB_ENGINE_STREAM   always streamed from HBM/L2 by a cooperative grid.
  * TAB_ENGINE_AUTO (default) picks by size: single-CTA for n <= 256, else
  * grid-resident where it fits, else streaming.  Results are bit-identical
- * across engines.  TAB_ERANGE if SINGLE_CTA is asked for n > TAB_BATCH_MAX_QUBITS or
- * CLUSTER for a tableau larger than one cluster holds. */
+ * across engines.  TAB_ERANGE if SINGLE_CTA is asked for
+ * n > TAB_BATCH_MAX_QUBITS; TAB_EINVAL for any other value (3 is unused). */
 enum tab_engine {
-  TAB_ENGINE_AUTO = 0, TAB_ENGINE_SINGLE_CTA = 1, TAB_ENGINE_GRID = 2, TAB_ENGINE_CLUSTER = 3,
-  TAB_ENGINE_STREAM = 4
+  TAB_ENGINE_AUTO = 0, TAB_ENGINE_SINGLE_CTA = 1, TAB_ENGINE_GRID = 2, TAB_ENGINE_STREAM = 4
 };
 int tab_set_engine(tab_t h, int engine);
 
 /* The engine a run of Z measurements takes on this handle under its selected
- * engine and size (TAB_ENGINE_SINGLE_CTA, _CLUSTER, _GRID or _STREAM; never
+ * engine and size (TAB_ENGINE_SINGLE_CTA, _GRID or _STREAM; never
  * _AUTO) in *engine, and the CTAs it launches in *ctas.  GRID falls back to
  * STREAM for a tableau that no cooperative grid holds in shared memory; this
  * call shows which one runs.  No device work.  TAB_EINVAL on null pointers. */
@@ -436,6 +433,30 @@ int tab_server_inject(tab_server_t s, int64_t ticket, int kind);
 int tab_server_stats_get(tab_server_t s, tab_server_stats *out);
 /* Finish every submitted request, then stop the worker and free the server. */
 int tab_server_destroy(tab_server_t s);
+
+/* ---- roofline ceilings of the current device ---------------------------
+ * The paper has no counterpart: these are the ceilings the kernels above are
+ * measured against.  Every kernel here is GF(2) logic on words held in shared
+ * memory, L2 or HBM, so its roofline is the integer logic pipe, the shared
+ * memory port, L2 or HBM; the measurement engines also wait on chains of grid
+ * barriers.  tab_measure_peaks times one launch of each microbenchmark with
+ * CUDA events after a warm-up launch (about 0.2 s in all), on a stream of its
+ * own, and changes no device setting.  It allocates (and frees) 128 MiB of
+ * device memory.  TAB_ECUDA if a launch fails; TAB_ETIMEOUT if the barrier
+ * benchmark's bounded wait ran out (then grid_barrier_us is 0). */
+typedef struct {
+  int32_t sms;                  /* multiprocessors of the current device */
+  double sm_clock_mhz;          /* SM clock during the logic run (clock64 over globaltimer) */
+  double logic_tops;            /* lop3.b32 per second, all SMs (1e12) */
+  double logic_ops_per_clk_sm;  /* the same per SM per clock */
+  double logic_ms;              /* duration of the logic run */
+  double smem_gbs;              /* ld.shared.v4 bytes per second, all SMs, no bank conflicts */
+  double smem_bytes_per_clk_sm; /* the same per SM per clock */
+  double l2_read_gbs;           /* ld.global.cg bytes per second over a 64 MiB set */
+  double l2_rw_gbs;             /* read + write bytes per second over a 64 MiB set */
+  double grid_barrier_us;       /* one bounded grid barrier, one CTA per SM */
+} tab_peaks;
+int tab_measure_peaks(tab_peaks *out);
 
 #ifdef __cplusplus
 }

@@ -50,20 +50,11 @@ void launch_init(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh, cudaStrea
   k_init<<<blocks, 256, 0, s>>>(X, Z, R, n, Wh);
 }
 
-// ------------------------------------------------- fused row-slab gates ----
-// Grid: one CTA per 32-row slab (row word w = blockIdx.x), W CTAs.  The slab
-// of every column (x and z words, 8 bytes per qubit) is staged in shared
-// memory, the segment's layers are applied in order with one CTA barrier per
-// layer, and the slab is written back.
-//
-// The gate stream (32-bit codes) is the same for every CTA and is read from
-// L2.  Thread 0 streams it into a shared-memory ring with TMA bulk copies
-// (cp.async.bulk, completion on one mbarrier per ring slot), kGateSlots
-// chunks ahead, so no thread waits on an L2 round trip per gate.  A slot is
-// refilled once every thread has passed the layer barrier after its last
-// code; layers are at most kMaxLayerOps codes (the host splits larger ones),
-// so the chunks of the previous and the current layer always fit in the ring.
-
+// ------------------------------------------------- TMA ring helpers ------
+// The gate kernel streams its block records (the same for every CTA, read
+// from L2) into a shared-memory ring with TMA bulk copies (cp.async.bulk,
+// completion on one mbarrier per ring slot), several chunks ahead, so no
+// thread waits on an L2 round trip per block.  Every wait is bounded.
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -114,270 +105,16 @@ __device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_
       : "memory");
 }
 
-constexpr int kGateChunk = 512;                      // codes per TMA copy (2 KB)
-constexpr int kGateSlots = 16;                       // ring slots
-constexpr int kGateRing = kGateChunk * kGateSlots;   // 8192 codes = 32 KB
-
-template <int T>
-__global__ void __launch_bounds__(T) k_gates_slab(uint32_t* __restrict__ X, uint32_t* __restrict__ Z,
-                                                  uint32_t* __restrict__ R, int n, int W,
-                                                  const uint32_t* __restrict__ ops,
-                                                  const uint32_t* __restrict__ layer_off,
-                                                  int nlayers, int* __restrict__ err) {
-  extern __shared__ __align__(128) uint32_t sm[];
-  uint32_t* ring = sm;                // gate-code ring (kGateRing codes)
-  uint32_t* sx = sm + kGateRing;      // X-plane word of every column (this slab's 32 rows)
-  uint32_t* sz = sx + n;              // Z-plane word of every column
-  __shared__ __align__(8) uint64_t bars[kGateSlots];
-  __shared__ uint32_t s_r;
-  __shared__ int s_abort;
-  const int w = blockIdx.x, tid = threadIdx.x;
-  const uint32_t ob = __ldg(layer_off), oe = __ldg(layer_off + nlayers);
-  const uint32_t base = ob & ~3u;     // 16-byte aligned start of the stream
-  const int nchunks = (int)((oe - base + kGateChunk - 1) / kGateChunk);
-  int issued = 0, waited = 0;         // thread 0's pipeline state
-  if (tid == 0) {
-    for (int i = 0; i < kGateSlots; ++i) mbar_init(&bars[i], 1);
-    mbar_fence_init();
-    s_r = 0u;
-    s_abort = 0;
-    for (; issued < nchunks && issued < kGateSlots; ++issued)
-      tma_bulk_g2s(ring + (size_t)issued * kGateChunk, ops + base + (size_t)issued * kGateChunk,
-                   kGateChunk * 4, &bars[issued]);
-  }
-  for (int a = tid; a < n; a += T) {
-    sx[a] = X[(size_t)a * W + w];
-    sz[a] = Z[(size_t)a * W + w];
-  }
-  __syncthreads();
-
-  uint32_t racc = 0u;
-  uint32_t prev_lb = ob;  // first code of the previous layer
-  uint32_t lb = ob;
-  for (int L = 0; L < nlayers; ++L) {
-    const uint32_t le = __ldg(layer_off + L + 1);
-    if (tid == 0) {
-      // refill slots whose chunk ended before the previous layer began: every
-      // thread has passed the barrier after the layer that read it last
-      while (issued < nchunks &&
-             (int64_t)base + (int64_t)(issued - kGateSlots + 1) * kGateChunk <= (int64_t)prev_lb) {
-        const int slot = issued % kGateSlots;
-        fence_proxy_async_smem();
-        tma_bulk_g2s(ring + (size_t)slot * kGateChunk, ops + base + (size_t)issued * kGateChunk,
-                     kGateChunk * 4, &bars[slot]);
-        ++issued;
-      }
-      if (le > lb) {
-        const int c_last = (int)((le - 1 - base) / kGateChunk);
-        if (c_last >= issued) {
-          atomicCAS(err, 0, DERR_BOUNDS);
-          s_abort = 1;
-        } else {
-          for (; waited <= c_last; ++waited)
-            if (!mbar_wait_bounded(&bars[waited % kGateSlots], (uint32_t)(waited / kGateSlots) & 1u)) {
-              atomicCAS(err, 0, DERR_TIMEOUT);
-              s_abort = 1;
-              break;
-            }
-        }
-      }
-    }
-    __syncthreads();
-    if (s_abort) break;
-    for (uint32_t g = lb + tid; g < le; g += T)
-      apply_gate(ring[(g - base) & (kGateRing - 1)], sx, sz, 1, 0, racc);
-    prev_lb = lb;
-    lb = le;
-  }
-  // every copy issued must land before the CTA exits (normally all have been
-  // waited for already; after an abort some may still be in flight)
-  if (tid == 0)
-    for (; waited < issued; ++waited)
-      mbar_wait_bounded(&bars[waited % kGateSlots], (uint32_t)(waited / kGateSlots) & 1u);
-  __syncthreads();
-  if (s_abort) return;
-
-  for (int a = tid; a < n; a += T) {
-    X[(size_t)a * W + w] = sx[a];
-    Z[(size_t)a * W + w] = sz[a];
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) racc ^= __shfl_xor_sync(0xffffffffu, racc, o);
-  if ((tid & 31) == 0 && racc) atomicXor(&s_r, racc);
-  __syncthreads();
-  if (tid == 0) R[w] ^= s_r;
-}
-
-// -------------------------------------------- dataflow row-slab gates ----
-// Same slab layout as k_gates_slab, without layer barriers.  Each gate record
-// (64 bits: code | required column versions) says how many earlier gates of
-// the run touch each of its qubits; a thread applies the gate once both
-// columns have reached those versions and then bumps them.  Records are in
-// ASAP-layer order, a topological order of the gate dependencies, and each
-// thread takes its records in increasing order, so the earliest unfinished
-// gate can always proceed: the run never deadlocks, and gates of different
-// layers overlap instead of meeting at a CTA barrier.
-//
-// Warp 0 is the producer: lane 0 streams the records into a shared ring with
-// TMA bulk copies and publishes how many chunks have landed; a slot is reused
-// once every worker warp has reported progress past it.  Every wait is
-// bounded (~1 s) and latches an error instead of hanging.
-constexpr int kFlowChunk = 512;                     // records per TMA copy (4 KB)
-constexpr int kFlowSlots = 16;                      // 64 KB ring
-constexpr int kFlowRing = kFlowChunk * kFlowSlots;
-
-__device__ __forceinline__ uint32_t ld_volatile_s(const uint32_t* p) {
-  return *(const volatile uint32_t*)p;
-}
-
-template <int T>
-__global__ void __launch_bounds__(T) k_gates_flow(uint32_t* __restrict__ X, uint32_t* __restrict__ Z,
-                                                  uint32_t* __restrict__ R, int n, int W,
-                                                  const uint2* __restrict__ rec, uint32_t rb,
-                                                  uint32_t re, int* __restrict__ err) {
-  constexpr int NW = T / 32 - 1;  // worker warps
-  constexpr int TW = NW * 32;     // worker threads
-  extern __shared__ __align__(128) uint32_t sm[];
-  uint2* ring = reinterpret_cast<uint2*>(sm);               // kFlowRing records
-  uint32_t* sx = sm + 2 * kFlowRing;
-  uint32_t* sz = sx + n;
-  uint32_t* ver = sz + n;                                   // column versions
-  __shared__ __align__(8) uint64_t bars[kFlowSlots];
-  __shared__ uint32_t s_r, s_ready;
-  __shared__ uint32_t s_prog[NW];                           // steps completed per worker warp
-  __shared__ int s_abort;
-  const int w = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t base = rb & ~1u;  // 16-byte aligned start
-  const uint32_t nrec = re - base;
-  const int nchunks = (int)((nrec + kFlowChunk - 1) / kFlowChunk);
-  if (tid == 0) {
-    for (int i = 0; i < kFlowSlots; ++i) mbar_init(&bars[i], 1);
-    mbar_fence_init();
-    s_r = 0u;
-    s_ready = 0u;
-    s_abort = 0;
-  }
-  for (int i = tid; i < NW; i += T) s_prog[i] = 0u;
-  for (int a = tid; a < n; a += T) {
-    sx[a] = X[(size_t)a * W + w];
-    sz[a] = Z[(size_t)a * W + w];
-    ver[a] = 0u;
-  }
-  __syncthreads();
-
-  uint32_t racc = 0u;
-  if (warp == 0) {
-    // ---------------- producer ----------------
-    if (lane == 0) {
-      int issued = 0, landed = 0;
-      unsigned long long t0 = gate_gtimer();  // time of the last progress
-      while (landed < nchunks) {
-        const int before = issued + landed;
-        // reuse slot of chunk issued - kFlowSlots once all workers are past it
-        uint32_t minp = 0xffffffffu;
-        for (int i = 0; i < NW; ++i) minp = min(minp, ld_volatile_s(&s_prog[i]));
-        const uint64_t consumed = (uint64_t)minp * TW;  // records [0, consumed) done
-        while (issued < nchunks &&
-               (issued < kFlowSlots ||
-                (uint64_t)(issued - kFlowSlots + 1) * kFlowChunk <= consumed)) {
-          const int slot = issued % kFlowSlots;
-          fence_proxy_async_smem();
-          tma_bulk_g2s(ring + (size_t)slot * kFlowChunk, rec + base + (size_t)issued * kFlowChunk,
-                       kFlowChunk * 8, &bars[slot]);
-          ++issued;
-        }
-        if (landed < issued &&
-            mbar_try_wait(&bars[landed % kFlowSlots], (uint32_t)(landed / kFlowSlots) & 1u)) {
-          ++landed;
-          __threadfence_block();
-          *(volatile uint32_t*)&s_ready = (uint32_t)landed;
-        }
-        if (*(volatile int*)&s_abort) break;
-        if (issued + landed != before) {
-          t0 = gate_gtimer();
-        } else if (gate_gtimer() - t0 > 1000000000ull) {
-          atomicCAS(err, 0, DERR_TIMEOUT);
-          *(volatile int*)&s_abort = 1;
-          break;
-        }
-      }
-      // copies in flight must land before the CTA exits
-      for (; landed < issued; ++landed)
-        mbar_wait_bounded(&bars[landed % kFlowSlots], (uint32_t)(landed / kFlowSlots) & 1u);
-    }
-  } else {
-    // ---------------- workers ----------------
-    const int wt = tid - 32;  // worker thread index
-    uint32_t step = 0;
-    bool abort = false;
-    for (uint32_t g0 = (uint32_t)(wt - lane); g0 < nrec && !abort; g0 += TW, ++step) {
-      const uint32_t g = g0 + lane;
-      if (g < nrec && g + base >= rb) {
-        const uint32_t chunk = g / kFlowChunk;
-        const unsigned long long t0 = gate_gtimer();
-        while (ld_volatile_s(&s_ready) <= chunk) {
-          if (*(volatile int*)&s_abort || gate_gtimer() - t0 > 1000000000ull) {
-            atomicCAS(err, 0, DERR_TIMEOUT);
-            *(volatile int*)&s_abort = 1;
-            abort = true;
-            break;
-          }
-        }
-        if (!abort) {
-          __threadfence_block();
-          const uint2 r = ring[g & (kFlowRing - 1)];
-          const uint32_t code = r.x;
-          const uint32_t a = dq1(code), b = dq2(code), op = dop(code);
-          const bool two = op == OP_CNOT || op == OP_CZ || op == OP_SWAP;
-          const uint32_t va = r.y & 0xFFFFu, vb = r.y >> 16;
-          const unsigned long long t1 = gate_gtimer();
-          int polls = 0;
-          while ((ld_volatile_s(&ver[a]) & 0xFFFFu) != va ||
-                 (two && (ld_volatile_s(&ver[b]) & 0xFFFFu) != vb)) {
-            if (++polls > 8) __nanosleep(32);  // leave shared-memory bandwidth to others
-            if (*(volatile int*)&s_abort || gate_gtimer() - t1 > 1000000000ull) {
-              atomicCAS(err, 0, DERR_TIMEOUT);
-              *(volatile int*)&s_abort = 1;
-              abort = true;
-              break;
-            }
-          }
-          if (!abort) {
-            __threadfence_block();
-            apply_gate(code, sx, sz, 1, 0, racc);
-            __threadfence_block();
-            *(volatile uint32_t*)&ver[a] = va + 1u;
-            if (two) *(volatile uint32_t*)&ver[b] = vb + 1u;
-          }
-        }
-      }
-      __syncwarp();
-      if (lane == 0) *(volatile uint32_t*)&s_prog[warp - 1] = step + 1;
-      abort = __any_sync(0xffffffffu, abort);
-    }
-    if (lane == 0) *(volatile uint32_t*)&s_prog[warp - 1] = 0xffffffffu;  // done
-  }
-  __syncthreads();
-  if (s_abort) return;
-  for (int a = tid; a < n; a += T) {
-    X[(size_t)a * W + w] = sx[a];
-    Z[(size_t)a * W + w] = sz[a];
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) racc ^= __shfl_xor_sync(0xffffffffu, racc, o);
-  if (lane == 0 && racc) atomicXor(&s_r, racc);
-  __syncthreads();
-  if (tid == 0) R[w] ^= s_r;
-}
-
 // ------------------------------------------------ block row-slab gates ----
-// Same slab layout as k_gates_slab; the gate run is compiled into two-qubit
-// blocks (blocks.cpp) grouped in super-layers of pairwise-disjoint blocks,
-// with one CTA barrier per super-layer instead of one per ASAP layer.  A
-// thread applies a whole block to the slab's 32 rows in registers -- U_0 (x)
-// U_1, the entangler, V_0 (x) V_1 -- without branching on the gates, and
-// stores the two columns back (exchanged if the block swaps them).  The
-// records (8 bytes) stream through the same kind of TMA ring as the codes.
+// Grid: one CTA per 32-row slab (row word w = blockIdx.x), W CTAs.  The slab
+// of every column (x and z words, 8 bytes per qubit) is staged in shared
+// memory, and the slab is written back at the end.  The gate run is compiled
+// into two-qubit blocks (blocks.cpp) grouped in super-layers of pairwise-
+// disjoint blocks, with one CTA barrier per super-layer.  A thread applies a
+// whole block to the slab's 32 rows in registers -- U_0 (x) U_1, the
+// entangler, V_0 (x) V_1 -- without branching on the gates, and stores the
+// two columns back (exchanged if the block swaps them).  The records (8
+// bytes) stream through the TMA ring.
 constexpr int kBlkChunk = 512;                  // records per TMA copy (4 KB)
 constexpr int kBlkSlots = 16;                   // 64 KB ring (12 slots, 48 KB, for large n)
 constexpr int kBlkRing = kBlkChunk * kBlkSlots;
@@ -516,58 +253,6 @@ __global__ void __launch_bounds__(T) k_gates_block(uint32_t* __restrict__ X, uin
 
 constexpr int kMaxSmemBytes = 227 * 1024;
 
-int gates_max_n() { return (kMaxSmemBytes - 4096 - kGateRing * 4) / 8; }
-
-// Threads per CTA of the slab kernel: more threads shorten each thread's chain
-// of gates per layer (the kernel is latency-bound per layer).  TAB_GATE_THREADS
-// (256, 512 or 1024) overrides the default for tuning sweeps.
-static int gate_threads() {
-  static int t = 0;
-  if (t == 0) {
-    t = 512;
-    if (const char* e = getenv("TAB_GATE_THREADS")) {
-      const int v = atoi(e);
-      if (v == 256 || v == 512 || v == 1024) t = v;
-    }
-  }
-  return t;
-}
-
-template <int T>
-static cudaError_t launch_gates_t(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
-                                  const uint32_t* ops, const uint32_t* layer_off, int nlayers,
-                                  int* err, cudaStream_t s) {
-  const size_t smem = (size_t)kGateRing * 4 + (size_t)n * 2 * sizeof(uint32_t);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_gates_slab<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kMaxSmemBytes - 4096);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  k_gates_slab<T><<<W, T, smem, s>>>(X, Z, R, n, W, ops, layer_off, nlayers, err);
-  return cudaGetLastError();
-}
-
-int gates_flow_max_n() { return (kMaxSmemBytes - 4096 - kFlowRing * 8) / 12; }
-
-cudaError_t launch_gates_flow(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
-                              const uint2* rec, uint32_t rb, uint32_t re, int* err,
-                              cudaStream_t s) {
-  if (re <= rb) return cudaSuccess;
-  constexpr int T = 512;
-  const size_t smem = (size_t)kFlowRing * 8 + (size_t)n * 3 * sizeof(uint32_t);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_gates_flow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kMaxSmemBytes - 4096);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  k_gates_flow<T><<<W, T, smem, s>>>(X, Z, R, n, W, rec, rb, re, err);
-  return cudaGetLastError();
-}
-
 int gates_block_max_n() { return (kMaxSmemBytes - 4096 - kBlkRing * 8) / 8; }
 
 // Threads per CTA of the block kernel: the kernel is latency-bound per
@@ -620,17 +305,6 @@ cudaError_t launch_gates_block(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int
     case 128: return launch_gates_block_t<128, 16>(X, Z, R, n, W, blk, blk_off, nlayers, err, s);
     case 256: return launch_gates_block_t<256, 16>(X, Z, R, n, W, blk, blk_off, nlayers, err, s);
     default: return launch_gates_block_t<512, 16>(X, Z, R, n, W, blk, blk_off, nlayers, err, s);
-  }
-}
-
-cudaError_t launch_gates_slab(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
-                              const uint32_t* ops, const uint32_t* layer_off, int nlayers,
-                              int* err, cudaStream_t s) {
-  if (nlayers <= 0) return cudaSuccess;
-  switch (gate_threads()) {
-    case 256: return launch_gates_t<256>(X, Z, R, n, W, ops, layer_off, nlayers, err, s);
-    case 1024: return launch_gates_t<1024>(X, Z, R, n, W, ops, layer_off, nlayers, err, s);
-    default: return launch_gates_t<512>(X, Z, R, n, W, ops, layer_off, nlayers, err, s);
   }
 }
 

@@ -34,64 +34,6 @@ void set_error(const char* fmt, ...) {
 
 const char* last_error() { return g_last_error.c_str(); }
 
-// Program-order compile for the dataflow gate kernel: one pass, no layering.
-// Program order is itself a topological order of the gate dependencies, and a
-// gate's column versions are its per-qubit positions in program order within
-// its gate run.  Gate runs carry no layer table (layer_begin == layer_end).
-static int build_program_stream(int32_t n, const tab_gate* gates, int64_t count,
-                                HostProgram* out) {
-  HostProgram& P = *out;
-  P = HostProgram();
-  P.n = n;
-  P.layered = false;
-  P.ops.reserve((size_t)count);
-  P.vers.reserve((size_t)count);
-  std::vector<uint32_t> cnt((size_t)n, 0u), stamp((size_t)n, 0u);
-  uint32_t seg_id = 1;  // stamps: counters restart in every gate run
-  int cur = -1;         // kind of the open segment (-1: none)
-  for (int64_t i = 0; i < count; ++i) {
-    const uint64_t g = gates[i];
-    const uint32_t op = (uint32_t)(g >> 56);
-    const uint32_t q1 = (uint32_t)((g >> 28) & 0xFFFFFFFull), q2 = (uint32_t)(g & 0xFFFFFFFull);
-    if (op == TAB_BARRIER || op == TAB_I) continue;
-    const bool meas = op == TAB_MZ || op == TAB_MZR;
-    const int kind = meas ? 1 : 0;
-    if (cur != kind) {
-      if (cur == 0) ++seg_id;
-      Seg s{};
-      s.kind = (uint32_t)kind;
-      s.op_begin = s.op_end = (uint32_t)P.ops.size();
-      s.meas_before = (uint32_t)P.n_meas;
-      P.segs.push_back(s);
-      cur = kind;
-    }
-    if (meas) {
-      P.ops.push_back(dcode(op, q1, 0));
-      P.vers.push_back(0u);
-      P.n_meas++;
-    } else {
-      const bool two = (op == TAB_CNOT || op == TAB_CZ || op == TAB_SWAP);
-      if (stamp[q1] != seg_id) {
-        stamp[q1] = seg_id;
-        cnt[q1] = 0;
-      }
-      uint32_t v = cnt[q1]++ & 0xFFFFu;
-      if (two) {
-        if (stamp[q2] != seg_id) {
-          stamp[q2] = seg_id;
-          cnt[q2] = 0;
-        }
-        v |= (cnt[q2]++ & 0xFFFFu) << 16;
-      }
-      P.ops.push_back(dcode(op, q1, two ? q2 : 0));
-      P.vers.push_back(v);
-      P.n_gates++;
-    }
-    P.segs.back().op_end++;
-  }
-  return TAB_OK;
-}
-
 // Every word of gates[begin, end) is a valid gate for n qubits (index i in
 // messages is the position in the whole list).  Extended ops (TAB_MX ..
 // TAB_ZERR, one-qubit) are valid only when `ext` is given; *ext then counts
@@ -152,16 +94,15 @@ static int validate(int32_t n, const tab_gate* gates, int64_t begin, int64_t end
   return TAB_OK;
 }
 
-// Compile a validated gate list into the forms `mode` names (not kProgStream).
+// Compile a validated gate list into the forms `mode` names.
 static int build_range(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out,
                        int mode);
 
 void concat_programs(HostProgram& P, const HostProgram* part, size_t T, bool with_blk) {
-  std::vector<size_t> o_ops(T + 1, 0), o_vers(T + 1, 0), o_blk(T + 1, 0), o_loff(T + 1, 0),
+  std::vector<size_t> o_ops(T + 1, 0), o_blk(T + 1, 0), o_loff(T + 1, 0),
       o_boff(T + 1, 0), o_segs(T + 1, 0), o_meas(T + 1, 0);
   for (size_t t = 0; t < T; ++t) {
     o_ops[t + 1] = o_ops[t] + part[t].ops.size();
-    o_vers[t + 1] = o_vers[t] + part[t].vers.size();
     o_blk[t + 1] = o_blk[t] + part[t].blk.size();
     o_loff[t + 1] = o_loff[t] + part[t].layer_off.size();
     o_boff[t + 1] = o_boff[t] + part[t].blk_off.size();
@@ -170,9 +111,7 @@ void concat_programs(HostProgram& P, const HostProgram* part, size_t T, bool wit
   }
   P.clear(part[0].n);
   P.mode = part[0].mode;
-  P.layered = part[0].layered;
   P.ops.resize(o_ops[T]);
-  P.vers.resize(o_vers[T]);
   if (with_blk) P.blk.resize(o_blk[T]);
   P.layer_off.resize(o_loff[T]);
   P.blk_off.resize(o_boff[T]);
@@ -185,7 +124,6 @@ void concat_programs(HostProgram& P, const HostProgram* part, size_t T, bool wit
     const size_t t = (size_t)ti;
     const HostProgram& Q = part[t];
     std::copy(Q.ops.begin(), Q.ops.end(), P.ops.begin() + (ptrdiff_t)o_ops[t]);
-    std::copy(Q.vers.begin(), Q.vers.end(), P.vers.begin() + (ptrdiff_t)o_vers[t]);
     if (with_blk) std::copy(Q.blk.begin(), Q.blk.end(), P.blk.begin() + (ptrdiff_t)o_blk[t]);
     for (size_t i = 0; i < Q.layer_off.size(); ++i)
       P.layer_off[o_loff[t] + i] = Q.layer_off[i] + (uint32_t)o_ops[t];
@@ -276,11 +214,6 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
   const int vrc = validate(n, gates, 0, count);
   if (vrc != TAB_OK) return vrc;
 
-  if (mode & kProgStream) {
-    const int rc = build_program_stream(n, gates, count, out);
-    out->mode = kProgStream;
-    return rc;
-  }
   return build_range(n, gates, count, out, mode);
 }
 
@@ -302,7 +235,6 @@ static int build_range(int32_t n, const tab_gate* gates, int64_t count, HostProg
   int64_t nlayers = 0;                       // layers emitted so far (global)
   std::vector<uint32_t> seg_codes;
   std::vector<int32_t> seg_layer;
-  std::vector<uint32_t> seg_ver((size_t)n, 0u);
 
   // Each gate segment owns one contiguous run of layer_off entries:
   // layer_off[layer_begin] = op_begin, layer_off[layer_begin + L + 1] = end
@@ -370,21 +302,6 @@ static int build_range(int32_t n, const tab_gate* gates, int64_t count, HostProg
       s.blk_begin = s.blk_end = (uint32_t)P.blk_off.size();
     }
     P.segs.push_back(s);
-    // column versions in the final (layered) order
-    P.vers.resize(P.ops.size(), 0u);
-    for (uint32_t i = op_base; i < (uint32_t)P.ops.size(); ++i) {
-      const uint32_t c = P.ops[i];
-      const uint32_t a = dq1(c), b = dq2(c), op = dop(c);
-      const bool two = op == OP_CNOT || op == OP_CZ || op == OP_SWAP;
-      uint32_t v = seg_ver[a]++ & 0xFFFFu;
-      if (two) v |= (seg_ver[b]++ & 0xFFFFu) << 16;
-      P.vers[i] = v;
-    }
-    for (uint32_t i = op_base; i < (uint32_t)P.ops.size(); ++i) {  // reset touched counters
-      const uint32_t c = P.ops[i];
-      seg_ver[dq1(c)] = 0;
-      seg_ver[dq2(c)] = 0;
-    }
     nlayers = top;
     seg_codes.clear();
     seg_layer.clear();
@@ -405,7 +322,6 @@ static int build_range(int32_t n, const tab_gate* gates, int64_t count, HostProg
         P.segs.push_back(s);
       }
       P.ops.push_back(dcode(op, q1, 0));
-      P.vers.push_back(0u);
       P.segs.back().op_end++;
       P.n_meas++;
       continue;

@@ -238,8 +238,8 @@ int tab_sharded_create(int32_t n, int32_t shards, tab_shard_t* out) {
     return TAB_EINVAL;
   }
   *out = nullptr;
-  if (n < 1 || n > TAB_MAX_QUBITS || n > gates_max_n()) {
-    set_error("n=%d outside [1, %d]", n, std::min(TAB_MAX_QUBITS, gates_max_n()));
+  if (n < 1 || n > TAB_MAX_QUBITS || n > gates_block_max_n()) {
+    set_error("n=%d outside [1, %d]", n, std::min(TAB_MAX_QUBITS, gates_block_max_n()));
     return TAB_ERANGE;
   }
   const int Wh = half_words(n), used = (n + 31) / 32;

@@ -89,7 +89,6 @@ struct tab_prog_s {
   uint32_t* d_ops = nullptr;
   uint32_t* d_layer = nullptr;
   Seg* d_segs = nullptr;
-  uint2* d_rec = nullptr;
   uint2* d_blk = nullptr;
   uint32_t* d_blk_off = nullptr;
 };
@@ -99,7 +98,6 @@ struct DevProg {
   uint32_t* ops = nullptr;
   uint32_t* layer = nullptr;
   Seg* segs = nullptr;
-  uint2* rec = nullptr;       // (code, versions) per op, for the dataflow gate kernel
   uint2* blk = nullptr;       // block records, for the block gate kernel
   uint32_t* blk_off = nullptr;
   void* base = nullptr;       // single allocation holding all of the above (staged uploads)
@@ -109,9 +107,6 @@ struct DevProg {
 
 namespace {
 
-bool use_flow_gates(int n);
-enum GateKernel { GK_BLOCK = 0, GK_SLAB = 1, GK_FLOW = 2 };
-GateKernel gate_kernel(int n);
 
 int sm_count_of(int dev) {
   int v = 0;
@@ -228,9 +223,8 @@ bool use_single_cta(tab_t h) {
 }
 
 // Engine that runs a run of measurements on this handle (single-CTA runs the
-// whole program), and its CTA count: grid-resident > cluster-resident >
-// streaming, as the selected engine allows (the grid-resident engine spreads
-// a batch over every SM; a cluster holds it on at most 16).
+// whole program), and its CTA count: grid-resident where the tableau fits the
+// grid's shared memory and the selected engine allows, else streaming.
 int measure_engine(tab_t h, int* ctas) {
   if (use_single_cta(h)) {
     *ctas = 1;
@@ -241,11 +235,6 @@ int measure_engine(tab_t h, int* ctas) {
   if (G > 0) {
     *ctas = G;
     return TAB_ENGINE_GRID;
-  }
-  const int C = (any || h->engine == TAB_ENGINE_CLUSTER) ? cluster_size_for(h->n, h->Wh) : 0;
-  if (C > 0) {
-    *ctas = C;
-    return TAB_ENGINE_CLUSTER;
   }
   *ctas = h->meas_ctas;
   return TAB_ENGINE_STREAM;
@@ -281,12 +270,14 @@ int run_program(tab_t h, const HostProgram& hp, const DevProg& dp, uint64_t seed
     h->log_len += hp.n_meas;
     return TAB_OK;
   }
-  const GateKernel gk = gate_kernel(h->n);
-  const bool can_blk = (hp.mode & kProgBlocks) != 0, can_lay = (hp.mode & kProgLayers) != 0;
+  if (hp.n_gates > 0 && !(hp.mode & kProgBlocks)) {
+    set_error("the program has no block records for the multi-CTA gate kernel");
+    return TAB_EINVAL;
+  }
   for (size_t si = 0; si < hp.segs.size(); ++si) {
     const Seg& s = hp.segs[si];
     if (s.kind == 0) {
-      if (can_blk && (gk == GK_BLOCK || (!can_lay && dp.rec == nullptr))) {
+      {
         // gate runs that follow one another with adjacent super-layer offsets
         // (pieces of one list compiled apart) run as one launch: the shared
         // bound between two runs is an empty super-layer
@@ -297,22 +288,13 @@ int run_program(tab_t h, const HostProgram& hp, const DevProg& dp, uint64_t seed
         CU(launch_gates_block(h->X, h->Z, h->R, h->n, h->W, dp.blk, dp.blk_off + s.blk_begin,
                               (int)(hp.segs[sj].blk_end - s.blk_begin), h->mw.err, h->stream));
         si = sj;
-      } else if (dp.rec != nullptr && (gk == GK_FLOW || !can_lay))
-        CU(launch_gates_flow(h->X, h->Z, h->R, h->n, h->W, dp.rec, s.op_begin, s.op_end,
-                             h->mw.err, h->stream));
-      else
-        CU(launch_gates_slab(h->X, h->Z, h->R, h->n, h->W, dp.ops, dp.layer + s.layer_begin,
-                             (int)(s.layer_end - s.layer_begin), h->mw.err, h->stream));
+      }
       h->launches++;
     } else {
       const int nm = (int)(s.op_end - s.op_begin);
       int ctas = 0;
       const int me = measure_engine(h, &ctas);
-      if (me == TAB_ENGINE_CLUSTER)
-        CU(launch_measure_cluster(h->X, h->Z, h->R, h->n, h->Wh, dp.ops + s.op_begin, nm, h->k,
-                                  seed, h->cid, h->shot, h->log + h->log_len, h->mw.err, ctas,
-                                  h->stream));
-      else if (me == TAB_ENGINE_GRID)
+      if (me == TAB_ENGINE_GRID)
         CU(launch_measure_resident(h->X, h->Z, h->R, h->n, h->Wh, dp.ops + s.op_begin, nm, h->k,
                                    seed, h->cid, h->shot, h->log + h->log_len, h->mw.err, h->rw,
                                    h->rbar, ctas, h->stream));
@@ -368,24 +350,6 @@ int upload(const HostProgram& hp, DevProg* d, cudaStream_t s, bool async_alloc) 
       CU(cudaMemcpyAsync(d->blk_off, hp.blk_off.data(), hp.blk_off.size() * 4,
                          cudaMemcpyHostToDevice, s));
   }
-  // 64-bit records for the dataflow gate kernel (same padding rule as ops);
-  // only when that kernel will run for this n
-  if (hp.n_gates == 0 ||
-      !((hp.mode & kProgStream) || ((hp.mode & kProgLayers) && use_flow_gates(hp.n))))
-    return TAB_OK;
-  const size_t rb = (hp.ops.size() + kOpsPad) * sizeof(uint2);
-  if (async_alloc) {
-    CU(cudaMallocAsync((void**)&d->rec, rb, s));
-  } else {
-    CU(cudaMalloc((void**)&d->rec, rb));
-  }
-  {
-    std::vector<uint2> rec(hp.ops.size() + kOpsPad);
-    for (size_t i = 0; i < hp.ops.size(); ++i) rec[i] = make_uint2(hp.ops[i], hp.vers[i]);
-    for (size_t i = hp.ops.size(); i < rec.size(); ++i) rec[i] = make_uint2(0u, 0u);
-    CU(cudaMemcpyAsync(d->rec, rec.data(), rb, cudaMemcpyHostToDevice, s));
-    if (async_alloc) CU(cudaStreamSynchronize(s));  // rec is a stack temporary
-  }
   return TAB_OK;
 }
 
@@ -398,7 +362,6 @@ void free_async(DevProg& d, cudaStream_t s) {
   if (d.ops) cudaFreeAsync(d.ops, s);
   if (d.layer) cudaFreeAsync(d.layer, s);
   if (d.segs) cudaFreeAsync(d.segs, s);
-  if (d.rec) cudaFreeAsync(d.rec, s);
   if (d.blk) cudaFreeAsync(d.blk, s);
   if (d.blk_off) cudaFreeAsync(d.blk_off, s);
 }
@@ -425,17 +388,14 @@ struct ExtBlocks {
 // waits for them: a program's upload overlaps the previous program's kernels.
 int upload_staged(tab_t h, const HostProgram& hp, DevProg* d, const ExtBlocks* ext = nullptr,
                   bool side = false) {
-  const bool want_rec =
-      hp.n_gates > 0 && ((hp.mode & kProgStream) || ((hp.mode & kProgLayers) && use_flow_gates(hp.n)));
   const bool want_blk = (hp.mode & kProgBlocks) != 0;
   const size_t nblk = ext ? ext->total : hp.blk.size();
   const size_t ob = align256((hp.ops.size() + kOpsPad) * 4);
   const size_t lb = align256(std::max<size_t>(hp.layer_off.size(), 1) * 4);
   const size_t sb = align256(std::max<size_t>(hp.segs.size(), 1) * sizeof(Seg));
-  const size_t rb = want_rec ? align256((hp.ops.size() + kOpsPad) * sizeof(uint2)) : 0;
   const size_t bb = want_blk ? align256((nblk + kOpsPad) * sizeof(uint2)) : 0;
   const size_t bo = want_blk ? align256(std::max<size_t>(hp.blk_off.size(), 1) * 4) : 0;
-  const size_t total = ob + lb + sb + rb + bb + bo;
+  const size_t total = ob + lb + sb + bb + bo;
   const int stage = h->stg_next;
   tab_s::Stage& sg = h->stg[stage];
   h->stg_next = (h->stg_next + 1) % tab_s::kStages;
@@ -458,14 +418,8 @@ int upload_staged(tab_t h, const HostProgram& hp, DevProg* d, const ExtBlocks* e
   memset(ops + hp.ops.size(), 0, (size_t)kOpsPad * 4);
   if (!hp.layer_off.empty()) memcpy(st + ob, hp.layer_off.data(), hp.layer_off.size() * 4);
   if (!hp.segs.empty()) memcpy(st + ob + lb, hp.segs.data(), hp.segs.size() * sizeof(Seg));
-  if (want_rec) {
-    uint2* rec = reinterpret_cast<uint2*>(st + ob + lb + sb);
-    const size_t no = hp.ops.size();
-    for (size_t i = 0; i < no; ++i) rec[i] = make_uint2(hp.ops[i], hp.vers[i]);
-    memset(rec + no, 0, (size_t)kOpsPad * sizeof(uint2));
-  }
   if (want_blk) {
-    uint8_t* b0 = st + ob + lb + sb + rb;
+    uint8_t* b0 = st + ob + lb + sb;
     if (!hp.blk.empty()) {  // large programs: the copy into pinned memory in pieces
       const size_t bytes = hp.blk.size() * sizeof(uint2);
       const int pieces = bytes >= ((size_t)1 << 20) ? pool_threads() : 1;
@@ -513,7 +467,7 @@ int upload_staged(tab_t h, const HostProgram& hp, DevProg* d, const ExtBlocks* e
   if (ext && want_blk) {
     // everything but the records through the staging area, the records from
     // the parts' own pinned buffers
-    const size_t rec0 = ob + lb + sb + rb, recb = nblk * sizeof(uint2);
+    const size_t rec0 = ob + lb + sb, recb = nblk * sizeof(uint2);
     CU(cudaMemcpyAsync(dev, st, rec0, cudaMemcpyHostToDevice, cs));
     size_t at = rec0;
     for (int i = 0; i < ext->n; ++i) {
@@ -534,41 +488,14 @@ int upload_staged(tab_t h, const HostProgram& hp, DevProg* d, const ExtBlocks* e
   d->ops = reinterpret_cast<uint32_t*>(dev);
   d->layer = reinterpret_cast<uint32_t*>(dev + ob);
   d->segs = reinterpret_cast<Seg*>(dev + ob + lb);
-  d->rec = want_rec ? reinterpret_cast<uint2*>(dev + ob + lb + sb) : nullptr;
-  d->blk = want_blk ? reinterpret_cast<uint2*>(dev + ob + lb + sb + rb) : nullptr;
-  d->blk_off = want_blk ? reinterpret_cast<uint32_t*>(dev + ob + lb + sb + rb + bb) : nullptr;
+  d->blk = want_blk ? reinterpret_cast<uint2*>(dev + ob + lb + sb) : nullptr;
+  d->blk_off = want_blk ? reinterpret_cast<uint32_t*>(dev + ob + lb + sb + bb) : nullptr;
   return TAB_OK;
 }
 
-// Gate kernel of the multi-CTA engines: the block kernel by default (one
-// barrier per super-layer of two-qubit blocks); TAB_GATE_KERNEL=slab selects
-// the layer-barrier kernel and TAB_GATE_KERNEL=flow the dataflow kernel, each
-// where its shared-memory slab fits.
-GateKernel gate_kernel(int n) {
-  static int mode = -1;
-  if (mode < 0) {
-    const char* e = getenv("TAB_GATE_KERNEL");
-    mode = GK_BLOCK;
-    if (e && strcmp(e, "slab") == 0) mode = GK_SLAB;
-    if (e && strcmp(e, "flow") == 0) mode = GK_FLOW;
-  }
-  if (mode == GK_FLOW && n > gates_flow_max_n()) return GK_SLAB;
-  if (mode == GK_BLOCK && n > gates_block_max_n()) return GK_SLAB;
-  return (GateKernel)mode;
-}
-
-bool use_flow_gates(int n) { return gate_kernel(n) == GK_FLOW; }
-
 // Compile forms for a call on this handle: ASAP layers for the single-CTA
-// engine, else what the gate kernel reads.
-int compile_mode_for(tab_t h) {
-  if (use_single_cta(h)) return kProgLayers;
-  switch (gate_kernel(h->n)) {
-    case GK_BLOCK: return kProgBlocks;
-    case GK_FLOW: return kProgStream;
-    default: return kProgLayers;
-  }
-}
+// engine, else the block records the multi-CTA gate kernel reads.
+int compile_mode_for(tab_t h) { return use_single_cta(h) ? kProgLayers : kProgBlocks; }
 
 }  // namespace
 
@@ -1043,7 +970,6 @@ int tab_prog_create(int32_t n, const tab_gate* gates, int64_t count, tab_prog_t*
     p->d_ops = d.ops;
     p->d_layer = d.layer;
     p->d_segs = d.segs;
-    p->d_rec = d.rec;
     p->d_blk = d.blk;
     p->d_blk_off = d.blk_off;
   }
@@ -1067,7 +993,6 @@ int tab_prog_destroy(tab_prog_t p) {
   if (p->d_ops) cudaFree(p->d_ops);
   if (p->d_layer) cudaFree(p->d_layer);
   if (p->d_segs) cudaFree(p->d_segs);
-  if (p->d_rec) cudaFree(p->d_rec);
   if (p->d_blk) cudaFree(p->d_blk);
   if (p->d_blk_off) cudaFree(p->d_blk_off);
   delete p;
@@ -1106,7 +1031,6 @@ int tab_run(tab_t h, tab_prog_t p) {
   d.ops = p->d_ops;
   d.layer = p->d_layer;
   d.segs = p->d_segs;
-  d.rec = p->d_rec;
   d.blk = p->d_blk;
   d.blk_off = p->d_blk_off;
   return run_program(h, p->hp, d, h->seed);
@@ -1129,7 +1053,7 @@ static int measure_common(tab_t h, const int32_t* qubits, int32_t k, uint64_t se
     g[(size_t)i] = tab_make_gate(TAB_MZ, (uint32_t)qubits[i], 0);
   }
   HostProgram hp;
-  rc = build_program(h->n, g.data(), k, &hp, kProgStream);  // measurements only
+  rc = build_program(h->n, g.data(), k, &hp, compile_mode_for(h));  // measurements only
   if (rc) return rc;
   *first = h->log_len;
   if (hp.ops.empty()) return TAB_OK;
@@ -1287,16 +1211,13 @@ int tab_clear_outcomes(tab_t h) {
 int tab_set_engine(tab_t h, int engine) {
   int rc = check_handle(h);
   if (rc) return rc;
-  if (engine < TAB_ENGINE_AUTO || engine > TAB_ENGINE_STREAM) {
+  if (engine != TAB_ENGINE_AUTO && engine != TAB_ENGINE_SINGLE_CTA &&
+      engine != TAB_ENGINE_GRID && engine != TAB_ENGINE_STREAM) {
     set_error("unknown engine %d", engine);
     return TAB_EINVAL;
   }
   if (engine == TAB_ENGINE_SINGLE_CTA && h->n > TAB_BATCH_MAX_QUBITS) {
     set_error("single-CTA engine needs n <= %d (n=%d)", TAB_BATCH_MAX_QUBITS, h->n);
-    return TAB_ERANGE;
-  }
-  if (engine == TAB_ENGINE_CLUSTER && cluster_size_for(h->n, h->Wh) == 0) {
-    set_error("the tableau (n=%d) does not fit one cluster's shared memory", h->n);
     return TAB_ERANGE;
   }
   h->engine = engine;
@@ -1402,13 +1323,7 @@ int handle_set_meas_ctas(tab_t h, int ctas) {
 size_t handle_device_bytes(int32_t n) { return tab_bytes_required(n); }
 
 // Compile forms a request of n qubits needs on a multi-CTA engine handle.
-int grid_compile_mode(int n) {
-  switch (gate_kernel(n)) {
-    case GK_BLOCK: return kProgBlocks;
-    case GK_FLOW: return kProgStream;
-    default: return kProgLayers;
-  }
-}
+int grid_compile_mode(int) { return kProgBlocks; }
 
 // Enqueue an already compiled program (the request server compiles at submit).
 int handle_apply_program(tab_t h, const HostProgram& hp) {

@@ -51,18 +51,15 @@ struct Seg {
   uint32_t blk_begin, blk_end;      // gates: block super-layers [blk_begin, blk_end)
 };
 
-// Compile forms of gate runs (build_program's mode, any combination):
+// Compile forms of gate runs (build_program's mode, either or both):
 //   kProgLayers  ASAP layers of gate codes (ops, layer_off): the single-CTA
-//                engine and the layer-barrier slab kernel;
+//                engine;
 //   kProgBlocks  two-qubit blocks in super-layers (blk, blk_off): the block
-//                gate kernel (blocks.cpp);
-//   kProgStream  program order with column versions (ops, vers): the
-//                dataflow gate kernel (exclusive with kProgLayers).
-enum : int { kProgLayers = 1, kProgBlocks = 2, kProgStream = 4 };
+//                gate kernel of the multi-CTA engines (blocks.cpp).
+enum : int { kProgLayers = 1, kProgBlocks = 2 };
 
 struct HostProgram {
   int32_t n = 0;
-  bool layered = true;  // gate runs grouped into ASAP layers (else program order)
   int mode = kProgLayers;
   int64_t n_gates = 0, n_meas = 0;
   // block records: lo = qa | qb<<14 | has_b<<28 | ent<<29 (0 none, 1 CNOT,
@@ -71,22 +68,16 @@ struct HostProgram {
   std::vector<uint2> blk;
   std::vector<uint32_t> blk_off;  // absolute record offsets of super-layer bounds
   std::vector<uint32_t> ops;
-  // per gate op: versions its qubits must have reached within the segment
-  // (count of earlier gates on each qubit, mod 2^16): q1 in bits 0..15, q2 in
-  // 16..31; zero for measurement ops
-  std::vector<uint32_t> vers;
   std::vector<uint32_t> layer_off;  // size = layers + 1 when any gate exists
   std::vector<Seg> segs;
   // empty program for n qubits (the arrays keep their capacity)
   void clear(int32_t n_) {
     n = n_;
-    layered = true;
     mode = kProgLayers;
     n_gates = n_meas = 0;
     blk.clear();
     blk_off.clear();
     ops.clear();
-    vers.clear();
     layer_off.clear();
     segs.clear();
   }
@@ -157,18 +148,11 @@ struct MeasWork {
 
 // ---- launches (kernels_*.cu) ---------------------------------------------------------
 void launch_init(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh, cudaStream_t s);
-int gates_max_n();
-int gates_flow_max_n();
-cudaError_t launch_gates_flow(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
-                              const uint2* rec, uint32_t rb, uint32_t re, int* err,
-                              cudaStream_t s);
-// Layers handed to launch_gates_slab hold at most kMaxLayerOps gates, and the
-// device op buffer extends at least kOpsPad codes past its last code.
+// Gate layers (single-CTA engine) and block super-layers hold at most
+// kMaxLayerOps entries; device op and record buffers extend at least kOpsPad
+// entries past their last one.
 constexpr int kMaxLayerOps = 2048;
 constexpr int kOpsPad = 1024;
-cudaError_t launch_gates_slab(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
-                              const uint32_t* ops, const uint32_t* layer_off,
-                              int nlayers, int* err, cudaStream_t s);
 // Block gate kernel: super-layers of at most kMaxLayerOps records, the
 // device record buffer padded by kOpsPad records past its end.
 int gates_block_max_n();
@@ -180,14 +164,7 @@ cudaError_t launch_measure(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh,
                            uint64_t cid, uint32_t shot, uint8_t* out, const MeasWork& mw,
                            int ctas, cudaStream_t s);
 int measure_ctas_for(int n, int sm_count, int max_ctas);
-// Cluster measurement engine (kernels_cluster.cu): cluster size for a tableau
-// of n qubits, or 0 when it does not fit in one cluster's shared memory.
-int cluster_size_for(int n, int Wh);
-cudaError_t launch_measure_cluster(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh,
-                                   const uint32_t* mops, int nm, uint64_t k0, uint64_t seed,
-                                   uint64_t cid, uint32_t shot, uint8_t* out, int* err, int C,
-                                   cudaStream_t s);
-// Grid-resident measurement engine (kernels_cluster.cu): CTA count for n
+// Grid-resident measurement engine (kernels_resident.cu): CTA count for n
 // qubits (0 if the tableau does not fit the GPU's shared memory), its global
 // workspace in words, and the launch.
 int resident_ctas_for(int n, int Wh, int sm_count);

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "TAB_OK", -1: "TAB_EINVAL", -2: "TAB_ERANGE", -3: "TAB_ENOMEM
                 -4: "TAB_ECUDA", -5: "TAB_EDEVICE", -6: "TAB_ETIMEOUT", -7: "TAB_ESTATE"}
 MAX_QUBITS = 16384
 NOALLOC_SCRATCH_BYTES = 1 << 20
-ENGINE_AUTO, ENGINE_SINGLE_CTA, ENGINE_GRID, ENGINE_CLUSTER, ENGINE_STREAM = 0, 1, 2, 3, 4
+ENGINE_AUTO, ENGINE_SINGLE_CTA, ENGINE_GRID, ENGINE_STREAM = 0, 1, 2, 4
 BATCH_MAX_QUBITS = 640
 
 if not os.path.exists(LIB_PATH):
@@ -118,6 +118,27 @@ _sig("tab_server_inject", ctypes.c_int, [_vp, _i64, ctypes.c_int])
 _sig("tab_server_stats_get", ctypes.c_int, [_vp, _P(TabServerStats)])
 _sig("tab_server_destroy", ctypes.c_int, [_vp])
 
+
+
+class TabPeaks(ctypes.Structure):
+    _fields_ = [("sms", _i32), ("sm_clock_mhz", ctypes.c_double),
+                ("logic_tops", ctypes.c_double), ("logic_ops_per_clk_sm", ctypes.c_double),
+                ("logic_ms", ctypes.c_double), ("smem_gbs", ctypes.c_double),
+                ("smem_bytes_per_clk_sm", ctypes.c_double), ("l2_read_gbs", ctypes.c_double),
+                ("l2_rw_gbs", ctypes.c_double), ("grid_barrier_us", ctypes.c_double)]
+
+
+_sig("tab_measure_peaks", ctypes.c_int, [_P(TabPeaks)])
+
+
+def measure_peaks() -> dict:
+    """Roofline ceilings of the current device (tab_measure_peaks): logic
+    ops/s, shared-memory and L2 bandwidth, grid-barrier latency."""
+    p = TabPeaks()
+    _check(_L.tab_measure_peaks(ctypes.byref(p)))
+    return {k: getattr(p, k) for k, _ in TabPeaks._fields_}
+
+
 REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 FAULT_DROP_COMPLETION = 1
 
@@ -175,6 +196,12 @@ class Program:
             self._h = None
 
     __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Tableau:
