@@ -1,27 +1,43 @@
 """Benchmark of the stabilizer-tableau hot path on GB300.
 
-Default workload (one "step" = the whole path once): a plain tableau of
-n = 1,000 qubits, reset to |0^n>, 1,000 random layers (H or S on every qubit,
-then n/2 random disjoint CNOT/CZ pairs, CNOT:CZ = 3:1), then a Z measurement
-of every qubit with Philox outcomes -- 1,500,000 gates and 1,000 measurements.
-Inputs are resident in device memory when timing starts (a compiled program);
-L2 is flushed (a 256 MB device write) before every timed step.
+Default workload (the batched family): 4,096 independent random-layer
+Clifford circuits, n ~ U{16..512}, depth n (H or S on every qubit, then n/2
+random disjoint CNOT/CZ pairs, CNOT:CZ = 3:1), 1-64 shots each, a final Z
+measurement of every qubit with Philox outcomes -- 5.5e8 gates (counted once
+per circuit) and 3.5e7 measurements (over all shots).  One "step" is one
+replay of the whole batch as one persistent launch (a CUDA graph), with the
+compiled batch resident in device memory when timing starts; the compiled
+batch (2.3 GB) is larger than L2, and L2 is flushed (a 256 MB device write)
+before every timed step anyway.
 
-Prints ONE JSON line.  `--impl reference` times the CPU oracle (an unpacked
-one-byte-per-bit restatement of the same algorithm) instead.  Under torchrun
-every rank runs an independent replica on its own GPU (weak scaling, no
-collective on the data path); rank 0 prints.
+The JSON line carries, beside the batched (per-shot) value:
+* the plain path: the same circuits one launch sequence per shot
+  (tab_run of a compiled program), timed on every 16th circuit and scaled;
+* the terminal-measurement sampler on the same batch (same outcome bytes);
+* e2e: tab_batch_run through the C ABI with host gate lists and a pinned host
+  output buffer (host compile, upload, run and the outcome copy per step);
+* the roofline of the batched kernel against the logic-op ceiling measured
+  live by tab_measure_peaks;
+* the n = 1,000 plain tableau (1,000 layers, 1,000 final measurements) as an
+  extra key;
+* cpu_baseline: the CPU oracle on (circuit, shot) runs drawn from the same
+  batch, on one core and on every core.
 
-Other workloads (`--workload`): `cfg1` (n=10), `cfg3` (n=10,000 with MZR
-rounds), `batched` (4,096 circuits with n in [16, 512] and 1-64 shots),
-`sweep` (the paper's own benchmark: uniformly random n-qubit Cliffords, no
-measurements, n = 2 ... 8192; one JSON line with a point per n), `extras`
-(the next-step features timed on their own: expectation values, the state
-vector export, the row-sharded tableau, noisy and X/Y-measured circuits).
+`--impl reference` times the CPU oracle (an unpacked one-byte-per-bit
+restatement of the same algorithm) on the same workload instead.  Under
+torchrun every rank runs an independent replica on its own GPU (weak scaling,
+no collective on the data path); rank 0 prints.
+
+Other workloads (`--workload`): `cfg1` (n=10), `cfg2` (the n=1,000 plain
+step), `cfg3` (n=10,000 with MZR rounds), `served` (Poisson request stream to
+the continuous-batching server), `sweep` (the paper's own benchmark: uniformly
+random n-qubit Cliffords, no measurements, n = 2 ... 8192; one JSON line with
+a point per n), `extras` (the next-step features timed on their own).
 """
 from __future__ import annotations
 
 import argparse
+import concurrent.futures as cf
 import json
 import os
 import statistics
@@ -39,34 +55,37 @@ METRIC = ("Clifford gates/sec and measurements/sec, batched vs plain path; "
           "p50/p99 latency")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-# INT32 logic lanes per SM (4 sub-partitions x 16) and SMs of a GB300: the
-# peak of the "alu" roofline is SMs x lanes x the SM clock sampled during the
-# timed region.
-ALU_LANES_PER_SM = 64
-GB300_SMS = 152
-# DRAM bytes (read + write) per launch of each kernel from one ncu capture of
-# this workload (profiles/); None once a kernel has changed since its capture.
-TRAFFIC_BYTES = {
-    "k_measure_resident": 582656 + 256,
-    "k_gates_block": 4540160,
-}
+
+# Algorithmic work per unit (a unit is one 32-row word of a touched column).
+# Logic ops of each gate rule per 32-row word: H 1, S 2, S^dag 2, Paulis 1,
+# CNOT 4, CZ 4, SWAP 0; a random-outcome measurement's rowsum costs 9 logic
+# ops per (column, 32-row word) on the columns where the pivot row is not I,
+# about 3/4 of the n columns.  A gate covers 2n/32 words of each column.
+GATE_OPS = {1: 1, 2: 1, 3: 1, 4: 1, 5: 2, 6: 2, 7: 4, 8: 4, 9: 0}
+MEAS_OPS_PER_UNIT = 9
+PIVOT_SUPPORT = 0.75
+# Bytes a random-outcome measurement of the streaming engine reads and writes:
+# ~3/4 n supported columns, X and Z planes, 2n/8 bytes each, read + written.
+# DRAM bytes (read + write) per launch from one ncu capture of the current
+# build, by kernel; None until a capture of the current build exists.
+TRAFFIC_BYTES = {}
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=50)
-    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="cfg2",
-                   choices=["cfg1", "cfg2", "cfg3", "batched", "served", "sweep", "extras"])
+    p.add_argument("--workload", default="batched",
+                   choices=["batched", "cfg1", "cfg2", "cfg3", "served", "sweep", "extras"])
     p.add_argument("--sweep-max", type=int, default=8192, help="sweep: largest n")
-    p.add_argument("--requests", type=int, default=48, help="served: number of requests")
+    p.add_argument("--requests", type=int, default=500, help="served: number of requests")
     p.add_argument("--circuits", type=int, default=4096, help="batched: number of circuits")
-    p.add_argument("--engine", default="auto",
-                   choices=["auto", "single", "grid", "stream"])
+    p.add_argument("--engine", default="auto", choices=["auto", "single", "grid", "stream"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="batched: skip the n=1000 key")
     return p.parse_args()
 
 
@@ -119,6 +138,22 @@ def workload(name, rank):
     return c, desc
 
 
+def batch_circuits(count, rank):
+    """The batched family's circuits (circuit ids offset by rank), generated
+    on all cores: each circuit has its own seeded generator, so the result
+    does not depend on the thread count."""
+    from workloads import circuits as C
+    idx = list(range(count))
+    chunks = [idx[i::32] for i in range(32)]
+    with cf.ThreadPoolExecutor(max_workers=min(32, os.cpu_count() or 1)) as ex:
+        parts = list(ex.map(lambda ch: C.config4(m=4096, only=ch), chunks))
+    circs = [None] * count
+    for ch, part in zip(chunks, parts):
+        for i, c in zip(ch, part):
+            circs[i] = c
+    return circs, [(c.n, c.gates, c.shots, c.circuit_id + 4096 * rank) for c in circs]
+
+
 def split_runs(c):
     """Maximal runs of gates and of measurements of a circuit, in program
     order: [("gates", words), ("measure", words), ...]."""
@@ -130,6 +165,19 @@ def split_runs(c):
     cuts = np.flatnonzero(np.diff(m.astype(np.int8))) + 1
     bounds = [0] + cuts.tolist() + [int(m.size)]
     return [("measure" if m[a] else "gates", c.gates[a:b]) for a, b in zip(bounds[:-1], bounds[1:])]
+
+
+def gate_ops(c):
+    """Logic ops of a circuit's gates (GATE_OPS per 32-row word, 2n/32 words)."""
+    from workloads import circuits as C
+    op, _, _ = C.decode(c.gates)
+    hist = np.bincount(op.astype(np.int64), minlength=16)
+    return (2.0 * c.n / 32.0) * float(sum(GATE_OPS.get(i, 0) * int(hist[i]) for i in range(16)))
+
+
+def meas_ops(n, count):
+    """Logic ops of `count` random-outcome measurements on n qubits."""
+    return count * MEAS_OPS_PER_UNIT * PIVOT_SUPPORT * n * (2.0 * n / 32.0)
 
 
 # ------------------------------------------------------------------ clocks --
@@ -189,12 +237,18 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- oracle ---
 
+def all_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def oracle_step_seconds(c, budget_s):
-    """Oracle seconds for one full step of circuit c, extrapolated from a
-    time-bounded sample: random layers are run one at a time for about half
-    the budget, then the circuit's measurement ops one at a time for the other
-    half; the full step is (seconds per layer x depth) + (seconds per
-    measurement x measurements)."""
+    """Oracle seconds (one core) for one full step of circuit c, extrapolated
+    from a time-bounded sample: random layers one at a time for about half
+    the budget, then the circuit's measurement ops one at a time for the
+    other half."""
     import oracle
     from workloads import circuits as C
     op, _, _ = C.decode(c.gates)
@@ -219,55 +273,169 @@ def oracle_step_seconds(c, budget_s):
     return est, sample
 
 
+def oracle_batch_rate(shapes, get_circuit, budget_s, threads, seed):
+    """The oracle as it stands on the batched family: (circuit, shot) pairs
+    drawn uniformly from all of the batch's pairs, each a full run from |0^n>
+    (gates, then the shot's measurements), on `threads` threads, new pairs
+    started while the elapsed time is under budget_s.  A circuit's gates
+    count once per circuit in the metric, so a shot is credited with
+    gates / shots (and its n measurements); the ratio of credited work to
+    elapsed time estimates the whole batch's rate.  Returns (gates/s,
+    meas/s, seconds, pairs done)."""
+    import oracle
+    from workloads import circuits as C
+    ns, shots = shapes
+    rng = np.random.default_rng(seed)
+    pair_c = np.repeat(np.arange(len(ns)), shots)
+    pair_s = np.concatenate([np.arange(s) for s in shots])
+    order = rng.permutation(pair_c.size)
+    cache = {}
+
+    def run_pair(i):
+        c = get_circuit(int(pair_c[i]), cache)
+        oracle.run_circuit(c.n, c.gates, seed=C.PHILOX_SEED, circuit_id=c.circuit_id,
+                           shot=int(pair_s[i]))
+        return c.n_gates / c.shots, c.n_meas
+
+    t0 = time.perf_counter()
+    credit_g = credit_m = 0.0
+    done = 0
+    nxt = 0
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        running = set()
+        while True:
+            while len(running) < threads and time.perf_counter() - t0 < budget_s \
+                    and nxt < order.size:
+                running.add(ex.submit(run_pair, order[nxt]))
+                nxt += 1
+            if not running:
+                break
+            fin, running = cf.wait(running, return_when=cf.FIRST_COMPLETED)
+            for f in fin:
+                g, m = f.result()
+                credit_g += g
+                credit_m += m
+                done += 1
+    dt = time.perf_counter() - t0
+    return credit_g / dt, credit_m / dt, dt, done
+
+
+def batch_circuit_getter(rank):
+    from workloads import circuits as C
+
+    def get(ci, cache):
+        if ci not in cache:
+            c = C.config4(m=4096, only=[ci])[0]
+            c.circuit_id += 4096 * rank
+            cache[ci] = c
+        return cache[ci]
+    return get
+
+
 # ------------------------------------------------------------- reference ---
 
 def run_reference(args, ws, rank):
     if rank != 0:
         return
-    c, desc = workload(args.workload if args.workload in ("cfg1", "cfg2", "cfg3") else "cfg2", 0)
-    budget = max(1.0, 150.0 / (args.steps + args.warmup))
-    for _ in range(args.warmup):
-        oracle_step_seconds(c, min(budget, 2.0))
-    times, samples = [], []
-    for _ in range(args.steps):
-        est, sample = oracle_step_seconds(c, budget)
-        times.append(est)
-        samples.append(sample)
-    ms = 1000.0 * statistics.mean(times)
-    value = c.n_gates / (ms / 1000.0)
+    from workloads import circuits as C
+    if args.workload in ("cfg1", "cfg2", "cfg3"):
+        c, desc = workload(args.workload, 0)
+        budget = max(1.0, 150.0 / (args.steps + args.warmup))
+        for _ in range(args.warmup):
+            oracle_step_seconds(c, min(budget, 2.0))
+        times, samples = [], []
+        for _ in range(args.steps):
+            est, sample = oracle_step_seconds(c, budget)
+            times.append(est)
+            samples.append(sample)
+        ms = 1000.0 * statistics.mean(times)
+        value, meas_s = c.n_gates / (ms / 1000.0), c.n_meas / (ms / 1000.0)
+        cores, sample = 1, samples[-1]
+        config = {"workload": desc, "n": c.n, "gates": c.n_gates, "measurements": c.n_meas}
+    else:
+        # the batched family: each step is a time-bounded sample of the
+        # batch's (circuit, shot) runs on every core; ms_per_step is the
+        # sample's own duration
+        shapes = C.config4_shapes()
+        cores = all_cores()
+        budget = min(12.0, max(2.0, 150.0 / (args.steps + args.warmup)))
+        get = batch_circuit_getter(0)
+        for w in range(args.warmup):
+            oracle_batch_rate(shapes, get, min(budget, 2.0), cores, seed=100 + w)
+        rates, durs, pairs = [], [], 0
+        for s in range(args.steps):
+            g, m, dt, done = oracle_batch_rate(shapes, get, budget, cores, seed=200 + s)
+            rates.append((g, m))
+            durs.append(dt)
+            pairs += done
+        value = statistics.mean(r[0] for r in rates)
+        meas_s = statistics.mean(r[1] for r in rates)
+        ms = 1000.0 * statistics.mean(durs)
+        sample = (f"{pairs} (circuit, shot) runs drawn uniformly from the batch's "
+                  f"{int(shapes[1].sum())}, {args.steps} steps of ~{budget:.0f} s on {cores} "
+                  "cores, each shot credited with its circuit's gates / shots")
+        config = {"workload": "batched: 4096 random-layer circuits, n ~ U[16,512], depth n, "
+                              "1-64 shots, final MZ on all qubits",
+                  "step": "a time-bounded sample of (circuit, shot) runs"}
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "gates/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "meas_per_s": c.n_meas / (ms / 1000.0),
-        "config": {"workload": desc, "n": c.n, "gates": c.n_gates,
-                   "measurements": c.n_meas},
-        "cpu_baseline": {"value": value, "unit": "gates/s", "cores": 1, "kind": "oracle",
-                         "sample": samples[-1]},
+        "meas_per_s": meas_s, "config": config,
+        "cpu_baseline": {"value": value, "unit": "gates/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": value, "unit": "gates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-# ------------------------------------------------------------------ ours ---
+# ----------------------------------------------------------------- peaks ---
 
-def peaks():
+def measured_hbm():
     try:
         with open(PEAKS_FILE) as f:
-            return json.load(f), "measured"
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
     except Exception:
-        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+        return FALLBACK_HBM_GBS, "fallback"
 
 
-def run_plain(args, ws, rank, local):
+def live_peaks():
+    """Ceilings of this GPU measured now (tab_measure_peaks) plus the
+    measured HBM copy bandwidth."""
+    from paper_2408_00384_gb300 import tab
+    pk = tab.measure_peaks()
+    pk["hbm_gbs"], pk["hbm_source"] = measured_hbm()
+    return pk
+
+
+def alu_roofline(kernel, ops, kernel_ms, pk, extra=None):
+    achieved = ops / (kernel_ms / 1000.0) / 1e12
+    roof = {"kernel": kernel, "bound": "alu", "unit": "Top/s", "achieved": achieved,
+            "peak": pk["logic_tops"], "frac": achieved / pk["logic_tops"],
+            "peak_source": (f"measured: lop3.b32 on {pk['sms']} SMs at "
+                            f"{pk['sm_clock_mhz']:.0f} MHz "
+                            f"({pk['logic_ops_per_clk_sm']:.1f} ops/clk/SM), tab_measure_peaks"),
+            "traffic": TRAFFIC_BYTES.get(kernel), "kernel_ms": kernel_ms,
+            "alg_ops_per_launch": ops}
+    if extra:
+        roof.update(extra)
+    return roof
+
+
+# ------------------------------------------------------------- plain path ---
+
+def run_plain(args, ws, rank, local, name=None, steps=None, warmup=None, cpu=True, pk=None):
     import torch
     from paper_2408_00384_gb300 import tab
     from workloads import circuits as C
 
+    name = name or args.workload
+    steps = steps or args.steps
+    warmup = warmup if warmup is not None else args.warmup
     torch.cuda.set_device(local)
-    c, desc = workload(args.workload, rank)
+    c, desc = workload(name, rank)
     runs = split_runs(c)
     stream = torch.cuda.Stream()
     t = tab.Tableau(c.n, stream=stream)
@@ -290,19 +458,21 @@ def run_plain(args, ws, rank, local):
             if evs:
                 evs[i + 1].record(stream)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     t.sync()
+    if pk is None:
+        pk = live_peaks()
     nprog = len(progs)
     all_evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nprog + 1)]
-               for _ in range(args.steps)]
+               for _ in range(steps)]
     launches0 = t.launches
     clocks = ClockSampler(local)
     clocks.start()
     barrier(ws)
     torch.cuda.synchronize()
-    for s in range(args.steps):
+    for s in range(steps):
         with torch.cuda.stream(stream):   # same stream as the timed work
             flush.fill_(s & 0xFF)
         step(all_evs[s])
@@ -311,11 +481,11 @@ def run_plain(args, ws, rank, local):
     clk = clocks.stop()
     t.sync()
     launches = t.launches - launches0
-    per_step = [all_evs[s][0].elapsed_time(all_evs[s][-1]) for s in range(args.steps)]
+    per_step = [all_evs[s][0].elapsed_time(all_evs[s][-1]) for s in range(steps)]
     per_kind = {}
     for k in set(kinds):
         per_kind[k] = [sum(all_evs[s][i].elapsed_time(all_evs[s][i + 1])
-                           for i, kk in enumerate(kinds) if kk == k) for s in range(args.steps)]
+                           for i, kk in enumerate(kinds) if kk == k) for s in range(steps)]
     ms_local = statistics.mean(per_step)
     ms = allreduce_max(ms_local, ws)
     value = ws * c.n_gates / (ms / 1000.0)
@@ -327,7 +497,7 @@ def run_plain(args, ws, rank, local):
         pinned = torch.from_numpy(c.gates.view(np.int64)).pin_memory()
         host_gates = pinned.numpy().view(np.uint64)
         out = np.zeros(c.n_meas, np.uint8)
-        ke = max(3, min(args.steps, 10))
+        ke = max(3, min(steps, 10))
         for i in range(ke + 2):
             if i == 2:
                 torch.cuda.synchronize()
@@ -351,61 +521,39 @@ def run_plain(args, ws, rank, local):
                "host_input_bytes_per_step": int(c.gates.nbytes),
                "ms_per_step": 1000.0 * e2e_s}
 
-    # ---- roofline of the dominant kernel.  Both kernels of this path keep
-    # the tableau on chip (the gate kernel a 32-row slab per CTA, the
-    # measurement kernel every column in some CTA's shared memory); DRAM
-    # carries only the program and one load/store of the tableau, so the bound
-    # is the integer logic the AG rules need, the "alu" roofline.
-    pk, src = peaks()
+    # ---- roofline of the dominant kernel
     kind_ms = {k: statistics.mean(v) for k, v in per_kind.items()}
     dom = max(kind_ms, key=kind_ms.get)
     n = c.n
-    words = 2.0 * n / 32.0  # 32-row words of the 2n tableau rows
     eng_res = t.engine_resolved()[0]
     if dom == "measure":
-        # a random-outcome measurement is a rowsum of row p into the rows of
-        # S' on every column where row p is not I (3/4 of the n columns for a
-        # random state); per such column and word: x ^= S, z ^= S (as row p
-        # has X / Z there) and the mod-4 exponent update, 6 logic ops
-        alg = 6.0 * 0.75 * n * words * c.n_meas
-        kname = {tab.ENGINE_SINGLE_CTA: "k_sct_program",
-                 tab.ENGINE_GRID: "k_measure_resident",
+        kname = {tab.ENGINE_SINGLE_CTA: "k_sct_program", tab.ENGINE_GRID: "k_measure_resident",
                  tab.ENGINE_STREAM: "k_measure"}[eng_res]
+        alg = meas_ops(n, c.n_meas)
     else:
-        # logic ops of each gate rule on one 32-row word (x, z, r):
-        # X/Z 1, Y 2, H 2, S 3, S^dag 3, CNOT 6, CZ 6, SWAP 0
-        opsof = {1: 1, 2: 2, 3: 1, 4: 2, 5: 3, 6: 3, 7: 6, 8: 6, 9: 0}
-        op, _, _ = C.decode(c.gates)
-        hist = np.bincount(op.astype(np.int64), minlength=16)
-        alg = words * float(sum(opsof.get(i, 0) * int(hist[i]) for i in range(16)))
         kname = "k_sct_program" if eng_res == tab.ENGINE_SINGLE_CTA else "k_gates_block"
-    sm_mhz = clk.get("sm_mhz") or 2070.0
+        alg = gate_ops(c)
     if kname == "k_measure":
         # the streaming engine sweeps the tableau in HBM/L2: a random
         # measurement reads and writes the ~3/4 n supported columns, 2 planes
-        # of 2n/8 bytes each, ~0.75 n^2 bytes
+        # of 2n/8 bytes each (~0.75 n^2 bytes); the tableau (n^2/2 bytes)
+        # fits GB300's L2 up to n ~ 16,000, so both ceilings are given
         alg_bytes = 0.75 * n * n * c.n_meas
         achieved = alg_bytes / (kind_ms[dom] / 1000.0) / 1e9
-        peak = pk.get("hbm_gbs", FALLBACK_HBM_GBS)
         roof = {"kernel": kname, "bound": "hbm", "unit": "GB/s", "achieved": achieved,
-                "peak": peak, "frac": achieved / peak,
-                "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)",
-                "traffic": TRAFFIC_BYTES.get(kname), "kernel_ms": kind_ms}
+                "peak": pk["hbm_gbs"], "frac": achieved / pk["hbm_gbs"],
+                "peak_source": pk["hbm_source"],
+                "l2": {"peak_gbs": pk["l2_rw_gbs"], "frac": achieved / pk["l2_rw_gbs"],
+                       "peak_source": "measured: read + write over a 64 MiB set, "
+                                      "tab_measure_peaks"},
+                "traffic": TRAFFIC_BYTES.get(kname), "kernel_ms": kind_ms,
+                "alg_bytes_per_launch": alg_bytes}
     else:
-        peak_tops = GB300_SMS * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e12
-        achieved = alg / (kind_ms[dom] / 1000.0) / 1e12
-        roof = {"kernel": kname, "bound": "alu", "unit": "Top/s", "achieved": achieved,
-                "peak": peak_tops, "frac": achieved / peak_tops,
-                "peak_source": f"{GB300_SMS} SMs x {ALU_LANES_PER_SM} INT32 lanes x {sm_mhz:.0f} "
-                               "MHz (unit counts and the sampled SM clock)",
-                "traffic": TRAFFIC_BYTES.get(kname),
-                "kernel_ms": kind_ms,
-                "hbm_peak_gbs": pk.get("hbm_gbs", FALLBACK_HBM_GBS),
-                "hbm_peak_source": src}
+        roof = alu_roofline(kname, alg, kind_ms[dom], pk, {"kernel_ms": kind_ms})
 
     line = {
         "metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "steps": steps, "warmup": warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32", "data": "synthetic",
         "meas_per_s": meas_s,
@@ -423,15 +571,19 @@ def run_plain(args, ws, rank, local):
         "roofline": roof,
         "e2e": e2e,
     }
-    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+    if cpu and rank == 0 and not args.no_cpu_baseline and ws == 1:
         est, sample = oracle_step_seconds(c, 12.0)
         line["cpu_baseline"] = {"value": c.n_gates / est, "unit": "gates/s", "cores": 1,
                                 "kind": "oracle", "sample": sample}
     elif rank == 0 and ws == 1:
         line["cpu_baseline"] = None
+    for p in progs:
+        p.close()
     t.close()
     return line
 
+
+# ---------------------------------------------------------- batched path ---
 
 def run_batched(args, ws, rank, local):
     import torch
@@ -439,9 +591,12 @@ def run_batched(args, ws, rank, local):
     from workloads import circuits as C
 
     torch.cuda.set_device(local)
-    circs = C.config4(only=list(range(args.circuits)) if args.circuits < 4096 else None)
-    circuits = [(c.n, c.gates, c.shots, c.circuit_id + 4096 * rank) for c in circs]
+    t_gen = time.perf_counter()
+    circs, circuits = batch_circuits(args.circuits, rank)
+    gen_s = time.perf_counter() - t_gen
+    t_c = time.perf_counter()
     b = tab.Batch(circuits)
+    compile_s = time.perf_counter() - t_c
     info = b.info()
     out = torch.empty(max(info["out_bytes"], 1), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.Stream()
@@ -452,6 +607,7 @@ def run_batched(args, ws, rank, local):
     for _ in range(args.warmup):
         b.exec(C.PHILOX_SEED, out.data_ptr(), stream)
     torch.cuda.synchronize()
+    pk = live_peaks()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     clocks = ClockSampler(local)
@@ -469,14 +625,15 @@ def run_batched(args, ws, rank, local):
     clk = clocks.stop()
     per = [a.elapsed_time(z) for a, z in evs]
     ms = allreduce_max(statistics.mean(per), ws)
+    n_gates, n_meas = info["n_gates"], info["n_meas"]
 
-    # plain one-circuit-per-launch path on a 1/64 sample of the same circuits
-    # (circuits are i.i.d., so 64 x the sample estimates the whole batch)
-    stride = 64
+    # ---- the plain one-circuit-per-launch path on every 16th circuit, all
+    # its shots (circuits are i.i.d., so 16 x the sample estimates the batch)
+    stride = 16
     plain_ms = 0.0
-    for c in circs[::stride]:
-        prog = tab.Program(c.n, c.gates)
-        with tab.Tableau(c.n, stream=stream) as t:
+    sample_g = sample_m = 0
+    for c, (_, _, _, cid) in zip(circs[::stride], circuits[::stride]):
+        with tab.Program(c.n, c.gates) as prog, tab.Tableau(c.n, stream=stream) as t:
             t.reset()
             t.run(prog)   # warm the engine's first-use set-up outside the timing
             e0 = torch.cuda.Event(enable_timing=True)
@@ -484,16 +641,18 @@ def run_batched(args, ws, rank, local):
             e0.record(stream)
             for shot in range(c.shots):
                 t.reset()
-                t.set_rng(C.PHILOX_SEED, c.circuit_id + 4096 * rank, shot)
+                t.set_rng(C.PHILOX_SEED, cid, shot)
                 t.run(prog)
             e1.record(stream)
             t.sync()
             plain_ms += e0.elapsed_time(e1)
-        prog.close()
-    plain_est_ms = plain_ms * stride
+        sample_g += c.n_gates
+        sample_m += c.n_meas * c.shots
+    plain_gps = sample_g / (plain_ms / 1000.0)
+    plain_mps = sample_m / (plain_ms / 1000.0)
 
-    # the terminal-measurement sampler on the same batch (reported apart from
-    # the per-shot numbers): same outcome bytes, checked here
+    # ---- the terminal-measurement sampler on the same batch (reported apart
+    # from the per-shot numbers): same outcome bytes, checked here
     sb = tab.Batch(circuits, sample_terminal=True)
     s_out = torch.empty_like(out)
     s_threads, _ = sb.tune(C.PHILOX_SEED, s_out.data_ptr(), stream)
@@ -512,35 +671,97 @@ def run_batched(args, ws, rank, local):
         s_evs[s][1].record(stream)
     torch.cuda.synchronize()
     s_ms = allreduce_max(statistics.mean(a.elapsed_time(z) for a, z in s_evs), ws)
-    sampler = {"ms_per_step": s_ms, "gates_per_s": ws * info["n_gates"] / (s_ms / 1000.0),
-               "meas_per_s": ws * info["n_meas"] / (s_ms / 1000.0),
+    sampler = {"ms_per_step": s_ms, "gates_per_s": ws * n_gates / (s_ms / 1000.0),
+               "meas_per_s": ws * n_meas / (s_ms / 1000.0),
                "circuits_sampled": sb.sampled, "threads": s_threads,
                "outcomes_equal_per_shot_run": same,
                "note": "terminal measurements run once per circuit with affine sign forms, "
                        "every shot evaluated from its Philox bits"}
     sb.close()
+
+    # ---- end to end: tab_batch_run with host gate lists and a pinned host
+    # output buffer (host compile, upload, run, outcome copy) per step
+    e2e = None
+    if not args.no_e2e:
+        host_out = torch.empty(max(info["out_bytes"], 1), dtype=torch.uint8).pin_memory().numpy()
+        ke = 2
+        tab.batch_run(circuits, C.PHILOX_SEED, out=host_out)   # warm-up
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            tab.batch_run(circuits, C.PHILOX_SEED, out=host_out)
+        e2e_s = allreduce_max((time.perf_counter() - t0) / ke, ws)
+        same_e2e = bool(np.array_equal(host_out[:info["out_bytes"]],
+                                       out.cpu().numpy()[:info["out_bytes"]]))
+        e2e = {"value": ws * n_gates / e2e_s, "unit": "gates/s",
+               "h2d_bytes_per_step": int(b.h2d_bytes), "d2h_bytes_per_step": int(info["out_bytes"]),
+               "host_input_bytes_per_step": int(sum(c.gates.nbytes for c in circs)),
+               "ms_per_step": 1000.0 * e2e_s, "meas_per_s": ws * n_meas / e2e_s,
+               "outcomes_equal_device_run": same_e2e,
+               "call": "tab_batch_run (compile on the host pool, upload, one persistent "
+                       "launch, outcome copy to pinned host memory)"}
+
+    # ---- roofline of the batched kernel: every circuit's gates once, every
+    # shot's measurements counted as random-outcome rowsums
+    ops = sum(gate_ops(c) + c.shots * meas_ops(c.n, c.n_meas) for c in circs)
+    roof = alu_roofline("k_batch", ops, statistics.mean(per), pk,
+                        {"smem_gbs_peak": pk["smem_gbs"],
+                         "note": "per-shot tableaus live in shared memory; the compiled batch "
+                                 "streams from HBM once per step"})
+
     line = {
-        "metric": METRIC, "value": ws * info["n_gates"] / (ms / 1000.0), "unit": "gates/s",
+        "metric": METRIC, "value": ws * n_gates / (ms / 1000.0), "unit": "gates/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic", "meas_per_s": ws * info["n_meas"] / (ms / 1000.0),
-        "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99))},
+        "data": "synthetic", "meas_per_s": ws * n_meas / (ms / 1000.0),
+        "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99)),
+                       "unit": "per batch replay"},
         "config": {"workload": f"batched: {len(circs)} random-layer circuits, n ~ U[16,512], "
                                "depth n, 1-64 shots, final MZ on all qubits",
-                   "gates": info["n_gates"], "measurements": info["n_meas"],
-                   "l2": "flushed before every timed step (256 MB device write)",
-                   "launch": launch,
+                   "gates": n_gates, "measurements": n_meas, "parallelism": f"replicas x{ws}",
+                   "l2": "flushed before every timed step (256 MB device write); the compiled "
+                         "batch is larger than L2",
+                   "launch": launch, "generate_s": gen_s, "compile_s": compile_s,
                    "autotune": {"threads": tuned_threads, "best_run_ms": tuned_ms,
                                 "tried": "128/256/512/1024 threads per CTA, one full run each"}},
-        "gpu_launches": b.launches * args.steps, "clocks": clk, "roofline": None, "e2e": None,
-        "plain_path": {"ms_estimated": plain_est_ms,
-                       "gates_per_s": info["n_gates"] / (plain_est_ms / 1000.0),
-                       "meas_per_s": info["n_meas"] / (plain_est_ms / 1000.0),
-                       "sample": f"every {stride}th circuit, all its shots, one launch "
-                                 "sequence per shot, CUDA events, x{stride}",
-                       "batched_speedup": plain_est_ms / ms},
+        "gpu_launches": b.launches * args.steps, "clocks": clk, "roofline": roof,
+        "e2e": e2e,
+        "plain_path": {"gates_per_s": ws * plain_gps, "meas_per_s": ws * plain_mps,
+                       "ms_estimated": n_gates / plain_gps * 1000.0,
+                       "sample": f"every {stride}th circuit ({len(circs[::stride])}), all its "
+                                 "shots, one tab_run per shot, CUDA events",
+                       "batched_speedup": (n_gates / plain_gps * 1000.0) / ms},
         "sampler": sampler,
+        "peaks": pk,
     }
+    b.close()
+    del out, flush
+    torch.cuda.empty_cache()
+    if not args.no_extras:
+        p = run_plain(args, ws, rank, local, name="cfg2", steps=10, warmup=3, cpu=False, pk=pk)
+        line["cfg2"] = {k: p[k] for k in ("value", "unit", "ms_per_step", "meas_per_s",
+                                          "latency_ms", "roofline", "e2e", "gpu_launches")}
+        line["cfg2"]["workload"] = p["config"]["workload"]
+        line["gpu_launches"] += p["gpu_launches"]
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        shapes = (np.array([c.n for c in circs]), np.array([c.shots for c in circs]))
+
+        def get(ci, cache):
+            return circs[ci]
+        g1, m1, d1, n1 = oracle_batch_rate(shapes, get, 8.0, 1, seed=7)
+        cores = all_cores()
+        ga, ma, da, na = oracle_batch_rate(shapes, get, 8.0, cores, seed=8)
+        line["cpu_baseline"] = {
+            "value": ga, "unit": "gates/s", "cores": cores, "kind": "oracle",
+            "meas_per_s": ma,
+            "sample": f"{na} (circuit, shot) runs drawn uniformly from the batch in {da:.1f} s "
+                      f"on {cores} threads, each a full oracle run, each shot credited with "
+                      "its circuit's gates / shots",
+            "single_core": {"value": g1, "meas_per_s": m1, "cores": 1,
+                            "sample": f"{n1} runs in {d1:.1f} s on one core"}}
+    elif rank == 0 and ws == 1:
+        line["cpu_baseline"] = None
     return line
 
 
@@ -557,7 +778,8 @@ def run_served(args, ws, rank, local):
 
     torch.cuda.set_device(local)
     t_gen = time.perf_counter()
-    reqs = [C.config5_request(c + 100000 * rank) for c in range(args.requests)]
+    with cf.ThreadPoolExecutor(max_workers=min(32, os.cpu_count() or 1)) as ex:
+        reqs = list(ex.map(lambda c: C.config5_request(c + 100000 * rank), range(args.requests)))
     print(f"[served] generated {len(reqs)} requests in {time.perf_counter() - t_gen:.1f} s",
           file=sys.stderr, flush=True)
     gates_total = sum(r.n_gates for r in reqs)
@@ -578,8 +800,6 @@ def run_served(args, ws, rank, local):
                 tickets.append((srv.submit(r.n, r.gates, 1, r.circuit_id), time.perf_counter()))
             for i, ((tk, ts), r) in enumerate(zip(tickets, reqs)):
                 rc, out, l = srv.wait(tk, timeout_s=300.0)
-                print(f"[served] request {i} n={r.n} done in {l:.3f} s", file=sys.stderr,
-                      flush=True)
                 if rc != tab.TAB_OK or out.size != r.n_meas:
                     raise RuntimeError(f"request failed: {rc} {tab.last_error()}")
                 lat.append(l)

@@ -15,10 +15,13 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <numeric>
+#include <string>
 #include <vector>
 
+#include "pool.h"
 #include "sct.h"
 #include "tab_internal.h"
 #include "trace.h"
@@ -37,6 +40,7 @@ using namespace tab;
 struct tab_batch_s {
   int m = 0;
   int64_t n_gates = 0, n_meas = 0, out_bytes = 0;
+  int64_t h2d_bytes = 0;                    // compiled tables copied to the device
   int max_n = 1;
   bool sample = false;                      // terminal measurements by the sampler
   int nsampled = 0;
@@ -72,12 +76,6 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
     set_error("bad circuit array");
     return TAB_EINVAL;
   }
-  std::vector<uint32_t> ops, layer_off;
-  std::vector<Seg> segs;
-  std::vector<BatchCirc> circs((size_t)m);
-  std::vector<double> pre_cost((size_t)m), shot_cost((size_t)m);
-  uint64_t img_words = 0;
-  int64_t out_packed = 0, out_max = 0;
   for (int32_t c = 0; c < m; ++c) {
     const tab_circuit& tc = circuits[c];
     if (tc.n < 1 || tc.n > TAB_BATCH_MAX_QUBITS) {
@@ -88,19 +86,52 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
       set_error("circuit %d: shots=%d < 1", c, tc.shots);
       return TAB_EINVAL;
     }
-    HostProgram hp;
-    int rc = build_program(tc.n, tc.gates, tc.n_gates, &hp);
-    if (rc != TAB_OK) {
-      char msg[600];
-      snprintf(msg, sizeof msg, "circuit %d: %s", c, tab_last_error());
-      set_error("%s", msg);
-      return rc;
+  }
+  // ---- compile every circuit on the host pool (circuits claimed one at a
+  // time: their sizes differ by orders of magnitude); the error message is
+  // per thread, so a failing circuit keeps its own
+  std::vector<HostProgram> progs((size_t)m);
+  std::vector<int> rcs((size_t)m, TAB_OK);
+  std::vector<std::string> msgs((size_t)m);
+  {
+    std::atomic<int> next{0};
+    pool_run(pool_threads(), [&](int) {
+      for (;;) {
+        const int c = next.fetch_add(1);
+        if (c >= m) break;
+        const tab_circuit& tc = circuits[c];
+        rcs[(size_t)c] = build_program(tc.n, tc.gates, tc.n_gates, &progs[(size_t)c]);
+        if (rcs[(size_t)c] != TAB_OK) msgs[(size_t)c] = tab_last_error();
+      }
+    });
+  }
+  for (int32_t c = 0; c < m; ++c)
+    if (rcs[(size_t)c] != TAB_OK) {
+      set_error("circuit %d: %s", c, msgs[(size_t)c].c_str());
+      return rcs[(size_t)c];
     }
-    const uint32_t op_base = (uint32_t)ops.size(), lo_base = (uint32_t)layer_off.size();
+  // ---- offsets of each circuit in the concatenated tables (in order)
+  std::vector<size_t> o_ops((size_t)m + 1, 0), o_lo((size_t)m + 1, 0), o_seg((size_t)m + 1, 0);
+  for (int32_t c = 0; c < m; ++c) {
+    const HostProgram& hp = progs[(size_t)c];
+    o_ops[(size_t)c + 1] = o_ops[(size_t)c] + hp.ops.size();
+    o_lo[(size_t)c + 1] = o_lo[(size_t)c] + hp.layer_off.size();
+    o_seg[(size_t)c + 1] = o_seg[(size_t)c] + hp.segs.size();
+  }
+  std::vector<uint32_t> ops(o_ops[(size_t)m]), layer_off(o_lo[(size_t)m]);
+  std::vector<Seg> segs(o_seg[(size_t)m]);
+  std::vector<BatchCirc> circs((size_t)m);
+  std::vector<double> pre_cost((size_t)m), shot_cost((size_t)m);
+  uint64_t img_words = 0;
+  int64_t out_packed = 0, out_max = 0;
+  for (int32_t c = 0; c < m; ++c) {
+    const tab_circuit& tc = circuits[c];
+    const HostProgram& hp = progs[(size_t)c];
     BatchCirc& bc = circs[(size_t)c];
     bc.n = tc.n;
     bc.shots = tc.shots;
-    bc.seg_begin = (uint32_t)segs.size();
+    bc.seg_begin = (uint32_t)o_seg[(size_t)c];
+    bc.seg_end = (uint32_t)o_seg[(size_t)c + 1];
     bc.n_prefix = (!hp.segs.empty() && hp.segs[0].kind == 0) ? 1u : 0u;
     bc.n_meas = (uint32_t)hp.n_meas;
     bc.cid = tc.circuit_id;
@@ -128,28 +159,44 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
     bc.out_off = (uint64_t)(out_offsets ? out_offsets[c] : out_packed);
     out_packed += span;
     out_max = std::max<int64_t>(out_max, (int64_t)bc.out_off + span);
-    ops.insert(ops.end(), hp.ops.begin(), hp.ops.end());
-    for (uint32_t v : hp.layer_off) layer_off.push_back(v + op_base);
     double pre = 0, rest = 0;
     const double wc = 2.0 * ((tc.n + 31) / 32);
     for (size_t i = 0; i < hp.segs.size(); ++i) {
-      Seg s = hp.segs[i];
+      const Seg& s = hp.segs[i];
       const double len = (double)(s.op_end - s.op_begin);
       if (s.kind == 0) (i == 0 && bc.n_prefix ? pre : rest) += len * wc + (s.layer_end - s.layer_begin) * 8.0;
       else rest += len * (double)tc.n * wc;
-      s.op_begin += op_base;
-      s.op_end += op_base;
-      s.layer_begin += lo_base;
-      s.layer_end += lo_base;
-      segs.push_back(s);
     }
-    bc.seg_end = (uint32_t)segs.size();
     // a sampled circuit is one item: prefix, one terminal pass, every shot
     pre_cost[(size_t)c] = bc.sampled ? pre + rest + (double)tc.shots * hp.n_meas : pre;
     shot_cost[(size_t)c] = rest;
     B->n_gates += hp.n_gates;
     B->n_meas += span;
     B->max_n = std::max(B->max_n, tc.n);
+  }
+  // ---- fill the concatenated tables, circuits in parallel
+  {
+    std::atomic<int> next{0};
+    pool_run(pool_threads(), [&](int) {
+      for (;;) {
+        const int c = next.fetch_add(1);
+        if (c >= m) break;
+        HostProgram& hp = progs[(size_t)c];
+        const uint32_t op_base = (uint32_t)o_ops[(size_t)c], lo_base = (uint32_t)o_lo[(size_t)c];
+        std::copy(hp.ops.begin(), hp.ops.end(), ops.begin() + (ptrdiff_t)op_base);
+        for (size_t i = 0; i < hp.layer_off.size(); ++i)
+          layer_off[lo_base + i] = hp.layer_off[i] + op_base;
+        for (size_t i = 0; i < hp.segs.size(); ++i) {
+          Seg sg = hp.segs[i];
+          sg.op_begin += op_base;
+          sg.op_end += op_base;
+          sg.layer_begin += lo_base;
+          sg.layer_end += lo_base;
+          segs[o_seg[(size_t)c] + i] = sg;
+        }
+        hp = HostProgram();  // release this circuit's arrays
+      }
+    });
   }
   B->m = m;
   B->out_bytes = out_max;
@@ -178,6 +225,8 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
   const size_t b_img = a256(img_words * 4 + 16);
   B->ctl_bytes = a256(16 + (size_t)m * 4 + 4);
   const size_t total = b_circs + b_segs + b_ops + b_lo + b_items + b_img + B->ctl_bytes;
+  B->h2d_bytes = (int64_t)(circs.size() * sizeof(BatchCirc) + segs.size() * sizeof(Seg) +
+                           ops.size() * 4 + layer_off.size() * 4 + items.size() * 8);
   if (cudaMalloc(&B->dmem, total) != cudaSuccess) {
     cudaGetLastError();
     set_error("cudaMalloc of %zu bytes for the batch failed", total);
@@ -309,6 +358,15 @@ int tab_batch_info(tab_batch_t B, int64_t* n_gates, int64_t* n_meas, int64_t* ou
   if (n_gates) *n_gates = B->n_gates;
   if (n_meas) *n_meas = B->n_meas;
   if (out_bytes) *out_bytes = B->out_bytes;
+  return TAB_OK;
+}
+
+int tab_batch_h2d_bytes(tab_batch_t B, int64_t* bytes) {
+  if (!B || !bytes) {
+    set_error("null argument");
+    return TAB_EINVAL;
+  }
+  *bytes = B->h2d_bytes;
   return TAB_OK;
 }
 
