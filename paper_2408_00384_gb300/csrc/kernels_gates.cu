@@ -260,14 +260,8 @@ int gates_block_max_n() { return (kMaxSmemBytes - 4096 - kBlkRing * 8) / 8; }
 // blocks in a full layer) keeps its barrier cheap: 128, 256 or 512 threads.
 // TAB_BLOCK_THREADS overrides (tuning sweeps).
 static int block_threads(int n) {
-  static const int forced = [] {  // read once (thread-safe initialisation)
-    if (const char* e = getenv("TAB_BLOCK_THREADS")) {
-      const int v = atoi(e);
-      if (v == 128 || v == 256 || v == 512) return v;
-    }
-    return 0;
-  }();
-  if (forced) return forced;
+  const int forced = run_config().block_threads;
+  if (forced == 128 || forced == 256 || forced == 512) return forced;
   return n <= 256 ? 128 : n <= 512 ? 256 : 512;
 }
 

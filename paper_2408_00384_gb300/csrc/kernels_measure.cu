@@ -51,6 +51,7 @@ struct MArgs {
   uint32_t* ph;  // [G][2][W]
   uint32_t* r4;  // [2][W]
   uint32_t* dp;  // [2][G]
+  unsigned long long wait_ns;  // limit of each grid-barrier wait
   GridBar* bar;
   int* err;
 };
@@ -83,6 +84,7 @@ __device__ int det_outcome_warp(const uint32_t* dp, int G) {
 }
 
 __global__ void __launch_bounds__(kMeasThreads) k_measure(MArgs A) {
+  unsigned int epoch = 0;  // grid barriers passed (grid_sync)
   extern __shared__ uint32_t smem[];
   const int G = gridDim.x, c = blockIdx.x, tid = threadIdx.x;
   const int n = A.n, Wh = A.Wh, W = A.W, Q = W / 4;
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(kMeasThreads) k_measure(MArgs A) {
   for (int m = 0; m < A.nm; ++m) {
     const uint32_t code = next_code;
     if (m + 1 < A.nm) next_code = __ldg(A.mops + m + 1);
-    if (m > 0 && !grid_sync(A.bar, A.err)) return;
+    if (m > 0 && !grid_sync(A.bar, A.err, epoch, A.wait_ns)) return;
     // ---- resolve the previous deterministic outcome (needs every CTA's partial)
     if (prev_det) {
       const uint32_t* dbuf = A.dp + (size_t)((m - 1) & 1) * G;
@@ -364,7 +366,7 @@ __global__ void __launch_bounds__(kMeasThreads) k_measure(MArgs A) {
 
   // ---- epilogue: resolve the last deterministic outcome, materialize the
   // deferred column, fold the partial signs into R
-  if (!grid_sync(A.bar, A.err)) return;
+  if (!grid_sync(A.bar, A.err, epoch, A.wait_ns)) return;
   if (prev_det) {
     const uint32_t* dbuf = A.dp + (size_t)((A.nm - 1) & 1) * G;
     const bool owner = (prev_a % G) == c;
@@ -387,7 +389,7 @@ __global__ void __launch_bounds__(kMeasThreads) k_measure(MArgs A) {
     for (int w = tid; w < W; w += blockDim.x)
       xc[w] = (w == (pend_pd >> 5)) ? (1u << (pend_pd & 31)) : 0u;
   }
-  if (!grid_sync(A.bar, A.err)) return;
+  if (!grid_sync(A.bar, A.err, epoch, A.wait_ns)) return;
   for (int w = c * blockDim.x + tid; w < W; w += G * blockDim.x) {
     uint32_t L = __ldcg(R4lo + w), H = __ldcg(R4hi + w);
     for (int cc = 0; cc < G; ++cc) {
@@ -432,6 +434,7 @@ cudaError_t launch_measure(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh,
   A.k0 = k0; A.seed = seed; A.cid = cid; A.shot = shot;
   A.out = out;
   A.ph = mw.ph; A.r4 = mw.r4; A.dp = mw.dp; A.bar = mw.bar; A.err = mw.err;
+  A.wait_ns = run_wait_limit_ns();
   const size_t smem = meas_smem_bytes(n, A.W, ctas);
   cudaError_t e = ensure_smem_limit((const void*)k_measure, 200 * 1024);
   if (e != cudaSuccess) return e;

@@ -13,8 +13,9 @@
 //    so each counted op is exactly one instruction), 2 CTAs of 1,024 threads
 //    per SM.  The SM clock over the run is read from clock64 against the
 //    global timer on CTA 0, so ops per SM per clock follow as well.
-//  * shared memory: 128-bit ld.shared.v4 of consecutive 16-byte chunks per
-//    warp (no bank conflicts), XOR-accumulated so the loads stay live.
+//  * shared memory: 128-bit ld.volatile.shared.v4 of consecutive 16-byte
+//    chunks per warp (no bank conflicts), a new address every load,
+//    XOR-accumulated so the loads stay live.
 //  * L2: 128-bit ld.global.cg (cached in L2 only) over a 64 MiB buffer, which
 //    fits GB300's L2, read-only and read-modify-write, many passes in one
 //    launch after a warm-up pass.
@@ -68,15 +69,18 @@ __global__ void __launch_bounds__(kPeakThreads, 2) k_peak_smem(int iters, uint32
   for (int i = threadIdx.x; i < kSmemWords; i += blockDim.x) buf[i] = i * 0x27D4EB2Fu;
   __syncthreads();
   const uint32_t base = (uint32_t)__cvta_generic_to_shared(buf);
+  constexpr uint32_t kMask = kSmemWords * 4u - 1u;  // 32 KB, a power of two
   uint32_t x0 = 0, x1 = 0, x2 = 0, x3 = 0;
-  // each warp reads 512 consecutive bytes per load: 4 conflict-free wavefronts
-  uint32_t off = (threadIdx.x * 16u) % (kSmemWords * 4u);
+  // each warp reads 512 consecutive bytes per load (4 conflict-free
+  // wavefronts); the address moves every load, and the loads are volatile
+  // so none is merged with another
+  uint32_t off = threadIdx.x * 16u;
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       uint32_t v0, v1, v2, v3;
-      const uint32_t addr = base + ((off + u * kPeakThreads * 16u) % (kSmemWords * 4u));
-      asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+      const uint32_t addr = base + ((off + u * 4112u) & kMask);
+      asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
                    : "=r"(v0), "=r"(v1), "=r"(v2), "=r"(v3)
                    : "r"(addr));
       x0 ^= v0;
@@ -84,7 +88,7 @@ __global__ void __launch_bounds__(kPeakThreads, 2) k_peak_smem(int iters, uint32
       x2 ^= v2;
       x3 ^= v3;
     }
-    off = (off + 8u * kPeakThreads * 16u) % (kSmemWords * 4u);
+    off += 528u;
   }
   if ((x0 ^ x1 ^ x2 ^ x3) == 0x2545F491u) sink[0] = x0;
 }
@@ -108,8 +112,9 @@ __global__ void k_peak_l2(const uint4* __restrict__ src, uint4* __restrict__ dst
 }
 
 __global__ void k_peak_barrier(GridBar* bar, int* err, int rounds) {
+  unsigned int epoch = 0;
   for (int i = 0; i < rounds; ++i)
-    if (!grid_sync(bar, err)) return;
+    if (!grid_sync(bar, err, epoch)) return;
 }
 
 }  // namespace tab
@@ -232,6 +237,7 @@ extern "C" int tab_measure_peaks(tab_peaks* out) {
       void* args0[] = {&bar, &err, &warm};
       e = cudaLaunchCooperativeKernel((const void*)k_peak_barrier, dim3(sms), dim3(256), args0, 0,
                                       s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(bar, 0, sizeof(GridBar), s);  // counter restarts
       if (e == cudaSuccess) cudaEventRecord(t.a, s);
       if (e == cudaSuccess)
         e = cudaLaunchCooperativeKernel((const void*)k_peak_barrier, dim3(sms), dim3(256), args1,

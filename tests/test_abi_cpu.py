@@ -61,3 +61,24 @@ def test_gate_word_layout_matches_header():
     for name in ("I", "X", "Y", "Z", "H", "S", "SDG", "CNOT", "CZ", "SWAP", "MZ", "MZR", "BARRIER"):
         m = re.search(rf"TAB_{name}\s*=\s*(\d+)", src)
         assert m and int(m.group(1)) == getattr(C, f"TAB_{name}"), name
+
+
+def test_run_config_validation_without_gpu(lib):
+    """tab_set_config rejects out-of-range fields and changes nothing then;
+    a valid change reads back and can be undone (host logic, no GPU)."""
+    from paper_2408_00384_gb300 import tab
+    old = tab.get_config()
+    for bad in ({"block_threads": 100}, {"meas_batch": 3}, {"meas_batch": 64},
+                {"grid_ctas": -1}, {"debug": 1 << 7}):
+        with pytest.raises(tab.TabError) as ei:
+            tab.set_config(bad)
+        assert ei.value.code == tab.TAB_EINVAL
+        assert tab.get_config() == old
+    try:
+        tab.set_config({"block_threads": 256, "meas_batch": 8, "wait_limit_ns": 123456})
+        got = tab.get_config()
+        assert got["block_threads"] == 256 and got["meas_batch"] == 8
+        assert got["wait_limit_ns"] == 123456
+    finally:
+        tab.set_config(old)
+    assert tab.get_config() == old
