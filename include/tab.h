@@ -361,6 +361,10 @@ int tab_batch_info(tab_batch_t b, int64_t *n_gates, int64_t *n_meas, int64_t *ou
 /* Enqueue one run of the whole batch on cuda_stream: outcomes (packed back to
  * back per circuit and shot) go to dev_out (device memory, >= out_bytes). */
 int tab_batch_exec(tab_batch_t b, uint64_t seed, uint8_t *dev_out, void *cuda_stream);
+/* Bytes of compiled tables (circuit descriptors, segments, gate codes, layer
+ * offsets, work items) the batch copied host -> device when it was created;
+ * tab_batch_run copies the same amount per call. */
+int tab_batch_h2d_bytes(tab_batch_t b, int64_t *bytes);
 /* Number of kernels one tab_batch_exec launches. */
 int tab_batch_launches(tab_batch_t b, int64_t *count);
 /* Autotuner: runs the whole batch once per CTA shape the persistent kernel is
@@ -433,6 +437,31 @@ int tab_server_inject(tab_server_t s, int64_t ticket, int kind);
 int tab_server_stats_get(tab_server_t s, tab_server_stats *out);
 /* Finish every submitted request, then stop the worker and free the server. */
 int tab_server_destroy(tab_server_t s);
+
+/* ---- run-time configuration (process-wide) ------------------------------
+ * Launch-shape knobs (0 = the library's choice by size), the limit of the
+ * device-side grid-barrier waits, and test-only fault injection.  The
+ * paper has no counterpart.  Initial values come from the environment
+ * (TAB_BLOCK_THREADS, TAB_MEAS_BATCH, TAB_GRID_CTAS), read on first use.
+ * tab_set_config applies to launches issued after it returns; grid_ctas
+ * applies to handles created after it.  TAB_EINVAL (nothing changed) for an
+ * out-of-range field. */
+typedef struct {
+  int32_t block_threads;  /* block gate kernel threads per CTA: 0, 128, 256, 512 */
+  int32_t meas_batch;     /* grid-resident engine measurements per batch: 0 or 1..32 (power of 2) */
+  int32_t grid_ctas;      /* grid-resident engine CTAs: 0 = one per SM */
+  uint32_t debug;         /* TAB_DEBUG_* bits */
+  uint64_t wait_limit_ns; /* limit of each grid-barrier wait in the measurement
+                             engines; 0 = 2 s.  A wait that runs out latches a
+                             device error reported as TAB_ETIMEOUT */
+} tab_config;
+/* Test-only: in every grid-resident measurement launch the last CTA skips its
+ * first grid-barrier arrival and leaves, so the other CTAs' bounded waits run
+ * out (TAB_ETIMEOUT at the next synchronizing call).  Nothing hangs or
+ * faults: every CTA returns once its wait has run out. */
+#define TAB_DEBUG_SKIP_BARRIER_ARRIVAL 1u
+int tab_get_config(tab_config *out);
+int tab_set_config(const tab_config *cfg);
 
 /* ---- roofline ceilings of the current device ---------------------------
  * The paper has no counterpart: these are the ceilings the kernels above are

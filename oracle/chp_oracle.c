@@ -171,7 +171,7 @@ static void for_rows(orc_tab *t, orc_rows_fn fn, void *arg, int64_t nrows) {
   if (lo < hi) fn(t, arg, lo, hi);
   long spins = 0;
   while (atomic_load_explicit(&p->done, memory_order_acquire) != p->threads - 1)
-    if (++spins > (1L << 12)) sched_yield();
+    if (++spins > (1L << 18)) sched_yield();
 }
 
 /* Use `threads` threads (>= 1) for this tableau's row loops. */

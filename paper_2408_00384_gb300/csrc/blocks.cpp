@@ -144,6 +144,43 @@ void BlockBuilder::add(uint32_t op, uint32_t a, uint32_t b) {
   }
 }
 
+// Within one super-layer, reorder each kind group's records so that every
+// aligned window of 32 records (the records one warp takes together) reads
+// its first qubits, and its second qubits, from 32 distinct shared-memory
+// banks: distinct qa mod 32 and, among two-qubit blocks, distinct qb mod 32.
+// The blocks of a super-layer act on disjoint qubits and commute, so any
+// order gives the same tableau; groups stay contiguous (warp-uniform paths).
+// Greedy: each window slot takes the first record within kScan of the
+// group's remaining records that fits the window, else the next one.
+static void bank_order(uint2* recs, const uint32_t* group_size, int ngroups) {
+  constexpr size_t kScan = 64;
+  uint32_t used_a = 0u, used_b = 0u;
+  int slot = 0;
+  size_t at = 0;
+  for (int g = 0; g < ngroups; ++g) {
+    uint2* G = recs + at;
+    const size_t size = group_size[g];
+    for (size_t k = 0; k < size; ++k) {
+      size_t pick = k;
+      for (size_t j = k; j < size && j < k + kScan; ++j) {
+        const uint32_t qa = G[j].x & 31u, qb = (G[j].x >> 14) & 31u, two = (G[j].x >> 28) & 1u;
+        if (!((used_a >> qa) & 1u) && !(two && ((used_b >> qb) & 1u))) {
+          pick = j;
+          break;
+        }
+      }
+      std::swap(G[k], G[pick]);
+      used_a |= 1u << (G[k].x & 31u);
+      if ((G[k].x >> 28) & 1u) used_b |= 1u << ((G[k].x >> 14) & 31u);
+      if (++slot == 32) {
+        slot = 0;
+        used_a = used_b = 0u;
+      }
+    }
+    at += size;
+  }
+}
+
 // Emit the run's blocks, grouped by super-layer and, inside one, by kind
 // (single- or two-qubit, entangler, whether the U codes are identities, and
 // the class -- identity, H, S or other -- of each V code) so that the threads
@@ -213,6 +250,7 @@ void BlockBuilder::emit(HostProgram& P, Seg& s) {
   for (int32_t L = 0; L < top; ++L) {
     uint32_t sz = 0;
     for (int t = 0; t < kKinds; ++t) sz += cnt[(size_t)L * kKinds + t];
+    bank_order(P.blk.data() + run, cnt.data() + (size_t)L * kKinds, kKinds);
     while (sz > (uint32_t)kMaxLayerOps) {
       run += kMaxLayerOps;
       sz -= kMaxLayerOps;

@@ -18,15 +18,8 @@ namespace tab {
 // Measurements per batch: TAB_MEAS_BATCH (1, 2, 4, ..., 32) caps it for
 // tuning sweeps; the default is the largest that fits.
 static int batch_cap() {
-  static int cap = 0;
-  if (cap == 0) {
-    cap = kBatchMax;
-    if (const char* e = getenv("TAB_MEAS_BATCH")) {
-      const int v = atoi(e);
-      if (v >= 1 && v <= kBatchMax && (v & (v - 1)) == 0) cap = v;
-    }
-  }
-  return cap;
+  const int v = run_config().meas_batch;
+  return v >= 1 && v <= kBatchMax ? v : kBatchMax;
 }
 
 
@@ -36,6 +29,7 @@ struct CommGrid {
   static constexpr bool kPush = false;
   const ResArgs& A;
   int C, r;
+  unsigned int epoch = 0;  // grid barriers passed (grid_sync)
   __device__ explicit CommGrid(const ResArgs& a) : A(a), C((int)gridDim.x), r((int)blockIdx.x) {}
   __device__ int size() const { return C; }
   __device__ int rank() const { return r; }
@@ -43,7 +37,12 @@ struct CommGrid {
     __syncthreads();
     return true;
   }
-  __device__ bool sync() { return grid_sync(A.bar, A.err); }
+  // test-only fault injection: the last CTA leaves without arriving, so the
+  // others' bounded wait runs out
+  __device__ bool sync() {
+    if (A.skip_arrival && r == C - 1) return false;
+    return grid_sync(A.bar, A.err, epoch, A.wait_ns);
+  }
   // owners write the measured columns (their current state) to stage[buf]
   __device__ void stage_columns(const ResSmem& s, int buf, const ResBatch& b, int W, int Wp,
                                 int KB) {
@@ -79,7 +78,7 @@ struct CommGrid {
         A.r4[W + w] = s.R4hi[w];
       }
     }
-    if (!grid_sync(A.bar, A.err)) return false;
+    if (!grid_sync(A.bar, A.err, epoch, A.wait_ns)) return false;
     for (int w = r * (int)blockDim.x + threadIdx.x; w < W; w += C * (int)blockDim.x) {
       uint32_t L = __ldcg(A.r4 + w), H = __ldcg(A.r4 + W + w);
       for (int t = 0; t < C; ++t)
@@ -93,7 +92,7 @@ struct CommGrid {
 };
 
 template <int WL>
-__global__ void __launch_bounds__(32 * res_warps(WL)) k_measure_resident(ResArgs A) {
+__global__ void __launch_bounds__(32 * kResMaxWarps) k_measure_resident(const __grid_constant__ ResArgs A) {
   extern __shared__ __align__(16) uint32_t sm[];
   CommGrid cm(A);
   measure_resident<WL>(A, cm, sm);
@@ -157,11 +156,7 @@ static ResArgs res_args(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh, co
 // more CTAs there are, and the per-batch barrier costs about the same -- or
 // TAB_GRID_CTAS if set and the share fits (tuning sweeps).
 int resident_ctas_for(int n, int Wh, int sm_count) {
-  static int pref = -1;
-  if (pref < 0) {
-    pref = 0;
-    if (const char* e = getenv("TAB_GRID_CTAS")) pref = atoi(e);
-  }
+  const int pref = run_config().grid_ctas;
   const int wl = res_words_per_lane(Wh);
   if (wl == 0) return 0;
   if (ensure_smem_limit(resident_kernel(wl), res_dyn_limit()) != cudaSuccess) {
@@ -192,8 +187,20 @@ cudaError_t launch_measure_resident(uint32_t* X, uint32_t* Z, uint32_t* R, int n
   if (fn == nullptr) return cudaErrorInvalidValue;
   ResArgs A = res_args(X, Z, R, n, Wh, mops, nm, k0, seed, cid, shot, out, err);
   const int W = 2 * Wh;
-  A.kb = res_batch_for(n, Wh, G, res_dyn_limit(), std::min(batch_cap(), res_warps(wl)), false);
+  A.kb = res_batch_for(n, Wh, G, res_dyn_limit(), std::min(batch_cap(), res_batch_cap(wl)), false);
   if (A.kb == 0) return cudaErrorInvalidValue;
+  // replay warps: enough for the batch's columns; apply warps: one column
+  // each where the CTA's warp budget allows, at most 32 columns each
+  const int cpr = res_cols_per_replay(wl);
+  A.nreplay = (A.kb + cpr - 1) / cpr;
+  const int nown = (n + G - 1) / G;
+  int napply = std::min(nown, kResMaxWarps - A.nreplay);
+  napply = std::max(napply, (nown + 31) / 32);
+  napply = std::max(1, std::min(napply, kResMaxWarps - A.nreplay));
+  if ((nown + napply - 1) / napply > 32) return cudaErrorInvalidValue;
+  A.napply = napply;
+  A.wait_ns = run_wait_limit_ns();
+  A.skip_arrival = (run_config().debug & TAB_DEBUG_SKIP_BARRIER_ARRIVAL) ? 1 : 0;
   A.stage = work;
   A.dp = A.stage + 4 * (size_t)A.kb * W;
   A.ph = A.dp + 2 * (size_t)A.kb * G;
@@ -202,8 +209,8 @@ cudaError_t launch_measure_resident(uint32_t* X, uint32_t* Z, uint32_t* R, int n
   cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBar), s);
   if (e != cudaSuccess) return e;
   void* args[] = {&A};
-  return cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(32 * res_warps(wl)), args,
-                                     res_layout(n, Wh, G, A.kb, false).words * 4, s);
+  return cudaLaunchCooperativeKernel(fn, dim3((unsigned)G), dim3(32 * (A.nreplay + A.napply)),
+                                     args, res_layout(n, Wh, G, A.kb, false).words * 4, s);
 }
 
 }  // namespace tab

@@ -48,7 +48,7 @@ __host__ __device__ inline size_t sct_smem_words(int n, int threads) {
   int GG = threads / Wc;
   if (GG < 1) GG = 1;
   if (GG > n) GG = n;
-  return (size_t)2 * n * sct_wp(n) + 2 * (size_t)Wc + (size_t)n + 2 * (size_t)GG * Wc;
+  return (size_t)2 * n * sct_wp(n) + 2 * (size_t)Wc + 3 * (size_t)n + 2 * (size_t)GG * Wc;
 }
 
 size_t sct_smem_bytes(int n, int threads) { return sizeof(uint32_t) * sct_smem_words(n, threads); }
@@ -64,7 +64,7 @@ size_t sct_sampler_bytes(int n, int K, int shots) {
 
 struct Sct {
   int n, Whc, Wc, Wp, GG;
-  uint32_t *X, *Z, *R, *sS, *supp, *redlo, *redhi;
+  uint32_t *X, *Z, *R, *sS, *supp, *redlo, *redhi;  // supp: [3][n] (X, Z, Y columns)
 };
 
 __device__ __forceinline__ void sct_setup(Sct& s, uint32_t* base, int n) {
@@ -80,7 +80,7 @@ __device__ __forceinline__ void sct_setup(Sct& s, uint32_t* base, int n) {
   s.R = s.Z + (size_t)n * s.Wp;
   s.sS = s.R + s.Wc;
   s.supp = s.sS + s.Wc;
-  s.redlo = s.supp + n;
+  s.redlo = s.supp + 3 * n;
   s.redhi = s.redlo + (size_t)s.GG * s.Wc;
 }
 
@@ -156,7 +156,7 @@ __device__ void sct_gates(const Sct& s, const uint32_t* __restrict__ ops,
 // Measure Z_a (code = MZ / MZR on qubit a) with pre-drawn bit rbit.  Returns
 // the outcome (same value in every thread).
 __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err) {
-  __shared__ int s_pw, s_nsupp, s_kc;
+  __shared__ int s_pw, s_nx, s_nz, s_kc;
   __shared__ uint32_t s_acc;
   const int tid = threadIdx.x, T = blockDim.x;
   const int a = (int)dq1(code);
@@ -169,7 +169,8 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err)
     const uint32_t bal = __ballot_sync(0xffffffffu, v != 0u);
     if (tid == 0) {
       s_pw = bal ? Whc + __ffs(bal) - 1 : -1;
-      s_nsupp = 0;
+      s_nx = 0;
+      s_nz = 0;
       s_kc = 0;
       s_acc = 0u;
     }
@@ -184,59 +185,79 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err)
     const uint32_t bpm = 1u << (P & 31);
     const uint32_t rp = (s.R[wp] & bpm) ? 1u : 0u;
     const int lane = tid & 31;
+    // row p on every column: the columns where it is X, Z or Y go to three
+    // lists (warp-aggregated appends).  Rows p-n and p are rewritten here, on
+    // every column (row p-n := row p, row p := Z_a): the rowsum below leaves
+    // both rows alone (S' excludes them), and their exponent counters are
+    // never read.
+    uint32_t* lX = s.supp;
+    uint32_t* lZ = s.supp + n;
+    uint32_t* lY = s.supp + 2 * n;
     for (int j0 = tid - lane; j0 < n; j0 += T) {  // warp-uniform trip count
       const int j = j0 + lane;
       uint32_t xp = 0u, zp = 0u;
       if (j < n) {
-        const uint32_t xw = s.X[(size_t)j * Wp + wp], zw = s.Z[(size_t)j * Wp + wp];
-        xp = (xw & bpm) ? 1u : 0u;
-        zp = (zw & bpm) ? 1u : 0u;
+        uint32_t* xc = s.X + (size_t)j * Wp;
+        uint32_t* zc = s.Z + (size_t)j * Wp;
+        xp = (xc[wp] & bpm) ? 1u : 0u;
+        zp = (zc[wp] & bpm) ? 1u : 0u;
+        xc[wd] = (xc[wd] & ~bpm) | (xp ? bpm : 0u);
+        zc[wd] = (zc[wd] & ~bpm) | (zp ? bpm : 0u);
+        xc[wp] &= ~bpm;
+        zc[wp] = (zc[wp] & ~bpm) | ((j == a) ? bpm : 0u);
       }
-      // warp-aggregated append to the support list (one shared atomic per warp)
-      const uint32_t in = __ballot_sync(0xffffffffu, (xp | zp) != 0u);
-      const uint32_t yy = __ballot_sync(0xffffffffu, (xp & zp) != 0u);
-      int base = 0;
-      if (lane == 0 && in) {
-        base = atomicAdd(&s_nsupp, __popc(in));
-        if (yy) atomicAdd(&s_kc, __popc(yy));
+      const uint32_t bx = __ballot_sync(0xffffffffu, xp & ~zp);
+      const uint32_t bz = __ballot_sync(0xffffffffu, ~xp & zp);
+      const uint32_t by = __ballot_sync(0xffffffffu, xp & zp);
+      int ox = 0, oz = 0, oy = 0;
+      if (lane == 0) {
+        if (bx) ox = atomicAdd(&s_nx, __popc(bx));
+        if (bz) oz = atomicAdd(&s_nz, __popc(bz));
+        if (by) oy = atomicAdd(&s_kc, __popc(by));
       }
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (xp | zp) {
-        s.supp[base + __popc(in & ((1u << lane) - 1u))] = (uint32_t)j | (xp << 30) | (zp << 31);
-      } else if (j < n) {  // row p is I here: row p-n := row p clears this bit
-        s.X[(size_t)j * Wp + wd] &= ~bpm;
-        s.Z[(size_t)j * Wp + wd] &= ~bpm;
-      }
+      ox = __shfl_sync(0xffffffffu, ox, 0);
+      oz = __shfl_sync(0xffffffffu, oz, 0);
+      oy = __shfl_sync(0xffffffffu, oy, 0);
+      const uint32_t lt = (1u << lane) - 1u;
+      if (xp & ~zp) lX[ox + __popc(bx & lt)] = (uint32_t)j;
+      if (~xp & zp) lZ[oz + __popc(bz & lt)] = (uint32_t)j;
+      if (xp & zp) lY[oy + __popc(by & lt)] = (uint32_t)j;
     }
     __syncthreads();
-    const int nsupp = s_nsupp;
+    const int nx = s_nx, nz = s_nz, ny = s_kc;
     const int g = tid / Wc, w = tid - g * Wc;
     if (g < s.GG) {
+      // per row h of this word: rows in S' (x_ha = 1, h != p, p-n) take
+      // row p into them; the exponent counter (lo, hi) adds, per column,
+      //   X: +1 if x z, -1 if !x z         Z: +1 if x z, -1 if x !z, +2 if x
+      //   Y: +1 if x z, -1 if !x !z, +2 if x
+      // (the terms of 2 r_h' above with row p's bits fixed); rows outside S'
+      // get counts too, but only S' rows are read
       uint32_t lo = 0u, hi = 0u;
       uint32_t Sw = s.sS[w];
       if (w == wp || w == wd) Sw &= ~bpm;  // S' excludes rows p and p-n
-      for (int idx = g; idx < nsupp; idx += s.GG) {
-        const uint32_t e = s.supp[idx];
-        const int j = (int)(e & 0x3FFFu);
-        const uint32_t XP = (e & (1u << 30)) ? 0xffffffffu : 0u;
-        const uint32_t ZP = (e & (1u << 31)) ? 0xffffffffu : 0u;
-        const size_t i = (size_t)j * Wp + w;
+      for (int idx = g; idx < nx; idx += s.GG) {
+        const size_t i = (size_t)lX[idx] * Wp + w;
         const uint32_t x = s.X[i], z = s.Z[i];
-        const uint32_t A0 = x & z, B0 = (x ^ XP) & (z ^ ZP);
-        const uint32_t inc = A0 & ~B0, dec = B0 & ~A0;
-        hi ^= ((lo & inc) | (~lo & dec)) ^ (ZP & x);
-        lo ^= inc | dec;
-        uint32_t xn = x ^ (XP & Sw), zn = z ^ (ZP & Sw);
-        if (w == wd) {  // row p-n := row p
-          xn = (xn & ~bpm) | (XP & bpm);
-          zn = (zn & ~bpm) | (ZP & bpm);
-        }
-        if (w == wp) {  // row p := Z_a
-          xn &= ~bpm;
-          zn = (zn & ~bpm) | ((j == a) ? bpm : 0u);
-        }
-        s.X[i] = xn;
-        s.Z[i] = zn;
+        hi ^= z & ~(x ^ lo);
+        lo ^= z;
+        s.X[i] = x ^ Sw;
+      }
+      for (int idx = g; idx < nz; idx += s.GG) {
+        const size_t i = (size_t)lZ[idx] * Wp + w;
+        const uint32_t x = s.X[i], z = s.Z[i];
+        hi ^= x & (z ^ lo);
+        lo ^= x;
+        s.Z[i] = z ^ Sw;
+      }
+      for (int idx = g; idx < ny; idx += s.GG) {
+        const size_t i = (size_t)lY[idx] * Wp + w;
+        const uint32_t x = s.X[i], z = s.Z[i];
+        const uint32_t e = ~(x ^ z);
+        hi ^= (e & ~(x ^ lo)) ^ x;
+        lo ^= e;
+        s.X[i] = x ^ Sw;
+        s.Z[i] = z ^ Sw;
       }
       s.redlo[g * Wc + w] = lo;
       s.redhi[g * Wc + w] = hi;

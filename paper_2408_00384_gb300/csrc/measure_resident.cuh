@@ -34,28 +34,25 @@
 // on X|Z bits (never on signs or outcomes), and the pivot and the mask of rows
 // with x_ha = 1 of measurement m depend only on the measured columns.  So a
 // batch of K consecutive measurements runs in two overlapping phases:
-//   phase 1: the measured columns of the batch (pushed or staged by their
-//            owners at the end of the previous batch) are replayed through
-//            the K measurements, one warp per column, in registers, until the
+//   phase 1: the measured columns of the batch (staged by their owners at
+//            the end of the previous batch) are replayed through the K
+//            measurements in the registers of the CTA's R replay warps, each
+//            holding up to res_cols_per_replay(WL) columns, until each
 //            column's last measurement in the batch; one named barrier per
-//            measurement among the warps still replaying.  The warp whose
-//            column measurement m measures publishes its pivot p_m and mask
-//            S_m (the measured column at that time) with a release store of a
-//            counter;
-//   phase 2: every warp that owns columns applies the K rowsums, in order, to
-//            its columns and its share, each as soon as the counter shows it
-//            published (an acquire load, a bounded wait) -- a warp leaves
-//            phase 1 and starts phase 2 at once, so the two overlap.
-// One CTA barrier and one cluster/grid barrier per batch.  A deterministic
+//            measurement among the replay warps still running (a __syncwarp
+//            when R = 1).  The warp holding the column measurement m measures
+//            publishes its pivot p_m and mask S_m (the measured column at that
+//            time) with a release store of a counter;
+//   phase 2: the CTA's A apply warps, each owning a contiguous block of the
+//            CTA's columns, apply the K rowsums, in order, to their columns
+//            and their shares, each as soon as the counter shows it published
+//            (an acquire load, a bounded wait); the replay and apply warps
+//            run concurrently.
+// One CTA barrier and one grid barrier per batch.  A deterministic
 // measurement with reset ends its batch (its outcome, needed for the reset,
-// is only known once every share is summed).
-//
-// The communication policy decides how batches meet:
-//   CommCluster -- one thread-block cluster: owners push the next batch's
-//                  columns into every CTA's shared memory over DSMEM, and the
-//                  hardware cluster barrier publishes them;
-//   CommGrid    -- a cooperative grid: owners stage the next batch's columns
-//                  in global memory (L2), bounded software grid barrier.
+// is only known once every share is summed).  The communication policy
+// (CommGrid, kernels_resident.cu) stages the next batch's columns in global
+// memory (L2) and meets at a bounded software grid barrier.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -66,12 +63,25 @@
 
 namespace tab {
 
-// Warps per CTA: 32 (1,024 threads) while the register share is small
-// (W <= 128 words, n <= 2,048), else 16; batches hold at most one measured
-// column per warp (phase 1).
-__host__ __device__ constexpr int res_warps(int wl) { return wl <= 4 ? 32 : 16; }
+// Warp roles.  R replay warps (phase 1), each holding up to
+// res_cols_per_replay(WL) measured columns of the batch in registers (8, 4,
+// 2, 1 for 2, 4, 8, 16 words per lane: 32 registers of columns), then A apply
+// warps (phase 2), each owning at most 32 of the CTA's columns (one ballot);
+// R + A <= kResMaxWarps.  The host picks R from the batch size and A from the
+// CTA's columns, one column per apply warp where that fits
+// (kernels_resident.cu): the work of one measurement is a short dependent
+// chain per warp, so several warps per SM hide each other's latency.
+constexpr int kResMaxWarps = 16;
+constexpr int kResMaxReplay = 8;
 constexpr int kBatchMax = 32;                       // largest batch of any instance
-constexpr int kResMaxLocalCols = 32 * 16;           // a warp's columns fit one ballot
+__host__ __device__ constexpr int res_cols_per_replay(int wl) { return wl >= 16 ? 1 : 16 / wl; }
+// Largest batch the replay warps hold for WL words per lane.
+__host__ __device__ constexpr int res_batch_cap(int wl) {
+  return kResMaxReplay * res_cols_per_replay(wl) < kBatchMax
+             ? kResMaxReplay * res_cols_per_replay(wl)
+             : kBatchMax;
+}
+constexpr int kResMaxLocalCols = 32 * (kResMaxWarps - 1);  // columns of one CTA
 constexpr int kPubSpinMax = 1 << 22;              // polls (64 ns apart) before a wait gives up
 
 struct ResArgs {
@@ -84,6 +94,9 @@ struct ResArgs {
   uint8_t* out;
   int* err;
   int kb;  // measurements per batch (1..kBatchMax)
+  int nreplay, napply;  // replay warps R, apply warps A (blockDim = 32 (R + A))
+  unsigned long long wait_ns;  // limit of each grid-barrier wait
+  int skip_arrival;            // test-only fault injection (TAB_DEBUG_SKIP_BARRIER_ARRIVAL)
   // CommGrid workspace (global memory)
   uint32_t* stage;  // [2][kb][2][W] measured columns of the next batch
   uint32_t* dp;     // [2][kb][C] deterministic partials
@@ -201,7 +214,10 @@ struct ResBatch {
   int lw[kBatchMax];         // warp of this CTA owning that column, or -1
   int q[kBatchMax];          // qubit of each slot
   int last[kBatchMax];       // last measurement of each slot
-  int cnt[kBatchMax];        // slots still live at each measurement (replaying warps)
+  int cntw[kBatchMax];       // replay warps still running at each measurement
+  int wlast[kResMaxReplay];  // last measurement each replay warp takes part in
+  uint32_t wlive[kResMaxReplay][kBatchMax];  // replay warp w, measurement i: its columns
+                                             // still needed after i (bit j: slot w*CPR+j)
   int own[kBatchMax];        // slots whose column this CTA owns
   int P[kBatchMax];          // pivot row of each measurement (-1: deterministic)
   uint32_t dacc[kBatchMax];  // this CTA's deterministic partial
@@ -215,10 +231,12 @@ struct ResBatch {
 
 // Slots of a batch of K <= 32 measurements, lane i holding code i: distinct
 // measured qubits in first-occurrence order, each slot's last measurement,
-// the slots live at each measurement, and the slots, columns and warps this
-// CTA owns.  Warp-wide (one warp).
+// the replay warp (R of them, cpr slots each) that holds each slot and when
+// each replay warp's columns are still needed, and the slots, columns and
+// apply warps (warp R + local column / cpw) this CTA owns.  Warp-wide (one
+// warp).
 __device__ __forceinline__ void res_batch_slots(uint32_t code, int K, int C, int r, int cpw,
-                                                ResBatch& b) {
+                                                int R, int cpr, ResBatch& b) {
   const int lane = threadIdx.x & 31;
   const bool v = lane < K;
   const int a = v ? (int)dq1(code) : -1 - lane;
@@ -235,30 +253,56 @@ __device__ __forceinline__ void res_batch_slots(uint32_t code, int K, int C, int
     b.code[lane] = code;
     b.slot[lane] = slot;
     b.la[lane] = la;
-    b.lw[lane] = (la >= 0 && cpw > 0) ? la / cpw : -1;
+    b.lw[lane] = (la >= 0 && cpw > 0) ? R + la / cpw : -1;
   }
   if (lead) {
     b.q[slot] = a;
     b.last[slot] = lastv;
   }
   __syncwarp();
-  if (v) {  // slots whose last measurement is at or after this one
-    const int D = __popc(firsts);
+  const int D = __popc(firsts);
+  if (lane < R) {
+    int wl = -1;
+    for (int d = lane * cpr; d < D && d < (lane + 1) * cpr; ++d) wl = b.last[d] > wl ? b.last[d] : wl;
+    b.wlast[lane] = wl;
+  }
+  if (v) {  // columns of each replay warp still needed after measurement `lane`
+    for (int w = 0; w < R; ++w) {
+      uint32_t live = 0u;
+      for (int j = 0; j < cpr; ++j) {
+        const int d = w * cpr + j;
+        if (d < D && b.last[d] > lane) live |= 1u << j;
+      }
+      b.wlive[w][lane] = live;
+    }
+  }
+  __syncwarp();
+  if (v) {
     int cnt = 0;
-    for (int d = 0; d < D; ++d) cnt += b.last[d] >= lane;
-    b.cnt[lane] = cnt;
+    for (int w = 0; w < R; ++w) cnt += b.wlast[w] >= lane;
+    b.cntw[lane] = cnt;
   }
   if (mine) b.own[__popc(owned & ((1u << lane) - 1u))] = slot;
   if (lane == 0) {
-    b.D = __popc(firsts);
+    b.D = D;
     b.nown = __popc(owned);
   }
 }
 
+// Column j of a replay warp's register block (j warp-uniform).
+template <int CPR, int WL>
+__device__ __forceinline__ uint32_t res_pick_col(const uint32_t (&t)[CPR][WL], int j, int k) {
+  uint32_t o = 0u;
+#pragma unroll
+  for (int c = 0; c < CPR; ++c) o |= t[c][k] & (0u - (uint32_t)(c == j));
+  return o;
+}
+
 template <int WL, class Comm>
 __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
-  constexpr int NW = res_warps(WL);
+  constexpr int CPR = res_cols_per_replay(WL);
   constexpr bool kPush = Comm::kPush;
+  const int R = A.nreplay, NA = A.napply;
   const int C = cm.size(), r = cm.rank(), tid = threadIdx.x, T = blockDim.x;
   const int n = A.n, Wh = A.Wh, W = 2 * Wh, KB = A.kb;
   const ResLayout Ly = res_layout(n, Wh, C, KB, kPush);
@@ -266,10 +310,11 @@ __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
   const int nown = (n - r + C - 1) / C;  // columns owned: r, r+C, ...
   const ResSmem s = res_smem(sm, Ly, W, KB, kPush);
   const int lane = tid & 31, warp = tid >> 5;
-  const int cpw = (nown + NW - 1) / NW;  // this warp's local columns: c0 .. c0+ncw-1
-  const int c0 = warp * cpw;
-  const int ncw = nown - c0 < 0 ? 0 : (nown - c0 < cpw ? nown - c0 : cpw);
-  const bool base_warp = (r == 0 && warp == 0);
+  const int cpw = (nown + NA - 1) / NA;  // an apply warp's local columns: c0 .. c0+ncw-1
+  const int av = warp - R;                 // apply-warp index (negative: a replay warp)
+  const int c0 = av * cpw;
+  const int ncw = (av < 0 || nown - c0 < 0) ? 0 : (nown - c0 < cpw ? nown - c0 : cpw);
+  const bool base_warp = (r == 0 && warp == R);
   const uint32_t lt = (1u << lane) - 1u;
   __shared__ ResBatch b;
 
@@ -292,7 +337,7 @@ __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
   if (warp == 0) {
     const int K0 = A.nm < KB ? A.nm : KB;
     const uint32_t c = lane < K0 ? __ldg(A.mops + lane) : 0u;
-    res_batch_slots(c, K0, C, r, cpw, b);
+    res_batch_slots(c, K0, C, r, cpw, R, CPR, b);
     if (lane == 0) b.anydet = 0;
   }
   if (!cm.start()) return;
@@ -325,7 +370,7 @@ __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
       // added to the share of the warp that owns column a
       if (b.ptype[prev_count - 1] && b.det[prev_count - 1] && dop(b.plast) == OP_MZR) {
         const int pa = (int)dq1(b.plast);
-        if (pa % C == r && (pa / C) / cpw == warp) {
+        if (pa % C == r && R + (pa / C) / cpw == warp) {
           const uint32_t* zc = s.Zs + (size_t)(pa / C) * Wp;
 #pragma unroll
           for (int k = 0; k < WL; ++k) {
@@ -342,32 +387,41 @@ __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
     }
     __syncthreads();
 
-    // ---- phase 1: replay the batch on its measured columns, warp d holding
-    // slot d's column in registers until that column's last measurement; the
-    // owner of measurement i publishes its mask S_i and pivot P_i
+    // ---- phase 1: replay the batch on its measured columns, replay warp w
+    // holding slots w*CPR .. w*CPR+CPR-1 in registers until their last
+    // measurement; the holder of measurement i's column publishes its mask
+    // S_i and pivot P_i
     const int D = b.D;
-    if (warp < D) {
-      uint32_t tx[WL], tz[WL];
+    if (warp < R && warp * CPR < D) {
+      const int s0 = warp * CPR;
+      uint32_t tx[CPR][WL], tz[CPR][WL];
 #pragma unroll
-      for (int k = 0; k < WL; ++k) {
-        const int w = lane + 32 * k;
-        tx[k] = w < W ? cm.slot_word(s, par, warp, w, 0, W, KB) : 0u;
-        tz[k] = w < W ? cm.slot_word(s, par, warp, w, 1, W, KB) : 0u;
+      for (int j = 0; j < CPR; ++j) {
+#pragma unroll
+        for (int k = 0; k < WL; ++k) {
+          const int w = lane + 32 * k;
+          const bool ok = s0 + j < D && w < W;
+          tx[j][k] = ok ? cm.slot_word(s, par, s0 + j, w, 0, W, KB) : 0u;
+          tz[j][k] = ok ? cm.slot_word(s, par, s0 + j, w, 1, W, KB) : 0u;
+        }
       }
-      const int qd = b.q[warp], lastd = b.last[warp];
-      for (int i = 0; i <= lastd; ++i) {
+      const int wlast = b.wlast[warp];
+      for (int i = 0; i <= wlast; ++i) {
         const uint32_t code = b.code[i];
-        if (b.slot[i] == warp) {
+        const int si = b.slot[i];
+        if (si >= s0 && si < s0 + CPR) {
+          const int jj = si - s0;
           uint32_t* Si = s.SM + (size_t)i * W;
           int P = -1;
 #pragma unroll
           for (int k = 0; k < WL; ++k) {
             const int w = lane + 32 * k;
-            if (w < W) Si[w] = tx[k];
-            const uint32_t bal = __ballot_sync(0xffffffffu, w >= Wh && w < W && tx[k] != 0u);
+            const uint32_t v = res_pick_col<CPR, WL>(tx, jj, k);
+            if (w < W) Si[w] = v;
+            const uint32_t bal = __ballot_sync(0xffffffffu, w >= Wh && w < W && v != 0u);
             if (P < 0 && bal) {
               const int l = __ffs(bal) - 1;
-              const uint32_t word = __shfl_sync(0xffffffffu, tx[k], l);
+              const uint32_t word = __shfl_sync(0xffffffffu, v, l);
               P = (32 * k + l) * 32 + __ffs(word) - 1;
             }
           }
@@ -378,28 +432,48 @@ __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
           __syncwarp();
           if (lane == 0) res_st_release(&b.npub, i + 1);
         }
-        res_named_sync(1, 32 * b.cnt[i]);
+        if (R > 1)
+          res_named_sync(1, 32 * b.cntw[i]);
+        else
+          __syncwarp();
         const int P = b.P[i];
         if (P < 0) {  // deterministic: X|Z unchanged; with reset the batch ends
           if (dop(code) == OP_MZR) break;
           continue;
         }
-        if (i == lastd) break;  // this column is not needed any more
+        if (i == wlast) break;  // none of this warp's columns is needed any more
+        const uint32_t live = b.wlive[warp][i];
         const int wp = P >> 5, wd = (P - 32 * Wh) >> 5;
         const uint32_t bpm = 1u << (P & 31);
+        // row p's X and Z bits on this warp's columns: gathered by the lane
+        // holding word wp, one bit per column, then broadcast
+        const int kp = wp >> 5, bp = P & 31;
+        uint32_t gx = 0u, gz = 0u;
+#pragma unroll
+        for (int j = 0; j < CPR; ++j) {
+          gx |= ((res_pick(tx[j], kp) >> bp) & 1u) << j;
+          gz |= ((res_pick(tz[j], kp) >> bp) & 1u) << j;
+        }
+        gx = __shfl_sync(0xffffffffu, gx, wp & 31);
+        gz = __shfl_sync(0xffffffffu, gz, wp & 31);
         const uint32_t* Si = s.SM + (size_t)i * W;
-        const uint32_t XP =
-            (__shfl_sync(0xffffffffu, res_pick(tx, wp >> 5), wp & 31) & bpm) ? 0xffffffffu : 0u;
-        const uint32_t ZP =
-            (__shfl_sync(0xffffffffu, res_pick(tz, wp >> 5), wp & 31) & bpm) ? 0xffffffffu : 0u;
-        const uint32_t zpa = (qd == (int)dq1(code)) ? bpm : 0u;
+        uint32_t Sw[WL];
 #pragma unroll
         for (int k = 0; k < WL; ++k) {
           const int w = lane + 32 * k;
-          if (w < W) {
-            uint32_t Sw = Si[w];
-            if (w == wp || w == wd) Sw &= ~bpm;
-            uint32_t x = tx[k] ^ (Sw & XP), z = tz[k] ^ (Sw & ZP);
+          Sw[k] = w < W ? Si[w] : 0u;
+          if (w == wp || w == wd) Sw[k] &= ~bpm;
+        }
+#pragma unroll
+        for (int j = 0; j < CPR; ++j) {
+          if (!((live >> j) & 1u)) continue;
+          const uint32_t XP = ((gx >> j) & 1u) ? 0xffffffffu : 0u;
+          const uint32_t ZP = ((gz >> j) & 1u) ? 0xffffffffu : 0u;
+          const uint32_t zpa = (s0 + j == si) ? bpm : 0u;
+#pragma unroll
+          for (int k = 0; k < WL; ++k) {
+            const int w = lane + 32 * k;
+            uint32_t x = tx[j][k] ^ (Sw[k] & XP), z = tz[j][k] ^ (Sw[k] & ZP);
             if (w == wd) {  // row p-n := row p
               x = (x & ~bpm) | (XP & bpm);
               z = (z & ~bpm) | (ZP & bpm);
@@ -408,16 +482,16 @@ __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
               x &= ~bpm;
               z = (z & ~bpm) | zpa;
             }
-            tx[k] = x;
-            tz[k] = z;
+            tx[j][k] = x;
+            tz[j][k] = z;
           }
         }
       }
     }
 
-    // ---- phase 2: every warp with columns (and the base warp) applies the
-    // batch to its columns and its share, each measurement as soon as it is
-    // published; a warp without columns keeps a zero share and has no work
+    // ---- phase 2: every apply warp with columns (and the base warp) applies
+    // the batch to its columns and its share, each measurement as soon as it
+    // is published; a warp without columns keeps a zero share and has no work
     if (ncw > 0 || base_warp) {
       int seen = 0;
       for (int i = 0; i < K; ++i) {
@@ -618,7 +692,7 @@ __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
       const int mn = m + keff;
       const int Kn = (A.nm - mn < KB) ? A.nm - mn : KB;
       if (keff != K && lane < Kn) next_code = __ldg(A.mops + mn + lane);  // batch ended early
-      res_batch_slots(next_code, Kn > 0 ? Kn : 0, C, r, cpw, b);
+      res_batch_slots(next_code, Kn > 0 ? Kn : 0, C, r, cpw, R, CPR, b);
     }
     __syncthreads();
     cm.stage_columns(s, par ^ 1, b, W, Wp, KB);  // next batch's measured columns
@@ -646,7 +720,7 @@ __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
   __syncthreads();
   if (b.anydet && b.ptype[prev_count - 1] && b.det[prev_count - 1] && dop(b.plast) == OP_MZR) {
     const int pa = (int)dq1(b.plast);
-    if (pa % C == r && (pa / C) / cpw == warp) {
+    if (pa % C == r && R + (pa / C) / cpw == warp) {
       const uint32_t* zc = s.Zs + (size_t)(pa / C) * Wp;
 #pragma unroll
       for (int k = 0; k < WL; ++k) {

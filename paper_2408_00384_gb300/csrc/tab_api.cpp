@@ -645,6 +645,14 @@ int tab_set_rng(tab_t h, uint64_t seed, uint64_t circuit_id, uint32_t shot) {
 }
 
 int tab_reset(tab_t h) {
+  // an error latched on the device by a bounded wait or a consistency check
+  // leaves the CUDA context usable: reset clears it (after the failed work
+  // has drained) and re-initialises the tableau
+  if (h && (h->sticky == TAB_ETIMEOUT || h->sticky == TAB_EDEVICE)) {
+    CU(cudaStreamSynchronize(h->stream));
+    CU(cudaMemsetAsync(h->mw.err, 0, sizeof(int), h->stream));
+    h->sticky = TAB_OK;
+  }
   int rc = check_handle(h);
   if (rc) return rc;
   launch_init(h->X, h->Z, h->R, h->n, h->Wh, h->stream);

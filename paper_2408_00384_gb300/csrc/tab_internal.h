@@ -188,6 +188,12 @@ cudaError_t launch_unpack(const uint32_t* X, const uint32_t* Z, const uint32_t* 
 // thread-local error message
 void set_error(const char* fmt, ...);
 
+// Process-wide run-time configuration (config.cpp): a copy of the current
+// settings, and the grid-barrier wait limit in effect.
+constexpr unsigned long long kDefaultWaitLimitNs = 2000000000ull;  // 2 s
+tab_config run_config();
+unsigned long long run_wait_limit_ns();
+
 // Raise fn's dynamic shared-memory limit to `bytes` on the current device,
 // once per (kernel, device, limit).  Thread-safe; never allocates.
 cudaError_t ensure_smem_limit(const void* fn, int bytes);

@@ -95,6 +95,7 @@ _sig("tab_batch_tune", ctypes.c_int, [_vp, _u64, _vp, _vp, _P(_i32), _P(ctypes.c
 _sig("tab_batch_config", ctypes.c_int, [_vp, _P(_i32), _P(_i32), _P(_i64)])
 _sig("tab_batch_create_ex", ctypes.c_int, [_vp, _i32, _u32, _P(_vp)])
 _sig("tab_batch_sampled", ctypes.c_int, [_vp, _P(_i32)])
+_sig("tab_batch_h2d_bytes", ctypes.c_int, [_vp, _P(_i64)])
 
 
 class TabServerConfig(ctypes.Structure):
@@ -118,6 +119,32 @@ _sig("tab_server_inject", ctypes.c_int, [_vp, _i64, ctypes.c_int])
 _sig("tab_server_stats_get", ctypes.c_int, [_vp, _P(TabServerStats)])
 _sig("tab_server_destroy", ctypes.c_int, [_vp])
 
+
+
+class TabConfig(ctypes.Structure):
+    _fields_ = [("block_threads", _i32), ("meas_batch", _i32), ("grid_ctas", _i32),
+                ("debug", _u32), ("wait_limit_ns", _u64)]
+
+
+_sig("tab_get_config", ctypes.c_int, [_P(TabConfig)])
+_sig("tab_set_config", ctypes.c_int, [_P(TabConfig)])
+DEBUG_SKIP_BARRIER_ARRIVAL = 1
+
+
+def get_config() -> dict:
+    """The process-wide run-time configuration (tab_get_config)."""
+    c = TabConfig()
+    _check(_L.tab_get_config(ctypes.byref(c)))
+    return {k: getattr(c, k) for k, _ in TabConfig._fields_}
+
+
+def set_config(cfg: dict):
+    """Set the run-time configuration (tab_set_config); missing keys keep
+    their current values."""
+    cur = get_config()
+    cur.update(cfg)
+    c = TabConfig(*[cur[k] for k, _ in TabConfig._fields_])
+    _check(_L.tab_set_config(ctypes.byref(c)))
 
 
 class TabPeaks(ctypes.Structure):
@@ -417,14 +444,19 @@ def n_meas_of(gates) -> int:
     return int(np.isin(op, (10, 11)).sum())
 
 
-def batch_run(circuits, seed: int = 1) -> list:
+def batch_run(circuits, seed: int = 1, out=None) -> list:
     """Run (n, gates, shots, circuit_id) circuits in one batched call.
 
-    Returns, per circuit, a (shots, n_meas) uint8 array of outcomes."""
+    Returns, per circuit, a (shots, n_meas) uint8 array of outcomes (views of
+    `out`, a host uint8 array of at least the total outcome count, if given,
+    e.g. in pinned memory)."""
     arr, keep = _circuit_array(circuits)
     sizes = [shots * n_meas_of(g) for (_, g, shots, _) in circuits]
     total = int(sum(sizes))
-    out = np.zeros(max(total, 1), np.uint8)
+    if out is None:
+        out = np.zeros(max(total, 1), np.uint8)
+    elif out.dtype != np.uint8 or out.size < total or not out.flags.c_contiguous:
+        raise ValueError("out must be a contiguous uint8 array of the total outcome count")
     _check(_L.tab_batch_run(ctypes.cast(arr, _vp), len(circuits), seed, out.ctypes.data, None))
     res, off = [], 0
     for (n, g, shots, _), sz in zip(circuits, sizes):
@@ -485,6 +517,13 @@ class Batch:
     def launches(self) -> int:
         c = _i64()
         _check(_L.tab_batch_launches(self._h, ctypes.byref(c)))
+        return c.value
+
+    @property
+    def h2d_bytes(self) -> int:
+        """Compiled-table bytes copied to the device at creation."""
+        c = _i64()
+        _check(_L.tab_batch_h2d_bytes(self._h, ctypes.byref(c)))
         return c.value
 
     def close(self):
