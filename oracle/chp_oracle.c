@@ -74,13 +74,23 @@ typedef struct {
   int32_t n;
   int64_t rows; /* 2n + 1: the last row is AG's scratch row */
   uint8_t *x, *z, *r;
+  uint8_t *spare;         /* rows * n bytes: the target of a change of storage order */
+  int64_t srow, scol;     /* element (i, j) of x and z sits at [i * srow + j * scol] */
+  int64_t row_gates;      /* gate rules run since the last measurement in row-major order */
   uint64_t noise_counter; /* next noise-op index */
   orc_pool *pool;         /* worker threads, or NULL for one thread */
 } orc_tab;
 
-/* storage: element (row i, qubit j) at [j * rows + i] */
-#define XB(t, i, j) ((t)->x[(int64_t)(j) * (t)->rows + (i)])
-#define ZB(t, i, j) ((t)->z[(int64_t)(j) * (t)->rows + (i)])
+/* storage: one byte per bit, element (row i, qubit j) at
+ * [i * srow + j * scol].  A gate reads and writes one or two qubits' columns
+ * of every row, a rowsum whole rows; the tableau is kept row-major (srow n,
+ * scol 1) while measurements run and qubit-major (srow 1, scol rows) while
+ * gates run, switching to qubit-major once more than n/16 + 16 gate rules
+ * follow a measurement (so that a reset's X between measurements does not
+ * reorder twice).  Every access goes through these macros, so results do not
+ * depend on the order. */
+#define XB(t, i, j) ((t)->x[(int64_t)(i) * (t)->srow + (int64_t)(j) * (t)->scol])
+#define ZB(t, i, j) ((t)->z[(int64_t)(i) * (t)->srow + (int64_t)(j) * (t)->scol])
 
 /* ---- worker threads over a range of rows --------------------------------
  * A job is a function applied to rows [lo, hi).  With T threads, thread i
@@ -209,6 +219,41 @@ int32_t orc_set_threads(orc_tab *t, int32_t threads) {
 
 int32_t orc_threads(const orc_tab *t) { return t->pool ? t->pool->threads : 1; }
 
+/* ---- storage order ------------------------------------------------------ */
+
+typedef struct { const uint8_t *src; uint8_t *dst; int64_t ss_row, ss_col; } reorder_job;
+
+/* rows [lo, hi) of one array copied into the other order */
+static void reorder_rows(orc_tab *t, void *arg, int64_t lo, int64_t hi) {
+  const reorder_job *job = (const reorder_job *)arg;
+  const int64_t n = t->n;
+  for (int64_t i0 = lo; i0 < hi; i0 += 64) {
+    const int64_t i1 = i0 + 64 < hi ? i0 + 64 : hi;
+    for (int64_t j0 = 0; j0 < n; j0 += 64) {
+      const int64_t j1 = j0 + 64 < n ? j0 + 64 : n;
+      for (int64_t i = i0; i < i1; i++)
+        for (int64_t j = j0; j < j1; j++)
+          job->dst[i * t->srow + j * t->scol] = job->src[i * job->ss_row + j * job->ss_col];
+    }
+  }
+}
+
+/* Keep x and z row-major (rows = 1) or qubit-major (rows = 0). */
+static void storage_order(orc_tab *t, int rows) {
+  if (rows) t->row_gates = 0;
+  if ((t->scol == 1) == (rows != 0)) return;
+  const int64_t old_row = t->srow, old_col = t->scol;
+  t->srow = rows ? t->n : 1;
+  t->scol = rows ? 1 : t->rows;
+  uint8_t **arr[2] = {&t->x, &t->z};
+  for (int k = 0; k < 2; k++) {
+    reorder_job job = {*arr[k], t->spare, old_row, old_col};
+    for_rows(t, reorder_rows, &job, t->rows);
+    t->spare = *arr[k];
+    *arr[k] = job.dst;
+  }
+}
+
 void orc_reset(orc_tab *t) {
   int64_t cells = (int64_t)t->n * t->rows;
   memset(t->x, 0, (size_t)cells);
@@ -228,12 +273,15 @@ orc_tab *orc_new(int32_t n) {
   if (!t) return NULL;
   t->n = n;
   t->rows = 2 * (int64_t)n + 1;
+  t->srow = 1;
+  t->scol = t->rows;
   int64_t cells = (int64_t)n * t->rows;
   t->x = (uint8_t *)malloc((size_t)cells);
   t->z = (uint8_t *)malloc((size_t)cells);
+  t->spare = (uint8_t *)malloc((size_t)cells);
   t->r = (uint8_t *)malloc((size_t)t->rows);
-  if (!t->x || !t->z || !t->r) {
-    free(t->x); free(t->z); free(t->r); free(t);
+  if (!t->x || !t->z || !t->spare || !t->r) {
+    free(t->x); free(t->z); free(t->spare); free(t->r); free(t);
     return NULL;
   }
   orc_reset(t);
@@ -243,10 +291,17 @@ orc_tab *orc_new(int32_t n) {
 void orc_free(orc_tab *t) {
   if (!t) return;
   if (t->pool) pool_stop(t->pool, t->pool->threads - 1);
-  free(t->x); free(t->z); free(t->r); free(t);
+  free(t->x); free(t->z); free(t->spare); free(t->r); free(t);
 }
 
 int32_t orc_n(const orc_tab *t) { return t->n; }
+
+/* before a gate rule: qubit-major order, unless few rules have run since the
+ * last measurement */
+static void gate_order(orc_tab *t) {
+  if (t->scol == 1 && ++t->row_gates <= t->n / 16 + 16) return;
+  storage_order(t, 0);
+}
 
 /* ---- AG's three gate rules, for every row i in [0, 2n) ----------------
  * Each rule is written for a range of rows; the public function runs it over
@@ -283,12 +338,19 @@ static void s_rows(orc_tab *t, void *arg, int64_t lo, int64_t hi) {
 
 void orc_cnot(orc_tab *t, int32_t a, int32_t b) {
   int32_t ab[2] = {a, b};
+  gate_order(t);
   for_rows(t, cnot_rows, ab, 2 * (int64_t)t->n);
 }
 
-void orc_h(orc_tab *t, int32_t a) { for_rows(t, h_rows, &a, 2 * (int64_t)t->n); }
+void orc_h(orc_tab *t, int32_t a) {
+  gate_order(t);
+  for_rows(t, h_rows, &a, 2 * (int64_t)t->n);
+}
 
-void orc_s(orc_tab *t, int32_t a) { for_rows(t, s_rows, &a, 2 * (int64_t)t->n); }
+void orc_s(orc_tab *t, int32_t a) {
+  gate_order(t);
+  for_rows(t, s_rows, &a, 2 * (int64_t)t->n);
+}
 
 /* ---- gates built from the three rules --------------------------------- */
 
@@ -314,15 +376,22 @@ int32_t orc_g(int32_t x1, int32_t z1, int32_t x2, int32_t z2) {
 /* AG rowsum(h, i): row h := row i * row h.  Returns ORC_EPHASE (and leaves
  * row h unchanged) when the exponent is odd, i.e. the rows anticommute. */
 int32_t orc_rowsum(orc_tab *t, int64_t h, int64_t i) {
+  /* g over its 16 arguments, indexed by x1 z1 x2 z2 (high to low bit) */
+  int8_t g[16];
+  for (int32_t k = 0; k < 16; k++)
+    g[k] = (int8_t)orc_g((k >> 3) & 1, (k >> 2) & 1, (k >> 1) & 1, k & 1);
+  const int64_t sc = t->scol;
+  const uint8_t *xi = &XB(t, i, 0), *zi = &ZB(t, i, 0);
+  uint8_t *xh = &XB(t, h, 0), *zh = &ZB(t, h, 0);
   int64_t sum = 2 * (int64_t)t->r[h] + 2 * (int64_t)t->r[i];
-  for (int32_t j = 0; j < t->n; j++)
-    sum += orc_g(XB(t, i, j), ZB(t, i, j), XB(t, h, j), ZB(t, h, j));
+  for (int64_t j = 0; j < t->n; j++)
+    sum += g[(xi[j * sc] << 3) | (zi[j * sc] << 2) | (xh[j * sc] << 1) | zh[j * sc]];
   int64_t m = ((sum % 4) + 4) % 4;
   if (m != 0 && m != 2) return ORC_EPHASE;
   t->r[h] = (uint8_t)(m == 2);
-  for (int32_t j = 0; j < t->n; j++) {
-    XB(t, h, j) ^= XB(t, i, j);
-    ZB(t, h, j) ^= ZB(t, i, j);
+  for (int64_t j = 0; j < t->n; j++) {
+    xh[j * sc] ^= xi[j * sc];
+    zh[j * sc] ^= zi[j * sc];
   }
   return ORC_OK;
 }
@@ -387,6 +456,7 @@ static void random_case_rows(orc_tab *t, void *arg, int64_t lo, int64_t hi) {
  * outcome (0/1) or a negative error; *deterministic is set to 1 or 0. */
 int32_t orc_measure(orc_tab *t, int32_t a, int32_t rbit, int32_t *deterministic) {
   if (a < 0 || a >= t->n) return ORC_ERANGE;
+  storage_order(t, 1);
   const int64_t n = t->n;
   int64_t p = -1;
   for (int64_t i = n; i < 2 * n; i++)
@@ -507,6 +577,7 @@ int32_t orc_expect(orc_tab *t, const uint8_t *p) {
   int64_t s = 2 * (int64_t)n;
   for (int32_t j = 0; j < n; j++)
     if (p[j] > 3) return ORC_EINVAL;
+  storage_order(t, 1);
   uint8_t *anti = (uint8_t *)calloc((size_t)t->rows, 1);
   if (!anti) return ORC_ENOMEM;
   for (int64_t i = 0; i < 2 * (int64_t)n; i++) {
@@ -536,8 +607,8 @@ void orc_get(const orc_tab *t, uint8_t *x, uint8_t *z, uint8_t *r) {
   int64_t n = t->n;
   for (int64_t i = 0; i < 2 * n; i++) {
     for (int64_t j = 0; j < n; j++) {
-      x[i * n + j] = t->x[j * t->rows + i];
-      z[i * n + j] = t->z[j * t->rows + i];
+      x[i * n + j] = XB(t, i, j);
+      z[i * n + j] = ZB(t, i, j);
     }
     r[i] = t->r[i];
   }
@@ -547,8 +618,8 @@ void orc_set(orc_tab *t, const uint8_t *x, const uint8_t *z, const uint8_t *r) {
   int64_t n = t->n;
   for (int64_t i = 0; i < 2 * n; i++) {
     for (int64_t j = 0; j < n; j++) {
-      t->x[j * t->rows + i] = x[i * n + j] & 1;
-      t->z[j * t->rows + i] = z[i * n + j] & 1;
+      XB(t, i, j) = x[i * n + j] & 1;
+      ZB(t, i, j) = z[i * n + j] & 1;
     }
     t->r[i] = r[i] & 1;
   }
