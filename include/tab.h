@@ -57,9 +57,9 @@ enum tab_op {
   TAB_MZ = 10,  /* measure Z; outcome appended to the handle's outcome log */
   TAB_MZR = 11, /* measure Z, then apply X when the outcome is 1 (reset to |0>) */
   TAB_BARRIER = 12,
-  /* Extended ops, accepted by tab_apply and (all but the noise ops) by
-   * tab_prog_create; batches and the server reject them (TAB_EINVAL).  They
-   * are lowered to the ops above on the host. */
+  /* Extended ops, accepted by tab_apply, batches and the server, and (all
+   * but the noise ops) by tab_prog_create.  MX / MY are lowered to the ops
+   * above on the host; noise ops are drawn per shot (below). */
   TAB_MX = 13,     /* measure X: H, TAB_MZ, H (outcome logged like TAB_MZ) */
   TAB_MY = 14,     /* measure Y: S^dag, H, TAB_MZ, H, S */
   TAB_DEPOL1 = 15, /* depolarizing noise on q1: X, Y or Z with total probability p */
@@ -72,10 +72,14 @@ enum tab_op {
  * tab_reset, in program order -- draws r = Philox4x32-10 with counter
  * (j, shot, circuit_id lo, circuit_id hi) and key (seed lo, seed hi XOR
  * 0x4E4F4953).  It fires when (r.x >> 4) < field; TAB_DEPOL1 then applies
- * X, Y or Z for floor(r.y * 3 / 2^32) = 0, 1 or 2.  The draws are taken on
- * the host when tab_apply compiles the list (the noise of a circuit does not
- * depend on its state), so a fired noise op costs one Pauli gate and an
- * unfired one nothing. */
+ * X, Y or Z for floor(r.y * 3 / 2^32) = 0, 1 or 2.  The noise of a circuit
+ * does not depend on its state, so tab_apply and the server take the draws on
+ * the host when they compile the list (a fired noise op costs one Pauli gate,
+ * an unfired one nothing; the server compiles each shot of a noisy request
+ * apart), while a batch keeps its noise ops and every shot draws its own on
+ * the device (the counter starts at 0 in every shot, and the gates a batch
+ * runs once for all shots end at the circuit's first measurement or noise
+ * op).  At most 16,383 noise ops per batch circuit. */
 
 enum tab_status {
   TAB_OK = 0,
@@ -437,6 +441,31 @@ int tab_server_inject(tab_server_t s, int64_t ticket, int kind);
 int tab_server_stats_get(tab_server_t s, tab_server_stats *out);
 /* Finish every submitted request, then stop the worker and free the server. */
 int tab_server_destroy(tab_server_t s);
+
+/* ---- autotuner of the plain path --------------------------------------
+ * The paper has no counterpart.  tab_tune times `reps` runs (3 if reps is
+ * 0) of the compiled program p from |0^n> on handle h, with the handle's RNG
+ * settings, under each launch shape the kernels are built for: the
+ * measurement engine (single-CTA, grid-resident, streaming, where each holds
+ * n qubits), the grid-resident engine's measurements per batch (8, 16, 32),
+ * then the block gate kernel's threads per CTA (128, 256, 512) with the best
+ * engine.  It keeps the fastest shape for later runs on h (tab_set_engine
+ * and the handle's launch shape) and returns it in *out.  Every run's
+ * outcomes must equal the first run's; TAB_EDEVICE if a shape disagrees.
+ * With TAB_AUTOTUNE_CACHE naming a file, a shape stored there for the same
+ * (GPU name, n rounded up to a power of two, log2 of gates per qubit, log2 of
+ * measurements + 1) is applied without timing (from_cache = 1) unless reps <
+ * 0, and a tuning run adds its shape to the file.  Leaves the tableau reset
+ * to |0^n> and the outcome log empty.  Synchronizes. */
+typedef struct {
+  int32_t engine;         /* TAB_ENGINE_* the measurement runs take */
+  int32_t block_threads;  /* block gate kernel threads per CTA (0: the default by n) */
+  int32_t meas_batch;     /* grid-resident measurements per batch (0: the largest that fits) */
+  int32_t from_cache;     /* 1: taken from the TAB_AUTOTUNE_CACHE file, no timing */
+  int32_t tried;          /* shapes timed */
+  float best_ms;          /* mean time of one run of p with the kept shape */
+} tab_tuned;
+int tab_tune(tab_t h, tab_prog_t p, int32_t reps, tab_tuned *out);
 
 /* ---- run-time configuration (process-wide) ------------------------------
  * Launch-shape knobs (0 = the library's choice by size), the limit of the

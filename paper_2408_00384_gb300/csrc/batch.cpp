@@ -45,6 +45,7 @@ struct tab_batch_s {
   bool sample = false;                      // terminal measurements by the sampler
   int nsampled = 0;
   std::vector<int32_t> cn, ck, cshots;      // per circuit: n, terminal K, shots
+  std::vector<int32_t> cnoise;              // per circuit: noise ops (drawn per shot)
   std::vector<uint8_t> csampled;
   size_t smem = 0;
   int ctas = 1;
@@ -70,6 +71,54 @@ int configure(tab_batch_s* B, int threads);
 // maximum less a margin for the kernel's static shared memory).
 constexpr size_t kBatchSmemLimit = 227 * 1024 - 2048;
 
+// One circuit of a batch: extended ops lowered (MX / MY as in tab_apply;
+// noise ops kept, drawn per shot on the device), then compiled into ASAP
+// layers.  The shared prefix -- gates run once per circuit, before any shot
+// -- ends at the first measurement or noise op, so a circuit with noise
+// compiles its prefix and the rest apart.  *prefix: 1 if the program's first
+// segment is that prefix.
+int compile_circuit(const tab_circuit& tc, std::vector<tab_gate>& low, HostProgram& hp,
+                    uint8_t* prefix) {
+  int64_t ext = 0;
+  int rc = validate_program(tc.n, tc.gates, tc.n_gates, &ext);
+  if (rc != TAB_OK) return rc;
+  const tab_gate* g = tc.gates;
+  int64_t count = tc.n_gates;
+  bool noise = false;
+  if (ext) {
+    rc = lower_for_runs(tc.n, tc.gates, tc.n_gates, true, 0, 0, 0, low);
+    if (rc != TAB_OK) return rc;
+    g = low.data();
+    count = (int64_t)low.size();
+    for (int64_t i = 0; i < count && !noise; ++i) {
+      const uint32_t op = (uint32_t)(g[i] >> 56);
+      noise = op == TAB_DEPOL1 || op == TAB_XERR || op == TAB_ZERR;
+    }
+  }
+  if (!noise) {
+    rc = build_program(tc.n, g, count, &hp);
+    *prefix = (!hp.segs.empty() && hp.segs[0].kind == 0) ? 1 : 0;
+    return rc;
+  }
+  int64_t cut = 0;
+  while (cut < count) {
+    const uint32_t op = (uint32_t)(g[cut] >> 56);
+    if (op == TAB_MZ || op == TAB_MZR || op == TAB_DEPOL1 || op == TAB_XERR || op == TAB_ZERR) break;
+    ++cut;
+  }
+  HostProgram part[2];
+  rc = build_program(tc.n, g, cut, &part[0]);
+  if (rc == TAB_OK) rc = build_program(tc.n, g + cut, count - cut, &part[1], kProgLayers | kProgNoise);
+  if (rc != TAB_OK) return rc;
+  if (part[1].noise.size() > 0x3FFFu) {
+    set_error("more than %u noise ops in one circuit", 0x3FFFu);
+    return TAB_ERANGE;
+  }
+  concat_programs(hp, part, 2);
+  *prefix = part[0].segs.empty() ? 0 : 1;
+  return TAB_OK;
+}
+
 int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offsets,
                 tab_batch_s* B) {
   if (m < 0 || (m > 0 && !circuits)) {
@@ -92,16 +141,20 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
   // per thread, so a failing circuit keeps its own
   std::vector<HostProgram> progs((size_t)m);
   std::vector<int> rcs((size_t)m, TAB_OK);
+  std::vector<uint8_t> prefix((size_t)m, 0);
   std::vector<std::string> msgs((size_t)m);
   {
     std::atomic<int> next{0};
     pool_run(pool_threads(), [&](int) {
+      std::vector<tab_gate> low;
       for (;;) {
         const int c = next.fetch_add(1);
         if (c >= m) break;
         const tab_circuit& tc = circuits[c];
-        rcs[(size_t)c] = build_program(tc.n, tc.gates, tc.n_gates, &progs[(size_t)c]);
-        if (rcs[(size_t)c] != TAB_OK) msgs[(size_t)c] = tab_last_error();
+        HostProgram& hp = progs[(size_t)c];
+        int rc = compile_circuit(tc, low, hp, &prefix[(size_t)c]);
+        rcs[(size_t)c] = rc;
+        if (rc != TAB_OK) msgs[(size_t)c] = tab_last_error();
       }
     });
   }
@@ -119,10 +172,11 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
     o_seg[(size_t)c + 1] = o_seg[(size_t)c] + hp.segs.size();
   }
   std::vector<uint32_t> ops(o_ops[(size_t)m]), layer_off(o_lo[(size_t)m]);
+  std::vector<uint32_t> noise;
   std::vector<Seg> segs(o_seg[(size_t)m]);
   std::vector<BatchCirc> circs((size_t)m);
   std::vector<double> pre_cost((size_t)m), shot_cost((size_t)m);
-  uint64_t img_words = 0;
+  uint64_t img_words = 0, noise_words = 0;
   int64_t out_packed = 0, out_max = 0;
   for (int32_t c = 0; c < m; ++c) {
     const tab_circuit& tc = circuits[c];
@@ -132,7 +186,10 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
     bc.shots = tc.shots;
     bc.seg_begin = (uint32_t)o_seg[(size_t)c];
     bc.seg_end = (uint32_t)o_seg[(size_t)c + 1];
-    bc.n_prefix = (!hp.segs.empty() && hp.segs[0].kind == 0) ? 1u : 0u;
+    bc.n_prefix = prefix[(size_t)c];
+    bc.n_noise = (uint32_t)hp.noise.size();
+    bc.noise_off = noise_words;
+    noise_words += hp.noise.size();
     bc.n_meas = (uint32_t)hp.n_meas;
     bc.cid = tc.circuit_id;
     bc.img_off = img_words;
@@ -140,7 +197,8 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
     // terminal measurements only (one MZ run after the gates): the sampler
     // runs them once and evaluates every shot from the outcome forms
     bc.sampled = 0;
-    if (B->sample && hp.n_meas > 0 && hp.segs.size() == (size_t)bc.n_prefix + 1 &&
+    if (B->sample && hp.n_meas > 0 && hp.noise.empty() &&
+        hp.segs.size() == (size_t)bc.n_prefix + 1 &&
         hp.segs.back().kind == 1) {
       const Seg& ms = hp.segs.back();
       bool mz = true;
@@ -154,6 +212,7 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
     B->cn.push_back(tc.n);
     B->ck.push_back((int32_t)hp.n_meas);
     B->cshots.push_back(tc.shots);
+    B->cnoise.push_back((int32_t)hp.noise.size());
     B->csampled.push_back((uint8_t)bc.sampled);
     const int64_t span = (int64_t)tc.shots * hp.n_meas;
     bc.out_off = (uint64_t)(out_offsets ? out_offsets[c] : out_packed);
@@ -174,6 +233,7 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
     B->n_meas += span;
     B->max_n = std::max(B->max_n, tc.n);
   }
+  noise.resize(noise_words);
   // ---- fill the concatenated tables, circuits in parallel
   {
     std::atomic<int> next{0};
@@ -184,6 +244,8 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
         HostProgram& hp = progs[(size_t)c];
         const uint32_t op_base = (uint32_t)o_ops[(size_t)c], lo_base = (uint32_t)o_lo[(size_t)c];
         std::copy(hp.ops.begin(), hp.ops.end(), ops.begin() + (ptrdiff_t)op_base);
+        std::copy(hp.noise.begin(), hp.noise.end(),
+                  noise.begin() + (ptrdiff_t)circs[(size_t)c].noise_off);
         for (size_t i = 0; i < hp.layer_off.size(); ++i)
           layer_off[lo_base + i] = hp.layer_off[i] + op_base;
         for (size_t i = 0; i < hp.segs.size(); ++i) {
@@ -223,10 +285,12 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
   const size_t b_lo = a256(layer_off.size() * 4 + 4);
   const size_t b_items = a256(items.size() * 8 + 8);
   const size_t b_img = a256(img_words * 4 + 16);
+  const size_t b_noise = a256(noise.size() * 4 + 4);
   B->ctl_bytes = a256(16 + (size_t)m * 4 + 4);
-  const size_t total = b_circs + b_segs + b_ops + b_lo + b_items + b_img + B->ctl_bytes;
+  const size_t total = b_circs + b_segs + b_ops + b_lo + b_items + b_img + b_noise + B->ctl_bytes;
   B->h2d_bytes = (int64_t)(circs.size() * sizeof(BatchCirc) + segs.size() * sizeof(Seg) +
-                           ops.size() * 4 + layer_off.size() * 4 + items.size() * 8);
+                           ops.size() * 4 + layer_off.size() * 4 + items.size() * 8 +
+                           noise.size() * 4);
   if (cudaMalloc(&B->dmem, total) != cudaSuccess) {
     cudaGetLastError();
     set_error("cudaMalloc of %zu bytes for the batch failed", total);
@@ -252,6 +316,9 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
   p += b_items;
   A.img = reinterpret_cast<uint32_t*>(p);
   p += b_img;
+  A.noise = reinterpret_cast<const uint32_t*>(p);
+  if (!noise.empty()) CUB(cudaMemcpy(p, noise.data(), noise.size() * 4, cudaMemcpyHostToDevice));
+  p += b_noise;
   B->ctl = p;
   A.queue = reinterpret_cast<unsigned int*>(p);
   A.err = reinterpret_cast<int*>(p + 4);
@@ -267,6 +334,9 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
 // the batch's largest tableau, and as many CTAs as fit on the GPU at once.
 int configure(tab_batch_s* B, int threads) {
   size_t smem = sct_smem_bytes(B->max_n, threads);
+  for (size_t c = 0; c < B->cn.size(); ++c)  // a shot's noise draws follow its tableau
+    if (B->cnoise[c])
+      smem = std::max(smem, sct_smem_bytes(B->cn[c], threads) + (((size_t)B->cnoise[c] + 3) & ~(size_t)3));
   for (size_t c = 0; c < B->cn.size(); ++c)
     if (B->csampled[c])
       smem = std::max(smem, sct_smem_bytes(B->cn[c], threads) +

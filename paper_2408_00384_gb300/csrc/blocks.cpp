@@ -144,64 +144,104 @@ void BlockBuilder::add(uint32_t op, uint32_t a, uint32_t b) {
   }
 }
 
-// Within one super-layer, reorder each kind group's records so that every
-// aligned window of 32 records (the records one warp takes together) reads
-// its first qubits, and its second qubits, from 32 distinct shared-memory
-// banks: distinct qa mod 32 and, among two-qubit blocks, distinct qb mod 32.
-// The blocks of a super-layer act on disjoint qubits and commute, so any
-// order gives the same tableau; groups stay contiguous (warp-uniform paths).
-// Greedy: each window slot takes the first record within kScan of the
-// group's remaining records that fits the window, else the next one.
+// Within one super-layer, reorder each group's records so that every aligned
+// window of 32 records (the records one warp takes together) reads its first
+// qubits, and its second qubits, from as many distinct shared-memory banks
+// as the group allows (qa mod 32, and qb mod 32 for two-qubit blocks).  The
+// blocks of a super-layer act on disjoint qubits and commute, so any order
+// gives the same tableau; groups stay contiguous.  Greedy over buckets keyed
+// by (qa mod 32, qb mod 32): each window slot takes, among the residues the
+// window has not used yet, the first residue with the most records left and
+// then the second residue with the most records left (so the buckets drain
+// evenly and the last windows are not left with one residue), else any
+// record.
 static void bank_order(uint2* recs, const uint32_t* group_size, int ngroups) {
-  constexpr size_t kScan = 64;
+  constexpr int kB = 32 * 33;  // qb residue 32: a single-qubit block
+  thread_local std::vector<uint2> tmp;
+  thread_local std::vector<int32_t> next;
+  int32_t head[kB];
+  uint64_t row[32];  // row[i] bit j: bucket (i, j) is not empty
+  int cnt_a[32], cnt_b[33];  // records left with each first / second residue
   uint32_t used_a = 0u, used_b = 0u;
   int slot = 0;
   size_t at = 0;
   for (int g = 0; g < ngroups; ++g) {
-    uint2* G = recs + at;
     const size_t size = group_size[g];
+    uint2* G = recs + at;
+    at += size;
+    if (size == 0) continue;
+    tmp.assign(G, G + size);
+    next.assign(size, -1);
+    for (int b = 0; b < kB; ++b) head[b] = -1;
+    for (int i = 0; i < 32; ++i) row[i] = 0u;
+    for (int i = 0; i < 32; ++i) cnt_a[i] = 0;
+    for (int j = 0; j < 33; ++j) cnt_b[j] = 0;
+    for (size_t k = size; k-- > 0;) {
+      const uint32_t qa = tmp[k].x & 31u;
+      const uint32_t qb = ((tmp[k].x >> 28) & 1u) ? (tmp[k].x >> 14) & 31u : 32u;
+      const int b = (int)(qa * 33 + qb);
+      next[k] = head[b];
+      head[b] = (int32_t)k;
+      row[qa] |= 1ull << qb;
+      ++cnt_a[qa];
+      ++cnt_b[qb];
+    }
     for (size_t k = 0; k < size; ++k) {
-      size_t pick = k;
-      for (size_t j = k; j < size && j < k + kScan; ++j) {
-        const uint32_t qa = G[j].x & 31u, qb = (G[j].x >> 14) & 31u, two = (G[j].x >> 28) & 1u;
-        if (!((used_a >> qa) & 1u) && !(two && ((used_b >> qb) & 1u))) {
-          pick = j;
-          break;
+      int pick_b = -1, best_a = -1;
+      const uint64_t free_b = (uint64_t)(~used_b) | (1ull << 32);
+      for (uint32_t rows = ~used_a; rows; rows &= rows - 1u) {
+        const int i = __builtin_ctz(rows);
+        if (cnt_a[i] > best_a && (row[i] & free_b)) {
+          best_a = cnt_a[i];
+          pick_b = i;
         }
       }
-      std::swap(G[k], G[pick]);
-      used_a |= 1u << (G[k].x & 31u);
-      if ((G[k].x >> 28) & 1u) used_b |= 1u << ((G[k].x >> 14) & 31u);
+      if (pick_b >= 0) {
+        const int i = pick_b;
+        int best_b = -1;
+        for (uint64_t m = row[i] & free_b; m; m &= m - 1u) {
+          const int j = __builtin_ctzll(m);
+          if (cnt_b[j] > best_b) {
+            best_b = cnt_b[j];
+            pick_b = i * 33 + j;
+          }
+        }
+      }
+      // no bucket fits the window: a record whose first residue is free, or
+      // whose second residue is free, else any record
+      for (uint32_t rows = ~used_a; rows && pick_b < 0; rows &= rows - 1u) {
+        const int i = __builtin_ctz(rows);
+        if (row[i]) pick_b = i * 33 + __builtin_ctzll(row[i]);
+      }
+      for (int i = 0; i < 32 && pick_b < 0; ++i)
+        if (row[i] & free_b) pick_b = i * 33 + __builtin_ctzll(row[i] & free_b);
+      for (int i = 0; i < 32 && pick_b < 0; ++i)
+        if (row[i]) pick_b = i * 33 + __builtin_ctzll(row[i]);
+      const int32_t idx = head[pick_b];
+      head[pick_b] = next[(size_t)idx];
+      --cnt_a[pick_b / 33];
+      --cnt_b[pick_b % 33];
+      if (head[pick_b] < 0) row[pick_b / 33] &= ~(1ull << (pick_b % 33));
+      G[k] = tmp[(size_t)idx];
+      used_a |= 1u << (pick_b / 33);
+      if (pick_b % 33 < 32) used_b |= 1u << (pick_b % 33);
       if (++slot == 32) {
         slot = 0;
         used_a = used_b = 0u;
       }
     }
-    at += size;
   }
 }
 
-// Emit the run's blocks, grouped by super-layer and, inside one, by kind
-// (single- or two-qubit, entangler, whether the U codes are identities, and
-// the class -- identity, H, S or other -- of each V code) so that the threads
-// of a warp take the same path: identity codes are skipped and H / S take
-// their two-operation forms.  A CNOT is stored with its control in register
-// 0 (the block's two registers relabelled if needed: the qubits, the U and
-// the V codes trade places; the swap flag keeps its meaning).  Super-layers
-// above kMaxLayerOps blocks become consecutive sub-layers.  Appends to P.blk
-// and P.blk_off and sets s.blk_begin / s.blk_end.
+// Emit the run's blocks, grouped by super-layer and, inside one, into
+// single- and two-qubit blocks (a warp of one kind takes one path), each
+// group in bank order.  A CNOT is stored with its control in register 0 (the
+// block's two registers relabelled if needed: the qubits, the U and the V
+// codes trade places; the swap flag keeps its meaning).  Super-layers above
+// kMaxLayerOps blocks become consecutive sub-layers.  Appends to P.blk and
+// P.blk_off and sets s.blk_begin / s.blk_end.
 void BlockBuilder::emit(HostProgram& P, Seg& s) {
-  // (1q | 2q none / CNOT / CZ) x (U identity) x (V_0 class) x (V_1 class);
-  // the sort key of each live block and its record are formed in one pass
-  // (table lookups in place of data-dependent branches)
-  const int kKinds = 128;
-  static const std::vector<uint8_t> cls = [] {
-    std::vector<uint8_t> v(128, 3);
-    v[kC1Ident] = 0;
-    v[kC1H] = 1;
-    v[kC1S] = 2;
-    return v;
-  }();
+  const int kKinds = 2;
   const size_t nb = blk_.size();
   key_.resize(nb);
   rec_.resize(nb);
@@ -219,11 +259,9 @@ void BlockBuilder::emit(HostProgram& P, Seg& s) {
       std::swap(k.V[0], k.V[1]);
       k.dir = 0;
     }
-    const uint32_t e = k.has_b ? 1u + k.ent : 0u;
-    const uint32_t u = ((k.U[0] ^ kC1Ident) | (k.U[1] ^ kC1Ident)) != 0;
-    key_[i] = (uint32_t)k.layer * kKinds + ((e * 2 + u) * 4 + cls[k.V[0]]) * 4 + cls[k.V[1]];
+    key_[i] = (uint32_t)k.layer * kKinds + (k.has_b ? 1u : 0u);
     rec_[i] = make_uint2((uint32_t)k.qa | ((uint32_t)k.qb << 14) | ((uint32_t)k.has_b << 28) |
-                             ((uint32_t)k.ent << 29) | ((uint32_t)k.dir << 31),
+                             ((uint32_t)k.ent << 29),
                          (uint32_t)k.U[0] | ((uint32_t)k.U[1] << 7) | ((uint32_t)k.V[0] << 14) |
                              ((uint32_t)k.V[1] << 21) | ((uint32_t)k.swp << 28));
     top = std::max(top, k.layer + 1);

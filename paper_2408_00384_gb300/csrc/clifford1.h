@@ -66,20 +66,20 @@ __device__ __forceinline__ void c1_apply(uint32_t m, uint32_t& x, uint32_t& z, u
   x = xn;
 }
 
-// c1_apply for a code that the lanes in `act` hold: when they all hold the
-// identity, H or S (the codes random layers use), the warp takes the short
-// form; otherwise every lane applies its own code in general form.
-__device__ __forceinline__ void c1_apply_warp(uint32_t m, uint32_t act, uint32_t& x, uint32_t& z,
-                                              uint32_t& r) {
-  if (__all_sync(act, m == kC1Ident)) return;
-  if (__all_sync(act, m == kC1H)) {
+// c1_apply with short forms for the identity, H and S (the codes random
+// layers use); a branch per lane, so lanes of different classes diverge
+// briefly instead of voting.
+__device__ __forceinline__ void c1_apply_class(uint32_t m, uint32_t& x, uint32_t& z,
+                                               uint32_t& r) {
+  if (m == kC1Ident) return;
+  if (m == kC1H) {
     r ^= x & z;
     const uint32_t t = x;
     x = z;
     z = t;
     return;
   }
-  if (__all_sync(act, m == kC1S)) {
+  if (m == kC1S) {
     r ^= x & z;
     z ^= x;
     return;

@@ -18,9 +18,11 @@
 
 namespace tab {
 
+// npauli: the Pauli (OP_X / OP_Y / OP_Z, or 0 for none) each OP_NOISE code of
+// the run drew for this shot, by ordinal; needed only where noise codes occur.
 __device__ __forceinline__ void apply_gate(uint32_t code, uint32_t* __restrict__ X,
                                            uint32_t* __restrict__ Z, int stride, int w,
-                                           uint32_t& r) {
+                                           uint32_t& r, const uint8_t* npauli = nullptr) {
   const uint32_t op = dop(code);
   const int ia = (int)dq1(code) * stride + w;
   switch (op) {
@@ -43,6 +45,12 @@ __device__ __forceinline__ void apply_gate(uint32_t code, uint32_t* __restrict__
     case OP_X: r ^= Z[ia]; break;
     case OP_Y: r ^= X[ia] ^ Z[ia]; break;
     case OP_Z: r ^= X[ia]; break;
+    case OP_NOISE: {
+      const uint32_t p = npauli[dq2(code)];
+      if (p == OP_X) r ^= Z[ia];
+      else if (p == OP_Y) r ^= X[ia] ^ Z[ia];
+      else if (p == OP_Z) r ^= X[ia];
+    } break;
     case OP_CNOT: {
       const int ib = (int)dq2(code) * stride + w;
       const uint32_t xc = X[ia], zc = Z[ia], xt = X[ib], zt = Z[ib];

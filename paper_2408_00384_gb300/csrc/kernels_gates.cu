@@ -119,28 +119,24 @@ constexpr int kBlkChunk = 512;                  // records per TMA copy (4 KB)
 constexpr int kBlkSlots = 16;                   // 64 KB ring (12 slots, 48 KB, for large n)
 constexpr int kBlkRing = kBlkChunk * kBlkSlots;
 
-// Identity, H and S codes take their short forms when every thread of the
-// warp holds the same one (the compiler groups blocks by those classes); the
-// lanes of a warp that take part are given by `act`, and every warp vote
-// names exactly the lanes that reach it.
-__device__ __forceinline__ void apply_block(uint2 rec, uint32_t* sx, uint32_t* sz, uint32_t& r,
-                                            uint32_t act) {
+// Each lane branches on its own codes' classes: identity codes are skipped
+// and H / S take their two-operation forms (random layers mix only those, so
+// a warp that diverges runs two short paths); other codes take the general
+// form.  No warp votes.
+__device__ __forceinline__ void apply_block(uint2 rec, uint32_t* sx, uint32_t* sz, uint32_t& r) {
   const uint32_t qa = rec.x & 0x3FFFu, qb = (rec.x >> 14) & 0x3FFFu;
   const bool two = (rec.x >> 28) & 1u;
   const uint32_t ent = (rec.x >> 29) & 3u;
   const uint32_t m = rec.y;
-  // the lanes of `act` holding two-qubit blocks: the only lanes that take
-  // part in the votes after the single-qubit lanes leave
-  const uint32_t act2 = __ballot_sync(act, two);
   uint32_t x0 = sx[qa], z0 = sz[qa];
-  c1_apply_warp(m & 0x7Fu, act, x0, z0, r);
+  c1_apply_class(m & 0x7Fu, x0, z0, r);
   if (!two) {
     sx[qa] = x0;
     sz[qa] = z0;
     return;
   }
   uint32_t x1 = sx[qb], z1 = sz[qb];
-  c1_apply_warp((m >> 7) & 0x7Fu, act2, x1, z1, r);
+  c1_apply_class((m >> 7) & 0x7Fu, x1, z1, r);
   if (ent == 1u) {  // CNOT, control in register 0 (the compiler's convention)
     r ^= x0 & z1 & ~(x1 ^ z0);
     x1 ^= x0;
@@ -151,8 +147,8 @@ __device__ __forceinline__ void apply_block(uint2 rec, uint32_t* sx, uint32_t* s
     z1 ^= x0;
     z0 = z0n;
   }
-  c1_apply_warp((m >> 14) & 0x7Fu, act2, x0, z0, r);
-  c1_apply_warp((m >> 21) & 0x7Fu, act2, x1, z1, r);
+  c1_apply_class((m >> 14) & 0x7Fu, x0, z0, r);
+  c1_apply_class((m >> 21) & 0x7Fu, x1, z1, r);
   const bool sw = (m >> 28) & 1u;
   const uint32_t da = sw ? qb : qa, db = sw ? qa : qb;
   sx[da] = x0;
@@ -225,11 +221,8 @@ __global__ void __launch_bounds__(T) k_gates_block(uint32_t* __restrict__ X, uin
     }
     __syncthreads();
     if (s_abort) break;
-    for (uint32_t g0 = lb + (tid & ~31u); g0 < le; g0 += T) {  // warp-uniform trip count
-      const uint32_t g = g0 + (tid & 31);
-      const uint32_t act = __ballot_sync(0xffffffffu, g < le);
-      if (g < le) apply_block(ring[(g - base) % (SLOTS * kBlkChunk)], sx, sz, racc, act);
-    }
+    for (uint32_t g = lb + tid; g < le; g += T)
+      apply_block(ring[(g - base) % (SLOTS * kBlkChunk)], sx, sz, racc);
     prev_lb = lb;
     lb = le;
   }
@@ -291,11 +284,11 @@ static int block_slots(int n) {
 
 cudaError_t launch_gates_block(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
                                const uint2* blk, const uint32_t* blk_off, int nlayers, int* err,
-                               cudaStream_t s) {
+                               cudaStream_t s, int threads) {
   if (nlayers <= 0) return cudaSuccess;
   if (block_slots(n) == 12)
     return launch_gates_block_t<512, 12>(X, Z, R, n, W, blk, blk_off, nlayers, err, s);
-  switch (block_threads(n)) {
+  switch (threads == 128 || threads == 256 || threads == 512 ? threads : block_threads(n)) {
     case 128: return launch_gates_block_t<128, 16>(X, Z, R, n, W, blk, blk_off, nlayers, err, s);
     case 256: return launch_gates_block_t<256, 16>(X, Z, R, n, W, blk, blk_off, nlayers, err, s);
     default: return launch_gates_block_t<512, 16>(X, Z, R, n, W, blk, blk_off, nlayers, err, s);

@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(kMeasThreads) k_measure(MArgs A) {
   uint32_t* sSupp = sZA + W;              // [ncols] support list of the pivot row
   uint32_t* sRed = sSupp + ((ncols + 3) & ~3);  // [GG][Q][8] partial counters
   __shared__ int s_pw, s_nsupp, s_kc, s_det_out;
+  __shared__ uint32_t s_rbits;  // outcome bits of the current 32 measurements
   __shared__ uint32_t s_php, s_r4p;  // row p's own partial / base sign: bit0 lo, bit1 hi
 
   uint32_t* PHlo = A.ph + (size_t)c * 2 * W;
@@ -143,7 +144,13 @@ __global__ void __launch_bounds__(kMeasThreads) k_measure(MArgs A) {
 
     const int a = (int)dq1(code);
     const int reset = dop(code) == OP_MZR;
-    const uint32_t rbit = outcome_bit(A.seed, A.cid, A.shot, A.k0 + (uint64_t)m);
+    // outcome bits of measurements m .. m+31, drawn by warp 0 once every 32
+    // measurements (lane i: measurement m+i); read after the barrier below
+    if ((m & 31) == 0 && tid < 32) {
+      const uint32_t b = outcome_bit(A.seed, A.cid, A.shot, A.k0 + (uint64_t)(m + tid));
+      const uint32_t bits = __ballot_sync(0xffffffffu, b != 0u);
+      if (tid == 0) s_rbits = bits;
+    }
 
     // ---- phase A: mask S = X column a, pivot p = first stabilizer row in S
     if (tid == 0) s_pw = 0x7fffffff;
@@ -169,6 +176,7 @@ __global__ void __launch_bounds__(kMeasThreads) k_measure(MArgs A) {
     }
     pend_a = -1;
     __syncthreads();
+    const uint32_t rbit = (s_rbits >> (m & 31)) & 1u;
 
     if (pw != 0x7fffffff) {
       // ================= random outcome =================

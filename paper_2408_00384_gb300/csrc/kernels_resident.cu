@@ -180,14 +180,16 @@ size_t resident_work_words(int n, int max_ctas) {
 cudaError_t launch_measure_resident(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh,
                                     const uint32_t* mops, int nm, uint64_t k0, uint64_t seed,
                                     uint64_t cid, uint32_t shot, uint8_t* out, int* err,
-                                    uint32_t* work, GridBar* bar, int G, cudaStream_t s) {
+                                    uint32_t* work, GridBar* bar, int G, cudaStream_t s,
+                                    int batch) {
   if (nm <= 0) return cudaSuccess;
   const int wl = res_words_per_lane(Wh);
   const void* fn = resident_kernel(wl);
   if (fn == nullptr) return cudaErrorInvalidValue;
   ResArgs A = res_args(X, Z, R, n, Wh, mops, nm, k0, seed, cid, shot, out, err);
   const int W = 2 * Wh;
-  A.kb = res_batch_for(n, Wh, G, res_dyn_limit(), std::min(batch_cap(), res_batch_cap(wl)), false);
+  const int cap = batch >= 1 && batch <= kBatchMax ? batch : batch_cap();
+  A.kb = res_batch_for(n, Wh, G, res_dyn_limit(), std::min(cap, res_batch_cap(wl)), false);
   if (A.kb == 0) return cudaErrorInvalidValue;
   // replay warps: enough for the batch's columns; apply warps: one column
   // each where the CTA's warp budget allows, at most 32 columns each

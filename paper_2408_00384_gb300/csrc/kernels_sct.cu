@@ -33,6 +33,7 @@
 namespace tab {
 
 constexpr int kSctThreads = 512;
+constexpr uint32_t kNoiseKeyTag = 0x4E4F4953u;  // noise draws use a key of their own
 constexpr unsigned long long kReadyWaitNs = 2000000000ull;
 
 __host__ __device__ inline int sct_whc(int n) { return (n + 31) / 32; }
@@ -48,7 +49,7 @@ __host__ __device__ inline size_t sct_smem_words(int n, int threads) {
   int GG = threads / Wc;
   if (GG < 1) GG = 1;
   if (GG > n) GG = n;
-  return (size_t)2 * n * sct_wp(n) + 2 * (size_t)Wc + 3 * (size_t)n + 2 * (size_t)GG * Wc;
+  return (size_t)2 * n * sct_wp(n) + 2 * (size_t)Wc + 3 * (size_t)n + 2 * (size_t)GG * sct_wp(n);
 }
 
 size_t sct_smem_bytes(int n, int threads) { return sizeof(uint32_t) * sct_smem_words(n, threads); }
@@ -81,7 +82,7 @@ __device__ __forceinline__ void sct_setup(Sct& s, uint32_t* base, int n) {
   s.sS = s.R + s.Wc;
   s.supp = s.sS + s.Wc;
   s.redlo = s.supp + 3 * n;
-  s.redhi = s.redlo + (size_t)s.GG * s.Wc;
+  s.redhi = s.redlo + (size_t)s.GG * s.Wp;  // stride Wp (odd): lanes over groups read distinct banks
 }
 
 __device__ __forceinline__ unsigned long long sct_gtimer() {
@@ -119,7 +120,8 @@ __device__ void sct_identity(const Sct& s) {
 
 // Apply layers [0, nl) of a gate segment; layer_off[L]..layer_off[L+1].
 __device__ void sct_gates(const Sct& s, const uint32_t* __restrict__ ops,
-                          const uint32_t* __restrict__ layer_off, int nl) {
+                          const uint32_t* __restrict__ layer_off, int nl,
+                          const uint8_t* npauli = nullptr) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   uint32_t r0 = 0u, r1 = 0u;
   uint32_t lb = __ldg(layer_off);
@@ -129,8 +131,8 @@ __device__ void sct_gates(const Sct& s, const uint32_t* __restrict__ ops,
       const uint32_t le = __ldg(layer_off + L + 1);
       for (uint32_t g = lb + warp; g < le; g += nw) {
         const uint32_t code = __ldg(ops + g);
-        apply_gate(code, s.X, s.Z, s.Wp, lane, r0);
-        if (two) apply_gate(code, s.X, s.Z, s.Wp, lane + 32, r1);
+        apply_gate(code, s.X, s.Z, s.Wp, lane, r0, npauli);
+        if (two) apply_gate(code, s.X, s.Z, s.Wp, lane + 32, r1, npauli);
       }
       lb = le;
       __syncthreads();
@@ -144,7 +146,7 @@ __device__ void sct_gates(const Sct& s, const uint32_t* __restrict__ ops,
       const uint32_t le = __ldg(layer_off + L + 1);
       if (active)
         for (uint32_t g = lb + warp * sub + gsub; g < le; g += nw * sub)
-          apply_gate(__ldg(ops + g), s.X, s.Z, s.Wp, w, r0);
+          apply_gate(__ldg(ops + g), s.X, s.Z, s.Wp, w, r0, npauli);
       lb = le;
       __syncthreads();
     }
@@ -236,21 +238,58 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err)
       uint32_t lo = 0u, hi = 0u;
       uint32_t Sw = s.sS[w];
       if (w == wp || w == wd) Sw &= ~bpm;  // S' excludes rows p and p-n
-      for (int idx = g; idx < nx; idx += s.GG) {
+      // two columns per iteration, so the shared-memory loads of one overlap
+      // the other's (the list entries are distinct columns)
+      const int GG = s.GG;
+      int idx = g;
+      for (; idx + GG < nx; idx += 2 * GG) {
+        const size_t i0 = (size_t)lX[idx] * Wp + w, i1 = (size_t)lX[idx + GG] * Wp + w;
+        const uint32_t x0 = s.X[i0], z0 = s.Z[i0], x1 = s.X[i1], z1 = s.Z[i1];
+        hi ^= z0 & ~(x0 ^ lo);
+        lo ^= z0;
+        hi ^= z1 & ~(x1 ^ lo);
+        lo ^= z1;
+        s.X[i0] = x0 ^ Sw;
+        s.X[i1] = x1 ^ Sw;
+      }
+      if (idx < nx) {
         const size_t i = (size_t)lX[idx] * Wp + w;
         const uint32_t x = s.X[i], z = s.Z[i];
         hi ^= z & ~(x ^ lo);
         lo ^= z;
         s.X[i] = x ^ Sw;
       }
-      for (int idx = g; idx < nz; idx += s.GG) {
+      for (idx = g; idx + GG < nz; idx += 2 * GG) {
+        const size_t i0 = (size_t)lZ[idx] * Wp + w, i1 = (size_t)lZ[idx + GG] * Wp + w;
+        const uint32_t x0 = s.X[i0], z0 = s.Z[i0], x1 = s.X[i1], z1 = s.Z[i1];
+        hi ^= x0 & (z0 ^ lo);
+        lo ^= x0;
+        hi ^= x1 & (z1 ^ lo);
+        lo ^= x1;
+        s.Z[i0] = z0 ^ Sw;
+        s.Z[i1] = z1 ^ Sw;
+      }
+      if (idx < nz) {
         const size_t i = (size_t)lZ[idx] * Wp + w;
         const uint32_t x = s.X[i], z = s.Z[i];
         hi ^= x & (z ^ lo);
         lo ^= x;
         s.Z[i] = z ^ Sw;
       }
-      for (int idx = g; idx < ny; idx += s.GG) {
+      for (idx = g; idx + GG < ny; idx += 2 * GG) {
+        const size_t i0 = (size_t)lY[idx] * Wp + w, i1 = (size_t)lY[idx + GG] * Wp + w;
+        const uint32_t x0 = s.X[i0], z0 = s.Z[i0], x1 = s.X[i1], z1 = s.Z[i1];
+        const uint32_t e0 = ~(x0 ^ z0), e1 = ~(x1 ^ z1);
+        hi ^= (e0 & ~(x0 ^ lo)) ^ x0;
+        lo ^= e0;
+        hi ^= (e1 & ~(x1 ^ lo)) ^ x1;
+        lo ^= e1;
+        s.X[i0] = x0 ^ Sw;
+        s.Z[i0] = z0 ^ Sw;
+        s.X[i1] = x1 ^ Sw;
+        s.Z[i1] = z1 ^ Sw;
+      }
+      if (idx < ny) {
         const size_t i = (size_t)lY[idx] * Wp + w;
         const uint32_t x = s.X[i], z = s.Z[i];
         const uint32_t e = ~(x ^ z);
@@ -259,8 +298,8 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err)
         s.X[i] = x ^ Sw;
         s.Z[i] = z ^ Sw;
       }
-      s.redlo[g * Wc + w] = lo;
-      s.redhi[g * Wc + w] = hi;
+      s.redlo[g * Wp + w] = lo;
+      s.redhi[g * Wp + w] = hi;
     }
     __syncthreads();
     // combine the column groups: one warp per word, lanes over groups, then a
@@ -268,7 +307,7 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err)
     const int cwarp = tid >> 5, cnw = T >> 5;
     for (int ww = cwarp; ww < Wc; ww += cnw) {
       uint32_t L = 0u, H = 0u;
-      for (int gg = lane; gg < s.GG; gg += 32) add4s(L, H, s.redlo[gg * Wc + ww], s.redhi[gg * Wc + ww]);
+      for (int gg = lane; gg < s.GG; gg += 32) add4s(L, H, s.redlo[gg * Wp + ww], s.redhi[gg * Wp + ww]);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const uint32_t l2 = __shfl_xor_sync(0xffffffffu, L, o);
@@ -483,19 +522,29 @@ __device__ void sct_run_segments(const Sct& s, const Seg* __restrict__ segs, int
                                  int seg_end, const uint32_t* __restrict__ ops,
                                  const uint32_t* __restrict__ layer_off, uint64_t seed,
                                  uint64_t cid, uint32_t shot, uint64_t k0, uint8_t* out,
-                                 int* err) {
+                                 int* err, const uint8_t* npauli = nullptr) {
   uint64_t k = k0;
   int o = 0;
   for (int si = seg_begin; si < seg_end; ++si) {
     const Seg g = segs[si];
     if (g.kind == 0) {
-      sct_gates(s, ops, layer_off + g.layer_begin, (int)(g.layer_end - g.layer_begin));
+      sct_gates(s, ops, layer_off + g.layer_begin, (int)(g.layer_end - g.layer_begin), npauli);
     } else {
+      __shared__ uint32_t s_rbits;  // outcome bits of the current 32 measurements
       uint32_t next_code = __ldg(ops + g.op_begin);  // fetched one step ahead
       for (uint32_t op = g.op_begin; op < g.op_end; ++op) {
         const uint32_t code = next_code;
         if (op + 1 < g.op_end) next_code = __ldg(ops + op + 1);
-        const uint32_t rbit = outcome_bit(seed, cid, shot, k);
+        const uint32_t t = (op - g.op_begin) & 31u;
+        if (t == 0u) {  // warp 0 draws the next 32 outcome bits (lane i: k + i)
+          if (threadIdx.x < 32) {
+            const uint32_t b = outcome_bit(seed, cid, shot, k + threadIdx.x);
+            const uint32_t bits = __ballot_sync(0xffffffffu, b != 0u);
+            if (threadIdx.x == 0) s_rbits = bits;
+          }
+          __syncthreads();
+        }
+        const uint32_t rbit = (s_rbits >> t) & 1u;
         const int m = sct_measure(s, code, rbit, err);
         if (threadIdx.x == 0) out[o] = (uint8_t)m;
         ++k;
@@ -600,10 +649,27 @@ __global__ void __launch_bounds__(T) k_batch(BatchArgs A) {
       __syncthreads();
       if (s_stop) break;
       sct_load_image(s, img);
+      // this shot's noise draws: op j fires when word 0 >> 4 of its Philox
+      // block (counter (j, shot, cid lo, cid hi), key (seed lo, seed hi ^
+      // tag)) is below its 28-bit probability; DEPOL1 then takes X, Y or Z by
+      // floor(word 1 * 3 / 2^32)
+      uint8_t* npauli = reinterpret_cast<uint8_t*>(smem + sct_smem_words(C.n, (int)blockDim.x));
+      for (uint32_t j = threadIdx.x; j < C.n_noise; j += blockDim.x) {
+        const uint32_t e = __ldg(A.noise + C.noise_off + j), kind = e >> 28;
+        const uint4 rr = philox4x32_10(
+            make_uint4(j, shot, (uint32_t)C.cid, (uint32_t)(C.cid >> 32)),
+            make_uint2((uint32_t)seed, (uint32_t)(seed >> 32) ^ kNoiseKeyTag));
+        uint8_t p = 0;
+        if ((rr.x >> 4) < (e & 0xFFFFFFFu))
+          p = kind == 1u ? (uint8_t)OP_X
+                         : kind == 2u ? (uint8_t)OP_Z
+                                      : (uint8_t)(OP_X + (uint32_t)(((uint64_t)rr.y * 3u) >> 32));
+        npauli[j] = p;
+      }
       __syncthreads();
       sct_run_segments(s, A.segs, (int)(C.seg_begin + C.n_prefix), (int)C.seg_end, A.ops,
                        A.layer_off, seed, C.cid, shot, 0,
-                       out + C.out_off + (uint64_t)shot * C.n_meas, A.err);
+                       out + C.out_off + (uint64_t)shot * C.n_meas, A.err, npauli);
     }
     __syncthreads();
   }

@@ -100,7 +100,7 @@ static int build_range(int32_t n, const tab_gate* gates, int64_t count, HostProg
 
 void concat_programs(HostProgram& P, const HostProgram* part, size_t T, bool with_blk) {
   std::vector<size_t> o_ops(T + 1, 0), o_blk(T + 1, 0), o_loff(T + 1, 0),
-      o_boff(T + 1, 0), o_segs(T + 1, 0), o_meas(T + 1, 0);
+      o_boff(T + 1, 0), o_segs(T + 1, 0), o_meas(T + 1, 0), o_noise(T + 1, 0);
   for (size_t t = 0; t < T; ++t) {
     o_ops[t + 1] = o_ops[t] + part[t].ops.size();
     o_blk[t + 1] = o_blk[t] + part[t].blk.size();
@@ -108,6 +108,7 @@ void concat_programs(HostProgram& P, const HostProgram* part, size_t T, bool wit
     o_boff[t + 1] = o_boff[t] + part[t].blk_off.size();
     o_segs[t + 1] = o_segs[t] + part[t].segs.size();
     o_meas[t + 1] = o_meas[t] + (size_t)part[t].n_meas;
+    o_noise[t + 1] = o_noise[t] + part[t].noise.size();
   }
   P.clear(part[0].n);
   P.mode = part[0].mode;
@@ -116,6 +117,7 @@ void concat_programs(HostProgram& P, const HostProgram* part, size_t T, bool wit
   P.layer_off.resize(o_loff[T]);
   P.blk_off.resize(o_boff[T]);
   P.segs.resize(o_segs[T]);
+  P.noise.resize(o_noise[T]);
   for (size_t t = 0; t < T; ++t) {
     P.n_gates += part[t].n_gates;
     P.n_meas += part[t].n_meas;
@@ -124,6 +126,10 @@ void concat_programs(HostProgram& P, const HostProgram* part, size_t T, bool wit
     const size_t t = (size_t)ti;
     const HostProgram& Q = part[t];
     std::copy(Q.ops.begin(), Q.ops.end(), P.ops.begin() + (ptrdiff_t)o_ops[t]);
+    std::copy(Q.noise.begin(), Q.noise.end(), P.noise.begin() + (ptrdiff_t)o_noise[t]);
+    if (o_noise[t])  // noise ordinals count from the first part's first noise op
+      for (size_t i = o_ops[t]; i < o_ops[t + 1]; ++i)
+        if (dop(P.ops[i]) == OP_NOISE) P.ops[i] += (uint32_t)o_noise[t];
     if (with_blk) std::copy(Q.blk.begin(), Q.blk.end(), P.blk.begin() + (ptrdiff_t)o_blk[t]);
     for (size_t i = 0; i < Q.layer_off.size(); ++i)
       P.layer_off[o_loff[t] + i] = Q.layer_off[i] + (uint32_t)o_ops[t];
@@ -211,7 +217,8 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
       return TAB_OK;
     }
   }
-  const int vrc = validate(n, gates, 0, count);
+  int64_t n_ext = 0;
+  const int vrc = validate(n, gates, 0, count, (mode & kProgNoise) ? &n_ext : nullptr);
   if (vrc != TAB_OK) return vrc;
 
   return build_range(n, gates, count, out, mode);
@@ -257,7 +264,7 @@ static int build_range(int32_t n, const tab_gate* gates, int64_t count, HostProg
     int64_t top = base;
     for (int32_t L : seg_layer) top = std::max<int64_t>(top, (int64_t)L + 1);
     const int64_t nl = top - base;
-    const int kOps = 10;  // bucket by (layer, op) with a counting sort
+    const int kOps = 13;  // bucket by (layer, op) with a counting sort (ops 0..12)
     std::vector<uint32_t> cnt((size_t)nl * kOps, 0);
     for (size_t i = 0; i < seg_codes.size(); ++i)
       cnt[(size_t)(seg_layer[i] - base) * kOps + dop(seg_codes[i])]++;
@@ -309,9 +316,23 @@ static int build_range(int32_t n, const tab_gate* gates, int64_t count, HostProg
 
   for (int64_t i = 0; i < count; ++i) {
     const uint64_t g = gates[i];
-    const uint32_t op = (uint32_t)(g >> 56);
-    const uint32_t q1 = (uint32_t)((g >> 28) & 0xFFFFFFFull), q2 = (uint32_t)(g & 0xFFFFFFFull);
+    uint32_t op = (uint32_t)(g >> 56);
+    uint32_t q1 = (uint32_t)((g >> 28) & 0xFFFFFFFull), q2 = (uint32_t)(g & 0xFFFFFFFull);
     if (op == TAB_BARRIER || op == TAB_I) continue;
+    if (op > TAB_BARRIER) {
+      // kProgNoise: a noise op becomes a one-qubit OP_NOISE code whose second
+      // field is its ordinal (the device draws it per shot); any other
+      // extended op must have been lowered already
+      const bool noise = op == TAB_DEPOL1 || op == TAB_XERR || op == TAB_ZERR;
+      if (!noise || !(mode & kProgNoise) || !layers || blocks || P.noise.size() > 0x3FFFu) {
+        set_error("gate %lld: op %u is not accepted here", (long long)i, op);
+        return TAB_EINVAL;
+      }
+      const uint32_t kind = op == TAB_DEPOL1 ? 0u : op == TAB_XERR ? 1u : 2u;
+      P.noise.push_back(kind << 28 | (q2 & 0xFFFFFFFu));
+      op = OP_NOISE;
+      q2 = (uint32_t)P.noise.size() - 1u;
+    }
     if (op == TAB_MZ || op == TAB_MZR) {
       flush_gates();
       if (P.segs.empty() || P.segs.back().kind != 1) {
@@ -328,7 +349,7 @@ static int build_range(int32_t n, const tab_gate* gates, int64_t count, HostProg
     }
     const bool two = (op == TAB_CNOT || op == TAB_CZ || op == TAB_SWAP);
     ++run_gates;
-    P.n_gates++;
+    if (op != OP_NOISE) P.n_gates++;
     if (blocks) bb.add(op, q1, two ? q2 : 0);
     if (!layers) continue;
     int64_t L = std::max<int64_t>(last[q1], nlayers - 1);
@@ -336,7 +357,7 @@ static int build_range(int32_t n, const tab_gate* gates, int64_t count, HostProg
     L += 1;
     last[q1] = L;
     if (two) last[q2] = L;
-    seg_codes.push_back(dcode(op, q1, two ? q2 : 0));
+    seg_codes.push_back(dcode(op, q1, (two || op == OP_NOISE) ? q2 : 0));
     seg_layer.push_back((int32_t)L);
   }
   flush_gates();

@@ -33,6 +33,8 @@ struct BatchCirc {
   uint64_t img_off;             // word offset of the shared-prefix image (or the
                                 // outcome forms of a sampled circuit)
   uint32_t sampled;             // 1: terminal measurements by the sampler
+  uint32_t n_noise;             // noise ops (drawn per shot), entries noise_off ..
+  uint64_t noise_off;           //   of the batch's noise table
 };
 
 struct BatchArgs {
@@ -41,6 +43,7 @@ struct BatchArgs {
   const uint32_t* ops;
   const uint32_t* layer_off;
   const uint64_t* items;  // circuit | shot << 32 (shot = ~0: prefix item)
+  const uint32_t* noise;  // noise table: kind << 28 | probability (kProgNoise)
   int nitems;
   uint32_t* img;
   int* ready;

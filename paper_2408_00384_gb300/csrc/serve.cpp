@@ -60,6 +60,7 @@ struct Req {
   int32_t n = 0, shots = 1;
   uint64_t cid = 0;
   HostProgram prog;           // compiled at submit, in the caller's thread
+  std::vector<HostProgram> shot_progs;  // with noise ops: one program per shot
   int64_t n_meas = 0;
   size_t bytes = 0;
   tab_t h = nullptr;
@@ -170,7 +171,8 @@ int admit(tab_server_s* S, Req* r) {
   for (int32_t s = 0; rc == TAB_OK && s < r->shots; ++s) {
     if (s > 0) rc = tab_reset(r->h);
     if (rc == TAB_OK) rc = tab_set_rng(r->h, S->cfg.seed, r->cid, (uint32_t)s);
-    if (rc == TAB_OK) rc = handle_apply_program(r->h, r->prog);
+    if (rc == TAB_OK)
+      rc = handle_apply_program(r->h, r->shot_progs.empty() ? r->prog : r->shot_progs[(size_t)s]);
     if (rc == TAB_OK && r->n_meas > 0) {
       cudaStream_t used = nullptr;
       rc = handle_outcomes_async(r->h, r->pinned + (size_t)s * r->n_meas, &used);
@@ -349,35 +351,42 @@ int tab_server_submit(tab_server_t S, const tab_circuit* c, int64_t* ticket) {
     return TAB_EINVAL;
   }
   // validate now: a corrupted request is refused before it reaches the device
+  int64_t ext = 0;
+  int vrc = validate_program(c->n, c->gates, c->n_gates, &ext);
+  if (vrc != TAB_OK) return vrc;
   int64_t nm = 0;
+  bool noise = false;
   for (int64_t i = 0; i < c->n_gates; ++i) {
-    const uint64_t g = c->gates[i];
-    const uint32_t op = (uint32_t)(g >> 56);
-    const uint64_t q1 = (g >> 28) & 0xFFFFFFFull, q2 = g & 0xFFFFFFFull;
-    if (op > TAB_BARRIER) {
-      set_error("gate %lld: unknown op %u", (long long)i, op);
-      return TAB_EINVAL;
-    }
-    if (op == TAB_BARRIER) continue;
-    const bool two = op == TAB_CNOT || op == TAB_CZ || op == TAB_SWAP;
-    if (q1 >= (uint64_t)c->n || (two && q2 >= (uint64_t)c->n)) {
-      set_error("gate %lld: qubit index out of range", (long long)i);
-      return TAB_ERANGE;
-    }
-    if (two && q1 == q2) {
-      set_error("gate %lld: two-qubit op on one qubit", (long long)i);
-      return TAB_EINVAL;
-    }
-    nm += (op == TAB_MZ || op == TAB_MZR);
+    const uint32_t op = (uint32_t)(c->gates[i] >> 56);
+    nm += (op == TAB_MZ || op == TAB_MZR || op == TAB_MX || op == TAB_MY);
+    noise = noise || op == TAB_DEPOL1 || op == TAB_XERR || op == TAB_ZERR;
   }
   Req* r = new (std::nothrow) Req();
   if (!r) {
     set_error("host allocation failed");
     return TAB_ENOMEM;
   }
-  // single-SM requests need layers; grid-wide ones the form their gate kernel reads
+  // single-SM requests need layers; grid-wide ones the form their gate kernel
+  // reads.  Extended ops are lowered as tab_apply lowers them: X / Y
+  // measurements once, noise ops drawn for each shot (its own program).
   const int mode = c->n <= TAB_BATCH_MAX_QUBITS ? kProgLayers : grid_compile_mode(c->n);
-  const int crc = build_program(c->n, c->gates, c->n_gates, &r->prog, mode);
+  int crc = TAB_OK;
+  std::vector<tab_gate> low;
+  if (!ext) {
+    crc = build_program(c->n, c->gates, c->n_gates, &r->prog, mode);
+  } else if (!noise) {
+    crc = lower_for_runs(c->n, c->gates, c->n_gates, false, 0, 0, 0, low);
+    if (crc == TAB_OK) crc = build_program(c->n, low.data(), (int64_t)low.size(), &r->prog, mode);
+  } else {
+    r->shot_progs.resize((size_t)c->shots);
+    for (int32_t sh = 0; crc == TAB_OK && sh < c->shots; ++sh) {
+      crc = lower_for_runs(c->n, c->gates, c->n_gates, false, S->cfg.seed, c->circuit_id,
+                           (uint32_t)sh, low);
+      if (crc == TAB_OK)
+        crc = build_program(c->n, low.data(), (int64_t)low.size(), &r->shot_progs[(size_t)sh],
+                            mode);
+    }
+  }
   if (crc != TAB_OK) {
     delete r;
     return crc;

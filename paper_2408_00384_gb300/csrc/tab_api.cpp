@@ -59,6 +59,7 @@ struct tab_s {
   int64_t h2d_bytes = 0, d2h_bytes = 0;  // host <-> device copies made for callers
   int sticky = TAB_OK;        // latched device error
   int engine = TAB_ENGINE_AUTO;
+  int shape_threads = 0, shape_batch = 0;  // tuned launch shape (0: default)
   // pinned staging areas for program uploads (one H2D copy per upload), used
   // in turn: an upload waits only for the copy out of the area it reuses
   struct Stage {
@@ -286,7 +287,8 @@ int run_program(tab_t h, const HostProgram& hp, const DevProg& dp, uint64_t seed
                hp.segs[sj + 1].blk_begin == hp.segs[sj].blk_end + 1)
           ++sj;
         CU(launch_gates_block(h->X, h->Z, h->R, h->n, h->W, dp.blk, dp.blk_off + s.blk_begin,
-                              (int)(hp.segs[sj].blk_end - s.blk_begin), h->mw.err, h->stream));
+                              (int)(hp.segs[sj].blk_end - s.blk_begin), h->mw.err, h->stream,
+                              h->shape_threads));
         si = sj;
       }
       h->launches++;
@@ -297,7 +299,7 @@ int run_program(tab_t h, const HostProgram& hp, const DevProg& dp, uint64_t seed
       if (me == TAB_ENGINE_GRID)
         CU(launch_measure_resident(h->X, h->Z, h->R, h->n, h->Wh, dp.ops + s.op_begin, nm, h->k,
                                    seed, h->cid, h->shot, h->log + h->log_len, h->mw.err, h->rw,
-                                   h->rbar, ctas, h->stream));
+                                   h->rbar, ctas, h->stream, h->shape_batch));
       else
         CU(launch_measure(h->X, h->Z, h->R, h->n, h->Wh, dp.ops + s.op_begin, nm, h->k, seed,
                           h->cid, h->shot, h->log + h->log_len, h->mw, h->meas_ctas, h->stream));
@@ -821,7 +823,8 @@ static int apply_pipelined(tab_t h, const tab_gate* gates, int64_t count, int64_
 // The list has been validated with extended ops allowed.  Plain words are
 // copied in spans.
 static int lower_ops(int32_t n, const tab_gate* g, int64_t count, uint64_t seed, uint64_t cid,
-                     uint32_t shot, uint64_t* noise_k, std::vector<tab_gate>& out) {
+                     uint32_t shot, uint64_t* noise_k, std::vector<tab_gate>& out,
+                     bool keep_noise = false) {
   constexpr uint32_t kNoiseKeyTag = 0x4E4F4953u;  // noise draws use a key of their own
   out.clear();
   out.reserve((size_t)count + (size_t)count / 4 + 8);
@@ -866,6 +869,11 @@ static int lower_ops(int32_t n, const tab_gate* g, int64_t count, uint64_t seed,
       continue;
     }
     // a noise op
+    if (keep_noise) {  // kept as it is, for a per-shot draw on the device
+      out.push_back(g[i]);
+      span = i + 1;
+      continue;
+    }
     if (!noise_k) {
       set_error("gate %lld: noise ops are accepted by tab_apply only", (long long)i);
       return TAB_EINVAL;
@@ -1310,6 +1318,14 @@ int tab_sync(tab_t h) {
 }  // extern "C"
 
 namespace tab {
+int lower_for_runs(int32_t n, const tab_gate* g, int64_t count, bool keep_noise, uint64_t seed,
+                   uint64_t cid, uint32_t shot, std::vector<tab_gate>& out) {
+  uint64_t nk = 0;
+  return lower_ops(n, g, count, seed, cid, shot, &nk, out, keep_noise);
+}
+}  // namespace tab
+
+namespace tab {
 
 // Internal helpers for the request server (not part of the C ABI).
 int handle_outcomes_async(tab_t h, uint8_t* host, cudaStream_t* used_stream) {
@@ -1370,6 +1386,16 @@ int handle_view(tab_t h, HandleView* v) {
   v->err = h->mw.err;
   v->meas_ctas = h->meas_ctas;
   return TAB_OK;
+}
+
+void handle_set_shape(tab_t h, int block_threads, int meas_batch) {
+  h->shape_threads = block_threads;
+  h->shape_batch = meas_batch;
+}
+
+void handle_get_shape(tab_t h, int* block_threads, int* meas_batch) {
+  *block_threads = h->shape_threads;
+  *meas_batch = h->shape_batch;
 }
 
 void handle_advance_k(tab_t h, uint64_t dk) {

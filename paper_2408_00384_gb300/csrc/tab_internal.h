@@ -25,7 +25,11 @@ namespace tab {
 // ---- device op codes: op<<28 | q1<<14 | q2 (q < 2^14) --------------------
 enum : uint32_t {
   OP_I = 0, OP_X = 1, OP_Y = 2, OP_Z = 3, OP_H = 4, OP_S = 5, OP_SDG = 6,
-  OP_CNOT = 7, OP_CZ = 8, OP_SWAP = 9, OP_MZ = 10, OP_MZR = 11
+  OP_CNOT = 7, OP_CZ = 8, OP_SWAP = 9, OP_MZ = 10, OP_MZR = 11,
+  // a Pauli noise op resolved per shot on the device: q1 = qubit, q2 = its
+  // ordinal among the circuit's noise ops (index into the noise table, whose
+  // entry is kind << 28 | 28-bit probability, kind 0 DEPOL1, 1 XERR, 2 ZERR)
+  OP_NOISE = 12
 };
 __host__ __device__ __forceinline__ uint32_t dcode(uint32_t op, uint32_t a, uint32_t b) {
   return (op << 28) | (a << 14) | b;
@@ -56,19 +60,22 @@ struct Seg {
 //                engine;
 //   kProgBlocks  two-qubit blocks in super-layers (blk, blk_off): the block
 //                gate kernel of the multi-CTA engines (blocks.cpp).
-enum : int { kProgLayers = 1, kProgBlocks = 2 };
+//   kProgNoise   (with kProgLayers only) Pauli noise ops are kept as OP_NOISE
+//                codes and listed in `noise`, for per-shot draws on the device.
+enum : int { kProgLayers = 1, kProgBlocks = 2, kProgNoise = 4 };
 
 struct HostProgram {
   int32_t n = 0;
   int mode = kProgLayers;
   int64_t n_gates = 0, n_meas = 0;
-  // block records: lo = qa | qb<<14 | has_b<<28 | ent<<29 (0 none, 1 CNOT,
-  // 2 CZ) | dir<<31 (CNOT control in register 1); hi = U0 | U1<<7 | V0<<14 |
+  // block records: lo = qa | qb<<14 | has_b<<28 | ent<<29 (0 none, 1 CNOT
+  // with its control in register 0, 2 CZ); hi = U0 | U1<<7 | V0<<14 |
   // V1<<21 | swap<<28 (7-bit single-qubit Cliffords, clifford1.h)
   std::vector<uint2> blk;
   std::vector<uint32_t> blk_off;  // absolute record offsets of super-layer bounds
   std::vector<uint32_t> ops;
   std::vector<uint32_t> layer_off;  // size = layers + 1 when any gate exists
+  std::vector<uint32_t> noise;      // kProgNoise: kind << 28 | probability, per noise op
   std::vector<Seg> segs;
   // empty program for n qubits (the arrays keep their capacity)
   void clear(int32_t n_) {
@@ -79,6 +86,7 @@ struct HostProgram {
     blk_off.clear();
     ops.clear();
     layer_off.clear();
+    noise.clear();
     segs.clear();
   }
 };
@@ -88,6 +96,13 @@ struct HostProgram {
 // Returns TAB_OK or an error (message set).
 int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out,
                   int mode = kProgLayers);
+// Lower a validated list with extended ops to base ops for a batch or a
+// request: MX / MY become Z measurements between basis changes (as in
+// tab_apply); noise ops are kept as they are (keep_noise: drawn per shot on
+// the device) or resolved for (seed, cid, shot) with the noise counter
+// starting at 0.
+int lower_for_runs(int32_t n, const tab_gate* g, int64_t count, bool keep_noise, uint64_t seed,
+                   uint64_t cid, uint32_t shot, std::vector<tab_gate>& out);
 // Validate a gate list (in parallel on the host pool): TAB_OK, or the error of
 // the first bad word in list order (message set).  With `ext` given, the
 // extended ops (TAB_MX .. TAB_ZERR) are accepted and *ext counts them;
@@ -156,9 +171,10 @@ constexpr int kOpsPad = 1024;
 // Block gate kernel: super-layers of at most kMaxLayerOps records, the
 // device record buffer padded by kOpsPad records past its end.
 int gates_block_max_n();
+// threads: 128, 256 or 512 per CTA, 0 for the default by n
 cudaError_t launch_gates_block(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
                                const uint2* blk, const uint32_t* blk_off, int nlayers,
-                               int* err, cudaStream_t s);
+                               int* err, cudaStream_t s, int threads = 0);
 cudaError_t launch_measure(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh,
                            const uint32_t* mops, int nm, uint64_t k0, uint64_t seed,
                            uint64_t cid, uint32_t shot, uint8_t* out, const MeasWork& mw,
@@ -169,10 +185,12 @@ int measure_ctas_for(int n, int sm_count, int max_ctas);
 // workspace in words, and the launch.
 int resident_ctas_for(int n, int Wh, int sm_count);
 size_t resident_work_words(int n, int max_ctas);
+// batch: largest measurements per batch (a power of two), 0 for the default
 cudaError_t launch_measure_resident(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh,
                                     const uint32_t* mops, int nm, uint64_t k0, uint64_t seed,
                                     uint64_t cid, uint32_t shot, uint8_t* out, int* err,
-                                    uint32_t* work, GridBar* bar, int G, cudaStream_t s);
+                                    uint32_t* work, GridBar* bar, int G, cudaStream_t s,
+                                    int batch = 0);
 size_t measure_work_words(int n, int max_ctas);
 cudaError_t launch_expect(const uint32_t* X, const uint32_t* Z, const uint32_t* R, int n, int Wh,
                           const uint8_t* codes, int k, int8_t* out, int* err, cudaStream_t s);
@@ -210,5 +228,9 @@ struct HandleView {
 };
 int handle_view(tab_t h, HandleView* v);     // TAB_OK, or the handle's error
 void handle_advance_k(tab_t h, uint64_t dk);  // count dk more measurement ops
+// Launch shape of a handle's plain-path kernels (0: the library's default):
+// block gate kernel threads per CTA, grid-resident measurements per batch.
+void handle_set_shape(tab_t h, int block_threads, int meas_batch);
+void handle_get_shape(tab_t h, int* block_threads, int* meas_batch);
 
 }  // namespace tab

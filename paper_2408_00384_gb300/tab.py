@@ -121,6 +121,14 @@ _sig("tab_server_destroy", ctypes.c_int, [_vp])
 
 
 
+class TabTuned(ctypes.Structure):
+    _fields_ = [("engine", _i32), ("block_threads", _i32), ("meas_batch", _i32),
+                ("from_cache", _i32), ("tried", _i32), ("best_ms", ctypes.c_float)]
+
+
+_sig("tab_tune", ctypes.c_int, [_vp, _vp, _i32, _P(TabTuned)])
+
+
 class TabConfig(ctypes.Structure):
     _fields_ = [("block_threads", _i32), ("meas_batch", _i32), ("grid_ctas", _i32),
                 ("debug", _u32), ("wait_limit_ns", _u64)]
@@ -293,6 +301,14 @@ class Tableau:
         g = _u64arr(gates)
         _check(_L.tab_apply(self._h, g.ctypes.data if g.size else None, g.size))
 
+    def tune(self, prog: Program, reps: int = 3) -> dict:
+        """Autotune this handle's launch shape on a compiled program
+        (tab_tune); the tableau is left at |0^n>.  reps < 0 ignores the
+        TAB_AUTOTUNE_CACHE file."""
+        t = TabTuned()
+        _check(_L.tab_tune(self._h, prog._h, int(reps), ctypes.byref(t)))
+        return {k: getattr(t, k) for k, _ in TabTuned._fields_}
+
     def run(self, prog: Program):
         _check(_L.tab_run(self._h, prog._h))
 
@@ -441,7 +457,7 @@ def _circuit_array(circuits):
 
 def n_meas_of(gates) -> int:
     op = (_u64arr(gates) >> np.uint64(56))
-    return int(np.isin(op, (10, 11)).sum())
+    return int(np.isin(op, (10, 11, 13, 14)).sum())
 
 
 def batch_run(circuits, seed: int = 1, out=None) -> list:

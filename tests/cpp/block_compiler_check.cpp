@@ -26,6 +26,7 @@ static void c1h(uint32_t m, uint32_t& x, uint32_t& z, uint32_t& r) {
 static void blockh(uint2 rec, std::vector<uint32_t>& sx, std::vector<uint32_t>& sz, uint32_t& r) {
   const uint32_t qa = rec.x & 0x3FFFu, qb = (rec.x >> 14) & 0x3FFFu;
   const bool two = (rec.x >> 28) & 1u;
+  // emitted records keep a CNOT's control in register 0 (bit 31 is 0)
   const uint32_t ent = (rec.x >> 29) & 3u, dir = rec.x >> 31, m = rec.y;
   uint32_t x0 = sx[qa], z0 = sz[qa];
   c1h(m & 0x7F, x0, z0, r);
@@ -145,7 +146,25 @@ int main() {
       for (int i = 0; i + 1 < n; i += 2) g.push_back(tab_make_gate(rng() % 4 ? TAB_CNOT : TAB_CZ, p[i], p[i + 1]));
     }
     HostProgram hp; build_program(n, g.data(), (int64_t)g.size(), &hp, kProgBlocks);
-    printf("layer circuit: %zu gates -> %zu blocks, %zu super-layers\n", g.size(), hp.blk.size(), hp.blk_off.size() - 1);
+    // windows of 32 records (one warp's): how many read 32 distinct banks
+    // for both qubits (the bank order's goal), and the worst bank load
+    long long win = 0, distinct = 0; int worst = 0;
+    for (size_t L = 0; L + 1 < hp.blk_off.size(); ++L) {
+      for (uint32_t w0 = hp.blk_off[L]; w0 < hp.blk_off[L + 1]; w0 += 32) {
+        uint32_t ma = 0, mb = 0; bool ok = true; int ca[32] = {0}, cb[32] = {0};
+        for (uint32_t i = w0; i < std::min(hp.blk_off[L + 1], w0 + 32); ++i) {
+          const uint32_t a = hp.blk[i].x & 31u, b = (hp.blk[i].x >> 14) & 31u;
+          ok = ok && !((ma >> a) & 1u) && !((mb >> b) & 1u);
+          ma |= 1u << a; mb |= 1u << b;
+          worst = std::max(worst, std::max(++ca[a], ++cb[b]));
+          if (hp.blk[i].x >> 31) { printf("record bit 31 set\n"); ++bad; }
+        }
+        ++win; distinct += ok;
+      }
+    }
+    printf("layer circuit: %zu gates -> %zu blocks, %zu super-layers; windows %lld, "
+           "conflict-free %lld, worst bank load %d\n", g.size(), hp.blk.size(), hp.blk_off.size() - 1,
+           win, distinct, worst);
     if (hp.blk_off.size() - 1 != 50 || hp.blk.size() != 25000) ++bad;
   }
   // the pipelined apply's host side: chunks compiled apart (build_validated_

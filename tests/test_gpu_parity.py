@@ -215,9 +215,9 @@ def test_extended_ops_long_list():
     assert_same(700, g, seed=4, cid=1, engine=tab.ENGINE_GRID)
 
 
-def test_extended_ops_in_programs_and_batches():
-    """Programs take MX / MY (lowered once) but not noise ops; batches take
-    neither."""
+def test_extended_ops_in_programs():
+    """Programs take MX / MY (lowered once) but not noise ops (a program
+    replays under any RNG setting, and noise is drawn per shot)."""
     n = 40
     g = C.random_extended_ops(n, 300, seed=8, p_noise=0.0)
     with tab.Tableau(n) as t:
@@ -234,9 +234,6 @@ def test_extended_ops_in_programs_and_batches():
     noisy = C.random_extended_ops(n, 60, seed=9, p_meas=0.0, p_noise=0.5)
     with pytest.raises(tab.TabError) as ei:
         tab.Program(n, noisy)
-    assert ei.value.code == tab.TAB_EINVAL
-    with pytest.raises(tab.TabError) as ei:
-        tab.Batch([(n, g, 2, 0)])
     assert ei.value.code == tab.TAB_EINVAL
 
 
