@@ -119,42 +119,86 @@ constexpr int kBlkChunk = 512;                  // records per TMA copy (4 KB)
 constexpr int kBlkSlots = 16;                   // 64 KB ring (12 slots, 48 KB, for large n)
 constexpr int kBlkRing = kBlkChunk * kBlkSlots;
 
-// Each lane branches on its own codes' classes: identity codes are skipped
-// and H / S take their two-operation forms (random layers mix only those, so
-// a warp that diverges runs two short paths); other codes take the general
-// form.  No warp votes.
-__device__ __forceinline__ void apply_block(uint2 rec, uint32_t* sx, uint32_t* sz, uint32_t& r) {
-  const uint32_t qa = rec.x & 0x3FFFu, qb = (rec.x >> 14) & 0x3FFFu;
-  const bool two = (rec.x >> 28) & 1u;
-  const uint32_t ent = (rec.x >> 29) & 3u;
-  const uint32_t m = rec.y;
-  uint32_t x0 = sx[qa], z0 = sz[qa];
-  c1_apply_class(m & 0x7Fu, x0, z0, r);
-  if (!two) {
-    sx[qa] = x0;
-    sz[qa] = z0;
-    return;
+// Single-qubit codes as masks: for code m, {alpha, beta, gamma, delta} and
+// {eps, zeta, eta, 0} of clifford1.h as all-ones / all-zero words, two uint4
+// per code in shared memory, so applying a code is two vector loads (mostly
+// broadcasts: a layer uses few distinct codes) and branch-free LOP3 work.
+__device__ __forceinline__ void c1_masks_init(uint4* tab, int tid, int T) {
+  for (int m = tid; m < 128; m += T) {
+    const uint32_t u = (uint32_t)m;
+    tab[2 * m] = make_uint4(0u - (u & 1u), 0u - ((u >> 1) & 1u), 0u - ((u >> 2) & 1u),
+                            0u - ((u >> 3) & 1u));
+    tab[2 * m + 1] = make_uint4(0u - ((u >> 4) & 1u), 0u - ((u >> 5) & 1u), 0u - ((u >> 6) & 1u), 0u);
   }
-  uint32_t x1 = sx[qb], z1 = sz[qb];
-  c1_apply_class((m >> 7) & 0x7Fu, x1, z1, r);
-  if (ent == 1u) {  // CNOT, control in register 0 (the compiler's convention)
-    r ^= x0 & z1 & ~(x1 ^ z0);
-    x1 ^= x0;
-    z0 ^= z1;
-  } else if (ent == 2u) {  // CZ
-    r ^= x0 & x1 & (z0 ^ z1);
-    const uint32_t z0n = z0 ^ x1;
-    z1 ^= x0;
-    z0 = z0n;
+}
+__device__ __forceinline__ void c1_apply_masks(const uint4* tab, uint32_t m, uint32_t& x,
+                                               uint32_t& z, uint32_t& r) {
+  const uint4 a = tab[2 * m], e = tab[2 * m + 1];
+  r ^= (x & e.x) ^ (z & e.y) ^ (x & z & e.z);
+  const uint32_t xn = (x & a.x) ^ (z & a.y);
+  z = (x & a.z) ^ (z & a.w);
+  x = xn;
+}
+
+// NB blocks of one super-layer (pairwise-disjoint qubits) on the slab's 32
+// rows, blocks with on[j] false skipped: every load first, then the NB
+// independent computations, then every store, so the blocks' dependent
+// chains interleave.  Branch-free except where a whole warp usually agrees:
+// U_0 (x) U_1 is skipped when both are the identity (every block past a
+// qubit's first, as the compiler folds later single-qubit gates into V), and
+// a single-qubit block skips its second column's load and store.  The
+// entangler is computed as CNOT-or-CZ masks.
+template <int NB>
+__device__ __forceinline__ void apply_blocks(const uint2 (&rec)[NB], const bool (&on)[NB],
+                                             const uint4* c1m, uint32_t* sx, uint32_t* sz,
+                                             uint32_t& r) {
+  uint32_t qa[NB], qb[NB], m[NB], x0[NB], z0[NB], x1[NB], z1[NB];
+  bool two[NB];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    qa[j] = rec[j].x & 0x3FFFu;
+    qb[j] = (rec[j].x >> 14) & 0x3FFFu;
+    two[j] = on[j] && ((rec[j].x >> 28) & 1u);
+    m[j] = rec[j].y;
+    x0[j] = on[j] ? sx[qa[j]] : 0u;
+    z0[j] = on[j] ? sz[qa[j]] : 0u;
+    x1[j] = two[j] ? sx[qb[j]] : 0u;
+    z1[j] = two[j] ? sz[qb[j]] : 0u;
   }
-  c1_apply_class((m >> 14) & 0x7Fu, x0, z0, r);
-  c1_apply_class((m >> 21) & 0x7Fu, x1, z1, r);
-  const bool sw = (m >> 28) & 1u;
-  const uint32_t da = sw ? qb : qa, db = sw ? qa : qb;
-  sx[da] = x0;
-  sz[da] = z0;
-  sx[db] = x1;
-  sz[db] = z1;
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    if ((m[j] & 0x3FFFu) != (kC1Ident | (kC1Ident << 7))) {
+      c1_apply_masks(c1m, m[j] & 0x7Fu, x0[j], z0[j], r);
+      c1_apply_masks(c1m, (m[j] >> 7) & 0x7Fu, x1[j], z1[j], r);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    // CNOT with control in register 0 (the compiler's convention), or CZ
+    const uint32_t ent = (rec[j].x >> 29) & 3u;
+    const uint32_t cn = ent == 1u ? 0xffffffffu : 0u, cz = ent == 2u ? 0xffffffffu : 0u;
+    r ^= (cn & x0[j] & z1[j] & ~(x1[j] ^ z0[j])) ^ (cz & x0[j] & x1[j] & (z0[j] ^ z1[j]));
+    const uint32_t x1n = x1[j] ^ (cn & x0[j]);
+    const uint32_t z0n = z0[j] ^ (cn & z1[j]) ^ (cz & x1[j]);
+    z1[j] ^= cz & x0[j];
+    x1[j] = x1n;
+    z0[j] = z0n;
+    c1_apply_masks(c1m, (m[j] >> 14) & 0x7Fu, x0[j], z0[j], r);
+    c1_apply_masks(c1m, (m[j] >> 21) & 0x7Fu, x1[j], z1[j], r);
+  }
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    const bool sw = (m[j] >> 28) & 1u;
+    const uint32_t da = sw ? qb[j] : qa[j], db = sw ? qa[j] : qb[j];
+    if (on[j]) {
+      sx[da] = x0[j];
+      sz[da] = z0[j];
+    }
+    if (two[j]) {
+      sx[db] = x1[j];
+      sz[db] = z1[j];
+    }
+  }
 }
 
 template <int T, int SLOTS>
@@ -168,6 +212,7 @@ __global__ void __launch_bounds__(T) k_gates_block(uint32_t* __restrict__ X, uin
   uint32_t* sx = sm + 2 * SLOTS * kBlkChunk;            // X-plane word of every column (this slab)
   uint32_t* sz = sx + n;                       // Z-plane word of every column
   __shared__ __align__(8) uint64_t bars[SLOTS];
+  __shared__ uint4 c1m[256];  // masks of the 128 single-qubit codes
   __shared__ uint32_t s_r;
   __shared__ int s_abort;
   const int w = blockIdx.x, tid = threadIdx.x;
@@ -188,6 +233,7 @@ __global__ void __launch_bounds__(T) k_gates_block(uint32_t* __restrict__ X, uin
     sx[a] = X[(size_t)a * W + w];
     sz[a] = Z[(size_t)a * W + w];
   }
+  c1_masks_init(c1m, tid, T);
   __syncthreads();
 
   uint32_t racc = 0u;
@@ -221,8 +267,14 @@ __global__ void __launch_bounds__(T) k_gates_block(uint32_t* __restrict__ X, uin
     }
     __syncthreads();
     if (s_abort) break;
-    for (uint32_t g = lb + tid; g < le; g += T)
-      apply_block(ring[(g - base) % (SLOTS * kBlkChunk)], sx, sz, racc);
+    // thread tid takes blocks lb + tid, lb + tid + T, ... two at a time
+    for (uint32_t g = lb + tid; g < le; g += 2 * T) {
+      const uint32_t g2 = g + T;
+      const uint2 recs[2] = {ring[(g - base) % (SLOTS * kBlkChunk)],
+                             ring[(g2 < le ? g2 - base : g - base) % (SLOTS * kBlkChunk)]};
+      const bool on[2] = {true, g2 < le};
+      apply_blocks<2>(recs, on, c1m, sx, sz, racc);
+    }
     prev_lb = lb;
     lb = le;
   }
@@ -246,7 +298,11 @@ __global__ void __launch_bounds__(T) k_gates_block(uint32_t* __restrict__ X, uin
 
 constexpr int kMaxSmemBytes = 227 * 1024;
 
-int gates_block_max_n() { return (kMaxSmemBytes - 4096 - kBlkRing * 8) / 8; }
+// dynamic shared memory of the block kernel: what is left next to its static
+// share (mbarriers, code masks: under 5 KB)
+constexpr int kBlkDynMax = kMaxSmemBytes - 8192;
+
+int gates_block_max_n() { return (kBlkDynMax - kBlkRing * 8) / 8; }
 
 // Threads per CTA of the block kernel: the kernel is latency-bound per
 // super-layer, so a CTA just large enough for one block per thread (n/2
@@ -265,7 +321,7 @@ static cudaError_t launch_gates_block_t(uint32_t* X, uint32_t* Z, uint32_t* R, i
   const size_t smem = (size_t)SLOTS * kBlkChunk * 8 + (size_t)n * 2 * sizeof(uint32_t);
   // once per device; shard threads may launch concurrently
   const cudaError_t attr =
-      ensure_smem_limit((const void*)k_gates_block<T, SLOTS>, kMaxSmemBytes - 4096);
+      ensure_smem_limit((const void*)k_gates_block<T, SLOTS>, kBlkDynMax);
   if (attr != cudaSuccess) return attr;
   k_gates_block<T, SLOTS><<<W, T, smem, s>>>(X, Z, R, n, W, blk, blk_off, nlayers, err);
   return cudaGetLastError();
@@ -273,10 +329,10 @@ static cudaError_t launch_gates_block_t(uint32_t* X, uint32_t* Z, uint32_t* R, i
 
 // Ring slots: 16, or 12 where the smaller ring (still two super-layers of at
 // most kMaxLayerOps records plus a chunk on each side) is what lets two CTAs
-// share an SM (228 KB per SM, 1 KB of it reserved per CTA, a few hundred
-// bytes of static shared memory).
+// share an SM (228 KB per SM, 1 KB of it reserved per CTA, about 4.4 KB of
+// static shared memory).
 static int block_slots(int n) {
-  const size_t two_per_sm = 115000;
+  const size_t two_per_sm = 111000;
   const size_t c16 = (size_t)16 * kBlkChunk * 8 + (size_t)8 * n;
   const size_t c12 = (size_t)12 * kBlkChunk * 8 + (size_t)8 * n;
   return (c16 > two_per_sm && c12 <= two_per_sm) ? 12 : 16;

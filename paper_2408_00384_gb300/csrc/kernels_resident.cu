@@ -43,22 +43,19 @@ struct CommGrid {
     if (A.skip_arrival && r == C - 1) return false;
     return grid_sync(A.bar, A.err, epoch, A.wait_ns);
   }
-  // owners write the measured columns (their current state) to stage[buf]
+  // owners write the X bits of the measured columns (their current state)
+  // to stage[buf]
   __device__ void stage_columns(const ResSmem& s, int buf, const ResBatch& b, int W, int Wp,
                                 int KB) {
     for (int e = threadIdx.x; e < b.nown * W; e += blockDim.x) {
       const int j = e / W, w = e - j * W;
       const int d = b.own[j];
-      const size_t off = (size_t)(b.q[d] / C) * Wp + w;
-      uint32_t* dst = A.stage + (((size_t)buf * KB + d) * 2) * W;
-      dst[w] = s.Xs[off];
-      dst[W + w] = s.Zs[off];
+      A.stage[((size_t)buf * KB + d) * W + w] = s.Xs[(size_t)(b.q[d] / C) * Wp + w];
     }
   }
-  // word w of slot d's measured column (plane 0: X, 1: Z), staged in L2
-  __device__ uint32_t slot_word(const ResSmem&, int buf, int d, int w, int plane, int W,
-                                int KB) const {
-    return __ldcg(A.stage + (((size_t)buf * KB + d) * 2 + plane) * W + w);
+  // word w of the X bits of slot d's measured column, staged in L2
+  __device__ uint32_t slot_word(const ResSmem&, int buf, int d, int w, int W, int KB) const {
+    return __ldcg(A.stage + ((size_t)buf * KB + d) * W + w);
   }
   __device__ void publish_dp(uint32_t*, int buf, int i, int kb, uint32_t v) {
     if (threadIdx.x == 0) A.dp[((size_t)buf * kb + i) * C + r] = v;
@@ -92,7 +89,7 @@ struct CommGrid {
 };
 
 template <int WL>
-__global__ void __launch_bounds__(32 * kResMaxWarps) k_measure_resident(const __grid_constant__ ResArgs A) {
+__global__ void __launch_bounds__(32 * kResMaxWarps, 1) k_measure_resident(const __grid_constant__ ResArgs A) {
   extern __shared__ __align__(16) uint32_t sm[];
   CommGrid cm(A);
   measure_resident<WL>(A, cm, sm);
@@ -171,7 +168,7 @@ int resident_ctas_for(int n, int Wh, int sm_count) {
 
 size_t resident_work_words(int n, int max_ctas) {
   const int W = 2 * half_words(n);
-  return 4 * (size_t)kBatchMax * W          // staged columns [2][kb][2][W]
+  return 2 * (size_t)kBatchMax * W          // staged X bits of measured columns [2][kb][W]
          + 2 * (size_t)kBatchMax * max_ctas // deterministic partials [2][kb][G]
          + (size_t)max_ctas * 2 * W         // sign partials for the fold
          + 2 * (size_t)W + 16;              // base signs
@@ -189,12 +186,11 @@ cudaError_t launch_measure_resident(uint32_t* X, uint32_t* Z, uint32_t* R, int n
   ResArgs A = res_args(X, Z, R, n, Wh, mops, nm, k0, seed, cid, shot, out, err);
   const int W = 2 * Wh;
   const int cap = batch >= 1 && batch <= kBatchMax ? batch : batch_cap();
-  A.kb = res_batch_for(n, Wh, G, res_dyn_limit(), std::min(cap, res_batch_cap(wl)), false);
+  A.kb = res_batch_for(n, Wh, G, res_dyn_limit(), cap, false);
   if (A.kb == 0) return cudaErrorInvalidValue;
-  // replay warps: enough for the batch's columns; apply warps: one column
-  // each where the CTA's warp budget allows, at most 32 columns each
-  const int cpr = res_cols_per_replay(wl);
-  A.nreplay = (A.kb + cpr - 1) / cpr;
+  // the replay chain warp and its helpers; apply warps: one column each
+  // where the CTA's warp budget allows, at most 32 columns each
+  A.nreplay = 1 + kResHelpers;
   const int nown = (n + G - 1) / G;
   int napply = std::min(nown, kResMaxWarps - A.nreplay);
   napply = std::max(napply, (nown + 31) / 32);
@@ -204,7 +200,7 @@ cudaError_t launch_measure_resident(uint32_t* X, uint32_t* Z, uint32_t* R, int n
   A.wait_ns = run_wait_limit_ns();
   A.skip_arrival = (run_config().debug & TAB_DEBUG_SKIP_BARRIER_ARRIVAL) ? 1 : 0;
   A.stage = work;
-  A.dp = A.stage + 4 * (size_t)A.kb * W;
+  A.dp = A.stage + 2 * (size_t)A.kb * W;
   A.ph = A.dp + 2 * (size_t)A.kb * G;
   A.r4 = A.ph + (size_t)G * 2 * W;
   A.bar = bar;

@@ -32,17 +32,18 @@
 //
 // Blocked measurements.  The X|Z bits a measurement leaves behind depend only
 // on X|Z bits (never on signs or outcomes), and the pivot and the mask of rows
-// with x_ha = 1 of measurement m depend only on the measured columns.  So a
+// with x_ha = 1 of measurement m depend only on the X bits of the measured
+// columns: a column's X bits change only through the X bits of the mask and
+// of row p (x_hc ^= x_pc for h in S', row p-n := row p, x_pc := 0).  So a
 // batch of K consecutive measurements runs in two overlapping phases:
-//   phase 1: the measured columns of the batch (staged by their owners at
-//            the end of the previous batch) are replayed through the K
-//            measurements in the registers of the CTA's R replay warps, each
-//            holding up to res_cols_per_replay(WL) columns, until each
-//            column's last measurement in the batch; one named barrier per
-//            measurement among the replay warps still running (a __syncwarp
-//            when R = 1).  The warp holding the column measurement m measures
-//            publishes its pivot p_m and mask S_m (the measured column at that
-//            time) with a release store of a counter;
+//   phase 1: the X bits of the batch's measured columns (staged by their
+//            owners at the end of the previous batch) are copied into shared
+//            memory and replayed through the K measurements: a chain warp
+//            finds each pivot p_m on the measured column, publishes p_m and
+//            the mask S_m (the measured column at that time) with a release
+//            store of a counter and applies measurement m to the next two
+//            measured columns in registers; helper warps apply it to the
+//            other columns still measured later in the batch;
 //   phase 2: the CTA's A apply warps, each owning a contiguous block of the
 //            CTA's columns, apply the K rowsums, in order, to their columns
 //            and their shares, each as soon as the counter shows it published
@@ -63,24 +64,15 @@
 
 namespace tab {
 
-// Warp roles.  R replay warps (phase 1), each holding up to
-// res_cols_per_replay(WL) measured columns of the batch in registers (8, 4,
-// 2, 1 for 2, 4, 8, 16 words per lane: 32 registers of columns), then A apply
-// warps (phase 2), each owning at most 32 of the CTA's columns (one ballot);
-// R + A <= kResMaxWarps.  The host picks R from the batch size and A from the
-// CTA's columns, one column per apply warp where that fits
-// (kernels_resident.cu): the work of one measurement is a short dependent
-// chain per warp, so several warps per SM hide each other's latency.
+// Warp roles.  Warp 0 and kResHelpers helper warps replay the batch (phase
+// 1); the next A warps are apply warps (phase 2), each owning at most 32 of
+// the CTA's columns (one ballot); 1 + kResHelpers + A <= kResMaxWarps.  The host picks A from the CTA's columns, one column
+// per apply warp where that fits (kernels_resident.cu): the work of one
+// measurement is a short dependent chain per warp, so several warps per SM
+// hide each other's latency.
 constexpr int kResMaxWarps = 16;
-constexpr int kResMaxReplay = 8;
 constexpr int kBatchMax = 32;                       // largest batch of any instance
-__host__ __device__ constexpr int res_cols_per_replay(int wl) { return wl >= 16 ? 1 : 16 / wl; }
-// Largest batch the replay warps hold for WL words per lane.
-__host__ __device__ constexpr int res_batch_cap(int wl) {
-  return kResMaxReplay * res_cols_per_replay(wl) < kBatchMax
-             ? kResMaxReplay * res_cols_per_replay(wl)
-             : kBatchMax;
-}
+constexpr int kResHelpers = 4;                      // helper warps of the replay
 constexpr int kResMaxLocalCols = 32 * (kResMaxWarps - 1);  // columns of one CTA
 constexpr int kPubSpinMax = 1 << 22;              // polls (64 ns apart) before a wait gives up
 
@@ -94,11 +86,11 @@ struct ResArgs {
   uint8_t* out;
   int* err;
   int kb;  // measurements per batch (1..kBatchMax)
-  int nreplay, napply;  // replay warps R, apply warps A (blockDim = 32 (R + A))
+  int nreplay, napply;  // replay warps R = 1 + kResHelpers, apply warps A (blockDim = 32 (R + A))
   unsigned long long wait_ns;  // limit of each grid-barrier wait
   int skip_arrival;            // test-only fault injection (TAB_DEBUG_SKIP_BARRIER_ARRIVAL)
   // CommGrid workspace (global memory)
-  uint32_t* stage;  // [2][kb][2][W] measured columns of the next batch
+  uint32_t* stage;  // [2][kb][W] X bits of the measured columns of the next batch
   uint32_t* dp;     // [2][kb][C] deterministic partials
   uint32_t* ph;     // [C][2][W] sign partials for the fold
   uint32_t* r4;     // [2][W] base signs for the fold
@@ -121,6 +113,7 @@ __host__ __device__ inline ResLayout res_layout(int n, int Wh, int C, int kb, bo
   L.words = 2 * (size_t)L.ncl * L.Wp            // own X, Z columns
             + 4 * (size_t)W                      // CTA sign partial (lo, hi), base signs (lo, hi)
             + (size_t)kb * W                     // mask of each measurement of the batch
+            + (size_t)kb * L.Wp                  // X bits of the batch's measured columns
             + (push ? 4 * (size_t)kb * W : 0)    // measured columns X, Z, double-buffered
             + 2 * (size_t)kb * C;                // deterministic partials, double-buffered
   return L;
@@ -176,6 +169,17 @@ __device__ __forceinline__ int res_ld_acquire(const int* p) {
                : "memory");
   return v;
 }
+// Wait until *p >= v (lane 0 polls with acquire loads; warp-wide); false
+// when the wait gives up after kPubSpinMax polls.  With `nap`, polls after
+// the first 256 are 64 ns apart.
+__device__ __forceinline__ bool res_wait_geq(const int* p, int v, bool nap) {
+  for (int it = 0; it <= kPubSpinMax; ++it) {
+    const int seen = __shfl_sync(0xffffffffu, (threadIdx.x & 31) == 0 ? res_ld_acquire(p) : 0, 0);
+    if (seen >= v) return true;
+    if (nap && it >= 256) __nanosleep(64);
+  }
+  return false;
+}
 // v[k] for a warp-uniform k, without dynamic register indexing
 template <int WL>
 __device__ __forceinline__ uint32_t res_pick(const uint32_t (&v)[WL], int k) {
@@ -187,7 +191,7 @@ __device__ __forceinline__ uint32_t res_pick(const uint32_t (&v)[WL], int k) {
 
 // Shared-memory pointers of the per-CTA state.
 struct ResSmem {
-  uint32_t *Xs, *Zs, *PHlo, *PHhi, *R4lo, *R4hi, *SM, *TX, *TZ, *dpv;
+  uint32_t *Xs, *Zs, *PHlo, *PHhi, *R4lo, *R4hi, *SM, *CX, *TX, *TZ, *dpv;
 };
 
 __device__ __forceinline__ ResSmem res_smem(uint32_t* sm, const ResLayout& Ly, int W, int kb,
@@ -200,7 +204,8 @@ __device__ __forceinline__ ResSmem res_smem(uint32_t* sm, const ResLayout& Ly, i
   s.R4lo = s.PHhi + W;
   s.R4hi = s.R4lo + W;
   s.SM = s.R4hi + W;             // [kb][W] mask of each measurement of the batch
-  s.TX = s.SM + (size_t)kb * W;  // [2][kb][W] measured columns, X plane (push only)
+  s.CX = s.SM + (size_t)kb * W;  // [kb][Wp] replayed X bits of the measured columns
+  s.TX = s.CX + (size_t)kb * Ly.Wp;  // [2][kb][W] measured columns, X plane (push only)
   s.TZ = s.TX + (push ? 2 * (size_t)kb * W : 0);
   s.dpv = s.TZ + (push ? 2 * (size_t)kb * W : 0);  // [2][kb][C]
   return s;
@@ -214,10 +219,9 @@ struct ResBatch {
   int lw[kBatchMax];         // warp of this CTA owning that column, or -1
   int q[kBatchMax];          // qubit of each slot
   int last[kBatchMax];       // last measurement of each slot
-  int cntw[kBatchMax];       // replay warps still running at each measurement
-  int wlast[kResMaxReplay];  // last measurement each replay warp takes part in
-  uint32_t wlive[kResMaxReplay][kBatchMax];  // replay warp w, measurement i: its columns
-                                             // still needed after i (bit j: slot w*CPR+j)
+  uint32_t live[kBatchMax];  // slots measured again after measurement i (bit d: slot d)
+  uint32_t hm[kBatchMax];    // live[i] less slot[i+1] and slot[i+2]: the helpers' slots at i
+  int s3[kBatchMax];         // slot[i+3], or -1
   int own[kBatchMax];        // slots whose column this CTA owns
   int P[kBatchMax];          // pivot row of each measurement (-1: deterministic)
   uint32_t dacc[kBatchMax];  // this CTA's deterministic partial
@@ -226,17 +230,17 @@ struct ResBatch {
   int D, nown, anydet;
   volatile int keff;         // measurements of the batch (a deterministic reset ends it)
   int npub;                  // measurements whose pivot and mask are published
+  int hpri[kResHelpers];     // helper h: updates whose look-ahead column it has applied
   uint32_t plast;            // code of the previous batch's last measurement
 };
 
 // Slots of a batch of K <= 32 measurements, lane i holding code i: distinct
 // measured qubits in first-occurrence order, each slot's last measurement,
-// the replay warp (R of them, cpr slots each) that holds each slot and when
-// each replay warp's columns are still needed, and the slots, columns and
+// the slots still needed after each measurement, and the slots, columns and
 // apply warps (warp R + local column / cpw) this CTA owns.  Warp-wide (one
 // warp).
 __device__ __forceinline__ void res_batch_slots(uint32_t code, int K, int C, int r, int cpw,
-                                                int R, int cpr, ResBatch& b) {
+                                                int R, ResBatch& b) {
   const int lane = threadIdx.x & 31;
   const bool v = lane < K;
   const int a = v ? (int)dq1(code) : -1 - lane;
@@ -261,26 +265,17 @@ __device__ __forceinline__ void res_batch_slots(uint32_t code, int K, int C, int
   }
   __syncwarp();
   const int D = __popc(firsts);
-  if (lane < R) {
-    int wl = -1;
-    for (int d = lane * cpr; d < D && d < (lane + 1) * cpr; ++d) wl = b.last[d] > wl ? b.last[d] : wl;
-    b.wlast[lane] = wl;
-  }
-  if (v) {  // columns of each replay warp still needed after measurement `lane`
-    for (int w = 0; w < R; ++w) {
-      uint32_t live = 0u;
-      for (int j = 0; j < cpr; ++j) {
-        const int d = w * cpr + j;
-        if (d < D && b.last[d] > lane) live |= 1u << j;
-      }
-      b.wlive[w][lane] = live;
-    }
-  }
-  __syncwarp();
-  if (v) {
-    int cnt = 0;
-    for (int w = 0; w < R; ++w) cnt += b.wlast[w] >= lane;
-    b.cntw[lane] = cnt;
+  const int s1 = __shfl_down_sync(0xffffffffu, slot, 1), s2 = __shfl_down_sync(0xffffffffu, slot, 2);
+  const int s3 = __shfl_down_sync(0xffffffffu, slot, 3);
+  if (v) {  // slots still needed after measurement `lane`
+    uint32_t live = 0u;
+    for (int d = 0; d < D; ++d)
+      if (b.last[d] > lane) live |= 1u << d;
+    b.live[lane] = live;
+    if (lane + 1 < K) live &= ~(1u << s1);
+    if (lane + 2 < K) live &= ~(1u << s2);
+    b.hm[lane] = live;
+    b.s3[lane] = lane + 3 < K ? s3 : -1;
   }
   if (mine) b.own[__popc(owned & ((1u << lane) - 1u))] = slot;
   if (lane == 0) {
@@ -289,18 +284,8 @@ __device__ __forceinline__ void res_batch_slots(uint32_t code, int K, int C, int
   }
 }
 
-// Column j of a replay warp's register block (j warp-uniform).
-template <int CPR, int WL>
-__device__ __forceinline__ uint32_t res_pick_col(const uint32_t (&t)[CPR][WL], int j, int k) {
-  uint32_t o = 0u;
-#pragma unroll
-  for (int c = 0; c < CPR; ++c) o |= t[c][k] & (0u - (uint32_t)(c == j));
-  return o;
-}
-
 template <int WL, class Comm>
 __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
-  constexpr int CPR = res_cols_per_replay(WL);
   constexpr bool kPush = Comm::kPush;
   const int R = A.nreplay, NA = A.napply;
   const int C = cm.size(), r = cm.rank(), tid = threadIdx.x, T = blockDim.x;
@@ -337,7 +322,7 @@ __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
   if (warp == 0) {
     const int K0 = A.nm < KB ? A.nm : KB;
     const uint32_t c = lane < K0 ? __ldg(A.mops + lane) : 0u;
-    res_batch_slots(c, K0, C, r, cpw, R, CPR, b);
+    res_batch_slots(c, K0, C, r, cpw, R, b);
     if (lane == 0) b.anydet = 0;
   }
   if (!cm.start()) return;
@@ -384,107 +369,279 @@ __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
     if (tid == 0) {
       b.keff = K;
       b.npub = 0;
+      for (int h = 0; h < kResHelpers; ++h) b.hpri[h] = 0;
+    }
+    // the X bits of the batch's measured columns into shared memory for the
+    // replay warp, by every thread (independent L2 loads, four in flight)
+    {
+      const int DW = b.D * W;
+      for (int e0 = tid; e0 < DW; e0 += 4 * T) {
+        uint32_t v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = e0 + u * T;
+          v[u] = e < DW ? cm.slot_word(s, par, e / W, e % W, W, KB) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = e0 + u * T;
+          if (e < DW) s.CX[(size_t)(e / W) * Wp + e % W] = v[u];
+        }
+      }
     }
     __syncthreads();
 
-    // ---- phase 1: replay the batch on its measured columns, replay warp w
-    // holding slots w*CPR .. w*CPR+CPR-1 in registers until their last
-    // measurement; the holder of measurement i's column publishes its mask
-    // S_i and pivot P_i
-    const int D = b.D;
-    if (warp < R && warp * CPR < D) {
-      const int s0 = warp * CPR;
-      uint32_t tx[CPR][WL], tz[CPR][WL];
+    // ---- phase 1: replay the batch on the X bits of its measured columns
+    // (shared memory, slot d at CX + d*Wp, lane l taking words l, l+32, ...).
+    // Warp 0 runs the chain: for measurement i it holds slot[i] and
+    // slot[i+1] in registers, current through measurement i-1; it finds the
+    // pivot P_i on slot[i], publishes P_i and the mask S_i (release store of
+    // npub), then applies measurement i to slot[i+1] and slot[i+2] (stored
+    // back) and moves on.  The helper warps apply measurement j to every
+    // other slot still measured later in the batch (helper h: slots
+    // d = h mod kResHelpers), in order, the slot warp 0 takes next
+    // (slot[j+3]) first, after which they bump hpri[h]; warp 0 waits for that
+    // before it loads slot[i+2].  So each slot sees the measurements in
+    // order, and the chain from one publication to the next is one pivot
+    // search and two column updates in registers.
+    uint32_t* CX = s.CX;
+    // measurement i (pivot P, mask v = S_i less rows p and p-n) on one
+    // column's words held by this lane, with xp row p's bit on that column:
+    // x ^= v where xp, then row p-n := row p (keep/setd: the bit of row p-n
+    // or p in this lane's words) and row p := Z_a (no X)
+    struct Upd {
+      uint32_t v[WL], keep[WL], setd[WL];
+    };
+    auto make_upd = [&](const uint32_t (&S)[WL], int P, Upd& u) {
+      const int wp = P >> 5, wd = (P - 32 * Wh) >> 5;
+      const uint32_t bpm = 1u << (P & 31);
 #pragma unroll
-      for (int j = 0; j < CPR; ++j) {
-#pragma unroll
-        for (int k = 0; k < WL; ++k) {
-          const int w = lane + 32 * k;
-          const bool ok = s0 + j < D && w < W;
-          tx[j][k] = ok ? cm.slot_word(s, par, s0 + j, w, 0, W, KB) : 0u;
-          tz[j][k] = ok ? cm.slot_word(s, par, s0 + j, w, 1, W, KB) : 0u;
-        }
+      for (int k = 0; k < WL; ++k) {
+        const int w = lane + 32 * k;
+        const bool pk = w == wp || w == wd;
+        u.keep[k] = pk ? ~bpm : 0xffffffffu;
+        u.setd[k] = w == wd ? bpm : 0u;
+        u.v[k] = S[k] & u.keep[k];
       }
-      const int wlast = b.wlast[warp];
-      for (int i = 0; i <= wlast; ++i) {
-        const uint32_t code = b.code[i];
-        const int si = b.slot[i];
-        if (si >= s0 && si < s0 + CPR) {
-          const int jj = si - s0;
-          uint32_t* Si = s.SM + (size_t)i * W;
-          int P = -1;
+    };
+    auto upd_words = [&](uint32_t (&c)[WL], const Upd& u, bool xp) {
+      const uint32_t XP = xp ? 0xffffffffu : 0u;
 #pragma unroll
-          for (int k = 0; k < WL; ++k) {
-            const int w = lane + 32 * k;
-            const uint32_t v = res_pick_col<CPR, WL>(tx, jj, k);
-            if (w < W) Si[w] = v;
-            const uint32_t bal = __ballot_sync(0xffffffffu, w >= Wh && w < W && v != 0u);
-            if (P < 0 && bal) {
-              const int l = __ffs(bal) - 1;
-              const uint32_t word = __shfl_sync(0xffffffffu, v, l);
-              P = (32 * k + l) * 32 + __ffs(word) - 1;
-            }
-          }
-          if (lane == 0) {
-            b.P[i] = P;
-            if (P < 0 && dop(code) == OP_MZR) b.keff = i + 1;  // ends the batch
-          }
-          __syncwarp();
-          if (lane == 0) res_st_release(&b.npub, i + 1);
-        }
-        if (R > 1)
-          res_named_sync(1, 32 * b.cntw[i]);
-        else
-          __syncwarp();
-        const int P = b.P[i];
-        if (P < 0) {  // deterministic: X|Z unchanged; with reset the batch ends
-          if (dop(code) == OP_MZR) break;
-          continue;
-        }
-        if (i == wlast) break;  // none of this warp's columns is needed any more
-        const uint32_t live = b.wlive[warp][i];
-        const int wp = P >> 5, wd = (P - 32 * Wh) >> 5;
-        const uint32_t bpm = 1u << (P & 31);
-        // row p's X and Z bits on this warp's columns: gathered by the lane
-        // holding word wp, one bit per column, then broadcast
-        const int kp = wp >> 5, bp = P & 31;
-        uint32_t gx = 0u, gz = 0u;
+      for (int k = 0; k < WL; ++k) c[k] = ((c[k] ^ (u.v[k] & XP)) & u.keep[k]) | (u.setd[k] & XP);
+    };
+    auto load_col = [&](uint32_t (&c)[WL], int d) {
 #pragma unroll
-        for (int j = 0; j < CPR; ++j) {
-          gx |= ((res_pick(tx[j], kp) >> bp) & 1u) << j;
-          gz |= ((res_pick(tz[j], kp) >> bp) & 1u) << j;
-        }
-        gx = __shfl_sync(0xffffffffu, gx, wp & 31);
-        gz = __shfl_sync(0xffffffffu, gz, wp & 31);
-        const uint32_t* Si = s.SM + (size_t)i * W;
-        uint32_t Sw[WL];
+      for (int k = 0; k < WL; ++k) {
+        const int w = lane + 32 * k;
+        c[k] = (d >= 0 && w < W) ? CX[(size_t)d * Wp + w] : 0u;
+      }
+    };
+    auto store_col = [&](const uint32_t (&c)[WL], int d) {
+#pragma unroll
+      for (int k = 0; k < WL; ++k) {
+        const int w = lane + 32 * k;
+        if (w < W) CX[(size_t)d * Wp + w] = c[k];
+      }
+    };
+    constexpr int NQ = kBatchMax / kResHelpers;  // slots per helper: d = kResHelpers q + h
+    if (warp == 0) {
+      uint32_t ca[WL], cb[WL];
+      load_col(ca, b.slot[0]);
+      load_col(cb, K > 1 ? b.slot[1] : -1);
+      const int k_stab = Wh >> 5;  // first k whose words reach the stabilizer half
+      uint32_t code = b.code[0];
+      for (int i = 0; i < K; ++i) {
+        const int d2 = i + 2 < K ? b.slot[i + 2] : -1;
+        const uint32_t code_next = i + 1 < K ? b.code[i + 1] : 0u;
+        // has slot[i+2]'s helper applied measurement i-1 to it?  (looked at
+        // early; waited for below)
+        bool ready = d2 < 0 || res_ld_acquire(&b.hpri[d2 % kResHelpers]) >= i;
+        uint32_t* Si = s.SM + (size_t)i * W;
+        int P = -1;
 #pragma unroll
         for (int k = 0; k < WL; ++k) {
           const int w = lane + 32 * k;
-          Sw[k] = w < W ? Si[w] : 0u;
-          if (w == wp || w == wd) Sw[k] &= ~bpm;
+          if (w < W) Si[w] = ca[k];
+          if (k < k_stab || P >= 0) continue;  // warp-uniform
+          const uint32_t bal = __ballot_sync(0xffffffffu, w >= Wh && ca[k] != 0u);
+          if (bal) {
+            const int l = __ffs(bal) - 1;
+            const uint32_t word = __shfl_sync(0xffffffffu, ca[k], l);
+            P = (32 * k + l) * 32 + __ffs(word) - 1;
+          }
+        }
+        if (lane == 0) {
+          b.P[i] = P;
+          if (P < 0 && dop(code) == OP_MZR) b.keff = i + 1;  // ends the batch
+        }
+        __syncwarp();
+        if (lane == 0) res_st_release(&b.npub, i + 1);
+        if (P < 0 && dop(code) == OP_MZR) break;
+        if (i + 1 >= K) break;
+        if (!__all_sync(0xffffffffu, ready)) {  // wait (every lane polls; bounded)
+          for (int it = 0; it <= kPubSpinMax && !ready; ++it)
+            ready = res_ld_acquire(&b.hpri[d2 % kResHelpers]) >= i;
+          if (!__all_sync(0xffffffffu, ready)) {
+            if (lane == 0) atomicCAS(A.err, 0, DERR_TIMEOUT);
+            break;
+          }
+        }
+        uint32_t cc[WL];
+        load_col(cc, d2);
+        if (P >= 0) {  // random outcome: measurement i on slot[i+1] and slot[i+2]
+          Upd u;
+          make_upd(ca, P, u);
+          // row p's bits on slot[i+1] (bit 0) and slot[i+2] (bit 1), from the
+          // lane holding word P>>5
+          const int wp = P >> 5;
+          const uint32_t bb = (res_pick(cb, wp >> 5) >> (P & 31)) & 1u;
+          const uint32_t bc = (res_pick(cc, wp >> 5) >> (P & 31)) & 1u;
+          const uint32_t bits = __shfl_sync(0xffffffffu, bb | (bc << 1), wp & 31);
+          upd_words(cb, u, bits & 1u);
+          store_col(cb, b.slot[i + 1]);
+          if (d2 >= 0) {
+            upd_words(cc, u, (bits >> 1) & 1u);
+            store_col(cc, d2);
+          }
         }
 #pragma unroll
-        for (int j = 0; j < CPR; ++j) {
-          if (!((live >> j) & 1u)) continue;
-          const uint32_t XP = ((gx >> j) & 1u) ? 0xffffffffu : 0u;
-          const uint32_t ZP = ((gz >> j) & 1u) ? 0xffffffffu : 0u;
-          const uint32_t zpa = (s0 + j == si) ? bpm : 0u;
-#pragma unroll
-          for (int k = 0; k < WL; ++k) {
-            const int w = lane + 32 * k;
-            uint32_t x = tx[j][k] ^ (Sw[k] & XP), z = tz[j][k] ^ (Sw[k] & ZP);
-            if (w == wd) {  // row p-n := row p
-              x = (x & ~bpm) | (XP & bpm);
-              z = (z & ~bpm) | (ZP & bpm);
-            }
-            if (w == wp) {  // row p := Z_a
-              x &= ~bpm;
-              z = (z & ~bpm) | zpa;
-            }
-            tx[j][k] = x;
-            tz[j][k] = z;
+        for (int k = 0; k < WL; ++k) {
+          ca[k] = cb[k];
+          cb[k] = cc[k];
+        }
+        code = code_next;
+      }
+    } else if (warp <= kResHelpers && warp < R) {
+      const int h = warp - 1;
+      const uint32_t own = 0x11111111u << h;  // slots d = h mod kResHelpers
+      static_assert(kResHelpers == 4, "slot ownership mask");
+      if constexpr (WL <= 4) {
+        // this helper's slots in registers; `held`: slots whose register
+        // copy is current through the previous measurement
+        uint32_t xr[NQ][WL];
+        uint32_t held = 0u;
+        for (int j = 0; j < K; ++j) {
+          if (!res_wait_geq(&b.npub, j + 1, false)) {
+            if (lane == 0) atomicCAS(A.err, 0, DERR_TIMEOUT);
+            break;
           }
+          __syncwarp();
+          const int P = b.P[j];
+          const int d3 = b.s3[j];
+          const uint32_t mine = P >= 0 ? b.hm[j] & own : 0u;
+          if (mine != 0u) {
+            // slots last written by warp 0 or by the staging: reload
+            const uint32_t rl = mine & ~held;
+            if (rl != 0u) {
+#pragma unroll
+              for (int q = 0; q < NQ; ++q)
+                if ((rl >> (kResHelpers * q + h)) & 1u) load_col(xr[q], kResHelpers * q + h);
+            }
+            uint32_t Sr[WL];
+            load_col(Sr, -1);
+#pragma unroll
+            for (int k = 0; k < WL; ++k) {
+              const int w = lane + 32 * k;
+              if (w < W) Sr[k] = s.SM[(size_t)j * W + w];
+            }
+            Upd u;
+            make_upd(Sr, P, u);
+            // row p's bit on each slot, from the lane holding word P>>5
+            const int wp = P >> 5;
+            uint32_t gl = 0u;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) gl |= ((res_pick(xr[q], wp >> 5) >> (P & 31)) & 1u) << q;
+            const uint32_t g = __shfl_sync(0xffffffffu, gl, wp & 31);
+            if (d3 >= 0 && ((mine >> d3) & 1u)) {  // warp 0's next slot first
+              const int qp = d3 / kResHelpers;
+              uint32_t c[WL];
+#pragma unroll
+              for (int k = 0; k < WL; ++k) {
+                c[k] = 0u;
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) c[k] |= xr[q][k] & (0u - (uint32_t)(q == qp));
+              }
+              upd_words(c, u, (g >> qp) & 1u);
+              store_col(c, d3);
+              __syncwarp();
+            }
+            if (lane == 0) res_st_release(&b.hpri[h], j + 1);
+            // every slot of `mine` (the one above again, identically)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+              const uint32_t act = 0u - ((mine >> (kResHelpers * q + h)) & 1u);
+              uint32_t c[WL];
+#pragma unroll
+              for (int k = 0; k < WL; ++k) c[k] = xr[q][k];
+              upd_words(c, u, (g >> q) & 1u);
+#pragma unroll
+              for (int k = 0; k < WL; ++k) xr[q][k] = (c[k] & act) | (xr[q][k] & ~act);
+            }
+            held = mine;
+          } else if (P >= 0) {
+            held = 0u;
+            if (lane == 0) res_st_release(&b.hpri[h], j + 1);
+          } else {
+            // a deterministic measurement changes no X bit: the register
+            // copies stay current; warp 0 loads slot[j+3] next, so store it
+            // if this helper holds it
+            if (d3 >= 0 && ((held >> d3) & 1u)) {
+              const int qp = d3 / kResHelpers;
+#pragma unroll
+              for (int q = 0; q < NQ; ++q)
+                if (q == qp) store_col(xr[q], d3);
+              __syncwarp();
+            }
+            if (lane == 0) res_st_release(&b.hpri[h], j + 1);
+          }
+          if (__shfl_sync(0xffffffffu, lane == 0 ? b.keff : 0, 0) == j + 1) break;  // batch ends here
+        }
+      } else {
+        // this helper's slots in shared memory (CX), updated in place
+        for (int j = 0; j < K; ++j) {
+          if (!res_wait_geq(&b.npub, j + 1, false)) {
+            if (lane == 0) atomicCAS(A.err, 0, DERR_TIMEOUT);
+            break;
+          }
+          __syncwarp();
+          const int P = b.P[j];
+          const int d3 = b.s3[j];
+          uint32_t mine = P >= 0 ? b.hm[j] & own : 0u;
+          if (mine != 0u) {
+            const uint32_t bpm = 1u << (P & 31);
+            uint32_t Sr[WL];
+#pragma unroll
+            for (int k = 0; k < WL; ++k) {
+              const int w = lane + 32 * k;
+              Sr[k] = w < W ? s.SM[(size_t)j * W + w] : 0u;
+            }
+            Upd u;
+            make_upd(Sr, P, u);
+            // row p's bit on each of this helper's slots (lane d: slot d)
+            const uint32_t g = __ballot_sync(
+                0xffffffffu, ((mine >> lane) & 1u) && ((CX[(size_t)lane * Wp + (P >> 5)] & bpm) != 0u));
+            __syncwarp();
+            if (d3 >= 0 && ((mine >> d3) & 1u)) {  // warp 0's next slot first
+              uint32_t c[WL];
+              load_col(c, d3);
+              upd_words(c, u, (g >> d3) & 1u);
+              store_col(c, d3);
+              mine &= ~(1u << d3);
+              __syncwarp();
+            }
+            if (lane == 0) res_st_release(&b.hpri[h], j + 1);
+            for (uint32_t l = mine; l != 0u; l &= l - 1u) {
+              const int d = __ffs(l) - 1;
+              uint32_t c[WL];
+              load_col(c, d);
+              upd_words(c, u, (g >> d) & 1u);
+              store_col(c, d);
+            }
+            __syncwarp();
+          } else if (lane == 0) {
+            res_st_release(&b.hpri[h], j + 1);
+          }
+          if (__shfl_sync(0xffffffffu, lane == 0 ? b.keff : 0, 0) == j + 1) break;  // batch ends here
         }
       }
     }
@@ -499,7 +656,7 @@ __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
           for (int it = 0;; ++it) {
             seen = __shfl_sync(0xffffffffu, lane == 0 ? res_ld_acquire(&b.npub) : 0, 0);
             if (seen > i || it > kPubSpinMax) break;
-            __nanosleep(64);
+            if (it >= 256) __nanosleep(64);
           }
           if (seen <= i) {
             if (lane == 0) atomicCAS(A.err, 0, DERR_TIMEOUT);
@@ -692,7 +849,7 @@ __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
       const int mn = m + keff;
       const int Kn = (A.nm - mn < KB) ? A.nm - mn : KB;
       if (keff != K && lane < Kn) next_code = __ldg(A.mops + mn + lane);  // batch ended early
-      res_batch_slots(next_code, Kn > 0 ? Kn : 0, C, r, cpw, R, CPR, b);
+      res_batch_slots(next_code, Kn > 0 ? Kn : 0, C, r, cpw, R, b);
     }
     __syncthreads();
     cm.stage_columns(s, par ^ 1, b, W, Wp, KB);  // next batch's measured columns
