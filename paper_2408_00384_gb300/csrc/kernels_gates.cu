@@ -305,13 +305,13 @@ constexpr int kBlkDynMax = kMaxSmemBytes - 8192;
 int gates_block_max_n() { return (kBlkDynMax - kBlkRing * 8) / 8; }
 
 // Threads per CTA of the block kernel: the kernel is latency-bound per
-// super-layer, so a CTA just large enough for one block per thread (n/2
-// blocks in a full layer) keeps its barrier cheap: 128, 256 or 512 threads.
-// TAB_BLOCK_THREADS overrides (tuning sweeps).
+// super-layer, so a CTA just large enough for two blocks per thread (n/2
+// blocks in a full layer, interleaved in pairs) keeps its barrier cheap:
+// 128, 256 or 512 threads.  TAB_BLOCK_THREADS overrides (tuning sweeps).
 static int block_threads(int n) {
   const int forced = run_config().block_threads;
   if (forced == 128 || forced == 256 || forced == 512) return forced;
-  return n <= 256 ? 128 : n <= 512 ? 256 : 512;
+  return n <= 512 ? 128 : n <= 1024 ? 256 : 512;
 }
 
 template <int T, int SLOTS>
