@@ -333,8 +333,8 @@ typedef struct {
 /* Run m circuits, each for its number of shots, with Philox key `seed`.
  * Outcomes of (circuit c, shot s) go, in program order, to
  * out_bits[out_offsets[c] + s * n_meas(c) ...] where n_meas(c) counts the
- * MZ/MZR ops of circuit c; out_offsets may be NULL, meaning circuits are
- * packed back to back in order.  All shots of a circuit share the gates
+ * MZ, MZR, MX and MY ops of circuit c (tab_meas_counts); out_offsets may be
+ * NULL, meaning circuits are packed back to back in order.  All shots of a circuit share the gates
  * before its first measurement (gates do not depend on outcomes).  Uses the
  * current CUDA device and the legacy default stream; synchronizes. */
 int tab_batch_run(const tab_circuit *circuits, int32_t m, uint64_t seed,
@@ -362,6 +362,12 @@ int tab_batch_destroy(tab_batch_t b);
 /* totals: gate ops (once per circuit), measurement ops (over all shots),
  * outcome bytes needed */
 int tab_batch_info(tab_batch_t b, int64_t *n_gates, int64_t *n_meas, int64_t *out_bytes);
+/* n_meas(c) of every circuit: counts[c] for c < m (the caller's array). */
+int tab_batch_meas_counts(tab_batch_t b, int64_t *counts);
+/* n_meas(c) of m host gate lists (MZ, MZR, MX, MY words), counted on the
+ * host's worker threads without compiling anything: the sizes tab_batch_run
+ * writes.  TAB_EINVAL on a null array. */
+int tab_meas_counts(const tab_circuit *circuits, int32_t m, int64_t *counts);
 /* Enqueue one run of the whole batch on cuda_stream: outcomes (packed back to
  * back per circuit and shot) go to dev_out (device memory, >= out_bytes). */
 int tab_batch_exec(tab_batch_t b, uint64_t seed, uint8_t *dev_out, void *cuda_stream);
@@ -491,6 +497,27 @@ typedef struct {
 #define TAB_DEBUG_SKIP_BARRIER_ARRIVAL 1u
 int tab_get_config(tab_config *out);
 int tab_set_config(const tab_config *cfg);
+
+/* ---- debug build ---------------------------------------------------------
+ * The same library compiled with -DTAB_DEBUG (libtab_debug.so, built by
+ * `python -m paper_2408_00384_gb300.build --debug`; the Python binding loads
+ * it when the environment variable TAB_DEBUG is 1).  In it every qubit index
+ * a kernel reads from its inputs (gate and measurement codes, block records,
+ * the batch's work items) is checked against the tableau's size on the
+ * device; an index out of range latches a device error, reported as
+ * TAB_EDEVICE ("index out of range") by the next synchronizing call, and is
+ * replaced by 0, so no kernel touches memory outside its tableau.  Nothing
+ * traps.  Host-side validation is the same in both builds.
+ *
+ * tab_debug_build: 1 in the debug build, 0 otherwise.
+ * tab_debug_check: runs the device check once, on `index` against `limit`,
+ *   in a one-thread kernel on the current device; *checked gets the index
+ *   the kernel went on with.  Returns TAB_OK (index in range, or a release
+ *   build, where the check is compiled out and the index passes unchanged),
+ *   TAB_EDEVICE (debug build, index out of range: the error latched), or
+ *   TAB_ECUDA. */
+int tab_debug_build(void);
+int tab_debug_check(uint32_t index, uint32_t limit, uint32_t *checked);
 
 /* ---- roofline ceilings of the current device ---------------------------
  * The paper has no counterpart: these are the ceilings the kernels above are

@@ -2,7 +2,9 @@
 
 Each translation unit is compiled by nvcc in parallel, then linked as one
 shared library next to this file.  No torch headers are involved: the ABI is
-plain C, and the Python binding loads it with ctypes.
+plain C, and the Python binding loads it with ctypes.  `--debug` builds
+libtab_debug.so instead: the same sources with -DTAB_DEBUG, whose kernels
+check every qubit index they read (include/tab.h, "debug build").
 """
 import concurrent.futures as cf
 import os
@@ -13,6 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtab.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libtab_debug.so")
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
@@ -29,13 +33,13 @@ def headers():
         [os.path.join(os.path.dirname(HERE), "include", "tab.h")]
 
 
-def _compile(src, extra):
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src, extra, bdir, defs):
+    obj = os.path.join(bdir, os.path.basename(src) + ".o")
     hdr_t = max(os.path.getmtime(h) for h in headers())
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_t) \
             and not extra:
         return obj
-    cmd = [NVCC] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
+    cmd = [NVCC] + ARCH + FLAGS + defs + extra + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -44,24 +48,27 @@ def _compile(src, extra):
     return obj
 
 
-def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose_ptxas: bool = False, debug: bool = False) -> str:
+    bdir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    defs = ["-DTAB_DEBUG=1"] if debug else []
+    os.makedirs(bdir, exist_ok=True)
     srcs = sources()
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
     if force:
-        for f in os.listdir(BUILD):
-            os.remove(os.path.join(BUILD, f))
+        for f in os.listdir(bdir):
+            os.remove(os.path.join(bdir, f))
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
+        objs = list(ex.map(lambda s: _compile(s, extra, bdir, defs), srcs))
     newest = max(os.path.getmtime(o) for o in objs)
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
-        cmd = [NVCC] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", LIB + ".tmp"] + objs
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < newest:
+        cmd = [NVCC] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", lib + ".tmp"] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(LIB + ".tmp", LIB)
-    return LIB
+        os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose_ptxas="--ptxas" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose_ptxas="--ptxas" in sys.argv,
+                debug="--debug" in sys.argv))

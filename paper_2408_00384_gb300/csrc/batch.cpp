@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <memory>
 #include <new>
 #include <numeric>
 #include <string>
@@ -77,6 +78,18 @@ constexpr size_t kBatchSmemLimit = 227 * 1024 - 2048;
 // -- ends at the first measurement or noise op, so a circuit with noise
 // compiles its prefix and the rest apart.  *prefix: 1 if the program's first
 // segment is that prefix.
+// A word array left uninitialized on allocation (std::vector would zero it).
+struct RawWords {
+  std::unique_ptr<uint32_t[]> p;
+  size_t n;
+  explicit RawWords(size_t count) : p(new uint32_t[count]), n(count) {}
+  uint32_t* data() { return p.get(); }
+  uint32_t* begin() { return p.get(); }
+  size_t size() const { return n; }
+  bool empty() const { return n == 0; }
+  uint32_t& operator[](size_t i) { return p[i]; }
+};
+
 int compile_circuit(const tab_circuit& tc, std::vector<tab_gate>& low, HostProgram& hp,
                     uint8_t* prefix) {
   int64_t ext = 0;
@@ -171,7 +184,9 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
     o_lo[(size_t)c + 1] = o_lo[(size_t)c] + hp.layer_off.size();
     o_seg[(size_t)c + 1] = o_seg[(size_t)c] + hp.segs.size();
   }
-  std::vector<uint32_t> ops(o_ops[(size_t)m]), layer_off(o_lo[(size_t)m]);
+  // the concatenated tables are written in full by the parallel fill below,
+  // so they are allocated without the serial zeroing of a std::vector
+  RawWords ops(o_ops[(size_t)m]), layer_off(o_lo[(size_t)m]);
   std::vector<uint32_t> noise;
   std::vector<Seg> segs(o_seg[(size_t)m]);
   std::vector<BatchCirc> circs((size_t)m);
@@ -324,6 +339,7 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
   A.err = reinterpret_cast<int*>(p + 4);
   A.ready = reinterpret_cast<int*>(p + 16);
   A.nitems = B->nitems;
+  A.ncirc = (int)circs.size();
   int dev = 0;
   CUB(cudaGetDevice(&dev));
   CUB(cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, dev));
@@ -499,55 +515,124 @@ static int batch_error(tab_batch_t B, void* cuda_stream) {
 
 extern "C" {
 
+int tab_meas_counts(const tab_circuit* circuits, int32_t m, int64_t* counts) {
+  if (m < 0 || (m > 0 && (!circuits || !counts))) {
+    set_error("null argument");
+    return TAB_EINVAL;
+  }
+  std::atomic<int> next{0};
+  pool_run(pool_threads(), [&](int) {
+    for (;;) {
+      const int c = next.fetch_add(1);
+      if (c >= m) break;
+      const tab_gate* g = circuits[c].gates;
+      int64_t nm = 0;
+      for (int64_t i = 0; g && i < circuits[c].n_gates; ++i) {
+        const uint32_t op = (uint32_t)(g[i] >> 56);
+        nm += (op == TAB_MZ) | (op == TAB_MZR) | (op == TAB_MX) | (op == TAB_MY);
+      }
+      counts[c] = nm;
+    }
+  });
+  return TAB_OK;
+}
+
+int tab_batch_meas_counts(tab_batch_t B, int64_t* counts) {
+  if (!B || !counts) {
+    set_error("null argument");
+    return TAB_EINVAL;
+  }
+  for (size_t c = 0; c < B->ck.size(); ++c) counts[c] = B->ck[c];
+  return TAB_OK;
+}
+
 int tab_batch_run(const tab_circuit* circuits, int32_t m, uint64_t seed, uint8_t* out_bits,
                   const int64_t* out_offsets) {
-  tab_batch_s* B = new (std::nothrow) tab_batch_s();
-  if (!B) {
-    set_error("host allocation failed");
-    return TAB_ENOMEM;
+  tab::TraceRange trace_("tab_batch_run");
+  if (m < 0 || (m > 0 && !circuits)) {
+    set_error("bad circuit array");
+    return TAB_EINVAL;
   }
-  int rc = build_batch(circuits, m, out_offsets, B);
-  if (rc == TAB_OK && prepare_batch_kernel(B->threads) != cudaSuccess) {
-    set_error("kernel attribute setup failed");
-    rc = TAB_ECUDA;
+  // output spans: the caller's offsets, or circuits packed in order
+  std::vector<int64_t> counts((size_t)m + 1, 0), offs((size_t)m + 1, 0);
+  int rc = tab_meas_counts(circuits, m, counts.data());
+  if (rc != TAB_OK) return rc;
+  int64_t out_end = 0, packed = 0, gates = 0;
+  for (int32_t c = 0; c < m; ++c) {
+    const int64_t span = counts[(size_t)c] * std::max(circuits[c].shots, 0);
+    offs[(size_t)c] = out_offsets ? out_offsets[c] : packed;
+    packed += span;
+    out_end = std::max(out_end, offs[(size_t)c] + span);
+    gates += std::max<int64_t>(circuits[c].n_gates, 0);
   }
-  uint8_t* dout = nullptr;
-  if (rc == TAB_OK && B->out_bytes > 0) {
-    if (!out_bits) {
-      set_error("null output buffer");
-      rc = TAB_EINVAL;
-    } else if (cudaMalloc((void**)&dout, (size_t)B->out_bytes) != cudaSuccess) {
-      cudaGetLastError();
-      set_error("cudaMalloc of %lld output bytes failed", (long long)B->out_bytes);
-      rc = TAB_ENOMEM;
+  if (out_end > 0 && !out_bits) {
+    set_error("null output buffer");
+    return TAB_EINVAL;
+  }
+  // Contiguous chunks of about equal gate count, compiled and launched in
+  // order on one stream: the device runs chunk k while the host pool
+  // compiles chunk k+1.  Small batches are one chunk.
+  const int K = (m >= 256 && gates >= ((int64_t)1 << 24)) ? 4 : 1;
+  std::vector<int32_t> cut(1, 0);
+  int64_t before = 0;
+  for (int32_t c = 0, k = 1; c < m && k < K; ++c) {
+    before += std::max<int64_t>(circuits[c].n_gates, 0);
+    if (before * K >= gates * k) {
+      cut.push_back(c + 1);
+      ++k;
     }
   }
-  if (rc == TAB_OK) rc = tab_batch_exec(B, seed, dout, nullptr);
-  if (rc == TAB_OK) rc = batch_error(B, nullptr);
-  if (rc == TAB_OK && B->out_bytes > 0) {
+  if (cut.back() != m) cut.push_back(m);
+  cudaStream_t st = nullptr;
+  CUB(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  uint8_t* dout = nullptr;
+  if (out_end > 0 && cudaMalloc((void**)&dout, (size_t)out_end) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc of %lld output bytes failed", (long long)out_end);
+    rc = TAB_ENOMEM;
+  }
+  std::vector<tab_batch_s*> parts;
+  for (size_t k = 0; rc == TAB_OK && k + 1 < cut.size(); ++k) {
+    const int32_t c0 = cut[k], mk = cut[k + 1] - cut[k];
+    tab_batch_s* B = new (std::nothrow) tab_batch_s();
+    if (!B) {
+      set_error("host allocation failed");
+      rc = TAB_ENOMEM;
+      break;
+    }
+    parts.push_back(B);
+    rc = build_batch(circuits + c0, mk, offs.data() + c0, B);
+    if (rc == TAB_OK && prepare_batch_kernel(B->threads) != cudaSuccess) {
+      set_error("kernel attribute setup failed");
+      rc = TAB_ECUDA;
+    }
+    if (rc == TAB_OK) rc = tab_batch_exec(B, seed, dout, st);
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess && rc == TAB_OK) {
+    set_error("batch run failed: %s", cudaGetErrorString(cudaGetLastError()));
+    rc = TAB_ECUDA;
+  }
+  for (tab_batch_s* B : parts)
+    if (rc == TAB_OK) rc = batch_error(B, st);
+  if (rc == TAB_OK && out_end > 0) {
     if (out_offsets) {  // copy only the spans written, leave the rest untouched
       for (int32_t c = 0; c < m; ++c) {
-        int64_t nm = 0;
-        for (int64_t i = 0; i < circuits[c].n_gates; ++i) {
-          const uint32_t op = (uint32_t)(circuits[c].gates[i] >> 56);
-          nm += (op == TAB_MZ || op == TAB_MZR);
-        }
-        const int64_t span = nm * circuits[c].shots;
-        if (span && cudaMemcpy(out_bits + out_offsets[c], dout + out_offsets[c], (size_t)span,
+        const int64_t span = counts[(size_t)c] * circuits[c].shots;
+        if (span && cudaMemcpy(out_bits + offs[(size_t)c], dout + offs[(size_t)c], (size_t)span,
                                cudaMemcpyDeviceToHost) != cudaSuccess) {
           set_error("outcome copy failed");
           rc = TAB_ECUDA;
           break;
         }
       }
-    } else if (cudaMemcpy(out_bits, dout, (size_t)B->out_bytes, cudaMemcpyDeviceToHost) !=
-               cudaSuccess) {
+    } else if (cudaMemcpy(out_bits, dout, (size_t)out_end, cudaMemcpyDeviceToHost) != cudaSuccess) {
       set_error("outcome copy failed");
       rc = TAB_ECUDA;
     }
   }
   if (dout) cudaFree(dout);
-  tab_batch_destroy(B);
+  for (tab_batch_s* B : parts) tab_batch_destroy(B);
+  cudaStreamDestroy(st);
   return rc;
 }
 

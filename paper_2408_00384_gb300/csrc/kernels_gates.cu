@@ -151,13 +151,13 @@ __device__ __forceinline__ void c1_apply_masks(const uint4* tab, uint32_t m, uin
 template <int NB>
 __device__ __forceinline__ void apply_blocks(const uint2 (&rec)[NB], const bool (&on)[NB],
                                              const uint4* c1m, uint32_t* sx, uint32_t* sz,
-                                             uint32_t& r) {
+                                             uint32_t& r, int n, int* err) {
   uint32_t qa[NB], qb[NB], m[NB], x0[NB], z0[NB], x1[NB], z1[NB];
   bool two[NB];
 #pragma unroll
   for (int j = 0; j < NB; ++j) {
-    qa[j] = rec[j].x & 0x3FFFu;
-    qb[j] = (rec[j].x >> 14) & 0x3FFFu;
+    qa[j] = dbg_index(rec[j].x & 0x3FFFu, (uint32_t)n, err);
+    qb[j] = dbg_index((rec[j].x >> 14) & 0x3FFFu, (uint32_t)n, err);
     two[j] = on[j] && ((rec[j].x >> 28) & 1u);
     m[j] = rec[j].y;
     x0[j] = on[j] ? sx[qa[j]] : 0u;
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(T) k_gates_block(uint32_t* __restrict__ X, uin
       const uint2 recs[2] = {ring[(g - base) % (SLOTS * kBlkChunk)],
                              ring[(g2 < le ? g2 - base : g - base) % (SLOTS * kBlkChunk)]};
       const bool on[2] = {true, g2 < le};
-      apply_blocks<2>(recs, on, c1m, sx, sz, racc);
+      apply_blocks<2>(recs, on, c1m, sx, sz, racc, n, err);
     }
     prev_lb = lb;
     lb = le;

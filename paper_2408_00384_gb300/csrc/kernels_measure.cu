@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kMeasThreads) k_measure(MArgs A) {
       prev_det = 0;
     }
 
-    const int a = (int)dq1(code);
+    const int a = (int)dbg_index(dq1(code), (uint32_t)A.n, A.err);
     const int reset = dop(code) == OP_MZR;
     // outcome bits of measurements m .. m+31, drawn by warp 0 once every 32
     // measurements (lane i: measurement m+i); read after the barrier below

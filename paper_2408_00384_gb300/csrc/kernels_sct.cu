@@ -66,10 +66,12 @@ size_t sct_sampler_bytes(int n, int K, int shots) {
 struct Sct {
   int n, Whc, Wc, Wp, GG;
   uint32_t *X, *Z, *R, *sS, *supp, *redlo, *redhi;  // supp: [3][n] (X, Z, Y columns)
+  int* err;  // the launch's error word (debug-build index checks)
 };
 
-__device__ __forceinline__ void sct_setup(Sct& s, uint32_t* base, int n) {
+__device__ __forceinline__ void sct_setup(Sct& s, uint32_t* base, int n, int* err) {
   s.n = n;
+  s.err = err;
   s.Whc = sct_whc(n);
   s.Wc = 2 * s.Whc;
   s.Wp = s.Wc | 1;
@@ -130,7 +132,7 @@ __device__ void sct_gates(const Sct& s, const uint32_t* __restrict__ ops,
     for (int L = 0; L < nl; ++L) {
       const uint32_t le = __ldg(layer_off + L + 1);
       for (uint32_t g = lb + warp; g < le; g += nw) {
-        const uint32_t code = __ldg(ops + g);
+        const uint32_t code = dbg_code(__ldg(ops + g), (uint32_t)s.n, s.err);
         apply_gate(code, s.X, s.Z, s.Wp, lane, r0, npauli);
         if (two) apply_gate(code, s.X, s.Z, s.Wp, lane + 32, r1, npauli);
       }
@@ -146,7 +148,7 @@ __device__ void sct_gates(const Sct& s, const uint32_t* __restrict__ ops,
       const uint32_t le = __ldg(layer_off + L + 1);
       if (active)
         for (uint32_t g = lb + warp * sub + gsub; g < le; g += nw * sub)
-          apply_gate(__ldg(ops + g), s.X, s.Z, s.Wp, w, r0, npauli);
+          apply_gate(dbg_code(__ldg(ops + g), (uint32_t)s.n, s.err), s.X, s.Z, s.Wp, w, r0, npauli);
       lb = le;
       __syncthreads();
     }
@@ -161,7 +163,7 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err)
   __shared__ int s_pw, s_nx, s_nz, s_kc;
   __shared__ uint32_t s_acc;
   const int tid = threadIdx.x, T = blockDim.x;
-  const int a = (int)dq1(code);
+  const int a = (int)dbg_index(dq1(code), (uint32_t)s.n, err);
   const bool reset = dop(code) == OP_MZR;
   const int n = s.n, Whc = s.Whc, Wc = s.Wc, Wp = s.Wp;
   const uint32_t* xa = s.X + (size_t)a * Wp;
@@ -558,7 +560,7 @@ __device__ void sct_run_segments(const Sct& s, const Seg* __restrict__ segs, int
 __global__ void __launch_bounds__(kSctThreads) k_sct_program(SctProgArgs A) {
   extern __shared__ uint32_t smem[];
   Sct s;
-  sct_setup(s, smem, A.n);
+  sct_setup(s, smem, A.n, A.err);
   sct_load_global(s, A.X, A.Z, A.R, A.Wh);
   __syncthreads();
   sct_run_segments(s, A.segs, 0, A.nsegs, A.ops, A.layer_off, A.seed, A.cid, A.shot, A.k0,
@@ -601,10 +603,11 @@ __global__ void __launch_bounds__(T) k_batch(BatchArgs A) {
     __syncthreads();
     if (stop || it >= (unsigned int)A.nitems) break;
     const uint64_t item = A.items[it];
-    const uint32_t ci = (uint32_t)item, shot = (uint32_t)(item >> 32);
+    const uint32_t ci = dbg_index((uint32_t)item, (uint32_t)A.ncirc, A.err),
+                   shot = (uint32_t)(item >> 32);
     const BatchCirc C = A.circs[ci];
     Sct s;
-    sct_setup(s, smem, C.n);
+    sct_setup(s, smem, C.n, A.err);
     uint32_t* img = A.img + C.img_off;
     if (shot == 0xFFFFFFFFu) {
       sct_identity(s);

@@ -240,8 +240,9 @@ struct ResBatch {
 // apply warps (warp R + local column / cpw) this CTA owns.  Warp-wide (one
 // warp).
 __device__ __forceinline__ void res_batch_slots(uint32_t code, int K, int C, int r, int cpw,
-                                                int R, ResBatch& b) {
+                                                int R, ResBatch& b, int n, int* err) {
   const int lane = threadIdx.x & 31;
+  if (lane < K) code = dbg_code(code, (uint32_t)n, err);
   const bool v = lane < K;
   const int a = v ? (int)dq1(code) : -1 - lane;
   const uint32_t grp = __match_any_sync(0xffffffffu, a);
@@ -322,7 +323,7 @@ __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
   if (warp == 0) {
     const int K0 = A.nm < KB ? A.nm : KB;
     const uint32_t c = lane < K0 ? __ldg(A.mops + lane) : 0u;
-    res_batch_slots(c, K0, C, r, cpw, R, b);
+    res_batch_slots(c, K0, C, r, cpw, R, b, n, A.err);
     if (lane == 0) b.anydet = 0;
   }
   if (!cm.start()) return;
@@ -849,7 +850,7 @@ __device__ void measure_resident(const ResArgs& A, Comm& cm, uint32_t* sm) {
       const int mn = m + keff;
       const int Kn = (A.nm - mn < KB) ? A.nm - mn : KB;
       if (keff != K && lane < Kn) next_code = __ldg(A.mops + mn + lane);  // batch ended early
-      res_batch_slots(next_code, Kn > 0 ? Kn : 0, C, r, cpw, R, b);
+      res_batch_slots(next_code, Kn > 0 ? Kn : 0, C, r, cpw, R, b, n, A.err);
     }
     __syncthreads();
     cm.stage_columns(s, par ^ 1, b, W, Wp, KB);  // next batch's measured columns

@@ -45,6 +45,7 @@ struct BatchArgs {
   const uint64_t* items;  // circuit | shot << 32 (shot = ~0: prefix item)
   const uint32_t* noise;  // noise table: kind << 28 | probability (kProgNoise)
   int nitems;
+  int ncirc;              // circuits (entries of circs)
   uint32_t* img;
   int* ready;
   unsigned int* queue;

@@ -159,6 +159,11 @@ int poll_device_error(tab_t h) {
     h->sticky = TAB_ETIMEOUT;
     return TAB_ETIMEOUT;
   }
+  if (err == DERR_BOUNDS) {
+    set_error("device reported an index out of range (debug build check)");
+    h->sticky = TAB_EDEVICE;
+    return TAB_EDEVICE;
+  }
   if (err != 0) {
     set_error("device reported inconsistency code %d", err);
     h->sticky = TAB_EDEVICE;

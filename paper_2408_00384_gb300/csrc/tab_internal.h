@@ -43,6 +43,36 @@ inline int half_words(int n) { return (((n + 31) / 32) + 3) & ~3; }
 // ---- device error word values ---------------------------------------------
 enum : int { DERR_NONE = 0, DERR_TIMEOUT = 1, DERR_PHASE = 2, DERR_BOUNDS = 3 };
 
+// ---- debug builds (compiled with -DTAB_DEBUG: libtab_debug.so) ---------------
+// Every qubit index a kernel takes from its inputs goes through dbg_index.  In
+// a debug build an index at or past `lim` latches DERR_BOUNDS in the error
+// word and is replaced by 0, so the kernel finishes without touching memory
+// outside its tableau and the next synchronizing call reports the error; in a
+// release build the index passes unchanged and the check compiles away.
+#ifdef TAB_DEBUG
+constexpr bool kDebugBuild = true;
+#else
+constexpr bool kDebugBuild = false;
+#endif
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t dbg_index(uint32_t i, uint32_t lim, int* err) {
+  if (kDebugBuild && i >= lim) {
+    if (err) atomicCAS(err, 0, DERR_BOUNDS);
+    return 0u;
+  }
+  return i;
+}
+// A gate or measurement code with its qubit fields checked against n
+// (dbg_index; the second field only for two-qubit gates).
+__device__ __forceinline__ uint32_t dbg_code(uint32_t c, uint32_t n, int* err) {
+  if (!kDebugBuild) return c;
+  const uint32_t op = dop(c);
+  const uint32_t q1 = dbg_index(dq1(c), n, err);
+  const uint32_t q2 = (op == OP_CNOT || op == OP_CZ || op == OP_SWAP) ? dbg_index(dq2(c), n, err) : dq2(c);
+  return (c & 0xF0000000u) | (q1 << 14) | q2;
+}
+#endif
+
 // ---- compiled program ----------------------------------------------------------
 // ops[] holds gate segments (gates grouped by layer; a layer's gates act on
 // pairwise-disjoint qubits) and measurement segments (MZ/MZR codes in program

@@ -14,7 +14,9 @@ from typing import Iterable, Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libtab.so")
+# TAB_DEBUG=1 selects the debug build (device-side index checks; include/tab.h)
+DEBUG = os.environ.get("TAB_DEBUG", "") == "1"
+LIB_PATH = os.path.join(_HERE, "libtab_debug.so" if DEBUG else "libtab.so")
 
 TAB_OK, TAB_EINVAL, TAB_ERANGE, TAB_ENOMEM = 0, -1, -2, -3
 TAB_ECUDA, TAB_EDEVICE, TAB_ETIMEOUT, TAB_ESTATE = -4, -5, -6, -7
@@ -27,8 +29,10 @@ BATCH_MAX_QUBITS = 640
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
-        f"libtab.so not found at {LIB_PATH}: build it with "
-        "`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback exists)")
+        f"{os.path.basename(LIB_PATH)} not found at {LIB_PATH}: build it with "
+        + ("`python -m paper_2408_00384_gb300.build --debug`" if DEBUG else
+           "`python -c 'import __graft_entry__ as g; g.build()'`")
+        + " (no CPU fallback exists)")
 
 _L = ctypes.CDLL(LIB_PATH)
 
@@ -172,6 +176,24 @@ def measure_peaks() -> dict:
     p = TabPeaks()
     _check(_L.tab_measure_peaks(ctypes.byref(p)))
     return {k: getattr(p, k) for k, _ in TabPeaks._fields_}
+
+
+_sig("tab_debug_build", ctypes.c_int, [])
+_sig("tab_debug_check", ctypes.c_int, [_u32, _u32, _P(_u32)])
+
+
+def debug_build() -> bool:
+    """True in the debug build (libtab_debug.so, device-side index checks)."""
+    return bool(_L.tab_debug_build())
+
+
+def debug_check(index: int, limit: int) -> int:
+    """Run the debug build's device index check once (tab_debug_check):
+    returns the index the kernel went on with; raises TabError(TAB_EDEVICE)
+    when the debug build finds it out of range."""
+    out = _u32(0)
+    _check(_L.tab_debug_check(index, limit, ctypes.byref(out)))
+    return out.value
 
 
 REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
@@ -460,6 +482,16 @@ def n_meas_of(gates) -> int:
     return int(np.isin(op, (10, 11, 13, 14)).sum())
 
 
+_sig("tab_meas_counts", ctypes.c_int, [_vp, _i32, _P(_i64)])
+_sig("tab_batch_meas_counts", ctypes.c_int, [_vp, _P(_i64)])
+
+
+def _meas_counts(arr, m) -> list:
+    counts = (_i64 * max(m, 1))()
+    _check(_L.tab_meas_counts(ctypes.cast(arr, _vp), m, counts))
+    return list(counts[:m])
+
+
 def batch_run(circuits, seed: int = 1, out=None) -> list:
     """Run (n, gates, shots, circuit_id) circuits in one batched call.
 
@@ -467,7 +499,8 @@ def batch_run(circuits, seed: int = 1, out=None) -> list:
     `out`, a host uint8 array of at least the total outcome count, if given,
     e.g. in pinned memory)."""
     arr, keep = _circuit_array(circuits)
-    sizes = [shots * n_meas_of(g) for (_, g, shots, _) in circuits]
+    nms = _meas_counts(arr, len(circuits))
+    sizes = [shots * nm for (_, _, shots, _), nm in zip(circuits, nms)]
     total = int(sum(sizes))
     if out is None:
         out = np.zeros(max(total, 1), np.uint8)
@@ -498,7 +531,9 @@ class Batch:
         _check(_L.tab_batch_create_ex(ctypes.cast(arr, _vp), len(circuits), flags,
                                       ctypes.byref(h)))
         self._h = h
-        self.sizes = [shots * n_meas_of(g) for (_, g, shots, _) in circuits]
+        counts = (_i64 * max(len(circuits), 1))()
+        _check(_L.tab_batch_meas_counts(h, counts))
+        self.sizes = [shots * counts[i] for i, (_, _, shots, _) in enumerate(circuits)]
 
     def info(self):
         a, b, c = _i64(), _i64(), _i64()

@@ -125,6 +125,34 @@ def test_config4_batch_vs_oracle(cfg4, sampler):
                     + str(_batch_mismatch(circs, ref, out, offsets)))
 
 
+def test_config4_batch_run_host_buffers_vs_oracle(cfg4):
+    """The same family through tab_batch_run (host gate lists in, host
+    outcome buffer out; large enough to run as several chunks whose host
+    compile overlaps the previous chunk's launch): every circuit against the
+    oracle's digest; then a caller-given layout (circuits in reverse order,
+    a gap after each) gets the same bytes in each circuit's span."""
+    circs, ref = cfg4
+    tc = [(c.n, c.gates, c.shots, c.circuit_id) for c in circs]
+    res = tab.batch_run(tc, seed=ref["seed"])
+    bad = [i for i, (e, r) in enumerate(zip(ref["circuits"], res))
+           if D.outcomes_sha(np.ascontiguousarray(r).reshape(-1))[:32] != e["outcomes_sha256"]]
+    assert not bad, f"cfg4 via tab_batch_run: {len(bad)} circuits differ (first {bad[:5]})"
+    sizes = [c.shots * c.n_meas for c in circs]
+    offs, pos = [0] * len(circs), 0
+    for i in reversed(range(len(circs))):
+        offs[i] = pos
+        pos += sizes[i] + 3
+    out = np.full(pos, 7, np.uint8)
+    arr, keep = tab._circuit_array(tc)
+    offs_arr = (tab._i64 * len(offs))(*offs)
+    tab._check(tab._L.tab_batch_run(tab.ctypes.cast(arr, tab._vp), len(tc), ref["seed"],
+                                    out.ctypes.data, tab.ctypes.cast(offs_arr, tab._vp)))
+    for i in (0, 1, len(circs) // 2, len(circs) - 1):
+        got = out[offs[i]:offs[i] + sizes[i]]
+        assert np.array_equal(got, np.ascontiguousarray(res[i]).reshape(-1)), i
+        assert (out[offs[i] + sizes[i]:offs[i] + sizes[i] + 3] == 7).all(), i
+
+
 # ------------------------------------------------------------- config 5 ---
 
 @pytest.fixture(scope="module")
