@@ -358,7 +358,7 @@ def run_reference(args, ws, rank):
         # sample's own duration
         shapes = C.config4_shapes()
         cores = all_cores()
-        budget = min(12.0, max(2.0, 150.0 / (args.steps + args.warmup)))
+        budget = min(12.0, max(2.0, 90.0 / (args.steps + args.warmup)))
         get = batch_circuit_getter(0)
         for w in range(args.warmup):
             oracle_batch_rate(shapes, get, min(budget, 2.0), cores, seed=100 + w)
