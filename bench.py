@@ -603,7 +603,7 @@ def run_batched(args, ws, rank, local):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     # autotune the persistent launch's CTA shape on this batch (untimed)
     tuned_threads, tuned_ms = b.tune(C.PHILOX_SEED, out.data_ptr(), stream)
-    launch = b.config()
+    launch = {"size_classes": [{k: v for k, v in c.items()} for c in b.classes()]}
     for _ in range(args.warmup):
         b.exec(C.PHILOX_SEED, out.data_ptr(), stream)
     torch.cuda.synchronize()
@@ -723,8 +723,10 @@ def run_batched(args, ws, rank, local):
                    "l2": "flushed before every timed step (256 MB device write); the compiled "
                          "batch is larger than L2",
                    "launch": launch, "generate_s": gen_s, "compile_s": compile_s,
-                   "autotune": {"threads": tuned_threads, "best_run_ms": tuned_ms,
-                                "tried": "128/256/512/1024 threads per CTA, one full run each"}},
+                   "autotune": {"threads_first_class": tuned_threads,
+                                "best_runs_ms_sum": tuned_ms,
+                                "tried": "128/256/512/1024 threads per CTA, each size class "
+                                         "run alone once per shape"}},
         "gpu_launches": b.launches * args.steps, "clocks": clk, "roofline": roof,
         "e2e": e2e,
         "plain_path": {"gates_per_s": ws * plain_gps, "meas_per_s": ws * plain_mps,

@@ -375,20 +375,37 @@ int tab_batch_exec(tab_batch_t b, uint64_t seed, uint8_t *dev_out, void *cuda_st
  * offsets, work items) the batch copied host -> device when it was created;
  * tab_batch_run copies the same amount per call. */
 int tab_batch_h2d_bytes(tab_batch_t b, int64_t *bytes);
-/* Number of kernels one tab_batch_exec launches. */
+/* Size classes.  The batch's circuits are grouped by qubit count into size
+ * classes -- runs of 32-qubit groups (one tableau word per 32 qubits) whose
+ * tableaus take the same number of CTAs per SM -- and each class runs as a
+ * persistent launch of its own, shaped for it (threads per CTA, shared
+ * memory for its largest tableau, as many CTAs as fit); tab_batch_exec
+ * launches the classes one after another (one CUDA graph), the largest
+ * qubit counts first.  tab_batch_classes: their number; tab_batch_class:
+ * class k's range and shape. */
+typedef struct {
+  int32_t lo_n, max_n;   /* qubit counts of the class: lo_n .. max_n */
+  int32_t threads, ctas; /* launch shape */
+  int64_t smem_bytes;    /* dynamic shared memory per CTA */
+  int64_t items;         /* work items (prefix and shot items) */
+} tab_batch_class_info;
+int tab_batch_classes(tab_batch_t b, int32_t *count);
+int tab_batch_class(tab_batch_t b, int32_t k, tab_batch_class_info *out);
+/* Number of kernels one tab_batch_exec launches (one per non-empty class). */
 int tab_batch_launches(tab_batch_t b, int64_t *count);
-/* Autotuner: runs the whole batch once per CTA shape the persistent kernel is
- * built for (128, 256, 512 or 1024 threads per CTA; shared memory sized to
- * the largest tableau; as many CTAs as fit on the GPU), timed with events on
- * cuda_stream, and keeps the fastest for later tab_batch_exec replays.  Each
- * run writes the outcomes an exec with this seed writes (dev_out as for
- * tab_batch_exec).  Synchronises cuda_stream.  *threads_out / *best_ms_out
- * (either may be null) get the choice and its time.  TAB_EDEVICE /
- * TAB_ETIMEOUT if a run reports a device error. */
+/* Autotuner: runs each size class's launch alone once per CTA size the
+ * persistent kernel is built for (128, 256, 512 or 1024 threads per CTA;
+ * shared memory sized to the class's largest tableau; as many CTAs as fit on
+ * the GPU), timed with events on cuda_stream, and keeps the fastest per
+ * class for later tab_batch_exec replays.  Each run writes the outcomes an
+ * exec with this seed writes for that class (dev_out as for tab_batch_exec).
+ * Synchronises cuda_stream.  *threads_out gets the first (largest-qubit)
+ * class's choice and *best_ms_out the sum of the classes' best times (either
+ * may be null).  TAB_EDEVICE / TAB_ETIMEOUT if a run reports a device
+ * error. */
 int tab_batch_tune(tab_batch_t b, uint64_t seed, uint8_t *dev_out, void *cuda_stream,
                    int32_t *threads_out, float *best_ms_out);
-/* Current CTA shape of the batch's launch (threads per CTA, CTAs, dynamic
- * shared memory bytes); any pointer may be null. */
+/* Launch shape of the first (largest-qubit) size class. */
 int tab_batch_config(tab_batch_t b, int32_t *threads, int32_t *ctas, int64_t *smem_bytes);
 
 /* ---- serving: continuous batching of circuit requests -------------------- */

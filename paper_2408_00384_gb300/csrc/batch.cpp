@@ -48,25 +48,39 @@ struct tab_batch_s {
   std::vector<int32_t> cn, ck, cshots;      // per circuit: n, terminal K, shots
   std::vector<int32_t> cnoise;              // per circuit: noise ops (drawn per shot)
   std::vector<uint8_t> csampled;
-  size_t smem = 0;
-  int ctas = 1;
-  int threads = kBatchDefaultThreads;  // CTA shape (set by tab_batch_tune)
   int sms = 1;
   int nitems = 0;
+  // Size classes: circuits whose tableaus take the same number of CTAs per
+  // SM run in a persistent launch of their own, shaped for them (threads,
+  // shared memory, CTAs); the launches follow one another in one graph.
+  struct Class {
+    int lo_n = 0, max_n = 0;         // qubit range of the class
+    int item_begin = 0, item_end = 0;
+    int threads = kBatchDefaultThreads;  // CTA shape (tab_batch_tune sets it per class)
+    size_t smem = 0;
+    int ctas = 1;
+    BatchArgs args{};
+    cudaGraphNode_t knode = nullptr;
+  };
+  std::vector<Class> cls;
+  std::vector<int32_t> ccls;  // per circuit: its class
   // device
   void* dmem = nullptr;
-  BatchArgs args{};
-  void* ctl = nullptr;  // queue counter, ready flags, error word (zeroed per run)
+  BatchArgs args{};     // fields shared by the classes' launches
+  void* ctl = nullptr;  // error word, queue counters, ready flags (zeroed per run)
   size_t ctl_bytes = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
-  cudaGraphNode_t knode = nullptr;
 };
 
 namespace {
 
 size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
-int configure(tab_batch_s* B, int threads);
+int configure(tab_batch_s* B, int k, int threads);
+
+// CTA size a class starts with (before tab_batch_tune): about one thread per
+// two tableau words of a 32-qubit group, 128 .. 512.
+int default_threads(int max_n) { return max_n <= 128 ? 128 : max_n <= 256 ? 256 : 512; }
 
 // Shared memory a batch kernel CTA of `threads` may take (the device's opt-in
 // maximum less a margin for the kernel's static shared memory).
@@ -277,21 +291,54 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
   }
   B->m = m;
   B->out_bytes = out_max;
-  // ---- work items, longest first within each class
+  // ---- size classes: 32-qubit groups (one tableau word per 32 qubits, so
+  // one shared-memory footprint per group) merged while they take the same
+  // CTAs per SM at their default CTA size; the largest first
+  {
+    std::vector<int> occ_of(TAB_BATCH_MAX_QUBITS / 32 + 2, 0);
+    for (int g = 1; g <= TAB_BATCH_MAX_QUBITS / 32; ++g) {
+      const int nn = 32 * g, T = default_threads(nn);
+      occ_of[(size_t)g] = batch_ctas_per_sm(T, sct_smem_bytes(nn, T));
+    }
+    int top = 0;
+    for (int32_t c = 0; c < m; ++c) top = std::max(top, (circuits[c].n + 31) / 32);
+    B->ccls.assign((size_t)m, 0);
+    std::vector<int> cls_of_group((size_t)top + 1, -1);
+    for (int g = top; g >= 1; --g) {
+      if (B->cls.empty() || occ_of[(size_t)g] != occ_of[(size_t)(B->cls.back().lo_n + 31) / 32] ||
+          default_threads(32 * g) != default_threads(B->cls.back().max_n)) {
+        tab_batch_s::Class k;
+        k.max_n = 32 * g;
+        B->cls.push_back(k);
+      }
+      B->cls.back().lo_n = 32 * (g - 1) + 1;
+      cls_of_group[(size_t)g] = (int)B->cls.size() - 1;
+    }
+    for (int32_t c = 0; c < m; ++c) B->ccls[(size_t)c] = cls_of_group[(size_t)((circuits[c].n + 31) / 32)];
+    for (auto& k : B->cls) k.threads = default_threads(k.max_n);
+  }
+  // ---- work items per class, longest first within each: the class's
+  // prefix items, then its shot items (grouped per circuit)
   std::vector<uint64_t> items;
   std::vector<int32_t> order((size_t)m);
   std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(),
+  std::vector<int32_t> by_pre = order, by_shot = order;
+  std::stable_sort(by_pre.begin(), by_pre.end(),
                    [&](int32_t a, int32_t b) { return pre_cost[(size_t)a] > pre_cost[(size_t)b]; });
-  for (int32_t c : order) items.push_back((uint64_t)(uint32_t)c | (0xFFFFFFFFull << 32));
-  std::stable_sort(order.begin(), order.end(),
+  std::stable_sort(by_shot.begin(), by_shot.end(),
                    [&](int32_t a, int32_t b) { return shot_cost[(size_t)a] > shot_cost[(size_t)b]; });
-  for (int32_t c : order) {
-    if (circs[(size_t)c].n_meas == 0 || circs[(size_t)c].sampled) continue;
-    for (int32_t s = 0; s < circs[(size_t)c].shots; ++s)
-      items.push_back((uint64_t)(uint32_t)c | ((uint64_t)(uint32_t)s << 32));
+  for (size_t k = 0; k < B->cls.size(); ++k) {
+    B->cls[k].item_begin = (int)items.size();
+    for (int32_t c : by_pre)
+      if (B->ccls[(size_t)c] == (int32_t)k) items.push_back((uint64_t)(uint32_t)c | (0xFFFFFFFFull << 32));
+    for (int32_t c : by_shot) {
+      if (B->ccls[(size_t)c] != (int32_t)k || circs[(size_t)c].n_meas == 0 || circs[(size_t)c].sampled)
+        continue;
+      for (int32_t s = 0; s < circs[(size_t)c].shots; ++s)
+        items.push_back((uint64_t)(uint32_t)c | ((uint64_t)(uint32_t)s << 32));
+    }
+    B->cls[k].item_end = (int)items.size();
   }
-  // shot items of equal cost stay grouped per circuit; interleave nothing else
   B->nitems = (int)items.size();
   // ---- device image: one allocation
   const size_t b_circs = a256(circs.size() * sizeof(BatchCirc) + 1);
@@ -301,7 +348,8 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
   const size_t b_items = a256(items.size() * 8 + 8);
   const size_t b_img = a256(img_words * 4 + 16);
   const size_t b_noise = a256(noise.size() * 4 + 4);
-  B->ctl_bytes = a256(16 + (size_t)m * 4 + 4);
+  const size_t q_bytes = ((B->cls.size() * 4) + 15) & ~(size_t)15;  // queue counters
+  B->ctl_bytes = a256(16 + q_bytes + (size_t)m * 4 + 4);
   const size_t total = b_circs + b_segs + b_ops + b_lo + b_items + b_img + b_noise + B->ctl_bytes;
   B->h2d_bytes = (int64_t)(circs.size() * sizeof(BatchCirc) + segs.size() * sizeof(Seg) +
                            ops.size() * 4 + layer_off.size() * 4 + items.size() * 8 +
@@ -335,36 +383,46 @@ int build_batch(const tab_circuit* circuits, int32_t m, const int64_t* out_offse
   if (!noise.empty()) CUB(cudaMemcpy(p, noise.data(), noise.size() * 4, cudaMemcpyHostToDevice));
   p += b_noise;
   B->ctl = p;
-  A.queue = reinterpret_cast<unsigned int*>(p);
-  A.err = reinterpret_cast<int*>(p + 4);
-  A.ready = reinterpret_cast<int*>(p + 16);
-  A.nitems = B->nitems;
+  A.err = reinterpret_cast<int*>(p);
+  A.ready = reinterpret_cast<int*>(p + 16 + q_bytes);
   A.ncirc = (int)circs.size();
   int dev = 0;
   CUB(cudaGetDevice(&dev));
   CUB(cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, dev));
-  return configure(B, kBatchDefaultThreads);
+  for (size_t k = 0; k < B->cls.size(); ++k) {
+    tab_batch_s::Class& K = B->cls[k];
+    K.args = A;
+    K.args.items = A.items + K.item_begin;
+    K.args.nitems = K.item_end - K.item_begin;
+    K.args.queue = reinterpret_cast<unsigned int*>(p + 16) + k;
+    const int rc = configure(B, (int)k, K.threads);
+    if (rc != TAB_OK) return rc;
+  }
+  return TAB_OK;
 }
 
-// CTA shape of the persistent launch: `threads` per CTA, shared memory for
-// the batch's largest tableau, and as many CTAs as fit on the GPU at once.
-int configure(tab_batch_s* B, int threads) {
-  size_t smem = sct_smem_bytes(B->max_n, threads);
-  for (size_t c = 0; c < B->cn.size(); ++c)  // a shot's noise draws follow its tableau
-    if (B->cnoise[c])
+// CTA shape of class k's persistent launch: `threads` per CTA, shared memory
+// for the class's largest tableau (with a shot's noise draws or a sampled
+// circuit's forms), and as many CTAs as fit on the GPU at once.
+int configure(tab_batch_s* B, int k, int threads) {
+  tab_batch_s::Class& K = B->cls[(size_t)k];
+  size_t smem = sct_smem_bytes(K.max_n, threads);
+  for (size_t c = 0; c < B->cn.size(); ++c) {
+    if (B->ccls[c] != k) continue;
+    if (B->cnoise[c])  // a shot's noise draws follow its tableau
       smem = std::max(smem, sct_smem_bytes(B->cn[c], threads) + (((size_t)B->cnoise[c] + 3) & ~(size_t)3));
-  for (size_t c = 0; c < B->cn.size(); ++c)
     if (B->csampled[c])
       smem = std::max(smem, sct_smem_bytes(B->cn[c], threads) +
                                 sct_sampler_bytes(B->cn[c], B->ck[c], B->cshots[c]));
+  }
   const int occ = batch_ctas_per_sm(threads, smem);
   if (occ <= 0) {
     set_error("the batched kernel does not launch with %d threads", threads);
     return TAB_ECUDA;
   }
-  B->threads = threads;
-  B->smem = smem;
-  B->ctas = std::max(1, std::min(B->nitems, B->sms * occ));
+  K.threads = threads;
+  K.smem = smem;
+  K.ctas = std::max(1, std::min(std::max(K.args.nitems, 1), B->sms * occ));
   return TAB_OK;
 }
 
@@ -377,17 +435,34 @@ int make_graph(tab_batch_s* B) {
   mp.width = B->ctl_bytes;
   mp.height = 1;
   mp.pitch = 0;
-  cudaGraphNode_t mnode;
-  CUB(cudaGraphAddMemsetNode(&mnode, B->graph, nullptr, 0, &mp));
-  void* kargs[] = {&B->args};
-  cudaKernelNodeParams kp{};
-  kp.func = const_cast<void*>(batch_kernel_ptr(B->threads));
-  kp.gridDim = dim3(B->ctas);
-  kp.blockDim = dim3(B->threads);
-  kp.sharedMemBytes = (unsigned)B->smem;
-  kp.kernelParams = kargs;
-  CUB(cudaGraphAddKernelNode(&B->knode, B->graph, &mnode, 1, &kp));
+  cudaGraphNode_t prev;
+  CUB(cudaGraphAddMemsetNode(&prev, B->graph, nullptr, 0, &mp));
+  for (auto& K : B->cls) {
+    if (K.args.nitems == 0) {
+      K.knode = nullptr;
+      continue;
+    }
+    void* kargs[] = {&K.args};
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void*>(batch_kernel_ptr(K.threads));
+    kp.gridDim = dim3(K.ctas);
+    kp.blockDim = dim3(K.threads);
+    kp.sharedMemBytes = (unsigned)K.smem;
+    kp.kernelParams = kargs;
+    CUB(cudaGraphAddKernelNode(&K.knode, B->graph, &prev, 1, &kp));
+    prev = K.knode;
+  }
   CUB(cudaGraphInstantiate(&B->gexec, B->graph, 0));
+  return TAB_OK;
+}
+
+// Kernel attributes of every class's CTA shape.
+int prepare_classes(tab_batch_s* B) {
+  for (const auto& K : B->cls)
+    if (prepare_batch_kernel(K.threads) != cudaSuccess) {
+      set_error("kernel attribute setup failed");
+      return TAB_ECUDA;
+    }
   return TAB_OK;
 }
 
@@ -417,7 +492,7 @@ int tab_batch_create_ex(const tab_circuit* circuits, int32_t m, uint32_t flags,
   }
   B->sample = (flags & TAB_BATCH_SAMPLE_TERMINAL) != 0;
   int rc = build_batch(circuits, m, nullptr, B);
-  if (rc == TAB_OK) rc = prepare_batch_kernel(B->threads) == cudaSuccess ? TAB_OK : TAB_ECUDA;
+  if (rc == TAB_OK) rc = prepare_classes(B);
   if (rc != TAB_OK) {
     tab_batch_destroy(B);
     return rc;
@@ -461,7 +536,9 @@ int tab_batch_launches(tab_batch_t B, int64_t* count) {
     set_error("null argument");
     return TAB_EINVAL;
   }
-  *count = 1;
+  int64_t n = 0;
+  for (const auto& K : B->cls) n += K.args.nitems > 0;
+  *count = n;
   return TAB_OK;
 }
 
@@ -478,18 +555,25 @@ int tab_batch_exec(tab_batch_t B, uint64_t seed, uint8_t* dev_out, void* cuda_st
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   B->args.seed = seed;
   B->args.out = dev_out;
+  for (auto& K : B->cls) {
+    K.args.seed = seed;
+    K.args.out = dev_out;
+  }
   if (!B->gexec) {
     int rc = make_graph(B);
     if (rc != TAB_OK) return rc;
   } else {
-    void* kargs[] = {&B->args};
-    cudaKernelNodeParams kp{};
-    kp.func = const_cast<void*>(batch_kernel_ptr(B->threads));
-    kp.gridDim = dim3(B->ctas);
-    kp.blockDim = dim3(B->threads);
-    kp.sharedMemBytes = (unsigned)B->smem;
-    kp.kernelParams = kargs;
-    CUB(cudaGraphExecKernelNodeSetParams(B->gexec, B->knode, &kp));
+    for (auto& K : B->cls) {
+      if (!K.knode) continue;
+      void* kargs[] = {&K.args};
+      cudaKernelNodeParams kp{};
+      kp.func = const_cast<void*>(batch_kernel_ptr(K.threads));
+      kp.gridDim = dim3(K.ctas);
+      kp.blockDim = dim3(K.threads);
+      kp.sharedMemBytes = (unsigned)K.smem;
+      kp.kernelParams = kargs;
+      CUB(cudaGraphExecKernelNodeSetParams(B->gexec, K.knode, &kp));
+    }
   }
   CUB(cudaGraphLaunch(B->gexec, st));
   return TAB_OK;
@@ -602,10 +686,7 @@ int tab_batch_run(const tab_circuit* circuits, int32_t m, uint64_t seed, uint8_t
     }
     parts.push_back(B);
     rc = build_batch(circuits + c0, mk, offs.data() + c0, B);
-    if (rc == TAB_OK && prepare_batch_kernel(B->threads) != cudaSuccess) {
-      set_error("kernel attribute setup failed");
-      rc = TAB_ECUDA;
-    }
+    if (rc == TAB_OK) rc = prepare_classes(B);
     if (rc == TAB_OK) rc = tab_batch_exec(B, seed, dout, st);
   }
   if (cudaStreamSynchronize(st) != cudaSuccess && rc == TAB_OK) {
@@ -636,11 +717,13 @@ int tab_batch_run(const tab_circuit* circuits, int32_t m, uint64_t seed, uint8_t
   return rc;
 }
 
-// Autotuner: run the whole batch once with every CTA shape the kernel is
-// built for (threads per CTA; shared memory sized to the largest tableau; as
-// many CTAs as fit), time each run with events on `cuda_stream`, keep the
-// fastest for later tab_batch_exec replays.  The runs write the same outcomes
-// as an exec with this seed would.
+// Autotuner: run each size class's launch alone with every CTA size the
+// kernel is built for (shared memory sized to the class's largest tableau;
+// as many CTAs as fit), time each run with events on `cuda_stream`, keep the
+// fastest per class for later tab_batch_exec replays.  The runs write the
+// same outcomes as an exec with this seed would.  *threads_out: the CTA size
+// of the first (largest-qubit) class; *best_ms_out: the sum of the classes'
+// best times.
 int tab_batch_tune(tab_batch_t B, uint64_t seed, uint8_t* dev_out, void* cuda_stream,
                    int32_t* threads_out, float* best_ms_out) {
   if (!B) {
@@ -655,49 +738,59 @@ int tab_batch_tune(tab_batch_t B, uint64_t seed, uint8_t* dev_out, void* cuda_st
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CUB(cudaEventCreate(&e0));
   CUB(cudaEventCreate(&e1));
-  int best = -1;
-  float best_ms = 0.f;
   int rc = TAB_OK;
-  for (int threads : kBatchThreadChoices) {
-    if (configure(B, threads) != TAB_OK) continue;
-    B->args.seed = seed;
-    B->args.out = dev_out;
-    void* kargs[] = {&B->args};
-    cudaError_t e = cudaMemsetAsync(B->ctl, 0, B->ctl_bytes, st);
-    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-    if (e == cudaSuccess)
-      e = cudaLaunchKernel(batch_kernel_ptr(threads), dim3(B->ctas), dim3(threads), kargs, B->smem,
-                           st);
-    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-    if (e != cudaSuccess) {
-      set_error("tuning launch failed: %s", cudaGetErrorString(e));
+  float total_ms = 0.f;
+  for (size_t k = 0; k < B->cls.size() && rc == TAB_OK; ++k) {
+    tab_batch_s::Class& K = B->cls[k];
+    if (K.args.nitems == 0) continue;
+    K.args.seed = seed;
+    K.args.out = dev_out;
+    int best = -1;
+    float best_ms = 0.f;
+    for (int threads : kBatchThreadChoices) {
+      if (prepare_batch_kernel(threads) != cudaSuccess || configure(B, (int)k, threads) != TAB_OK) {
+        cudaGetLastError();
+        continue;
+      }
+      void* kargs[] = {&K.args};
+      cudaError_t e = cudaMemsetAsync(B->ctl, 0, B->ctl_bytes, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+      if (e == cudaSuccess)
+        e = cudaLaunchKernel(batch_kernel_ptr(threads), dim3(K.ctas), dim3(threads), kargs, K.smem,
+                             st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e != cudaSuccess) {
+        set_error("tuning launch failed: %s", cudaGetErrorString(e));
+        rc = TAB_ECUDA;
+        break;
+      }
+      rc = batch_error(B, cuda_stream);
+      if (rc != TAB_OK) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (best < 0 || ms < best_ms) {
+        best = threads;
+        best_ms = ms;
+      }
+    }
+    if (rc != TAB_OK) break;
+    if (best < 0) {
+      set_error("no CTA shape of the batched kernel launches for qubits %d..%d", K.lo_n, K.max_n);
       rc = TAB_ECUDA;
       break;
     }
-    rc = batch_error(B, cuda_stream);
-    if (rc != TAB_OK) break;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (best < 0 || ms < best_ms) {
-      best = threads;
-      best_ms = ms;
-    }
+    rc = configure(B, (int)k, best);
+    total_ms += best_ms;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != TAB_OK) return rc;
-  if (best < 0) {
-    set_error("no CTA shape of the batched kernel launches");
-    return TAB_ECUDA;
-  }
-  rc = configure(B, best);
-  if (rc != TAB_OK) return rc;
-  if (B->gexec) cudaGraphExecDestroy(B->gexec);  // rebuilt with the new shape
+  if (B->gexec) cudaGraphExecDestroy(B->gexec);  // rebuilt with the new shapes
   if (B->graph) cudaGraphDestroy(B->graph);
   B->gexec = nullptr;
   B->graph = nullptr;
-  if (threads_out) *threads_out = best;
-  if (best_ms_out) *best_ms_out = best_ms;
+  if (threads_out) *threads_out = B->cls.empty() ? 0 : B->cls[0].threads;
+  if (best_ms_out) *best_ms_out = total_ms;
   return TAB_OK;
 }
 
@@ -715,9 +808,38 @@ int tab_batch_config(tab_batch_t B, int32_t* threads, int32_t* ctas, int64_t* sm
     set_error("null batch");
     return TAB_EINVAL;
   }
-  if (threads) *threads = B->threads;
-  if (ctas) *ctas = B->ctas;
-  if (smem_bytes) *smem_bytes = (int64_t)B->smem;
+  const bool any = !B->cls.empty();
+  if (threads) *threads = any ? B->cls[0].threads : 0;
+  if (ctas) *ctas = any ? B->cls[0].ctas : 0;
+  if (smem_bytes) *smem_bytes = any ? (int64_t)B->cls[0].smem : 0;
+  return TAB_OK;
+}
+
+int tab_batch_classes(tab_batch_t B, int32_t* count) {
+  if (!B || !count) {
+    set_error("null argument");
+    return TAB_EINVAL;
+  }
+  *count = (int32_t)B->cls.size();
+  return TAB_OK;
+}
+
+int tab_batch_class(tab_batch_t B, int32_t k, tab_batch_class_info* out) {
+  if (!B || !out) {
+    set_error("null argument");
+    return TAB_EINVAL;
+  }
+  if (k < 0 || k >= (int32_t)B->cls.size()) {
+    set_error("class %d outside [0, %d)", k, (int)B->cls.size());
+    return TAB_ERANGE;
+  }
+  const tab_batch_s::Class& K = B->cls[(size_t)k];
+  out->lo_n = K.lo_n;
+  out->max_n = K.max_n;
+  out->threads = K.threads;
+  out->ctas = K.ctas;
+  out->smem_bytes = (int64_t)K.smem;
+  out->items = K.item_end - K.item_begin;
   return TAB_OK;
 }
 

@@ -237,11 +237,12 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err)
       //   Y: +1 if x z, -1 if !x !z, +2 if x
       // (the terms of 2 r_h' above with row p's bits fixed); rows outside S'
       // get counts too, but only S' rows are read
-      uint32_t lo = 0u, hi = 0u;
+      uint32_t lo = 0u, hi = 0u, lo2 = 0u, hi2 = 0u;
       uint32_t Sw = s.sS[w];
       if (w == wp || w == wd) Sw &= ~bpm;  // S' excludes rows p and p-n
-      // two columns per iteration, so the shared-memory loads of one overlap
-      // the other's (the list entries are distinct columns)
+      // two columns per iteration, each into a counter of its own (summed
+      // at the end: addition mod 4 is associative), so the two columns'
+      // loads and updates are independent chains
       const int GG = s.GG;
       int idx = g;
       for (; idx + GG < nx; idx += 2 * GG) {
@@ -249,8 +250,8 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err)
         const uint32_t x0 = s.X[i0], z0 = s.Z[i0], x1 = s.X[i1], z1 = s.Z[i1];
         hi ^= z0 & ~(x0 ^ lo);
         lo ^= z0;
-        hi ^= z1 & ~(x1 ^ lo);
-        lo ^= z1;
+        hi2 ^= z1 & ~(x1 ^ lo2);
+        lo2 ^= z1;
         s.X[i0] = x0 ^ Sw;
         s.X[i1] = x1 ^ Sw;
       }
@@ -266,16 +267,16 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err)
         const uint32_t x0 = s.X[i0], z0 = s.Z[i0], x1 = s.X[i1], z1 = s.Z[i1];
         hi ^= x0 & (z0 ^ lo);
         lo ^= x0;
-        hi ^= x1 & (z1 ^ lo);
-        lo ^= x1;
+        hi2 ^= x1 & (z1 ^ lo2);
+        lo2 ^= x1;
         s.Z[i0] = z0 ^ Sw;
         s.Z[i1] = z1 ^ Sw;
       }
       if (idx < nz) {
         const size_t i = (size_t)lZ[idx] * Wp + w;
         const uint32_t x = s.X[i], z = s.Z[i];
-        hi ^= x & (z ^ lo);
-        lo ^= x;
+        hi2 ^= x & (z ^ lo2);
+        lo2 ^= x;
         s.Z[i] = z ^ Sw;
       }
       for (idx = g; idx + GG < ny; idx += 2 * GG) {
@@ -284,8 +285,8 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err)
         const uint32_t e0 = ~(x0 ^ z0), e1 = ~(x1 ^ z1);
         hi ^= (e0 & ~(x0 ^ lo)) ^ x0;
         lo ^= e0;
-        hi ^= (e1 & ~(x1 ^ lo)) ^ x1;
-        lo ^= e1;
+        hi2 ^= (e1 & ~(x1 ^ lo2)) ^ x1;
+        lo2 ^= e1;
         s.X[i0] = x0 ^ Sw;
         s.Z[i0] = z0 ^ Sw;
         s.X[i1] = x1 ^ Sw;
@@ -300,6 +301,7 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err)
         s.X[i] = x ^ Sw;
         s.Z[i] = z ^ Sw;
       }
+      add4s(lo, hi, lo2, hi2);
       s.redlo[g * Wp + w] = lo;
       s.redhi[g * Wp + w] = hi;
     }

@@ -518,6 +518,15 @@ def batch_run(circuits, seed: int = 1, out=None) -> list:
 BATCH_SAMPLE_TERMINAL = 1
 
 
+class TabBatchClass(ctypes.Structure):
+    _fields_ = [("lo_n", _i32), ("max_n", _i32), ("threads", _i32), ("ctas", _i32),
+                ("smem_bytes", _i64), ("items", _i64)]
+
+
+_sig("tab_batch_classes", ctypes.c_int, [_vp, _P(_i32)])
+_sig("tab_batch_class", ctypes.c_int, [_vp, _i32, _P(TabBatchClass)])
+
+
 class Batch:
     """A compiled batch (tab_batch_create_ex) replayed with exec().
     sample_terminal: circuits whose measurements all follow their gates run
@@ -558,8 +567,21 @@ class Batch:
         _check(_L.tab_batch_sampled(self._h, ctypes.byref(c)))
         return c.value
 
+    def classes(self) -> list:
+        """Size classes (tab_batch_class): per class its qubit range, launch
+        shape and work items, largest qubit counts first."""
+        cnt = _i32()
+        _check(_L.tab_batch_classes(self._h, ctypes.byref(cnt)))
+        out = []
+        for k in range(cnt.value):
+            ci = TabBatchClass()
+            _check(_L.tab_batch_class(self._h, k, ctypes.byref(ci)))
+            out.append({f: getattr(ci, f) for f, _ in TabBatchClass._fields_})
+        return out
+
     def config(self):
-        """Current launch shape: {"threads", "ctas", "smem_bytes"}."""
+        """Launch shape of the first (largest-qubit) size class:
+        {"threads", "ctas", "smem_bytes"}."""
         t, c, s = _i32(), _i32(), _i64()
         _check(_L.tab_batch_config(self._h, ctypes.byref(t), ctypes.byref(c), ctypes.byref(s)))
         return {"threads": t.value, "ctas": c.value, "smem_bytes": s.value}
