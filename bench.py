@@ -86,6 +86,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="batched: skip the n=1000 key")
+    p.add_argument("--timed-only", action="store_true",
+                   help="batched: only the tuned replays (profiler launch lists); no plain-path, "
+                        "sampler, e2e, extra or baseline keys")
     return p.parse_args()
 
 
@@ -633,6 +636,8 @@ def run_batched(args, ws, rank, local):
     plain_ms = 0.0
     sample_g = sample_m = 0
     for c, (_, _, _, cid) in zip(circs[::stride], circuits[::stride]):
+        if args.timed_only:
+            break
         with tab.Program(c.n, c.gates) as prog, tab.Tableau(c.n, stream=stream) as t:
             t.reset()
             t.run(prog)   # warm the engine's first-use set-up outside the timing
@@ -648,36 +653,42 @@ def run_batched(args, ws, rank, local):
             plain_ms += e0.elapsed_time(e1)
         sample_g += c.n_gates
         sample_m += c.n_meas * c.shots
-    plain_gps = sample_g / (plain_ms / 1000.0)
-    plain_mps = sample_m / (plain_ms / 1000.0)
+    plain_gps = sample_g / (plain_ms / 1000.0) if plain_ms else float("nan")
+    plain_mps = sample_m / (plain_ms / 1000.0) if plain_ms else float("nan")
+    if args.timed_only:
+        args.no_e2e = args.no_extras = args.no_cpu_baseline = True
 
     # ---- the terminal-measurement sampler on the same batch (reported apart
     # from the per-shot numbers): same outcome bytes, checked here
-    sb = tab.Batch(circuits, sample_terminal=True)
-    s_out = torch.empty_like(out)
-    s_threads, _ = sb.tune(C.PHILOX_SEED, s_out.data_ptr(), stream)
-    b.exec(C.PHILOX_SEED, out.data_ptr(), stream)
-    for _ in range(max(args.warmup, 1)):
-        sb.exec(C.PHILOX_SEED, s_out.data_ptr(), stream)
-    torch.cuda.synchronize()
-    same = bool(torch.equal(out, s_out))
-    s_evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-             for _ in range(args.steps)]
-    for s in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(s & 0xFF)
-        s_evs[s][0].record(stream)
-        sb.exec(C.PHILOX_SEED, s_out.data_ptr(), stream)
-        s_evs[s][1].record(stream)
-    torch.cuda.synchronize()
-    s_ms = allreduce_max(statistics.mean(a.elapsed_time(z) for a, z in s_evs), ws)
-    sampler = {"ms_per_step": s_ms, "gates_per_s": ws * n_gates / (s_ms / 1000.0),
-               "meas_per_s": ws * n_meas / (s_ms / 1000.0),
-               "circuits_sampled": sb.sampled, "threads": s_threads,
-               "outcomes_equal_per_shot_run": same,
-               "note": "terminal measurements run once per circuit with affine sign forms, "
-                       "every shot evaluated from its Philox bits"}
-    sb.close()
+    sampler = None
+    sb = None if args.timed_only else tab.Batch(circuits, sample_terminal=True)
+    s_out = torch.empty_like(out) if sb is not None else None
+    if sb is None:
+        s_ms = float("nan")
+    else:
+        s_threads, _ = sb.tune(C.PHILOX_SEED, s_out.data_ptr(), stream)
+        b.exec(C.PHILOX_SEED, out.data_ptr(), stream)
+        for _ in range(max(args.warmup, 1)):
+            sb.exec(C.PHILOX_SEED, s_out.data_ptr(), stream)
+        torch.cuda.synchronize()
+        same = bool(torch.equal(out, s_out))
+        s_evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                 for _ in range(args.steps)]
+        for s in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(s & 0xFF)
+            s_evs[s][0].record(stream)
+            sb.exec(C.PHILOX_SEED, s_out.data_ptr(), stream)
+            s_evs[s][1].record(stream)
+        torch.cuda.synchronize()
+        s_ms = allreduce_max(statistics.mean(a.elapsed_time(z) for a, z in s_evs), ws)
+        sampler = {"ms_per_step": s_ms, "gates_per_s": ws * n_gates / (s_ms / 1000.0),
+                   "meas_per_s": ws * n_meas / (s_ms / 1000.0),
+                   "circuits_sampled": sb.sampled, "threads": s_threads,
+                   "outcomes_equal_per_shot_run": same,
+                   "note": "terminal measurements run once per circuit with affine sign forms, "
+                           "every shot evaluated from its Philox bits"}
+        sb.close()
 
     # ---- end to end: tab_batch_run with host gate lists and a pinned host
     # output buffer (host compile, upload, run, outcome copy) per step
@@ -729,11 +740,12 @@ def run_batched(args, ws, rank, local):
                                          "run alone once per shape"}},
         "gpu_launches": b.launches * args.steps, "clocks": clk, "roofline": roof,
         "e2e": e2e,
-        "plain_path": {"gates_per_s": ws * plain_gps, "meas_per_s": ws * plain_mps,
-                       "ms_estimated": n_gates / plain_gps * 1000.0,
-                       "sample": f"every {stride}th circuit ({len(circs[::stride])}), all its "
-                                 "shots, one tab_run per shot, CUDA events",
-                       "batched_speedup": (n_gates / plain_gps * 1000.0) / ms},
+        "plain_path": None if args.timed_only else {
+            "gates_per_s": ws * plain_gps, "meas_per_s": ws * plain_mps,
+            "ms_estimated": n_gates / plain_gps * 1000.0,
+            "sample": f"every {stride}th circuit ({len(circs[::stride])}), all its "
+                      "shots, one tab_run per shot, CUDA events",
+            "batched_speedup": (n_gates / plain_gps * 1000.0) / ms},
         "sampler": sampler,
         "peaks": pk,
     }
