@@ -235,9 +235,10 @@ static void bank_order(uint2* recs, const uint32_t* group_size, int ngroups) {
 
 // Emit the run's blocks, grouped by super-layer and, inside one, into
 // single- and two-qubit blocks (a warp of one kind takes one path), each
-// group in bank order.  A CNOT is stored with its control in register 0 (the
-// block's two registers relabelled if needed: the qubits, the U and the V
-// codes trade places; the swap flag keeps its meaning).  Super-layers above
+// group in bank order where bank_order_on.  A CNOT is stored with its
+// control in register 0 (the block's two registers relabelled if needed: the
+// qubits, the U and the V codes trade places; the swap flag keeps its
+// meaning).  Super-layers above
 // kMaxLayerOps blocks become consecutive sub-layers.  Appends to P.blk and
 // P.blk_off and sets s.blk_begin / s.blk_end.
 void BlockBuilder::emit(HostProgram& P, Seg& s) {
@@ -288,7 +289,7 @@ void BlockBuilder::emit(HostProgram& P, Seg& s) {
   for (int32_t L = 0; L < top; ++L) {
     uint32_t sz = 0;
     for (int t = 0; t < kKinds; ++t) sz += cnt[(size_t)L * kKinds + t];
-    bank_order(P.blk.data() + run, cnt.data() + (size_t)L * kKinds, kKinds);
+    if (bank_order_on) bank_order(P.blk.data() + run, cnt.data() + (size_t)L * kKinds, kKinds);
     while (sz > (uint32_t)kMaxLayerOps) {
       run += kMaxLayerOps;
       sz -= kMaxLayerOps;

@@ -20,6 +20,8 @@
 #include <stdint.h>
 #include <stdlib.h>
 
+#include <atomic>
+
 #include "clifford1.h"
 #include "gate_rules.cuh"
 #include "tab_internal.h"
@@ -116,7 +118,7 @@ __device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_
 // two columns back (exchanged if the block swaps them).  The records (8
 // bytes) stream through the TMA ring.
 constexpr int kBlkChunk = 512;                  // records per TMA copy (4 KB)
-constexpr int kBlkSlots = 16;                   // 64 KB ring (12 slots, 48 KB, for large n)
+constexpr int kBlkSlots = 16;                   // 64 KB ring (10 slots, 40 KB, for large n)
 constexpr int kBlkRing = kBlkChunk * kBlkSlots;
 
 // Single-qubit codes as masks: for code m, {alpha, beta, gamma, delta} and
@@ -327,23 +329,45 @@ static cudaError_t launch_gates_block_t(uint32_t* X, uint32_t* Z, uint32_t* R, i
   return cudaGetLastError();
 }
 
-// Ring slots: 16, or 12 where the smaller ring (still two super-layers of at
-// most kMaxLayerOps records plus a chunk on each side) is what lets two CTAs
-// share an SM (228 KB per SM, 1 KB of it reserved per CTA, about 4.4 KB of
-// static shared memory).
+// Ring slots: 16, or 10 where the smaller ring (still two super-layers of at
+// most kMaxLayerOps records plus a chunk on each side: 5,120 records) is what
+// lets two CTAs share an SM.  The budget is the device's shared memory per SM
+// split in two, less the per-CTA reservation and the kernel's static share
+// (mbarriers, the code-mask table), queried once per device.
 static int block_slots(int n) {
-  const size_t two_per_sm = 111000;
-  const size_t c16 = (size_t)16 * kBlkChunk * 8 + (size_t)8 * n;
-  const size_t c12 = (size_t)12 * kBlkChunk * 8 + (size_t)8 * n;
-  return (c16 > two_per_sm && c12 <= two_per_sm) ? 12 : 16;
+  constexpr int kMaxDev = 64;
+  static std::atomic<long long> budget[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+    cudaGetLastError();
+    return 16;
+  }
+  long long two = budget[dev].load();
+  if (two == 0) {
+    int per_sm = 0, reserved = 0;
+    cudaFuncAttributes fa{};
+    if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) !=
+            cudaSuccess ||
+        cudaFuncGetAttributes(&fa, (const void*)k_gates_block<512, 10>) != cudaSuccess) {
+      cudaGetLastError();
+      return 16;
+    }
+    two = (long long)per_sm / 2 - reserved - (long long)fa.sharedSizeBytes;
+    budget[dev].store(two > 0 ? two : -1);
+  }
+  const long long c16 = 16LL * kBlkChunk * 8 + 8LL * n;
+  const long long c10 = 10LL * kBlkChunk * 8 + 8LL * n;
+  return (c16 > two && c10 <= two) ? 10 : 16;
 }
 
 cudaError_t launch_gates_block(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int W,
                                const uint2* blk, const uint32_t* blk_off, int nlayers, int* err,
                                cudaStream_t s, int threads) {
   if (nlayers <= 0) return cudaSuccess;
-  if (block_slots(n) == 12)
-    return launch_gates_block_t<512, 12>(X, Z, R, n, W, blk, blk_off, nlayers, err, s);
+  if (block_slots(n) == 10)
+    return launch_gates_block_t<512, 10>(X, Z, R, n, W, blk, blk_off, nlayers, err, s);
   switch (threads == 128 || threads == 256 || threads == 512 ? threads : block_threads(n)) {
     case 128: return launch_gates_block_t<128, 16>(X, Z, R, n, W, blk, blk_off, nlayers, err, s);
     case 256: return launch_gates_block_t<256, 16>(X, Z, R, n, W, blk, blk_off, nlayers, err, s);

@@ -195,7 +195,7 @@ int build_program(int32_t n, const tab_gate* gates, int64_t count, HostProgram* 
   // are cut into chunks that the pool's threads validate and compile at once;
   // each chunk's gates become gate runs of their own, concatenated in order.
   const int64_t kChunk = 1 << 16;
-  if (mode == kProgBlocks && count >= 2 * kChunk) {
+  if ((mode & ~kProgBankOrder) == kProgBlocks && count >= 2 * kChunk) {
     const int T = (int)std::min<int64_t>(count / kChunk, pool_threads());
     if (T >= 2) {
       std::vector<HostProgram> part((size_t)T);
@@ -233,6 +233,7 @@ static int build_range(int32_t n, const tab_gate* gates, int64_t count, HostProg
   if (layers) P.ops.reserve((size_t)count);
   // one builder per thread, kept between calls with its arrays' capacity
   static thread_local BlockBuilder bb;
+  bb.bank_order_on = (mode & kProgBankOrder) != 0;
   if (blocks) {
     bb.reset(n, (size_t)count / 2 + 16);
     P.blk.reserve((size_t)count / 2 + 16);

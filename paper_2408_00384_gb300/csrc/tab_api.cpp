@@ -984,7 +984,8 @@ int tab_prog_create(int32_t n, const tab_gate* gates, int64_t count, tab_prog_t*
     count = (int64_t)lowered.size();
   }
   // both forms: the program may run on any engine
-  if (rc == TAB_OK) rc = build_program(n, gates, count, &p->hp, kProgLayers | kProgBlocks);
+  if (rc == TAB_OK)
+    rc = build_program(n, gates, count, &p->hp, kProgLayers | kProgBlocks | kProgBankOrder);
   if (rc == TAB_OK) {
     DevProg d;
     rc = upload(p->hp, &d, nullptr, false);

@@ -92,7 +92,12 @@ struct Seg {
 //                gate kernel of the multi-CTA engines (blocks.cpp).
 //   kProgNoise   (with kProgLayers only) Pauli noise ops are kept as OP_NOISE
 //                codes and listed in `noise`, for per-shot draws on the device.
-enum : int { kProgLayers = 1, kProgBlocks = 2, kProgNoise = 4 };
+//   kProgBankOrder  (with kProgBlocks) order each super-layer's records so
+//                that a warp's 32 lanes touch distinct shared-memory banks
+//                where the layer allows: about twice the host compile time,
+//                so it is used where a program is compiled once and replayed
+//                (tab_prog_create), not on the per-call paths.
+enum : int { kProgLayers = 1, kProgBlocks = 2, kProgNoise = 4, kProgBankOrder = 8 };
 
 struct HostProgram {
   int32_t n = 0;
@@ -160,6 +165,7 @@ class BlockBuilder {
   void reset(int32_t n, size_t hint);             // start a gate run (hint: blocks)
   void add(uint32_t op, uint32_t a, uint32_t b);  // next gate of the run (tab_op)
   void emit(HostProgram& P, Seg& s);              // append the run's blocks
+  bool bank_order_on = false;                     // kProgBankOrder
  private:
   struct QSlot {
     int32_t cur;     // latest block of the qubit in this run

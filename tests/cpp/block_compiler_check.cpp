@@ -80,8 +80,9 @@ int main() {
       if (op >= TAB_CNOT) while (b == a) b = (uint32_t)(rng() % n);
       g.push_back(tab_make_gate(op, a, op >= TAB_CNOT ? b : 0));
     }
-    HostProgram hp;
-    if (build_program(n, g.data(), (int64_t)g.size(), &hp, kProgBlocks) != TAB_OK) { printf("build failed\n"); return 1; }
+    HostProgram hp;  // every other circuit also with the bank order of replayed programs
+    const int mode = kProgBlocks | ((rng() & 1) ? kProgBankOrder : 0);
+    if (build_program(n, g.data(), (int64_t)g.size(), &hp, mode) != TAB_OK) { printf("build failed\n"); return 1; }
     std::vector<uint32_t> X(n), Z(n), X2, Z2;
     for (int a = 0; a < n; ++a) { X[a] = (uint32_t)rng(); Z[a] = (uint32_t)rng(); }
     uint32_t r = (uint32_t)rng(), r2 = r;
@@ -145,7 +146,7 @@ int main() {
       std::vector<int> p(n); for (int i = 0; i < n; ++i) p[i] = i; std::shuffle(p.begin(), p.end(), rng);
       for (int i = 0; i + 1 < n; i += 2) g.push_back(tab_make_gate(rng() % 4 ? TAB_CNOT : TAB_CZ, p[i], p[i + 1]));
     }
-    HostProgram hp; build_program(n, g.data(), (int64_t)g.size(), &hp, kProgBlocks);
+    HostProgram hp; build_program(n, g.data(), (int64_t)g.size(), &hp, kProgBlocks | kProgBankOrder);
     // windows of 32 records (one warp's): how many read 32 distinct banks
     // for both qubits (the bank order's goal), and the worst bank load
     long long win = 0, distinct = 0; int worst = 0;
