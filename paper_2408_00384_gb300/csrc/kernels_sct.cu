@@ -49,7 +49,8 @@ __host__ __device__ inline size_t sct_smem_words(int n, int threads) {
   int GG = threads / Wc;
   if (GG < 1) GG = 1;
   if (GG > n) GG = n;
-  return (size_t)2 * n * sct_wp(n) + 2 * (size_t)Wc + 3 * (size_t)n + 2 * (size_t)GG * sct_wp(n);
+  (void)GG;
+  return (size_t)2 * n * sct_wp(n) + 2 * (size_t)Wc + 3 * (size_t)n + 2 * (size_t)sct_wp(n);
 }
 
 size_t sct_smem_bytes(int n, int threads) { return sizeof(uint32_t) * sct_smem_words(n, threads); }
@@ -83,8 +84,8 @@ __device__ __forceinline__ void sct_setup(Sct& s, uint32_t* base, int n, int* er
   s.R = s.Z + (size_t)n * s.Wp;
   s.sS = s.R + s.Wc;
   s.supp = s.sS + s.Wc;
-  s.redlo = s.supp + 3 * n;
-  s.redhi = s.redlo + (size_t)s.GG * s.Wp;  // stride Wp (odd): lanes over groups read distinct banks
+  s.redlo = s.supp + 3 * n;  // per-word sign counters of a rowsum (low, high plane)
+  s.redhi = s.redlo + s.Wp;
 }
 
 __device__ __forceinline__ unsigned long long sct_gtimer() {
@@ -167,7 +168,11 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err)
   const bool reset = dop(code) == OP_MZR;
   const int n = s.n, Whc = s.Whc, Wc = s.Wc, Wp = s.Wp;
   const uint32_t* xa = s.X + (size_t)a * Wp;
-  for (int w = tid; w < Wc; w += T) s.sS[w] = xa[w];
+  for (int w = tid; w < Wc; w += T) {
+    s.sS[w] = xa[w];
+    s.redlo[w] = 0u;
+    s.redhi[w] = 0u;
+  }
   if (tid < 32) {
     const uint32_t v = (tid < Whc) ? xa[Whc + tid] : 0u;
     const uint32_t bal = __ballot_sync(0xffffffffu, v != 0u);
@@ -302,23 +307,20 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err)
         s.Z[i] = z ^ Sw;
       }
       add4s(lo, hi, lo2, hi2);
-      s.redlo[g * Wp + w] = lo;
-      s.redhi[g * Wp + w] = hi;
+      // this group's counters into the word's accumulator: a bit-sliced add
+      // through two atomic XORs, exact under any interleaving (the carry
+      // uses the low plane as the atomic returned it, so the adds serialise
+      // in the order of the low-plane atomics; the high plane only takes
+      // XORs)
+      if (lo | hi) {
+        const uint32_t old = atomicXor(&s.redlo[w], lo);
+        atomicXor(&s.redhi[w], hi ^ (old & lo));
+      }
     }
     __syncthreads();
-    // combine the column groups: one warp per word, lanes over groups, then a
-    // shuffle tree (mod-4 addition is associative and commutative)
-    const int cwarp = tid >> 5, cnw = T >> 5;
-    for (int ww = cwarp; ww < Wc; ww += cnw) {
-      uint32_t L = 0u, H = 0u;
-      for (int gg = lane; gg < s.GG; gg += 32) add4s(L, H, s.redlo[gg * Wp + ww], s.redhi[gg * Wp + ww]);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const uint32_t l2 = __shfl_xor_sync(0xffffffffu, L, o);
-        const uint32_t h2 = __shfl_xor_sync(0xffffffffu, H, o);
-        add4s(L, H, l2, h2);
-      }
-      if (lane != 0) continue;
+    // every word: the summed counters, row p's share and the sign update
+    for (int ww = tid; ww < Wc; ww += T) {
+      uint32_t L = s.redlo[ww], H = s.redhi[ww];
       const uint32_t scal = ((uint32_t)s_kc + 2u * rp) & 3u;
       add4s(L, H, (scal & 1u) ? 0xffffffffu : 0u, (scal & 2u) ? 0xffffffffu : 0u);
       uint32_t Sw = s.sS[ww];
