@@ -159,32 +159,40 @@ __device__ void sct_gates(const Sct& s, const uint32_t* __restrict__ ops,
 }
 
 // Measure Z_a (code = MZ / MZR on qubit a) with pre-drawn bit rbit.  Returns
-// the outcome (same value in every thread).
-__device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err) {
-  __shared__ int s_pw, s_nx, s_nz, s_kc;
+// the outcome (same value in every thread).  `next_code` (kNoNext: none) is
+// the measurement that follows with no gate in between: a random-outcome
+// measurement then also does the next one's pivot phase (its column's X bits
+// are final once the rowsum is done) inside its last phase, and sets *pre;
+// the next call, given *pre, skips that phase and its barrier.
+constexpr uint32_t kNoNext = 0xFFFFFFFFu;
+__device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err,
+                           uint32_t next_code = kNoNext, bool* pre = nullptr) {
+  __shared__ int s_pw;
+  __shared__ uint32_t s_cnt;  // list lengths: X in bits 0-9, Z 10-19, Y 20-29
+  static_assert(TAB_BATCH_MAX_QUBITS < 1024, "list lengths are packed in 10-bit fields");
   __shared__ uint32_t s_acc;
   const int tid = threadIdx.x, T = blockDim.x;
   const int a = (int)dbg_index(dq1(code), (uint32_t)s.n, err);
   const bool reset = dop(code) == OP_MZR;
   const int n = s.n, Whc = s.Whc, Wc = s.Wc, Wp = s.Wp;
   const uint32_t* xa = s.X + (size_t)a * Wp;
-  for (int w = tid; w < Wc; w += T) {
-    s.sS[w] = xa[w];
-    s.redlo[w] = 0u;
-    s.redhi[w] = 0u;
-  }
-  if (tid < 32) {
-    const uint32_t v = (tid < Whc) ? xa[Whc + tid] : 0u;
-    const uint32_t bal = __ballot_sync(0xffffffffu, v != 0u);
-    if (tid == 0) {
-      s_pw = bal ? Whc + __ffs(bal) - 1 : -1;
-      s_nx = 0;
-      s_nz = 0;
-      s_kc = 0;
-      s_acc = 0u;
+  if (!(pre && *pre)) {  // pivot phase: the mask S, zeroed counters, the pivot word
+    for (int w = tid; w < Wc; w += T) {
+      s.sS[w] = xa[w];
+      s.redlo[w] = 0u;
+      s.redhi[w] = 0u;
     }
+    if (tid < 32) {
+      const uint32_t v = (tid < Whc) ? xa[Whc + tid] : 0u;
+      const uint32_t bal = __ballot_sync(0xffffffffu, v != 0u);
+      if (tid == 0) {
+        s_pw = bal ? Whc + __ffs(bal) - 1 : -1;
+        s_cnt = 0u;
+        s_acc = 0u;
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
   const int pw = s_pw;
   if (pw >= 0) {
     // ---------------- random outcome ----------------
@@ -218,22 +226,22 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err)
       const uint32_t bx = __ballot_sync(0xffffffffu, xp & ~zp);
       const uint32_t bz = __ballot_sync(0xffffffffu, ~xp & zp);
       const uint32_t by = __ballot_sync(0xffffffffu, xp & zp);
-      int ox = 0, oz = 0, oy = 0;
-      if (lane == 0) {
-        if (bx) ox = atomicAdd(&s_nx, __popc(bx));
-        if (bz) oz = atomicAdd(&s_nz, __popc(bz));
-        if (by) oy = atomicAdd(&s_kc, __popc(by));
-      }
-      ox = __shfl_sync(0xffffffffu, ox, 0);
-      oz = __shfl_sync(0xffffffffu, oz, 0);
-      oy = __shfl_sync(0xffffffffu, oy, 0);
+      // one atomic for the three list lengths (packed 10-bit fields)
+      uint32_t old = 0u;
+      if (lane == 0 && (bx | bz | by))
+        old = atomicAdd(&s_cnt, (uint32_t)__popc(bx) | ((uint32_t)__popc(bz) << 10) |
+                                    ((uint32_t)__popc(by) << 20));
+      old = __shfl_sync(0xffffffffu, old, 0);
+      const int ox = (int)(old & 1023u), oz = (int)((old >> 10) & 1023u),
+                oy = (int)((old >> 20) & 1023u);
       const uint32_t lt = (1u << lane) - 1u;
       if (xp & ~zp) lX[ox + __popc(bx & lt)] = (uint32_t)j;
       if (~xp & zp) lZ[oz + __popc(bz & lt)] = (uint32_t)j;
       if (xp & zp) lY[oy + __popc(by & lt)] = (uint32_t)j;
     }
     __syncthreads();
-    const int nx = s_nx, nz = s_nz, ny = s_kc;
+    const uint32_t cnt = s_cnt;
+    const int nx = (int)(cnt & 1023u), nz = (int)((cnt >> 10) & 1023u), ny = (int)((cnt >> 20) & 1023u);
     const int g = tid / Wc, w = tid - g * Wc;
     if (g < s.GG) {
       // per row h of this word: rows in S' (x_ha = 1, h != p, p-n) take
@@ -318,10 +326,14 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err)
       }
     }
     __syncthreads();
-    // every word: the summed counters, row p's share and the sign update
+    // every word: the summed counters, row p's share and the sign update;
+    // then (with a next measurement) that measurement's pivot phase, each
+    // thread on the words it has just read
+    const bool nxt = next_code != kNoNext;
+    const uint32_t* xn = s.X + (size_t)(nxt ? dbg_index(dq1(next_code), (uint32_t)n, err) : 0u) * Wp;
     for (int ww = tid; ww < Wc; ww += T) {
       uint32_t L = s.redlo[ww], H = s.redhi[ww];
-      const uint32_t scal = ((uint32_t)s_kc + 2u * rp) & 3u;
+      const uint32_t scal = ((uint32_t)ny + 2u * rp) & 3u;
       add4s(L, H, (scal & 1u) ? 0xffffffffu : 0u, (scal & 2u) ? 0xffffffffu : 0u);
       uint32_t Sw = s.sS[ww];
       if (ww == wp || ww == wd) Sw &= ~bpm;
@@ -331,8 +343,26 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err)
       if (ww == wp) r = (r & ~bpm) | (rbit ? bpm : 0u);
       if (reset && rbit) r ^= s.Z[(size_t)a * Wp + ww];  // X_a on every row
       s.R[ww] = r;
+      if (nxt) {
+        s.sS[ww] = xn[ww];
+        s.redlo[ww] = 0u;
+        s.redhi[ww] = 0u;
+      }
+    }
+    // the next pivot word on the last warp, beside the per-word updates of
+    // the first (T >= 64; Whc <= 20 words fit one warp)
+    const int pt = tid - (T - 32);
+    if (nxt && pt >= 0) {
+      const uint32_t v = (pt < Whc) ? xn[Whc + pt] : 0u;
+      const uint32_t bal = __ballot_sync(0xffffffffu, v != 0u);
+      if (pt == 0) {
+        s_pw = bal ? Whc + __ffs(bal) - 1 : -1;
+        s_cnt = 0u;
+        s_acc = 0u;
+      }
     }
     __syncthreads();
+    if (pre) *pre = nxt;
     return (int)rbit;
   }
   // ---------------- deterministic outcome ----------------
@@ -368,6 +398,7 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err)
   if (reset && out)
     for (int w = tid; w < Wc; w += T) s.R[w] ^= s.Z[(size_t)a * Wp + w];
   __syncthreads();
+  if (pre) *pre = false;
   return out;
 }
 
@@ -538,9 +569,10 @@ __device__ void sct_run_segments(const Sct& s, const Seg* __restrict__ segs, int
     } else {
       __shared__ uint32_t s_rbits;  // outcome bits of the current 32 measurements
       uint32_t next_code = __ldg(ops + g.op_begin);  // fetched one step ahead
+      bool pre = false;  // the next measurement's pivot phase is done
       for (uint32_t op = g.op_begin; op < g.op_end; ++op) {
         const uint32_t code = next_code;
-        if (op + 1 < g.op_end) next_code = __ldg(ops + op + 1);
+        next_code = op + 1 < g.op_end ? __ldg(ops + op + 1) : kNoNext;
         const uint32_t t = (op - g.op_begin) & 31u;
         if (t == 0u) {  // warp 0 draws the next 32 outcome bits (lane i: k + i)
           if (threadIdx.x < 32) {
@@ -551,7 +583,7 @@ __device__ void sct_run_segments(const Sct& s, const Seg* __restrict__ segs, int
           __syncthreads();
         }
         const uint32_t rbit = (s_rbits >> t) & 1u;
-        const int m = sct_measure(s, code, rbit, err);
+        const int m = sct_measure(s, code, rbit, err, next_code, &pre);
         if (threadIdx.x == 0) out[o] = (uint8_t)m;
         ++k;
         ++o;
