@@ -334,9 +334,14 @@ typedef struct {
  * Outcomes of (circuit c, shot s) go, in program order, to
  * out_bits[out_offsets[c] + s * n_meas(c) ...] where n_meas(c) counts the
  * MZ, MZR, MX and MY ops of circuit c (tab_meas_counts); out_offsets may be
- * NULL, meaning circuits are packed back to back in order.  All shots of a circuit share the gates
- * before its first measurement (gates do not depend on outcomes).  Uses the
- * current CUDA device and the legacy default stream; synchronizes. */
+ * NULL, meaning circuits are packed back to back in order.  All shots of a
+ * circuit share the gates before its first measurement (gates do not depend
+ * on outcomes).  Large lists are cut into chunks (tab_config.batch_chunks)
+ * that the host compiles while the device runs the chunk before; with
+ * packed output in pinned host memory each chunk's outcomes are copied back
+ * behind its launch.  Uses the current CUDA device and streams of its own;
+ * synchronizes before returning.  The outcomes do not depend on the
+ * chunking. */
 int tab_batch_run(const tab_circuit *circuits, int32_t m, uint64_t seed,
                   uint8_t *out_bits, const int64_t *out_offsets);
 
@@ -380,8 +385,9 @@ int tab_batch_h2d_bytes(tab_batch_t b, int64_t *bytes);
  * tableaus take the same number of CTAs per SM -- and each class runs as a
  * persistent launch of its own, shaped for it (threads per CTA, shared
  * memory for its largest tableau, as many CTAs as fit); tab_batch_exec
- * launches the classes one after another (one CUDA graph), the largest
- * qubit counts first.  tab_batch_classes: their number; tab_batch_class:
+ * launches the classes in one CUDA graph, the largest qubit counts first,
+ * each class's launch starting once every CTA of the one before is running
+ * (its CTAs then take SMs as the earlier classes finish).  tab_batch_classes: their number; tab_batch_class:
  * class k's range and shape. */
 typedef struct {
   int32_t lo_n, max_n;   /* qubit counts of the class: lo_n .. max_n */
@@ -494,7 +500,8 @@ int tab_tune(tab_t h, tab_prog_t p, int32_t reps, tab_tuned *out);
  * Launch-shape knobs (0 = the library's choice by size), the limit of the
  * device-side grid-barrier waits, and test-only fault injection.  The
  * paper has no counterpart.  Initial values come from the environment
- * (TAB_BLOCK_THREADS, TAB_MEAS_BATCH, TAB_GRID_CTAS), read on first use.
+ * (TAB_BLOCK_THREADS, TAB_MEAS_BATCH, TAB_GRID_CTAS, TAB_BATCH_CHUNKS), read on
+ * first use.
  * tab_set_config applies to launches issued after it returns; grid_ctas
  * applies to handles created after it.  TAB_EINVAL (nothing changed) for an
  * out-of-range field. */
@@ -506,6 +513,10 @@ typedef struct {
   uint64_t wait_limit_ns; /* limit of each grid-barrier wait in the measurement
                              engines; 0 = 2 s.  A wait that runs out latches a
                              device error reported as TAB_ETIMEOUT */
+  int32_t batch_chunks;   /* tab_batch_run: pieces the circuit list is cut into,
+                             each compiled on the host while the device runs
+                             the one before; 0 = by size, else 1..64 */
+  int32_t reserved;       /* 0 */
 } tab_config;
 /* Test-only: in every grid-resident measurement launch the last CTA skips its
  * first grid-barrier arrival and leaves, so the other CTAs' bounded waits run

@@ -52,7 +52,11 @@ struct tab_batch_s {
   int nitems = 0;
   // Size classes: circuits whose tableaus take the same number of CTAs per
   // SM run in a persistent launch of their own, shaped for them (threads,
-  // shared memory, CTAs); the launches follow one another in one graph.
+  // shared memory, CTAs).  In the batch's graph each class's launch follows
+  // the control memset and starts as soon as every CTA of the class before it
+  // is running (largest tableaus first), so its CTAs take the SMs that the
+  // earlier classes leave as their queues run dry: no class waits for the
+  // tail of the one before.
   struct Class {
     int lo_n = 0, max_n = 0;         // qubit range of the class
     int item_begin = 0, item_end = 0;
@@ -123,7 +127,9 @@ int compile_circuit(const tab_circuit& tc, std::vector<tab_gate>& low, HostProgr
     }
   }
   if (!noise) {
-    rc = build_program(tc.n, g, count, &hp);
+    // a list with no extended ops was validated above; a lowered list is
+    // checked again on its way in
+    rc = ext ? build_program(tc.n, g, count, &hp) : build_validated(tc.n, g, count, &hp, kProgLayers);
     *prefix = (!hp.segs.empty() && hp.segs[0].kind == 0) ? 1 : 0;
     return rc;
   }
@@ -435,8 +441,8 @@ int make_graph(tab_batch_s* B) {
   mp.width = B->ctl_bytes;
   mp.height = 1;
   mp.pitch = 0;
-  cudaGraphNode_t prev;
-  CUB(cudaGraphAddMemsetNode(&prev, B->graph, nullptr, 0, &mp));
+  cudaGraphNode_t mset, prev = nullptr;
+  CUB(cudaGraphAddMemsetNode(&mset, B->graph, nullptr, 0, &mp));
   for (auto& K : B->cls) {
     if (K.args.nitems == 0) {
       K.knode = nullptr;
@@ -449,7 +455,13 @@ int make_graph(tab_batch_s* B) {
     kp.blockDim = dim3(K.threads);
     kp.sharedMemBytes = (unsigned)K.smem;
     kp.kernelParams = kargs;
-    CUB(cudaGraphAddKernelNode(&K.knode, B->graph, &prev, 1, &kp));
+    CUB(cudaGraphAddKernelNode(&K.knode, B->graph, &mset, 1, &kp));
+    if (prev) {  // launches once every CTA of the class before it has begun
+      cudaGraphEdgeData ed{};
+      ed.from_port = cudaGraphKernelNodePortLaunchCompletion;
+      ed.type = cudaGraphDependencyTypeProgrammatic;
+      CUB(cudaGraphAddDependencies(B->graph, &prev, &K.knode, &ed, 1));
+    }
     prev = K.knode;
   }
   CUB(cudaGraphInstantiate(&B->gexec, B->graph, 0));
@@ -637,26 +649,15 @@ int tab_batch_run(const tab_circuit* circuits, int32_t m, uint64_t seed, uint8_t
     set_error("bad circuit array");
     return TAB_EINVAL;
   }
-  // output spans: the caller's offsets, or circuits packed in order
-  std::vector<int64_t> counts((size_t)m + 1, 0), offs((size_t)m + 1, 0);
-  int rc = tab_meas_counts(circuits, m, counts.data());
-  if (rc != TAB_OK) return rc;
-  int64_t out_end = 0, packed = 0, gates = 0;
-  for (int32_t c = 0; c < m; ++c) {
-    const int64_t span = counts[(size_t)c] * std::max(circuits[c].shots, 0);
-    offs[(size_t)c] = out_offsets ? out_offsets[c] : packed;
-    packed += span;
-    out_end = std::max(out_end, offs[(size_t)c] + span);
-    gates += std::max<int64_t>(circuits[c].n_gates, 0);
-  }
-  if (out_end > 0 && !out_bits) {
-    set_error("null output buffer");
-    return TAB_EINVAL;
-  }
-  // Contiguous chunks of about equal gate count, compiled and launched in
-  // order on one stream: the device runs chunk k while the host pool
-  // compiles chunk k+1.  Small batches are one chunk.
-  const int K = (m >= 256 && gates >= ((int64_t)1 << 24)) ? 4 : 1;
+  int64_t gates = 0;
+  for (int32_t c = 0; c < m; ++c) gates += std::max<int64_t>(circuits[c].n_gates, 0);
+  // Contiguous chunks of about equal gate count, compiled in order on the
+  // host pool and launched on two streams in turn: the device runs chunk k
+  // (and the tail of chunk k-1) while the host compiles chunk k+1.
+  const int cfg_chunks = run_config().batch_chunks;
+  int K = cfg_chunks > 0 ? cfg_chunks
+                         : (m >= 256 && gates >= ((int64_t)1 << 24)) ? 4 : 1;
+  K = std::max(1, std::min(K, m));
   std::vector<int32_t> cut(1, 0);
   int64_t before = 0;
   for (int32_t c = 0, k = 1; c < m && k < K; ++c) {
@@ -667,15 +668,53 @@ int tab_batch_run(const tab_circuit* circuits, int32_t m, uint64_t seed, uint8_t
     }
   }
   if (cut.back() != m) cut.push_back(m);
-  cudaStream_t st = nullptr;
-  CUB(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  // Output.  Caller's offsets: one device buffer spanning them all (sized
+  // from the measurement counts first), spans copied back at the end.
+  // Packed: each chunk's outcomes are packed in a device buffer of its own
+  // and copied to the next free bytes of out_bits behind the chunk's launch
+  // (pinned out_bits) or after the last launch (pageable).
+  int rc = TAB_OK;
+  std::vector<int64_t> counts, offs;
+  int64_t out_end = 0;
+  if (out_offsets) {
+    counts.assign((size_t)m + 1, 0);
+    offs.assign((size_t)m + 1, 0);
+    rc = tab_meas_counts(circuits, m, counts.data());
+    if (rc != TAB_OK) return rc;
+    for (int32_t c = 0; c < m; ++c) {
+      const int64_t span = counts[(size_t)c] * std::max(circuits[c].shots, 0);
+      offs[(size_t)c] = out_offsets[c];
+      out_end = std::max(out_end, offs[(size_t)c] + span);
+    }
+    if (out_end > 0 && !out_bits) {
+      set_error("null output buffer");
+      return TAB_EINVAL;
+    }
+  }
+  bool pinned = false;
+  if (out_bits) {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, out_bits) == cudaSuccess)
+      pinned = pa.type == cudaMemoryTypeHost;
+    cudaGetLastError();
+  }
+  cudaStream_t st[2] = {nullptr, nullptr};
+  for (auto& s : st)
+    if (rc == TAB_OK && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("stream creation failed");
+      rc = TAB_ECUDA;
+    }
   uint8_t* dout = nullptr;
-  if (out_end > 0 && cudaMalloc((void**)&dout, (size_t)out_end) != cudaSuccess) {
+  if (rc == TAB_OK && out_end > 0 && cudaMalloc((void**)&dout, (size_t)out_end) != cudaSuccess) {
     cudaGetLastError();
     set_error("cudaMalloc of %lld output bytes failed", (long long)out_end);
     rc = TAB_ENOMEM;
   }
   std::vector<tab_batch_s*> parts;
+  std::vector<uint8_t*> pout;   // packed: per chunk device outcomes
+  std::vector<int64_t> pbase;   // packed: where the chunk's outcomes go in out_bits
+  int64_t base = 0;
   for (size_t k = 0; rc == TAB_OK && k + 1 < cut.size(); ++k) {
     const int32_t c0 = cut[k], mk = cut[k + 1] - cut[k];
     tab_batch_s* B = new (std::nothrow) tab_batch_s();
@@ -685,35 +724,70 @@ int tab_batch_run(const tab_circuit* circuits, int32_t m, uint64_t seed, uint8_t
       break;
     }
     parts.push_back(B);
-    rc = build_batch(circuits + c0, mk, offs.data() + c0, B);
+    rc = build_batch(circuits + c0, mk, out_offsets ? offs.data() + c0 : nullptr, B);
     if (rc == TAB_OK) rc = prepare_classes(B);
-    if (rc == TAB_OK) rc = tab_batch_exec(B, seed, dout, st);
-  }
-  if (cudaStreamSynchronize(st) != cudaSuccess && rc == TAB_OK) {
-    set_error("batch run failed: %s", cudaGetErrorString(cudaGetLastError()));
-    rc = TAB_ECUDA;
-  }
-  for (tab_batch_s* B : parts)
-    if (rc == TAB_OK) rc = batch_error(B, st);
-  if (rc == TAB_OK && out_end > 0) {
-    if (out_offsets) {  // copy only the spans written, leave the rest untouched
-      for (int32_t c = 0; c < m; ++c) {
-        const int64_t span = counts[(size_t)c] * circuits[c].shots;
-        if (span && cudaMemcpy(out_bits + offs[(size_t)c], dout + offs[(size_t)c], (size_t)span,
-                               cudaMemcpyDeviceToHost) != cudaSuccess) {
-          set_error("outcome copy failed");
-          rc = TAB_ECUDA;
-          break;
-        }
+    if (rc != TAB_OK) break;
+    uint8_t* dk = dout;
+    if (!out_offsets) {
+      dk = nullptr;
+      if (B->out_bytes > 0 && !out_bits) {
+        set_error("null output buffer");
+        rc = TAB_EINVAL;
+        break;
       }
-    } else if (cudaMemcpy(out_bits, dout, (size_t)out_end, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      if (B->out_bytes > 0 && cudaMalloc((void**)&dk, (size_t)B->out_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc of %lld output bytes failed", (long long)B->out_bytes);
+        rc = TAB_ENOMEM;
+        break;
+      }
+      pout.push_back(dk);
+      pbase.push_back(base);
+    }
+    cudaStream_t s = st[k & 1];
+    rc = tab_batch_exec(B, seed, dk, s);
+    if (rc == TAB_OK && !out_offsets && pinned && B->out_bytes > 0 &&
+        cudaMemcpyAsync(out_bits + base, dk, (size_t)B->out_bytes, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess) {
       set_error("outcome copy failed");
       rc = TAB_ECUDA;
     }
+    base += B->out_bytes;
   }
+  for (cudaStream_t s : st)
+    if (s && cudaStreamSynchronize(s) != cudaSuccess && rc == TAB_OK) {
+      set_error("batch run failed: %s", cudaGetErrorString(cudaGetLastError()));
+      rc = TAB_ECUDA;
+    }
+  for (tab_batch_s* B : parts)
+    if (rc == TAB_OK) rc = batch_error(B, st[0]);
+  if (rc == TAB_OK && out_offsets && out_end > 0) {
+    // copy only the spans written, leave the rest untouched
+    for (int32_t c = 0; c < m; ++c) {
+      const int64_t span = counts[(size_t)c] * circuits[c].shots;
+      if (span && cudaMemcpy(out_bits + offs[(size_t)c], dout + offs[(size_t)c], (size_t)span,
+                             cudaMemcpyDeviceToHost) != cudaSuccess) {
+        set_error("outcome copy failed");
+        rc = TAB_ECUDA;
+        break;
+      }
+    }
+  }
+  if (rc == TAB_OK && !out_offsets && !pinned)
+    for (size_t k = 0; k < pout.size() && rc == TAB_OK; ++k) {
+      const int64_t bytes = parts[k]->out_bytes;
+      if (bytes > 0 && cudaMemcpy(out_bits + pbase[k], pout[k], (size_t)bytes,
+                                  cudaMemcpyDeviceToHost) != cudaSuccess) {
+        set_error("outcome copy failed");
+        rc = TAB_ECUDA;
+      }
+    }
   if (dout) cudaFree(dout);
+  for (uint8_t* p : pout)
+    if (p) cudaFree(p);
   for (tab_batch_s* B : parts) tab_batch_destroy(B);
-  cudaStreamDestroy(st);
+  for (cudaStream_t s : st)
+    if (s) cudaStreamDestroy(s);
   return rc;
 }
 

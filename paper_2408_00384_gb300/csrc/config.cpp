@@ -2,7 +2,7 @@
 // tab_set_config in include/tab.h).
 //
 // The launch-shape knobs start from the environment (TAB_BLOCK_THREADS,
-// TAB_MEAS_BATCH, TAB_GRID_CTAS; read once, on first use) and can then be
+// TAB_MEAS_BATCH, TAB_GRID_CTAS, TAB_BATCH_CHUNKS; read once, on first use) and can then be
 // changed through the C ABI.  Launchers read a copy of the whole struct per
 // launch, under a mutex, so a change takes effect for launches issued after
 // tab_set_config returns.
@@ -37,6 +37,8 @@ void init_locked() {
   if (valid_batch(mb)) g_cfg.meas_batch = mb;
   const int gc = env_int("TAB_GRID_CTAS");
   if (gc >= 0) g_cfg.grid_ctas = gc;
+  const int bc = env_int("TAB_BATCH_CHUNKS");
+  if (bc >= 0 && bc <= kMaxBatchChunks) g_cfg.batch_chunks = bc;
   g_cfg_init = true;
 }
 
@@ -81,6 +83,14 @@ extern "C" int tab_set_config(const tab_config* cfg) {
   }
   if (cfg->grid_ctas < 0) {
     set_error("grid_ctas %d < 0", cfg->grid_ctas);
+    return TAB_EINVAL;
+  }
+  if (cfg->batch_chunks < 0 || cfg->batch_chunks > kMaxBatchChunks) {
+    set_error("batch_chunks %d outside [0, %d]", cfg->batch_chunks, kMaxBatchChunks);
+    return TAB_EINVAL;
+  }
+  if (cfg->reserved != 0) {
+    set_error("reserved field is %d, not 0", cfg->reserved);
     return TAB_EINVAL;
   }
   if (cfg->debug & ~(uint32_t)TAB_DEBUG_SKIP_BARRIER_ARRIVAL) {

@@ -13,6 +13,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -177,6 +178,10 @@ int validate_program(int32_t n, const tab_gate* gates, int64_t count, int64_t* e
   return TAB_OK;
 }
 
+int build_validated(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out, int mode) {
+  return build_range(n, gates, count, out, mode);
+}
+
 int build_validated_blocks(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out) {
   return build_range(n, gates, count, out, kProgBlocks);
 }
@@ -241,8 +246,18 @@ static int build_range(int32_t n, const tab_gate* gates, int64_t count, HostProg
   int64_t run_gates = 0;  // gates in the open gate run
   std::vector<int64_t> last((size_t)n, -1);  // global layer of the last gate per qubit
   int64_t nlayers = 0;                       // layers emitted so far (global)
-  std::vector<uint32_t> seg_codes;
-  std::vector<int32_t> seg_layer;
+  // The open segment's gate codes with their bucket keys (layer - first
+  // layer of the segment) * kOps + op, and the count per bucket, kept as the
+  // gates arrive: a layer is at most one past the segment's last, so the
+  // count table grows a layer at a time.
+  constexpr int kOps = 13;  // device op codes 0..12
+  // (plain arrays with a fill index: a segment holds at most every gate,
+  // and the per-gate appends stay inline in the loop)
+  std::unique_ptr<uint32_t[]> seg_buf(layers && count > 0 ? new uint32_t[2 * (size_t)count] : nullptr);
+  uint32_t* const seg_codes = seg_buf.get();
+  uint32_t* const seg_key = layers && count > 0 ? seg_buf.get() + count : nullptr;
+  size_t nseg = 0;
+  std::vector<uint32_t> cnt;
 
   // Each gate segment owns one contiguous run of layer_off entries:
   // layer_off[layer_begin] = op_begin, layer_off[layer_begin + L + 1] = end
@@ -261,37 +276,34 @@ static int build_range(int32_t n, const tab_gate* gates, int64_t count, HostProg
       P.segs.push_back(s);
       return;
     }
-    const int64_t base = nlayers;
-    int64_t top = base;
-    for (int32_t L : seg_layer) top = std::max<int64_t>(top, (int64_t)L + 1);
-    const int64_t nl = top - base;
-    const int kOps = 13;  // bucket by (layer, op) with a counting sort (ops 0..12)
-    std::vector<uint32_t> cnt((size_t)nl * kOps, 0);
-    for (size_t i = 0; i < seg_codes.size(); ++i)
-      cnt[(size_t)(seg_layer[i] - base) * kOps + dop(seg_codes[i])]++;
-    std::vector<uint32_t> pos(cnt.size(), 0);
+    // counting sort by (layer, op): layer sizes first, then the bucket
+    // starts in place of the counts
+    const int64_t nl = (int64_t)(cnt.size() / kOps);
+    std::vector<uint32_t> lsz((size_t)nl);
     uint32_t acc = 0;
-    for (size_t b = 0; b < cnt.size(); ++b) {
-      pos[b] = acc;
-      acc += cnt[b];
+    for (int64_t L = 0; L < nl; ++L) {
+      const uint32_t l0 = acc;
+      for (int o = 0; o < kOps; ++o) {
+        const uint32_t c = cnt[(size_t)L * kOps + o];
+        cnt[(size_t)L * kOps + o] = acc;
+        acc += c;
+      }
+      lsz[(size_t)L] = acc - l0;
     }
     const uint32_t op_base = (uint32_t)P.ops.size();
-    P.ops.resize(P.ops.size() + seg_codes.size());
-    for (size_t i = 0; i < seg_codes.size(); ++i) {
-      const size_t b = (size_t)(seg_layer[i] - base) * kOps + dop(seg_codes[i]);
-      P.ops[op_base + pos[b]++] = seg_codes[i];
-    }
+    P.ops.resize(P.ops.size() + nseg);
+    uint32_t* dst = P.ops.data() + op_base;
+    for (size_t i = 0; i < nseg; ++i) dst[cnt[seg_key[i]]++] = seg_codes[i];
     Seg s{};
     s.kind = 0;
     s.op_begin = op_base;
-    s.op_end = op_base + (uint32_t)seg_codes.size();
+    s.op_end = op_base + (uint32_t)nseg;
     s.meas_before = (uint32_t)P.n_meas;
     s.layer_begin = (uint32_t)P.layer_off.size();
     P.layer_off.push_back(op_base);
     uint32_t run = op_base;
     for (int64_t L = 0; L < nl; ++L) {
-      uint32_t sz = 0;
-      for (int o = 0; o < kOps; ++o) sz += cnt[(size_t)L * kOps + o];
+      uint32_t sz = lsz[(size_t)L];
       // a layer larger than kMaxLayerOps becomes consecutive sub-layers (its
       // gates are pairwise disjoint, so any split keeps the result)
       while (sz > (uint32_t)kMaxLayerOps) {
@@ -310,9 +322,9 @@ static int build_range(int32_t n, const tab_gate* gates, int64_t count, HostProg
       s.blk_begin = s.blk_end = (uint32_t)P.blk_off.size();
     }
     P.segs.push_back(s);
-    nlayers = top;
-    seg_codes.clear();
-    seg_layer.clear();
+    nlayers += nl;
+    nseg = 0;
+    cnt.clear();
   };
 
   for (int64_t i = 0; i < count; ++i) {
@@ -358,8 +370,11 @@ static int build_range(int32_t n, const tab_gate* gates, int64_t count, HostProg
     L += 1;
     last[q1] = L;
     if (two) last[q2] = L;
-    seg_codes.push_back(dcode(op, q1, (two || op == OP_NOISE) ? q2 : 0));
-    seg_layer.push_back((int32_t)L);
+    const size_t key = (size_t)(L - nlayers) * kOps + op;
+    if (key >= cnt.size()) cnt.resize(cnt.size() + kOps, 0);  // a new layer
+    cnt[key]++;
+    seg_codes[nseg] = dcode(op, q1, (two || op == OP_NOISE) ? q2 : 0);
+    seg_key[nseg++] = (uint32_t)key;
   }
   flush_gates();
   return TAB_OK;

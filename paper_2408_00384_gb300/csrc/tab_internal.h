@@ -143,6 +143,9 @@ int lower_for_runs(int32_t n, const tab_gate* g, int64_t count, bool keep_noise,
 // extended ops (TAB_MX .. TAB_ZERR) are accepted and *ext counts them;
 // without it they are errors.
 int validate_program(int32_t n, const tab_gate* gates, int64_t count, int64_t* ext = nullptr);
+// Compile an already validated gate list (validate_program returned TAB_OK
+// with no extended ops) in one of build_program's modes, on this thread.
+int build_validated(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out, int mode);
 // Compile an already validated piece of a gate list into blocks (kProgBlocks).
 int build_validated_blocks(int32_t n, const tab_gate* gates, int64_t count, HostProgram* out);
 // Concatenate part[0..T) -- programs compiled for consecutive pieces of one
@@ -245,6 +248,7 @@ void set_error(const char* fmt, ...);
 // Process-wide run-time configuration (config.cpp): a copy of the current
 // settings, and the grid-barrier wait limit in effect.
 constexpr unsigned long long kDefaultWaitLimitNs = 2000000000ull;  // 2 s
+constexpr int kMaxBatchChunks = 64;  // tab_config.batch_chunks upper bound
 tab_config run_config();
 unsigned long long run_wait_limit_ns();
 

@@ -135,7 +135,8 @@ _sig("tab_tune", ctypes.c_int, [_vp, _vp, _i32, _P(TabTuned)])
 
 class TabConfig(ctypes.Structure):
     _fields_ = [("block_threads", _i32), ("meas_batch", _i32), ("grid_ctas", _i32),
-                ("debug", _u32), ("wait_limit_ns", _u64)]
+                ("debug", _u32), ("wait_limit_ns", _u64), ("batch_chunks", _i32),
+                ("reserved", _i32)]
 
 
 _sig("tab_get_config", ctypes.c_int, [_P(TabConfig)])

@@ -69,16 +69,18 @@ def test_run_config_validation_without_gpu(lib):
     from paper_2408_00384_gb300 import tab
     old = tab.get_config()
     for bad in ({"block_threads": 100}, {"meas_batch": 3}, {"meas_batch": 64},
-                {"grid_ctas": -1}, {"debug": 1 << 7}):
+                {"grid_ctas": -1}, {"debug": 1 << 7}, {"batch_chunks": -1},
+                {"batch_chunks": 65}, {"reserved": 1}):
         with pytest.raises(tab.TabError) as ei:
             tab.set_config(bad)
         assert ei.value.code == tab.TAB_EINVAL
         assert tab.get_config() == old
     try:
-        tab.set_config({"block_threads": 256, "meas_batch": 8, "wait_limit_ns": 123456})
+        tab.set_config({"block_threads": 256, "meas_batch": 8, "wait_limit_ns": 123456,
+                        "batch_chunks": 64})
         got = tab.get_config()
         assert got["block_threads"] == 256 and got["meas_batch"] == 8
-        assert got["wait_limit_ns"] == 123456
+        assert got["wait_limit_ns"] == 123456 and got["batch_chunks"] == 64
     finally:
         tab.set_config(old)
     assert tab.get_config() == old

@@ -11,6 +11,7 @@ mismatch names the first differing measurement (for the batch, the circuit is
 rerun on the oracle to find the shot and index).
 """
 import numpy as np
+import torch
 import pytest
 
 import oracle
@@ -151,6 +152,22 @@ def test_config4_batch_run_host_buffers_vs_oracle(cfg4):
         got = out[offs[i]:offs[i] + sizes[i]]
         assert np.array_equal(got, np.ascontiguousarray(res[i]).reshape(-1)), i
         assert (out[offs[i] + sizes[i]:offs[i] + sizes[i] + 3] == 7).all(), i
+    # the bytes do not depend on the chunking (7 chunks on alternating
+    # streams, copied back per chunk into pinned memory; one chunk into
+    # pageable memory)
+    packed = np.concatenate([np.ascontiguousarray(r).reshape(-1) for r in res])
+    old = tab.get_config()
+    try:
+        tab.set_config({"batch_chunks": 7})
+        pinned = torch.full((int(packed.size),), 9, dtype=torch.uint8).pin_memory().numpy()
+        tab.batch_run(tc, seed=ref["seed"], out=pinned)
+        assert np.array_equal(pinned, packed)
+        tab.set_config({"batch_chunks": 1})
+        one = np.concatenate([np.ascontiguousarray(r).reshape(-1)
+                              for r in tab.batch_run(tc, seed=ref["seed"])])
+        assert np.array_equal(one, packed)
+    finally:
+        tab.set_config(old)
 
 
 # ------------------------------------------------------------- config 5 ---
