@@ -145,23 +145,26 @@ void BlockBuilder::add(uint32_t op, uint32_t a, uint32_t b) {
 }
 
 // Within one super-layer, reorder each group's records so that every aligned
-// window of 32 records (the records one warp takes together) reads its first
-// qubits, and its second qubits, from as many distinct shared-memory banks
-// as the group allows (qa mod 32, and qb mod 32 for two-qubit blocks).  The
-// blocks of a super-layer act on disjoint qubits and commute, so any order
-// gives the same tableau; groups stay contiguous.  Greedy over buckets keyed
-// by (qa mod 32, qb mod 32): each window slot takes, among the residues the
+// window of 16 records (the records one half-warp takes together) reads its
+// first qubits, and its second qubits, from as many distinct shared-memory
+// bank pairs as the group allows.  The gate kernel keeps a qubit's X and Z
+// words side by side (one 8-byte load per qubit, 16 bank pairs), so the key
+// is qa mod 16, and qb mod 16 for two-qubit blocks.  The blocks of a
+// super-layer act on disjoint qubits and commute, so any order gives the
+// same tableau; groups stay contiguous.  Greedy over buckets keyed by
+// (qa mod 16, qb mod 16): each window slot takes, among the residues the
 // window has not used yet, the first residue with the most records left and
 // then the second residue with the most records left (so the buckets drain
 // evenly and the last windows are not left with one residue), else any
 // record.
 static void bank_order(uint2* recs, const uint32_t* group_size, int ngroups) {
-  constexpr int kB = 32 * 33;  // qb residue 32: a single-qubit block
+  constexpr int kR = 16;  // residues (64-bit words: 16 bank pairs), window of kR records
+  constexpr int kB = kR * (kR + 1);  // qb residue kR: a single-qubit block
   thread_local std::vector<uint2> tmp;
   thread_local std::vector<int32_t> next;
   int32_t head[kB];
-  uint64_t row[32];  // row[i] bit j: bucket (i, j) is not empty
-  int cnt_a[32], cnt_b[33];  // records left with each first / second residue
+  uint64_t row[kR];  // row[i] bit j: bucket (i, j) is not empty
+  int cnt_a[kR], cnt_b[kR + 1];  // records left with each first / second residue
   uint32_t used_a = 0u, used_b = 0u;
   int slot = 0;
   size_t at = 0;
@@ -173,13 +176,13 @@ static void bank_order(uint2* recs, const uint32_t* group_size, int ngroups) {
     tmp.assign(G, G + size);
     next.assign(size, -1);
     for (int b = 0; b < kB; ++b) head[b] = -1;
-    for (int i = 0; i < 32; ++i) row[i] = 0u;
-    for (int i = 0; i < 32; ++i) cnt_a[i] = 0;
-    for (int j = 0; j < 33; ++j) cnt_b[j] = 0;
+    for (int i = 0; i < kR; ++i) row[i] = 0u;
+    for (int i = 0; i < kR; ++i) cnt_a[i] = 0;
+    for (int j = 0; j <= kR; ++j) cnt_b[j] = 0;
     for (size_t k = size; k-- > 0;) {
-      const uint32_t qa = tmp[k].x & 31u;
-      const uint32_t qb = ((tmp[k].x >> 28) & 1u) ? (tmp[k].x >> 14) & 31u : 32u;
-      const int b = (int)(qa * 33 + qb);
+      const uint32_t qa = tmp[k].x & (kR - 1u);
+      const uint32_t qb = ((tmp[k].x >> 28) & 1u) ? (tmp[k].x >> 14) & (kR - 1u) : (uint32_t)kR;
+      const int b = (int)(qa * (kR + 1) + qb);
       next[k] = head[b];
       head[b] = (int32_t)k;
       row[qa] |= 1ull << qb;
@@ -188,8 +191,8 @@ static void bank_order(uint2* recs, const uint32_t* group_size, int ngroups) {
     }
     for (size_t k = 0; k < size; ++k) {
       int pick_b = -1, best_a = -1;
-      const uint64_t free_b = (uint64_t)(~used_b) | (1ull << 32);
-      for (uint32_t rows = ~used_a; rows; rows &= rows - 1u) {
+      const uint64_t free_b = ((uint64_t)(~used_b) & ((1ull << kR) - 1u)) | (1ull << kR);
+      for (uint32_t rows = ~used_a & ((1u << kR) - 1u); rows; rows &= rows - 1u) {
         const int i = __builtin_ctz(rows);
         if (cnt_a[i] > best_a && (row[i] & free_b)) {
           best_a = cnt_a[i];
@@ -203,29 +206,29 @@ static void bank_order(uint2* recs, const uint32_t* group_size, int ngroups) {
           const int j = __builtin_ctzll(m);
           if (cnt_b[j] > best_b) {
             best_b = cnt_b[j];
-            pick_b = i * 33 + j;
+            pick_b = i * (kR + 1) + j;
           }
         }
       }
       // no bucket fits the window: a record whose first residue is free, or
       // whose second residue is free, else any record
-      for (uint32_t rows = ~used_a; rows && pick_b < 0; rows &= rows - 1u) {
+      for (uint32_t rows = ~used_a & ((1u << kR) - 1u); rows && pick_b < 0; rows &= rows - 1u) {
         const int i = __builtin_ctz(rows);
-        if (row[i]) pick_b = i * 33 + __builtin_ctzll(row[i]);
+        if (row[i]) pick_b = i * (kR + 1) + __builtin_ctzll(row[i]);
       }
-      for (int i = 0; i < 32 && pick_b < 0; ++i)
-        if (row[i] & free_b) pick_b = i * 33 + __builtin_ctzll(row[i] & free_b);
-      for (int i = 0; i < 32 && pick_b < 0; ++i)
-        if (row[i]) pick_b = i * 33 + __builtin_ctzll(row[i]);
+      for (int i = 0; i < kR && pick_b < 0; ++i)
+        if (row[i] & free_b) pick_b = i * (kR + 1) + __builtin_ctzll(row[i] & free_b);
+      for (int i = 0; i < kR && pick_b < 0; ++i)
+        if (row[i]) pick_b = i * (kR + 1) + __builtin_ctzll(row[i]);
       const int32_t idx = head[pick_b];
       head[pick_b] = next[(size_t)idx];
-      --cnt_a[pick_b / 33];
-      --cnt_b[pick_b % 33];
-      if (head[pick_b] < 0) row[pick_b / 33] &= ~(1ull << (pick_b % 33));
+      --cnt_a[pick_b / (kR + 1)];
+      --cnt_b[pick_b % (kR + 1)];
+      if (head[pick_b] < 0) row[pick_b / (kR + 1)] &= ~(1ull << (pick_b % (kR + 1)));
       G[k] = tmp[(size_t)idx];
-      used_a |= 1u << (pick_b / 33);
-      if (pick_b % 33 < 32) used_b |= 1u << (pick_b % 33);
-      if (++slot == 32) {
+      used_a |= 1u << (pick_b / (kR + 1));
+      if (pick_b % (kR + 1) < kR) used_b |= 1u << (pick_b % (kR + 1));
+      if (++slot == kR) {
         slot = 0;
         used_a = used_b = 0u;
       }

@@ -109,8 +109,10 @@ __device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_
 
 // ------------------------------------------------ block row-slab gates ----
 // Grid: one CTA per 32-row slab (row word w = blockIdx.x), W CTAs.  The slab
-// of every column (x and z words, 8 bytes per qubit) is staged in shared
-// memory, and the slab is written back at the end.  The gate run is compiled
+// of every column is staged in shared memory with each qubit's x and z words
+// side by side (one 8-byte access per qubit; the compiler orders a
+// super-layer's records so a half-warp's qubits fall on distinct bank
+// pairs), and the slab is written back at the end.  The gate run is compiled
 // into two-qubit blocks (blocks.cpp) grouped in super-layers of pairwise-
 // disjoint blocks, with one CTA barrier per super-layer.  A thread applies a
 // whole block to the slab's 32 rows in registers -- U_0 (x) U_1, the
@@ -152,7 +154,7 @@ __device__ __forceinline__ void c1_apply_masks(const uint4* tab, uint32_t m, uin
 // entangler is computed as CNOT-or-CZ masks.
 template <int NB>
 __device__ __forceinline__ void apply_blocks(const uint2 (&rec)[NB], const bool (&on)[NB],
-                                             const uint4* c1m, uint32_t* sx, uint32_t* sz,
+                                             const uint4* c1m, uint2* sxz,
                                              uint32_t& r, int n, int* err) {
   uint32_t qa[NB], qb[NB], m[NB], x0[NB], z0[NB], x1[NB], z1[NB];
   bool two[NB];
@@ -162,10 +164,12 @@ __device__ __forceinline__ void apply_blocks(const uint2 (&rec)[NB], const bool 
     qb[j] = dbg_index((rec[j].x >> 14) & 0x3FFFu, (uint32_t)n, err);
     two[j] = on[j] && ((rec[j].x >> 28) & 1u);
     m[j] = rec[j].y;
-    x0[j] = on[j] ? sx[qa[j]] : 0u;
-    z0[j] = on[j] ? sz[qa[j]] : 0u;
-    x1[j] = two[j] ? sx[qb[j]] : 0u;
-    z1[j] = two[j] ? sz[qb[j]] : 0u;
+    const uint2 va = on[j] ? sxz[qa[j]] : make_uint2(0u, 0u);
+    const uint2 vb = two[j] ? sxz[qb[j]] : make_uint2(0u, 0u);
+    x0[j] = va.x;
+    z0[j] = va.y;
+    x1[j] = vb.x;
+    z1[j] = vb.y;
   }
 #pragma unroll
   for (int j = 0; j < NB; ++j) {
@@ -192,14 +196,8 @@ __device__ __forceinline__ void apply_blocks(const uint2 (&rec)[NB], const bool 
   for (int j = 0; j < NB; ++j) {
     const bool sw = (m[j] >> 28) & 1u;
     const uint32_t da = sw ? qb[j] : qa[j], db = sw ? qa[j] : qb[j];
-    if (on[j]) {
-      sx[da] = x0[j];
-      sz[da] = z0[j];
-    }
-    if (two[j]) {
-      sx[db] = x1[j];
-      sz[db] = z1[j];
-    }
+    if (on[j]) sxz[da] = make_uint2(x0[j], z0[j]);
+    if (two[j]) sxz[db] = make_uint2(x1[j], z1[j]);
   }
 }
 
@@ -211,8 +209,7 @@ __global__ void __launch_bounds__(T) k_gates_block(uint32_t* __restrict__ X, uin
                                                    int nlayers, int* __restrict__ err) {
   extern __shared__ __align__(128) uint32_t sm[];
   uint2* ring = reinterpret_cast<uint2*>(sm);  // block-record ring (SLOTS * kBlkChunk records)
-  uint32_t* sx = sm + 2 * SLOTS * kBlkChunk;            // X-plane word of every column (this slab)
-  uint32_t* sz = sx + n;                       // Z-plane word of every column
+  uint2* sxz = reinterpret_cast<uint2*>(sm + 2 * SLOTS * kBlkChunk);  // (X, Z) words of every column (this slab)
   __shared__ __align__(8) uint64_t bars[SLOTS];
   __shared__ uint4 c1m[256];  // masks of the 128 single-qubit codes
   __shared__ uint32_t s_r;
@@ -231,10 +228,7 @@ __global__ void __launch_bounds__(T) k_gates_block(uint32_t* __restrict__ X, uin
       tma_bulk_g2s(ring + (size_t)issued * kBlkChunk, blk + base + (size_t)issued * kBlkChunk,
                    kBlkChunk * 8, &bars[issued]);
   }
-  for (int a = tid; a < n; a += T) {
-    sx[a] = X[(size_t)a * W + w];
-    sz[a] = Z[(size_t)a * W + w];
-  }
+  for (int a = tid; a < n; a += T) sxz[a] = make_uint2(X[(size_t)a * W + w], Z[(size_t)a * W + w]);
   c1_masks_init(c1m, tid, T);
   __syncthreads();
 
@@ -275,7 +269,7 @@ __global__ void __launch_bounds__(T) k_gates_block(uint32_t* __restrict__ X, uin
       const uint2 recs[2] = {ring[(g - base) % (SLOTS * kBlkChunk)],
                              ring[(g2 < le ? g2 - base : g - base) % (SLOTS * kBlkChunk)]};
       const bool on[2] = {true, g2 < le};
-      apply_blocks<2>(recs, on, c1m, sx, sz, racc, n, err);
+      apply_blocks<2>(recs, on, c1m, sxz, racc, n, err);
     }
     prev_lb = lb;
     lb = le;
@@ -288,8 +282,9 @@ __global__ void __launch_bounds__(T) k_gates_block(uint32_t* __restrict__ X, uin
   if (s_abort) return;
 
   for (int a = tid; a < n; a += T) {
-    X[(size_t)a * W + w] = sx[a];
-    Z[(size_t)a * W + w] = sz[a];
+    const uint2 v = sxz[a];
+    X[(size_t)a * W + w] = v.x;
+    Z[(size_t)a * W + w] = v.y;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) racc ^= __shfl_xor_sync(0xffffffffu, racc, o);

@@ -147,14 +147,15 @@ int main() {
       for (int i = 0; i + 1 < n; i += 2) g.push_back(tab_make_gate(rng() % 4 ? TAB_CNOT : TAB_CZ, p[i], p[i + 1]));
     }
     HostProgram hp; build_program(n, g.data(), (int64_t)g.size(), &hp, kProgBlocks | kProgBankOrder);
-    // windows of 32 records (one warp's): how many read 32 distinct banks
-    // for both qubits (the bank order's goal), and the worst bank load
+    // windows of 16 records (one half-warp's 8-byte loads): how many read
+    // 16 distinct bank pairs for both qubits (the bank order's goal), and
+    // the worst bank-pair load
     long long win = 0, distinct = 0; int worst = 0;
     for (size_t L = 0; L + 1 < hp.blk_off.size(); ++L) {
-      for (uint32_t w0 = hp.blk_off[L]; w0 < hp.blk_off[L + 1]; w0 += 32) {
-        uint32_t ma = 0, mb = 0; bool ok = true; int ca[32] = {0}, cb[32] = {0};
-        for (uint32_t i = w0; i < std::min(hp.blk_off[L + 1], w0 + 32); ++i) {
-          const uint32_t a = hp.blk[i].x & 31u, b = (hp.blk[i].x >> 14) & 31u;
+      for (uint32_t w0 = hp.blk_off[L]; w0 < hp.blk_off[L + 1]; w0 += 16) {
+        uint32_t ma = 0, mb = 0; bool ok = true; int ca[16] = {0}, cb[16] = {0};
+        for (uint32_t i = w0; i < std::min(hp.blk_off[L + 1], w0 + 16); ++i) {
+          const uint32_t a = hp.blk[i].x & 15u, b = (hp.blk[i].x >> 14) & 15u;
           ok = ok && !((ma >> a) & 1u) && !((mb >> b) & 1u);
           ma |= 1u << a; mb |= 1u << b;
           worst = std::max(worst, std::max(++ca[a], ++cb[b]));
