@@ -344,6 +344,14 @@ typedef struct {
  * chunking. */
 int tab_batch_run(const tab_circuit *circuits, int32_t m, uint64_t seed,
                   uint8_t *out_bits, const int64_t *out_offsets);
+/* tab_batch_run with packed output into a caller buffer of out_capacity
+ * bytes, without counting the outcomes first: counts (NULL: not wanted)
+ * receives n_meas(c) of every circuit as the chunks are compiled.
+ * TAB_ERANGE when the outcomes would pass out_capacity; the chunks launched
+ * before that point have written their bytes (all within the buffer) and
+ * nothing is written past it.  TAB_EINVAL for out_capacity < 0. */
+int tab_batch_run_packed(const tab_circuit *circuits, int32_t m, uint64_t seed,
+                         uint8_t *out_bits, int64_t out_capacity, int64_t *counts);
 
 /* A batch compiled once (gate lists validated, layered, uploaded, work items
  * sorted by cost) and replayable with tab_batch_exec; replays are captured in
@@ -515,7 +523,9 @@ typedef struct {
                              device error reported as TAB_ETIMEOUT */
   int32_t batch_chunks;   /* tab_batch_run: pieces the circuit list is cut into,
                              each compiled on the host while the device runs
-                             the one before; 0 = by size, else 1..64 */
+                             the one before; 0 = by size (five for large
+                             lists, a small first one), else 1..64 pieces of
+                             equal gate count */
   int32_t reserved;       /* 0 */
 } tab_config;
 /* Test-only: in every grid-resident measurement launch the last CTA skips its

@@ -90,6 +90,7 @@ _sig("tab_export", ctypes.c_int, [_vp, _vp, _vp, _vp])
 _sig("tab_import", ctypes.c_int, [_vp, _vp, _vp, _vp, _u64])
 _sig("tab_sync", ctypes.c_int, [_vp])
 _sig("tab_batch_run", ctypes.c_int, [_vp, _i32, _u64, _vp, _vp])
+_sig("tab_batch_run_packed", ctypes.c_int, [_vp, _i32, _u64, _vp, _i64, _vp])
 _sig("tab_batch_create", ctypes.c_int, [_vp, _i32, _P(_vp)])
 _sig("tab_batch_destroy", ctypes.c_int, [_vp])
 _sig("tab_batch_info", ctypes.c_int, [_vp, _P(_i64), _P(_i64), _P(_i64)])
@@ -500,14 +501,25 @@ def batch_run(circuits, seed: int = 1, out=None) -> list:
     `out`, a host uint8 array of at least the total outcome count, if given,
     e.g. in pinned memory)."""
     arr, keep = _circuit_array(circuits)
-    nms = _meas_counts(arr, len(circuits))
-    sizes = [shots * nm for (_, _, shots, _), nm in zip(circuits, nms)]
-    total = int(sum(sizes))
     if out is None:
+        nms = _meas_counts(arr, len(circuits))
+        total = int(sum(shots * nm for (_, _, shots, _), nm in zip(circuits, nms)))
         out = np.zeros(max(total, 1), np.uint8)
-    elif out.dtype != np.uint8 or out.size < total or not out.flags.c_contiguous:
-        raise ValueError("out must be a contiguous uint8 array of the total outcome count")
-    _check(_L.tab_batch_run(ctypes.cast(arr, _vp), len(circuits), seed, out.ctypes.data, None))
+        _check(_L.tab_batch_run(ctypes.cast(arr, _vp), len(circuits), seed, out.ctypes.data,
+                                None))
+    else:
+        # the library bounds the writes by out.size and returns the counts
+        if out.dtype != np.uint8 or not out.flags.c_contiguous:
+            raise ValueError("out must be a contiguous uint8 array")
+        nms = np.zeros(max(len(circuits), 1), np.int64)
+        code = _L.tab_batch_run_packed(ctypes.cast(arr, _vp), len(circuits), seed,
+                                       out.ctypes.data, out.size, nms.ctypes.data)
+        if code == TAB_ERANGE:
+            raise ValueError("out is smaller than the total outcome count: "
+                             + last_error())
+        _check(code)
+        nms = [int(v) for v in nms[:len(circuits)]]
+    sizes = [shots * nm for (_, _, shots, _), nm in zip(circuits, nms)]
     res, off = [], 0
     for (n, g, shots, _), sz in zip(circuits, sizes):
         res.append(out[off:off + sz].reshape(shots, -1) if sz else

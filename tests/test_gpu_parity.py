@@ -595,6 +595,43 @@ def test_batch_small_vs_oracle():
             assert np.array_equal(got[s], want), (n, cid, s)
 
 
+def test_batch_run_packed_capacity_and_counts():
+    """tab_batch_run_packed: the counts it returns are tab_meas_counts', the
+    bytes equal tab_batch_run's, and a buffer one byte short is refused with
+    TAB_ERANGE without a write past its end (chunks of two circuits, so the
+    refusal comes after earlier chunks ran)."""
+    rng = np.random.default_rng(5)
+    circuits = []
+    for c in range(12):
+        n = int(rng.integers(2, 70))
+        circ = C.random_layer_circuit(n, 6, seed=300 + c, meas_every=3, meas_frac=0.3)
+        circuits.append((n, circ.gates, int(rng.integers(1, 4)), 500 + c))
+    want = np.concatenate([r.reshape(-1) for r in tab.batch_run(circuits, seed=9)])
+    arr, keep = tab._circuit_array(circuits)
+    counts = tab._meas_counts(arr, len(circuits))
+    total = int(want.size)
+    old = tab.get_config()
+    try:
+        tab.set_config({"batch_chunks": 6})
+        out = np.full(total + 8, 0xA5, np.uint8)
+        got_counts = np.full(len(circuits), -1, np.int64)
+        tab._check(tab._L.tab_batch_run_packed(tab.ctypes.cast(arr, tab._vp), len(circuits), 9,
+                                               out.ctypes.data, total, got_counts.ctypes.data))
+        assert list(got_counts) == [int(v) for v in counts]
+        assert np.array_equal(out[:total], want) and (out[total:] == 0xA5).all()
+        short = np.full(total + 8, 0xA5, np.uint8)
+        rc = tab._L.tab_batch_run_packed(tab.ctypes.cast(arr, tab._vp), len(circuits), 9,
+                                         short.ctypes.data, total - 1, None)
+        assert rc == tab.TAB_ERANGE
+        assert (short[total - 1:] == 0xA5).all()
+        with pytest.raises(ValueError):
+            tab.batch_run(circuits, seed=9, out=np.zeros(total - 1, np.uint8))
+        assert tab._L.tab_batch_run_packed(tab.ctypes.cast(arr, tab._vp), len(circuits), 9,
+                                           out.ctypes.data, -1, None) == tab.TAB_EINVAL
+    finally:
+        tab.set_config(old)
+
+
 def test_batch_config4_sample():
     """A slice of the batched family (n up to 512) against the oracle."""
     circs = C.config4(only=list(range(0, 4096, 512)))
