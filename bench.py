@@ -68,7 +68,11 @@ PIVOT_SUPPORT = 0.75
 # ~3/4 n supported columns, X and Z planes, 2n/8 bytes each, read + written.
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # build, by kernel; None until a capture of the current build exists.
-TRAFFIC_BYTES = {}
+# k_batch: the four size-class launches of one step.  Captured on the
+# 512-circuit slice (294.3 MB over its four launches for 7.03e7 gates: the
+# compiled gate stream, the circuit images and the outcomes, all in
+# proportion to the gates), scaled to the full family's 5.52e8 gates.
+TRAFFIC_BYTES = {"k_batch": 294.3e6 * 551688025 / 70335522}
 
 
 def parse():
