@@ -72,7 +72,9 @@ PIVOT_SUPPORT = 0.75
 # 512-circuit slice (294.3 MB over its four launches for 7.03e7 gates: the
 # compiled gate stream, the circuit images and the outcomes, all in
 # proportion to the gates), scaled to the full family's 5.52e8 gates.
-TRAFFIC_BYTES = {"k_batch": 294.3e6 * 551688025 / 70335522}
+# k_measure_resident: one launch of the n=1000 step's 1,000 measurements
+# (profiles/k_measure_resident_n1000.md, 595.2 KB read, nothing written).
+TRAFFIC_BYTES = {"k_batch": 294.3e6 * 551688025 / 70335522, "k_measure_resident": 595.2e3}
 
 
 def parse():
