@@ -14,8 +14,9 @@ The JSON line carries, beside the batched (per-shot) value:
 * the plain path: the same circuits one launch sequence per shot
   (tab_run of a compiled program), timed on every 16th circuit and scaled;
 * the terminal-measurement sampler on the same batch (same outcome bytes);
-* e2e: tab_batch_run through the C ABI with host gate lists and a pinned host
-  output buffer (host compile, upload, run and the outcome copy per step);
+* e2e: tab_batch_run_packed (the batched run through the C ABI) with host
+  gate lists and a pinned host output buffer (host compile, upload, run and
+  the outcome copy per step);
 * the roofline of the batched kernel against the logic-op ceiling measured
   live by tab_measure_peaks;
 * the n = 1,000 plain tableau (1,000 layers, 1,000 final measurements) as an
@@ -696,8 +697,8 @@ def run_batched(args, ws, rank, local):
                            "every shot evaluated from its Philox bits"}
         sb.close()
 
-    # ---- end to end: tab_batch_run with host gate lists and a pinned host
-    # output buffer (host compile, upload, run, outcome copy) per step
+    # ---- end to end: tab_batch_run_packed with host gate lists and a pinned
+    # host output buffer (host compile, upload, run, outcome copy) per step
     e2e = None
     if not args.no_e2e:
         host_out = torch.empty(max(info["out_bytes"], 1), dtype=torch.uint8).pin_memory().numpy()
@@ -716,8 +717,10 @@ def run_batched(args, ws, rank, local):
                "host_input_bytes_per_step": int(sum(c.gates.nbytes for c in circs)),
                "ms_per_step": 1000.0 * e2e_s, "meas_per_s": ws * n_meas / e2e_s,
                "outcomes_equal_device_run": same_e2e,
-               "call": "tab_batch_run (compile on the host pool, upload, one persistent "
-                       "launch, outcome copy to pinned host memory)"}
+               "call": "tab.batch_run -> tab_batch_run_packed (chunks compiled on the host "
+                       "pool while the device runs the chunk before, uploads, the size-class "
+                       "launches of each chunk, per-chunk outcome copies to pinned host "
+                       "memory)"}
 
     # ---- roofline of the batched kernel: every circuit's gates once, every
     # shot's measurements counted as random-outcome rowsums
