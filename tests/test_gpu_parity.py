@@ -632,6 +632,35 @@ def test_batch_run_packed_capacity_and_counts():
         tab.set_config(old)
 
 
+def test_batch_run_degenerate_lists():
+    """Empty circuit lists, circuits without measurements between measured
+    ones, and a buffer of exactly the outcome count, in 1 and 3 chunks: the
+    bytes of the measured circuits equal the oracle's."""
+    assert tab.batch_run([], seed=3) == []
+    arr, keep = tab._circuit_array([])
+    assert tab._L.tab_batch_run_packed(tab.ctypes.cast(arr, tab._vp), 0, 3, None, 0,
+                                       None) == tab.TAB_OK
+    circuits = []
+    for c in range(6):
+        n = 5 + 7 * c
+        # odd circuits: gates only, no outcomes
+        circ = C.random_layer_circuit(n, 4, seed=900 + c, final_measure=c % 2 == 0)
+        circuits.append((n, circ.gates, 2, 700 + c))
+    old = tab.get_config()
+    try:
+        for chunks in (1, 3):
+            tab.set_config({"batch_chunks": chunks})
+            arr, keep = tab._circuit_array(circuits)
+            total = int(sum(2 * m for m in tab._meas_counts(arr, len(circuits))))
+            res = tab.batch_run(circuits, seed=3, out=np.zeros(total, np.uint8))
+            for (n, g, shots, cid), got in zip(circuits, res):
+                for sh in range(shots):
+                    want, _ = oracle.run_circuit(n, g, seed=3, circuit_id=cid, shot=sh)
+                    assert np.array_equal(got[sh], want), (n, cid, sh, chunks)
+    finally:
+        tab.set_config(old)
+
+
 def test_batch_config4_sample():
     """A slice of the batched family (n up to 512) against the oracle."""
     circs = C.config4(only=list(range(0, 4096, 512)))
