@@ -75,7 +75,11 @@ PIVOT_SUPPORT = 0.75
 # proportion to the gates), scaled to the full family's 5.52e8 gates.
 # k_measure_resident: one launch of the n=1000 step's 1,000 measurements
 # (profiles/k_measure_resident_n1000.md, 595.2 KB read, nothing written).
-TRAFFIC_BYTES = {"k_batch": 294.3e6 * 551688025 / 70335522, "k_measure_resident": 595.2e3}
+# k_measure: one step of the n=10,000 family, 10 launches (one per MZR
+# round) of 169.6 MB each (profiles/k_measure_n10000.md); its roofline's
+# algorithmic bytes are per step too.
+TRAFFIC_BYTES = {"k_batch": 294.3e6 * 551688025 / 70335522, "k_measure_resident": 595.2e3,
+                 "k_measure": 10 * 169.6e6}
 
 
 def parse():
