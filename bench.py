@@ -76,10 +76,10 @@ PIVOT_SUPPORT = 0.75
 # k_measure_resident: one launch of the n=1000 step's 1,000 measurements
 # (profiles/k_measure_resident_n1000.md, 595.2 KB read, nothing written).
 # k_measure: one step of the n=10,000 family, 10 launches (one per MZR
-# round) of 169.6 MB each (profiles/k_measure_n10000.md); its roofline's
+# round) of 173.1 MB each (profiles/k_measure_n10000.md); its roofline's
 # algorithmic bytes are per step too.
 TRAFFIC_BYTES = {"k_batch": 294.3e6 * 551688025 / 70335522, "k_measure_resident": 595.2e3,
-                 "k_measure": 10 * 169.6e6}
+                 "k_measure": 10 * 173.1e6}
 
 
 def parse():
@@ -548,11 +548,23 @@ def run_plain(args, ws, rank, local, name=None, steps=None, warmup=None, cpu=Tru
         kname = "k_sct_program" if eng_res == tab.ENGINE_SINGLE_CTA else "k_gates_block"
         alg = gate_ops(c)
     if kname == "k_measure":
-        # the streaming engine sweeps the tableau in HBM/L2: a random
-        # measurement reads and writes the ~3/4 n supported columns, 2 planes
-        # of 2n/8 bytes each (~0.75 n^2 bytes); the tableau (n^2/2 bytes)
-        # fits GB300's L2 up to n ~ 16,000, so both ceilings are given
-        alg_bytes = 0.75 * n * n * c.n_meas
+        # the streaming engine sweeps the tableau in HBM/L2.  Algorithmic
+        # bytes of one step, exactly, from the engine's work counters (one
+        # more step, untimed, counted): a random measurement reads the pivot
+        # column (n/8 B) and row p (2n/8 B) and reads and writes its pivot
+        # row's |supp(p)| columns, 2 planes of 2n/8 B each; a deterministic
+        # one reads its k multiplied rows (2n/8 B each).  The model that
+        # takes |supp(p)| = 3/4 n (0.75 n^2 bytes per measurement) is kept
+        # beside it.  The tableau (n^2/2 bytes) fits GB300's L2 up to
+        # n ~ 16,000, so both ceilings are given.
+        t.count_work(True)
+        step()
+        wc = t.work_counts()
+        t.count_work(False)
+        col = 2.0 * n / 8.0
+        alg_bytes = (wc["support_cols"] * 2 * col * 2 + wc["random"] * (n / 8.0 + col)
+                     + wc["det_rows"] * col)
+        model_bytes = 0.75 * n * n * c.n_meas
         achieved = alg_bytes / (kind_ms[dom] / 1000.0) / 1e9
         roof = {"kernel": kname, "bound": "hbm", "unit": "GB/s", "achieved": achieved,
                 "peak": pk["hbm_gbs"], "frac": achieved / pk["hbm_gbs"],
@@ -561,7 +573,10 @@ def run_plain(args, ws, rank, local, name=None, steps=None, warmup=None, cpu=Tru
                        "peak_source": "measured: read + write over a 64 MiB set, "
                                       "tab_measure_peaks"},
                 "traffic": TRAFFIC_BYTES.get(kname), "kernel_ms": kind_ms,
-                "alg_bytes_per_launch": alg_bytes}
+                "alg_bytes_per_launch": alg_bytes, "work_counts": wc,
+                "model": {"bytes": model_bytes,
+                          "achieved": model_bytes / (kind_ms[dom] / 1000.0) / 1e9,
+                          "note": "0.75 n^2 bytes per measurement (support 3/4 n)"}}
     else:
         roof = alu_roofline(kname, alg, kind_ms[dom], pk, {"kernel_ms": kind_ms})
 

@@ -302,6 +302,22 @@ int tab_transfer_bytes(tab_t h, int64_t* h2d, int64_t* d2h);
 /* Number of CUDA kernels this handle has launched since creation. */
 int tab_kernel_launches(tab_t h, int64_t *count);
 
+/* Work counters of the streaming measurement engine, for stating a run's
+ * algorithmic bytes exactly (the work model of AG Sec. III's measurement:
+ * a random outcome's rowsum touches the columns where the pivot row p is not
+ * I -- its support -- and a deterministic outcome multiplies the stabilizer
+ * rows n+i with x_ia = 1).  The paper has no counterpart.  tab_count_work(h,
+ * 1) zeroes the counters and starts counting on h's later streaming-engine
+ * runs (one atomic add per CTA and measurement); 0 stops it.  Other engines
+ * leave the counters alone.  tab_work_counts synchronizes h's stream and
+ * writes counts[0] = the support columns summed over random-outcome
+ * measurements, counts[1] = the rows multiplied summed over deterministic
+ * ones, counts[2] / counts[3] = the random / deterministic measurements
+ * counted (all 0 if counting never started).  TAB_ENOMEM when the 32-byte
+ * counter buffer cannot be allocated. */
+int tab_count_work(tab_t h, int32_t on);
+int tab_work_counts(tab_t h, int64_t *counts);
+
 /* ---- state transfer (checkpoint / oracle comparison) --------------------- */
 
 /* Synchronize and unpack the tableau into row-major host arrays: x and z of

@@ -54,6 +54,7 @@ struct MArgs {
   unsigned long long wait_ns;  // limit of each grid-barrier wait
   GridBar* bar;
   int* err;
+  unsigned long long* work;  // MeasWork::work (null: not counting)
 };
 
 // mod-4 bit-sliced add: (h, l) += (bh, bl)
@@ -215,6 +216,10 @@ __global__ void __launch_bounds__(kMeasThreads) k_measure(MArgs A) {
       }
       __syncthreads();
       const int nsupp = s_nsupp;
+      if (A.work && tid == 0) {  // work counters: this CTA's support columns
+        atomicAdd(A.work, (unsigned long long)nsupp);
+        if (c == 0) atomicAdd(A.work + 2, 1ull);
+      }
       // scalar added to every row in S': this CTA's share of
       // 2 r_p (= its partial of row p, plus the base for CTA 0) + sum x_pj z_pj
       uint32_t scal = (uint32_t)s_kc + (s_php & 1u) + 2u * (s_php >> 1);
@@ -331,6 +336,12 @@ __global__ void __launch_bounds__(kMeasThreads) k_measure(MArgs A) {
       // T = stabilizer rows n+i for destabilizers i in S; e = sum_{m in T}
       // (2 r_m + |x_m & z_m|) + 2 sum_{m<l in T} z_m . x_l  (mod 4)
       uint32_t acc = 0u;
+      if (A.work && c == 0) {  // work counters: the rows multiplied
+        uint32_t k = 0u;
+        for (int w = tid; w < Wh; w += blockDim.x) k += __popc(sS[w]);
+        if (k) atomicAdd(A.work + 1, (unsigned long long)k);
+        if (tid == 0) atomicAdd(A.work + 3, 1ull);
+      }
       for (int w = Wh + tid; w < W; w += blockDim.x) {
         const uint32_t t = sS[w - Wh];
         acc += __popc(PHlo[w] & t) + 2u * __popc(PHhi[w] & t);
@@ -442,6 +453,7 @@ cudaError_t launch_measure(uint32_t* X, uint32_t* Z, uint32_t* R, int n, int Wh,
   A.k0 = k0; A.seed = seed; A.cid = cid; A.shot = shot;
   A.out = out;
   A.ph = mw.ph; A.r4 = mw.r4; A.dp = mw.dp; A.bar = mw.bar; A.err = mw.err;
+  A.work = mw.work;
   A.wait_ns = run_wait_limit_ns();
   const size_t smem = meas_smem_bytes(n, A.W, ctas);
   cudaError_t e = ensure_smem_limit((const void*)k_measure, 200 * 1024);

@@ -83,6 +83,7 @@ struct tab_s {
   cudaEvent_t pipe_end = nullptr; // after the last copy out of the pinned buffers
   static constexpr int kPipeEv = 4;
   cudaEvent_t pipe_ev[kPipeEv] = {};  // ends of the pipelined apply's launches
+  unsigned long long* workc = nullptr;  // work counters (tab_count_work), 4 words
 };
 
 struct tab_prog_s {
@@ -609,6 +610,7 @@ int tab_destroy(tab_t h) {
   for (uint2* p : h->pipe_pin)
     if (p) cudaFreeHost(p);
   if (h->pipe_end) cudaEventDestroy(h->pipe_end);
+  if (h->workc) cudaFree(h->workc);
   delete h;
   return TAB_OK;
 }
@@ -1319,6 +1321,39 @@ int tab_sync(tab_t h) {
   int rc = check_handle(h);
   if (rc) return rc;
   return poll_device_error(h);
+}
+
+int tab_count_work(tab_t h, int32_t on) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (on && !h->workc) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaMalloc of the work counters failed");
+      return TAB_ENOMEM;
+    }
+    h->workc = static_cast<unsigned long long*>(p);
+  }
+  if (on) CU(cudaMemsetAsync(h->workc, 0, 4 * sizeof(unsigned long long), h->stream));
+  h->mw.work = on ? h->workc : nullptr;
+  return TAB_OK;
+}
+
+int tab_work_counts(tab_t h, int64_t* counts) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!counts) {
+    set_error("null output");
+    return TAB_EINVAL;
+  }
+  unsigned long long v[4] = {0ull, 0ull, 0ull, 0ull};
+  if (h->workc) {
+    CU(cudaMemcpyAsync(v, h->workc, sizeof v, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  }
+  for (int i = 0; i < 4; ++i) counts[i] = (int64_t)v[i];
+  return TAB_OK;
 }
 
 }  // extern "C"

@@ -198,6 +198,10 @@ struct MeasWork {
   GridBar* bar;
   int* err;
   int max_ctas;
+  // work counters (tab_count_work; null: off): [0] support columns of the
+  // random-outcome pivot rows, [1] stabilizer rows the deterministic
+  // outcomes multiply, [2] random and [3] deterministic measurements
+  unsigned long long* work = nullptr;
 };
 
 // ---- launches (kernels_*.cu) ---------------------------------------------------------

@@ -82,6 +82,8 @@ _sig("tab_sharded_read_outcomes", ctypes.c_int, [_vp, _vp, _i64, _P(_i64)])
 _sig("tab_sharded_export", ctypes.c_int, [_vp, _vp, _vp, _vp])
 _sig("tab_clear_outcomes", ctypes.c_int, [_vp])
 _sig("tab_kernel_launches", ctypes.c_int, [_vp, _P(_i64)])
+_sig("tab_count_work", ctypes.c_int, [_vp, _i32])
+_sig("tab_work_counts", ctypes.c_int, [_vp, _P(_i64)])
 _sig("tab_set_engine", ctypes.c_int, [_vp, ctypes.c_int])
 _sig("tab_engine_resolved", ctypes.c_int, [_vp, _P(ctypes.c_int), _P(ctypes.c_int)])
 _sig("tab_transfer_bytes", ctypes.c_int, [_vp, _P(_i64), _P(_i64)])
@@ -391,6 +393,16 @@ class Tableau:
         c = _i64()
         _check(_L.tab_kernel_launches(self._h, ctypes.byref(c)))
         return c.value
+
+    def count_work(self, on: bool = True):
+        """Start (zeroing them) or stop the streaming engine's work counters."""
+        _check(_L.tab_count_work(self._h, 1 if on else 0))
+
+    def work_counts(self) -> dict:
+        """The work counters (tab_work_counts)."""
+        c = (_i64 * 4)()
+        _check(_L.tab_work_counts(self._h, c))
+        return {"support_cols": c[0], "det_rows": c[1], "random": c[2], "deterministic": c[3]}
 
     # -- state transfer
     def export(self):

@@ -661,6 +661,47 @@ def test_batch_run_degenerate_lists():
         tab.set_config(old)
 
 
+def test_streaming_work_counters():
+    """The streaming engine's work counters against their definition on the
+    state each measurement meets: a random outcome adds its pivot row's
+    support (columns where stabilizer row p, the first with x_pa = 1, is not
+    I), a deterministic one the destabilizer rows i with x_ia = 1.  The
+    state before each measurement is exported and the measurement then run
+    alone; counting off leaves the counters unchanged."""
+    n = 40
+    # H then two Z measurements of qubit 0: support 1, then one row
+    with tab.Tableau(n) as t:
+        t.set_engine(tab.ENGINE_STREAM)
+        t.count_work(True)
+        t.apply(np.array([_gate(C.TAB_H, 0), _gate(C.TAB_MZ, 0), _gate(C.TAB_MZ, 0)], np.uint64))
+        assert t.work_counts() == {"support_cols": 1, "det_rows": 1, "random": 1,
+                                   "deterministic": 1}
+    circ = C.random_layer_circuit(n, 6, seed=4242, final_measure=False)
+    rng = np.random.default_rng(7)
+    with tab.Tableau(n) as t:
+        t.set_engine(tab.ENGINE_STREAM)
+        t.set_rng(seed=5, circuit_id=1, shot=0)
+        t.apply(circ.gates)
+        t.count_work(True)
+        want = {"support_cols": 0, "det_rows": 0, "random": 0, "deterministic": 0}
+        for a in rng.integers(0, n, 24):
+            x, z, _ = t.export()
+            piv = np.nonzero(x[n:, a])[0]
+            if piv.size:
+                p = n + int(piv[0])
+                want["support_cols"] += int(np.count_nonzero(x[p] | z[p]))
+                want["random"] += 1
+            else:
+                want["det_rows"] += int(np.count_nonzero(x[:n, a]))
+                want["deterministic"] += 1
+            t.apply(np.array([_gate(C.TAB_MZ if a % 3 else C.TAB_MZR, int(a))], np.uint64))
+        assert want["random"] > 0 and want["deterministic"] > 0
+        assert t.work_counts() == want
+        t.count_work(False)
+        t.apply(np.array([_gate(C.TAB_MZ, 0)], np.uint64))
+        assert t.work_counts() == want
+
+
 def test_batch_config4_sample():
     """A slice of the batched family (n up to 512) against the oracle."""
     circs = C.config4(only=list(range(0, 4096, 512)))
