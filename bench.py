@@ -70,7 +70,7 @@ PIVOT_SUPPORT = 0.75
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # build, by kernel; None until a capture of the current build exists.
 # k_batch: the four size-class launches of one step.  Captured on the
-# 512-circuit slice (294.3 MB over its four launches for 7.03e7 gates: the
+# 512-circuit slice (294.9 MB over its four launches for 7.03e7 gates: the
 # compiled gate stream, the circuit images and the outcomes, all in
 # proportion to the gates), scaled to the full family's 5.52e8 gates.
 # k_measure_resident: one launch of the n=1000 step's 1,000 measurements
@@ -78,7 +78,7 @@ PIVOT_SUPPORT = 0.75
 # k_measure: one step of the n=10,000 family, 10 launches (one per MZR
 # round) of 173.1 MB each (profiles/k_measure_n10000.md); its roofline's
 # algorithmic bytes are per step too.
-TRAFFIC_BYTES = {"k_batch": 294.3e6 * 551688025 / 70335522, "k_measure_resident": 595.2e3,
+TRAFFIC_BYTES = {"k_batch": 294.9e6 * 551688025 / 70335522, "k_measure_resident": 595.2e3,
                  "k_measure": 10 * 173.1e6}
 
 
@@ -540,10 +540,32 @@ def run_plain(args, ws, rank, local, name=None, steps=None, warmup=None, cpu=Tru
     dom = max(kind_ms, key=kind_ms.get)
     n = c.n
     eng_res = t.engine_resolved()[0]
+    extra = None
     if dom == "measure":
         kname = {tab.ENGINE_SINGLE_CTA: "k_sct_program", tab.ENGINE_GRID: "k_measure_resident",
                  tab.ENGINE_STREAM: "k_measure"}[eng_res]
         alg = meas_ops(n, c.n_meas)
+        if kname != "k_measure":
+            # exact logic ops: MEAS_OPS_PER_UNIT per (support column, 32-row
+            # word) of the random-outcome rowsums, the supports counted by the
+            # streaming engine's work counters on one untimed step (every
+            # engine meets the same tableaus, bit for bit); the model that
+            # takes every measurement as random with a support of 3/4 n is
+            # kept beside it
+            with tab.Tableau(c.n, stream=stream) as tw:
+                tw.set_engine(tab.ENGINE_STREAM)
+                tw.count_work(True)
+                tw.reset()
+                tw.set_rng(C.PHILOX_SEED, rank, 0)
+                for prog in progs:
+                    tw.run(prog)
+                wcnt = tw.work_counts()
+            model = alg
+            alg = MEAS_OPS_PER_UNIT * wcnt["support_cols"] * 2.0 * ((n + 31) // 32)
+            extra = {"work_counts": wcnt,
+                     "model": {"ops": model,
+                               "frac": model / (kind_ms[dom] / 1000.0) / 1e12 / pk["logic_tops"],
+                               "note": "every measurement random, support 3/4 n"}}
     else:
         kname = "k_sct_program" if eng_res == tab.ENGINE_SINGLE_CTA else "k_gates_block"
         alg = gate_ops(c)
@@ -578,7 +600,7 @@ def run_plain(args, ws, rank, local, name=None, steps=None, warmup=None, cpu=Tru
                           "achieved": model_bytes / (kind_ms[dom] / 1000.0) / 1e9,
                           "note": "0.75 n^2 bytes per measurement (support 3/4 n)"}}
     else:
-        roof = alu_roofline(kname, alg, kind_ms[dom], pk, {"kernel_ms": kind_ms})
+        roof = alu_roofline(kname, alg, kind_ms[dom], pk, dict({"kernel_ms": kind_ms}, **(extra or {})))
 
     line = {
         "metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": ws,
@@ -741,11 +763,25 @@ def run_batched(args, ws, rank, local):
                        "launches of each chunk, per-chunk outcome copies to pinned host "
                        "memory)"}
 
-    # ---- roofline of the batched kernel: every circuit's gates once, every
-    # shot's measurements counted as random-outcome rowsums
-    ops = sum(gate_ops(c) + c.shots * meas_ops(c.n, c.n_meas) for c in circs)
-    roof = alu_roofline("k_batch", ops, statistics.mean(per), pk,
-                        {"smem_gbs_peak": pk["smem_gbs"],
+    # ---- roofline of the batched kernel: every circuit's gates once, and
+    # every shot's random-outcome rowsums at MEAS_OPS_PER_UNIT per (support
+    # column, 32-row word), the supports counted on the device by one more,
+    # untimed replay with the kernel's work counters on.  The model that
+    # takes every measurement as random with a support of 3/4 n is kept
+    # beside it.
+    b.count_work(True)
+    b.exec(C.PHILOX_SEED, out.data_ptr(), stream)
+    torch.cuda.synchronize()
+    work = b.work_counts()
+    b.count_work(False)
+    ops = sum(gate_ops(c) for c in circs) + MEAS_OPS_PER_UNIT * work["support_words"]
+    model_ops = sum(gate_ops(c) + c.shots * meas_ops(c.n, c.n_meas) for c in circs)
+    k_ms = statistics.mean(per)
+    roof = alu_roofline("k_batch", ops, k_ms, pk,
+                        {"smem_gbs_peak": pk["smem_gbs"], "work_counts": work,
+                         "model": {"ops": model_ops,
+                                   "frac": model_ops / (k_ms / 1000.0) / 1e12 / pk["logic_tops"],
+                                   "note": "every measurement random, support 3/4 n"},
                          "note": "per-shot tableaus live in shared memory; the compiled batch "
                                  "streams from HBM once per step"})
 

@@ -423,6 +423,20 @@ int tab_batch_classes(tab_batch_t b, int32_t *count);
 int tab_batch_class(tab_batch_t b, int32_t k, tab_batch_class_info *out);
 /* Number of kernels one tab_batch_exec launches (one per non-empty class). */
 int tab_batch_launches(tab_batch_t b, int64_t *count);
+/* Work counters of the batched kernel (as tab_count_work, for stating a
+ * run's algorithmic work exactly; the paper has no counterpart).
+ * tab_batch_count_work(b, 1) zeroes them and makes b's later execs count:
+ * those launch the kernel's counting instances (one atomic add per
+ * measurement) one size class after another, outside the batch's graph,
+ * and the timed instances carry no counting code; 0 stops it.
+ * tab_batch_work_counts, once those runs have finished, writes counts[0] =
+ * the random-outcome measurements' pivot-row supports, each times its
+ * tableau's 32-row words per column (2 ceil(n/32)), summed over every
+ * (circuit, shot); counts[1] = the rows the deterministic outcomes multiply,
+ * times the same words per column; counts[2] / counts[3] = the random /
+ * deterministic measurements (all 0 if counting never started). */
+int tab_batch_count_work(tab_batch_t b, int32_t on);
+int tab_batch_work_counts(tab_batch_t b, int64_t *counts);
 /* Autotuner: runs each size class's launch alone once per CTA size the
  * persistent kernel is built for (128, 256, 512 or 1024 threads per CTA;
  * shared memory sized to the class's largest tableau; as many CTAs as fit on

@@ -75,6 +75,7 @@ struct tab_batch_s {
   size_t ctl_bytes = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  unsigned long long* workc = nullptr;  // work counters (tab_batch_count_work), 4 words
 };
 
 namespace {
@@ -519,7 +520,40 @@ int tab_batch_destroy(tab_batch_t B) {
   if (B->gexec) cudaGraphExecDestroy(B->gexec);
   if (B->graph) cudaGraphDestroy(B->graph);
   if (B->dmem) cudaFree(B->dmem);
+  if (B->workc) cudaFree(B->workc);
   delete B;
+  return TAB_OK;
+}
+
+int tab_batch_count_work(tab_batch_t B, int32_t on) {
+  if (!B) {
+    set_error("null batch");
+    return TAB_EINVAL;
+  }
+  if (on && !B->workc) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaMalloc of the work counters failed");
+      return TAB_ENOMEM;
+    }
+    B->workc = static_cast<unsigned long long*>(p);
+  }
+  if (on) CUB(cudaMemset(B->workc, 0, 4 * sizeof(unsigned long long)));
+  unsigned long long* w = on ? B->workc : nullptr;
+  B->args.work = w;
+  for (auto& K : B->cls) K.args.work = w;
+  return TAB_OK;
+}
+
+int tab_batch_work_counts(tab_batch_t B, int64_t* counts) {
+  if (!B || !counts) {
+    set_error("null argument");
+    return TAB_EINVAL;
+  }
+  unsigned long long v[4] = {0ull, 0ull, 0ull, 0ull};
+  if (B->workc) CUB(cudaMemcpy(v, B->workc, sizeof v, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < 4; ++i) counts[i] = (int64_t)v[i];
   return TAB_OK;
 }
 
@@ -570,6 +604,16 @@ int tab_batch_exec(tab_batch_t B, uint64_t seed, uint8_t* dev_out, void* cuda_st
   for (auto& K : B->cls) {
     K.args.seed = seed;
     K.args.out = dev_out;
+  }
+  if (B->args.work) {  // counting: the counting instances, one class after another
+    CUB(cudaMemsetAsync(B->ctl, 0, B->ctl_bytes, st));
+    for (auto& K : B->cls) {
+      if (K.args.nitems == 0) continue;
+      void* kargs[] = {&K.args};
+      CUB(cudaLaunchKernel(batch_kernel_ptr(K.threads, true), dim3(K.ctas), dim3(K.threads), kargs,
+                           K.smem, st));
+    }
+    return TAB_OK;
   }
   if (!B->gexec) {
     int rc = make_graph(B);

@@ -68,11 +68,13 @@ struct Sct {
   int n, Whc, Wc, Wp, GG;
   uint32_t *X, *Z, *R, *sS, *supp, *redlo, *redhi;  // supp: [3][n] (X, Z, Y columns)
   int* err;  // the launch's error word (debug-build index checks)
+  unsigned long long* work;  // BatchArgs::work (null: not counting)
 };
 
 __device__ __forceinline__ void sct_setup(Sct& s, uint32_t* base, int n, int* err) {
   s.n = n;
   s.err = err;
+  s.work = nullptr;
   s.Whc = sct_whc(n);
   s.Wc = 2 * s.Whc;
   s.Wp = s.Wc | 1;
@@ -165,6 +167,9 @@ __device__ void sct_gates(const Sct& s, const uint32_t* __restrict__ ops,
 // are final once the rowsum is done) inside its last phase, and sets *pre;
 // the next call, given *pre, skips that phase and its barrier.
 constexpr uint32_t kNoNext = 0xFFFFFFFFu;
+// kCount: instances that update the work counters (s.work) are separate
+// from the ones timed, which carry no counting code.
+template <bool kCount = false>
 __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err,
                            uint32_t next_code = kNoNext, bool* pre = nullptr) {
   __shared__ int s_pw;
@@ -242,6 +247,10 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err,
     __syncthreads();
     const uint32_t cnt = s_cnt;
     const int nx = (int)(cnt & 1023u), nz = (int)((cnt >> 10) & 1023u), ny = (int)((cnt >> 20) & 1023u);
+    if (kCount && s.work && tid == 0) {  // work counters: the pivot row's support
+      atomicAdd(s.work, (unsigned long long)(nx + nz + ny) * (unsigned long long)Wc);
+      atomicAdd(s.work + 2, 1ull);
+    }
     const int g = tid / Wc, w = tid - g * Wc;
     if (g < s.GG) {
       // per row h of this word: rows in S' (x_ha = 1, h != p, p-n) take
@@ -366,6 +375,12 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err,
     return (int)rbit;
   }
   // ---------------- deterministic outcome ----------------
+  if (kCount && s.work && tid == 0) {  // work counters: the rows multiplied
+    uint32_t k = 0u;
+    for (int hw = 0; hw < Whc; ++hw) k += __popc(s.sS[hw]);
+    atomicAdd(s.work + 1, (unsigned long long)k * (unsigned long long)Wc);
+    atomicAdd(s.work + 3, 1ull);
+  }
   const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;  // (random case returned above)
   const uint32_t lt = (1u << lane) - 1u;
   uint32_t acc = 0u;
@@ -417,6 +432,7 @@ __device__ int sct_measure(const Sct& s, uint32_t code, uint32_t rbit, int* err,
 //
 // forms[i*(1+FW)]: bit 0 = measurement i is random (outcome b_i), bit 1 =
 // constant of a deterministic outcome; words 1..FW: its coefficients.
+template <bool kCount = false>
 __device__ void sct_form_pass(const Sct& s, const uint32_t* __restrict__ ops, uint32_t op_begin,
                               int K, uint32_t* F, int* fpl, uint32_t* forms, int FW, int* err) {
   __shared__ int s_fpw, s_nf;
@@ -428,7 +444,7 @@ __device__ void sct_form_pass(const Sct& s, const uint32_t* __restrict__ ops, ui
   for (int i = 0; i < K; ++i) {
     const uint32_t code = __ldg(ops + op_begin + i);
     // X|Z bits, pivot, mask and the constant parts of the signs, with b_i = 0
-    const int c = sct_measure(s, code, 0u, err);
+    const int c = sct_measure<kCount>(s, code, 0u, err);
     // s.sS still holds the measured column's X plane before the measurement
     if (tid < 32) {
       const uint32_t v = (tid < Whc) ? s.sS[Whc + tid] : 0u;
@@ -555,6 +571,7 @@ __device__ void sct_store_global(const Sct& s, uint32_t* X, uint32_t* Z, uint32_
 
 // Run segments [seg_begin, seg_end) of a program on the resident tableau.
 // Outcome k of this run goes to out[k]; k0 is the first measurement index.
+template <bool kCount = false>
 __device__ void sct_run_segments(const Sct& s, const Seg* __restrict__ segs, int seg_begin,
                                  int seg_end, const uint32_t* __restrict__ ops,
                                  const uint32_t* __restrict__ layer_off, uint64_t seed,
@@ -583,7 +600,7 @@ __device__ void sct_run_segments(const Sct& s, const Seg* __restrict__ segs, int
           __syncthreads();
         }
         const uint32_t rbit = (s_rbits >> t) & 1u;
-        const int m = sct_measure(s, code, rbit, err, next_code, &pre);
+        const int m = sct_measure<kCount>(s, code, rbit, err, next_code, &pre);
         if (threadIdx.x == 0) out[o] = (uint8_t)m;
         ++k;
         ++o;
@@ -621,7 +638,7 @@ cudaError_t launch_sct_program(const SctProgArgs& A, cudaStream_t st) {
 // Items are dequeued in order from one atomic counter; every prefix item is
 // dequeued before any shot item, and prefix items never wait, so every wait
 // ends.  Waits are bounded anyway and latch DERR_TIMEOUT.
-template <int T>
+template <int T, bool kCount>
 __global__ void __launch_bounds__(T) k_batch(BatchArgs A) {
   extern __shared__ uint32_t smem[];
   __shared__ unsigned int s_item;
@@ -644,6 +661,7 @@ __global__ void __launch_bounds__(T) k_batch(BatchArgs A) {
     const BatchCirc C = A.circs[ci];
     Sct s;
     sct_setup(s, smem, C.n, A.err);
+    s.work = kCount ? A.work : nullptr;
     uint32_t* img = A.img + C.img_off;
     if (shot == 0xFFFFFFFFu) {
       sct_identity(s);
@@ -658,7 +676,7 @@ __global__ void __launch_bounds__(T) k_batch(BatchArgs A) {
         int* fpl = reinterpret_cast<int*>(F + (size_t)K * s.Wp);
         uint32_t* Bs = reinterpret_cast<uint32_t*>(fpl + K);
         const Seg g = A.segs[C.seg_begin + C.n_prefix];
-        sct_form_pass(s, A.ops, g.op_begin, K, F, fpl, img, FW, A.err);
+        sct_form_pass<kCount>(s, A.ops, g.op_begin, K, F, fpl, img, FW, A.err);
         __syncthreads();
         sct_sample(img, K, FW, C.shots, seed, C.cid, out + C.out_off, Bs);
         __syncthreads();
@@ -706,7 +724,7 @@ __global__ void __launch_bounds__(T) k_batch(BatchArgs A) {
         npauli[j] = p;
       }
       __syncthreads();
-      sct_run_segments(s, A.segs, (int)(C.seg_begin + C.n_prefix), (int)C.seg_end, A.ops,
+      sct_run_segments<kCount>(s, A.segs, (int)(C.seg_begin + C.n_prefix), (int)C.seg_end, A.ops,
                        A.layer_off, seed, C.cid, shot, 0,
                        out + C.out_off + (uint64_t)shot * C.n_meas, A.err, npauli);
     }
@@ -716,24 +734,29 @@ __global__ void __launch_bounds__(T) k_batch(BatchArgs A) {
 
 // Thread counts the batched kernel is built for; the autotuner
 // (tab_batch_tune) times each on the batch itself.
-static const void* batch_kernel_for(int threads) {
+static const void* batch_kernel_for(int threads, bool count = false) {
   switch (threads) {
-    case 128: return (const void*)k_batch<128>;
-    case 256: return (const void*)k_batch<256>;
-    case 512: return (const void*)k_batch<512>;
-    case 1024: return (const void*)k_batch<1024>;
+    case 128: return count ? (const void*)k_batch<128, true> : (const void*)k_batch<128, false>;
+    case 256: return count ? (const void*)k_batch<256, true> : (const void*)k_batch<256, false>;
+    case 512: return count ? (const void*)k_batch<512, true> : (const void*)k_batch<512, false>;
+    case 1024: return count ? (const void*)k_batch<1024, true> : (const void*)k_batch<1024, false>;
     default: return nullptr;
   }
 }
 
-const void* batch_kernel_ptr(int threads) { return batch_kernel_for(threads); }
+const void* batch_kernel_ptr(int threads, bool count) { return batch_kernel_for(threads, count); }
 
 cudaError_t prepare_batch_kernel(int threads) {
-  const void* fn = batch_kernel_for(threads);
-  if (!fn) return cudaErrorInvalidValue;
-  // the largest tableau, or a sampled circuit's tableau plus its forms
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              227 * 1024 - 2048);
+  // the largest tableau, or a sampled circuit's tableau plus its forms; both
+  // instances (timed and counting)
+  for (const bool count : {false, true}) {
+    const void* fn = batch_kernel_for(threads, count);
+    if (!fn) return cudaErrorInvalidValue;
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               227 * 1024 - 2048);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // Resident CTAs per SM for `threads` and `smem` bytes (0: does not launch).

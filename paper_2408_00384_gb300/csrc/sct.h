@@ -52,6 +52,11 @@ struct BatchArgs {
   int* err;
   uint64_t seed;  // Philox key of this run
   uint8_t* out;   // outcome buffer of this run
+  // work counters (tab_batch_count_work; null: off): [0] the pivot rows'
+  // support columns times the tableau's words per column, over random
+  // outcomes, [1] the rows multiplied times the words per column, over
+  // deterministic ones, [2] / [3] random / deterministic measurements
+  unsigned long long* work = nullptr;
 };
 
 size_t sct_image_words(int n);
@@ -65,6 +70,8 @@ constexpr int kBatchThreadChoices[4] = {128, 256, 512, 1024};
 constexpr int kBatchDefaultThreads = 512;
 int batch_ctas_per_sm(int threads, size_t smem);
 cudaError_t prepare_batch_kernel(int threads);
-const void* batch_kernel_ptr(int threads);
+// The batched kernel for `threads`; `count`: the instance that updates the
+// work counters (BatchArgs::work).
+const void* batch_kernel_ptr(int threads, bool count = false);
 
 }  // namespace tab

@@ -98,6 +98,8 @@ _sig("tab_batch_destroy", ctypes.c_int, [_vp])
 _sig("tab_batch_info", ctypes.c_int, [_vp, _P(_i64), _P(_i64), _P(_i64)])
 _sig("tab_batch_exec", ctypes.c_int, [_vp, _u64, _vp, _vp])
 _sig("tab_batch_launches", ctypes.c_int, [_vp, _P(_i64)])
+_sig("tab_batch_count_work", ctypes.c_int, [_vp, _i32])
+_sig("tab_batch_work_counts", ctypes.c_int, [_vp, _P(_i64)])
 _sig("tab_batch_tune", ctypes.c_int, [_vp, _u64, _vp, _vp, _P(_i32), _P(ctypes.c_float)])
 _sig("tab_batch_config", ctypes.c_int, [_vp, _P(_i32), _P(_i32), _P(_i64)])
 _sig("tab_batch_create_ex", ctypes.c_int, [_vp, _i32, _u32, _P(_vp)])
@@ -616,6 +618,18 @@ class Batch:
         c = _i64()
         _check(_L.tab_batch_launches(self._h, ctypes.byref(c)))
         return c.value
+
+    def count_work(self, on: bool = True):
+        """Start (zeroing them) or stop the batched kernel's work counters."""
+        _check(_L.tab_batch_count_work(self._h, 1 if on else 0))
+
+    def work_counts(self) -> dict:
+        """The work counters (tab_batch_work_counts), once the counted runs
+        have finished."""
+        c = (_i64 * 4)()
+        _check(_L.tab_batch_work_counts(self._h, c))
+        return {"support_words": c[0], "det_row_words": c[1], "random": c[2],
+                "deterministic": c[3]}
 
     @property
     def h2d_bytes(self) -> int:

@@ -702,6 +702,47 @@ def test_streaming_work_counters():
         assert t.work_counts() == want
 
 
+def test_batch_work_counters_match_streaming():
+    """The batched kernel's work counters equal, per (circuit, shot), the
+    streaming engine's counts on the same circuit (pinned to their definition
+    above) times the tableau's 32-row words per column: the X|Z evolution,
+    and so every pivot row's support, is the same in every shot.  Counting
+    off leaves them unchanged."""
+    import torch
+    rng = np.random.default_rng(3)
+    circuits = []
+    for c in range(10):
+        n = int(rng.integers(3, 70))
+        circ = C.random_layer_circuit(n, 5, seed=1300 + c, meas_every=2, meas_frac=0.3)
+        circuits.append((n, circ.gates, int(rng.integers(1, 4)), 40 + c))
+    want = {"support_words": 0, "det_row_words": 0, "random": 0, "deterministic": 0}
+    for n, g, shots, cid in circuits:
+        with tab.Tableau(n) as t:
+            t.set_engine(tab.ENGINE_STREAM)
+            t.set_rng(seed=2, circuit_id=cid, shot=0)
+            t.count_work(True)
+            t.apply(g)
+            w = t.work_counts()
+        words = 2 * ((n + 31) // 32)
+        want["support_words"] += shots * words * w["support_cols"]
+        want["det_row_words"] += shots * words * w["det_rows"]
+        want["random"] += shots * w["random"]
+        want["deterministic"] += shots * w["deterministic"]
+    assert want["random"] > 0 and want["deterministic"] > 0
+    b = tab.Batch(circuits)
+    out = torch.zeros(max(b.info()["out_bytes"], 1), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    b.count_work(True)
+    b.exec(9, out.data_ptr(), stream)
+    torch.cuda.synchronize()
+    assert b.work_counts() == want
+    b.count_work(False)
+    b.exec(9, out.data_ptr(), stream)
+    torch.cuda.synchronize()
+    assert b.work_counts() == want
+    b.close()
+
+
 def test_batch_config4_sample():
     """A slice of the batched family (n up to 512) against the oracle."""
     circs = C.config4(only=list(range(0, 4096, 512)))
