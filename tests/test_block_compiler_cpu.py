@@ -1,9 +1,14 @@
-"""Host logic of the block gate compiler, without a GPU.
+"""Host logic of the gate compilers, without a GPU.
 
-The C++ check in tests/cpp compiles random gate lists into two-qubit blocks
-with the library's own compiler (program.cpp, blocks.cpp), applies the blocks
-to random 32-row words with the device kernel's block formulas, and compares
-with the gates applied one at a time by the Aaronson-Gottesman rules.
+The C++ checks in tests/cpp compile random gate lists with the library's own
+compiler (program.cpp, blocks.cpp):
+* into two-qubit blocks, applied to random 32-row words with the device
+  kernel's block formulas and compared with the gates applied one at a time
+  by the Aaronson-Gottesman rules;
+* into ASAP layers (the form the single-CTA and batched engines run),
+  checked against the list: segments, codes, per-qubit order, each gate's
+  ASAP layer computed independently, disjoint qubits within a layer, the
+  noise table.
 """
 import os
 import shutil
@@ -31,6 +36,22 @@ def test_block_compiler_matches_gate_rules(tmp_path):
     exe = str(tmp_path / "block_compiler_check")
     cmd = [cxx, "-O2", "-std=c++17", "-pthread", "-I", inc, "-I", CSRC, "-I", os.path.join(ROOT, "include"),
            os.path.join(HERE, "cpp", "block_compiler_check.cpp"),
+           os.path.join(CSRC, "program.cpp"), os.path.join(CSRC, "blocks.cpp"),
+           os.path.join(CSRC, "pool.cpp"), "-o", exe]
+    subprocess.run(cmd, check=True, capture_output=True, text=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "bad 0" in r.stdout
+
+
+def test_layer_compiler_matches_list(tmp_path):
+    cxx = shutil.which("g++")
+    inc = _cuda_include()
+    if cxx is None or inc is None:
+        pytest.skip("needs g++ and the CUDA headers")
+    exe = str(tmp_path / "layer_compiler_check")
+    cmd = [cxx, "-O2", "-std=c++17", "-pthread", "-I", inc, "-I", CSRC, "-I", os.path.join(ROOT, "include"),
+           os.path.join(HERE, "cpp", "layer_compiler_check.cpp"),
            os.path.join(CSRC, "program.cpp"), os.path.join(CSRC, "blocks.cpp"),
            os.path.join(CSRC, "pool.cpp"), "-o", exe]
     subprocess.run(cmd, check=True, capture_output=True, text=True)
