@@ -720,18 +720,7 @@ static int batch_run(const tab_circuit* circuits, int32_t m, uint64_t seed, uint
   // chunk boundaries by gate count: chunk 0 takes first_share of the gates,
   // the others equal parts of the rest
   const double first_share = K <= 1 ? 1.0 : cfg_chunks > 0 ? 1.0 / K : kFirstChunkShare;
-  std::vector<int32_t> cut(1, 0);
-  int64_t before = 0;
-  for (int32_t c = 0, k = 1; c < m && k < K; ++c) {
-    before += std::max<int64_t>(circuits[c].n_gates, 0);
-    const double target =
-        (double)gates * (first_share + (1.0 - first_share) * (double)(k - 1) / (double)(K - 1));
-    if ((double)before >= target) {
-      cut.push_back(c + 1);
-      ++k;
-    }
-  }
-  if (cut.back() != m) cut.push_back(m);
+  const std::vector<int32_t> cut = batch_chunk_cuts(circuits, m, K, first_share);
   // Output.  Caller's offsets: one device buffer spanning them all (sized
   // from the measurement counts first), spans copied back at the end.
   // Packed: each chunk's outcomes are packed in a device buffer of its own

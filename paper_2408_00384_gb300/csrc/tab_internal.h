@@ -253,6 +253,30 @@ void set_error(const char* fmt, ...);
 // settings, and the grid-barrier wait limit in effect.
 constexpr unsigned long long kDefaultWaitLimitNs = 2000000000ull;  // 2 s
 constexpr int kMaxBatchChunks = 64;  // tab_config.batch_chunks upper bound
+
+// tab_batch_run's chunks of a circuit list: contiguous runs of circuits cut
+// where the running gate count first reaches each target -- first_share of
+// all gates for the first chunk, then equal parts of the rest -- so at most
+// K chunks, none empty.  Returns the bounds: 0, ..., m (one entry, 0, for
+// m = 0).
+inline std::vector<int32_t> batch_chunk_cuts(const tab_circuit* circuits, int32_t m, int K,
+                                             double first_share) {
+  int64_t gates = 0;
+  for (int32_t c = 0; c < m; ++c) gates += circuits[c].n_gates > 0 ? circuits[c].n_gates : 0;
+  std::vector<int32_t> cut(1, 0);
+  int64_t before = 0;
+  for (int32_t c = 0, k = 1; c < m && k < K; ++c) {
+    before += circuits[c].n_gates > 0 ? circuits[c].n_gates : 0;
+    const double target =
+        (double)gates * (first_share + (1.0 - first_share) * (double)(k - 1) / (double)(K - 1));
+    if ((double)before >= target) {
+      cut.push_back(c + 1);
+      ++k;
+    }
+  }
+  if (cut.back() != m) cut.push_back(m);
+  return cut;
+}
 tab_config run_config();
 unsigned long long run_wait_limit_ns();
 

@@ -9,6 +9,7 @@ compiler (program.cpp, blocks.cpp):
   checked against the list: segments, codes, per-qubit order, each gate's
   ASAP layer computed independently, disjoint qubits within a layer, the
   noise table.
+A third check covers tab_batch_run's chunking of a circuit list.
 """
 import os
 import shutil
@@ -54,6 +55,20 @@ def test_layer_compiler_matches_list(tmp_path):
            os.path.join(HERE, "cpp", "layer_compiler_check.cpp"),
            os.path.join(CSRC, "program.cpp"), os.path.join(CSRC, "blocks.cpp"),
            os.path.join(CSRC, "pool.cpp"), "-o", exe]
+    subprocess.run(cmd, check=True, capture_output=True, text=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "bad 0" in r.stdout
+
+
+def test_batch_chunk_cuts(tmp_path):
+    cxx = shutil.which("g++")
+    inc = _cuda_include()
+    if cxx is None or inc is None:
+        pytest.skip("needs g++ and the CUDA headers")
+    exe = str(tmp_path / "chunk_cuts_check")
+    cmd = [cxx, "-O2", "-std=c++17", "-I", inc, "-I", CSRC, "-I", os.path.join(ROOT, "include"),
+           os.path.join(HERE, "cpp", "chunk_cuts_check.cpp"), "-o", exe]
     subprocess.run(cmd, check=True, capture_output=True, text=True)
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
